@@ -1,0 +1,709 @@
+// Diamond-sampling oracle: a plain, slow, single-threaded CPU statement of
+// what the GPU library computes.  TEST INFRASTRUCTURE ONLY: the tests, the
+// smoke check and the CPU-baseline leg of the benchmark load it; the product
+// path never does.  It shares no source with the CUDA library.
+//
+// Paper: Ballard, Kolda, Pinar, Seshadhri, "Diamond Sampling for Approximate
+// Maximum All-pairs Dot-product (MAD) Search", arXiv:1506.03872.
+//
+// Orientation.  A is m x d with rows a_i, B is d x n with rows b_k* and
+// columns b_j, C = AB, c_ij = sum_k a_ik b_kj.  The paper writes A^T B with
+// vectors as columns (Sec. 2); its a_ki is our a_ik.
+//
+// Every step below follows Alg. 2 (general diamond sampling) and Alg. 3
+// (postprocessing), with the numeric readings that the paper leaves open
+// written out where they are used:
+//   * weights are FP32, row sums use one fixed summation order
+//     (canonical_sum_f32), products are rounded to FP32 before summing;
+//   * the sampling distributions are held as integer prefix tables whose
+//     entries are the FP32 weights scaled by a power of two and rounded to
+//     nearest-even (a nonzero weight that rounds to 0 becomes 1);
+//   * the center edge (i,k) ~ w_ik/||W||_1 is drawn in two stages: row i with
+//     probability r_i/sum r, r_i = ||a_i*||_1 * sum_k |a_ik| ||b_k*||_1, then
+//     k within row i proportional to |a_ik| ||b_k*||_1 (same joint law);
+//   * a draw maps a 64-bit uniform u to target = floor(u*T/2^64) and returns
+//     the first position whose inclusive prefix exceeds target;
+//   * uniforms come from Philox4x32-10 with key = seed, counter =
+//     (l_lo, l_hi, instance, block) for diamond index l;
+//   * the increment sgn(a_ik b_kj a_ik') b_k'j is accumulated in int64 fixed
+//     point: b_k'j (as FP32) times 2^F rounded to nearest-even;
+//   * 0/1 CSR inputs run in exact integer mode (no scaling at all).
+//
+// Parity is pinned by the tests: Philox known-answer vectors, Lemma 1 and
+// Lemma 2 closed forms, the binary diamond count c_ij^2, brute-force top-t
+// and long-double dot products.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+enum { FMT_DENSE = 0, FMT_CSR = 1 };
+enum { DT_F32 = 0, DT_F64 = 1, DT_BINARY = 2 };
+enum { FL_NONNEG = 1u, FL_GRAM = 2u, FL_EXCLUDE_DIAG = 4u };
+enum {
+  ST_OK = 0, ST_ARG = 1, ST_OVERFLOW = 4, ST_EMPTY = 5, ST_UNSUPPORTED = 8
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC'11).  Ten rounds; each round multiplies words 0 and 2
+// by the two round multipliers, swaps in the high halves XORed with the other
+// words and the round key; the key is bumped by the two Weyl constants
+// between rounds.
+// ---------------------------------------------------------------------------
+void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const uint64_t p0 = (uint64_t)M0 * (uint64_t)x0;
+    const uint64_t p1 = (uint64_t)M1 * (uint64_t)x2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t y0 = hi1 ^ x1 ^ k0;
+    const uint32_t y1 = lo1;
+    const uint32_t y2 = hi0 ^ x3 ^ k1;
+    const uint32_t y3 = lo0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+// The four 64-bit uniforms of diamond l: u[0] picks i, u[1] picks k,
+// u[2] picks j, u[3] picks k'.
+void diamond_uniforms(uint64_t seed, uint64_t ell, uint32_t instance, uint64_t u[4]) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (uint32_t block = 0; block < 2; ++block) {
+    const uint32_t ctr[4] = {(uint32_t)ell, (uint32_t)(ell >> 32), instance, block};
+    uint32_t w[4];
+    philox4x32_10(ctr, key, w);
+    u[2 * block + 0] = ((uint64_t)w[1] << 32) | w[0];
+    u[2 * block + 1] = ((uint64_t)w[3] << 32) | w[2];
+  }
+}
+
+// floor(u * total / 2^64): the draw target in [0, total).
+uint64_t draw_target(uint64_t u, uint64_t total) {
+  return (uint64_t)(((unsigned __int128)u * (unsigned __int128)total) >> 64);
+}
+
+// Inverse-CDF search (Sec. 4.1): first position whose inclusive prefix
+// exceeds target.  std::upper_bound is the library search primitive.
+template <typename T>
+int64_t inverse_cdf(const T* prefix, int64_t len, uint64_t target) {
+  const T* p = std::upper_bound(prefix, prefix + len, (T)target,
+                                [](T t, T v) { return (uint64_t)t < (uint64_t)v; });
+  return (int64_t)(p - prefix);
+}
+
+// Fixed FP32 summation order used for every L1 norm and row sum: 256
+// partial sums, partial q taking the elements whose index is q mod 256 in
+// ascending order, then folded in halves (q += q+128, then q += q+64, ...,
+// q += q+1).  FP32 round-to-nearest-even, no fused operations.
+float canonical_sum_f32(const std::vector<float>& w) {
+  float part[256];
+  for (int q = 0; q < 256; ++q) part[q] = 0.0f;
+  for (size_t idx = 0; idx < w.size(); ++idx) {
+    part[idx % 256] = part[idx % 256] + w[idx];
+  }
+  for (int h = 128; h >= 1; h /= 2)
+    for (int q = 0; q < h; ++q) {
+      part[q] = part[q] + part[q + h];
+    }
+  return part[0];
+}
+
+// ceil(log2(x)) for x >= 1.
+int ceil_log2(uint64_t x) {
+  int e = 0;
+  while (e < 64 && ((uint64_t)1 << e) < x) ++e;
+  return e;
+}
+
+// Row table exponent: the largest power of two keeping the scaled row sum
+// below 2^30, so the row's prefix stays below 2^31 (bit 31 stays free).
+int row_exponent(float rowsum) { return 29 - std::ilogb(rowsum); }
+
+uint32_t quantize_row(float w, int e) {
+  const double q = std::rint(std::ldexp((double)w, e));
+  uint32_t v = (uint32_t)q;
+  if (w > 0.0f && v == 0) v = 1;  // keep the support of the paper's distribution
+  return v;
+}
+
+struct Mat {
+  int64_t rows = 0, cols = 0;
+  std::vector<int64_t> ptr;    // rows+1
+  std::vector<int32_t> col;    // stored entries, ascending within a row
+  std::vector<double> val;     // values as given (1.0 for binary)
+  std::vector<float> valf;     // values rounded to FP32
+  bool dense = false, binary = false;
+};
+
+bool load_matrix(int fmt, int dt, int64_t rows, int64_t cols, int64_t ld, const void* values,
+                 const int64_t* rowptr, const int32_t* colidx, Mat& M) {
+  M.rows = rows;
+  M.cols = cols;
+  M.ptr.assign(rows + 1, 0);
+  M.dense = (fmt == FMT_DENSE);
+  M.binary = (dt == DT_BINARY);
+  if (fmt == FMT_DENSE) {
+    if (dt == DT_BINARY || ld < cols) return false;
+    for (int64_t r = 0; r < rows; ++r) {
+      M.ptr[r + 1] = M.ptr[r] + cols;
+      for (int64_t c = 0; c < cols; ++c) {
+        const double v = (dt == DT_F64) ? ((const double*)values)[r * ld + c]
+                                        : (double)((const float*)values)[r * ld + c];
+        M.col.push_back((int32_t)c);
+        M.val.push_back(v);
+        M.valf.push_back((float)v);
+      }
+    }
+    return true;
+  }
+  if (fmt != FMT_CSR || dt != DT_BINARY || rowptr[0] != 0) return false;
+  for (int64_t r = 0; r < rows; ++r) {
+    M.ptr[r + 1] = rowptr[r + 1];
+    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+      M.col.push_back(colidx[e]);
+      M.val.push_back(1.0);
+      M.valf.push_back(1.0f);
+    }
+  }
+  return true;
+}
+
+struct Oracle {
+  uint32_t flags = 0;
+  bool integer = false;
+  uint64_t s_max = 0;
+  Mat A, B;
+  int64_t m = 0, d = 0, n = 0;
+  // Float-mode norms and row weights.
+  std::vector<float> na, nb, srow, r;
+  // Tables: T1 over rows of A; T2, TA aligned with A's entries; TB with B's.
+  std::vector<uint64_t> T1;
+  std::vector<uint32_t> T2, TA, TB;
+  int E1 = 0, F = 0;
+  uint64_t bumps = 0;
+  // Sampling state.
+  std::unordered_map<uint64_t, int64_t> X;
+  uint64_t sampled = 0, inserted = 0, diag_skipped = 0;
+};
+
+int build_tables(Oracle& o) {
+  const Mat& A = o.A;
+  const Mat& B = o.B;
+  o.m = A.rows;
+  o.d = A.cols;
+  o.n = B.cols;
+  if (B.rows != o.d || o.m <= 0 || o.d <= 0 || o.n <= 0) return ST_ARG;
+  if (o.m > 0xFFFFFFFFll || o.n > 0xFFFFFFFFll) return ST_ARG;
+  o.T1.assign(o.m, 0);
+  o.T2.assign(A.col.size(), 0);
+  o.TA.assign(A.col.size(), 0);
+  o.TB.assign(B.col.size(), 0);
+
+  if (o.integer) {
+    // Exact integer mode for 0/1 inputs (Alg. 1): w_ik = deg_i^A deg_k^B.
+    // T2 holds deg_k^B along row i, TA and TB hold 1 per neighbour.
+    unsigned __int128 total = 0;
+    for (int64_t k = 0; k < o.d; ++k) {
+      uint32_t p = 0;
+      for (int64_t e = B.ptr[k]; e < B.ptr[k + 1]; ++e) o.TB[e] = ++p;
+    }
+    for (int64_t i = 0; i < o.m; ++i) {
+      uint64_t p2 = 0;
+      uint32_t pa = 0;
+      for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+        const int32_t k = A.col[e];
+        p2 += (uint64_t)(B.ptr[k + 1] - B.ptr[k]);
+        if (p2 > 0xFFFFFFFFull) return ST_OVERFLOW;
+        o.T2[e] = (uint32_t)p2;
+        o.TA[e] = ++pa;
+      }
+      const uint64_t ri = (uint64_t)(A.ptr[i + 1] - A.ptr[i]) * p2;
+      total += ri;
+      if (total >= ((unsigned __int128)1 << 63)) return ST_OVERFLOW;
+      o.T1[i] = (uint64_t)total;
+    }
+    if (total == 0) return ST_EMPTY;
+    o.E1 = 0;
+    o.F = 0;
+    return ST_OK;
+  }
+
+  // Float mode.  L1 norms (Alg. 2 weight line): ||b_k*||_1 and ||a_i*||_1.
+  o.nb.assign(o.d, 0.0f);
+  float maxb = 0.0f;
+  for (int64_t k = 0; k < o.d; ++k) {
+    std::vector<float> w;
+    for (int64_t e = B.ptr[k]; e < B.ptr[k + 1]; ++e) {
+      w.push_back(std::fabs(B.valf[e]));
+      maxb = std::max(maxb, std::fabs(B.valf[e]));
+    }
+    o.nb[k] = canonical_sum_f32(w);
+    if (o.nb[k] > 0.0f) {
+      const int e = row_exponent(o.nb[k]);
+      uint32_t p = 0;
+      for (size_t q = 0; q < w.size(); ++q) {
+        const uint32_t v = quantize_row(w[q], e);
+        if (w[q] > 0.0f && std::rint(std::ldexp((double)w[q], e)) == 0.0) ++o.bumps;
+        p += v;
+        o.TB[B.ptr[k] + q] = p;
+      }
+    }
+  }
+  o.na.assign(o.m, 0.0f);
+  o.srow.assign(o.m, 0.0f);
+  o.r.assign(o.m, 0.0f);
+  float maxr = 0.0f;
+  for (int64_t i = 0; i < o.m; ++i) {
+    std::vector<float> wa, w2;
+    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+      const float a = std::fabs(A.valf[e]);
+      const float prod = a * o.nb[A.col[e]];
+      wa.push_back(a);
+      w2.push_back(prod);
+    }
+    o.na[i] = canonical_sum_f32(wa);
+    o.srow[i] = canonical_sum_f32(w2);
+    o.r[i] = o.na[i] * o.srow[i];
+    maxr = std::max(maxr, o.r[i]);
+    if (o.srow[i] > 0.0f) {
+      const int e2 = row_exponent(o.srow[i]);
+      const int ea = row_exponent(o.na[i]);
+      uint32_t p2 = 0, pa = 0;
+      for (size_t q = 0; q < w2.size(); ++q) {
+        if (w2[q] > 0.0f && std::rint(std::ldexp((double)w2[q], e2)) == 0.0) ++o.bumps;
+        if (wa[q] > 0.0f && std::rint(std::ldexp((double)wa[q], ea)) == 0.0) ++o.bumps;
+        p2 += quantize_row(w2[q], e2);
+        pa += quantize_row(wa[q], ea);
+        o.T2[A.ptr[i] + q] = p2;
+        o.TA[A.ptr[i] + q] = pa;
+      }
+    }
+  }
+  if (maxr == 0.0f || maxb == 0.0f) return ST_EMPTY;
+  // T1: r_i scaled so that every entry is below 2^(62 - ceil(log2 m)); the
+  // whole prefix then stays below 2^62.
+  o.E1 = 62 - ceil_log2((uint64_t)o.m) - (std::ilogb(maxr) + 1);
+  uint64_t p1 = 0;
+  for (int64_t i = 0; i < o.m; ++i) {
+    const double q = std::rint(std::ldexp((double)o.r[i], o.E1));
+    uint64_t v = (uint64_t)q;
+    if (o.r[i] > 0.0f && v == 0) {
+      v = 1;
+      ++o.bumps;
+    }
+    p1 += v;
+    o.T1[i] = p1;
+  }
+  // Increment scale: |b| 2^F < 2^(62 - ceil(log2 s_max)), so s_max
+  // increments cannot overflow int64.
+  o.F = 62 - ceil_log2(std::max<uint64_t>(o.s_max, 1)) - (std::ilogb(maxb) + 1);
+  return ST_OK;
+}
+
+// Value b_{k'j} of B (0 when absent).
+double b_value(const Oracle& o, int64_t kp, int64_t j, float* valf) {
+  const Mat& B = o.B;
+  if (B.dense) {
+    const int64_t e = B.ptr[kp] + j;
+    *valf = B.valf[e];
+    return B.val[e];
+  }
+  const int32_t* lo = B.col.data() + B.ptr[kp];
+  const int32_t* hi = B.col.data() + B.ptr[kp + 1];
+  const int32_t* p = std::lower_bound(lo, hi, (int32_t)j);
+  if (p != hi && *p == (int32_t)j) {
+    *valf = B.valf[p - B.col.data()];
+    return B.val[p - B.col.data()];
+  }
+  *valf = 0.0f;
+  return 0.0;
+}
+
+struct Draw {
+  uint32_t i, k, j, kp;
+  int64_t v;
+};
+
+// One iteration of the sampling loop of Alg. 2 for diamond index ell.
+Draw draw_diamond(const Oracle& o, uint64_t seed, uint64_t ell) {
+  uint64_t u[4];
+  diamond_uniforms(seed, ell, 0, u);
+  const Mat& A = o.A;
+  const Mat& B = o.B;
+  Draw dr;
+  // Center edge (i,k) with probability w_ik / ||W||_1, in two stages.
+  const int64_t i = inverse_cdf(o.T1.data(), o.m, draw_target(u[0], o.T1[o.m - 1]));
+  const int64_t a0 = A.ptr[i], alen = A.ptr[i + 1] - A.ptr[i];
+  const int64_t pk = inverse_cdf(o.T2.data() + a0, alen, draw_target(u[1], o.T2[a0 + alen - 1]));
+  const int64_t k = A.col[a0 + pk];
+  // j with probability |b_kj| / ||b_k*||_1.
+  const int64_t b0 = B.ptr[k], blen = B.ptr[k + 1] - B.ptr[k];
+  const int64_t pj = inverse_cdf(o.TB.data() + b0, blen, draw_target(u[2], o.TB[b0 + blen - 1]));
+  const int64_t j = B.col[b0 + pj];
+  // k' with probability |a_ik'| / ||a_i*||_1.
+  const int64_t pkp = inverse_cdf(o.TA.data() + a0, alen, draw_target(u[3], o.TA[a0 + alen - 1]));
+  const int64_t kp = A.col[a0 + pkp];
+  // Increment sgn(a_ik b_kj a_ik') b_k'j.
+  float bf = 0.0f;
+  b_value(o, kp, j, &bf);
+  int64_t v;
+  if (o.integer) {
+    v = (bf != 0.0f) ? 1 : 0;
+  } else {
+    v = (int64_t)std::llrint(std::ldexp((double)bf, o.F));
+    if (!(o.flags & FL_NONNEG)) {
+      int sgn = 1;
+      if (A.valf[a0 + pk] < 0.0f) sgn = -sgn;
+      if (B.valf[b0 + pj] < 0.0f) sgn = -sgn;
+      if (A.valf[a0 + pkp] < 0.0f) sgn = -sgn;
+      v *= sgn;
+    }
+  }
+  dr.i = (uint32_t)i;
+  dr.k = (uint32_t)k;
+  dr.j = (uint32_t)j;
+  dr.kp = (uint32_t)kp;
+  dr.v = v;
+  return dr;
+}
+
+uint64_t pair_key(const Oracle& o, uint64_t i, uint64_t j) {
+  if ((o.flags & FL_GRAM) && j < i) std::swap(i, j);
+  return (i << 32) | j;
+}
+
+// Dot product c_ij in FP64 with the fixed order shared by the library:
+// 32 partial sums (partial L takes k = L mod 32, ascending, fused
+// multiply-add), folded in halves (L += L+16, ..., L += L+1).
+double dense_dot(const Oracle& o, uint32_t i, uint32_t j) {
+  double part[32];
+  for (int L = 0; L < 32; ++L) part[L] = 0.0;
+  for (int64_t k = 0; k < o.d; ++k) {
+    const double a = o.A.val[o.A.ptr[i] + k];
+    const double b = o.B.val[o.B.ptr[k] + j];
+    part[k % 32] = std::fma(a, b, part[k % 32]);
+  }
+  for (int h = 16; h >= 1; h /= 2)
+    for (int L = 0; L < h; ++L) part[L] = part[L] + part[L + h];
+  return part[0];
+}
+
+// 0/1 CSR: c_ij = |{k : a_ik = 1 and b_kj = 1}|, counted exactly.
+double csr_dot(const Oracle& o, uint32_t i, uint32_t j) {
+  int64_t count = 0;
+  for (int64_t e = o.A.ptr[i]; e < o.A.ptr[i + 1]; ++e) {
+    float bf;
+    b_value(o, o.A.col[e], j, &bf);
+    if (bf != 0.0f) ++count;
+  }
+  return (double)count;
+}
+
+struct Scored {
+  uint64_t key;
+  double c;
+};
+
+bool by_abs_c(const Scored& a, const Scored& b) {
+  const double x = std::fabs(a.c), y = std::fabs(b.c);
+  if (x != y) return x > y;
+  return a.key < b.key;
+}
+
+}  // namespace
+
+extern "C" {
+
+void or_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  philox4x32_10(ctr, key, out);
+}
+
+void or_diamond_uniforms(uint64_t seed, uint64_t ell, uint32_t instance, uint64_t* u) {
+  diamond_uniforms(seed, ell, instance, u);
+}
+
+void* or_create(int fmtA, int dtA, int64_t m, int64_t d, int64_t ldA, const void* valA,
+                const int64_t* ptrA, const int32_t* colA, int fmtB, int dtB, int64_t dB,
+                int64_t n, int64_t ldB, const void* valB, const int64_t* ptrB,
+                const int32_t* colB, uint32_t flags, uint64_t s_max, int* status) {
+  Oracle* o = new Oracle();
+  o->flags = flags;
+  o->s_max = s_max;
+  if (!load_matrix(fmtA, dtA, m, d, ldA, valA, ptrA, colA, o->A) ||
+      !load_matrix(fmtB, dtB, dB, n, ldB, valB, ptrB, colB, o->B) ||
+      (dtA == DT_BINARY) != (dtB == DT_BINARY)) {
+    *status = ST_UNSUPPORTED;
+    delete o;
+    return nullptr;
+  }
+  o->integer = (dtA == DT_BINARY);
+  *status = build_tables(*o);
+  if (*status != ST_OK) {
+    delete o;
+    return nullptr;
+  }
+  return o;
+}
+
+void or_destroy(void* h) { delete (Oracle*)h; }
+
+// Table export.  which: 0 T1 (u64, m), 1 T2 (u32, nnz A), 2 TA (u32, nnz A),
+// 3 TB (u32, nnz B), 4 na (f32, m), 5 nb (f32, d), 6 r (f32, m),
+// 7 srow (f32, m).  Returns the element count.
+int64_t or_table(void* h, int which, void* out) {
+  Oracle* o = (Oracle*)h;
+  switch (which) {
+    case 0: if (out) std::memcpy(out, o->T1.data(), o->T1.size() * 8); return (int64_t)o->T1.size();
+    case 1: if (out) std::memcpy(out, o->T2.data(), o->T2.size() * 4); return (int64_t)o->T2.size();
+    case 2: if (out) std::memcpy(out, o->TA.data(), o->TA.size() * 4); return (int64_t)o->TA.size();
+    case 3: if (out) std::memcpy(out, o->TB.data(), o->TB.size() * 4); return (int64_t)o->TB.size();
+    case 4: if (out) std::memcpy(out, o->na.data(), o->na.size() * 4); return (int64_t)o->na.size();
+    case 5: if (out) std::memcpy(out, o->nb.data(), o->nb.size() * 4); return (int64_t)o->nb.size();
+    case 6: if (out) std::memcpy(out, o->r.data(), o->r.size() * 4); return (int64_t)o->r.size();
+    case 7: if (out) std::memcpy(out, o->srow.data(), o->srow.size() * 4); return (int64_t)o->srow.size();
+  }
+  return -1;
+}
+
+// Scalars: E1, F, bumps, T1 total, sampled, inserted, diag_skipped, |X|.
+void or_scalars(void* h, int64_t* out) {
+  Oracle* o = (Oracle*)h;
+  out[0] = o->E1;
+  out[1] = o->F;
+  out[2] = (int64_t)o->bumps;
+  out[3] = (int64_t)o->T1[o->m - 1];
+  out[4] = (int64_t)o->sampled;
+  out[5] = (int64_t)o->inserted;
+  out[6] = (int64_t)o->diag_skipped;
+  out[7] = (int64_t)o->X.size();
+}
+
+// Draws of diamonds first .. first+count-1 (no accumulation).
+void or_draw(void* h, uint64_t seed, uint64_t first, uint64_t count, uint32_t* oi, uint32_t* ok,
+             uint32_t* oj, uint32_t* okp, int64_t* ov) {
+  Oracle* o = (Oracle*)h;
+  for (uint64_t q = 0; q < count; ++q) {
+    const Draw dr = draw_diamond(*o, seed, first + q);
+    oi[q] = dr.i;
+    ok[q] = dr.k;
+    oj[q] = dr.j;
+    okp[q] = dr.kp;
+    ov[q] = dr.v;
+  }
+}
+
+// Draws of an arbitrary list of diamond indices (sampled parity checks).
+void or_draw_list(void* h, uint64_t seed, uint64_t count, const uint64_t* ells, uint32_t* oi,
+                  uint32_t* ok, uint32_t* oj, uint32_t* okp, int64_t* ov) {
+  Oracle* o = (Oracle*)h;
+  for (uint64_t q = 0; q < count; ++q) {
+    const Draw dr = draw_diamond(*o, seed, ells[q]);
+    oi[q] = dr.i;
+    ok[q] = dr.k;
+    oj[q] = dr.j;
+    okp[q] = dr.kp;
+    ov[q] = dr.v;
+  }
+}
+
+// The sampling loop of Alg. 2 for diamonds first .. first+s-1, accumulating
+// into X.  Gram inputs (B = A^T, Sec. 3.2.2) accumulate into the unordered
+// pair, which is twice the symmetrised X of Eq. (xsym) and orders the same;
+// the diagonal is skipped when asked (Sec. 6.2, distinct pairs only).
+int or_sample(void* h, uint64_t s, uint64_t seed, uint64_t first) {
+  Oracle* o = (Oracle*)h;
+  if (o->sampled + s > o->s_max) return ST_OVERFLOW;
+  for (uint64_t q = 0; q < s; ++q) {
+    const Draw dr = draw_diamond(*o, seed, first + q);
+    if ((o->flags & FL_EXCLUDE_DIAG) && dr.i == dr.j) {
+      ++o->diag_skipped;
+      continue;
+    }
+    if (dr.v == 0) continue;
+    o->X[pair_key(*o, dr.i, dr.j)] += dr.v;
+    ++o->inserted;
+  }
+  o->sampled += s;
+  return ST_OK;
+}
+
+void or_reset(void* h) {
+  Oracle* o = (Oracle*)h;
+  o->X.clear();
+  o->sampled = o->inserted = o->diag_skipped = 0;
+}
+
+// X in ascending key order; returns |X| (entries with x = 0 included).
+int64_t or_x_export(void* h, uint64_t* keys, int64_t* vals) {
+  Oracle* o = (Oracle*)h;
+  std::vector<std::pair<uint64_t, int64_t>> all(o->X.begin(), o->X.end());
+  std::sort(all.begin(), all.end());
+  if (keys)
+    for (size_t q = 0; q < all.size(); ++q) {
+      keys[q] = all[q].first;
+      vals[q] = all[q].second;
+    }
+  return (int64_t)all.size();
+}
+
+// Alg. 3, first step: Omega_s = {x > 0}; the t' largest by (x desc,
+// key asc).  Returns |Omega_t'| <= t'.
+int64_t or_topk(void* h, uint64_t tprime, uint64_t* keys, int64_t* xs) {
+  Oracle* o = (Oracle*)h;
+  std::vector<std::pair<uint64_t, int64_t>> pos;
+  for (const auto& kv : o->X)
+    if (kv.second > 0) pos.push_back(kv);
+  std::sort(pos.begin(), pos.end(), [](const std::pair<uint64_t, int64_t>& a,
+                                       const std::pair<uint64_t, int64_t>& b) {
+    if (a.second != b.second) return a.second > b.second;
+    return a.first < b.first;
+  });
+  const size_t cnt = std::min<size_t>(pos.size(), tprime);
+  for (size_t q = 0; q < cnt; ++q) {
+    keys[q] = pos[q].first;
+    xs[q] = pos[q].second;
+  }
+  return (int64_t)cnt;
+}
+
+// Alg. 3, dot products of the candidates: FP64 for dense inputs, exact
+// counts for 0/1 CSR inputs.
+void or_rescore(void* h, int64_t count, const uint64_t* keys, double* c) {
+  Oracle* o = (Oracle*)h;
+  for (int64_t q = 0; q < count; ++q) {
+    const uint32_t i = (uint32_t)(keys[q] >> 32), j = (uint32_t)keys[q];
+    c[q] = o->integer ? csr_dot(*o, i, j) : dense_dot(*o, i, j);
+  }
+}
+
+// Alg. 3, last step: the t largest by (|c| desc, key asc).
+int64_t or_topt(int64_t count, const uint64_t* keys, const double* c, uint64_t t,
+                uint64_t* out_keys, double* out_c) {
+  std::vector<Scored> v(count);
+  for (int64_t q = 0; q < count; ++q) v[q] = {keys[q], c[q]};
+  std::sort(v.begin(), v.end(), by_abs_c);
+  const int64_t cnt = std::min<int64_t>(count, (int64_t)t);
+  for (int64_t q = 0; q < cnt; ++q) {
+    out_keys[q] = v[q].key;
+    out_c[q] = v[q].c;
+  }
+  return cnt;
+}
+
+// Exact top-t by brute force over all pairs (ground truth of Defn. 1):
+// long-double sequential dot products, (|c| desc, key asc).  Gram inputs
+// enumerate unordered pairs; the diagonal is skipped when asked.
+int64_t or_bruteforce(void* h, uint64_t t, uint64_t* out_keys, double* out_c) {
+  Oracle* o = (Oracle*)h;
+  std::vector<long double> bcol(o->d);
+  std::vector<Scored> best;
+  std::vector<long double> dense_b;
+  // Column j of B as a dense vector (both formats).
+  std::vector<std::vector<std::pair<int32_t, double>>> bcols(o->n);
+  for (int64_t k = 0; k < o->d; ++k)
+    for (int64_t e = o->B.ptr[k]; e < o->B.ptr[k + 1]; ++e)
+      if (o->B.val[e] != 0.0) bcols[o->B.col[e]].push_back({(int32_t)k, o->B.val[e]});
+  std::vector<long double> arow(o->d, 0.0L);
+  for (int64_t i = 0; i < o->m; ++i) {
+    std::fill(arow.begin(), arow.end(), 0.0L);
+    for (int64_t e = o->A.ptr[i]; e < o->A.ptr[i + 1]; ++e) arow[o->A.col[e]] = o->A.val[e];
+    for (int64_t j = 0; j < o->n; ++j) {
+      if ((o->flags & FL_GRAM) && j < i) continue;
+      if ((o->flags & FL_EXCLUDE_DIAG) && j == i) continue;
+      long double acc = 0.0L;
+      for (const auto& kb : bcols[j]) acc += arow[kb.first] * (long double)kb.second;
+      best.push_back({((uint64_t)i << 32) | (uint64_t)j, (double)acc});
+    }
+    if (best.size() > 4 * t + 4096) {
+      std::nth_element(best.begin(), best.begin() + t, best.end(), by_abs_c);
+      best.resize(t);
+    }
+  }
+  std::sort(best.begin(), best.end(), by_abs_c);
+  const int64_t cnt = std::min<int64_t>((int64_t)best.size(), (int64_t)t);
+  for (int64_t q = 0; q < cnt; ++q) {
+    out_keys[q] = best[q].key;
+    out_c[q] = best[q].c;
+  }
+  return cnt;
+}
+
+// Lemma 1 / Lemma 2 enumerator for tiny instances: the exact probability of
+// every three-path (k', i, k, j) under the oracle's tables and its
+// increment.  Writes up to cap rows (i, k, j, k', prob, v) and returns the
+// number of three-paths with nonzero probability.
+int64_t or_enumerate(void* h, int64_t cap, uint32_t* oi, uint32_t* ok, uint32_t* oj,
+                     uint32_t* okp, double* prob, int64_t* ov) {
+  Oracle* o = (Oracle*)h;
+  const Mat& A = o->A;
+  const Mat& B = o->B;
+  int64_t cnt = 0;
+  const long double T1tot = (long double)o->T1[o->m - 1];
+  for (int64_t i = 0; i < o->m; ++i) {
+    const uint64_t qi = o->T1[i] - (i ? o->T1[i - 1] : 0);
+    if (qi == 0) continue;
+    const int64_t a0 = A.ptr[i], alen = A.ptr[i + 1] - a0;
+    const long double t2 = (long double)o->T2[a0 + alen - 1];
+    const long double ta = (long double)o->TA[a0 + alen - 1];
+    for (int64_t pk = 0; pk < alen; ++pk) {
+      const uint32_t qk = o->T2[a0 + pk] - (pk ? o->T2[a0 + pk - 1] : 0);
+      if (qk == 0) continue;
+      const int64_t k = A.col[a0 + pk];
+      const int64_t b0 = B.ptr[k], blen = B.ptr[k + 1] - b0;
+      const long double tb = (long double)o->TB[b0 + blen - 1];
+      for (int64_t pj = 0; pj < blen; ++pj) {
+        const uint32_t qj = o->TB[b0 + pj] - (pj ? o->TB[b0 + pj - 1] : 0);
+        if (qj == 0) continue;
+        const int64_t j = B.col[b0 + pj];
+        for (int64_t pkp = 0; pkp < alen; ++pkp) {
+          const uint32_t qkp = o->TA[a0 + pkp] - (pkp ? o->TA[a0 + pkp - 1] : 0);
+          if (qkp == 0) continue;
+          const int64_t kp = A.col[a0 + pkp];
+          if (cnt < cap) {
+            float bf = 0.0f;
+            b_value(*o, kp, j, &bf);
+            int64_t v;
+            if (o->integer) {
+              v = bf != 0.0f ? 1 : 0;
+            } else {
+              v = (int64_t)std::llrint(std::ldexp((double)bf, o->F));
+              if (!(o->flags & FL_NONNEG)) {
+                int sgn = 1;
+                if (A.valf[a0 + pk] < 0.0f) sgn = -sgn;
+                if (B.valf[b0 + pj] < 0.0f) sgn = -sgn;
+                if (A.valf[a0 + pkp] < 0.0f) sgn = -sgn;
+                v *= sgn;
+              }
+            }
+            oi[cnt] = (uint32_t)i;
+            ok[cnt] = (uint32_t)k;
+            oj[cnt] = (uint32_t)j;
+            okp[cnt] = (uint32_t)kp;
+            prob[cnt] = (double)(((long double)qi / T1tot) * ((long double)qk / t2) *
+                                 ((long double)qj / tb) * ((long double)qkp / ta));
+            ov[cnt] = v;
+          }
+          ++cnt;
+        }
+      }
+    }
+  }
+  return cnt;
+}
+
+}  // extern "C"

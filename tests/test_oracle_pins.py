@@ -1,0 +1,364 @@
+"""Pins of the CPU oracle to facts fixed outside it (no GPU).
+
+Each test checks the oracle against something it cannot agree with by
+construction: published Philox known-answer vectors, the paper's closed forms
+(Lemma 1, Lemma 2, the binary diamond count c_ij^2 of Sec. 3.1), brute-force
+products computed here with numpy, and long-double dot products.
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from oracle import Matrix, Oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _w1_closed_form(A, B):
+    """||W||_1 = sum_ik |a_ik| ||a_i*||_1 ||b_k*||_1 (Alg. 2 weight line)."""
+    na = np.abs(A).sum(axis=1)
+    nb = np.abs(B).sum(axis=1)
+    return float((np.abs(A) * na[:, None] * nb[None, :]).sum())
+
+
+def _dense(A, B, flags=0, s_max=1 << 20):
+    return Oracle(Matrix(A), Matrix(B), flags=flags, s_max=s_max)
+
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10
+# ---------------------------------------------------------------------------
+def test_philox_known_answers():
+    rows = 0
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            w = [int(x, 16) for x in line.split()]
+            out = oracle.philox4x32_10(w[0:4], w[4:6])
+            assert list(out) == w[6:10]
+            rows += 1
+    assert rows == 3
+
+
+def test_diamond_uniforms_layout():
+    # u0,u1 come from counter block 0, u2,u3 from block 1; word order lo|hi.
+    seed, ell = 0x0123456789ABCDEF, (5 << 32) | 7
+    u = oracle.diamond_uniforms(seed, ell)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    b0 = oracle.philox4x32_10([7, 5, 0, 0], key)
+    b1 = oracle.philox4x32_10([7, 5, 0, 1], key)
+    assert int(u[0]) == (int(b0[1]) << 32) | int(b0[0])
+    assert int(u[1]) == (int(b0[3]) << 32) | int(b0[2])
+    assert int(u[2]) == (int(b1[1]) << 32) | int(b1[0])
+    assert int(u[3]) == (int(b1[3]) << 32) | int(b1[2])
+
+
+def test_philox_uniformity():
+    # 64-bit outputs: top byte uniform over 256 bins (chi-square).
+    vals = np.array([oracle.diamond_uniforms(99, ell)[0] for ell in range(20000)], dtype=np.uint64)
+    counts = np.bincount((vals >> np.uint64(56)).astype(np.int64), minlength=256)
+    p = stats.chisquare(counts).pvalue
+    assert p > 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Norms and tables (Alg. 2 weight line, Sec. 4.2 cumulative tables)
+# ---------------------------------------------------------------------------
+def test_norms_match_exact_sums():
+    rng = _rng(11)
+    A = rng.standard_normal((40, 300)).astype(np.float32)
+    B = rng.standard_normal((300, 700)).astype(np.float32)
+    o = _dense(A, B)
+    na = o.table("na").astype(np.float64)
+    nb = o.table("nb").astype(np.float64)
+    exact_a = np.abs(A.astype(np.float64)).sum(axis=1)
+    exact_b = np.abs(B.astype(np.float64)).sum(axis=1)
+    # FP32 error bound of 256 sequential partials + an 8-level tree.
+    tol_a = (300 / 256 + 10) * 2.0 ** -24
+    tol_b = (700 / 256 + 10) * 2.0 ** -24
+    assert np.all(np.abs(na - exact_a) <= tol_a * exact_a)
+    assert np.all(np.abs(nb - exact_b) <= tol_b * exact_b)
+
+
+def _row_probs(prefix, ptr):
+    out = []
+    for r in range(len(ptr) - 1):
+        seg = prefix[ptr[r]:ptr[r + 1]].astype(np.float64)
+        q = np.diff(np.concatenate([[0.0], seg]))
+        out.append(q / seg[-1] if len(seg) and seg[-1] > 0 else q)
+    return out
+
+
+def test_center_edge_law_equals_w_over_w1():
+    """P(i,k) = (T1 step) x (T2 step) must equal w_ik / ||W||_1."""
+    rng = _rng(12)
+    A = rng.standard_normal((30, 20))
+    B = rng.standard_normal((20, 50))
+    o = _dense(A, B)
+    T1 = o.table("T1").astype(np.float64)
+    p_i = np.diff(np.concatenate([[0.0], T1])) / T1[-1]
+    ptr = np.arange(0, 30 * 20 + 1, 20)
+    p_k = np.array(_row_probs(o.table("T2"), ptr))
+    joint = p_i[:, None] * p_k
+    na = np.abs(A).sum(axis=1)
+    nb = np.abs(B).sum(axis=1)
+    w = np.abs(A) * na[:, None] * nb[None, :]
+    ref = w / w.sum()
+    assert np.max(np.abs(joint - ref) / ref) < 2e-5
+
+
+def test_endpoint_laws():
+    """j ~ |b_kj| / ||b_k*||_1 and k' ~ |a_ik'| / ||a_i*||_1."""
+    rng = _rng(13)
+    A = rng.standard_normal((25, 30)).astype(np.float32)
+    B = rng.standard_normal((30, 40)).astype(np.float32)
+    o = _dense(A, B)
+    pa = np.array(_row_probs(o.table("TA"), np.arange(0, 25 * 30 + 1, 30)))
+    pb = np.array(_row_probs(o.table("TB"), np.arange(0, 30 * 40 + 1, 40)))
+    ra = np.abs(A.astype(np.float64))
+    rb = np.abs(B.astype(np.float64))
+    assert np.max(np.abs(pa - ra / ra.sum(1, keepdims=True))) < 2.0 ** -25
+    assert np.max(np.abs(pb - rb / rb.sum(1, keepdims=True))) < 2.0 ** -25
+
+
+def test_row_prefix_headroom():
+    rng = _rng(14)
+    A = (rng.standard_normal((10, 64)) * 1e30).astype(np.float32)
+    B = (rng.standard_normal((64, 5000)) * 1e-30).astype(np.float32)
+    o = _dense(A, B)
+    for name in ("T2", "TA", "TB"):
+        t = o.table(name)
+        assert t.max() < 2 ** 31
+        assert t.max() >= 2 ** 29  # scaled near the top of the range
+    assert o.table("T1")[-1] < 2 ** 62
+
+
+def test_zero_weights_never_drawn_and_bumped_weights_kept():
+    A = np.array([[1.0, 0.0, 1e-30], [0.0, 0.0, 0.0], [2.0, -1.0, 0.0]])
+    B = np.array([[1.0, 2.0], [0.0, -1.0], [3.0, 0.0]])
+    o = _dense(A, B)
+    T1 = o.table("T1")
+    assert T1[1] == T1[0]  # the all-zero row of A is never a center
+    T2 = o.table("T2")
+    assert T2[1] == T2[0]  # a_01 = 0 gets no mass
+    TA = o.table("TA")
+    assert TA[2] - TA[1] == 1  # a_02 = 1e-30 is tiny but stays reachable
+    assert o.scalars()["bumps"] >= 1
+    i, k, j, kp, v = o.draw(5, 0, 20000)
+    assert not np.any(i == 1)
+    assert not np.any(A[i, k] == 0.0)
+    assert not np.any(A[i, kp] == 0.0)
+    assert not np.any(B[k, j] == 0.0)
+
+
+def test_integer_tables_closed_form():
+    """0/1 inputs: r_i = deg_i sum_{k in N(i)} deg_k; T2 = prefix of deg_k."""
+    from paper_1506_03872_gb300.workloads import chung_lu
+    w = chung_lu(nodes=300, edges=1500, seed=5)
+    M = Matrix(rowptr=w.rowptr, colidx=w.colidx, shape=(w.m, w.d))
+    o = Oracle(M, M, flags=w.flags)
+    deg = np.diff(w.rowptr)
+    r = np.array([deg[i] * deg[w.colidx[w.rowptr[i]:w.rowptr[i + 1]]].sum() for i in range(w.m)])
+    assert np.array_equal(o.table("T1"), np.cumsum(r).astype(np.uint64))
+    T2 = o.table("T2")
+    TA = o.table("TA")
+    for i in range(w.m):
+        seg = slice(w.rowptr[i], w.rowptr[i + 1])
+        assert np.array_equal(T2[seg], np.cumsum(deg[w.colidx[seg]]))
+        assert np.array_equal(TA[seg], np.arange(1, deg[i] + 1))
+
+
+# ---------------------------------------------------------------------------
+# Lemma 1 and Lemma 2 (Sec. 5.1)
+# ---------------------------------------------------------------------------
+def _tiny_float():
+    rng = _rng(21)
+    A = rng.standard_normal((3, 2))
+    B = rng.standard_normal((2, 3))
+    return A, B
+
+
+def test_lemma1_three_path_probability():
+    A, B = _tiny_float()
+    o = _dense(A, B)
+    i, k, j, kp, prob, v = o.enumerate()
+    w1 = _w1_closed_form(A, B)
+    ref = np.abs(A[i, k] * B[k, j] * A[i, kp]) / w1
+    assert len(i) == 3 * 2 * 3 * 2
+    assert np.max(np.abs(prob - ref) / ref) < 1e-5
+    assert abs(prob.sum() - 1.0) < 1e-12
+
+
+def test_lemma2_expectation_dense():
+    """E[x_ij / s] = c_ij^2 / ||W||_1 (x in units of 2^-F)."""
+    rng = _rng(22)
+    A = rng.standard_normal((4, 3))
+    B = rng.standard_normal((3, 5))
+    o = _dense(A, B)
+    F = o.scalars()["F"]
+    i, k, j, kp, prob, v = o.enumerate()
+    ex = np.zeros((4, 5))
+    np.add.at(ex, (i, j), prob * v.astype(np.float64) * 2.0 ** -F)
+    C = A @ B
+    ref = C ** 2 / _w1_closed_form(A, B)
+    assert np.max(np.abs(ex - ref)) < 2e-5 * ref.max()
+
+
+def test_lemma2_expectation_binary_exact():
+    """0/1 inputs: every three-path has probability 1/||W||_1 and pair
+    (i,j) closes exactly c_ij^2 of them (Sec. 3.1)."""
+    rng = _rng(23)
+    A = (rng.random((5, 4)) < 0.5).astype(np.int64)
+    B = (rng.random((4, 6)) < 0.5).astype(np.int64)
+    A[0, 0] = B[0, 0] = 1
+    rpA = np.concatenate([[0], np.cumsum(A.sum(1))]).astype(np.int64)
+    rpB = np.concatenate([[0], np.cumsum(B.sum(1))]).astype(np.int64)
+    o = Oracle(Matrix(rowptr=rpA, colidx=np.nonzero(A)[1], shape=A.shape),
+               Matrix(rowptr=rpB, colidx=np.nonzero(B)[1], shape=B.shape))
+    i, k, j, kp, prob, v = o.enumerate()
+    w1 = _w1_closed_form(A.astype(float), B.astype(float))
+    assert np.allclose(prob * w1, 1.0, rtol=1e-12, atol=0)
+    closed = np.zeros((5, 6), dtype=np.int64)
+    np.add.at(closed, (i, j), v)
+    C = A @ B
+    assert np.array_equal(closed, C ** 2)
+    # brute-force diamond count: (k, k') with a_ik b_kj a_ik' b_k'j = 1
+    for ii in range(5):
+        for jj in range(6):
+            cnt = sum(A[ii, a] * B[a, jj] * A[ii, b] * B[b, jj] for a in range(4) for b in range(4))
+            assert cnt == C[ii, jj] ** 2
+
+
+def test_draw_frequencies_match_lemma1():
+    """Chi-square of 200k oracle draws against the enumerated law."""
+    A, B = _tiny_float()
+    o = _dense(A, B)
+    i, k, j, kp, prob, v = o.enumerate()
+    index = {(a, b, c, d): q for q, (a, b, c, d) in enumerate(zip(i, k, j, kp))}
+    di, dk, dj, dkp, dv = o.draw(seed=77, first=0, count=200_000)
+    counts = np.zeros(len(prob))
+    for q in zip(di, dk, dj, dkp):
+        counts[index[tuple(int(x) for x in q)]] += 1
+    exp = prob * len(di)
+    small = exp < 5  # pool sparse bins so the chi-square approximation holds
+    counts = np.concatenate([counts[~small], [counts[small].sum()]])
+    exp = np.concatenate([exp[~small], [exp[small].sum()]])
+    assert counts.sum() == len(di)
+    p = stats.chisquare(counts, exp).pvalue
+    assert p > 1e-4
+
+
+def test_empirical_mean_within_5_sigma():
+    A, B = _tiny_float()
+    o = _dense(A, B, s_max=1 << 30)
+    F = o.scalars()["F"]
+    i, k, j, kp, prob, v = o.enumerate()
+    mean = np.zeros((3, 3))
+    second = np.zeros((3, 3))
+    np.add.at(mean, (i, j), prob * v)
+    np.add.at(second, (i, j), prob * v.astype(np.float64) ** 2)
+    var = second - mean ** 2
+    s, seeds = 4000, 40
+    acc = np.zeros((3, 3))
+    for seed in range(seeds):
+        o.reset()
+        assert o.sample(s, seed) == 0
+        keys, vals = o.x()
+        acc[(keys >> np.uint64(32)).astype(int), (keys & np.uint64(0xFFFFFFFF)).astype(int)] += vals
+    emp = acc / seeds
+    sigma = np.sqrt(s * var / seeds)
+    assert np.all(np.abs(emp - s * mean) <= 5 * sigma + 1e-9 * 2.0 ** F)
+
+
+# ---------------------------------------------------------------------------
+# Postprocessing (Alg. 3) and ground truth
+# ---------------------------------------------------------------------------
+def test_bruteforce_matches_numpy():
+    rng = _rng(31)
+    A = rng.standard_normal((60, 8))
+    B = rng.standard_normal((8, 70))
+    o = _dense(A, B)
+    keys, c = o.bruteforce(25)
+    C = A @ B
+    flat = np.abs(C).ravel()
+    order = np.lexsort((np.arange(flat.size), -flat))[:25]
+    ref_keys = (order // 70).astype(np.uint64) << np.uint64(32) | (order % 70).astype(np.uint64)
+    assert np.array_equal(keys, ref_keys)
+    assert np.allclose(c, C.ravel()[order], rtol=1e-14)
+
+
+def test_rescore_dot_within_1e12_of_long_double():
+    rng = _rng(32)
+    A = rng.standard_normal((50, 300))
+    B = rng.standard_normal((300, 40))
+    o = _dense(A, B)
+    ii, jj = np.meshgrid(np.arange(50), np.arange(40), indexing="ij")
+    keys = (ii.ravel().astype(np.uint64) << np.uint64(32)) | jj.ravel().astype(np.uint64)
+    c = o.rescore(keys)
+    Al = A.astype(np.longdouble)
+    Bl = B.astype(np.longdouble)
+    ref = (Al[ii.ravel()] * Bl[:, jj.ravel()].T).sum(axis=1)
+    scale = (np.abs(Al[ii.ravel()]) * np.abs(Bl[:, jj.ravel()].T)).sum(axis=1)
+    err = np.abs(c.astype(np.longdouble) - ref)
+    assert np.all(err <= 1e-12 * np.maximum(np.abs(ref), 1e-3 * scale))
+
+
+def test_topk_order_and_ties():
+    A = np.ones((4, 1))
+    B = np.ones((1, 4))
+    o = _dense(A, B, s_max=1 << 20)
+    o.sample(4000, 3)
+    keys, xs = o.topk(100)
+    assert len(keys) == 16
+    for q in range(len(keys) - 1):
+        assert xs[q] > xs[q + 1] or (xs[q] == xs[q + 1] and keys[q] < keys[q + 1])
+    allk, allx = o.x()
+    assert set(keys.tolist()) == set(allk[allx > 0].tolist())
+
+
+def test_topt_orders_by_abs_then_key():
+    keys = np.array([5, 3, 9, 1], dtype=np.uint64)
+    c = np.array([-2.0, 2.0, 1.0, -3.0])
+    k, v = oracle.topt(keys, c, 3)
+    assert k.tolist() == [1, 3, 5]
+    assert v.tolist() == [-3.0, 2.0, -2.0]
+
+
+def test_gram_keys_unordered_and_diagonal_skipped():
+    from paper_1506_03872_gb300.workloads import chung_lu
+    w = chung_lu(nodes=200, edges=1000, seed=6)
+    M = Matrix(rowptr=w.rowptr, colidx=w.colidx, shape=(w.m, w.d))
+    o = Oracle(M, M, flags=w.flags, s_max=1 << 20)
+    o.sample(50_000, 1)
+    keys, vals = o.x()
+    i = keys >> np.uint64(32)
+    j = keys & np.uint64(0xFFFFFFFF)
+    assert np.all(i < j)
+    sc = o.scalars()
+    assert sc["diag_skipped"] > 0
+    assert sc["inserted"] == vals.sum()
+
+
+def test_planted_pairs_found_with_enough_samples():
+    """With s well above ||W||_1 / tau^2 (Sec. 5.2) the top-t is exact."""
+    from paper_1506_03872_gb300.workloads import plain_small
+    w = plain_small(m=200, d=25, n=200, planted=10, seed=9)
+    o = _dense(w.A, w.B, s_max=1 << 22)
+    truth_keys, _ = o.bruteforce(10)
+    keys, c = o.run(s=200_000, seed=4, tprime=100, t=10)
+    assert set(keys.tolist()) == set(truth_keys.tolist())
+
+
+def test_overflow_guard_on_s_max():
+    A, B = _tiny_float()
+    o = _dense(A, B, s_max=100)
+    assert o.sample(60, 1) == 0
+    assert o.sample(60, 1, 60) == 4  # overflow: more diamonds than s_max
