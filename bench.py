@@ -1,0 +1,399 @@
+"""Benchmark of diamond sampling (arXiv:1506.03872) on GB300.
+
+One step = the whole hot path on one synthetic batch, inputs resident in
+HBM: mad_build_tables (weights and cumulative tables), mad_sample (s
+diamonds), mad_topk (Omega_t') and mad_rescore (Omega_t).  Default workload:
+dense recommender factors, A 200000x100 and B 100x50000 FP32, s = 1e7,
+t = 100, t' = 1e4.
+
+Prints one JSON line.  value = diamonds per second over whole steps
+(device-timed, CUDA events, L2 flushed between steps); e2e = the same metric
+through the C ABI with the inputs copied from pinned host memory and the
+top-t read back inside the timed region.
+
+--impl reference times the CPU oracle on a bounded sample of the same
+workload (the reference arm of this comparison).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-top-t at recall>=0.95 vs dense GEMM+top-t on 1 GB300; diamonds/sec"
+SAMPLER_SOURCES = ["paper_1506_03872_gb300/csrc/sample.cu",
+                   "paper_1506_03872_gb300/csrc/mad_device.cuh"]
+# Algorithmic DRAM bytes of one dense diamond: the final entry of each of the
+# four inverse-CDF searches (T1, T2, TB, TA), b_k'j, and the read-modify-write
+# of the hash key and value sectors; one 32-byte sector per touch.
+DENSE_SECTORS_READ = 5
+DENSE_SECTORS_RMW = 2
+DENSE_BYTES_PER_DIAMOND = 32 * DENSE_SECTORS_READ + 64 * DENSE_SECTORS_RMW
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _sources_sha():
+    h = hashlib.sha256()
+    for p in SAMPLER_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_record():
+    path = os.path.join(ROOT, "profiles", "sampler_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("source_sha") == _sources_sha():
+            return rec
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons (background)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def start(self):
+        def run():
+            while not self._stop.is_set():
+                try:
+                    out = subprocess.run(
+                        ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                         "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                        timeout=5).stdout.strip()
+                    if out:
+                        self.rows.append([x.strip() for x in out.split(",")])
+                except Exception:
+                    pass
+                self._stop.wait(0.2)
+        self._t = threading.Thread(target=run, daemon=True)
+        self._t.start()
+
+    def stop(self):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in self.rows for q in range(4)
+                          if len(r) > 4 + q and r[4 + q].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1
+    import torch.distributed as dist
+    dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND") != "gloo" else "gloo")
+    return dist, dist.get_rank(), ws
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    """Largest value over all ranks (the slowest rank sets the job time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _workload(name: str, scale: float):
+    from paper_1506_03872_gb300 import workloads as W
+    if name == "dense_factors":
+        if scale != 1.0:
+            return W.dense_factors(m=int(200_000 * scale), n=int(50_000 * scale),
+                                   s=int(10_000_000 * scale))
+        return W.dense_factors()
+    if name == "plain_small":
+        return W.plain_small()
+    if name == "chung_lu":
+        return W.chung_lu()
+    raise KeyError(name)
+
+
+def _ground_truth_dense(A, B, t):
+    """Exact top-t of |A B| (harness only): FP32 cuBLAS GEMM in row blocks
+    with a margin covering its rounding error, then FP64 rescoring."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    m, d = A.shape
+    n = B.shape[1]
+    na = A.double().norm(dim=1).max().item()
+    nb = B.double().norm(dim=0).max().item()
+    err = 2.0 * d * 2.0 ** -24 * na * nb
+    block = 8192
+    vals = []
+    for r0 in range(0, m, block):
+        c = (A[r0:r0 + block] @ B).abs_()
+        v, _ = torch.topk(c.flatten(), min(8 * t, c.numel()))
+        vals.append(v)
+    theta = torch.topk(torch.cat(vals), t).values[-1].item()
+    cand = []
+    for r0 in range(0, m, block):
+        c = (A[r0:r0 + block] @ B).abs_()
+        idx = torch.nonzero(c >= theta - 2 * err)
+        idx[:, 0] += r0
+        cand.append(idx)
+    cand = torch.cat(cand)
+    exact = (A[cand[:, 0]].double() * B[:, cand[:, 1]].T.double()).sum(dim=1).abs()
+    order = torch.argsort(-exact, stable=True)[:t]
+    keys = (cand[order, 0].to(torch.int64) << 32) | cand[order, 1].to(torch.int64)
+    tau = exact[order[-1]].item()
+    return set(keys.cpu().tolist()), tau
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1506_03872_gb300 as mad
+    from paper_1506_03872_gb300 import build as _build
+    dist, rank, world = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    _build.build()
+    w = _workload(args.workload, args.scale)
+    s, t, tprime, seed = w.s, w.t, w.tprime, w.sampler_seed
+    dev = torch.device("cuda", local)
+    if w.csr:
+        tensors = [torch.from_numpy(x).to(dev) for x in (w.rowptr, w.colidx)]
+        Am = mad.csr(tensors[0], tensors[1], (w.m, w.d))
+        Bm = Am
+        host_inputs = [torch.from_numpy(x).pin_memory() for x in (w.rowptr, w.colidx)]
+    else:
+        tensors = [torch.from_numpy(w.A).to(dev), torch.from_numpy(w.B).to(dev)]
+        Am, Bm = mad.dense(tensors[0]), mad.dense(tensors[1])
+        host_inputs = [torch.from_numpy(w.A).pin_memory(), torch.from_numpy(w.B).pin_memory()]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ctx = mad.Context(w.flags)
+    out_c = mad.new_pairs(tprime)
+    out_t = mad.new_pairs(t)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(A_, B_, timing=None):
+        e = [ev() for _ in range(5)] if timing is not None else None
+        if e: e[0].record(stream)
+        mad.mad_build_tables(ctx.ctx, A_, B_, s)
+        if e: e[1].record(stream)
+        mad.mad_sample(ctx.ctx, s, seed)
+        if e: e[2].record(stream)
+        cand, nc = mad.mad_topk(ctx.ctx, tprime, out_c)
+        if e: e[3].record(stream)
+        res, nr = mad.mad_rescore(ctx.ctx, cand, nc, t, out_t)
+        if e: e[4].record(stream)
+        if timing is not None:
+            timing.append(e)
+        return res, nr
+
+    for _ in range(args.warmup):
+        step(Am, Bm)
+    torch.cuda.synchronize()
+    launches0 = mad.mad_stats(ctx.ctx)["launches"]
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks: clocks.start()
+    if dist: dist.barrier()
+    torch.cuda.synchronize()
+    timings = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)   # evict the 129 MB L2 between timed steps
+        step(Am, Bm, timings)
+    torch.cuda.synchronize()
+    if dist: dist.barrier()
+    clk = clocks.stop() if clocks else None
+    launches = mad.mad_stats(ctx.ctx)["launches"] - launches0
+    phase = np.array([[e[q].elapsed_time(e[q + 1]) for q in range(4)] for e in timings])
+    step_ms = phase.sum(axis=1)
+    total_ms = max_over_ranks(dist, float(step_ms.sum()), dev)
+    ms_per_step = total_ms / args.steps
+    value = world * s * args.steps / (total_ms / 1e3)
+
+    # Recall of the last step against exact ground truth (not timed).
+    res, nr = step(Am, Bm)
+    gi, gj, gx, gc = mad.decode_pairs(res, nr)
+    recall = None
+    tau = None
+    if not w.csr and rank == 0 and not args.no_recall:
+        truth, tau = _ground_truth_dense(tensors[0], tensors[1], t)
+        got = set(mad.keys_of(gi, gj).astype(np.int64).tolist())
+        recall = len(got & truth) / t
+    stats = mad.mad_stats(ctx.ctx)
+
+    # End to end through the C ABI from pinned host memory.
+    e2e_ms = []
+    for q in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        a0, a1 = ev(), ev()
+        a0.record(stream)
+        dev_inputs = [h.to(dev, non_blocking=True) for h in host_inputs]
+        if w.csr:
+            A_ = mad.csr(dev_inputs[0], dev_inputs[1], (w.m, w.d))
+            B_ = A_
+        else:
+            A_, B_ = mad.dense(dev_inputs[0]), mad.dense(dev_inputs[1])
+        res, nr = step(A_, B_)
+        host_res = res[:nr].cpu()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        if q >= args.warmup:
+            e2e_ms.append(a0.elapsed_time(a1))
+    e2e_total = max_over_ranks(dist, float(sum(e2e_ms)), dev)
+    h2d = int(sum(h.numel() * h.element_size() for h in host_inputs))
+    d2h = int(host_res.numel() * host_res.element_size())
+
+    # Roofline of the dominant kernel (the sampler): algorithmic bytes per
+    # launch over its event-timed duration on the launching stream.
+    sample_ms = float(phase[:, 1].mean())
+    peak, peak_kind = _peaks()
+    roof = None
+    if not w.csr:
+        alg_bytes = DENSE_BYTES_PER_DIAMOND * s
+        achieved = alg_bytes / (sample_ms / 1e3) / 1e9
+        rec = _traffic_record()
+        roof = {"bound": "hbm", "kernel": "k_sample", "achieved": round(achieved, 1),
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": (round(rec["bytes_per_diamond"] * s) if rec else None),
+                "algorithmic_bytes_per_launch": alg_bytes}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w, args.cpu_diamonds)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "diamonds/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "m": w.m, "d": w.d, "n": w.n, "s": s, "t": t,
+                       "tprime": tprime, "flags": w.flags, "l2": "flushed between steps",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "phases_ms": {k: round(float(phase[:, q].mean()), 4)
+                          for q, k in enumerate(["build_tables", "sample", "topk", "rescore"])},
+            "diamonds_per_s_sampler": round(s / (sample_ms / 1e3), 1),
+            "recall_at_s": recall, "tau_t": tau,
+            "stats": {k: stats[k] for k in ("w1", "inserted", "distinct", "positive",
+                                              "hash_capacity")},
+            "e2e": {"value": round(world * s * args.steps / (e2e_total / 1e3), 1),
+                    "unit": "diamonds/s", "ms_per_step": round(e2e_total / args.steps, 4),
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def _oracle_step(w, s):
+    import oracle
+    t0 = time.perf_counter()
+    if w.csr:
+        M = oracle.Matrix(rowptr=w.rowptr, colidx=w.colidx, shape=(w.m, w.d))
+        o = oracle.Oracle(M, M, w.flags, s)
+    else:
+        o = oracle.Oracle(oracle.Matrix(w.A), oracle.Matrix(w.B), w.flags, s)
+    if o.sample(s, w.sampler_seed):
+        raise RuntimeError("oracle sampling failed")
+    keys, _ = o.topk(w.tprime)
+    oracle.topt(keys, o.rescore(keys), w.t)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(w, diamonds):
+    sec = _oracle_step(w, diamonds)
+    return {"value": round(diamonds / sec, 1), "unit": "diamonds/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"full {w.name} tables + {diamonds} of the {w.s} diamonds + top-t' + rescore",
+            "seconds": round(sec, 3)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = _workload(args.workload, args.scale)
+    for _ in range(args.warmup):
+        _oracle_step(w, args.cpu_diamonds)
+    secs = [_oracle_step(w, args.cpu_diamonds) for _ in range(args.steps)]
+    total = sum(secs)
+    value = args.cpu_diamonds * args.steps / total
+    sample = (f"full {w.name} tables + {args.cpu_diamonds} of the {w.s} diamonds + top-t' + "
+              "rescore per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "diamonds/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "m": w.m, "d": w.d, "n": w.n, "s": w.s, "t": w.t,
+                   "tprime": w.tprime, "flags": w.flags},
+        "cpu_baseline": {"value": round(value, 1), "unit": "diamonds/s", "cores": 1,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 1), "unit": "diamonds/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dense_factors")
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--cpu-diamonds", type=int, default=2_000_000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-recall", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * mad.h -- C ABI of a GB300 (sm_103a) library for approximate Maximum
+ * All-pairs Dot-product (MAD) search by diamond sampling.
+ *
+ * Paper: G. Ballard, T. G. Kolda, A. Pinar, C. Seshadhri, "Diamond Sampling
+ * for Approximate Maximum All-pairs Dot-product (MAD) Search",
+ * arXiv:1506.03872.
+ *
+ * Problem (Defn. 1): given A (m x d, rows a_i) and B (d x n, columns b_j),
+ * find the t pairs (i, j) with the largest |a_i . b_j|.  The paper stores
+ * vectors as columns (A^T B); here A holds them as rows, so a_ik below is
+ * the paper's a_ki.
+ *
+ * Pipeline (one call per step, all asynchronous on the caller's stream):
+ *   mad_build_tables  weights w_ik = |a_ik| ||a_i*||_1 ||b_k*||_1 and the
+ *                     cumulative sampling tables (Alg. 2 weight line; Sec. 4.2)
+ *   mad_sample        s diamonds: (i,k) ~ w_ik, j ~ |b_kj|, k' ~ |a_ik'|,
+ *                     x_ij += sgn(a_ik b_kj a_ik') b_k'j (Alg. 2 loop)
+ *   mad_topk          Omega_t': the t' largest positive x_ij (Alg. 3, step 1)
+ *   mad_rescore       exact c_ij for the candidates, top t by |c| (Alg. 3)
+ *
+ * Numeric contract (fixed here because the paper leaves it open):
+ *   - Weights are FP32; L1 norms use one fixed summation order (256 strided
+ *     partial sums folded in halves).  Sampling tables are integer prefix
+ *     sums (uint64 over rows of A, uint32 within a row) of the FP32 weights
+ *     scaled by a power of two and rounded to nearest-even.
+ *   - Diamond l draws its four 64-bit uniforms from Philox4x32-10 with key =
+ *     seed and counter (l_lo, l_hi, 0, block), block 0 -> (i, k), block 1 ->
+ *     (j, k'); a uniform u selects the first prefix entry exceeding
+ *     floor(u * total / 2^64).
+ *   - x_ij is int64 fixed point: b_k'j (FP32) times 2^F, F chosen from s_max
+ *     and max|b| so that s_max increments cannot overflow.  0/1 CSR inputs
+ *     run in exact integer mode (F = 0, x_ij counts diamonds).
+ *   - Rescoring is FP64 (32 strided fused-multiply-add partial sums folded
+ *     in halves) for dense inputs and exact integer counts for 0/1 inputs.
+ *   Given the same inputs, seed and diamond range, every result is
+ *   bit-identical run to run and independent of launch configuration.
+ *
+ * Memory: the caller owns A, B and every output buffer (device memory unless
+ * a parameter says host).  A and B must stay alive and unchanged from
+ * mad_build_tables until mad_destroy or the next mad_build_tables: sampling
+ * and rescoring read them.  The library owns its tables, hash and scratch,
+ * allocated stream-ordered on the stream of mad_build_tables.
+ *
+ * Errors: every call returns a status and never aborts.  Device-side
+ * failures (hash probe limit, bad index) set a sticky flag that the next
+ * synchronising call (mad_topk, mad_rescore, mad_stats) reports.
+ * Thread safety: one context must not be used from two host threads at once.
+ */
+#ifndef MAD_H_
+#define MAD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream handle (the same type as cudaStream_t); NULL is the legacy
+ * default stream. */
+struct CUstream_st;
+typedef struct CUstream_st* mad_stream;
+
+typedef enum mad_status {
+  MAD_OK = 0,
+  MAD_ERR_ARG = 1,          /* bad shape, pointer, flag or size */
+  MAD_ERR_OOM = 2,          /* device allocation failed */
+  MAD_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  MAD_ERR_OVERFLOW = 4,     /* a table total or the diamond count exceeds its range */
+  MAD_ERR_EMPTY = 5,        /* ||W||_1 == 0: no three-path exists */
+  MAD_ERR_HASH_FULL = 6,    /* an insert exceeded the probe limit */
+  MAD_ERR_STATE = 7,        /* call out of order (e.g. sample before tables) */
+  MAD_ERR_UNSUPPORTED = 8   /* valid request outside what this build handles */
+} mad_status;
+
+typedef enum mad_format { MAD_DENSE_ROWMAJOR = 0, MAD_CSR = 1 } mad_format;
+typedef enum mad_dtype { MAD_F32 = 0, MAD_F64 = 1, MAD_BINARY = 2 } mad_dtype;
+
+/* A matrix in device memory.
+ *   dense: values[r * ld + c], dtype MAD_F32 or MAD_F64, ld >= cols.
+ *   CSR:   rowptr[rows + 1] (rowptr[0] == 0), colidx[rowptr[rows]] sorted
+ *          ascending within each row, dtype MAD_BINARY (values == NULL,
+ *          every stored entry is 1). */
+typedef struct mad_matrix {
+  int32_t fmt;              /* mad_format */
+  int32_t dt;               /* mad_dtype */
+  int64_t rows, cols, ld;
+  const void* values;
+  const int64_t* rowptr;
+  const int32_t* colidx;
+} mad_matrix;
+
+/* One candidate or result pair: x is the sampled score (Alg. 2), c the
+ * exact dot product a_i . b_j (Alg. 3).  24 bytes, 8-byte aligned. */
+typedef struct mad_pair {
+  uint32_t i, j;
+  int64_t x;
+  double c;
+} mad_pair;
+
+/* Context flags (mad_create).
+ *   MAD_NONNEG        caller asserts A, B >= 0: the sign product of Alg. 2 is
+ *                     skipped (Sec. 3.2.1).
+ *   MAD_GRAM          caller asserts B = A^T, so C is symmetric: pairs are
+ *                     accumulated unordered, key (min(i,j), max(i,j)), which
+ *                     is twice the symmetrised X of Sec. 3.2.2 and ranks the
+ *                     same.
+ *   MAD_EXCLUDE_DIAG  diamonds with i == j are drawn but not accumulated
+ *                     (the distinct-pairs application of Sec. 6.2). */
+enum { MAD_NONNEG = 1u, MAD_GRAM = 2u, MAD_EXCLUDE_DIAG = 4u };
+
+typedef struct mad_stats_t {
+  double w1;                /* ||W||_1 as represented by the tables */
+  uint64_t t1_total;        /* integer total of the row table */
+  int32_t e1;               /* row-table scale exponent */
+  int32_t f;                /* increment scale exponent (0 in integer mode) */
+  uint64_t sampled;         /* diamonds drawn since the last reset */
+  uint64_t inserted;        /* diamonds with a nonzero increment */
+  uint64_t diag_skipped;    /* diamonds dropped because i == j */
+  uint64_t distinct;        /* occupied hash slots (updated by mad_topk) */
+  uint64_t positive;        /* keys with x > 0 (updated by mad_topk) */
+  uint64_t hash_capacity;   /* hash slots */
+  uint64_t launches;        /* kernels launched by this context so far */
+  uint32_t integer_mode;    /* 1 for 0/1 inputs */
+  uint32_t device_error;    /* sticky device error bits (0 = none) */
+} mad_stats_t;
+
+typedef struct mad_ctx mad_ctx;
+
+/* Create a context on the current CUDA device.  flags: MAD_NONNEG |
+ * MAD_GRAM | MAD_EXCLUDE_DIAG.  Returns MAD_ERR_ARG for unknown flags. */
+mad_status mad_create(mad_ctx** ctx, uint32_t flags);
+
+/* Free everything the context owns (synchronises the device). */
+void mad_destroy(mad_ctx* ctx);
+
+/* Static description of a status code. */
+const char* mad_strerror(mad_status status);
+
+/* Hash capacity in slots for the next mad_build_tables (a power of two,
+ * >= 1024), or 0 for the default: the smallest power of two >= s_max / 0.6.
+ * Each slot is 16 bytes. */
+mad_status mad_set_hash_capacity(mad_ctx* ctx, uint64_t slots);
+
+/* Alg. 2 weight line and the cumulative tables of Sec. 4.2.
+ *   A: m x d, B: d x n (B->rows == A->cols).  Both dense (F32/F64, any mix)
+ *   or both 0/1 CSR.  Dense inputs need d <= 1024.  m, n < 2^32.
+ *   s_max: the most diamonds mad_sample may accumulate before the next
+ *   mad_reset_hash; it fixes the increment scale F and the hash size.
+ * Synchronises the stream once to read the table totals.  Errors:
+ *   MAD_ERR_EMPTY when ||W||_1 == 0, MAD_ERR_OVERFLOW when a 0/1 table total
+ *   exceeds its integer range, MAD_ERR_UNSUPPORTED for other formats. */
+mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B,
+                            uint64_t s_max, mad_stream stream);
+
+/* Alg. 2 sampling loop for diamonds first_diamond .. first_diamond+s-1,
+ * accumulated into the context's hash.  Calls may be repeated (resume or
+ * split a run): any split of a diamond range gives the same X as one call.
+ * Errors: MAD_ERR_STATE before mad_build_tables, MAD_ERR_OVERFLOW when the
+ * diamonds since the last reset would exceed s_max.  Asynchronous. */
+mad_status mad_sample(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first_diamond,
+                      mad_stream stream);
+
+/* Clear X (and the sampled count) without rebuilding tables. */
+mad_status mad_reset_hash(mad_ctx* ctx, mad_stream stream);
+
+/* Alg. 3, first step: Omega_t' = the min(t', |{x > 0}|) keys with the
+ * largest x, ties broken by smaller (i, j); written to out_dev sorted by
+ * (x desc, i asc, j asc) with c = 0.  Gram contexts report i < j.
+ * *n_out_host receives the count.  Synchronises the stream. */
+mad_status mad_topk(mad_ctx* ctx, uint32_t tprime, mad_pair* out_dev, uint32_t* n_out_host,
+                    mad_stream stream);
+
+/* Alg. 3, remaining steps: c_ij = a_i . b_j for each of the ncand candidates
+ * (cand_dev, device), then the min(t, ncand) pairs with the largest |c|,
+ * ties broken by smaller (i, j), sorted, written to out_dev with their x.
+ * Uses the A and B given to mad_build_tables.  Candidates must be distinct
+ * pairs with i < m, j < n.  Synchronises the stream. */
+mad_status mad_rescore(mad_ctx* ctx, const mad_pair* cand_dev, uint32_t ncand, uint32_t t,
+                       mad_pair* out_dev, uint32_t* n_out_host, mad_stream stream);
+
+/* Counters and table scalars (synchronises the device). */
+mad_status mad_stats(mad_ctx* ctx, mad_stats_t* out);
+
+/* ---- Diagnostics (used by the parity tests; not on the hot path) ------- */
+
+/* The draws of diamonds first .. first+count-1 without accumulating: the
+ * indices (i, k, j, k') and the increment v (Alg. 2 loop body).  Output
+ * arrays are device arrays of count elements. */
+mad_status mad_debug_draws(mad_ctx* ctx, uint64_t seed, uint64_t first, uint64_t count,
+                           uint32_t* i_dev, uint32_t* k_dev, uint32_t* j_dev, uint32_t* kp_dev,
+                           int64_t* v_dev, mad_stream stream);
+
+/* As mad_debug_draws for an arbitrary device list of diamond indices. */
+mad_status mad_debug_draws_list(mad_ctx* ctx, uint64_t seed, const uint64_t* ells_dev,
+                                uint64_t count, uint32_t* i_dev, uint32_t* k_dev,
+                                uint32_t* j_dev, uint32_t* kp_dev, int64_t* v_dev,
+                                mad_stream stream);
+
+/* Every occupied key of X and its value (order unspecified).  keys_dev and
+ * vals_dev hold cap entries; *n_host receives |X| (the copy stops at cap).
+ * Synchronises the stream. */
+mad_status mad_export_x(mad_ctx* ctx, uint64_t* keys_dev, int64_t* vals_dev, uint64_t cap,
+                        uint64_t* n_host, mad_stream stream);
+
+/* Copy an internal table to out_dev (device, cap elements):
+ *   0 T1 (uint64, m)      1 T2 (uint32, nnz(A))   2 TA (uint32, nnz(A))
+ *   3 TB (uint32, nnz(B)) 4 ||a_i*||_1 (f32, m)  5 ||b_k*||_1 (f32, d)
+ *   6 r_i (f32, m)
+ * Row-table entries carry the sign of the matching value of A or B in bit
+ * 31 (float mode).  Tables the mode keeps implicit report 0 elements.
+ * *n_host receives the element count.  Synchronises the stream. */
+mad_status mad_export_table(mad_ctx* ctx, int which, void* out_dev, uint64_t cap,
+                            uint64_t* n_host, mad_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAD_H_ */

@@ -1,0 +1,401 @@
+// The C ABI declared in include/mad.h: argument checks, memory ownership,
+// status codes and the order of the kernel launches.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "mad_internal.cuh"
+
+namespace mad {
+
+mad_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return MAD_OK;
+  if (e == cudaErrorMemoryAllocation) return MAD_ERR_OOM;
+  return MAD_ERR_CUDA;
+}
+
+mad_status ensure_scratch(mad_ctx* ctx, size_t bytes, cudaStream_t st) {
+  if (bytes <= ctx->scratch_bytes) return MAD_OK;
+  if (ctx->scratch) cudaFreeAsync(ctx->scratch, st);
+  ctx->scratch = nullptr;
+  ctx->scratch_bytes = 0;
+  const size_t rounded = (bytes + (1u << 20) - 1) & ~(size_t)((1u << 20) - 1);
+  const cudaError_t e = cudaMallocAsync(&ctx->scratch, rounded, st);
+  if (e != cudaSuccess) {
+    ctx->scratch = nullptr;
+    return cuda_status(e);
+  }
+  ctx->scratch_bytes = rounded;
+  return MAD_OK;
+}
+
+}  // namespace mad
+
+using namespace mad;
+
+namespace {
+
+int ceil_log2(uint64_t x) {
+  int e = 0;
+  while (e < 64 && (1ull << e) < x) ++e;
+  return e;
+}
+
+template <typename T>
+void free_async(T*& p, cudaStream_t st) {
+  if (p) cudaFreeAsync((void*)p, st);
+  p = nullptr;
+}
+
+void free_tables(mad_ctx* ctx, cudaStream_t st) {
+  free_async(ctx->T1, st);
+  free_async(ctx->T2, st);
+  free_async(ctx->TA, st);
+  free_async(ctx->TB, st);
+  free_async(ctx->na, st);
+  free_async(ctx->nb, st);
+  free_async(ctx->r, st);
+  free_async(ctx->r64, st);
+  free_async(ctx->bt, st);
+  free_async(ctx->hkeys, st);
+  free_async(ctx->hvals, st);
+  ctx->built = false;
+}
+
+template <typename T>
+mad_status alloc(T*& p, size_t count, cudaStream_t st) {
+  p = nullptr;
+  if (count == 0) count = 1;
+  return cuda_status(cudaMallocAsync((void**)&p, count * sizeof(T), st));
+}
+
+mad_status device_error_status(uint32_t err) {
+  if (err & DERR_HASH_FULL) return MAD_ERR_HASH_FULL;
+  if (err & DERR_OVERFLOW) return MAD_ERR_OVERFLOW;
+  if (err & DERR_SEARCH) return MAD_ERR_STATE;
+  if (err & DERR_EMPTY) return MAD_ERR_EMPTY;
+  return MAD_OK;
+}
+
+// Read the device scalars (synchronises the stream).
+mad_status read_scalars(mad_ctx* ctx, DevScalars* hs, cudaStream_t st) {
+  cudaMemcpyAsync(hs, ctx->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st);
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  ctx->device_error = hs->err;
+  return MAD_OK;
+}
+
+bool valid_dense(const mad_matrix* M) {
+  return M->fmt == MAD_DENSE_ROWMAJOR && (M->dt == MAD_F32 || M->dt == MAD_F64) && M->values &&
+         M->ld >= M->cols && M->rows > 0 && M->cols > 0;
+}
+
+bool valid_csr(const mad_matrix* M) {
+  return M->fmt == MAD_CSR && M->dt == MAD_BINARY && M->rowptr && M->colidx && M->rows > 0 &&
+         M->cols > 0 && M->cols < (1ll << 31);
+}
+
+mad_status clear_hash(mad_ctx* ctx, cudaStream_t st) {
+  cudaMemsetAsync(ctx->hkeys, 0xFF, ctx->hcap * sizeof(unsigned long long), st);
+  cudaMemsetAsync(ctx->hvals, 0, ctx->hcap * sizeof(long long), st);
+  cudaMemsetAsync(&ctx->sc->inserted, 0, 5 * sizeof(unsigned long long), st);
+  ctx->sampled = 0;
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+mad_status mad_create(mad_ctx** out, uint32_t flags) {
+  if (!out) return MAD_ERR_ARG;
+  *out = nullptr;
+  if (flags & ~(uint32_t)(MAD_NONNEG | MAD_GRAM | MAD_EXCLUDE_DIAG)) return MAD_ERR_ARG;
+  mad_ctx* ctx = new (std::nothrow) mad_ctx();
+  if (!ctx) return MAD_ERR_OOM;
+  ctx->flags = flags;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->sc, sizeof(DevScalars));
+  if (e == cudaSuccess) e = cudaMemset(ctx->sc, 0, sizeof(DevScalars));
+  if (e != cudaSuccess) {
+    if (ctx->sc) cudaFree(ctx->sc);
+    delete ctx;
+    return cuda_status(e);
+  }
+  *out = ctx;
+  return MAD_OK;
+}
+
+void mad_destroy(mad_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  free_tables(ctx, 0);
+  if (ctx->scratch) cudaFreeAsync(ctx->scratch, 0);
+  cudaStreamSynchronize(0);
+  cudaFree(ctx->sc);
+  delete ctx;
+}
+
+const char* mad_strerror(mad_status s) {
+  switch (s) {
+    case MAD_OK: return "success";
+    case MAD_ERR_ARG: return "invalid argument";
+    case MAD_ERR_OOM: return "device out of memory";
+    case MAD_ERR_CUDA: return "CUDA runtime error";
+    case MAD_ERR_OVERFLOW: return "integer range exceeded (table total or diamonds beyond s_max)";
+    case MAD_ERR_EMPTY: return "||W||_1 is zero: no three-path to sample";
+    case MAD_ERR_HASH_FULL: return "hash probe limit exceeded (capacity too small)";
+    case MAD_ERR_STATE: return "call out of order or inconsistent state";
+    case MAD_ERR_UNSUPPORTED: return "unsupported input format";
+  }
+  return "unknown status";
+}
+
+mad_status mad_set_hash_capacity(mad_ctx* ctx, uint64_t slots) {
+  if (!ctx) return MAD_ERR_ARG;
+  if (slots != 0 && (slots < 1024 || (slots & (slots - 1)) != 0)) return MAD_ERR_ARG;
+  ctx->hcap_request = slots;
+  return MAD_OK;
+}
+
+mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B,
+                            uint64_t s_max, mad_stream stream) {
+  if (!ctx || !A || !B || s_max == 0 || s_max > (1ull << 60)) return MAD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (B->rows != A->cols) return MAD_ERR_ARG;
+  if (A->rows >= (1ll << 32) - 1 || B->cols >= (1ll << 32) - 1) return MAD_ERR_ARG;
+  if ((ctx->flags & MAD_GRAM) && A->rows != B->cols) return MAD_ERR_ARG;  // B = A^T
+  const bool dense = A->fmt == MAD_DENSE_ROWMAJOR && B->fmt == MAD_DENSE_ROWMAJOR;
+  const bool csr = A->fmt == MAD_CSR && B->fmt == MAD_CSR;
+  if (dense) {
+    if (!valid_dense(A) || !valid_dense(B)) return MAD_ERR_ARG;
+    if (A->cols > 1024) return MAD_ERR_UNSUPPORTED;
+  } else if (csr) {
+    if (!valid_csr(A) || !valid_csr(B)) return MAD_ERR_ARG;
+  } else {
+    return MAD_ERR_UNSUPPORTED;
+  }
+  free_tables(ctx, st);
+  ctx->A = *A;
+  ctx->B = *B;
+  ctx->dense = dense;
+  ctx->integer = csr;
+  ctx->m = A->rows;
+  ctx->d = A->cols;
+  ctx->n = B->cols;
+  ctx->s_max = s_max;
+  mad_status rs = MAD_OK;
+  if (csr) {
+    int64_t na = 0, nb = 0;
+    cudaMemcpyAsync(&na, A->rowptr + A->rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&nb, B->rowptr + B->rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    rs = cuda_status(cudaStreamSynchronize(st));
+    if (rs != MAD_OK) return rs;
+    if (na <= 0 || nb <= 0) return MAD_ERR_EMPTY;
+    ctx->nnz_a = (uint64_t)na;
+    ctx->nnz_b = (uint64_t)nb;
+    if ((rs = alloc(ctx->T2, ctx->nnz_a, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx->r64, (size_t)ctx->m, st)) != MAD_OK) return rs;
+  } else {
+    ctx->nnz_a = (uint64_t)(ctx->m * ctx->d);
+    ctx->nnz_b = (uint64_t)(ctx->d * ctx->n);
+    const size_t eb = B->dt == MAD_F64 ? 8 : 4;
+    if ((rs = alloc(ctx->T2, ctx->nnz_a, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx->TA, ctx->nnz_a, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx->TB, ctx->nnz_b, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx->na, (size_t)ctx->m, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx->r, (size_t)ctx->m, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx->nb, (size_t)ctx->d, st)) != MAD_OK) return rs;
+    char* bt = nullptr;
+    if ((rs = alloc(bt, (size_t)(ctx->n * ctx->d) * eb, st)) != MAD_OK) return rs;
+    ctx->bt = bt;
+  }
+  if ((rs = alloc(ctx->T1, (size_t)ctx->m, st)) != MAD_OK) return rs;
+  uint64_t cap = ctx->hcap_request;
+  if (cap == 0) {
+    const double want = (double)s_max / 0.6;
+    cap = 1024;
+    while ((double)cap < want && cap < (1ull << 40)) cap <<= 1;
+  }
+  ctx->hcap = cap;
+  if ((rs = alloc(ctx->hkeys, cap, st)) != MAD_OK) return rs;
+  if ((rs = alloc(ctx->hvals, cap, st)) != MAD_OK) return rs;
+  cudaMemsetAsync(ctx->sc, 0, sizeof(DevScalars), st);
+  if ((rs = clear_hash(ctx, st)) != MAD_OK) return rs;
+  if ((rs = build_tables_impl(ctx, st)) != MAD_OK) return rs;
+  DevScalars hs;
+  if ((rs = read_scalars(ctx, &hs, st)) != MAD_OK) return rs;
+  if (hs.err & DERR_OVERFLOW) return MAD_ERR_OVERFLOW;
+  if (ctx->integer) {
+    if (hs.t1_total == 0) return MAD_ERR_EMPTY;
+    ctx->f = 0;
+    ctx->e1 = 0;
+  } else {
+    if (hs.maxr_bits == 0u || hs.maxb_bits == 0u) return MAD_ERR_EMPTY;
+    float maxb;
+    std::memcpy(&maxb, &hs.maxb_bits, sizeof(float));
+    ctx->f = 62 - ceil_log2(s_max) - (std::ilogb(maxb) + 1);
+    ctx->e1 = hs.e1;
+  }
+  ctx->t1_total = hs.t1_total;
+  ctx->built = true;
+  return MAD_OK;
+}
+
+mad_status mad_sample(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first_diamond,
+                      mad_stream stream) {
+  if (!ctx) return MAD_ERR_ARG;
+  if (!ctx->built) return MAD_ERR_STATE;
+  if (s > ctx->s_max || ctx->sampled > ctx->s_max - s) return MAD_ERR_OVERFLOW;
+  const mad_status rs = sample_impl(ctx, s, seed, first_diamond, (cudaStream_t)stream);
+  if (rs == MAD_OK) ctx->sampled += s;
+  return rs;
+}
+
+mad_status mad_reset_hash(mad_ctx* ctx, mad_stream stream) {
+  if (!ctx) return MAD_ERR_ARG;
+  if (!ctx->built) return MAD_ERR_STATE;
+  return clear_hash(ctx, (cudaStream_t)stream);
+}
+
+mad_status mad_topk(mad_ctx* ctx, uint32_t tprime, mad_pair* out_dev, uint32_t* n_out_host,
+                    mad_stream stream) {
+  if (!ctx || !n_out_host || (tprime > 0 && !out_dev)) return MAD_ERR_ARG;
+  *n_out_host = 0;
+  if (!ctx->built) return MAD_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevScalars hs;
+  mad_status rs = read_scalars(ctx, &hs, st);
+  if (rs != MAD_OK) return rs;
+  if ((rs = device_error_status(hs.err)) != MAD_OK) return rs;
+  uint64_t bound = hs.new_keys < ctx->hcap ? hs.new_keys : ctx->hcap;
+  if (tprime == 0 || bound == 0) return MAD_OK;
+  if ((rs = ensure_scratch(ctx, select_ws_bytes(bound, tprime), st)) != MAD_OK) return rs;
+  const SelectWs ws = select_ws_carve(ctx->scratch, bound, tprime);
+  uint64_t npos = 0;
+  if ((rs = compact_positive(ctx, ws, &npos, st)) != MAD_OK) return rs;
+  if ((rs = read_scalars(ctx, &hs, st)) != MAD_OK) return rs;
+  ctx->distinct = hs.distinct;
+  ctx->positive = npos;
+  uint64_t nsel = 0;
+  if ((rs = select_run(ctx, ws, npos, tprime, significant_bytes(hs.maxp), &nsel, st)) != MAD_OK)
+    return rs;
+  if ((rs = items_to_pairs(ctx, ws.out, nsel, nullptr, nullptr, out_dev, st)) != MAD_OK) return rs;
+  if ((rs = cuda_status(cudaStreamSynchronize(st))) != MAD_OK) return rs;
+  *n_out_host = (uint32_t)nsel;
+  return MAD_OK;
+}
+
+mad_status mad_rescore(mad_ctx* ctx, const mad_pair* cand_dev, uint32_t ncand, uint32_t t,
+                       mad_pair* out_dev, uint32_t* n_out_host, mad_stream stream) {
+  if (!ctx || !n_out_host || (ncand > 0 && !cand_dev) || (t > 0 && !out_dev)) return MAD_ERR_ARG;
+  *n_out_host = 0;
+  if (!ctx->built) return MAD_ERR_STATE;
+  if (ncand == 0 || t == 0) return MAD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ws_bytes = select_ws_bytes(ncand, t);
+  const size_t cv_off = (ws_bytes + 255) & ~(size_t)255;
+  mad_status rs = ensure_scratch(ctx, cv_off + (size_t)ncand * sizeof(double), st);
+  if (rs != MAD_OK) return rs;
+  const SelectWs ws = select_ws_carve(ctx->scratch, ncand, t);
+  double* cvals = (double*)((char*)ctx->scratch + cv_off);
+  if ((rs = rescore_items(ctx, cand_dev, ncand, ws.l0, cvals, st)) != MAD_OK) return rs;
+  uint64_t nsel = 0;
+  if ((rs = select_run(ctx, ws, ncand, t, 8, &nsel, st)) != MAD_OK) return rs;
+  if ((rs = items_to_pairs(ctx, ws.out, nsel, cand_dev, cvals, out_dev, st)) != MAD_OK) return rs;
+  DevScalars hs;
+  if ((rs = read_scalars(ctx, &hs, st)) != MAD_OK) return rs;
+  if ((rs = device_error_status(hs.err)) != MAD_OK) return rs;
+  *n_out_host = (uint32_t)nsel;
+  return MAD_OK;
+}
+
+mad_status mad_stats(mad_ctx* ctx, mad_stats_t* out) {
+  if (!ctx || !out) return MAD_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  DevScalars hs;
+  std::memset(&hs, 0, sizeof(hs));
+  mad_status rs = cuda_status(cudaDeviceSynchronize());
+  if (rs != MAD_OK) return rs;
+  if ((rs = cuda_status(cudaMemcpy(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost))) != MAD_OK)
+    return rs;
+  ctx->device_error = hs.err;
+  out->t1_total = ctx->t1_total;
+  out->e1 = ctx->e1;
+  out->f = ctx->f;
+  out->w1 = ctx->integer ? (double)ctx->t1_total : std::ldexp((double)ctx->t1_total, -ctx->e1);
+  out->sampled = ctx->sampled;
+  out->inserted = hs.inserted;
+  out->diag_skipped = hs.diag_skipped;
+  out->distinct = hs.new_keys;
+  out->positive = ctx->positive;
+  out->hash_capacity = ctx->hcap;
+  out->launches = ctx->launches;
+  out->integer_mode = ctx->integer ? 1u : 0u;
+  out->device_error = hs.err;
+  return MAD_OK;
+}
+
+mad_status mad_debug_draws(mad_ctx* ctx, uint64_t seed, uint64_t first, uint64_t count,
+                           uint32_t* i_dev, uint32_t* k_dev, uint32_t* j_dev, uint32_t* kp_dev,
+                           int64_t* v_dev, mad_stream stream) {
+  if (!ctx || (count && (!i_dev || !k_dev || !j_dev || !kp_dev || !v_dev))) return MAD_ERR_ARG;
+  if (!ctx->built) return MAD_ERR_STATE;
+  return debug_draws_impl(ctx, seed, first, nullptr, count, i_dev, k_dev, j_dev, kp_dev, v_dev,
+                          (cudaStream_t)stream);
+}
+
+mad_status mad_debug_draws_list(mad_ctx* ctx, uint64_t seed, const uint64_t* ells_dev,
+                                uint64_t count, uint32_t* i_dev, uint32_t* k_dev,
+                                uint32_t* j_dev, uint32_t* kp_dev, int64_t* v_dev,
+                                mad_stream stream) {
+  if (!ctx || (count && (!ells_dev || !i_dev || !k_dev || !j_dev || !kp_dev || !v_dev)))
+    return MAD_ERR_ARG;
+  if (!ctx->built) return MAD_ERR_STATE;
+  return debug_draws_impl(ctx, seed, 0, ells_dev, count, i_dev, k_dev, j_dev, kp_dev, v_dev,
+                          (cudaStream_t)stream);
+}
+
+mad_status mad_export_x(mad_ctx* ctx, uint64_t* keys_dev, int64_t* vals_dev, uint64_t cap,
+                        uint64_t* n_host, mad_stream stream) {
+  if (!ctx || !n_host || (cap && (!keys_dev || !vals_dev))) return MAD_ERR_ARG;
+  *n_host = 0;
+  if (!ctx->built) return MAD_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  mad_status rs = ensure_scratch(ctx, 256, st);
+  if (rs != MAD_OK) return rs;
+  return export_x(ctx, keys_dev, vals_dev, cap, n_host, (unsigned long long*)ctx->scratch, st);
+}
+
+mad_status mad_export_table(mad_ctx* ctx, int which, void* out_dev, uint64_t cap,
+                            uint64_t* n_host, mad_stream stream) {
+  if (!ctx || !n_host) return MAD_ERR_ARG;
+  *n_host = 0;
+  if (!ctx->built) return MAD_ERR_STATE;
+  const void* src = nullptr;
+  size_t elem = 4;
+  uint64_t count = 0;
+  switch (which) {
+    case 0: src = ctx->T1; elem = 8; count = (uint64_t)ctx->m; break;
+    case 1: src = ctx->T2; count = ctx->nnz_a; break;
+    case 2: src = ctx->TA; count = ctx->TA ? ctx->nnz_a : 0; break;
+    case 3: src = ctx->TB; count = ctx->TB ? ctx->nnz_b : 0; break;
+    case 4: src = ctx->na; count = ctx->na ? (uint64_t)ctx->m : 0; break;
+    case 5: src = ctx->nb; count = ctx->nb ? (uint64_t)ctx->d : 0; break;
+    case 6: src = ctx->r; count = ctx->r ? (uint64_t)ctx->m : 0; break;
+    default: return MAD_ERR_ARG;
+  }
+  *n_host = count;
+  if (count == 0 || cap == 0) return MAD_OK;
+  if (!out_dev) return MAD_ERR_ARG;
+  const uint64_t ncopy = count < cap ? count : cap;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaMemcpyAsync(out_dev, src, ncopy * elem, cudaMemcpyDeviceToDevice, st);
+  return cuda_status(cudaStreamSynchronize(st));
+}
+
+}  // extern "C"

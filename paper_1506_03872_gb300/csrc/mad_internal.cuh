@@ -1,0 +1,167 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mad.h"
+
+namespace mad {
+
+// ---------------------------------------------------------------------------
+// Device error bits (sticky per context).
+// ---------------------------------------------------------------------------
+enum : uint32_t {
+  DERR_HASH_FULL = 1u,     // an insert ran past the probe limit
+  DERR_SEARCH = 2u,        // an inverse-CDF search left its row (corrupt table)
+  DERR_OVERFLOW = 4u,      // an integer table total left its range
+  DERR_EMPTY = 8u,         // ||W||_1 == 0
+};
+
+constexpr uint64_t EMPTY_KEY = ~0ull;
+constexpr uint32_t SIGN_BIT = 0x80000000u;
+constexpr uint32_t PREFIX_MASK = 0x7FFFFFFFu;
+
+// Scalars produced and consumed on the device.
+struct DevScalars {
+  unsigned int maxr_bits;          // FP32 bits of max_i r_i (nonnegative)
+  unsigned int maxb_bits;          // FP32 bits of max |b_kj|
+  int e1;                          // row-table exponent
+  int pad0;
+  unsigned long long t1_total;     // last entry of T1
+  unsigned int err;                // DERR_* bits
+  unsigned int pad1;
+  unsigned long long inserted;     // diamonds accumulated
+  unsigned long long diag_skipped; // diamonds with i == j (dropped)
+  unsigned long long new_keys;     // keys created by sampling
+  unsigned long long distinct;     // occupied slots (compaction)
+  unsigned long long positive;     // slots with x > 0 (compaction)
+  unsigned long long maxp;         // largest select key (compaction)
+};
+
+// Everything a sampling kernel needs, passed by value.
+struct SampleParams {
+  // A (m x d): dense row-major or 0/1 CSR.
+  const void* a_val;
+  const int64_t* a_ptr;
+  const int32_t* a_col;
+  int64_t m, d, lda;
+  // B (d x n).
+  const void* b_val;
+  const int64_t* b_ptr;
+  const int32_t* b_col;
+  int64_t n, ldb;
+  // Tables.
+  const uint64_t* T1;
+  const uint32_t* T2;
+  const uint32_t* TA;
+  const uint32_t* TB;
+  unsigned long long t1_total;
+  double f_scale;                  // 2^F
+  // Hash.
+  unsigned long long* hkeys;
+  long long* hvals;
+  uint64_t hmask;
+  uint32_t max_probe;
+  // Modes.
+  int dense;                       // 1 dense A and B, 0 CSR
+  int a_f64, b_f64;                // dense dtypes
+  int integer;                     // 0/1 exact mode
+  uint32_t flags;                  // MAD_NONNEG | MAD_GRAM | MAD_EXCLUDE_DIAG
+  DevScalars* sc;
+};
+
+// Select item: primary key p (larger first), tie key (smaller first), aux.
+struct Item {
+  unsigned long long p;
+  unsigned long long key;
+  unsigned long long aux;
+};
+
+}  // namespace mad
+
+// ---------------------------------------------------------------------------
+// Context (host side).
+// ---------------------------------------------------------------------------
+struct mad_ctx {
+  uint32_t flags = 0;
+  int device = 0;
+  bool built = false;
+  bool integer = false;
+  bool dense = false;
+  mad_matrix A{}, B{};
+  int64_t m = 0, d = 0, n = 0;
+  uint64_t nnz_a = 0, nnz_b = 0;
+  uint64_t s_max = 0, sampled = 0;
+  int e1 = 0, f = 0;
+  unsigned long long t1_total = 0;
+  // Owned device memory.
+  uint64_t* T1 = nullptr;
+  uint32_t* T2 = nullptr;
+  uint32_t* TA = nullptr;
+  uint32_t* TB = nullptr;
+  float* na = nullptr;
+  float* nb = nullptr;
+  float* r = nullptr;
+  unsigned long long* r64 = nullptr;
+  void* bt = nullptr;               // dense B^T (n x d), the input dtype
+  unsigned long long* hkeys = nullptr;
+  long long* hvals = nullptr;
+  uint64_t hcap = 0, hcap_request = 0;
+  mad::DevScalars* sc = nullptr;
+  // Scratch (select, scans); grown on demand.
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  // Host mirrors.
+  uint64_t launches = 0;
+  uint64_t distinct = 0, positive = 0;
+  uint32_t device_error = 0;
+};
+
+namespace mad {
+
+// Launch bookkeeping: every kernel launch of the library goes through this.
+inline void count_launch(mad_ctx* ctx, int n = 1) { ctx->launches += (uint64_t)n; }
+
+mad_status cuda_status(cudaError_t e);
+mad_status ensure_scratch(mad_ctx* ctx, size_t bytes, cudaStream_t st);
+
+// tables.cu
+mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st);
+// sample.cu
+mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first,
+                       cudaStream_t st);
+mad_status debug_draws_impl(mad_ctx* ctx, uint64_t seed, uint64_t first, const uint64_t* ells,
+                            uint64_t count, uint32_t* oi, uint32_t* ok, uint32_t* oj,
+                            uint32_t* okp, int64_t* ov, cudaStream_t st);
+SampleParams make_params(const mad_ctx* ctx);
+// select.cu
+// Workspace of one top-K selection over at most n items.
+struct SelectWs {
+  Item* l0;          // input list (n items), preserved
+  Item* l1;          // ping-pong survivor lists
+  Item* l2;
+  Item* out;         // K selected items, sorted (padded to a power of two)
+  void* state;
+  unsigned long long* counter;
+  uint64_t cap_n, cap_out;
+};
+size_t select_ws_bytes(uint64_t n, uint64_t K);
+SelectWs select_ws_carve(void* base, uint64_t n, uint64_t K);
+// Occupied slots with x > 0 into ws.l0; synchronises.
+mad_status compact_positive(mad_ctx* ctx, const SelectWs& ws, uint64_t* n_pos, cudaStream_t st);
+// K largest of ws.l0[0..n) by (p desc, key asc), sorted into ws.out.  dp =
+// number of significant bytes of the largest p.  Asynchronous.
+mad_status select_run(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K, int dp,
+                      uint64_t* n_sel, cudaStream_t st);
+mad_status items_to_pairs(mad_ctx* ctx, const Item* items, uint64_t n, const mad_pair* cand,
+                          const double* cvals, mad_pair* out, cudaStream_t st);
+int significant_bytes(unsigned long long maxp);
+mad_status export_x(mad_ctx* ctx, uint64_t* keys, int64_t* vals, uint64_t cap, uint64_t* n,
+                    unsigned long long* counter, cudaStream_t st);
+// rescore.cu
+// Exact c for every candidate: items[q] = (bits |c|, key, q), cvals[q] = c.
+mad_status rescore_items(mad_ctx* ctx, const mad_pair* cand, uint64_t ncand, Item* items,
+                         double* cvals, cudaStream_t st);
+
+}  // namespace mad

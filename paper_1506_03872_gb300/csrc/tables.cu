@@ -1,0 +1,452 @@
+// Weights and cumulative sampling tables (Alg. 2 weight line; Sec. 4.2).
+//
+// Float mode (dense FP32/FP64 inputs):
+//   ||b_k*||_1, ||a_i*||_1 and s_i = sum_k |a_ik| ||b_k*||_1 are FP32 sums in
+//   one fixed order: 256 partial sums (partial q takes the indices equal to q
+//   mod 256, ascending), folded in halves.  r_i = ||a_i*||_1 * s_i.
+//   Row tables (T2 over k of |a_ik| ||b_k*||_1, TA over k of |a_ik|, TB over
+//   j of |b_kj|) hold inclusive prefixes of round(w * 2^E) with
+//   E = 29 - floor(log2(row sum)), so every prefix stays below 2^31 and bit
+//   31 carries the sign of the underlying value of A or B.  T1 holds the
+//   uint64 prefix of round(r_i * 2^E1), E1 = 62 - ceil(log2 m) -
+//   (floor(log2 max r) + 1).  A nonzero weight that rounds to 0 becomes 1.
+// Integer mode (0/1 CSR): T2 holds the prefix of deg_k^B along row i of A,
+//   T1 the prefix of r_i = deg_i^A * sum_{k in N(i)} deg_k^B; the uniform
+//   endpoint tables TA and TB are implicit.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#include "mad_device.cuh"
+#include "mad_internal.cuh"
+
+namespace mad {
+namespace {
+
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(double v) { return __double2float_rn(v); }
+
+// Inclusive warp scan of 32-bit values.
+__device__ __forceinline__ uint32_t warp_inclusive_u32(uint32_t v, int lane) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, v, off);
+    if (lane >= off) v += o;
+  }
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_inclusive_u64(unsigned long long v, int lane) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long o = __shfl_up_sync(0xFFFFFFFFu, v, off);
+    if (lane >= off) v += o;
+  }
+  return v;
+}
+
+// Exclusive scan of one 32-bit value per thread over a 256-thread block.
+__device__ __forceinline__ uint32_t block_exclusive_u32(uint32_t v, uint32_t* warp_tot,
+                                                        uint32_t* block_total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t inc = warp_inclusive_u32(v, lane);
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t t = lane < 8 ? warp_tot[lane] : 0u;
+    const uint32_t ti = warp_inclusive_u32(t, lane);
+    if (lane < 8) warp_tot[lane] = ti - t;  // exclusive warp offsets
+    if (lane == 7) warp_tot[8] = ti;
+  }
+  __syncthreads();
+  const uint32_t out = warp_tot[warp] + inc - v;
+  *block_total = warp_tot[8];
+  __syncthreads();
+  return out;
+}
+
+__device__ __forceinline__ unsigned long long block_exclusive_u64(unsigned long long v,
+                                                                  unsigned long long* warp_tot,
+                                                                  unsigned long long* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long inc = warp_inclusive_u64(v, lane);
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long t = lane < 8 ? warp_tot[lane] : 0ull;
+    const unsigned long long ti = warp_inclusive_u64(t, lane);
+    if (lane < 8) warp_tot[lane] = ti - t;
+    if (lane == 7) warp_tot[8] = ti;
+  }
+  __syncthreads();
+  const unsigned long long out = warp_tot[warp] + inc - v;
+  *total = warp_tot[8];
+  __syncthreads();
+  return out;
+}
+
+// round(w * scale) for a row table, with the support-preserving bump.
+__device__ __forceinline__ uint32_t quantize_row(float w, double scale) {
+  uint32_t q = __double2uint_rn((double)w * scale);
+  if (w > 0.0f && q == 0u) q = 1u;
+  return q;
+}
+
+// ---------------------------------------------------------------------------
+// Rows of dense B: ||b_k*||_1, max |b|, TB.  One 256-thread block per row.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_b_rows_dense(const T* __restrict__ B, int64_t n, int64_t ldb, float* __restrict__ nb,
+               uint32_t* __restrict__ TB, DevScalars* sc) {
+  __shared__ float part[256];
+  __shared__ uint32_t warp_tot[9];
+  const int64_t k = blockIdx.x;
+  const T* __restrict__ row = B + k * ldb;
+  const int t = threadIdx.x;
+  float acc = 0.0f, mx = 0.0f;
+  for (int64_t idx = t; idx < n; idx += 256) {
+    const float v = fabsf(to_f32(row[idx]));
+    acc = __fadd_rn(acc, v);
+    mx = fmaxf(mx, v);
+  }
+  part[t] = acc;
+  __syncthreads();
+  for (int h = 128; h >= 1; h >>= 1) {
+    if (t < h) part[t] = __fadd_rn(part[t], part[t + h]);
+    __syncthreads();
+  }
+  const float total = part[0];
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+  if ((t & 31) == 0 && mx > 0.0f) atomicMax(&sc->maxb_bits, __float_as_uint(mx));
+  if (t == 0) nb[k] = total;
+
+  uint32_t* __restrict__ out = TB + k * n;
+  const double scale = total > 0.0f ? pow2d(29 - ilogb_pos(total)) : 0.0;
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < n; base += 1024) {
+    uint32_t q[4], sg[4], local = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t idx = base + 4 * t + c;
+      q[c] = 0;
+      sg[c] = 0;
+      if (idx < n) {
+        const float v = to_f32(row[idx]);
+        if (total > 0.0f) local += quantize_row(fabsf(v), scale);
+        q[c] = local;
+        sg[c] = v < 0.0f ? SIGN_BIT : 0u;
+      }
+    }
+    uint32_t tile_total;
+    const uint32_t excl = block_exclusive_u32(local, warp_tot, &tile_total);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t idx = base + 4 * t + c;
+      if (idx < n) out[idx] = (carry + excl + q[c]) | sg[c];
+    }
+    carry += tile_total;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Rows of dense A: ||a_i*||_1, s_i, r_i, T2, TA.  One warp per row; the
+// 256 canonical partials live 8 per lane (partial L + 32c in slot c).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_a_rows_dense(const T* __restrict__ A, int64_t m, int64_t d, int64_t lda,
+               const float* __restrict__ nb_g, float* __restrict__ na_out,
+               float* __restrict__ r_out, uint32_t* __restrict__ T2, uint32_t* __restrict__ TA,
+               DevScalars* sc) {
+  extern __shared__ float nb[];
+  for (int64_t idx = threadIdx.x; idx < d; idx += blockDim.x) nb[idx] = nb_g[idx];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int warps = blockDim.x >> 5;
+  float rmax = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * warps + warp; i < m; i += (int64_t)gridDim.x * warps) {
+    const T* __restrict__ row = A + i * lda;
+    float pa[8], ps[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) pa[c] = ps[c] = 0.0f;
+    for (int64_t base = 0; base < d; base += 256) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int64_t idx = base + lane + 32 * c;
+        if (idx < d) {
+          const float a = fabsf(to_f32(row[idx]));
+          pa[c] = __fadd_rn(pa[c], a);
+          ps[c] = __fadd_rn(ps[c], __fmul_rn(a, nb[idx]));
+        }
+      }
+    }
+    // Fold halves: 128 and 64 and 32 inside the lane, 16..1 across lanes.
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      pa[c] = __fadd_rn(pa[c], pa[c + 4]);
+      ps[c] = __fadd_rn(ps[c], ps[c + 4]);
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      pa[c] = __fadd_rn(pa[c], pa[c + 2]);
+      ps[c] = __fadd_rn(ps[c], ps[c + 2]);
+    }
+    float na = __fadd_rn(pa[0], pa[1]);
+    float s = __fadd_rn(ps[0], ps[1]);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      na = __fadd_rn(na, __shfl_xor_sync(0xFFFFFFFFu, na, off));
+      s = __fadd_rn(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
+    }
+    const float r = __fmul_rn(na, s);
+    if (lane == 0) {
+      na_out[i] = na;
+      r_out[i] = r;
+    }
+    rmax = fmaxf(rmax, r);
+
+    const bool live = s > 0.0f;
+    const double sc2 = live ? pow2d(29 - ilogb_pos(s)) : 0.0;
+    const double sca = live ? pow2d(29 - ilogb_pos(na)) : 0.0;
+    uint32_t* __restrict__ o2 = T2 + i * d;
+    uint32_t* __restrict__ oa = TA + i * d;
+    uint32_t c2 = 0, ca = 0;
+    for (int64_t base = 0; base < d; base += 32) {
+      const int64_t idx = base + lane;
+      uint32_t q2 = 0, qa = 0, sg = 0;
+      if (idx < d) {
+        const float v = to_f32(row[idx]);
+        const float a = fabsf(v);
+        if (live) {
+          q2 = quantize_row(__fmul_rn(a, nb[idx]), sc2);
+          qa = quantize_row(a, sca);
+        }
+        sg = v < 0.0f ? SIGN_BIT : 0u;
+      }
+      const uint32_t i2 = warp_inclusive_u32(q2, lane);
+      const uint32_t ia = warp_inclusive_u32(qa, lane);
+      if (idx < d) {
+        o2[idx] = (c2 + i2) | sg;
+        oa[idx] = (ca + ia) | sg;
+      }
+      c2 += __shfl_sync(0xFFFFFFFFu, i2, 31);
+      ca += __shfl_sync(0xFFFFFFFFu, ia, 31);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1)
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xFFFFFFFFu, rmax, off));
+  if (lane == 0 && rmax > 0.0f) atomicMax(&sc->maxr_bits, __float_as_uint(rmax));
+}
+
+// ---------------------------------------------------------------------------
+// Rows of 0/1 CSR A (integer mode): T2 = prefix of deg_k^B, r_i.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_a_rows_binary(const int64_t* __restrict__ a_ptr, const int32_t* __restrict__ a_col,
+                const int64_t* __restrict__ b_ptr, int64_t m, uint32_t* __restrict__ T2,
+                unsigned long long* __restrict__ r64, DevScalars* sc) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int warps = blockDim.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * warps + warp; i < m; i += (int64_t)gridDim.x * warps) {
+    const int64_t a0 = a_ptr[i], a1 = a_ptr[i + 1];
+    unsigned long long carry = 0;
+    bool over = false;
+    for (int64_t base = a0; base < a1; base += 32) {
+      const int64_t e = base + lane;
+      unsigned long long q = 0;
+      if (e < a1) {
+        const int32_t k = a_col[e];
+        q = (unsigned long long)(b_ptr[k + 1] - b_ptr[k]);
+      }
+      const unsigned long long inc = warp_inclusive_u64(q, lane) + carry;
+      if (e < a1) {
+        if (inc > 0xFFFFFFFFull) over = true;
+        T2[e] = (uint32_t)inc;
+      }
+      carry = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    }
+    if (__any_sync(0xFFFFFFFFu, over) && lane == 0) atomicOr(&sc->err, DERR_OVERFLOW);
+    if (lane == 0) r64[i] = (unsigned long long)(a1 - a0) * carry;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// T1: scale exponent, per-chunk sums, chunk offsets, inclusive prefix.
+// ---------------------------------------------------------------------------
+constexpr int T1_CHUNK = 2048;  // 256 threads x 8 elements
+
+__device__ __forceinline__ int t1_exponent(const DevScalars* sc, int clog2m) {
+  const float maxr = __uint_as_float(sc->maxr_bits);
+  return 62 - clog2m - (ilogb_pos(maxr) + 1);
+}
+
+__device__ __forceinline__ unsigned long long t1_weight(const float* r, const unsigned long long* r64,
+                                                        int64_t i, double scale) {
+  if (r64) return r64[i];
+  const float v = r[i];
+  unsigned long long q = __double2ull_rn((double)v * scale);
+  if (v > 0.0f && q == 0ull) q = 1ull;
+  return q;
+}
+
+__global__ void __launch_bounds__(256)
+k_t1_chunk_sums(const float* __restrict__ r, const unsigned long long* __restrict__ r64,
+                int64_t m, int clog2m, unsigned long long* __restrict__ partial, DevScalars* sc) {
+  __shared__ unsigned long long warp_tot[9];
+  double scale = 0.0;
+  if (!r64) {
+    if (sc->maxr_bits == 0u) return;  // ||W||_1 == 0, reported by the host
+    scale = pow2d(t1_exponent(sc, clog2m));
+  }
+  const int64_t base = (int64_t)blockIdx.x * T1_CHUNK + threadIdx.x * 8;
+  unsigned long long acc = 0;
+  bool over = false;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int64_t i = base + c;
+    if (i < m) {
+      const unsigned long long q = t1_weight(r, r64, i, scale);
+      const unsigned long long nx = acc + q;
+      if (nx < acc || q >= (1ull << 63)) over = true;
+      acc = nx;
+    }
+  }
+  unsigned long long total;
+  // 256 values of at most 2^63 each: detect wrap on the chunk sum.
+  const unsigned long long excl = block_exclusive_u64(acc, warp_tot, &total);
+  if (over || excl + acc < excl) atomicOr(&sc->err, DERR_OVERFLOW);
+  if (threadIdx.x == 255 && total < excl) atomicOr(&sc->err, DERR_OVERFLOW);
+  if (threadIdx.x == 0) partial[blockIdx.x] = total;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !r64) sc->e1 = t1_exponent(sc, clog2m);
+}
+
+__global__ void k_t1_chunk_offsets(unsigned long long* __restrict__ partial, int64_t chunks,
+                                   DevScalars* sc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned long long acc = 0;
+  bool over = false;
+  for (int64_t b = 0; b < chunks; ++b) {
+    const unsigned long long v = partial[b];
+    partial[b] = acc;
+    const unsigned long long nx = acc + v;
+    if (nx < acc) over = true;
+    acc = nx;
+  }
+  if (over || acc >= (1ull << 63)) atomicOr(&sc->err, DERR_OVERFLOW);
+  if (acc == 0ull) atomicOr(&sc->err, DERR_EMPTY);
+  sc->t1_total = acc;
+}
+
+__global__ void __launch_bounds__(256)
+k_t1_write(const float* __restrict__ r, const unsigned long long* __restrict__ r64, int64_t m,
+           int clog2m, const unsigned long long* __restrict__ offset, uint64_t* __restrict__ T1,
+           const DevScalars* sc) {
+  __shared__ unsigned long long warp_tot[9];
+  double scale = 0.0;
+  if (!r64) {
+    if (sc->maxr_bits == 0u) return;
+    scale = pow2d(t1_exponent(sc, clog2m));
+  }
+  const int64_t base = (int64_t)blockIdx.x * T1_CHUNK + threadIdx.x * 8;
+  unsigned long long q[8], acc = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int64_t i = base + c;
+    q[c] = (i < m) ? t1_weight(r, r64, i, scale) : 0ull;
+    acc += q[c];
+    q[c] = acc;
+  }
+  unsigned long long total;
+  const unsigned long long excl = block_exclusive_u64(acc, warp_tot, &total);
+  const unsigned long long off = offset[blockIdx.x] + excl;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int64_t i = base + c;
+    if (i < m) T1[i] = off + q[c];
+  }
+}
+
+// Dense B (d x n) to B^T (n x d) for coalesced rescoring.
+template <typename T>
+__global__ void k_transpose(const T* __restrict__ B, int64_t d, int64_t n, int64_t ldb,
+                            T* __restrict__ Bt) {
+  __shared__ T tile[32][33];
+  const int64_t j0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t k = k0 + r, j = j0 + threadIdx.x;
+    if (k < d && j < n) tile[r][threadIdx.x] = B[k * ldb + j];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t j = j0 + r, k = k0 + threadIdx.x;
+    if (k < d && j < n) Bt[j * d + k] = tile[threadIdx.x][r];
+  }
+}
+
+int ceil_log2_host(uint64_t x) {
+  int e = 0;
+  while (e < 64 && (1ull << e) < x) ++e;
+  return e;
+}
+
+template <typename T>
+void launch_b_rows(mad_ctx* ctx, cudaStream_t st) {
+  k_b_rows_dense<T><<<(unsigned)ctx->d, 256, 0, st>>>((const T*)ctx->B.values, ctx->n, ctx->B.ld,
+                                                       ctx->nb, ctx->TB, ctx->sc);
+  count_launch(ctx);
+}
+
+template <typename T>
+void launch_a_rows(mad_ctx* ctx, cudaStream_t st) {
+  const int64_t blocks64 = (ctx->m + 7) / 8;
+  const unsigned blocks = (unsigned)(blocks64 < 152 * 16 ? blocks64 : 152 * 16);
+  k_a_rows_dense<T><<<blocks, 256, (size_t)ctx->d * sizeof(float), st>>>(
+      (const T*)ctx->A.values, ctx->m, ctx->d, ctx->A.ld, ctx->nb, ctx->na, ctx->r, ctx->T2,
+      ctx->TA, ctx->sc);
+  count_launch(ctx);
+}
+
+template <typename T>
+void launch_transpose(mad_ctx* ctx, cudaStream_t st) {
+  dim3 grid((unsigned)((ctx->n + 31) / 32), (unsigned)((ctx->d + 31) / 32));
+  k_transpose<T><<<grid, dim3(32, 8), 0, st>>>((const T*)ctx->B.values, ctx->d, ctx->n,
+                                               ctx->B.ld, (T*)ctx->bt);
+  count_launch(ctx);
+}
+
+}  // namespace
+
+mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st) {
+  const int64_t chunks = (ctx->m + T1_CHUNK - 1) / T1_CHUNK;
+  mad_status rs = ensure_scratch(ctx, (size_t)chunks * sizeof(unsigned long long), st);
+  if (rs != MAD_OK) return rs;
+  unsigned long long* partial = (unsigned long long*)ctx->scratch;
+  const int clog2m = ceil_log2_host((uint64_t)ctx->m);
+
+  if (ctx->integer) {
+    const int64_t blocks64 = (ctx->m + 7) / 8;
+    const unsigned blocks = (unsigned)(blocks64 < 152 * 16 ? blocks64 : 152 * 16);
+    k_a_rows_binary<<<blocks, 256, 0, st>>>(ctx->A.rowptr, ctx->A.colidx, ctx->B.rowptr, ctx->m,
+                                            ctx->T2, ctx->r64, ctx->sc);
+    count_launch(ctx);
+  } else {
+    if (ctx->B.dt == MAD_F64) launch_b_rows<double>(ctx, st); else launch_b_rows<float>(ctx, st);
+    if (ctx->A.dt == MAD_F64) launch_a_rows<double>(ctx, st); else launch_a_rows<float>(ctx, st);
+    if (ctx->B.dt == MAD_F64) launch_transpose<double>(ctx, st); else launch_transpose<float>(ctx, st);
+  }
+  const float* r = ctx->integer ? nullptr : ctx->r;
+  const unsigned long long* r64 = ctx->integer ? ctx->r64 : nullptr;
+  k_t1_chunk_sums<<<(unsigned)chunks, 256, 0, st>>>(r, r64, ctx->m, clog2m, partial, ctx->sc);
+  k_t1_chunk_offsets<<<1, 32, 0, st>>>(partial, chunks, ctx->sc);
+  k_t1_write<<<(unsigned)chunks, 256, 0, st>>>(r, r64, ctx->m, clog2m, partial, ctx->T1, ctx->sc);
+  count_launch(ctx, 3);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace mad

@@ -1,0 +1,94 @@
+"""Status codes of the C ABI on a GPU: every error is reported, none traps."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _dense_inputs(m=200, d=10, n=300, seed=1):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return (torch.from_numpy(rng.standard_normal((m, d)).astype(np.float32)).cuda(),
+            torch.from_numpy(rng.standard_normal((d, n)).astype(np.float32)).cuda())
+
+
+def test_sample_before_tables_is_a_state_error():
+    import paper_1506_03872_gb300 as mad
+    with mad.Context() as c:
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_sample(c.ctx, 10, 1)
+        assert e.value.status == mad.MAD_ERR_STATE
+
+
+def test_bad_flags_and_shapes():
+    import paper_1506_03872_gb300 as mad
+    with pytest.raises(mad.MadError) as e:
+        mad.mad_create(64)
+    assert e.value.status == mad.MAD_ERR_ARG
+    A, B = _dense_inputs()
+    with mad.Context() as c:
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_build_tables(c.ctx, mad.dense(A), mad.dense(B[:5]), 100)
+        assert e.value.status == mad.MAD_ERR_ARG
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_set_hash_capacity(c.ctx, 1000)   # not a power of two
+        assert e.value.status == mad.MAD_ERR_ARG
+
+
+def test_zero_matrix_is_empty():
+    import paper_1506_03872_gb300 as mad
+    A, B = _dense_inputs()
+    A.zero_()
+    with mad.Context() as c:
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_build_tables(c.ctx, mad.dense(A), mad.dense(B), 100)
+        assert e.value.status == mad.MAD_ERR_EMPTY
+
+
+def test_more_diamonds_than_s_max_overflows():
+    import paper_1506_03872_gb300 as mad
+    A, B = _dense_inputs()
+    with mad.Context() as c:
+        mad.mad_build_tables(c.ctx, mad.dense(A), mad.dense(B), 1000)
+        mad.mad_sample(c.ctx, 600, 1)
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_sample(c.ctx, 600, 1, 600)
+        assert e.value.status == mad.MAD_ERR_OVERFLOW
+        mad.mad_reset_hash(c.ctx)
+        mad.mad_sample(c.ctx, 1000, 1)      # allowed again after a reset
+
+
+def test_hash_too_small_reports_hash_full():
+    import paper_1506_03872_gb300 as mad
+    A, B = _dense_inputs(m=2000, n=3000)
+    with mad.Context() as c:
+        mad.mad_set_hash_capacity(c.ctx, 1024)
+        mad.mad_build_tables(c.ctx, mad.dense(A), mad.dense(B), 100_000)
+        mad.mad_sample(c.ctx, 100_000, 1)
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_topk(c.ctx, 10)
+        assert e.value.status == mad.MAD_ERR_HASH_FULL
+        assert mad.mad_stats(c.ctx)["device_error"] != 0
+    # the device stays usable
+    x = torch.ones(4, device="cuda")
+    assert float(x.sum()) == 4.0
+
+
+def test_unsupported_mixed_formats():
+    import paper_1506_03872_gb300 as mad
+    A, B = _dense_inputs()
+    rowptr = torch.zeros(11, dtype=torch.int64, device="cuda")
+    colidx = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with mad.Context() as c:
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_build_tables(c.ctx, mad.dense(A), mad.csr(rowptr, colidx, (10, 300)), 100)
+        assert e.value.status == mad.MAD_ERR_UNSUPPORTED
