@@ -180,6 +180,30 @@ mad_status mad_topk(mad_ctx* ctx, uint32_t tprime, mad_pair* out_dev, uint32_t* 
 mad_status mad_rescore(mad_ctx* ctx, const mad_pair* cand_dev, uint32_t ncand, uint32_t t,
                        mad_pair* out_dev, uint32_t* n_out_host, mad_stream stream);
 
+/* Rescoring and top-t without any device allocation.
+ *
+ * The paper has no counterpart to this entry point.  It returns exactly what
+ * mad_rescore returns (same pairs, same bits) for callers that cannot
+ * allocate device memory: applications whose GPU memory is reserved up
+ * front by another allocator (serving stacks, host frameworks), and loops
+ * that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ * It needs no context: A and B are the matrices the candidates index (the
+ * formats of mad_build_tables; dense B is read in place), and the caller
+ * owns every buffer passed in.
+ *
+ * Limit: ncand <= MAD_NOALLOC_MAX_CANDIDATES; larger requests return
+ * MAD_ERR_UNSUPPORTED.  The working memory is one fixed static device array
+ * (about 1.8 MB) that each GPU loading the library keeps until the process
+ * exits.  The first call on a device looks up that array's device address;
+ * make that first call before any stream capture.  All calls share the
+ * array and each clears what must start at zero, so calls that overlap on
+ * the GPU (other streams or host threads) race: serialise them.  A
+ * candidate outside A or B returns MAD_ERR_ARG.  Synchronises the stream. */
+#define MAD_NOALLOC_MAX_CANDIDATES 16384u
+mad_status mad_rescore_noalloc(const mad_matrix* A, const mad_matrix* B, const mad_pair* cand_dev,
+                               uint32_t ncand, uint32_t t, mad_pair* out_dev,
+                               uint32_t* n_out_host, mad_stream stream);
+
 /* Counters and table scalars (synchronises the device). */
 mad_status mad_stats(mad_ctx* ctx, mad_stats_t* out);
 

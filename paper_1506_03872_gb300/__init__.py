@@ -31,8 +31,9 @@ TABLES = {"T1": 0, "T2": 1, "TA": 2, "TB": 3, "na": 4, "nb": 5, "r": 6}
 EXPORTS = (
     "mad_create", "mad_destroy", "mad_strerror", "mad_set_hash_capacity", "mad_build_tables",
     "mad_sample", "mad_reset_hash", "mad_topk", "mad_rescore", "mad_stats", "mad_debug_draws",
-    "mad_debug_draws_list", "mad_export_x", "mad_export_table",
+    "mad_debug_draws_list", "mad_export_x", "mad_export_table", "mad_rescore_noalloc",
 )
+MAD_NOALLOC_MAX_CANDIDATES = 16384
 
 
 class mad_matrix(ctypes.Structure):
@@ -86,6 +87,8 @@ def lib() -> ctypes.CDLL:
         L.mad_topk.argtypes = [P, u32, P, ctypes.POINTER(u32), P]
         L.mad_rescore.argtypes = [P, P, u32, u32, P, ctypes.POINTER(u32), P]
         L.mad_stats.argtypes = [P, ctypes.POINTER(mad_stats_t)]
+        L.mad_rescore_noalloc.argtypes = [ctypes.POINTER(mad_matrix), ctypes.POINTER(mad_matrix),
+                                          P, u32, u32, P, ctypes.POINTER(u32), P]
         L.mad_debug_draws.argtypes = [P, u64, u64, u64, P, P, P, P, P, P]
         L.mad_debug_draws_list.argtypes = [P, u64, P, u64, P, P, P, P, P, P]
         L.mad_export_x.argtypes = [P, P, P, u64, ctypes.POINTER(u64), P]
@@ -192,6 +195,20 @@ def mad_rescore(ctx, cand, ncand: int, t: int, out=None, stream=None):
     n = ctypes.c_uint32(0)
     _check(lib().mad_rescore(ctx, _ptr(cand), ncand, t, _ptr(out), ctypes.byref(n),
                              _stream(stream)), "mad_rescore")
+    return out, n.value
+
+
+def mad_rescore_noalloc(A: mad_matrix, B: mad_matrix, cand, ncand: int, t: int, out=None,
+                        stream=None):
+    """mad_rescore without device allocation inside the library (the caller
+    owns every buffer).  For callers that cannot allocate GPU memory; at most
+    MAD_NOALLOC_MAX_CANDIDATES candidates per call."""
+    if out is None:
+        out = new_pairs(t)
+    n = ctypes.c_uint32(0)
+    _check(lib().mad_rescore_noalloc(ctypes.byref(A), ctypes.byref(B), _ptr(cand), ncand, t,
+                                     _ptr(out), ctypes.byref(n), _stream(stream)),
+           "mad_rescore_noalloc")
     return out, n.value
 
 

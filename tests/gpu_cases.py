@@ -80,7 +80,8 @@ class Case:
             self.A, self.B = A, B
             tA = torch.from_numpy(A).cuda()
             tB = torch.from_numpy(B).cuda()
-            self.ctx.build(mad.dense(tA), mad.dense(tB), s_max, keep=(tA, tB))
+            self.Am, self.Bm = mad.dense(tA), mad.dense(tB)
+            self.ctx.build(self.Am, self.Bm, s_max, keep=(tA, tB))
             self.oracle = oracle.Oracle(oracle.Matrix(A), oracle.Matrix(B), flags, s_max)
             self.m, self.d, self.n = A.shape[0], A.shape[1], B.shape[1]
         else:
@@ -95,8 +96,8 @@ class Case:
                 shapeA, shapeB = Ad.shape, Bd.shape
             self.csr = (ra, ca, rb, cb)
             t = [torch.from_numpy(x).cuda() for x in (ra, ca, rb, cb)]
-            self.ctx.build(mad.csr(t[0], t[1], shapeA), mad.csr(t[2], t[3], shapeB), s_max,
-                           keep=tuple(t))
+            self.Am, self.Bm = mad.csr(t[0], t[1], shapeA), mad.csr(t[2], t[3], shapeB)
+            self.ctx.build(self.Am, self.Bm, s_max, keep=tuple(t))
             self.oracle = oracle.Oracle(oracle.Matrix(rowptr=ra, colidx=ca, shape=shapeA),
                                         oracle.Matrix(rowptr=rb, colidx=cb, shape=shapeB),
                                         flags, s_max)
