@@ -248,6 +248,7 @@ def run_ours(args):
     gi, gj, gx, gc = mad.decode_pairs(res, nr)
     recall = None
     tau = None
+    truth = set()
     if not w.csr and rank == 0 and not args.no_recall:
         truth, tau = _ground_truth_dense(tensors[0], tensors[1], t)
         got = set(mad.keys_of(gi, gj).astype(np.int64).tolist())
@@ -292,6 +293,36 @@ def run_ours(args):
                 "traffic": (round(rec["bytes_per_diamond"] * s) if rec else None),
                 "algorithmic_bytes_per_launch": alg_bytes}
 
+    # The dense exact comparator (BF16 tensor-core GEMM + fused top filter +
+    # FP32 rescore) on the same inputs, timed the same way.
+    comp = None
+    if not w.csr and not args.no_comparator:
+        try:
+            out_cmp = mad.new_pairs(t)
+            for _ in range(max(2, args.warmup)):
+                mad.mad_dense_topt(ctx.ctx, Am, Bm, t, args.rescore, out=out_cmp)
+            cms = []
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                c0, c1 = ev(), ev()
+                c0.record(stream)
+                res_c, nrc = mad.mad_dense_topt(ctx.ctx, Am, Bm, t, args.rescore, out=out_cmp)
+                c1.record(stream)
+                torch.cuda.synchronize()
+                cms.append(c0.elapsed_time(c1))
+            ci, cj, _, _ = mad.decode_pairs(res_c, nrc)
+            kp = 64 if w.d <= 64 else 128
+            cm = float(np.mean(cms))
+            comp = {"kernel": "k_gemm_topk", "ms": round(cm, 4),
+                    "rescore": args.rescore or 8 * t,
+                    "tflops_useful": round(2.0 * w.m * w.n * w.d / (cm / 1e3) / 1e12, 1),
+                    "tflops_issued": round(2.0 * w.m * w.n * kp / (cm / 1e3) / 1e12, 1)}
+            if recall is not None:
+                got_c = set(mad.keys_of(ci, cj).astype(np.int64).tolist())
+                comp["recall"] = len(got_c & truth) / t
+        except Exception as ex:  # the comparator must not cost the main line
+            comp = {"error": str(ex)[:200]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, args.cpu_diamonds)
@@ -314,6 +345,10 @@ def run_ours(args):
                     "unit": "diamonds/s", "ms_per_step": round(e2e_total / args.steps, 4),
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
+            "comparator": comp,
+            "time_to_top_t": {"sampling_ms": round(ms_per_step, 4), "sampling_recall": recall,
+                              "comparator_ms": comp.get("ms") if comp else None,
+                              "comparator_recall": comp.get("recall") if comp else None},
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clk,
@@ -386,6 +421,9 @@ def main():
     ap.add_argument("--cpu-diamonds", type=int, default=2_000_000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-recall", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--rescore", type=int, default=0,
+                    help="comparator FP32 rescore budget (0: 8t)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

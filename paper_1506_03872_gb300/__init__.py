@@ -32,6 +32,7 @@ EXPORTS = (
     "mad_create", "mad_destroy", "mad_strerror", "mad_set_hash_capacity", "mad_build_tables",
     "mad_sample", "mad_reset_hash", "mad_topk", "mad_rescore", "mad_stats", "mad_debug_draws",
     "mad_debug_draws_list", "mad_export_x", "mad_export_table", "mad_rescore_noalloc",
+    "mad_dense_topt", "mad_debug_dense_product",
 )
 MAD_NOALLOC_MAX_CANDIDATES = 16384
 
@@ -89,6 +90,10 @@ def lib() -> ctypes.CDLL:
         L.mad_stats.argtypes = [P, ctypes.POINTER(mad_stats_t)]
         L.mad_rescore_noalloc.argtypes = [ctypes.POINTER(mad_matrix), ctypes.POINTER(mad_matrix),
                                           P, u32, u32, P, ctypes.POINTER(u32), P]
+        L.mad_dense_topt.argtypes = [P, ctypes.POINTER(mad_matrix), ctypes.POINTER(mad_matrix), u32,
+                                     u32, P, ctypes.POINTER(u32), P]
+        L.mad_debug_dense_product.argtypes = [P, ctypes.POINTER(mad_matrix),
+                                              ctypes.POINTER(mad_matrix), P, P]
         L.mad_debug_draws.argtypes = [P, u64, u64, u64, P, P, P, P, P, P]
         L.mad_debug_draws_list.argtypes = [P, u64, P, u64, P, P, P, P, P, P]
         L.mad_export_x.argtypes = [P, P, P, u64, ctypes.POINTER(u64), P]
@@ -210,6 +215,27 @@ def mad_rescore_noalloc(A: mad_matrix, B: mad_matrix, cand, ncand: int, t: int, 
                                      _ptr(out), ctypes.byref(n), _stream(stream)),
            "mad_rescore_noalloc")
     return out, n.value
+
+
+def mad_dense_topt(ctx, A: mad_matrix, B: mad_matrix, t: int, rescore: int = 0, out=None,
+                   stream=None):
+    """Top-t of |A B| by the BF16 tensor-core comparator (Sec. 4.3); the
+    `rescore` largest BF16 products (0: 8t) are rescored in FP32."""
+    if out is None:
+        out = new_pairs(t)
+    n = ctypes.c_uint32(0)
+    _check(lib().mad_dense_topt(ctx, ctypes.byref(A), ctypes.byref(B), t, rescore, _ptr(out),
+                                ctypes.byref(n), _stream(stream)), "mad_dense_topt")
+    return out, n.value
+
+
+def mad_debug_dense_product(ctx, A: mad_matrix, B: mad_matrix, stream=None):
+    """The comparator's BF16 product A B as an FP32 (m, n) CUDA tensor."""
+    import torch
+    c = torch.empty((A.rows, B.cols), dtype=torch.float32, device="cuda")
+    _check(lib().mad_debug_dense_product(ctx, ctypes.byref(A), ctypes.byref(B), _ptr(c),
+                                         _stream(stream)), "mad_debug_dense_product")
+    return c
 
 
 def mad_stats(ctx) -> dict:

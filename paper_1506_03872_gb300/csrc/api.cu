@@ -62,7 +62,11 @@ void free_tables(mad_ctx* ctx, cudaStream_t st) {
   free_async(ctx->bt, st);
   free_async(ctx->hkeys, st);
   free_async(ctx->hvals, st);
+  free_async(ctx->hreg, st);
+  free_async(ctx->T1c, st);
+  free_async(ctx->TBc, st);
   ctx->built = false;
+  ctx->regioned = false;
 }
 
 template <typename T>
@@ -215,20 +219,51 @@ mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
     ctx->bt = bt;
   }
   if ((rs = alloc(ctx->T1, (size_t)ctx->m, st)) != MAD_OK) return rs;
+  // Coarse search indices staged in shared memory by the sampling kernels:
+  // T1 in at most 16 KB, all rows of TB (dense) in at most 40 KB.
+  ctx->t1c_lg = 4;
+  while ((((uint64_t)ctx->m + (1ull << ctx->t1c_lg) - 1) >> ctx->t1c_lg) * 8 > 16384) ++ctx->t1c_lg;
+  ctx->t1c_n = (int64_t)(((uint64_t)ctx->m + (1ull << ctx->t1c_lg) - 1) >> ctx->t1c_lg);
+  if ((rs = alloc(ctx->T1c, (size_t)ctx->t1c_n, st)) != MAD_OK) return rs;
+  if (dense) {
+    ctx->tbc_lg = 4;
+    while ((uint64_t)ctx->d * ((((uint64_t)ctx->n + (1ull << ctx->tbc_lg) - 1) >> ctx->tbc_lg)) * 4 >
+           40960)
+      ++ctx->tbc_lg;
+    ctx->tbc_n = (int64_t)(((uint64_t)ctx->n + (1ull << ctx->tbc_lg) - 1) >> ctx->tbc_lg);
+    if ((rs = alloc(ctx->TBc, (size_t)(ctx->d * ctx->tbc_n), st)) != MAD_OK) return rs;
+  } else {
+    ctx->tbc_n = 0;
+  }
+  // Dense inputs get a hash with per-row home regions (sized after T1);
+  // 0/1 inputs, or an explicit capacity, a plain power-of-two table.
+  ctx->regioned = dense && ctx->hcap_request == 0;
   uint64_t cap = ctx->hcap_request;
-  if (cap == 0) {
+  if (ctx->regioned) {
+    cap = hash_region_bound((uint64_t)ctx->m, s_max);
+    if ((rs = alloc(ctx->hreg, (size_t)ctx->m + 1, st)) != MAD_OK) return rs;
+  } else if (cap == 0) {
     const double want = (double)s_max / 0.6;
     cap = 1024;
     while ((double)cap < want && cap < (1ull << 40)) cap <<= 1;
   }
-  ctx->hcap = cap;
+  ctx->hcap = ctx->hcap_alloc = cap;
   if ((rs = alloc(ctx->hkeys, cap, st)) != MAD_OK) return rs;
   if ((rs = alloc(ctx->hvals, cap, st)) != MAD_OK) return rs;
   cudaMemsetAsync(ctx->sc, 0, sizeof(DevScalars), st);
-  if ((rs = clear_hash(ctx, st)) != MAD_OK) return rs;
   if ((rs = build_tables_impl(ctx, st)) != MAD_OK) return rs;
+  if (ctx->regioned && (rs = build_hash_regions(ctx, st)) != MAD_OK) return rs;
   DevScalars hs;
-  if ((rs = read_scalars(ctx, &hs, st)) != MAD_OK) return rs;
+  if (ctx->regioned) {
+    unsigned long long used = 0;
+    cudaMemcpyAsync(&used, ctx->hreg + ctx->m, sizeof(used), cudaMemcpyDeviceToHost, st);
+    if ((rs = read_scalars(ctx, &hs, st)) != MAD_OK) return rs;
+    if (used == 0 || used > cap) return MAD_ERR_STATE;
+    ctx->hcap = used;
+  } else if ((rs = read_scalars(ctx, &hs, st)) != MAD_OK) {
+    return rs;
+  }
+  if ((rs = clear_hash(ctx, st)) != MAD_OK) return rs;
   if (hs.err & DERR_OVERFLOW) return MAD_ERR_OVERFLOW;
   if (ctx->integer) {
     if (hs.t1_total == 0) return MAD_ERR_EMPTY;
@@ -276,14 +311,10 @@ mad_status mad_topk(mad_ctx* ctx, uint32_t tprime, mad_pair* out_dev, uint32_t* 
   if (tprime == 0 || bound == 0) return MAD_OK;
   if ((rs = ensure_scratch(ctx, select_ws_bytes(bound, tprime), st)) != MAD_OK) return rs;
   const SelectWs ws = select_ws_carve(ctx->scratch, bound, tprime);
-  uint64_t npos = 0;
-  if ((rs = compact_positive(ctx, ws, &npos, st)) != MAD_OK) return rs;
-  if ((rs = read_scalars(ctx, &hs, st)) != MAD_OK) return rs;
-  ctx->distinct = hs.distinct;
+  uint64_t npos = 0, nsel = 0;
+  if ((rs = select_from_hash(ctx, ws, tprime, &nsel, &npos, st)) != MAD_OK) return rs;
   ctx->positive = npos;
-  uint64_t nsel = 0;
-  if ((rs = select_run(ctx, ws, npos, tprime, significant_bytes(hs.maxp), &nsel, st)) != MAD_OK)
-    return rs;
+  ctx->distinct = hs.new_keys;
   if ((rs = items_to_pairs(ctx, ws.out, nsel, nullptr, nullptr, out_dev, st)) != MAD_OK) return rs;
   if ((rs = cuda_status(cudaStreamSynchronize(st))) != MAD_OK) return rs;
   *n_out_host = (uint32_t)nsel;
@@ -305,7 +336,7 @@ mad_status mad_rescore(mad_ctx* ctx, const mad_pair* cand_dev, uint32_t ncand, u
   double* cvals = (double*)((char*)ctx->scratch + cv_off);
   if ((rs = rescore_items(ctx, cand_dev, ncand, ws.l0, cvals, st)) != MAD_OK) return rs;
   uint64_t nsel = 0;
-  if ((rs = select_run(ctx, ws, ncand, t, 8, &nsel, st)) != MAD_OK) return rs;
+  if ((rs = select_list(ctx, ws, ncand, t, 8, &nsel, st)) != MAD_OK) return rs;
   if ((rs = items_to_pairs(ctx, ws.out, nsel, cand_dev, cvals, out_dev, st)) != MAD_OK) return rs;
   DevScalars hs;
   if ((rs = read_scalars(ctx, &hs, st)) != MAD_OK) return rs;
@@ -338,6 +369,29 @@ mad_status mad_stats(mad_ctx* ctx, mad_stats_t* out) {
   out->integer_mode = ctx->integer ? 1u : 0u;
   out->device_error = hs.err;
   return MAD_OK;
+}
+
+mad_status mad_dense_topt(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, uint32_t t,
+                          uint32_t rescore, mad_pair* out_dev, uint32_t* n_out_host,
+                          mad_stream stream) {
+  if (!ctx || !A || !B || !n_out_host || !out_dev || t == 0) return MAD_ERR_ARG;
+  *n_out_host = 0;
+  if (!valid_dense(A) || !valid_dense(B)) return MAD_ERR_UNSUPPORTED;
+  if (B->rows != A->cols || A->rows >= (1ll << 31) || B->cols >= (1ll << 31)) return MAD_ERR_ARG;
+  if (rescore == 0) rescore = 8 * t;
+  if (A->cols > 128 || rescore < t || rescore > 2048) return MAD_ERR_UNSUPPORTED;
+  return dense_comparator(ctx, A, B, t, rescore, out_dev, n_out_host, nullptr,
+                          (cudaStream_t)stream);
+}
+
+mad_status mad_debug_dense_product(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B,
+                                   float* c_dev, mad_stream stream) {
+  if (!ctx || !A || !B || !c_dev) return MAD_ERR_ARG;
+  if (!valid_dense(A) || !valid_dense(B)) return MAD_ERR_UNSUPPORTED;
+  if (B->rows != A->cols || A->rows >= (1ll << 31) || B->cols >= (1ll << 31)) return MAD_ERR_ARG;
+  if (A->cols > 128) return MAD_ERR_UNSUPPORTED;
+  uint32_t dummy = 0;
+  return dense_comparator(ctx, A, B, 1, 1, nullptr, &dummy, c_dev, (cudaStream_t)stream);
 }
 
 mad_status mad_debug_draws(mad_ctx* ctx, uint64_t seed, uint64_t first, uint64_t count,

@@ -1,0 +1,727 @@
+// Exact-computation comparator of Sec. 4.3, rebuilt for GB300 tensor cores:
+// the top t of |A B| for dense A (m x d) and B (d x n).
+//
+// The paper streams dgemm column blocks through a priority queue.  Here:
+//  1. A and B^T are cast to BF16, K padded with zeros to 64 or 128.
+//  2. One persistent kernel per SM computes C~ = A B tile by tile with
+//     tcgen05.mma (BF16 in, FP32 accumulate in TMEM), operands brought into
+//     shared memory by TMA (128-byte swizzle), and never writes C~: its
+//     epilogue keeps only entries with |c~| >= theta in a per-CTA buffer.
+//     theta starts at 0 and rises whenever the buffer is compacted to its
+//     K_keep largest entries (the rescore budget, 8t by default) (a tile that overflows the buffer is
+//     rescanned from TMEM above the new theta); CTAs share theta
+//     through an atomicMax, so every kept threshold is a lower bound of the
+//     global K_keep-th largest |c~| and no entry of the global top K_keep is
+//     ever dropped.
+//  3. The K_keep largest |c~| of the merged buffers are rescored exactly in FP32
+//     and the t largest |c| returned.
+// Warp roles per CTA (192 threads): warp 0 issues TMA, warp 1 allocates TMEM
+// and issues the MMAs, warps 2-5 drain the accumulators (one TMEM lane
+// quarter each).  Two TMEM accumulators (2 x 256 columns) and two B stages
+// overlap loads, MMAs and the epilogue.  Every wait is bounded by a clock
+// limit after which the CTA sets an error flag and winds down.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "mad_device.cuh"
+#include "mad_internal.cuh"
+
+namespace mad {
+namespace {
+
+constexpr int BM = 128;             // rows of A per tile (TMEM lanes)
+constexpr int BN = 256;             // columns of C per tile (TMEM columns)
+constexpr int KATOM = 64;           // BF16 elements per 128-byte swizzle row
+constexpr int MAXKP = 128;          // padded K handled by this kernel
+constexpr int NSTAGE = 2;           // B pipeline depth
+constexpr int CAND_CAP = 4096;      // per-CTA candidate buffer
+constexpr int CAND_TRIGGER = 2048;  // compact before a tile when above this
+constexpr int kThreads = 192;
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s: a wait this long is a fault
+
+constexpr int A_BYTES = BM * MAXKP * 2;                 // 32 KB
+constexpr int B_STAGE_BYTES = BN * MAXKP * 2;           // 64 KB
+constexpr int SMEM_A = 0;
+constexpr int SMEM_B = SMEM_A + A_BYTES;
+constexpr int SMEM_CV = SMEM_B + NSTAGE * B_STAGE_BYTES;           // float[CAND_CAP]
+constexpr int SMEM_CK = SMEM_CV + CAND_CAP * 4;                    // u64[CAND_CAP]
+constexpr int SMEM_TOTAL = SMEM_CK + CAND_CAP * 8;
+constexpr int SMEM_ALLOC = SMEM_TOTAL + 1024;                      // alignment slack
+
+struct GemmArgs {
+  int64_t m, n;
+  int kp;                            // padded K (64 or 128)
+  int64_t tiles_m, tiles_n;
+  int kkeep;                         // entries kept per CTA at compaction
+  unsigned int* g_theta;             // shared threshold (FP32 bits)
+  unsigned int* g_err;
+  float* cand_val;                   // merged candidates
+  unsigned long long* cand_key;
+  unsigned long long* cand_count;
+  unsigned long long cand_cap;
+  float* dense_out;                  // diagnostics: full C~ (m x n) when set
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the CTA is aborting or the limit passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw128(const void* p) {
+  const uint32_t addr = smem_u32(p);
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = BM, N = BN.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Barrier among the 128 epilogue threads only.
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+struct Shared {
+  uint64_t a_full, a_empty, done;
+  uint64_t b_full[NSTAGE], b_empty[NSTAGE];
+  uint64_t acc_full[2], acc_empty[2];
+  uint32_t tmem_base;
+  int abort_flag;
+  int epi_abort;           // uniform exit decision of the four epilogue warps
+  unsigned int count;      // candidates in the buffer
+  unsigned int overflow;
+  float theta;
+  unsigned int hist[256];  // compaction
+  unsigned int sel_prefix, sel_mask, sel_krem, sel_pick;
+};
+
+// The kkeep-th largest value among vals[0..n) (all >= 0) by MSB radix
+// select on the FP32 bits; run by the 128 epilogue threads.
+__device__ float epi_kth_largest(const float* vals, unsigned n, unsigned kkeep, Shared* sh, int et) {
+  if (et == 0) {
+    sh->sel_prefix = 0;
+    sh->sel_mask = 0;
+    sh->sel_krem = kkeep;
+  }
+  for (int pass = 0; pass < 4; ++pass) {
+    for (int b = et; b < 256; b += 128) sh->hist[b] = 0;
+    epi_sync();
+    const unsigned prefix = sh->sel_prefix, mask = sh->sel_mask;
+    const int shift = 24 - 8 * pass;
+    for (unsigned x = et; x < n; x += 128) {
+      const unsigned bits = __float_as_uint(vals[x]);
+      if ((bits & mask) == prefix) atomicAdd(&sh->hist[(bits >> shift) & 0xFFu], 1u);
+    }
+    epi_sync();
+    if (et == 0) {
+      unsigned above = 0;
+      int b = 255;
+      for (; b > 0; --b) {
+        if (above + sh->hist[b] >= sh->sel_krem) break;
+        above += sh->hist[b];
+      }
+      sh->sel_krem -= above;
+      sh->sel_prefix |= (unsigned)b << shift;
+      sh->sel_mask |= 0xFFu << shift;
+    }
+    epi_sync();
+  }
+  return __uint_as_float(sh->sel_prefix);
+}
+
+// Keep buffer entries [0, n) with value >= theta, in place and in order
+// (each thread compacts a contiguous block; blocks are placed by a scan).
+__device__ unsigned epi_compact(float* cv, unsigned long long* ck, unsigned n, float theta,
+                                Shared* sh, int et) {
+  __shared__ unsigned int part[128];
+  const unsigned per = (n + 127) / 128;
+  const unsigned lo = et * per, hi = min(n, lo + per);
+  unsigned keep = 0;
+  for (unsigned x = lo; x < hi; ++x) keep += cv[x] >= theta ? 1u : 0u;
+  part[et] = keep;
+  epi_sync();
+  if (et == 0) {
+    unsigned acc = 0;
+    for (int q = 0; q < 128; ++q) {
+      const unsigned v = part[q];
+      part[q] = acc;
+      acc += v;
+    }
+    sh->count = acc;
+  }
+  epi_sync();
+  unsigned dst = part[et];
+  for (unsigned x = lo; x < hi; ++x) {
+    if (cv[x] >= theta) {
+      cv[dst] = cv[x];
+      ck[dst] = ck[x];
+      ++dst;
+    }
+  }
+  epi_sync();
+  return sh->count;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            const GemmArgs args) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem + SMEM_A;
+  unsigned char* sB = smem + SMEM_B;
+  float* cv = (float*)(smem + SMEM_CV);
+  unsigned long long* ck = (unsigned long long*)(smem + SMEM_CK);
+  __shared__ Shared shared_state;
+  Shared* sh = &shared_state;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int* abort_flag = &sh->abort_flag;
+
+  const long long total_tiles = args.tiles_m * args.tiles_n;
+  const long long t_begin = total_tiles * blockIdx.x / gridDim.x;
+  const long long t_end = total_tiles * (blockIdx.x + 1) / gridDim.x;
+  const int katoms = args.kp / KATOM;
+  const int ksteps = args.kp / 16;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&sh->a_full, 1);
+    mbar_init(&sh->a_empty, 1);
+    mbar_init(&sh->done, 1);
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&sh->b_full[s], 1);
+      mbar_init(&sh->b_empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh->acc_full[b], 1);
+      mbar_init(&sh->acc_empty[b], 4);
+    }
+    sh->abort_flag = 0;
+    sh->epi_abort = 0;
+    sh->count = 0;
+    sh->overflow = 0;
+    sh->theta = __uint_as_float(*((volatile unsigned int*)args.g_theta));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&sh->tmem_base)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem_base = sh->tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      long long prev_rb = -1, panel = 0;
+      for (long long t = t_begin; t < t_end && !*abort_flag; ++t) {
+        const long long it = t - t_begin;
+        const long long rb = t / args.tiles_n, cb = t % args.tiles_n;
+        if (rb != prev_rb) {
+          if (panel > 0 && !mbar_wait(&sh->a_empty, (uint32_t)((panel - 1) & 1), abort_flag)) break;
+          mbar_expect_tx(&sh->a_full, (uint32_t)(BM * args.kp * 2));
+          for (int ka = 0; ka < katoms; ++ka)
+            tma_load_2d(sA + ka * (BM * 128), &tmA, &sh->a_full, ka * KATOM, (int)(rb * BM));
+          prev_rb = rb;
+          ++panel;
+        }
+        const int s = (int)(it % NSTAGE);
+        const long long use = it / NSTAGE;
+        if (use > 0 && !mbar_wait(&sh->b_empty[s], (uint32_t)((use - 1) & 1), abort_flag)) break;
+        unsigned char* dstB = sB + s * B_STAGE_BYTES;
+        mbar_expect_tx(&sh->b_full[s], (uint32_t)(BN * args.kp * 2));
+        for (int ka = 0; ka < katoms; ++ka)
+          tma_load_2d(dstB + ka * (BN * 128), &tmB, &sh->b_full[s], ka * KATOM, (int)(cb * BN));
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      long long prev_rb = -1, panel = 0;
+      for (long long t = t_begin; t < t_end && !*abort_flag; ++t) {
+        const long long it = t - t_begin;
+        const long long rb = t / args.tiles_n;
+        if (rb != prev_rb) {
+          if (!mbar_wait(&sh->a_full, (uint32_t)(panel & 1), abort_flag)) break;
+          prev_rb = rb;
+          ++panel;
+        }
+        const int s = (int)(it % NSTAGE);
+        if (!mbar_wait(&sh->b_full[s], (uint32_t)((it / NSTAGE) & 1), abort_flag)) break;
+        const int buf = (int)(it & 1);
+        if (it >= 2 && !mbar_wait(&sh->acc_empty[buf], (uint32_t)(((it >> 1) - 1) & 1), abort_flag))
+          break;
+        fence_after_sync();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+        const unsigned char* tileB = sB + s * B_STAGE_BYTES;
+        for (int kk = 0; kk < ksteps; ++kk) {
+          const int ka = kk >> 2, ko = (kk & 3) * 32;  // atom and byte offset inside it
+          const uint64_t ad = desc_sw128(sA + ka * (BM * 128)) + (uint64_t)(ko >> 4);
+          const uint64_t bd = desc_sw128(tileB + ka * (BN * 128)) + (uint64_t)(ko >> 4);
+          mma_bf16(d_tmem, ad, bd, kk > 0 ? 1u : 0u);
+        }
+        mma_commit(&sh->b_empty[s]);
+        mma_commit(&sh->acc_full[buf]);
+        const bool panel_ends = (t + 1 == t_end) || ((t + 1) / args.tiles_n != rb);
+        if (panel_ends) mma_commit(&sh->a_empty);
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int et = threadIdx.x - 64;          // 0..127
+    const int quarter = warp & 3;             // TMEM lane quarter of this warp
+    const int row_in_tile = quarter * 32 + lane;
+    for (long long t = t_begin; t < t_end; ++t) {
+      const long long it = t - t_begin;
+      const long long rb = t / args.tiles_n, cb = t % args.tiles_n;
+      const int buf = (int)(it & 1);
+      // Compact first when the buffer is past its trigger.
+      if (!args.dense_out && sh->count > CAND_TRIGGER) {
+        const float th = epi_kth_largest(cv, sh->count, (unsigned)args.kkeep, sh, et);
+        epi_compact(cv, ck, sh->count, th, sh, et);
+        if (et == 0) {
+          sh->theta = fmaxf(sh->theta, th);
+          atomicMax(args.g_theta, __float_as_uint(sh->theta));
+        }
+        epi_sync();
+      }
+      // The four warps share named barriers below, so they leave together.
+      const bool ok = mbar_wait(&sh->acc_full[buf], (uint32_t)((it >> 1) & 1), abort_flag);
+      if (!ok) atomicOr(&sh->epi_abort, 1);
+      epi_sync();
+      if (*((volatile int*)&sh->epi_abort)) break;
+      fence_after_sync();
+      const int64_t row = rb * BM + row_in_tile;
+      const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN);
+      unsigned tile_start = sh->count;
+      for (int round = 0; round < 8; ++round) {
+        const float theta =
+            fmaxf(sh->theta, __uint_as_float(*((volatile unsigned int*)args.g_theta)));
+        for (int c = 0; c < BN / 32; ++c) {
+          float v[32];
+          tmem_ld32(taddr + (uint32_t)(c * 32), v);
+          const int64_t col0 = cb * BN + c * 32;
+          if (args.dense_out) {
+            if (row < args.m)
+              for (int q = 0; q < 32; ++q)
+                if (col0 + q < args.n) args.dense_out[row * args.n + col0 + q] = v[q];
+            continue;
+          }
+          float mx = 0.0f;
+#pragma unroll
+          for (int q = 0; q < 32; ++q) mx = fmaxf(mx, fabsf(v[q]));
+          if (mx >= theta && row < args.m) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              const float a = fabsf(v[q]);
+              if (a >= theta && col0 + q < args.n) {
+                const unsigned pos = atomicAdd(&sh->count, 1u);
+                if (pos < CAND_CAP) {
+                  cv[pos] = a;
+                  ck[pos] = ((unsigned long long)row << 32) | (unsigned long long)(col0 + q);
+                } else {
+                  sh->overflow = 1;
+                }
+              }
+            }
+          }
+        }
+        epi_sync();
+        if (!sh->overflow) break;
+        // Overflow: the buffer holds CAND_CAP real entries, so its kkeep-th
+        // largest is a valid lower bound.  Drop this tile's entries, tighten
+        // the earlier ones and rescan the tile (still in TMEM) above it.
+        const float th = epi_kth_largest(cv, CAND_CAP, (unsigned)args.kkeep, sh, et);
+        epi_compact(cv, ck, tile_start, th, sh, et);
+        if (et == 0) {
+          sh->theta = fmaxf(sh->theta, th);
+          sh->overflow = 0;
+          atomicMax(args.g_theta, __float_as_uint(sh->theta));
+        }
+        epi_sync();
+        tile_start = sh->count;  // the earlier tiles' survivors; the rescan appends after them
+        if (round == 7 && et == 0) atomicOr(args.g_err, 2u);  // pathological ties
+      }
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh->acc_empty[buf]);
+    }
+    // Publish this CTA's survivors.
+    epi_sync();
+    if (!args.dense_out) {
+      const float theta =
+          fmaxf(sh->theta, __uint_as_float(*((volatile unsigned int*)args.g_theta)));
+      const unsigned n = min(sh->count, (unsigned)CAND_CAP);
+      for (unsigned x = et; x < n; x += 128) {
+        if (cv[x] >= theta) {
+          const unsigned long long pos = atomicAdd(args.cand_count, 1ull);
+          if (pos < args.cand_cap) {
+            args.cand_val[pos] = cv[x];
+            args.cand_key[pos] = ck[x];
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && sh->abort_flag) atomicOr(args.g_err, 1u);
+  // Every MMA this CTA issued has completed: the epilogue consumed each
+  // accumulator (or the CTA aborted, in which case wait for the MMA queue).
+  if (warp == 1) {
+    if (sh->abort_flag && lane == 0) {
+      // Wait (bounded) for every MMA still queued before freeing TMEM.
+      mma_commit(&sh->done);
+      const long long t0 = clock64();
+      while (!mbar_try_wait(&sh->done, 0) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+    __syncwarp();
+    fence_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512)
+                 : "memory");
+  }
+}
+
+// ---- casts: FP32/FP64 -> BF16, K padded with zeros ------------------------
+template <typename T>
+__global__ void k_cast_rows_bf16(const T* __restrict__ src, int64_t rows, int64_t cols, int64_t ld,
+                                 int kp, __nv_bfloat16* __restrict__ dst) {
+  const int64_t total = rows * kp;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = x / kp, c = x % kp;
+    const float v = c < cols ? (float)src[r * ld + c] : 0.0f;
+    dst[x] = __float2bfloat16_rn(v);
+  }
+}
+
+// B (d x n) -> B^T (n x kp) in BF16.
+template <typename T>
+__global__ void k_cast_cols_bf16(const T* __restrict__ B, int64_t d, int64_t n, int64_t ldb, int kp,
+                                 __nv_bfloat16* __restrict__ dst) {
+  __shared__ float tile[32][33];
+  const int64_t j0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t k = k0 + r, j = j0 + threadIdx.x;
+    tile[r][threadIdx.x] = (k < d && j < n) ? (float)B[k * ldb + j] : 0.0f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t j = j0 + r, k = k0 + threadIdx.x;
+    if (j < n && k < kp) dst[j * kp + k] = __float2bfloat16_rn(tile[threadIdx.x][r]);
+  }
+}
+
+// FP32 rescore of the selected candidates: lane L sums k = L mod 32 with
+// fused multiply-add in FP32, then the partials fold in halves.
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(256)
+k_rescore_fp32(const Item* __restrict__ sel, unsigned long long nsel, const TA* __restrict__ A,
+               int64_t lda, const TB* __restrict__ B, int64_t ldb, int64_t d,
+               float* __restrict__ cvals, Item* __restrict__ items) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned long long q = warp; q < nsel; q += warps) {
+    const uint32_t i = (uint32_t)(sel[q].key >> 32), j = (uint32_t)sel[q].key;
+    float acc = 0.0f;
+    for (int64_t k = lane; k < d; k += 32)
+      acc = __fmaf_rn((float)A[(int64_t)i * lda + k], (float)B[k * ldb + j], acc);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, off));
+    if (lane == 0) {
+      cvals[q] = acc;
+      Item it;
+      it.p = (unsigned long long)__float_as_uint(fabsf(acc));
+      it.key = sel[q].key;
+      it.aux = q;
+      items[q] = it;
+    }
+  }
+}
+
+__global__ void k_cand_items(const float* __restrict__ val, const unsigned long long* __restrict__ key,
+                             unsigned long long n, Item* __restrict__ out) {
+  const unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  Item it;
+  it.p = (unsigned long long)__float_as_uint(val[x]);
+  it.key = key[x];
+  it.aux = x;
+  out[x] = it;
+}
+
+__global__ void k_fp32_pairs(const Item* __restrict__ items, unsigned long long n,
+                             const float* __restrict__ cvals, mad_pair* __restrict__ out) {
+  const unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  mad_pair pr;
+  pr.i = (uint32_t)(items[x].key >> 32);
+  pr.j = (uint32_t)items[x].key;
+  pr.x = 0;
+  pr.c = (double)cvals[items[x].aux];
+  out[x] = pr;
+}
+
+// ---- host side -----------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const void* base, uint64_t rows, int kp, uint32_t box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)KATOM, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename T>
+void launch_casts(const mad_matrix* A, const mad_matrix* B, int kp, __nv_bfloat16* Abf,
+                  __nv_bfloat16* Bbf, cudaStream_t st) {
+  const int64_t ta = A->rows * kp;
+  k_cast_rows_bf16<T><<<(unsigned)((ta + 255) / 256 < 152 * 32 ? (ta + 255) / 256 : 152 * 32), 256,
+                        0, st>>>((const T*)A->values, A->rows, A->cols, A->ld, kp, Abf);
+  dim3 grid((unsigned)((B->cols + 31) / 32), (unsigned)((kp + 31) / 32));
+  k_cast_cols_bf16<T><<<grid, dim3(32, 8), 0, st>>>((const T*)B->values, B->rows, B->cols, B->ld,
+                                                    kp, Bbf);
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+}  // namespace
+
+// Shared by mad_dense_topt and the diagnostic full-product entry point.
+mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, uint32_t t,
+                            uint32_t rescore, mad_pair* out, uint32_t* n_out, float* dense_out,
+                            cudaStream_t st) {
+  const int64_t m = A->rows, d = A->cols, n = B->cols;
+  if (d > MAXKP) return MAD_ERR_UNSUPPORTED;
+  const int kp = d <= 64 ? 64 : 128;
+  const int64_t tiles_m = (m + BM - 1) / BM, tiles_n = (n + BN - 1) / BN;
+  const int grid = (int)std::min<int64_t>(sm_count(), tiles_m * tiles_n);
+  const uint32_t kkeep = dense_out ? 1u : std::max(t, rescore);
+  if (!dense_out && kkeep > CAND_TRIGGER) return MAD_ERR_UNSUPPORTED;
+  const unsigned long long cand_cap = (unsigned long long)grid * CAND_CAP;
+  auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+  const size_t a_bytes = al((size_t)m * kp * 2), b_bytes = al((size_t)n * kp * 2);
+  const size_t cv_bytes = al(cand_cap * 4), ck_bytes = al(cand_cap * 8);
+  const size_t ws_bytes = al(select_ws_bytes(cand_cap, kkeep));
+  const size_t ws2_bytes = al(select_ws_bytes(kkeep, t ? t : 1));
+  const size_t cvals_bytes = al((size_t)kkeep * 4);
+  const size_t total = a_bytes + b_bytes + cv_bytes + ck_bytes + ws_bytes + ws2_bytes +
+                       cvals_bytes + 1024;
+  mad_status rs = ensure_scratch(ctx, total, st);
+  if (rs != MAD_OK) return rs;
+  char* p = (char*)ctx->scratch;
+  __nv_bfloat16* Abf = (__nv_bfloat16*)p;             p += a_bytes;
+  __nv_bfloat16* Bbf = (__nv_bfloat16*)p;             p += b_bytes;
+  float* cand_val = (float*)p;                        p += cv_bytes;
+  unsigned long long* cand_key = (unsigned long long*)p; p += ck_bytes;
+  char* wsb = p;                                      p += ws_bytes;
+  char* ws2b = p;                                     p += ws2_bytes;
+  float* cvals = (float*)p;                           p += cvals_bytes;
+  unsigned int* g_theta = (unsigned int*)p;
+  unsigned int* g_err = g_theta + 1;
+  unsigned long long* cand_count = (unsigned long long*)(g_theta + 2);
+  cudaMemsetAsync(g_theta, 0, 64, st);
+
+  if (A->dt == MAD_F64) launch_casts<double>(A, B, kp, Abf, Bbf, st);
+  else launch_casts<float>(A, B, kp, Abf, Bbf, st);
+  count_launch(ctx, 2);
+
+  CUtensorMap tmA, tmB;
+  if (!make_map(&tmA, Abf, (uint64_t)m, kp, BM) || !make_map(&tmB, Bbf, (uint64_t)n, kp, BN))
+    return MAD_ERR_CUDA;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_topk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_ALLOC);
+    if (e != cudaSuccess) return cuda_status(e);
+    attr_set = true;
+  }
+  GemmArgs ga;
+  ga.m = m;
+  ga.n = n;
+  ga.kp = kp;
+  ga.tiles_m = tiles_m;
+  ga.tiles_n = tiles_n;
+  ga.kkeep = (int)kkeep;
+  ga.g_theta = g_theta;
+  ga.g_err = g_err;
+  ga.cand_val = cand_val;
+  ga.cand_key = cand_key;
+  ga.cand_count = cand_count;
+  ga.cand_cap = cand_cap;
+  ga.dense_out = dense_out;
+  k_gemm_topk<<<grid, kThreads, SMEM_ALLOC, st>>>(tmA, tmB, ga);
+  count_launch(ctx);
+  if ((rs = cuda_status(cudaGetLastError())) != MAD_OK) return rs;
+
+  unsigned int herr = 0;
+  unsigned long long ncand = 0;
+  cudaMemcpyAsync(&herr, g_err, sizeof(herr), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&ncand, cand_count, sizeof(ncand), cudaMemcpyDeviceToHost, st);
+  if ((rs = cuda_status(cudaStreamSynchronize(st))) != MAD_OK) return rs;
+  if (herr & 1u) return MAD_ERR_CUDA;      // a pipeline wait timed out
+  if (dense_out) return MAD_OK;
+  if (herr & 2u) return MAD_ERR_STATE;     // candidate buffer could not be tightened
+  if (ncand > cand_cap) return MAD_ERR_STATE;
+
+  // 8t largest |c~| of the merged candidates, then the FP32 rescore.
+  const SelectWs ws = select_ws_carve(wsb, cand_cap, kkeep);
+  if (ncand) {
+    k_cand_items<<<(unsigned)((ncand + 255) / 256), 256, 0, st>>>(cand_val, cand_key, ncand, ws.l0);
+    count_launch(ctx);
+  }
+  uint64_t nsel = 0;
+  if ((rs = select_list(ctx, ws, ncand, kkeep, 4, &nsel, st)) != MAD_OK) return rs;
+  const SelectWs ws2 = select_ws_carve(ws2b, kkeep, t ? t : 1);
+  if (nsel) {
+    const unsigned long long blocks = (nsel * 32 + 255) / 256;
+    if (A->dt == MAD_F64 && B->dt == MAD_F64)
+      k_rescore_fp32<double, double><<<(unsigned)blocks, 256, 0, st>>>(
+          ws.out, nsel, (const double*)A->values, A->ld, (const double*)B->values, B->ld, d, cvals, ws2.l0);
+    else if (A->dt == MAD_F64)
+      k_rescore_fp32<double, float><<<(unsigned)blocks, 256, 0, st>>>(
+          ws.out, nsel, (const double*)A->values, A->ld, (const float*)B->values, B->ld, d, cvals, ws2.l0);
+    else if (B->dt == MAD_F64)
+      k_rescore_fp32<float, double><<<(unsigned)blocks, 256, 0, st>>>(
+          ws.out, nsel, (const float*)A->values, A->ld, (const double*)B->values, B->ld, d, cvals, ws2.l0);
+    else
+      k_rescore_fp32<float, float><<<(unsigned)blocks, 256, 0, st>>>(
+          ws.out, nsel, (const float*)A->values, A->ld, (const float*)B->values, B->ld, d, cvals, ws2.l0);
+    count_launch(ctx);
+  }
+  uint64_t nt = 0;
+  if ((rs = select_list(ctx, ws2, nsel, t, 4, &nt, st)) != MAD_OK) return rs;
+  if (nt) {
+    k_fp32_pairs<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(ws2.out, nt, cvals, out);
+    count_launch(ctx);
+  }
+  if ((rs = cuda_status(cudaStreamSynchronize(st))) != MAD_OK) return rs;
+  *n_out = (uint32_t)nt;
+  return MAD_OK;
+}
+
+}  // namespace mad

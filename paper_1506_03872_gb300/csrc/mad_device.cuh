@@ -89,6 +89,51 @@ __device__ __forceinline__ int64_t search_u32(const uint32_t* __restrict__ prefi
   return lo;
 }
 
+// The same searches through a coarse index (coarse[g] = prefix entry
+// min((g+1) 2^lg, len) - 1): the block whose last entry first exceeds the
+// target holds the answer, so the result equals the full search.
+__device__ __forceinline__ int64_t search_coarse_u64(const uint64_t* coarse, int64_t nc,
+                                                     const uint64_t* __restrict__ prefix,
+                                                     int64_t len, int lg,
+                                                     unsigned long long target, bool* bad) {
+  int64_t lo = 0, hi = nc;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((unsigned long long)coarse[mid] > target)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  if (lo >= nc) {
+    *bad = true;
+    lo = nc - 1;
+  }
+  const int64_t base = lo << lg;
+  const int64_t wlen = (len - base) < (1ll << lg) ? (len - base) : (1ll << lg);
+  return base + search_u64(prefix + base, wlen, target, bad);
+}
+
+__device__ __forceinline__ int64_t search_coarse_u32(const uint32_t* coarse, int64_t nc,
+                                                     const uint32_t* __restrict__ prefix,
+                                                     int64_t len, int lg, uint32_t target,
+                                                     uint32_t mask, bool* bad) {
+  int64_t lo = 0, hi = nc;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (coarse[mid] > target)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  if (lo >= nc) {
+    *bad = true;
+    lo = nc - 1;
+  }
+  const int64_t base = lo << lg;
+  const int64_t wlen = (len - base) < (1ll << lg) ? (len - base) : (1ll << lg);
+  return base + search_u32(prefix + base, wlen, target, mask, bad);
+}
+
 // Sorted-list membership (0/1 CSR closure test).
 __device__ __forceinline__ bool contains_sorted(const int32_t* __restrict__ list, int64_t len,
                                                 int32_t value) {
@@ -129,28 +174,38 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// Returns 0 when the probe limit is hit, 1 when the key existed, 2 when
-// this call created it.
-__device__ __forceinline__ int hash_add(unsigned long long* __restrict__ keys,
-                                        long long* __restrict__ vals, uint64_t mask,
-                                        uint32_t max_probe, unsigned long long key, long long v) {
-  uint64_t slot = mix64(key) & mask;
+// Linear probing from `slot`, wrapping at cap.  Returns 0 when the probe
+// limit is hit, 1 when the key existed, 2 when this call created it.
+__device__ __forceinline__ int hash_add_from(unsigned long long* __restrict__ keys,
+                                             long long* __restrict__ vals, uint64_t cap,
+                                             uint64_t slot, uint32_t max_probe,
+                                             unsigned long long key, long long v) {
   for (uint32_t probe = 0; probe < max_probe; ++probe) {
-    const unsigned long long cur = *((volatile unsigned long long*)keys + slot);
-    if (cur == key) {
+    // Claim-or-match in one atomic: the slot is ours when it was empty or
+    // already held the key.
+    const unsigned long long prev = atomicCAS(keys + slot, EMPTY_KEY, key);
+    if (prev == EMPTY_KEY || prev == key) {
       atomicAdd((unsigned long long*)vals + slot, (unsigned long long)v);
-      return 1;
+      return prev == EMPTY_KEY ? 2 : 1;
     }
-    if (cur == EMPTY_KEY) {
-      const unsigned long long prev = atomicCAS(keys + slot, EMPTY_KEY, key);
-      if (prev == EMPTY_KEY || prev == key) {
-        atomicAdd((unsigned long long*)vals + slot, (unsigned long long)v);
-        return prev == EMPTY_KEY ? 2 : 1;
-      }
-    }
-    slot = (slot + 1) & mask;
+    slot = (slot + 1 == cap) ? 0 : slot + 1;
   }
   return 0;
+}
+
+// First slot probed for key = (a << 32) | b.
+__device__ __forceinline__ uint64_t home_slot(const SampleParams& p, unsigned long long key) {
+  if (p.regioned) {
+    const uint32_t a = (uint32_t)(key >> 32);
+    const unsigned long long r0 = p.hreg[a];
+    const unsigned long long size = p.hreg[a + 1] - r0;  // a power of two
+    return r0 + (mix64(key) & (size - 1));
+  }
+  return mix64(key) & p.hmask;
+}
+
+__device__ __forceinline__ int hash_add(const SampleParams& p, unsigned long long key, long long v) {
+  return hash_add_from(p.hkeys, p.hvals, p.hcap, home_slot(p, key), p.max_probe, key, v);
 }
 
 }  // namespace mad

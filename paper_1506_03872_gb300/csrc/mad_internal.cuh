@@ -58,11 +58,25 @@ struct SampleParams {
   const uint32_t* TB;
   unsigned long long t1_total;
   double f_scale;                  // 2^F
-  // Hash.
+  // Coarse indices (every 2^lg-th prefix entry) staged in shared memory by
+  // the row-ordered kernels: T1c over T1, TBc over each row of TB (dense).
+  const uint64_t* T1c;
+  int64_t t1c_n;
+  int t1c_lg;
+  const uint32_t* TBc;
+  int64_t tbc_n;                   // entries per row of B
+  int tbc_lg;
+  // Hash.  Regioned (dense inputs): the key (a, b) starts probing in the
+  // home region of row a, [hreg[a], hreg[a+1]), sized from row a's expected
+  // share of the diamonds; otherwise at mix(key) & hmask.  Probing is
+  // linear and wraps at hcap.
   unsigned long long* hkeys;
   long long* hvals;
+  const unsigned long long* hreg;
   uint64_t hmask;
+  uint64_t hcap;
   uint32_t max_probe;
+  int regioned;
   // Modes.
   int dense;                       // 1 dense A and B, 0 CSR
   int a_f64, b_f64;                // dense dtypes
@@ -104,10 +118,16 @@ struct mad_ctx {
   float* nb = nullptr;
   float* r = nullptr;
   unsigned long long* r64 = nullptr;
+  uint64_t* T1c = nullptr;          // coarse index of T1
+  uint32_t* TBc = nullptr;          // coarse index of each TB row (dense)
+  int64_t t1c_n = 0, tbc_n = 0;
+  int t1c_lg = 0, tbc_lg = 0;
   void* bt = nullptr;               // dense B^T (n x d), the input dtype
   unsigned long long* hkeys = nullptr;
   long long* hvals = nullptr;
-  uint64_t hcap = 0, hcap_request = 0;
+  unsigned long long* hreg = nullptr;   // home regions (m + 1 offsets), dense inputs
+  bool regioned = false;
+  uint64_t hcap = 0, hcap_alloc = 0, hcap_request = 0;
   mad::DevScalars* sc = nullptr;
   // Scratch (select, scans); grown on demand.
   void* scratch = nullptr;
@@ -126,8 +146,18 @@ inline void count_launch(mad_ctx* ctx, int n = 1) { ctx->launches += (uint64_t)n
 mad_status cuda_status(cudaError_t e);
 mad_status ensure_scratch(mad_ctx* ctx, size_t bytes, cudaStream_t st);
 
+// scan.cu: out[0..n] = exclusive prefix of in[0..n) and the total at
+// out[n]; partial holds scan_partial_elems(n) elements.
+size_t scan_partial_elems(uint64_t n);
+mad_status scan_exclusive_u32(mad_ctx* ctx, const uint32_t* in, uint32_t* out, uint64_t n,
+                              uint32_t* partial, cudaStream_t st);
+mad_status scan_exclusive_u64(mad_ctx* ctx, const uint64_t* in, uint64_t* out, uint64_t n,
+                              uint64_t* partial, cudaStream_t st);
 // tables.cu
 mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st);
+// Home regions of the dense hash: sizes from T1 and s_max, then offsets.
+mad_status build_hash_regions(mad_ctx* ctx, cudaStream_t st);
+uint64_t hash_region_bound(uint64_t m, uint64_t s_max);
 // sample.cu
 mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first,
                        cudaStream_t st);
@@ -148,17 +178,23 @@ struct SelectWs {
 };
 size_t select_ws_bytes(uint64_t n, uint64_t K);
 SelectWs select_ws_carve(void* base, uint64_t n, uint64_t K);
-// Occupied slots with x > 0 into ws.l0; synchronises.
-mad_status compact_positive(mad_ctx* ctx, const SelectWs& ws, uint64_t* n_pos, cudaStream_t st);
 // K largest of ws.l0[0..n) by (p desc, key asc), sorted into ws.out.  dp =
 // number of significant bytes of the largest p.  Asynchronous.
-mad_status select_run(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K, int dp,
-                      uint64_t* n_sel, cudaStream_t st);
+mad_status select_list(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K, int dp,
+                       uint64_t* n_sel, cudaStream_t st);
+// Omega_t': the K largest positive x of the hash, sorted into ws.out.
+// *n_pos receives the number of positive keys.  Synchronises once.
+mad_status select_from_hash(mad_ctx* ctx, const SelectWs& ws, uint64_t K, uint64_t* n_sel,
+                            uint64_t* n_pos, cudaStream_t st);
 mad_status items_to_pairs(mad_ctx* ctx, const Item* items, uint64_t n, const mad_pair* cand,
                           const double* cvals, mad_pair* out, cudaStream_t st);
 int significant_bytes(unsigned long long maxp);
 mad_status export_x(mad_ctx* ctx, uint64_t* keys, int64_t* vals, uint64_t cap, uint64_t* n,
                     unsigned long long* counter, cudaStream_t st);
+// dense_topt.cu: the comparator; dense_out != NULL writes the full product.
+mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, uint32_t t,
+                            uint32_t rescore, mad_pair* out, uint32_t* n_out, float* dense_out,
+                            cudaStream_t st);
 // rescore.cu
 // Exact c for every candidate: items[q] = (bits |c|, key, q), cvals[q] = c.
 mad_status rescore_items(mad_ctx* ctx, const mad_pair* cand, uint64_t ncand, Item* items,

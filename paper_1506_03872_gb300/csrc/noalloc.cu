@@ -207,7 +207,7 @@ extern "C" mad_status mad_rescore_noalloc(const mad_matrix* A, const mad_matrix*
   // they are given; a host-side context object owns no device memory.
   mad_ctx bookkeeping;
   uint64_t nsel = 0;
-  if ((rs = select_run(&bookkeeping, ws, ncand, t, 8, &nsel, st)) != MAD_OK) return rs;
+  if ((rs = select_list(&bookkeeping, ws, ncand, t, 8, &nsel, st)) != MAD_OK) return rs;
   if ((rs = items_to_pairs(&bookkeeping, ws.out, nsel, cand_dev, cvals, out_dev, st)) != MAD_OK)
     return rs;
   uint32_t err = 0;

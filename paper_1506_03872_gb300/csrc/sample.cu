@@ -4,11 +4,17 @@
 // TB), k' with probability |a_ik'| / ||a_i*||_1 (row i of TA), and add
 // sgn(a_ik b_kj a_ik') b_k'j to x_ij (Alg. 2 increment line).
 //
-// GPU organisation: one diamond per thread, grid-stride over the diamond
-// range with a warp-uniform trip count; the signs of a_ik, b_kj and a_ik'
-// come for free with the table entries the searches land on (bit 31), so
-// only b_k'j is read from B.  Lanes of a warp whose diamonds hit the same
+// GPU organisation: one diamond per thread; the signs of a_ik, b_kj and
+// a_ik' come for free with the table entries the searches land on (bit 31),
+// so only b_k'j is read from B.  Lanes of a warp whose diamonds hit the same
 // key combine their increments before one lane inserts into the hash.
+//
+// Dense inputs are processed in row order: a counting sort by the row i of
+// each diamond's center edge (drawn from T1 alone) groups the diamonds, so
+// the lanes of a warp mostly share row i and its T2/TA/A entries come from
+// L1 once per row instead of once per diamond, and the hash keys (i, j) of
+// the rows in flight fall into a narrow band of home regions that stays in
+// L2.  The draws of every diamond are unchanged by the reordering.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,12 +31,20 @@ struct Draw {
   long long v;
 };
 
-__device__ __forceinline__ Draw draw_one(const SampleParams& p, unsigned long long seed,
-                                         unsigned long long ell, bool* bad) {
-  const Uniforms u = diamond_uniforms(seed, ell);
+// Center edge, stage 1: row i of A from T1 (through its coarse index when
+// it is staged in shared memory).
+__device__ __forceinline__ int64_t draw_row_i(const SampleParams& p, unsigned long long u0,
+                                              bool* bad, const uint64_t* t1c = nullptr) {
+  const unsigned long long target = draw_target(u0, p.t1_total);
+  if (t1c) return search_coarse_u64(t1c, p.t1c_n, p.T1, p.m, p.t1c_lg, target, bad);
+  return search_u64(p.T1, p.m, target, bad);
+}
+
+// The rest of the loop body for a diamond whose row i is known.
+__device__ __forceinline__ Draw draw_given_row(const SampleParams& p, const Uniforms& u,
+                                               int64_t i, bool* bad,
+                                               const uint32_t* tbc = nullptr) {
   const uint32_t mask = p.integer ? 0xFFFFFFFFu : PREFIX_MASK;
-  // Center edge, stage 1: row i of A.
-  const int64_t i = search_u64(p.T1, p.m, draw_target(u.u0, p.t1_total), bad);
   int64_t a0, alen;
   if (p.dense) {
     a0 = i * p.d;
@@ -59,7 +73,9 @@ __device__ __forceinline__ Draw draw_one(const SampleParams& p, unsigned long lo
     pj = (int64_t)draw_target(u.u2, (unsigned long long)blen);
   } else {
     const uint32_t tbtot = __ldg(p.TB + b0 + blen - 1) & mask;
-    pj = search_u32(p.TB + b0, blen, (uint32_t)draw_target(u.u2, tbtot), mask, bad);
+    const uint32_t target = (uint32_t)draw_target(u.u2, tbtot);
+    pj = tbc ? search_coarse_u32(tbc + k * p.tbc_n, p.tbc_n, p.TB + b0, blen, p.tbc_lg, target, mask, bad)
+             : search_u32(p.TB + b0, blen, target, mask, bad);
     e_j = __ldg(p.TB + b0 + pj);
   }
   const int64_t j = p.dense ? pj : (int64_t)__ldg(p.b_col + b0 + pj);
@@ -104,67 +120,153 @@ __device__ __forceinline__ Draw draw_one(const SampleParams& p, unsigned long lo
   return dr;
 }
 
+__device__ __forceinline__ Draw draw_one(const SampleParams& p, unsigned long long seed,
+                                         unsigned long long ell, bool* bad) {
+  const Uniforms u = diamond_uniforms(seed, ell);
+  return draw_given_row(p, u, draw_row_i(p, u.u0, bad), bad);
+}
+
+// Per-lane bookkeeping of the sampling kernels.
+struct Tally {
+  unsigned long long inserted = 0, diag = 0, created = 0;
+  bool bad = false, full = false;
+};
+
+// Filter one drawn diamond and add it to X with the other lanes of the warp
+// (all 32 lanes call this together; `valid` marks lanes holding a diamond).
+__device__ __forceinline__ void accumulate(const SampleParams& p, bool valid, const Draw& dr,
+                                           Tally& t) {
+  const int lane = threadIdx.x & 31;
+  bool want = false;
+  unsigned long long key = 0;
+  long long v = 0;
+  if (valid) {
+    if ((p.flags & MAD_EXCLUDE_DIAG) && dr.i == dr.j) {
+      ++t.diag;
+    } else if (dr.v != 0) {
+      uint32_t a = dr.i, b = dr.j;
+      if ((p.flags & MAD_GRAM) && b < a) {
+        a = dr.j;
+        b = dr.i;
+      }
+      key = ((unsigned long long)a << 32) | b;
+      v = dr.v;
+      want = true;
+      ++t.inserted;
+    }
+  }
+  const unsigned active = __ballot_sync(0xFFFFFFFFu, want);
+  if (want) {
+    const unsigned peers = __match_any_sync(active, key);
+    long long total = 0;
+    unsigned rem = peers;
+    while (rem) {
+      const int src = __ffs(rem) - 1;
+      total += __shfl_sync(peers, v, src);
+      rem &= rem - 1;
+    }
+    if (lane == __ffs(peers) - 1) {
+      const int r = hash_add(p, key, total);
+      if (r == 0) t.full = true;
+      if (r == 2) ++t.created;
+    }
+  }
+}
+
+__device__ __forceinline__ void flush_tally(const SampleParams& p, Tally& t) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    t.inserted += __shfl_xor_sync(0xFFFFFFFFu, t.inserted, off);
+    t.diag += __shfl_xor_sync(0xFFFFFFFFu, t.diag, off);
+    t.created += __shfl_xor_sync(0xFFFFFFFFu, t.created, off);
+  }
+  const unsigned any_bad = __ballot_sync(0xFFFFFFFFu, t.bad);
+  const unsigned any_full = __ballot_sync(0xFFFFFFFFu, t.full);
+  if (lane == 0) {
+    if (t.inserted) atomicAdd(&p.sc->inserted, t.inserted);
+    if (t.diag) atomicAdd(&p.sc->diag_skipped, t.diag);
+    if (t.created) atomicAdd(&p.sc->new_keys, t.created);
+    if (any_bad) atomicOr(&p.sc->err, DERR_SEARCH);
+    if (any_full) atomicOr(&p.sc->err, DERR_HASH_FULL);
+  }
+}
+
+// Diamonds in index order (0/1 CSR inputs).
 __global__ void __launch_bounds__(256)
 k_sample(const SampleParams p, unsigned long long seed, unsigned long long first,
          unsigned long long s) {
   const int lane = threadIdx.x & 31;
   const unsigned long long warp_id = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-  unsigned long long inserted = 0, diag = 0, created = 0;
-  bool bad = false, full = false;
+  Tally t;
   for (unsigned long long base = warp_id * 32; base < s; base += warps * 32) {
     const unsigned long long q = base + lane;
-    bool want = false;
-    unsigned long long key = 0;
-    long long v = 0;
+    Draw dr{};
+    if (q < s) dr = draw_one(p, seed, first + q, &t.bad);
+    accumulate(p, q < s, dr, t);
+  }
+  flush_tally(p, t);
+}
+
+// Counting sort of diamonds by row i, step 1: draw i (Philox block 0 and
+// T1), count it, remember (i, rank within row).
+__global__ void __launch_bounds__(256)
+k_bucket_count(const SampleParams p, unsigned long long seed, unsigned long long first,
+               unsigned long long s, unsigned int* __restrict__ cnt,
+               unsigned long long* __restrict__ rec) {
+  extern __shared__ uint64_t t1c[];
+  for (int64_t g = threadIdx.x; g < p.t1c_n; g += blockDim.x) t1c[g] = p.T1c[g];
+  __syncthreads();
+  bool bad = false;
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < s;
+       q += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long ell = first + q;
+    const uint4 b0 = philox4x32_10(make_uint4((uint32_t)ell, (uint32_t)(ell >> 32), 0u, 0u), key);
+    const unsigned long long u0 = ((unsigned long long)b0.y << 32) | b0.x;
+    const int64_t i = draw_row_i(p, u0, &bad, t1c);
+    const unsigned int r = atomicAdd(cnt + i, 1u);
+    rec[q] = ((unsigned long long)i << 32) | r;
+  }
+  if (bad) atomicOr(&p.sc->err, DERR_SEARCH);
+}
+
+// Step 3: place diamond q at off[i] + rank.
+__global__ void __launch_bounds__(256)
+k_bucket_scatter(const unsigned long long* __restrict__ rec, const unsigned int* __restrict__ off,
+                 unsigned long long s, unsigned long long* __restrict__ sorted) {
+  for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < s;
+       q += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long e = rec[q];
+    const uint32_t i = (uint32_t)(e >> 32);
+    sorted[off[i] + (uint32_t)e] = ((unsigned long long)i << 32) | q;
+  }
+}
+
+// Diamonds in row order (dense inputs): sorted[q] = (i << 32) | (l - first).
+__global__ void __launch_bounds__(256)
+k_sample_sorted(const SampleParams p, unsigned long long seed, unsigned long long first,
+                unsigned long long s, const unsigned long long* __restrict__ sorted) {
+  extern __shared__ uint32_t tbc[];
+  const int64_t ntbc = p.d * p.tbc_n;
+  for (int64_t g = threadIdx.x; g < ntbc; g += blockDim.x) tbc[g] = p.TBc[g];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const unsigned long long warp_id = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  Tally t;
+  for (unsigned long long base = warp_id * 32; base < s; base += warps * 32) {
+    const unsigned long long q = base + lane;
+    Draw dr{};
     if (q < s) {
-      const Draw dr = draw_one(p, seed, first + q, &bad);
-      if ((p.flags & MAD_EXCLUDE_DIAG) && dr.i == dr.j) {
-        ++diag;
-      } else if (dr.v != 0) {
-        uint32_t a = dr.i, b = dr.j;
-        if ((p.flags & MAD_GRAM) && b < a) {
-          a = dr.j;
-          b = dr.i;
-        }
-        key = ((unsigned long long)a << 32) | b;
-        v = dr.v;
-        want = true;
-        ++inserted;
-      }
+      const unsigned long long e = __ldg(sorted + q);
+      const Uniforms u = diamond_uniforms(seed, first + (uint32_t)e);
+      dr = draw_given_row(p, u, (int64_t)(e >> 32), &t.bad, tbc);
     }
-    const unsigned active = __ballot_sync(0xFFFFFFFFu, want);
-    if (want) {
-      const unsigned peers = __match_any_sync(active, key);
-      long long total = 0;
-      unsigned rem = peers;
-      while (rem) {
-        const int src = __ffs(rem) - 1;
-        total += __shfl_sync(peers, v, src);
-        rem &= rem - 1;
-      }
-      if (lane == __ffs(peers) - 1) {
-        const int r = hash_add(p.hkeys, p.hvals, p.hmask, p.max_probe, key, total);
-        if (r == 0) full = true;
-        if (r == 2) ++created;
-      }
-    }
+    accumulate(p, q < s, dr, t);
   }
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    inserted += __shfl_xor_sync(0xFFFFFFFFu, inserted, off);
-    diag += __shfl_xor_sync(0xFFFFFFFFu, diag, off);
-    created += __shfl_xor_sync(0xFFFFFFFFu, created, off);
-  }
-  const unsigned any_bad = __ballot_sync(0xFFFFFFFFu, bad);
-  const unsigned any_full = __ballot_sync(0xFFFFFFFFu, full);
-  if (lane == 0) {
-    if (inserted) atomicAdd(&p.sc->inserted, inserted);
-    if (diag) atomicAdd(&p.sc->diag_skipped, diag);
-    if (created) atomicAdd(&p.sc->new_keys, created);
-    if (any_bad) atomicOr(&p.sc->err, DERR_SEARCH);
-    if (any_full) atomicOr(&p.sc->err, DERR_HASH_FULL);
-  }
+  flush_tally(p, t);
 }
 
 // Diagnostic twin of k_sample: writes each diamond's draws instead of
@@ -187,21 +289,24 @@ k_draws(const SampleParams p, unsigned long long seed, unsigned long long first,
   if (bad) atomicOr(&p.sc->err, DERR_SEARCH);
 }
 
-int sample_grid(unsigned long long s) {
-  static int blocks_per_sm = -1, sms = 0;
-  if (blocks_per_sm < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_sample, 256, 0) !=
-            cudaSuccess ||
-        blocks_per_sm < 1)
-      blocks_per_sm = 1;
-  }
-  const unsigned long long need = (s + 255) / 256;
-  const unsigned long long full = (unsigned long long)sms * blocks_per_sm;
-  return (int)(need < full ? (need ? need : 1) : full);
+template <typename K>
+int full_grid(K kernel, size_t smem = 0) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return sms * per_sm;
 }
+
+unsigned grid_of(unsigned long long work, int full) {
+  const unsigned long long need = (work + 255) / 256;
+  return (unsigned)(need < (unsigned long long)full ? (need ? need : 1) : full);
+}
+
+// Diamonds per sorted batch (bounds the scratch at 16 bytes per diamond).
+constexpr unsigned long long kSortBatch = 1ull << 26;
 
 }  // namespace
 
@@ -223,11 +328,20 @@ SampleParams make_params(const mad_ctx* ctx) {
   p.TA = ctx->TA;
   p.TB = ctx->TB;
   p.t1_total = ctx->t1_total;
+  p.T1c = ctx->T1c;
+  p.t1c_n = ctx->t1c_n;
+  p.t1c_lg = ctx->t1c_lg;
+  p.TBc = ctx->TBc;
+  p.tbc_n = ctx->tbc_n;
+  p.tbc_lg = ctx->tbc_lg;
   p.f_scale = std::ldexp(1.0, ctx->f);
   p.hkeys = ctx->hkeys;
   p.hvals = ctx->hvals;
+  p.hreg = ctx->hreg;
   p.hmask = ctx->hcap - 1;
+  p.hcap = ctx->hcap;
   p.max_probe = (uint32_t)(ctx->hcap < 4096 ? ctx->hcap : 4096);
+  p.regioned = ctx->regioned ? 1 : 0;
   p.dense = ctx->dense ? 1 : 0;
   p.a_f64 = ctx->A.dt == MAD_F64;
   p.b_f64 = ctx->B.dt == MAD_F64;
@@ -240,8 +354,48 @@ SampleParams make_params(const mad_ctx* ctx) {
 mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, cudaStream_t st) {
   if (s == 0) return MAD_OK;
   const SampleParams p = make_params(ctx);
-  k_sample<<<sample_grid(s), 256, 0, st>>>(p, seed, first, s);
-  count_launch(ctx);
+  if (!ctx->dense) {
+    static int full = 0;
+    if (!full) full = full_grid(k_sample);
+    k_sample<<<grid_of(s, full), 256, 0, st>>>(p, seed, first, s);
+    count_launch(ctx);
+    return cuda_status(cudaGetLastError());
+  }
+  const size_t smem_t1c = (size_t)p.t1c_n * sizeof(uint64_t);
+  const size_t smem_tbc = (size_t)(p.d * p.tbc_n) * sizeof(uint32_t);
+  static bool attrs = false;
+  if (!attrs) {
+    cudaFuncSetAttribute(k_bucket_count, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+    cudaFuncSetAttribute(k_sample_sorted, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+    attrs = true;
+  }
+  const int full_count = full_grid(k_bucket_count, smem_t1c);
+  const int full_sorted = full_grid(k_sample_sorted, smem_tbc);
+  const uint64_t m = (uint64_t)ctx->m;
+  const uint64_t batch = s < kSortBatch ? s : kSortBatch;
+  const size_t cnt_bytes = ((m + 1) * sizeof(uint32_t) + 255) & ~(size_t)255;
+  const size_t part_bytes = (scan_partial_elems(m) * sizeof(uint32_t) + 255) & ~(size_t)255;
+  const size_t rec_bytes = batch * sizeof(unsigned long long);
+  mad_status rs = ensure_scratch(ctx, 2 * cnt_bytes + part_bytes + 2 * rec_bytes, st);
+  if (rs != MAD_OK) return rs;
+  char* base = (char*)ctx->scratch;
+  uint32_t* cnt = (uint32_t*)base;
+  uint32_t* off = (uint32_t*)(base + cnt_bytes);
+  uint32_t* part = (uint32_t*)(base + 2 * cnt_bytes);
+  unsigned long long* rec = (unsigned long long*)(base + 2 * cnt_bytes + part_bytes);
+  unsigned long long* sorted = rec + batch;
+  for (uint64_t done = 0; done < s; done += batch) {
+    const uint64_t n = (s - done) < batch ? (s - done) : batch;
+    cudaMemsetAsync(cnt, 0, m * sizeof(uint32_t), st);
+    k_bucket_count<<<grid_of(n, full_count), 256, smem_t1c, st>>>(p, seed, first + done, n, cnt,
+                                                                  rec);
+    count_launch(ctx);
+    if ((rs = scan_exclusive_u32(ctx, cnt, off, m, part, st)) != MAD_OK) return rs;
+    k_bucket_scatter<<<grid_of(n, full_count), 256, 0, st>>>(rec, off, n, sorted);
+    k_sample_sorted<<<grid_of(n, full_sorted), 256, smem_tbc, st>>>(p, seed, first + done, n,
+                                                                    sorted);
+    count_launch(ctx, 2);
+  }
   return cuda_status(cudaGetLastError());
 }
 

@@ -3,13 +3,16 @@
 // tie key (smaller first); since keys are distinct, the composite
 // (p, ~key) orders items totally and the K-th largest composite is unique.
 //
-// 1. Compaction: occupied hash slots with x > 0 become items.
+// 1. Hash path: one pass builds a 1024-bucket logarithmic histogram of the
+//    positive x; the bucket where the count from the top reaches K gives a
+//    threshold that keeps all of the top K and few others; a second pass
+//    compacts the slots at or above it into items.
 // 2. MSB-first radix select on the composite, one byte per pass, starting
-//    at the highest nonzero byte of p.  Each pass histograms the surviving
-//    tie set; the last block to finish picks the byte and, unless every
-//    survivor is in, the next pass keeps only the survivors with that byte.
-//    Passes whose work is already decided exit at once, so the host never
-//    waits between passes.
+//    at the highest nonzero byte of p: inside one 1024-thread block for
+//    short lists; otherwise across the grid, where each pass histograms the
+//    surviving tie set, the last block to finish picks the byte, and the
+//    next pass keeps only the survivors with that byte (passes whose work is
+//    already decided exit at once, so the host never waits between passes).
 // 3. Collection: every item whose composite is at least the threshold.
 // 4. Bitonic sort of the K items (shared-memory stages inside 2048-item
 //    chunks, global stages across chunks).
@@ -25,6 +28,12 @@ namespace mad {
 namespace {
 
 struct SelState {
+  unsigned int lhist[1024];   // log-bucket histogram of x (hash path)
+  unsigned long long theta;   // collect threshold from the histogram
+  unsigned long long maxp;
+  unsigned long long positive;
+  unsigned int ticket3;
+  unsigned int pad3;
   unsigned long long n_cur;   // survivors in the current list
   unsigned long long k_rem;   // survivors still to be taken
   unsigned long long tp, tk;  // threshold composite (tk applies to ~key)
@@ -56,45 +65,6 @@ __device__ __forceinline__ void append(Item* out, unsigned long long* counter, b
   if (want) {
     const unsigned long long pos = base + __popc(mask & ((1u << lane) - 1u));
     if (pos < cap) out[pos] = it;
-  }
-}
-
-__global__ void __launch_bounds__(256)
-k_compact(const unsigned long long* __restrict__ keys, const long long* __restrict__ vals,
-          uint64_t cap, Item* __restrict__ out, uint64_t out_cap, unsigned long long* counter,
-          DevScalars* sc, int positive_only) {
-  unsigned long long distinct = 0, maxp = 0;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  // Warp-uniform trip count so that the append's ballot sees every lane.
-  const uint64_t start = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t rounds = (cap + stride - 1) / stride;
-  for (uint64_t r = 0; r < rounds; ++r) {
-    const uint64_t slot = start + r * stride;
-    bool want = false;
-    Item it;
-    if (slot < cap) {
-      const unsigned long long key = keys[slot];
-      if (key != EMPTY_KEY) {
-        ++distinct;
-        const long long v = vals[slot];
-        want = !positive_only || v > 0;
-        it.p = (unsigned long long)v;
-        it.key = key;
-        it.aux = slot;
-        if (v > 0 && (unsigned long long)v > maxp) maxp = (unsigned long long)v;
-      }
-    }
-    append(out, counter, want, it, out_cap);
-  }
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    distinct += __shfl_xor_sync(0xFFFFFFFFu, distinct, off);
-    const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, maxp, off);
-    maxp = o > maxp ? o : maxp;
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (distinct) atomicAdd(&sc->distinct, distinct);
-    if (maxp) atomicMax(&sc->maxp, maxp);
   }
 }
 
@@ -191,6 +161,152 @@ k_collect(const Item* __restrict__ l0, unsigned long long n, const SelState* st,
       want = it.p > tp || (it.p == tp && (~it.key) >= tk);
     }
     append(out, counter, want, it, cap);
+  }
+}
+
+// ---- hash path: one-pass log-bucket histogram, then a threshold compaction --
+// Bucket of v >= 1: 16 * floor(log2 v) + the 4 bits below the leading bit
+// (1024 buckets, monotone in v).  The collect threshold is the lower bound
+// of the bucket in which the count from the top reaches K, so at least K
+// items (all of the top K) pass and few more do.
+__device__ __forceinline__ uint32_t log_bucket(unsigned long long v) {
+  const int e = 63 - __clzll((long long)v);
+  const uint32_t f = e >= 4 ? (uint32_t)(v >> (e - 4)) & 15u : (uint32_t)(v << (4 - e)) & 15u;
+  return (uint32_t)e * 16u + f;
+}
+
+__host__ __device__ __forceinline__ unsigned long long bucket_floor(uint32_t b) {
+  const int e = (int)(b >> 4);
+  const unsigned long long m = 16ull + (b & 15u);
+  return e >= 4 ? (m << (e - 4)) : (m >> (4 - e));
+}
+
+__global__ void __launch_bounds__(256)
+k_log_hist(const long long* __restrict__ vals, uint64_t cap, unsigned long long K,
+           SelState* st) {
+  __shared__ unsigned int h[1024];
+  for (int b = threadIdx.x; b < 1024; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  unsigned long long mx = 0;
+  for (uint64_t slot = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < cap;
+       slot += (uint64_t)gridDim.x * blockDim.x) {
+    const long long v = vals[slot];
+    if (v > 0) {
+      atomicAdd(&h[log_bucket((unsigned long long)v)], 1u);
+      if ((unsigned long long)v > mx) mx = (unsigned long long)v;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, mx, off);
+    mx = o > mx ? o : mx;
+  }
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(&st->maxp, mx);
+  __syncthreads();
+  for (int b = threadIdx.x; b < 1024; b += blockDim.x)
+    if (h[b]) atomicAdd(&st->lhist[b], h[b]);
+  __threadfence();
+  __shared__ unsigned int is_last;
+  if (threadIdx.x == 0) is_last = (atomicAdd(&st->ticket3, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last || threadIdx.x != 0) return;
+  __threadfence();
+  volatile unsigned int* gh = st->lhist;
+  unsigned long long cum = 0, theta = 1;  // fewer than K positive: take all
+  for (int b = 1023; b >= 0; --b) {
+    cum += gh[b];
+    if (cum >= K) {
+      theta = bucket_floor((uint32_t)b);
+      break;
+    }
+  }
+  unsigned long long total = 0;
+  for (int b = 0; b < 1024; ++b) total += gh[b];
+  st->theta = theta;
+  st->positive = total;
+}
+
+__global__ void __launch_bounds__(256)
+k_compact_ge(const unsigned long long* __restrict__ keys, const long long* __restrict__ vals,
+             uint64_t cap, const SelState* st, Item* __restrict__ out, uint64_t out_cap,
+             unsigned long long* counter) {
+  const unsigned long long theta = st->theta;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t rounds = (cap + stride - 1) / stride;
+  const uint64_t start = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (uint64_t r = 0; r < rounds; ++r) {
+    const uint64_t slot = start + r * stride;
+    bool want = false;
+    Item it;
+    if (slot < cap) {
+      const long long v = vals[slot];
+      if (v > 0 && (unsigned long long)v >= theta) {
+        it.p = (unsigned long long)v;
+        it.key = keys[slot];
+        it.aux = slot;
+        want = true;
+      }
+    }
+    append(out, counter, want, it, out_cap);
+  }
+}
+
+// ---- single-block MSB radix select for short lists -------------------------
+constexpr unsigned kBlockSelectMax = 1u << 15;
+
+__global__ void __launch_bounds__(1024)
+k_select_block(const Item* __restrict__ list, unsigned n, unsigned K, int dp,
+               Item* __restrict__ out) {
+  __shared__ unsigned int h[256];
+  __shared__ unsigned long long s_tp, s_tk, s_mp, s_mk;
+  __shared__ unsigned int s_krem, s_count;
+  __shared__ int s_done;
+  if (threadIdx.x == 0) {
+    s_tp = s_tk = s_mp = s_mk = 0;
+    s_krem = K;
+    s_done = 0;
+    s_count = 0;
+  }
+  __syncthreads();
+  const int last_q = dp + 7;
+  for (int q = 0; q <= last_q; ++q) {
+    if (s_done) break;
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const unsigned long long tp = s_tp, tk = s_tk, mp = s_mp, mk = s_mk;
+    for (unsigned x = threadIdx.x; x < n; x += blockDim.x) {
+      const Item it = list[x];
+      if ((it.p & mp) == tp && ((~it.key) & mk) == tk) atomicAdd(&h[digit_of(it, q, dp)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned above = 0;
+      int b = 255;
+      for (; b > 0; --b) {
+        if (above + h[b] >= s_krem) break;
+        above += h[b];
+      }
+      s_krem -= above;
+      if (q < dp) {
+        const int sh = 8 * (dp - 1 - q);
+        s_tp |= (unsigned long long)b << sh;
+        s_mp |= 0xFFull << sh;
+      } else {
+        const int sh = 8 * (7 - (q - dp));
+        s_tk |= (unsigned long long)b << sh;
+        s_mk |= 0xFFull << sh;
+      }
+      if (h[b] == s_krem || q == last_q) s_done = 1;
+    }
+    __syncthreads();
+  }
+  const unsigned long long tp = s_tp, tk = s_tk;
+  for (unsigned x = threadIdx.x; x < n; x += blockDim.x) {
+    const Item it = list[x];
+    if (it.p > tp || (it.p == tp && (~it.key) >= tk)) {
+      const unsigned pos = atomicAdd(&s_count, 1u);
+      if (pos < K) out[pos] = it;
+    }
   }
 }
 
@@ -309,6 +425,12 @@ void bitonic_sort(mad_ctx* ctx, Item* data, unsigned long long n, cudaStream_t s
 
 }  // namespace
 
+int significant_bytes(unsigned long long maxp) {
+  int b = 1;
+  while (b < 8 && (maxp >> (8 * b)) != 0) ++b;
+  return b;
+}
+
 size_t select_ws_bytes(uint64_t n, uint64_t K) {
   uint64_t n2 = 2;
   while (n2 < (K < n ? K : n)) n2 <<= 1;
@@ -332,36 +454,22 @@ SelectWs select_ws_carve(void* base, uint64_t n, uint64_t K) {
   return ws;
 }
 
-mad_status compact_positive(mad_ctx* ctx, const SelectWs& ws, uint64_t* n_pos, cudaStream_t st) {
-  cudaMemsetAsync(ws.counter, 0, sizeof(unsigned long long), st);
-  cudaMemsetAsync(&ctx->sc->distinct, 0, sizeof(unsigned long long), st);
-  cudaMemsetAsync(&ctx->sc->maxp, 0, sizeof(unsigned long long), st);
-  k_compact<<<grid_for(ctx->hcap, 152 * 8), 256, 0, st>>>(ctx->hkeys, ctx->hvals, ctx->hcap,
-                                                          ws.l0, ws.cap_n, ws.counter, ctx->sc, 1);
-  count_launch(ctx);
-  unsigned long long cnt = 0;
-  cudaMemcpyAsync(&cnt, ws.counter, sizeof(cnt), cudaMemcpyDeviceToHost, st);
-  const cudaError_t e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_status(e);
-  *n_pos = cnt < ws.cap_n ? cnt : ws.cap_n;
-  return cnt > ws.cap_n ? MAD_ERR_STATE : MAD_OK;
-}
-
-mad_status select_run(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K, int dp,
-                      uint64_t* n_sel, cudaStream_t st) {
+mad_status select_list(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K, int dp,
+                       uint64_t* n_sel, cudaStream_t st) {
   const uint64_t take = K < n ? K : n;
   *n_sel = take;
   if (take == 0) return MAD_OK;
   unsigned long long n2 = 0;
   if (take == n) {
     cudaMemcpyAsync(ws.out, ws.l0, n * sizeof(Item), cudaMemcpyDeviceToDevice, st);
+  } else if (n <= kBlockSelectMax) {
+    k_select_block<<<1, 1024, 0, st>>>(ws.l0, (unsigned)n, (unsigned)K, dp, ws.out);
+    count_launch(ctx);
   } else {
-    SelState init;
-    memset(&init, 0, sizeof(init));
-    init.n_cur = n;
-    init.k_rem = K;
     SelState* dst = (SelState*)ws.state;
-    cudaMemcpyAsync(dst, &init, sizeof(init), cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(dst, 0, sizeof(SelState), st);
+    const unsigned long long init[2] = {n, K};
+    cudaMemcpyAsync(&dst->n_cur, init, sizeof(init), cudaMemcpyHostToDevice, st);
     const int digits = dp + 8;
     const unsigned blocks = grid_for(n, 152 * 4);
     for (int q = 0; q < digits; ++q) {
@@ -377,18 +485,34 @@ mad_status select_run(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K, 
   return cuda_status(cudaGetLastError());
 }
 
+mad_status select_from_hash(mad_ctx* ctx, const SelectWs& ws, uint64_t K, uint64_t* n_sel,
+                            uint64_t* n_pos, cudaStream_t st) {
+  SelState* dst = (SelState*)ws.state;
+  cudaMemsetAsync(dst, 0, sizeof(SelState), st);
+  cudaMemsetAsync(ws.counter, 0, sizeof(unsigned long long), st);
+  const unsigned blocks = grid_for(ctx->hcap, 152 * 8);
+  k_log_hist<<<blocks, 256, 0, st>>>(ctx->hvals, ctx->hcap, K, dst);
+  k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, ctx->hcap, dst, ws.l0, ws.cap_n,
+                                       ws.counter);
+  count_launch(ctx, 2);
+  unsigned long long host[2] = {0, 0};
+  cudaMemcpyAsync(&host[0], ws.counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&host[1], &dst->maxp, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+  unsigned long long positive = 0;
+  cudaMemcpyAsync(&positive, &dst->positive, sizeof(positive), cudaMemcpyDeviceToHost, st);
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (host[0] > ws.cap_n) return MAD_ERR_STATE;
+  *n_pos = positive;
+  return select_list(ctx, ws, host[0], K, significant_bytes(host[1]), n_sel, st);
+}
+
 mad_status items_to_pairs(mad_ctx* ctx, const Item* items, uint64_t n, const mad_pair* cand,
                           const double* cvals, mad_pair* out, cudaStream_t st) {
   if (n == 0) return MAD_OK;
   k_to_pairs<<<grid_for(n, 1u << 30), 256, 0, st>>>(items, n, cand, cvals, out);
   count_launch(ctx);
   return cuda_status(cudaGetLastError());
-}
-
-int significant_bytes(unsigned long long maxp) {
-  int b = 1;
-  while (b < 8 && (maxp >> (8 * b)) != 0) ++b;
-  return b;
 }
 
 // Every occupied key with its value (diagnostics).

@@ -389,6 +389,43 @@ __global__ void k_transpose(const T* __restrict__ B, int64_t d, int64_t n, int64
   }
 }
 
+// Coarse indices for the sampling searches: every 2^lg-th prefix entry
+// (the last entry of each block).
+__global__ void k_coarse_u64(const uint64_t* __restrict__ T, int64_t len, int lg, int64_t nc,
+                             uint64_t* __restrict__ out) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nc;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t end = ((g + 1) << lg) < len ? ((g + 1) << lg) : len;
+    out[g] = T[end - 1];
+  }
+}
+
+__global__ void k_coarse_rows_u32(const uint32_t* __restrict__ T, int64_t rows, int64_t len, int lg,
+                                  int64_t nc, uint32_t* __restrict__ out) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < rows * nc;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = x / nc, g = x % nc;
+    const int64_t end = ((g + 1) << lg) < len ? ((g + 1) << lg) : len;
+    out[x] = T[r * len + end - 1] & PREFIX_MASK;
+  }
+}
+
+// Home-region size of row i: the smallest power of two >= 1.5 x the row's
+// expected number of diamonds among s_max (at least 1).
+__global__ void __launch_bounds__(256)
+k_region_sizes(const uint64_t* __restrict__ T1, int64_t m, unsigned long long s_max,
+               const DevScalars* sc, unsigned long long* __restrict__ sizes) {
+  const double scale = (double)s_max / (double)(sc->t1_total ? sc->t1_total : 1ull);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long q = T1[i] - (i ? T1[i - 1] : 0ull);
+    const double want = 1.5 * (double)q * scale;
+    unsigned long long size = 1;
+    while ((double)size < want && size < (1ull << 40)) size <<= 1;
+    sizes[i] = size;
+  }
+}
+
 int ceil_log2_host(uint64_t x) {
   int e = 0;
   while (e < 64 && (1ull << e) < x) ++e;
@@ -422,6 +459,21 @@ void launch_transpose(mad_ctx* ctx, cudaStream_t st) {
 
 }  // namespace
 
+uint64_t hash_region_bound(uint64_t m, uint64_t s_max) { return m + 3 * s_max + 1; }
+
+mad_status build_hash_regions(mad_ctx* ctx, cudaStream_t st) {
+  const uint64_t m = (uint64_t)ctx->m;
+  const size_t sizes_bytes = (m * sizeof(unsigned long long) + 255) & ~(size_t)255;
+  mad_status rs = ensure_scratch(ctx, sizes_bytes + scan_partial_elems(m) * 8, st);
+  if (rs != MAD_OK) return rs;
+  unsigned long long* sizes = (unsigned long long*)ctx->scratch;
+  uint64_t* part = (uint64_t*)((char*)ctx->scratch + sizes_bytes);
+  const unsigned blocks = (unsigned)((m + 255) / 256 < 152 * 8 ? (m + 255) / 256 : 152 * 8);
+  k_region_sizes<<<blocks, 256, 0, st>>>(ctx->T1, ctx->m, ctx->s_max, ctx->sc, sizes);
+  count_launch(ctx);
+  return scan_exclusive_u64(ctx, (const uint64_t*)sizes, (uint64_t*)ctx->hreg, m, part, st);
+}
+
 mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st) {
   const int64_t chunks = (ctx->m + T1_CHUNK - 1) / T1_CHUNK;
   mad_status rs = ensure_scratch(ctx, (size_t)chunks * sizeof(unsigned long long), st);
@@ -446,6 +498,18 @@ mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st) {
   k_t1_chunk_offsets<<<1, 32, 0, st>>>(partial, chunks, ctx->sc);
   k_t1_write<<<(unsigned)chunks, 256, 0, st>>>(r, r64, ctx->m, clog2m, partial, ctx->T1, ctx->sc);
   count_launch(ctx, 3);
+  if (ctx->T1c) {
+    k_coarse_u64<<<(unsigned)((ctx->t1c_n + 255) / 256), 256, 0, st>>>(ctx->T1, ctx->m, ctx->t1c_lg,
+                                                                       ctx->t1c_n, ctx->T1c);
+    count_launch(ctx);
+  }
+  if (ctx->TBc) {
+    const int64_t total = ctx->d * ctx->tbc_n;
+    k_coarse_rows_u32<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(ctx->TB, ctx->d, ctx->n,
+                                                                       ctx->tbc_lg, ctx->tbc_n,
+                                                                       ctx->TBc);
+    count_launch(ctx);
+  }
   return cuda_status(cudaGetLastError());
 }
 
