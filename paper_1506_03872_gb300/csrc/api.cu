@@ -65,6 +65,8 @@ void free_tables(mad_ctx* ctx, cudaStream_t st) {
   free_async(ctx->hreg, st);
   free_async(ctx->T1c, st);
   free_async(ctx->TBc, st);
+  free_async(ctx->T1c2, st);
+  free_async(ctx->TBc2, st);
   ctx->built = false;
   ctx->regioned = false;
 }
@@ -221,17 +223,21 @@ mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   if ((rs = alloc(ctx->T1, (size_t)ctx->m, st)) != MAD_OK) return rs;
   // Coarse search indices staged in shared memory by the sampling kernels:
   // T1 in at most 16 KB, all rows of TB (dense) in at most 40 KB.
-  ctx->t1c_lg = 4;
+  // Level-1 blocks hold at least 64 entries (whole 16-byte vectors at level 2).
+  ctx->t1c_lg = 6;
   while ((((uint64_t)ctx->m + (1ull << ctx->t1c_lg) - 1) >> ctx->t1c_lg) * 8 > 16384) ++ctx->t1c_lg;
   ctx->t1c_n = (int64_t)(((uint64_t)ctx->m + (1ull << ctx->t1c_lg) - 1) >> ctx->t1c_lg);
   if ((rs = alloc(ctx->T1c, (size_t)ctx->t1c_n, st)) != MAD_OK) return rs;
+  if ((rs = alloc(ctx->T1c2, (size_t)(ctx->t1c_n << (ctx->t1c_lg - 4)), st)) != MAD_OK) return rs;
   if (dense) {
-    ctx->tbc_lg = 4;
+    ctx->tbc_lg = 6;
     while ((uint64_t)ctx->d * ((((uint64_t)ctx->n + (1ull << ctx->tbc_lg) - 1) >> ctx->tbc_lg)) * 4 >
            40960)
       ++ctx->tbc_lg;
     ctx->tbc_n = (int64_t)(((uint64_t)ctx->n + (1ull << ctx->tbc_lg) - 1) >> ctx->tbc_lg);
     if ((rs = alloc(ctx->TBc, (size_t)(ctx->d * ctx->tbc_n), st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx->TBc2, (size_t)(ctx->d * (ctx->tbc_n << (ctx->tbc_lg - 4))), st)) != MAD_OK)
+      return rs;
   } else {
     ctx->tbc_n = 0;
   }

@@ -7,17 +7,21 @@
 //     tcgen05.mma (BF16 in, FP32 accumulate in TMEM), operands brought into
 //     shared memory by TMA (128-byte swizzle), and never writes C~: its
 //     epilogue keeps only entries with |c~| >= theta in a per-CTA buffer.
-//     theta starts at 0 and rises whenever the buffer is compacted to its
-//     K_keep largest entries (the rescore budget, 8t by default) (a tile that overflows the buffer is
+//     theta starts from a pre-pass (the same kernel over every 16th tile,
+//     recording half-row maxima, whose K_keep-th largest bounds the global
+//     K_keep-th largest from below) and rises whenever the buffer is
+//     compacted to its K_keep largest entries (the rescore budget, 8t by
+//     default) (a tile that overflows the buffer is
 //     rescanned from TMEM above the new theta); CTAs share theta
 //     through an atomicMax, so every kept threshold is a lower bound of the
 //     global K_keep-th largest |c~| and no entry of the global top K_keep is
 //     ever dropped.
 //  3. The K_keep largest |c~| of the merged buffers are rescored exactly in FP32
 //     and the t largest |c| returned.
-// Warp roles per CTA (192 threads): warp 0 issues TMA, warp 1 allocates TMEM
-// and issues the MMAs, warps 2-5 drain the accumulators (one TMEM lane
-// quarter each).  Two TMEM accumulators (2 x 256 columns) and two B stages
+// Warp roles per CTA (320 threads): warp 0 issues TMA, warp 1 allocates TMEM
+// and issues the MMAs, warps 2-9 drain the accumulators (warp w reads TMEM
+// lane quarter w mod 4 and one half of the columns, four 32-column loads in
+// flight before one wait).  Two TMEM accumulators (2 x 256 columns) and two B stages
 // overlap loads, MMAs and the epilogue.  Every wait is bounded by a clock
 // limit after which the CTA sets an error flag and winds down.
 #include <cuda.h>
@@ -43,7 +47,9 @@ constexpr int MAXKP = 128;          // padded K handled by this kernel
 constexpr int NSTAGE = 2;           // B pipeline depth
 constexpr int CAND_CAP = 4096;      // per-CTA candidate buffer
 constexpr int CAND_TRIGGER = 2048;  // compact before a tile when above this
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;       // 2 producer/MMA warps + 8 epilogue warps
+constexpr int kEpi = 256;           // epilogue threads
+constexpr long long kPreStride = 16; // threshold pre-pass visits every 16th tile
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s: a wait this long is a fault
 
 constexpr int A_BYTES = BM * MAXKP * 2;                 // 32 KB
@@ -67,6 +73,8 @@ struct GemmArgs {
   unsigned long long* cand_count;
   unsigned long long cand_cap;
   float* dense_out;                  // diagnostics: full C~ (m x n) when set
+  int64_t tile_stride;               // process every tile_stride-th tile
+  float* max_out;                    // threshold pre-pass: half-row maxima
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -151,8 +159,7 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -163,9 +170,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
         "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
 __device__ __forceinline__ void fence_before_sync() {
@@ -174,8 +182,8 @@ __device__ __forceinline__ void fence_before_sync() {
 __device__ __forceinline__ void fence_after_sync() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-// Barrier among the 128 epilogue threads only.
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Barrier among the epilogue threads only.
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 struct Shared {
   uint64_t a_full, a_empty, done;
@@ -192,7 +200,7 @@ struct Shared {
 };
 
 // The kkeep-th largest value among vals[0..n) (all >= 0) by MSB radix
-// select on the FP32 bits; run by the 128 epilogue threads.
+// select on the FP32 bits; run by the epilogue threads.
 __device__ float epi_kth_largest(const float* vals, unsigned n, unsigned kkeep, Shared* sh, int et) {
   if (et == 0) {
     sh->sel_prefix = 0;
@@ -200,13 +208,19 @@ __device__ float epi_kth_largest(const float* vals, unsigned n, unsigned kkeep, 
     sh->sel_krem = kkeep;
   }
   for (int pass = 0; pass < 4; ++pass) {
-    for (int b = et; b < 256; b += 128) sh->hist[b] = 0;
+    for (int b = et; b < 256; b += kEpi) sh->hist[b] = 0;
     epi_sync();
     const unsigned prefix = sh->sel_prefix, mask = sh->sel_mask;
     const int shift = 24 - 8 * pass;
-    for (unsigned x = et; x < n; x += 128) {
-      const unsigned bits = __float_as_uint(vals[x]);
-      if ((bits & mask) == prefix) atomicAdd(&sh->hist[(bits >> shift) & 0xFFu], 1u);
+    const unsigned rounds = (n + kEpi - 1) / kEpi;
+    for (unsigned r = 0; r < rounds; ++r) {
+      const unsigned x = r * kEpi + et;
+      const unsigned bits = x < n ? __float_as_uint(vals[x]) : 0u;
+      const bool in = x < n && (bits & mask) == prefix;
+      const unsigned bin = in ? (bits >> shift) & 0xFFu : 0x100u;
+      // one shared-memory atomic per distinct bin per warp
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, bin);
+      if (in && (et & 31) == __ffs(peers) - 1) atomicAdd(&sh->hist[bin], __popc(peers));
     }
     epi_sync();
     if (et == 0) {
@@ -225,37 +239,44 @@ __device__ float epi_kth_largest(const float* vals, unsigned n, unsigned kkeep, 
   return __uint_as_float(sh->sel_prefix);
 }
 
-// Keep buffer entries [0, n) with value >= theta, in place and in order
-// (each thread compacts a contiguous block; blocks are placed by a scan).
+// Keep buffer entries [0, n) with value >= theta, in place and in order.
+// Rounds of kEpi entries: every read of a round happens before any write of
+// it, and a round writes only below its own end, so no entry is overwritten
+// before it has been read.
 __device__ unsigned epi_compact(float* cv, unsigned long long* ck, unsigned n, float theta,
                                 Shared* sh, int et) {
-  __shared__ unsigned int part[128];
-  const unsigned per = (n + 127) / 128;
-  const unsigned lo = et * per, hi = min(n, lo + per);
-  unsigned keep = 0;
-  for (unsigned x = lo; x < hi; ++x) keep += cv[x] >= theta ? 1u : 0u;
-  part[et] = keep;
-  epi_sync();
-  if (et == 0) {
-    unsigned acc = 0;
-    for (int q = 0; q < 128; ++q) {
-      const unsigned v = part[q];
-      part[q] = acc;
-      acc += v;
+  __shared__ unsigned int warp_keep[kEpi / 32];
+  const int w = et >> 5, lane = et & 31;
+  unsigned out = 0;
+  for (unsigned base = 0; base < n; base += kEpi) {
+    const unsigned x = base + et;
+    float v = 0.0f;
+    unsigned long long k = 0;
+    bool keep = false;
+    if (x < n) {
+      v = cv[x];
+      k = ck[x];
+      keep = v >= theta;
     }
-    sh->count = acc;
-  }
-  epi_sync();
-  unsigned dst = part[et];
-  for (unsigned x = lo; x < hi; ++x) {
-    if (cv[x] >= theta) {
-      cv[dst] = cv[x];
-      ck[dst] = ck[x];
-      ++dst;
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, keep);
+    if (lane == 0) warp_keep[w] = __popc(mask);
+    epi_sync();
+    unsigned off = out, total = 0;
+    for (int q = 0; q < kEpi / 32; ++q) {
+      if (q < w) off += warp_keep[q];
+      total += warp_keep[q];
     }
+    if (keep) {
+      const unsigned dst = off + __popc(mask & ((1u << lane) - 1u));
+      cv[dst] = v;
+      ck[dst] = k;
+    }
+    out += total;
+    epi_sync();
   }
+  if (et == 0) sh->count = out;
   epi_sync();
-  return sh->count;
+  return out;
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -273,7 +294,9 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort_flag = &sh->abort_flag;
 
-  const long long total_tiles = args.tiles_m * args.tiles_n;
+  // Virtual tile v is real tile v * tile_stride (row-major over row blocks).
+  const long long stride = args.tile_stride;
+  const long long total_tiles = (args.tiles_m * args.tiles_n + stride - 1) / stride;
   const long long t_begin = total_tiles * blockIdx.x / gridDim.x;
   const long long t_end = total_tiles * (blockIdx.x + 1) / gridDim.x;
   const int katoms = args.kp / KATOM;
@@ -289,7 +312,7 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh->acc_full[b], 1);
-      mbar_init(&sh->acc_empty[b], 4);
+      mbar_init(&sh->acc_empty[b], kEpi / 32);
     }
     sh->abort_flag = 0;
     sh->epi_abort = 0;
@@ -314,8 +337,8 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       long long prev_rb = -1, panel = 0;
-      for (long long t = t_begin; t < t_end && !*abort_flag; ++t) {
-        const long long it = t - t_begin;
+      for (long long v = t_begin; v < t_end && !*abort_flag; ++v) {
+        const long long it = v - t_begin, t = v * stride;
         const long long rb = t / args.tiles_n, cb = t % args.tiles_n;
         if (rb != prev_rb) {
           if (panel > 0 && !mbar_wait(&sh->a_empty, (uint32_t)((panel - 1) & 1), abort_flag)) break;
@@ -338,8 +361,8 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       long long prev_rb = -1, panel = 0;
-      for (long long t = t_begin; t < t_end && !*abort_flag; ++t) {
-        const long long it = t - t_begin;
+      for (long long v = t_begin; v < t_end && !*abort_flag; ++v) {
+        const long long it = v - t_begin, t = v * stride;
         const long long rb = t / args.tiles_n;
         if (rb != prev_rb) {
           if (!mbar_wait(&sh->a_full, (uint32_t)(panel & 1), abort_flag)) break;
@@ -362,21 +385,22 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
         mma_commit(&sh->b_empty[s]);
         mma_commit(&sh->acc_full[buf]);
-        const bool panel_ends = (t + 1 == t_end) || ((t + 1) / args.tiles_n != rb);
+        const bool panel_ends = (v + 1 == t_end) || (((v + 1) * stride) / args.tiles_n != rb);
         if (panel_ends) mma_commit(&sh->a_empty);
       }
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
-    const int et = threadIdx.x - 64;          // 0..127
+    // ---------------- epilogue (warps 2..9) ----------------
+    const int et = threadIdx.x - 64;          // 0..kEpi-1
     const int quarter = warp & 3;             // TMEM lane quarter of this warp
+    const int half = (warp - 2) >> 2;         // column half of the tile
     const int row_in_tile = quarter * 32 + lane;
-    for (long long t = t_begin; t < t_end; ++t) {
-      const long long it = t - t_begin;
+    for (long long v = t_begin; v < t_end; ++v) {
+      const long long it = v - t_begin, t = v * stride;
       const long long rb = t / args.tiles_n, cb = t % args.tiles_n;
       const int buf = (int)(it & 1);
       // Compact first when the buffer is past its trigger.
-      if (!args.dense_out && sh->count > CAND_TRIGGER) {
+      if (!args.dense_out && !args.max_out && sh->count > CAND_TRIGGER) {
         const float th = epi_kth_largest(cv, sh->count, (unsigned)args.kkeep, sh, et);
         epi_compact(cv, ck, sh->count, th, sh, et);
         if (et == 0) {
@@ -385,62 +409,107 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
         epi_sync();
       }
-      // The four warps share named barriers below, so they leave together.
+      // The epilogue warps share named barriers below, so they leave together.
       const bool ok = mbar_wait(&sh->acc_full[buf], (uint32_t)((it >> 1) & 1), abort_flag);
       if (!ok) atomicOr(&sh->epi_abort, 1);
       epi_sync();
       if (*((volatile int*)&sh->epi_abort)) break;
       fence_after_sync();
       const int64_t row = rb * BM + row_in_tile;
-      const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN);
-      unsigned tile_start = sh->count;
-      for (int round = 0; round < 8; ++round) {
-        const float theta =
-            fmaxf(sh->theta, __uint_as_float(*((volatile unsigned int*)args.g_theta)));
-        for (int c = 0; c < BN / 32; ++c) {
-          float v[32];
-          tmem_ld32(taddr + (uint32_t)(c * 32), v);
-          const int64_t col0 = cb * BN + c * 32;
-          if (args.dense_out) {
-            if (row < args.m)
-              for (int q = 0; q < 32; ++q)
-                if (col0 + q < args.n) args.dense_out[row * args.n + col0 + q] = v[q];
-            continue;
+      const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                             (uint32_t)(buf * BN + half * (BN / 2));
+      const int64_t col_half = cb * BN + half * (BN / 2);
+      if (args.dense_out) {
+#pragma unroll 1
+        for (int ch = 0; ch < 2; ++ch) {
+          uint32_t r[64];
+          tmem_ld32_nowait(taddr + (uint32_t)(ch * 64), r);
+          tmem_ld32_nowait(taddr + (uint32_t)(ch * 64 + 32), r + 32);
+          tmem_wait_ld();
+          const int64_t col0 = col_half + ch * 64;
+          if (row < args.m) {
+#pragma unroll
+            for (int q = 0; q < 64; ++q)
+              if (col0 + q < args.n) args.dense_out[row * args.n + col0 + q] = __uint_as_float(r[q]);
           }
-          float mx = 0.0f;
+        }
+      } else if (args.max_out) {
+        // Threshold pre-pass: the largest |c~| of this thread's half row.
+        float hm = 0.0f;
+#pragma unroll 1
+        for (int ch = 0; ch < 2; ++ch) {
+          uint32_t r[64];
+          tmem_ld32_nowait(taddr + (uint32_t)(ch * 64), r);
+          tmem_ld32_nowait(taddr + (uint32_t)(ch * 64 + 32), r + 32);
+          tmem_wait_ld();
+          const int64_t rem = args.n - (col_half + ch * 64);
+          const int nvalid = rem >= 64 ? 64 : (rem > 0 ? (int)rem : 0);
 #pragma unroll
-          for (int q = 0; q < 32; ++q) mx = fmaxf(mx, fabsf(v[q]));
-          if (mx >= theta && row < args.m) {
+          for (int q = 0; q < 64; ++q)
+            hm = fmaxf(hm, q < nvalid ? fabsf(__uint_as_float(r[q])) : 0.0f);
+        }
+        args.max_out[v * kEpi + et] = row < args.m ? hm : 0.0f;
+      } else {
+        unsigned tile_start = sh->count;
+        for (int round = 0; round < 8; ++round) {
+          const float theta =
+              fmaxf(sh->theta, __uint_as_float(*((volatile unsigned int*)args.g_theta)));
+          // Two chunks of 64 columns, reloaded from TMEM on every pass (the
+          // accumulator stays put until this tile's buffer is released).
+#pragma unroll 1
+          for (int ch = 0; ch < 2; ++ch) {
+            uint32_t r[64];
+            tmem_ld32_nowait(taddr + (uint32_t)(ch * 64), r);
+            tmem_ld32_nowait(taddr + (uint32_t)(ch * 64 + 32), r + 32);
+            tmem_wait_ld();
+            const int64_t col0 = col_half + ch * 64;
+            const int64_t rem = args.n - col0;
+            const int nvalid = rem >= 64 ? 64 : (rem > 0 ? (int)rem : 0);
+            // Max first: the chunk is inspected element by element only when
+            // its largest valid |c~| reaches theta.
+            float mx = 0.0f;
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-              const float a = fabsf(v[q]);
-              if (a >= theta && col0 + q < args.n) {
-                const unsigned pos = atomicAdd(&sh->count, 1u);
-                if (pos < CAND_CAP) {
-                  cv[pos] = a;
-                  ck[pos] = ((unsigned long long)row << 32) | (unsigned long long)(col0 + q);
-                } else {
-                  sh->overflow = 1;
+            for (int q = 0; q < 64; ++q)
+              mx = fmaxf(mx, q < nvalid ? fabsf(__uint_as_float(r[q])) : 0.0f);
+            unsigned cnt = 0;
+            if (mx >= theta && row < args.m) {
+#pragma unroll
+              for (int q = 0; q < 64; ++q)
+                cnt += (q < nvalid && fabsf(__uint_as_float(r[q])) >= theta) ? 1u : 0u;
+            }
+            if (cnt) {
+              // Reserve this thread's slots with one atomic, then write them.
+              unsigned pos = atomicAdd(&sh->count, cnt);
+              if (pos + cnt > CAND_CAP) sh->overflow = 1;
+#pragma unroll
+              for (int q = 0; q < 64; ++q) {
+                const float a = fabsf(__uint_as_float(r[q]));
+                if (q < nvalid && a >= theta) {
+                  if (pos < CAND_CAP) {
+                    cv[pos] = a;
+                    ck[pos] = ((unsigned long long)row << 32) | (unsigned long long)(col0 + q);
+                  }
+                  ++pos;
                 }
               }
             }
           }
+          epi_sync();
+          if (!sh->overflow) break;
+          // Overflow: the buffer holds CAND_CAP real entries, so its kkeep-th
+          // largest is a valid lower bound.  Drop this tile's entries, tighten
+          // the earlier ones and rescan the tile above it.
+          const float th = epi_kth_largest(cv, CAND_CAP, (unsigned)args.kkeep, sh, et);
+          epi_compact(cv, ck, tile_start, th, sh, et);
+          if (et == 0) {
+            sh->theta = fmaxf(sh->theta, th);
+            sh->overflow = 0;
+            atomicMax(args.g_theta, __float_as_uint(sh->theta));
+          }
+          epi_sync();
+          tile_start = sh->count;  // the earlier tiles' survivors; the rescan appends after them
+          if (round == 7 && et == 0) atomicOr(args.g_err, 2u);  // pathological ties
         }
-        epi_sync();
-        if (!sh->overflow) break;
-        // Overflow: the buffer holds CAND_CAP real entries, so its kkeep-th
-        // largest is a valid lower bound.  Drop this tile's entries, tighten
-        // the earlier ones and rescan the tile (still in TMEM) above it.
-        const float th = epi_kth_largest(cv, CAND_CAP, (unsigned)args.kkeep, sh, et);
-        epi_compact(cv, ck, tile_start, th, sh, et);
-        if (et == 0) {
-          sh->theta = fmaxf(sh->theta, th);
-          sh->overflow = 0;
-          atomicMax(args.g_theta, __float_as_uint(sh->theta));
-        }
-        epi_sync();
-        tile_start = sh->count;  // the earlier tiles' survivors; the rescan appends after them
-        if (round == 7 && et == 0) atomicOr(args.g_err, 2u);  // pathological ties
       }
       fence_before_sync();
       __syncwarp();
@@ -448,11 +517,11 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
     // Publish this CTA's survivors.
     epi_sync();
-    if (!args.dense_out) {
+    if (!args.dense_out && !args.max_out) {
       const float theta =
           fmaxf(sh->theta, __uint_as_float(*((volatile unsigned int*)args.g_theta)));
       const unsigned n = min(sh->count, (unsigned)CAND_CAP);
-      for (unsigned x = et; x < n; x += 128) {
+      for (unsigned x = et; x < n; x += kEpi) {
         if (cv[x] >= theta) {
           const unsigned long long pos = atomicAdd(args.cand_count, 1ull);
           if (pos < args.cand_cap) {
@@ -509,6 +578,45 @@ __global__ void k_cast_cols_bf16(const T* __restrict__ B, int64_t d, int64_t n, 
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int64_t j = j0 + r, k = k0 + threadIdx.x;
     if (j < n && k < kp) dst[j * kp + k] = __float2bfloat16_rn(tile[threadIdx.x][r]);
+  }
+}
+
+// Threshold from the pre-pass maxima: every maximum is a distinct entry of
+// C~, so the kkeep-th largest maximum is at most the kkeep-th largest entry.
+// A 4096-bucket histogram of the FP32 bits (exponent and 4 mantissa bits)
+// gives the floor of the bucket where the count from the top reaches kkeep,
+// a lower bound of that maximum, in one pass; the last block publishes it.
+__global__ void __launch_bounds__(256)
+k_max_floor(const float* __restrict__ v, unsigned long long n, unsigned kkeep,
+            unsigned int* __restrict__ hist, unsigned int* ticket, unsigned int* g_theta) {
+  __shared__ unsigned int h[4096];
+  for (int b = threadIdx.x; b < 4096; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long rounds = (n + stride - 1) / stride;
+  for (unsigned long long r = 0; r < rounds; ++r) {
+    const unsigned long long x = r * stride + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned bin = x < n ? (__float_as_uint(fmaxf(v[x], 0.0f)) >> 19) : 0x1000u;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, bin);
+    if (bin < 4096u && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[bin], __popc(peers));
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < 4096; b += blockDim.x)
+    if (h[b]) atomicAdd(&hist[b], h[b]);
+  __threadfence();
+  __shared__ unsigned int is_last;
+  if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last || threadIdx.x != 0) return;
+  __threadfence();
+  volatile unsigned int* gh = hist;
+  unsigned long long cum = 0;
+  for (int b = 4095; b >= 0; --b) {
+    cum += gh[b];
+    if (cum >= kkeep) {
+      atomicMax(g_theta, (unsigned)b << 19);
+      return;
+    }
   }
 }
 
@@ -629,8 +737,11 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   const size_t ws_bytes = al(select_ws_bytes(cand_cap, kkeep));
   const size_t ws2_bytes = al(select_ws_bytes(kkeep, t ? t : 1));
   const size_t cvals_bytes = al((size_t)kkeep * 4);
+  const long long pre_tiles = (tiles_m * tiles_n + kPreStride - 1) / kPreStride;
+  const size_t pre_bytes = al((size_t)pre_tiles * kEpi * 4);
+  const size_t hist_bytes = al(4097 * 4);
   const size_t total = a_bytes + b_bytes + cv_bytes + ck_bytes + ws_bytes + ws2_bytes +
-                       cvals_bytes + 1024;
+                       cvals_bytes + pre_bytes + hist_bytes + 1024;
   mad_status rs = ensure_scratch(ctx, total, st);
   if (rs != MAD_OK) return rs;
   char* p = (char*)ctx->scratch;
@@ -641,10 +752,13 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   char* wsb = p;                                      p += ws_bytes;
   char* ws2b = p;                                     p += ws2_bytes;
   float* cvals = (float*)p;                           p += cvals_bytes;
+  float* pre_max = (float*)p;                         p += pre_bytes;
+  unsigned int* pre_hist = (unsigned int*)p;          p += hist_bytes;
   unsigned int* g_theta = (unsigned int*)p;
   unsigned int* g_err = g_theta + 1;
   unsigned long long* cand_count = (unsigned long long*)(g_theta + 2);
   cudaMemsetAsync(g_theta, 0, 64, st);
+  cudaMemsetAsync(pre_hist, 0, 4097 * 4, st);
 
   if (A->dt == MAD_F64) launch_casts<double>(A, B, kp, Abf, Bbf, st);
   else launch_casts<float>(A, B, kp, Abf, Bbf, st);
@@ -674,6 +788,19 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   ga.cand_count = cand_count;
   ga.cand_cap = cand_cap;
   ga.dense_out = dense_out;
+  ga.tile_stride = 1;
+  ga.max_out = nullptr;
+  if (!dense_out) {
+    // Threshold pre-pass over every kPreStride-th tile: half-row maxima.
+    GemmArgs pre = ga;
+    pre.tile_stride = kPreStride;
+    pre.max_out = pre_max;
+    const long long vt = (tiles_m * tiles_n + kPreStride - 1) / kPreStride;
+    k_gemm_topk<<<(int)std::min<long long>(grid, vt), kThreads, SMEM_ALLOC, st>>>(tmA, tmB, pre);
+    k_max_floor<<<152 * 2, 256, 0, st>>>(pre_max, (unsigned long long)vt * kEpi, kkeep, pre_hist,
+                                         pre_hist + 4096, g_theta);
+    count_launch(ctx, 2);
+  }
   k_gemm_topk<<<grid, kThreads, SMEM_ALLOC, st>>>(tmA, tmB, ga);
   count_launch(ctx);
   if ((rs = cuda_status(cudaGetLastError())) != MAD_OK) return rs;

@@ -74,19 +74,111 @@ __device__ __forceinline__ int64_t search_u64(const uint64_t* __restrict__ prefi
 
 __device__ __forceinline__ int64_t search_u32(const uint32_t* __restrict__ prefix, int64_t len,
                                               uint32_t target, uint32_t mask, bool* bad) {
-  int64_t lo = 0, hi = len;
+  // Row lengths are below 2^31: 32-bit indices.
+  int lo = 0, hi = (int)len;
   while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
+    const int mid = (int)(((unsigned)lo + (unsigned)hi) >> 1);
     if ((__ldg(prefix + mid) & mask) > target)
       hi = mid;
     else
       lo = mid + 1;
   }
-  if (lo >= len) {
+  if (lo >= (int)len) {
     *bad = true;
-    lo = len - 1;
+    lo = (int)len - 1;
   }
   return lo;
+}
+
+// Branch-free upper bound with a fixed number of steps (floor(log2 len) +
+// 1, the same for every lane of a row length): the number of entries <=
+// target, i.e. the position of the first entry above it.
+__device__ __forceinline__ int ub_steps(int len) { return 32 - __clz(len); }
+
+__device__ __forceinline__ int ub_u32(const uint32_t* __restrict__ P, int len, uint32_t target,
+                                      uint32_t mask) {
+  int pos = 0;
+  for (int step = 1 << (31 - __clz(len)); step > 0; step >>= 1) {
+    const int np = pos + step;
+    const uint32_t v = __ldg(P + (np <= len ? np : len) - 1) & mask;
+    pos = (np <= len && v <= target) ? np : pos;
+  }
+  return pos;
+}
+
+// Two searches over rows of the same length at once (independent loads).
+__device__ __forceinline__ void ub2_u32(const uint32_t* __restrict__ P, const uint32_t* __restrict__ Q,
+                                        int len, uint32_t tp, uint32_t tq, uint32_t mask, int* op,
+                                        int* oq) {
+  int a = 0, b = 0;
+  for (int step = 1 << (31 - __clz(len)); step > 0; step >>= 1) {
+    const int na = a + step, nb = b + step;
+    const uint32_t va = __ldg(P + (na <= len ? na : len) - 1) & mask;
+    const uint32_t vb = __ldg(Q + (nb <= len ? nb : len) - 1) & mask;
+    a = (na <= len && va <= tp) ? na : a;
+    b = (nb <= len && vb <= tq) ? nb : b;
+  }
+  *op = a;
+  *oq = b;
+}
+
+// The same over a shared-memory (or generic) array.
+template <typename T>
+__device__ __forceinline__ int ub_plain(const T* P, int len, T target) {
+  int pos = 0;
+  for (int step = 1 << (31 - __clz(len)); step > 0; step >>= 1) {
+    const int np = pos + step;
+    const T v = P[(np <= len ? np : len) - 1];
+    pos = (np <= len && v <= target) ? np : pos;
+  }
+  return pos;
+}
+
+// Number of entries <= target among the n (<= 16) entries at p: the
+// position of the first entry above target.  Independent loads, one round
+// trip.
+__device__ __forceinline__ int count_le_16_u32(const uint32_t* __restrict__ p, int n,
+                                               uint32_t target, uint32_t mask) {
+  int c = 0;
+#pragma unroll
+  for (int q = 0; q < 16; ++q)
+    if (q < n) c += ((__ldg(p + q) & mask) <= target) ? 1 : 0;
+  return c;
+}
+
+__device__ __forceinline__ int count_le_16_u64(const uint64_t* __restrict__ p, int n,
+                                               unsigned long long target) {
+  int c = 0;
+#pragma unroll
+  for (int q = 0; q < 16; ++q)
+    if (q < n) c += (__ldg((const unsigned long long*)p + q) <= target) ? 1 : 0;
+  return c;
+}
+
+// Entries <= target in a window of w (a multiple of 4) 16-byte-aligned
+// uint32 entries, loaded as uint4 (padding entries hold 0xFFFFFFFF).
+__device__ __forceinline__ int count_le_vec_u32(const uint32_t* __restrict__ p, int w,
+                                                uint32_t target) {
+  int c = 0;
+  const uint4* v = (const uint4*)p;
+#pragma unroll 8
+  for (int q = 0; q < (w >> 2); ++q) {
+    const uint4 x = __ldg(v + q);
+    c += (x.x <= target) + (x.y <= target) + (x.z <= target) + (x.w <= target);
+  }
+  return c;
+}
+
+__device__ __forceinline__ int count_le_vec_u64(const uint64_t* __restrict__ p, int w,
+                                                unsigned long long target) {
+  int c = 0;
+  const ulonglong2* v = (const ulonglong2*)p;
+#pragma unroll 8
+  for (int q = 0; q < (w >> 1); ++q) {
+    const ulonglong2 x = __ldg(v + q);
+    c += (x.x <= target) + (x.y <= target);
+  }
+  return c;
 }
 
 // The same searches through a coarse index (coarse[g] = prefix entry
@@ -134,6 +226,120 @@ __device__ __forceinline__ int64_t search_coarse_u32(const uint32_t* coarse, int
   return base + search_u32(prefix + base, wlen, target, mask, bad);
 }
 
+// Three-level inverse-CDF search (same result as the full search):
+//   level 1 (shared memory): c1[g] = prefix entry min((g+1) 2^lg1, len) - 1;
+//   level 2 (global): c2[h] = prefix entry min((h+1) 16, len) - 1, rows
+//     padded to a multiple of 4 with 0xFFFFFFFF; the level-1 block holds
+//     2^lg1 / 16 consecutive level-2 entries, counted with vector loads;
+//   level 3: the 16 prefix entries of the level-2 block, counted.
+// Each of levels 2 and 3 costs one round trip of independent loads.
+__device__ __forceinline__ int64_t search3_u32(const uint32_t* c1, int64_t n1,
+                                               const uint32_t* __restrict__ c2,
+                                               const uint32_t* __restrict__ prefix, int64_t len,
+                                               int lg1, uint32_t target, uint32_t mask,
+                                               bool* bad) {
+  int lo = ub_plain<uint32_t>(c1, (int)n1, target);
+  if (lo >= (int)n1) {
+    *bad = true;
+    lo = (int)n1 - 1;
+  }
+  const int w2 = 1 << (lg1 - 4);
+  const int64_t h0 = (int64_t)lo * w2;
+  const int64_t h = h0 + count_le_vec_u32(c2 + h0, w2, target);
+  const int64_t base = h << 4;
+  const int64_t n3 = (len - base) < 16 ? (len - base) : 16;
+  if (n3 <= 0) {
+    *bad = true;
+    return len - 1;
+  }
+  int c;
+  if (n3 == 16 && (((uintptr_t)(prefix + base)) & 15u) == 0) {
+    const uint4* v = (const uint4*)(prefix + base);
+    c = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 x = __ldg(v + q);
+      c += ((x.x & mask) <= target) + ((x.y & mask) <= target) + ((x.z & mask) <= target) +
+           ((x.w & mask) <= target);
+    }
+  } else {
+    c = count_le_16_u32(prefix + base, (int)n3, target, mask);
+  }
+  if (c >= n3) {
+    *bad = true;
+    return base + n3 - 1;
+  }
+  return base + c;
+}
+
+__device__ __forceinline__ int64_t search3_u64(const uint64_t* c1, int64_t n1,
+                                               const uint64_t* __restrict__ c2,
+                                               const uint64_t* __restrict__ prefix, int64_t len,
+                                               int lg1, unsigned long long target, bool* bad) {
+  int lo = ub_plain<unsigned long long>((const unsigned long long*)c1, (int)n1, target);
+  if (lo >= (int)n1) {
+    *bad = true;
+    lo = (int)n1 - 1;
+  }
+  const int w2 = 1 << (lg1 - 4);
+  const int64_t h0 = (int64_t)lo * w2;
+  const int64_t h = h0 + count_le_vec_u64(c2 + h0, w2, target);
+  const int64_t base = h << 4;
+  const int64_t n3 = (len - base) < 16 ? (len - base) : 16;
+  if (n3 <= 0) {
+    *bad = true;
+    return len - 1;
+  }
+  int c;
+  if (n3 == 16) {
+    const ulonglong2* v = (const ulonglong2*)(prefix + base);
+    c = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const ulonglong2 x = __ldg(v + q);
+      c += (x.x <= target) + (x.y <= target);
+    }
+  } else {
+    c = count_le_16_u64(prefix + base, (int)n3, target);
+  }
+  if (c >= n3) {
+    *bad = true;
+    return base + n3 - 1;
+  }
+  return base + c;
+}
+
+// round(b * 2^F) to nearest-even as an integer, from the FP32 fields of b
+// (exact: value = m * 2^E with a 24-bit m), without floating point.
+__device__ __forceinline__ long long fixed_point(float b, int F) {
+  const uint32_t bits = __float_as_uint(b);
+  const uint32_t e = (bits >> 23) & 0xFFu;
+  uint32_t m = bits & 0x7FFFFFu;
+  int E;
+  if (e == 0) {
+    if (m == 0) return 0;
+    E = -149;
+  } else {
+    m |= 0x800000u;
+    E = (int)e - 150;
+  }
+  const int sh = E + F;
+  long long r;
+  if (sh >= 0) {
+    r = (long long)m << sh;
+  } else if (sh < -25) {
+    r = 0;  // m * 2^sh < 1/2
+  } else {
+    const int rs = -sh;
+    const uint64_t mm = m;
+    const uint64_t q = mm >> rs;
+    const uint64_t rem = mm & ((1ull << rs) - 1ull);
+    const uint64_t half = 1ull << (rs - 1);
+    r = (long long)(q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull));
+  }
+  return (bits >> 31) ? -r : r;
+}
+
 // Sorted-list membership (0/1 CSR closure test).
 __device__ __forceinline__ bool contains_sorted(const int32_t* __restrict__ list, int64_t len,
                                                 int32_t value) {
@@ -174,21 +380,53 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// Linear probing from `slot`, wrapping at cap.  Returns 0 when the probe
-// limit is hit, 1 when the key existed, 2 when this call created it.
+// Linear probing from `slot`, wrapping at cap, four slots per round trip:
+// the keys of the 32-byte group holding `slot` are read with two 16-byte
+// loads, and the first slot of the group (from `slot` on) that is empty or
+// holds the key is claimed with one CAS.  Returns 0 when the probe limit is
+// hit, 1 when the key existed, 2 when this call created it.
 __device__ __forceinline__ int hash_add_from(unsigned long long* __restrict__ keys,
                                              long long* __restrict__ vals, uint64_t cap,
                                              uint64_t slot, uint32_t max_probe,
                                              unsigned long long key, long long v) {
-  for (uint32_t probe = 0; probe < max_probe; ++probe) {
-    // Claim-or-match in one atomic: the slot is ours when it was empty or
-    // already held the key.
-    const unsigned long long prev = atomicCAS(keys + slot, EMPTY_KEY, key);
-    if (prev == EMPTY_KEY || prev == key) {
-      atomicAdd((unsigned long long*)vals + slot, (unsigned long long)v);
-      return prev == EMPTY_KEY ? 2 : 1;
+  uint32_t probes = 0;
+  while (probes < max_probe) {
+    const uint64_t g = slot & ~3ull;
+    // Slots of the group at or past cap (a table size that is not a multiple
+    // of 4) are skipped; probing wraps to slot 0 after the group.
+    const uint32_t valid = (g + 4 <= cap) ? 4u : (uint32_t)(cap - g);
+    unsigned long long k4[4];
+    if (valid == 4) {
+      // L2 loads: keys only ever change from EMPTY to a key, and a stale
+      // EMPTY is caught by the CAS.
+      const ulonglong2 a = __ldcg((const ulonglong2*)(keys + g));
+      const ulonglong2 b = __ldcg((const ulonglong2*)(keys + g + 2));
+      k4[0] = a.x; k4[1] = a.y; k4[2] = b.x; k4[3] = b.y;
+    } else {
+#pragma unroll
+      for (uint32_t q = 0; q < 4; ++q) k4[q] = (q < valid) ? __ldcg(keys + g + q) : 0ull;
     }
-    slot = (slot + 1 == cap) ? 0 : slot + 1;
+    const uint32_t start = (uint32_t)(slot - g);
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      if (q < start || q >= valid) continue;
+      ++probes;
+      const unsigned long long cur = k4[q];
+      if (cur == key) {
+        atomicAdd((unsigned long long*)vals + g + q, (unsigned long long)v);
+        return 1;
+      }
+      if (cur == EMPTY_KEY) {
+        const unsigned long long prev = atomicCAS(keys + g + q, EMPTY_KEY, key);
+        if (prev == EMPTY_KEY || prev == key) {
+          atomicAdd((unsigned long long*)vals + g + q, (unsigned long long)v);
+          return prev == EMPTY_KEY ? 2 : 1;
+        }
+        // another key took the slot: look at the rest of the group
+      }
+    }
+    slot = g + 4;
+    if (slot >= cap) slot = 0;
   }
   return 0;
 }

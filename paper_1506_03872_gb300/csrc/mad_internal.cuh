@@ -57,7 +57,6 @@ struct SampleParams {
   const uint32_t* TA;
   const uint32_t* TB;
   unsigned long long t1_total;
-  double f_scale;                  // 2^F
   // Coarse indices (every 2^lg-th prefix entry) staged in shared memory by
   // the row-ordered kernels: T1c over T1, TBc over each row of TB (dense).
   const uint64_t* T1c;
@@ -66,6 +65,11 @@ struct SampleParams {
   const uint32_t* TBc;
   int64_t tbc_n;                   // entries per row of B
   int tbc_lg;
+  // Second level (every 16th entry, global, rows padded to whole level-1
+  // blocks with all-ones entries).
+  const uint64_t* T1c2;
+  const uint32_t* TBc2;
+  int f_exp;                       // F
   // Hash.  Regioned (dense inputs): the key (a, b) starts probing in the
   // home region of row a, [hreg[a], hreg[a+1]), sized from row a's expected
   // share of the diamonds; otherwise at mix(key) & hmask.  Probing is
@@ -120,6 +124,8 @@ struct mad_ctx {
   unsigned long long* r64 = nullptr;
   uint64_t* T1c = nullptr;          // coarse index of T1
   uint32_t* TBc = nullptr;          // coarse index of each TB row (dense)
+  uint64_t* T1c2 = nullptr;         // second-level indices
+  uint32_t* TBc2 = nullptr;
   int64_t t1c_n = 0, tbc_n = 0;
   int t1c_lg = 0, tbc_lg = 0;
   void* bt = nullptr;               // dense B^T (n x d), the input dtype

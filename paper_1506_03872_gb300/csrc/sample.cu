@@ -36,7 +36,7 @@ struct Draw {
 __device__ __forceinline__ int64_t draw_row_i(const SampleParams& p, unsigned long long u0,
                                               bool* bad, const uint64_t* t1c = nullptr) {
   const unsigned long long target = draw_target(u0, p.t1_total);
-  if (t1c) return search_coarse_u64(t1c, p.t1c_n, p.T1, p.m, p.t1c_lg, target, bad);
+  if (t1c) return search3_u64(t1c, p.t1c_n, p.T1c2, p.T1, p.m, p.t1c_lg, target, bad);
   return search_u64(p.T1, p.m, target, bad);
 }
 
@@ -53,10 +53,27 @@ __device__ __forceinline__ Draw draw_given_row(const SampleParams& p, const Unif
     a0 = __ldg(p.a_ptr + i);
     alen = __ldg(p.a_ptr + i + 1) - a0;
   }
-  // Center edge, stage 2: k within row i.
-  const uint32_t t2tot = __ldg(p.T2 + a0 + alen - 1) & mask;
-  const int64_t pk = search_u32(p.T2 + a0, alen, (uint32_t)draw_target(u.u1, t2tot), mask, bad);
-  const uint32_t e_k = __ldg(p.T2 + a0 + pk);
+  // Center edge, stage 2 (k within row i) and k' within row i: the two
+  // searches run over rows of the same length, side by side.
+  int64_t pk, pkp;
+  uint32_t e_k, e_kp = 0;
+  if (p.integer) {
+    const uint32_t t2tot = __ldg(p.T2 + a0 + alen - 1);
+    pk = ub_u32(p.T2 + a0, (int)alen, (uint32_t)draw_target(u.u1, t2tot), mask);
+    pkp = (int64_t)draw_target(u.u3, (unsigned long long)alen);
+  } else {
+    const uint32_t t2tot = __ldg(p.T2 + a0 + alen - 1) & mask;
+    const uint32_t tatot = __ldg(p.TA + a0 + alen - 1) & mask;
+    int a, b;
+    ub2_u32(p.T2 + a0, p.TA + a0, (int)alen, (uint32_t)draw_target(u.u1, t2tot),
+            (uint32_t)draw_target(u.u3, tatot), mask, &a, &b);
+    pk = a;
+    pkp = b;
+  }
+  if (pk >= alen) { *bad = true; pk = alen - 1; }
+  if (pkp >= alen) { *bad = true; pkp = alen - 1; }
+  e_k = __ldg(p.T2 + a0 + pk);
+  if (!p.integer) e_kp = __ldg(p.TA + a0 + pkp);
   const int64_t k = p.dense ? pk : (int64_t)__ldg(p.a_col + a0 + pk);
   // j from row k of B.
   int64_t b0, blen;
@@ -74,21 +91,16 @@ __device__ __forceinline__ Draw draw_given_row(const SampleParams& p, const Unif
   } else {
     const uint32_t tbtot = __ldg(p.TB + b0 + blen - 1) & mask;
     const uint32_t target = (uint32_t)draw_target(u.u2, tbtot);
-    pj = tbc ? search_coarse_u32(tbc + k * p.tbc_n, p.tbc_n, p.TB + b0, blen, p.tbc_lg, target, mask, bad)
-             : search_u32(p.TB + b0, blen, target, mask, bad);
+    if (tbc) {
+      pj = search3_u32(tbc + k * p.tbc_n, p.tbc_n, p.TBc2 + k * (p.tbc_n << (p.tbc_lg - 4)),
+                       p.TB + b0, blen, p.tbc_lg, target, mask, bad);
+    } else {
+      pj = ub_u32(p.TB + b0, (int)blen, target, mask);
+      if (pj >= blen) { *bad = true; pj = blen - 1; }
+    }
     e_j = __ldg(p.TB + b0 + pj);
   }
   const int64_t j = p.dense ? pj : (int64_t)__ldg(p.b_col + b0 + pj);
-  // k' from row i of A.
-  int64_t pkp;
-  uint32_t e_kp = 0;
-  if (p.integer) {
-    pkp = (int64_t)draw_target(u.u3, (unsigned long long)alen);
-  } else {
-    const uint32_t tatot = __ldg(p.TA + a0 + alen - 1) & mask;
-    pkp = search_u32(p.TA + a0, alen, (uint32_t)draw_target(u.u3, tatot), mask, bad);
-    e_kp = __ldg(p.TA + a0 + pkp);
-  }
   const int64_t kp = p.dense ? pkp : (int64_t)__ldg(p.a_col + a0 + pkp);
   // Increment.
   long long v;
@@ -108,7 +120,7 @@ __device__ __forceinline__ Draw draw_given_row(const SampleParams& p, const Unif
     const int64_t off = kp * p.ldb + j;
     const float b = p.b_f64 ? __double2float_rn(__ldg((const double*)p.b_val + off))
                             : __ldg((const float*)p.b_val + off);
-    v = __double2ll_rn((double)b * p.f_scale);
+    v = fixed_point(b, p.f_exp);
     if (!(p.flags & MAD_NONNEG) && ((e_k ^ e_j ^ e_kp) & SIGN_BIT)) v = -v;
   }
   Draw dr;
@@ -121,9 +133,10 @@ __device__ __forceinline__ Draw draw_given_row(const SampleParams& p, const Unif
 }
 
 __device__ __forceinline__ Draw draw_one(const SampleParams& p, unsigned long long seed,
-                                         unsigned long long ell, bool* bad) {
+                                         unsigned long long ell, bool* bad,
+                                         const uint64_t* t1c = nullptr) {
   const Uniforms u = diamond_uniforms(seed, ell);
-  return draw_given_row(p, u, draw_row_i(p, u.u0, bad), bad);
+  return draw_given_row(p, u, draw_row_i(p, u.u0, bad, t1c), bad);
 }
 
 // Per-lane bookkeeping of the sampling kernels.
@@ -132,45 +145,26 @@ struct Tally {
   bool bad = false, full = false;
 };
 
-// Filter one drawn diamond and add it to X with the other lanes of the warp
-// (all 32 lanes call this together; `valid` marks lanes holding a diamond).
+// Filter one drawn diamond and add it to X.  Lanes holding the same key
+// insert independently (the atomics combine them).
 __device__ __forceinline__ void accumulate(const SampleParams& p, bool valid, const Draw& dr,
                                            Tally& t) {
-  const int lane = threadIdx.x & 31;
-  bool want = false;
-  unsigned long long key = 0;
-  long long v = 0;
-  if (valid) {
-    if ((p.flags & MAD_EXCLUDE_DIAG) && dr.i == dr.j) {
-      ++t.diag;
-    } else if (dr.v != 0) {
-      uint32_t a = dr.i, b = dr.j;
-      if ((p.flags & MAD_GRAM) && b < a) {
-        a = dr.j;
-        b = dr.i;
-      }
-      key = ((unsigned long long)a << 32) | b;
-      v = dr.v;
-      want = true;
-      ++t.inserted;
-    }
+  if (!valid) return;
+  if ((p.flags & MAD_EXCLUDE_DIAG) && dr.i == dr.j) {
+    ++t.diag;
+    return;
   }
-  const unsigned active = __ballot_sync(0xFFFFFFFFu, want);
-  if (want) {
-    const unsigned peers = __match_any_sync(active, key);
-    long long total = 0;
-    unsigned rem = peers;
-    while (rem) {
-      const int src = __ffs(rem) - 1;
-      total += __shfl_sync(peers, v, src);
-      rem &= rem - 1;
-    }
-    if (lane == __ffs(peers) - 1) {
-      const int r = hash_add(p, key, total);
-      if (r == 0) t.full = true;
-      if (r == 2) ++t.created;
-    }
+  if (dr.v == 0) return;
+  uint32_t a = dr.i, b = dr.j;
+  if ((p.flags & MAD_GRAM) && b < a) {
+    a = dr.j;
+    b = dr.i;
   }
+  const unsigned long long key = ((unsigned long long)a << 32) | b;
+  ++t.inserted;
+  const int r = hash_add(p, key, dr.v);
+  if (r == 0) t.full = true;
+  if (r == 2) ++t.created;
 }
 
 __device__ __forceinline__ void flush_tally(const SampleParams& p, Tally& t) {
@@ -196,6 +190,9 @@ __device__ __forceinline__ void flush_tally(const SampleParams& p, Tally& t) {
 __global__ void __launch_bounds__(256)
 k_sample(const SampleParams p, unsigned long long seed, unsigned long long first,
          unsigned long long s) {
+  extern __shared__ uint64_t t1c[];
+  for (int64_t g = threadIdx.x; g < p.t1c_n; g += blockDim.x) t1c[g] = p.T1c[g];
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const unsigned long long warp_id = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -203,7 +200,7 @@ k_sample(const SampleParams p, unsigned long long seed, unsigned long long first
   for (unsigned long long base = warp_id * 32; base < s; base += warps * 32) {
     const unsigned long long q = base + lane;
     Draw dr{};
-    if (q < s) dr = draw_one(p, seed, first + q, &t.bad);
+    if (q < s) dr = draw_one(p, seed, first + q, &t.bad, t1c);
     accumulate(p, q < s, dr, t);
   }
   flush_tally(p, t);
@@ -245,7 +242,7 @@ k_bucket_scatter(const unsigned long long* __restrict__ rec, const unsigned int*
 }
 
 // Diamonds in row order (dense inputs): sorted[q] = (i << 32) | (l - first).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_sample_sorted(const SampleParams p, unsigned long long seed, unsigned long long first,
                 unsigned long long s, const unsigned long long* __restrict__ sorted) {
   extern __shared__ uint32_t tbc[];
@@ -334,7 +331,9 @@ SampleParams make_params(const mad_ctx* ctx) {
   p.TBc = ctx->TBc;
   p.tbc_n = ctx->tbc_n;
   p.tbc_lg = ctx->tbc_lg;
-  p.f_scale = std::ldexp(1.0, ctx->f);
+  p.T1c2 = ctx->T1c2;
+  p.TBc2 = ctx->TBc2;
+  p.f_exp = ctx->f;
   p.hkeys = ctx->hkeys;
   p.hvals = ctx->hvals;
   p.hreg = ctx->hreg;
@@ -354,14 +353,12 @@ SampleParams make_params(const mad_ctx* ctx) {
 mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, cudaStream_t st) {
   if (s == 0) return MAD_OK;
   const SampleParams p = make_params(ctx);
+  const size_t smem_t1c = (size_t)p.t1c_n * sizeof(uint64_t);
   if (!ctx->dense) {
-    static int full = 0;
-    if (!full) full = full_grid(k_sample);
-    k_sample<<<grid_of(s, full), 256, 0, st>>>(p, seed, first, s);
+    k_sample<<<grid_of(s, full_grid(k_sample, smem_t1c)), 256, smem_t1c, st>>>(p, seed, first, s);
     count_launch(ctx);
     return cuda_status(cudaGetLastError());
   }
-  const size_t smem_t1c = (size_t)p.t1c_n * sizeof(uint64_t);
   const size_t smem_tbc = (size_t)(p.d * p.tbc_n) * sizeof(uint32_t);
   static bool attrs = false;
   if (!attrs) {

@@ -188,11 +188,16 @@ k_log_hist(const long long* __restrict__ vals, uint64_t cap, unsigned long long 
   for (int b = threadIdx.x; b < 1024; b += blockDim.x) h[b] = 0;
   __syncthreads();
   unsigned long long mx = 0;
-  for (uint64_t slot = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < cap;
-       slot += (uint64_t)gridDim.x * blockDim.x) {
-    const long long v = vals[slot];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t rounds = (cap + stride - 1) / stride;
+  for (uint64_t r = 0; r < rounds; ++r) {
+    const uint64_t slot = r * stride + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long v = slot < cap ? vals[slot] : 0;
+    const uint32_t bin = v > 0 ? log_bucket((unsigned long long)v) : 0xFFFFu;
+    // one shared-memory atomic per distinct bucket per warp
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, bin);
     if (v > 0) {
-      atomicAdd(&h[log_bucket((unsigned long long)v)], 1u);
+      if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[bin], __popc(peers));
       if ((unsigned long long)v > mx) mx = (unsigned long long)v;
     }
   }
@@ -307,6 +312,56 @@ k_select_block(const Item* __restrict__ list, unsigned n, unsigned K, int dp,
       const unsigned pos = atomicAdd(&s_count, 1u);
       if (pos < K) out[pos] = it;
     }
+  }
+}
+
+// ---- rank sort for short lists ---------------------------------------------
+// Item x lands at its rank: the number of items that come before it by
+// (p desc, key asc, position asc).  The position makes ranks a permutation
+// even for repeated keys; only the first K ranks are written.  The n^2
+// comparisons are split over blockIdx.y slices of the list, each slice adding
+// its count with one atomic per item, so a list of a few thousand items still
+// spreads over the whole GPU.
+constexpr unsigned kRankSortMax = 1u << 14;
+constexpr int kRankTile = 1024;
+
+__global__ void __launch_bounds__(256)
+k_rank_count(const Item* __restrict__ in, unsigned n, unsigned slice, unsigned* __restrict__ rank) {
+  __shared__ ulonglong2 sv[kRankTile];
+  const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lo = blockIdx.y * slice;
+  const unsigned hi = min(n, lo + slice);
+  unsigned long long mp = 0, mk = 0;
+  if (x < n) {
+    mp = in[x].p;
+    mk = in[x].key;
+  }
+  unsigned cnt = 0;
+  for (unsigned base = lo; base < hi; base += kRankTile) {
+    const unsigned len = min((unsigned)kRankTile, hi - base);
+    __syncthreads();
+    for (unsigned q = threadIdx.x; q < len; q += blockDim.x)
+      sv[q] = make_ulonglong2(in[base + q].p, in[base + q].key);
+    __syncthreads();
+    if (x < n) {
+#pragma unroll 8
+      for (unsigned q = 0; q < len; ++q) {
+        const ulonglong2 o = sv[q];
+        const bool before = o.x > mp || (o.x == mp && (o.y < mk || (o.y == mk && base + q < x)));
+        cnt += before ? 1u : 0u;
+      }
+    }
+  }
+  if (x < n && cnt) atomicAdd(&rank[x], cnt);
+}
+
+__global__ void __launch_bounds__(256)
+k_rank_scatter(const Item* __restrict__ in, unsigned n, unsigned K, const unsigned* __restrict__ rank,
+               Item* __restrict__ out) {
+  const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < n) {
+    const unsigned r = rank[x];
+    if (r < K) out[r] = in[x];
   }
 }
 
@@ -460,10 +515,18 @@ mad_status select_list(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K,
   *n_sel = take;
   if (take == 0) return MAD_OK;
   unsigned long long n2 = 0;
-  if (take == n) {
-    cudaMemcpyAsync(ws.out, ws.l0, n * sizeof(Item), cudaMemcpyDeviceToDevice, st);
+  // Short lists are ranked whole (ranks >= K are dropped).  Longer ones
+  // first pick the K largest, unordered, into `sel`; those are then ranked
+  // when K is short, else sorted in place by a bitonic network.
+  const bool rank_sort = take <= kRankSortMax;
+  Item* sel = rank_sort ? ws.l2 : ws.out;
+  uint64_t nr = take;   // items ranked
+  if (take == n || n <= kRankSortMax) {
+    sel = ws.l0;
+    nr = n;
+    if (!rank_sort) cudaMemcpyAsync(ws.out, ws.l0, n * sizeof(Item), cudaMemcpyDeviceToDevice, st);
   } else if (n <= kBlockSelectMax) {
-    k_select_block<<<1, 1024, 0, st>>>(ws.l0, (unsigned)n, (unsigned)K, dp, ws.out);
+    k_select_block<<<1, 1024, 0, st>>>(ws.l0, (unsigned)n, (unsigned)K, dp, sel);
     count_launch(ctx);
   } else {
     SelState* dst = (SelState*)ws.state;
@@ -477,9 +540,25 @@ mad_status select_list(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K,
       k_radix_filter<<<blocks, 256, 0, st>>>(ws.l0, ws.l1, ws.l2, dst, q, dp, ws.cap_n);
       count_launch(ctx, 2);
     }
+    // The filter passes ping-pong through l1/l2; collect from l0 with the
+    // final digit state, so `sel` may reuse l2 once they are done.
     cudaMemsetAsync(ws.counter, 0, sizeof(unsigned long long), st);
-    k_collect<<<grid_for(n, 152 * 8), 256, 0, st>>>(ws.l0, n, dst, ws.out, ws.counter, ws.cap_out);
+    k_collect<<<grid_for(n, 152 * 8), 256, 0, st>>>(ws.l0, n, dst, sel, ws.counter,
+                                                     rank_sort ? ws.cap_n : ws.cap_out);
     count_launch(ctx);
+  }
+  if (rank_sort) {
+    unsigned* rank = (unsigned*)ws.l1;
+    const unsigned nt = (unsigned)nr;
+    const unsigned nb = (nt + 255) / 256;
+    unsigned slices = std::min((152u * 8u + nb - 1) / nb, nb);
+    const unsigned slice = (nt + slices - 1) / slices;
+    slices = (nt + slice - 1) / slice;
+    cudaMemsetAsync(rank, 0, nt * sizeof(unsigned), st);
+    k_rank_count<<<dim3(nb, slices), 256, 0, st>>>(sel, nt, slice, rank);
+    k_rank_scatter<<<nb, 256, 0, st>>>(sel, nt, (unsigned)take, rank, ws.out);
+    count_launch(ctx, 2);
+    return cuda_status(cudaGetLastError());
   }
   bitonic_sort(ctx, ws.out, take, st, &n2);
   return cuda_status(cudaGetLastError());

@@ -86,9 +86,10 @@ __device__ __forceinline__ unsigned long long block_exclusive_u64(unsigned long 
   return out;
 }
 
-// round(w * scale) for a row table, with the support-preserving bump.
-__device__ __forceinline__ uint32_t quantize_row(float w, double scale) {
-  uint32_t q = __double2uint_rn((double)w * scale);
+// round(w * 2^e) for a row table (integer round-to-nearest-even, no FP64),
+// with the support-preserving bump.
+__device__ __forceinline__ uint32_t quantize_row(float w, int e) {
+  uint32_t q = (uint32_t)fixed_point(w, e);
   if (w > 0.0f && q == 0u) q = 1u;
   return q;
 }
@@ -124,18 +125,19 @@ k_b_rows_dense(const T* __restrict__ B, int64_t n, int64_t ldb, float* __restric
   if (t == 0) nb[k] = total;
 
   uint32_t* __restrict__ out = TB + k * n;
-  const double scale = total > 0.0f ? pow2d(29 - ilogb_pos(total)) : 0.0;
+  const int e = total > 0.0f ? 29 - ilogb_pos(total) : 0;
+  constexpr int PER = 16;  // consecutive entries per thread and tile
   uint32_t carry = 0;
-  for (int64_t base = 0; base < n; base += 1024) {
-    uint32_t q[4], sg[4], local = 0;
+  for (int64_t base = 0; base < n; base += 256 * PER) {
+    uint32_t q[PER], sg[PER], local = 0;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int64_t idx = base + 4 * t + c;
+    for (int c = 0; c < PER; ++c) {
+      const int64_t idx = base + PER * t + c;
       q[c] = 0;
       sg[c] = 0;
       if (idx < n) {
         const float v = to_f32(row[idx]);
-        if (total > 0.0f) local += quantize_row(fabsf(v), scale);
+        if (total > 0.0f) local += quantize_row(fabsf(v), e);
         q[c] = local;
         sg[c] = v < 0.0f ? SIGN_BIT : 0u;
       }
@@ -143,8 +145,8 @@ k_b_rows_dense(const T* __restrict__ B, int64_t n, int64_t ldb, float* __restric
     uint32_t tile_total;
     const uint32_t excl = block_exclusive_u32(local, warp_tot, &tile_total);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int64_t idx = base + 4 * t + c;
+    for (int c = 0; c < PER; ++c) {
+      const int64_t idx = base + PER * t + c;
       if (idx < n) out[idx] = (carry + excl + q[c]) | sg[c];
     }
     carry += tile_total;
@@ -210,8 +212,8 @@ k_a_rows_dense(const T* __restrict__ A, int64_t m, int64_t d, int64_t lda,
     rmax = fmaxf(rmax, r);
 
     const bool live = s > 0.0f;
-    const double sc2 = live ? pow2d(29 - ilogb_pos(s)) : 0.0;
-    const double sca = live ? pow2d(29 - ilogb_pos(na)) : 0.0;
+    const int e2 = live ? 29 - ilogb_pos(s) : 0;
+    const int ea = live ? 29 - ilogb_pos(na) : 0;
     uint32_t* __restrict__ o2 = T2 + i * d;
     uint32_t* __restrict__ oa = TA + i * d;
     uint32_t c2 = 0, ca = 0;
@@ -222,8 +224,8 @@ k_a_rows_dense(const T* __restrict__ A, int64_t m, int64_t d, int64_t lda,
         const float v = to_f32(row[idx]);
         const float a = fabsf(v);
         if (live) {
-          q2 = quantize_row(__fmul_rn(a, nb[idx]), sc2);
-          qa = quantize_row(a, sca);
+          q2 = quantize_row(__fmul_rn(a, nb[idx]), e2);
+          qa = quantize_row(a, ea);
         }
         sg = v < 0.0f ? SIGN_BIT : 0u;
       }
@@ -287,10 +289,10 @@ __device__ __forceinline__ int t1_exponent(const DevScalars* sc, int clog2m) {
 }
 
 __device__ __forceinline__ unsigned long long t1_weight(const float* r, const unsigned long long* r64,
-                                                        int64_t i, double scale) {
+                                                        int64_t i, int e1) {
   if (r64) return r64[i];
   const float v = r[i];
-  unsigned long long q = __double2ull_rn((double)v * scale);
+  unsigned long long q = (unsigned long long)fixed_point(v, e1);
   if (v > 0.0f && q == 0ull) q = 1ull;
   return q;
 }
@@ -299,10 +301,10 @@ __global__ void __launch_bounds__(256)
 k_t1_chunk_sums(const float* __restrict__ r, const unsigned long long* __restrict__ r64,
                 int64_t m, int clog2m, unsigned long long* __restrict__ partial, DevScalars* sc) {
   __shared__ unsigned long long warp_tot[9];
-  double scale = 0.0;
+  int scale = 0;
   if (!r64) {
     if (sc->maxr_bits == 0u) return;  // ||W||_1 == 0, reported by the host
-    scale = pow2d(t1_exponent(sc, clog2m));
+    scale = t1_exponent(sc, clog2m);
   }
   const int64_t base = (int64_t)blockIdx.x * T1_CHUNK + threadIdx.x * 8;
   unsigned long long acc = 0;
@@ -348,10 +350,10 @@ k_t1_write(const float* __restrict__ r, const unsigned long long* __restrict__ r
            int clog2m, const unsigned long long* __restrict__ offset, uint64_t* __restrict__ T1,
            const DevScalars* sc) {
   __shared__ unsigned long long warp_tot[9];
-  double scale = 0.0;
+  int scale = 0;
   if (!r64) {
     if (sc->maxr_bits == 0u) return;
-    scale = pow2d(t1_exponent(sc, clog2m));
+    scale = t1_exponent(sc, clog2m);
   }
   const int64_t base = (int64_t)blockIdx.x * T1_CHUNK + threadIdx.x * 8;
   unsigned long long q[8], acc = 0;
@@ -407,6 +409,27 @@ __global__ void k_coarse_rows_u32(const uint32_t* __restrict__ T, int64_t rows, 
     const int64_t r = x / nc, g = x % nc;
     const int64_t end = ((g + 1) << lg) < len ? ((g + 1) << lg) : len;
     out[x] = T[r * len + end - 1] & PREFIX_MASK;
+  }
+}
+
+// Second-level indices: every 16th prefix entry, each row padded to whole
+// level-1 blocks (n1 * 2^(lg1-4) entries) with all-ones entries.
+__global__ void k_coarse2_u64(const uint64_t* __restrict__ T, int64_t len, int64_t padded,
+                              uint64_t* __restrict__ out) {
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < padded;
+       h += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t end = ((h + 1) << 4) < len ? ((h + 1) << 4) : len;
+    out[h] = (h << 4) < len ? T[end - 1] : ~0ull;
+  }
+}
+
+__global__ void k_coarse2_rows_u32(const uint32_t* __restrict__ T, int64_t rows, int64_t len,
+                                   int64_t padded, uint32_t* __restrict__ out) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < rows * padded;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = x / padded, h = x % padded;
+    const int64_t end = ((h + 1) << 4) < len ? ((h + 1) << 4) : len;
+    out[x] = (h << 4) < len ? (T[r * len + end - 1] & PREFIX_MASK) : 0xFFFFFFFFu;
   }
 }
 
@@ -501,6 +524,19 @@ mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st) {
   if (ctx->T1c) {
     k_coarse_u64<<<(unsigned)((ctx->t1c_n + 255) / 256), 256, 0, st>>>(ctx->T1, ctx->m, ctx->t1c_lg,
                                                                        ctx->t1c_n, ctx->T1c);
+    count_launch(ctx);
+  }
+  if (ctx->T1c2) {
+    const int64_t padded = ctx->t1c_n << (ctx->t1c_lg - 4);
+    k_coarse2_u64<<<(unsigned)((padded + 255) / 256), 256, 0, st>>>(ctx->T1, ctx->m, padded,
+                                                                    ctx->T1c2);
+    count_launch(ctx);
+  }
+  if (ctx->TBc2) {
+    const int64_t padded = ctx->tbc_n << (ctx->tbc_lg - 4);
+    const int64_t total = ctx->d * padded;
+    k_coarse2_rows_u32<<<(unsigned)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32),
+                         256, 0, st>>>(ctx->TB, ctx->d, ctx->n, padded, ctx->TBc2);
     count_launch(ctx);
   }
   if (ctx->TBc) {
