@@ -178,6 +178,157 @@ def _ground_truth_dense(A, B, t):
     return set(keys.cpu().tolist()), tau
 
 
+def ground_truth_gram_binary(rowptr, colidx, t, device, h0=2048):
+    """Exact top-t common-neighbour counts over unordered off-diagonal pairs
+    of a symmetric 0/1 adjacency (harness only; recall ground truth).
+
+    A pair's count is at most the smaller of its two degrees.  So with H the
+    h highest-degree nodes, once the t-th largest count among pairs inside H
+    exceeds the largest degree outside H, no pair with an end outside H can
+    reach or tie it, and the top t inside H is the top t overall.  Counts
+    inside H are dense products of 0/1 column blocks (FP16 on a GPU, partial
+    sums of at most 2048 ones exact; FP32 elsewhere) accumulated in FP32; h
+    doubles until the condition holds.
+
+    Returns (tau, counts) with tau the t-th largest count and `counts` a
+    function giving the exact count of given (i, j) pairs inside H (None
+    outside H)."""
+    import torch
+    rp = torch.as_tensor(np.asarray(rowptr, dtype=np.int64), device=device)
+    ci = torch.as_tensor(np.asarray(colidx).astype(np.int64), device=device)
+    n = rp.numel() - 1
+    deg = rp[1:] - rp[:-1]
+    order = torch.argsort(-deg, stable=True)
+    fdt = torch.float16 if rp.is_cuda else torch.float32
+    chunk = 2048
+    h = min(n, max(h0, 2 * t))
+    while True:
+        H = order[:h]
+        outside = int(deg[order[h]].item()) if h < n else -1
+        lens = deg[H]
+        total = int(lens.sum().item())
+        local = torch.repeat_interleave(torch.arange(h, device=device), lens)
+        first = torch.repeat_interleave(rp[H] - (torch.cumsum(lens, 0) - lens), lens)
+        cols = ci[torch.arange(total, device=device) + first]
+        cs, perm = torch.sort(cols)
+        ls = local[perm]
+        _, inv = torch.unique_consecutive(cs, return_inverse=True)
+        u = int(inv[-1].item()) + 1 if total else 0
+        C = torch.zeros(h, h, dtype=torch.float32, device=device)
+        bounds = torch.searchsorted(inv, torch.arange(0, u + chunk, chunk, device=device))
+        for q in range((u + chunk - 1) // chunk):
+            lo, hi = int(bounds[q].item()), int(bounds[q + 1].item())
+            blk = torch.zeros(h, chunk, dtype=fdt, device=device)
+            blk[ls[lo:hi], inv[lo:hi] - q * chunk] = 1
+            C += (blk @ blk.T).float()
+        iu = torch.triu_indices(h, h, 1, device=device)
+        vals = C[iu[0], iu[1]]
+        kk = min(t, vals.numel())
+        tau = float(torch.topk(vals, kk).values[-1].item()) if kk else 0.0
+        if tau > outside or h >= n:
+            break
+        h = min(n, 2 * h)
+    pos = torch.full((n,), -1, dtype=torch.int64, device=device)
+    pos[H] = torch.arange(h, device=device)
+    Cc = C
+
+    def counts(i, j):
+        pi = pos[torch.as_tensor(np.asarray(i, dtype=np.int64), device=device)]
+        pj = pos[torch.as_tensor(np.asarray(j, dtype=np.int64), device=device)]
+        inside = (pi >= 0) & (pj >= 0)
+        v = torch.full(pi.shape, float("nan"), dtype=torch.float64, device=device)
+        v[inside] = Cc[pi[inside], pj[inside]].double()
+        return v.cpu().numpy()
+
+    return tau, counts
+
+
+def recall_of(w, gi, gj, gc, truth, tau, counts=None):
+    """|Omega_t ∩ T_t| / t.  Dense: key intersection with the exact top t.
+    Integer (C3): results with an exact count >= the t-th largest count are
+    hits, since pairs tied with the t-th value are all top-t pairs; the
+    reported counts are also checked against the exact ones."""
+    if counts is None:
+        got = set(mad_keys(gi, gj))
+        return len(got & truth) / w.t, None
+    exact = counts(gi, gj)
+    known = ~np.isnan(exact)
+    mismatch = int(np.sum(exact[known] != gc[known]))
+    hits = int(np.sum(gc >= tau))
+    return min(hits, w.t) / w.t, mismatch
+
+
+def mad_keys(gi, gj):
+    return ((gi.astype(np.int64) << 32) | gj.astype(np.int64)).tolist()
+
+
+def _ladder(step, w, truth, tau, counts, flush, s_max_bytes, seeds, stream, recall_at_s):
+    """Time to top-t at recall >= 0.95: the smallest s on {1,2,5} x 10^k
+    whose median recall over `seeds` sampler seeds reaches 0.95.  The walk
+    starts at the workload's s and goes up while the median falls short, or
+    down while it still reaches the target.  Each rung is one warm-up, then
+    one timed step per seed (L2 flushed before each)."""
+    import torch
+
+    import paper_1506_03872_gb300 as mad
+    ladder = [m * 10 ** e for e in range(3, 12) for m in (1, 2, 5)]
+    q0 = min(range(len(ladder)), key=lambda q: abs(np.log(ladder[q] / w.s)))
+    up = recall_at_s < 0.95
+    rungs = []
+    result = {"rungs": rungs, "s": None, "ms": None, "recall": None}
+
+    def run(s):
+        rec, ms = [], []
+        step(s, w.sampler_seed)   # warm-up at this s (sizes the hash)
+        for q in range(seeds):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res, nr = step(s, w.sampler_seed + q)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            gi, gj, gx, gc = mad.decode_pairs(res, nr)
+            rec.append(recall_of(w, gi, gj, gc, truth, tau, counts)[0])
+        r = {"s": s, "recall_median": float(np.median(rec)),
+             "ms_median": round(float(np.median(ms)), 3)}
+        rungs.append(r)
+        return r
+
+    q = q0
+    while 0 <= q < len(ladder):
+        s = ladder[q]
+        if hash_bytes_estimate(w, s) > s_max_bytes:
+            result["stopped"] = f"s={s} needs more device memory than the cap"
+            break
+        r = run(s)
+        if r["recall_median"] >= 0.95:
+            result.update(s=s, ms=r["ms_median"], recall=r["recall_median"])
+            if up:
+                break
+            q -= 1
+        elif not up and result["s"] is None:
+            up = True   # one seed reached the target at this s, the median did not
+            q += 1
+        elif not up:
+            break
+        else:
+            q += 1
+    return result
+
+
+def hash_bytes_estimate(w, s):
+    """Device bytes the library allocates for the hash at budget s: 16-byte
+    slots, m + 3s of them for dense inputs (per-row regions), else the power
+    of two at or above s / 0.6."""
+    if w.csr:
+        cap = 1024
+        while cap < s / 0.6:
+            cap <<= 1
+        return 16 * cap
+    return 16 * (w.m + 3 * s + 1)
+
+
 def run_ours(args):
     import torch
 
@@ -206,12 +357,14 @@ def run_ours(args):
     out_t = mad.new_pairs(t)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
-    def step(A_, B_, timing=None):
+    def step(A_, B_, timing=None, s_=None, seed_=None):
+        s_ = s if s_ is None else s_
+        seed_ = seed if seed_ is None else seed_
         e = [ev() for _ in range(5)] if timing is not None else None
         if e: e[0].record(stream)
-        mad.mad_build_tables(ctx.ctx, A_, B_, s)
+        mad.mad_build_tables(ctx.ctx, A_, B_, s_)
         if e: e[1].record(stream)
-        mad.mad_sample(ctx.ctx, s, seed)
+        mad.mad_sample(ctx.ctx, s_, seed_)
         if e: e[2].record(stream)
         cand, nc = mad.mad_topk(ctx.ctx, tprime, out_c)
         if e: e[3].record(stream)
@@ -249,10 +402,14 @@ def run_ours(args):
     recall = None
     tau = None
     truth = set()
-    if not w.csr and rank == 0 and not args.no_recall:
-        truth, tau = _ground_truth_dense(tensors[0], tensors[1], t)
-        got = set(mad.keys_of(gi, gj).astype(np.int64).tolist())
-        recall = len(got & truth) / t
+    counts = None
+    mismatch = None
+    if rank == 0 and not args.no_recall:
+        if w.csr:
+            tau, counts = ground_truth_gram_binary(w.rowptr, w.colidx, t, dev)
+        else:
+            truth, tau = _ground_truth_dense(tensors[0], tensors[1], t)
+        recall, mismatch = recall_of(w, gi, gj, gc, truth, tau, counts)
     stats = mad.mad_stats(ctx.ctx)
 
     # End to end through the C ABI from pinned host memory.
@@ -323,6 +480,16 @@ def run_ours(args):
         except Exception as ex:  # the comparator must not cost the main line
             comp = {"error": str(ex)[:200]}
 
+    ladder = None
+    if rank == 0 and recall is not None and not args.no_ladder:
+        try:
+            free, _ = torch.cuda.mem_get_info(dev)
+            cap = int(0.6 * free)
+            ladder = _ladder(lambda s_, seed_: step(Am, Bm, s_=s_, seed_=seed_), w, truth, tau,
+                             counts, flush, cap, args.ladder_seeds, stream, recall)
+        except Exception as ex:  # the ladder must not cost the main line
+            ladder = {"error": str(ex)[:200]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, args.cpu_diamonds)
@@ -338,7 +505,7 @@ def run_ours(args):
             "phases_ms": {k: round(float(phase[:, q].mean()), 4)
                           for q, k in enumerate(["build_tables", "sample", "topk", "rescore"])},
             "diamonds_per_s_sampler": round(s / (sample_ms / 1e3), 1),
-            "recall_at_s": recall, "tau_t": tau,
+            "recall_at_s": recall, "tau_t": tau, "count_mismatches": mismatch,
             "stats": {k: stats[k] for k in ("w1", "inserted", "distinct", "positive",
                                               "hash_capacity")},
             "e2e": {"value": round(world * s * args.steps / (e2e_total / 1e3), 1),
@@ -346,7 +513,9 @@ def run_ours(args):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "comparator": comp,
-            "time_to_top_t": {"sampling_ms": round(ms_per_step, 4), "sampling_recall": recall,
+            "time_to_top_t": {"recall_target": 0.95,
+                              "sampling_ms_at_s": round(ms_per_step, 4), "sampling_recall_at_s": recall,
+                              "ladder": ladder,
                               "comparator_ms": comp.get("ms") if comp else None,
                               "comparator_recall": comp.get("recall") if comp else None},
             "roofline": roof,
@@ -422,6 +591,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--no-ladder", action="store_true",
+                    help="skip the time-to-recall ladder over s")
+    ap.add_argument("--ladder-seeds", type=int, default=5)
     ap.add_argument("--rescore", type=int, default=0,
                     help="comparator FP32 rescore budget (0: 8t)")
     args = ap.parse_args()

@@ -129,10 +129,14 @@ typedef struct mad_stats_t {
 typedef struct mad_ctx mad_ctx;
 
 /* Create a context on the current CUDA device.  flags: MAD_NONNEG |
- * MAD_GRAM | MAD_EXCLUDE_DIAG.  Returns MAD_ERR_ARG for unknown flags. */
+ * MAD_GRAM | MAD_EXCLUDE_DIAG.  Returns MAD_ERR_ARG for unknown flags.
+ * The context allocates its tables, hash and scratch from a private
+ * stream-ordered memory pool that keeps freed pages mapped, so repeated
+ * mad_build_tables calls of one shape do not map memory again. */
 mad_status mad_create(mad_ctx** ctx, uint32_t flags);
 
-/* Free everything the context owns (synchronises the device). */
+/* Free everything the context owns, its memory pool included
+ * (synchronises the device). */
 void mad_destroy(mad_ctx* ctx);
 
 /* Static description of a status code. */

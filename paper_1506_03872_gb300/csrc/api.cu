@@ -23,7 +23,7 @@ mad_status ensure_scratch(mad_ctx* ctx, size_t bytes, cudaStream_t st) {
   ctx->scratch = nullptr;
   ctx->scratch_bytes = 0;
   const size_t rounded = (bytes + (1u << 20) - 1) & ~(size_t)((1u << 20) - 1);
-  const cudaError_t e = cudaMallocAsync(&ctx->scratch, rounded, st);
+  const cudaError_t e = cudaMallocFromPoolAsync(&ctx->scratch, rounded, ctx->pool, st);
   if (e != cudaSuccess) {
     ctx->scratch = nullptr;
     return cuda_status(e);
@@ -72,10 +72,10 @@ void free_tables(mad_ctx* ctx, cudaStream_t st) {
 }
 
 template <typename T>
-mad_status alloc(T*& p, size_t count, cudaStream_t st) {
+mad_status alloc(mad_ctx* ctx, T*& p, size_t count, cudaStream_t st) {
   p = nullptr;
   if (count == 0) count = 1;
-  return cuda_status(cudaMallocAsync((void**)&p, count * sizeof(T), st));
+  return cuda_status(cudaMallocFromPoolAsync((void**)&p, count * sizeof(T), ctx->pool, st));
 }
 
 mad_status device_error_status(uint32_t err) {
@@ -125,10 +125,23 @@ mad_status mad_create(mad_ctx** out, uint32_t flags) {
   if (!ctx) return MAD_ERR_OOM;
   ctx->flags = flags;
   cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = ctx->device;
+    e = cudaMemPoolCreate(&ctx->pool, &props);
+  }
+  if (e == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->sc, sizeof(DevScalars));
   if (e == cudaSuccess) e = cudaMemset(ctx->sc, 0, sizeof(DevScalars));
   if (e != cudaSuccess) {
     if (ctx->sc) cudaFree(ctx->sc);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     delete ctx;
     return cuda_status(e);
   }
@@ -143,6 +156,7 @@ void mad_destroy(mad_ctx* ctx) {
   if (ctx->scratch) cudaFreeAsync(ctx->scratch, 0);
   cudaStreamSynchronize(0);
   cudaFree(ctx->sc);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   delete ctx;
 }
 
@@ -204,39 +218,39 @@ mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
     if (na <= 0 || nb <= 0) return MAD_ERR_EMPTY;
     ctx->nnz_a = (uint64_t)na;
     ctx->nnz_b = (uint64_t)nb;
-    if ((rs = alloc(ctx->T2, ctx->nnz_a, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx->r64, (size_t)ctx->m, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->T2, ctx->nnz_a, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->r64, (size_t)ctx->m, st)) != MAD_OK) return rs;
   } else {
     ctx->nnz_a = (uint64_t)(ctx->m * ctx->d);
     ctx->nnz_b = (uint64_t)(ctx->d * ctx->n);
     const size_t eb = B->dt == MAD_F64 ? 8 : 4;
-    if ((rs = alloc(ctx->T2, ctx->nnz_a, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx->TA, ctx->nnz_a, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx->TB, ctx->nnz_b, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx->na, (size_t)ctx->m, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx->r, (size_t)ctx->m, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx->nb, (size_t)ctx->d, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->T2, ctx->nnz_a, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->TA, ctx->nnz_a, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->TB, ctx->nnz_b, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->na, (size_t)ctx->m, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->r, (size_t)ctx->m, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->nb, (size_t)ctx->d, st)) != MAD_OK) return rs;
     char* bt = nullptr;
-    if ((rs = alloc(bt, (size_t)(ctx->n * ctx->d) * eb, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, bt, (size_t)(ctx->n * ctx->d) * eb, st)) != MAD_OK) return rs;
     ctx->bt = bt;
   }
-  if ((rs = alloc(ctx->T1, (size_t)ctx->m, st)) != MAD_OK) return rs;
+  if ((rs = alloc(ctx, ctx->T1, (size_t)ctx->m, st)) != MAD_OK) return rs;
   // Coarse search indices staged in shared memory by the sampling kernels:
   // T1 in at most 16 KB, all rows of TB (dense) in at most 40 KB.
   // Level-1 blocks hold at least 64 entries (whole 16-byte vectors at level 2).
   ctx->t1c_lg = 6;
   while ((((uint64_t)ctx->m + (1ull << ctx->t1c_lg) - 1) >> ctx->t1c_lg) * 8 > 16384) ++ctx->t1c_lg;
   ctx->t1c_n = (int64_t)(((uint64_t)ctx->m + (1ull << ctx->t1c_lg) - 1) >> ctx->t1c_lg);
-  if ((rs = alloc(ctx->T1c, (size_t)ctx->t1c_n, st)) != MAD_OK) return rs;
-  if ((rs = alloc(ctx->T1c2, (size_t)(ctx->t1c_n << (ctx->t1c_lg - 4)), st)) != MAD_OK) return rs;
+  if ((rs = alloc(ctx, ctx->T1c, (size_t)ctx->t1c_n, st)) != MAD_OK) return rs;
+  if ((rs = alloc(ctx, ctx->T1c2, (size_t)(ctx->t1c_n << (ctx->t1c_lg - 4)), st)) != MAD_OK) return rs;
   if (dense) {
     ctx->tbc_lg = 6;
     while ((uint64_t)ctx->d * ((((uint64_t)ctx->n + (1ull << ctx->tbc_lg) - 1) >> ctx->tbc_lg)) * 4 >
            40960)
       ++ctx->tbc_lg;
     ctx->tbc_n = (int64_t)(((uint64_t)ctx->n + (1ull << ctx->tbc_lg) - 1) >> ctx->tbc_lg);
-    if ((rs = alloc(ctx->TBc, (size_t)(ctx->d * ctx->tbc_n), st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx->TBc2, (size_t)(ctx->d * (ctx->tbc_n << (ctx->tbc_lg - 4))), st)) != MAD_OK)
+    if ((rs = alloc(ctx, ctx->TBc, (size_t)(ctx->d * ctx->tbc_n), st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->TBc2, (size_t)(ctx->d * (ctx->tbc_n << (ctx->tbc_lg - 4))), st)) != MAD_OK)
       return rs;
   } else {
     ctx->tbc_n = 0;
@@ -247,15 +261,15 @@ mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   uint64_t cap = ctx->hcap_request;
   if (ctx->regioned) {
     cap = hash_region_bound((uint64_t)ctx->m, s_max);
-    if ((rs = alloc(ctx->hreg, (size_t)ctx->m + 1, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->hreg, (size_t)ctx->m + 1, st)) != MAD_OK) return rs;
   } else if (cap == 0) {
     const double want = (double)s_max / 0.6;
     cap = 1024;
     while ((double)cap < want && cap < (1ull << 40)) cap <<= 1;
   }
   ctx->hcap = ctx->hcap_alloc = cap;
-  if ((rs = alloc(ctx->hkeys, cap, st)) != MAD_OK) return rs;
-  if ((rs = alloc(ctx->hvals, cap, st)) != MAD_OK) return rs;
+  if ((rs = alloc(ctx, ctx->hkeys, cap, st)) != MAD_OK) return rs;
+  if ((rs = alloc(ctx, ctx->hvals, cap, st)) != MAD_OK) return rs;
   cudaMemsetAsync(ctx->sc, 0, sizeof(DevScalars), st);
   if ((rs = build_tables_impl(ctx, st)) != MAD_OK) return rs;
   if (ctx->regioned && (rs = build_hash_regions(ctx, st)) != MAD_OK) return rs;

@@ -592,13 +592,22 @@ k_max_floor(const float* __restrict__ v, unsigned long long n, unsigned kkeep,
   __shared__ unsigned int h[4096];
   for (int b = threadIdx.x; b < 4096; b += blockDim.x) h[b] = 0;
   __syncthreads();
+  constexpr int U = 4;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long rounds = (n + stride - 1) / stride;
+  const unsigned long long rounds = (n + U * stride - 1) / (U * stride);
   for (unsigned long long r = 0; r < rounds; ++r) {
-    const unsigned long long x = r * stride + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned bin = x < n ? (__float_as_uint(fmaxf(v[x], 0.0f)) >> 19) : 0x1000u;
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, bin);
-    if (bin < 4096u && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[bin], __popc(peers));
+    float f[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const unsigned long long x = (r * U + q) * stride + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+      f[q] = x < n ? __ldcs(v + x) : -1.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const unsigned bin = f[q] >= 0.0f ? (__float_as_uint(f[q]) >> 19) : 0x1000u;
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, bin);
+      if (bin < 4096u && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[bin], __popc(peers));
+    }
   }
   __syncthreads();
   for (int b = threadIdx.x; b < 4096; b += blockDim.x)
@@ -607,17 +616,11 @@ k_max_floor(const float* __restrict__ v, unsigned long long n, unsigned kkeep,
   __shared__ unsigned int is_last;
   if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   __syncthreads();
-  if (!is_last || threadIdx.x != 0) return;
+  if (!is_last) return;
   __threadfence();
-  volatile unsigned int* gh = hist;
-  unsigned long long cum = 0;
-  for (int b = 4095; b >= 0; --b) {
-    cum += gh[b];
-    if (cum >= kkeep) {
-      atomicMax(g_theta, (unsigned)b << 19);
-      return;
-    }
-  }
+  unsigned long long total = 0;
+  const int b = block_pick_from_top<4096>(hist, kkeep, &total);
+  if (threadIdx.x == 0 && b >= 0) atomicMax(g_theta, (unsigned)b << 19);
 }
 
 // FP32 rescore of the selected candidates: lane L sums k = L mod 32 with

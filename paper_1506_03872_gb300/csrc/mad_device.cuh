@@ -309,35 +309,25 @@ __device__ __forceinline__ int64_t search3_u64(const uint64_t* c1, int64_t n1,
   return base + c;
 }
 
-// round(b * 2^F) to nearest-even as an integer, from the FP32 fields of b
-// (exact: value = m * 2^E with a 24-bit m), without floating point.
+// 2^e as an FP32 value, -126 <= e <= 127.
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+// b * 2^F rounded to the nearest integer, ties to even, as int64 (callers
+// keep |b * 2^F| < 2^63).  Scaling an FP32 value by a power of two is exact
+// while the product stays a normal number, so the product is formed exactly
+// (in two steps when 2^F itself is outside the normal range, each step
+// keeping its result normal) and converted once with round-to-nearest-even.
+// A product below 2^-126 in magnitude rounds to 0 whatever its last bits.
 __device__ __forceinline__ long long fixed_point(float b, int F) {
-  const uint32_t bits = __float_as_uint(b);
-  const uint32_t e = (bits >> 23) & 0xFFu;
-  uint32_t m = bits & 0x7FFFFFu;
-  int E;
-  if (e == 0) {
-    if (m == 0) return 0;
-    E = -149;
+  float x;
+  if (F > 127) {
+    x = (b * pow2f(127)) * pow2f(min(F - 127, 127));
+  } else if (F < -126) {
+    x = (b * pow2f(-126)) * pow2f(max(F + 126, -126));
   } else {
-    m |= 0x800000u;
-    E = (int)e - 150;
+    x = b * pow2f(F);
   }
-  const int sh = E + F;
-  long long r;
-  if (sh >= 0) {
-    r = (long long)m << sh;
-  } else if (sh < -25) {
-    r = 0;  // m * 2^sh < 1/2
-  } else {
-    const int rs = -sh;
-    const uint64_t mm = m;
-    const uint64_t q = mm >> rs;
-    const uint64_t rem = mm & ((1ull << rs) - 1ull);
-    const uint64_t half = 1ull << (rs - 1);
-    r = (long long)(q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull));
-  }
-  return (bits >> 31) ? -r : r;
+  return __float2ll_rn(x);
 }
 
 // Sorted-list membership (0/1 CSR closure test).
@@ -444,6 +434,53 @@ __device__ __forceinline__ uint64_t home_slot(const SampleParams& p, unsigned lo
 
 __device__ __forceinline__ int hash_add(const SampleParams& p, unsigned long long key, long long v) {
   return hash_add_from(p.hkeys, p.hvals, p.hcap, home_slot(p, key), p.max_probe, key, v);
+}
+
+// Histogram pick by one whole block of 256 threads: the highest bucket b
+// whose count from the top (buckets b .. NB-1) reaches K, or -1 when the
+// total stays below K; *total receives the sum of all buckets.  The counts
+// are read from global memory (L2), each thread owning NB/256 consecutive
+// buckets from the top, and a block scan finds the thread whose range the
+// running count crosses.  Every thread of the block must call it.
+template <int NB>
+__device__ int block_pick_from_top(const unsigned int* hist, unsigned long long K,
+                                   unsigned long long* total) {
+  static_assert(NB % 256 == 0, "buckets per thread");
+  constexpr int PER = NB / 256;
+  __shared__ unsigned long long csum[256];
+  __shared__ int pick;
+  const int t = threadIdx.x;
+  unsigned int v[PER];
+  unsigned long long mine = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    v[q] = __ldcg(hist + (NB - 1 - (t * PER + q)));
+    mine += v[q];
+  }
+  csum[t] = mine;
+  if (t == 0) pick = -1;
+  __syncthreads();
+  for (int off = 1; off < 256; off <<= 1) {
+    const unsigned long long add = t >= off ? csum[t - off] : 0ull;
+    __syncthreads();
+    csum[t] += add;
+    __syncthreads();
+  }
+  const unsigned long long before = t ? csum[t - 1] : 0ull;
+  if (before < K && csum[t] >= K) {
+    unsigned long long cum = before;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      cum += v[q];
+      if (cum >= K) {
+        pick = NB - 1 - (t * PER + q);
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  *total = csum[255];
+  return pick;
 }
 
 }  // namespace mad

@@ -104,6 +104,10 @@ struct Item {
 struct mad_ctx {
   uint32_t flags = 0;
   int device = 0;
+  // Private stream-ordered pool for every table, the hash and the scratch:
+  // it keeps freed memory mapped, so rebuilding tables of the same shape
+  // re-uses pages instead of mapping them again.
+  cudaMemPool_t pool = nullptr;
   bool built = false;
   bool integer = false;
   bool dense = false;

@@ -102,6 +102,94 @@ k_rescore_binary(const mad_pair* __restrict__ cand, unsigned long long ncand,
   }
 }
 
+// MAD_GRAM on 0/1 rows (B = A^T): c_ij = |row i of A ∩ row j of A|, an
+// exact count.  One warp per candidate picks the cheaper of two parallel
+// intersections: when one row is much shorter, lanes look its entries up in
+// the longer row by binary search; otherwise the two rows are merged along
+// 32 equal diagonals of their merge path (ties taken from the shorter row
+// first), each lane counting the entries of the shorter row it consumes
+// that equal the next entry of the longer row.
+__device__ __forceinline__ int ceil_log2_i(int64_t v) {
+  int r = 0;
+  while ((1ll << r) < v) ++r;
+  return r;
+}
+
+__global__ void __launch_bounds__(256)
+k_rescore_gram_binary(const mad_pair* __restrict__ cand, unsigned long long ncand,
+                      const int64_t* __restrict__ a_ptr, const int32_t* __restrict__ a_col,
+                      int64_t m, double* __restrict__ cvals, Item* __restrict__ items,
+                      DevScalars* sc) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned long long q = warp; q < ncand; q += warps) {
+    const uint32_t i = cand[q].i, j = cand[q].j;
+    long long count = 0;
+    const bool ok = i < m && j < m;
+    if (ok) {
+      const int64_t i0 = __ldg(a_ptr + i), i1 = __ldg(a_ptr + i + 1);
+      const int64_t j0 = __ldg(a_ptr + j), j1 = __ldg(a_ptr + j + 1);
+      const bool i_short = (i1 - i0) <= (j1 - j0);
+      const int32_t* S = a_col + (i_short ? i0 : j0);
+      const int32_t* L = a_col + (i_short ? j0 : i0);
+      const int64_t ps = i_short ? i1 - i0 : j1 - j0;
+      const int64_t ql = i_short ? j1 - j0 : i1 - i0;
+      const int lgq = ceil_log2_i(ql + 1);
+      if ((ps + 31) / 32 * lgq <= (ps + ql + 31) / 32 + ceil_log2_i(ps + 1)) {
+        for (int64_t e = lane; e < ps; e += 32) {
+          const int32_t x = __ldg(S + e);
+          int64_t lo = 0, len = ql;
+          while (len > 0) {
+            const int64_t half = len >> 1;
+            if (__ldg(L + lo + half) < x) {
+              lo += half + 1;
+              len -= half + 1;
+            } else {
+              len = half;
+            }
+          }
+          count += (lo < ql && __ldg(L + lo) == x) ? 1 : 0;
+        }
+      } else {
+        const int64_t total = ps + ql;
+        const int64_t per = (total + 31) / 32;
+        const int64_t d0 = min(total, per * lane), d1 = min(total, per * (lane + 1));
+        // number of S entries among the first d0 merged entries
+        int64_t lo = d0 > ql ? d0 - ql : 0, hi = d0 < ps ? d0 : ps;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (__ldg(S + mid) <= __ldg(L + (d0 - mid - 1))) lo = mid + 1;
+          else hi = mid;
+        }
+        int64_t a = lo, b = d0 - lo;
+        for (int64_t dd = d0; dd < d1; ++dd) {
+          const int32_t sv = a < ps ? __ldg(S + a) : 0x7FFFFFFF;
+          const int32_t lv = b < ql ? __ldg(L + b) : 0x7FFFFFFF;
+          if (a < ps && (b >= ql || sv <= lv)) {
+            count += (b < ql && sv == lv) ? 1 : 0;
+            ++a;
+          } else {
+            ++b;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) count += __shfl_xor_sync(0xFFFFFFFFu, count, off);
+    if (lane == 0) {
+      if (!ok) atomicOr(&sc->err, DERR_SEARCH);
+      const double c = ok ? (double)count : 0.0;
+      cvals[q] = c;
+      Item it;
+      it.p = (unsigned long long)__double_as_longlong(c);
+      it.key = ((unsigned long long)i << 32) | j;
+      it.aux = q;
+      items[q] = it;
+    }
+  }
+}
+
 template <typename TA, typename TB>
 void launch_dense(mad_ctx* ctx, const mad_pair* cand, uint64_t ncand, Item* items, double* cvals,
                   cudaStream_t st) {
@@ -117,7 +205,12 @@ void launch_dense(mad_ctx* ctx, const mad_pair* cand, uint64_t ncand, Item* item
 mad_status rescore_items(mad_ctx* ctx, const mad_pair* cand, uint64_t ncand, Item* items,
                          double* cvals, cudaStream_t st) {
   if (ncand == 0) return MAD_OK;
-  if (ctx->integer) {
+  if (ctx->integer && (ctx->flags & MAD_GRAM)) {
+    const unsigned long long blocks = (ncand * 32 + 255) / 256;
+    k_rescore_gram_binary<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(
+        cand, ncand, ctx->A.rowptr, ctx->A.colidx, ctx->m, cvals, items, ctx->sc);
+    count_launch(ctx);
+  } else if (ctx->integer) {
     const unsigned long long blocks = (ncand * 32 + 255) / 256;
     k_rescore_binary<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(
         cand, ncand, ctx->A.rowptr, ctx->A.colidx, ctx->B.rowptr, ctx->B.colidx, ctx->m, ctx->n,

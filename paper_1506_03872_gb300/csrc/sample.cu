@@ -206,30 +206,28 @@ k_sample(const SampleParams p, unsigned long long seed, unsigned long long first
   flush_tally(p, t);
 }
 
-// Counting sort of diamonds by row i, step 1: draw i (Philox block 0 and
-// T1), count it, remember (i, rank within row).
+// Counting sort of diamonds into row order, step 1: bucket each diamond by
+// the top bits of its stage-1 target (Philox block 0 and T1's total only).
+// The row i = upper_bound(T1, target) is non-decreasing in the target, so
+// bucket order is row order; the search itself is left to the draw kernel,
+// where neighbouring diamonds search the same few lines of T1.
 __global__ void __launch_bounds__(256)
-k_bucket_count(const SampleParams p, unsigned long long seed, unsigned long long first,
-               unsigned long long s, unsigned int* __restrict__ cnt,
+k_bucket_count(unsigned long long t1_total, int shift, unsigned long long seed,
+               unsigned long long first, unsigned long long s, unsigned int* __restrict__ cnt,
                unsigned long long* __restrict__ rec) {
-  extern __shared__ uint64_t t1c[];
-  for (int64_t g = threadIdx.x; g < p.t1c_n; g += blockDim.x) t1c[g] = p.T1c[g];
-  __syncthreads();
-  bool bad = false;
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < s;
        q += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned long long ell = first + q;
     const uint4 b0 = philox4x32_10(make_uint4((uint32_t)ell, (uint32_t)(ell >> 32), 0u, 0u), key);
     const unsigned long long u0 = ((unsigned long long)b0.y << 32) | b0.x;
-    const int64_t i = draw_row_i(p, u0, &bad, t1c);
-    const unsigned int r = atomicAdd(cnt + i, 1u);
-    rec[q] = ((unsigned long long)i << 32) | r;
+    const uint32_t b = (uint32_t)(draw_target(u0, t1_total) >> shift);
+    const unsigned int r = atomicAdd(cnt + b, 1u);
+    rec[q] = ((unsigned long long)b << 32) | r;
   }
-  if (bad) atomicOr(&p.sc->err, DERR_SEARCH);
 }
 
-// Step 3: place diamond q at off[i] + rank.
+// Step 3: place diamond q at off[bucket] + rank.
 __global__ void __launch_bounds__(256)
 k_bucket_scatter(const unsigned long long* __restrict__ rec, const unsigned int* __restrict__ off,
                  unsigned long long s, unsigned long long* __restrict__ sorted) {
@@ -241,27 +239,69 @@ k_bucket_scatter(const unsigned long long* __restrict__ rec, const unsigned int*
   }
 }
 
-// Diamonds in row order (dense inputs): sorted[q] = (i << 32) | (l - first).
+// Diamonds in row order (dense inputs): sorted[q] = (bucket << 32) | (l - first).
+// Draws only: diamond q's hash key goes to keys[q] (EMPTY_KEY when it adds
+// nothing: v = 0 or an excluded diagonal) and its increment over sorted[q]
+// (each thread rewrites only the entry it read).  k_insert adds them to X.
 __global__ void __launch_bounds__(256, 4)
 k_sample_sorted(const SampleParams p, unsigned long long seed, unsigned long long first,
-                unsigned long long s, const unsigned long long* __restrict__ sorted) {
+                unsigned long long s, unsigned long long* __restrict__ sorted,
+                unsigned long long* __restrict__ keys) {
   extern __shared__ uint32_t tbc[];
   const int64_t ntbc = p.d * p.tbc_n;
   for (int64_t g = threadIdx.x; g < ntbc; g += blockDim.x) tbc[g] = p.TBc[g];
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const unsigned long long warp_id = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-  Tally t;
-  for (unsigned long long base = warp_id * 32; base < s; base += warps * 32) {
-    const unsigned long long q = base + lane;
-    Draw dr{};
-    if (q < s) {
-      const unsigned long long e = __ldg(sorted + q);
-      const Uniforms u = diamond_uniforms(seed, first + (uint32_t)e);
-      dr = draw_given_row(p, u, (int64_t)(e >> 32), &t.bad, tbc);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  bool bad = false;
+  unsigned long long diag = 0;
+  for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < s;
+       q += stride) {
+    const unsigned long long e = sorted[q];
+    const Uniforms u = diamond_uniforms(seed, first + (uint32_t)e);
+    const int64_t i = draw_row_i(p, u.u0, &bad, p.T1c);
+    const Draw dr = draw_given_row(p, u, i, &bad, tbc);
+    unsigned long long key = EMPTY_KEY;
+    if ((p.flags & MAD_EXCLUDE_DIAG) && dr.i == dr.j) {
+      ++diag;
+    } else if (dr.v != 0) {
+      uint32_t a = dr.i, b = dr.j;
+      if ((p.flags & MAD_GRAM) && b < a) {
+        a = dr.j;
+        b = dr.i;
+      }
+      key = ((unsigned long long)a << 32) | b;
     }
-    accumulate(p, q < s, dr, t);
+    keys[q] = key;
+    sorted[q] = (unsigned long long)dr.v;
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) diag += __shfl_xor_sync(0xFFFFFFFFu, diag, off);
+  const unsigned any_bad = __ballot_sync(0xFFFFFFFFu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    if (diag) atomicAdd(&p.sc->diag_skipped, diag);
+    if (any_bad) atomicOr(&p.sc->err, DERR_SEARCH);
+  }
+}
+
+// X update for the row-ordered diamonds: a lean kernel (full occupancy) so
+// many inserts are in flight at once; consecutive entries share row i and
+// hence its hash region.
+__global__ void __launch_bounds__(256, 6)
+k_insert(const SampleParams p, const unsigned long long* __restrict__ keys,
+         const long long* __restrict__ vals, unsigned long long s) {
+  Tally t;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long rounds = (s + stride - 1) / stride;
+  for (unsigned long long r = 0; r < rounds; ++r) {
+    const unsigned long long q = base + r * stride;
+    const unsigned long long key = q < s ? __ldcs(keys + q) : EMPTY_KEY;
+    if (key != EMPTY_KEY) {
+      ++t.inserted;
+      const int res = hash_add(p, key, __ldcs(vals + q));
+      if (res == 0) t.full = true;
+      if (res == 2) ++t.created;
+    }
   }
   flush_tally(p, t);
 }
@@ -362,16 +402,22 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
   const size_t smem_tbc = (size_t)(p.d * p.tbc_n) * sizeof(uint32_t);
   static bool attrs = false;
   if (!attrs) {
-    cudaFuncSetAttribute(k_bucket_count, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
     cudaFuncSetAttribute(k_sample_sorted, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
     attrs = true;
   }
-  const int full_count = full_grid(k_bucket_count, smem_t1c);
+  const int full_count = full_grid(k_bucket_count);
   const int full_sorted = full_grid(k_sample_sorted, smem_tbc);
-  const uint64_t m = (uint64_t)ctx->m;
+  const int full_insert = full_grid(k_insert);
+  // Buckets of 2^shift target values, at most 2^ceil(log2 m) of them.
+  int lgm = 0;
+  while ((1ull << lgm) < (uint64_t)ctx->m) ++lgm;
+  int lgt = 0;
+  while (lgt < 64 && (ctx->t1_total - 1) >> lgt) ++lgt;
+  const int shift = lgt > lgm ? lgt - lgm : 0;
+  const uint64_t nbk = ((ctx->t1_total - 1) >> shift) + 1;
   const uint64_t batch = s < kSortBatch ? s : kSortBatch;
-  const size_t cnt_bytes = ((m + 1) * sizeof(uint32_t) + 255) & ~(size_t)255;
-  const size_t part_bytes = (scan_partial_elems(m) * sizeof(uint32_t) + 255) & ~(size_t)255;
+  const size_t cnt_bytes = ((nbk + 1) * sizeof(uint32_t) + 255) & ~(size_t)255;
+  const size_t part_bytes = (scan_partial_elems(nbk) * sizeof(uint32_t) + 255) & ~(size_t)255;
   const size_t rec_bytes = batch * sizeof(unsigned long long);
   mad_status rs = ensure_scratch(ctx, 2 * cnt_bytes + part_bytes + 2 * rec_bytes, st);
   if (rs != MAD_OK) return rs;
@@ -383,15 +429,16 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
   unsigned long long* sorted = rec + batch;
   for (uint64_t done = 0; done < s; done += batch) {
     const uint64_t n = (s - done) < batch ? (s - done) : batch;
-    cudaMemsetAsync(cnt, 0, m * sizeof(uint32_t), st);
-    k_bucket_count<<<grid_of(n, full_count), 256, smem_t1c, st>>>(p, seed, first + done, n, cnt,
-                                                                  rec);
+    cudaMemsetAsync(cnt, 0, nbk * sizeof(uint32_t), st);
+    k_bucket_count<<<grid_of(n, full_count), 256, 0, st>>>(ctx->t1_total, shift, seed,
+                                                           first + done, n, cnt, rec);
     count_launch(ctx);
-    if ((rs = scan_exclusive_u32(ctx, cnt, off, m, part, st)) != MAD_OK) return rs;
+    if ((rs = scan_exclusive_u32(ctx, cnt, off, nbk, part, st)) != MAD_OK) return rs;
     k_bucket_scatter<<<grid_of(n, full_count), 256, 0, st>>>(rec, off, n, sorted);
     k_sample_sorted<<<grid_of(n, full_sorted), 256, smem_tbc, st>>>(p, seed, first + done, n,
-                                                                    sorted);
-    count_launch(ctx, 2);
+                                                                    sorted, rec);
+    k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, rec, (const long long*)sorted, n);
+    count_launch(ctx, 3);
   }
   return cuda_status(cudaGetLastError());
 }

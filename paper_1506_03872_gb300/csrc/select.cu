@@ -188,17 +188,26 @@ k_log_hist(const long long* __restrict__ vals, uint64_t cap, unsigned long long 
   for (int b = threadIdx.x; b < 1024; b += blockDim.x) h[b] = 0;
   __syncthreads();
   unsigned long long mx = 0;
+  // Four independent loads per thread per round keep enough bytes in flight.
+  constexpr int U = 4;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t rounds = (cap + stride - 1) / stride;
+  const uint64_t rounds = (cap + U * stride - 1) / (U * stride);
   for (uint64_t r = 0; r < rounds; ++r) {
-    const uint64_t slot = r * stride + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long v = slot < cap ? vals[slot] : 0;
-    const uint32_t bin = v > 0 ? log_bucket((unsigned long long)v) : 0xFFFFu;
-    // one shared-memory atomic per distinct bucket per warp
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, bin);
-    if (v > 0) {
-      if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[bin], __popc(peers));
-      if ((unsigned long long)v > mx) mx = (unsigned long long)v;
+    long long v[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const uint64_t slot = (r * U + q) * stride + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+      v[q] = slot < cap ? __ldg(vals + slot) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const uint32_t bin = v[q] > 0 ? log_bucket((unsigned long long)v[q]) : 0xFFFFu;
+      // one shared-memory atomic per distinct bucket per warp
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, bin);
+      if (v[q] > 0) {
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[bin], __popc(peers));
+        if ((unsigned long long)v[q] > mx) mx = (unsigned long long)v[q];
+      }
     }
   }
 #pragma unroll
@@ -214,21 +223,14 @@ k_log_hist(const long long* __restrict__ vals, uint64_t cap, unsigned long long 
   __shared__ unsigned int is_last;
   if (threadIdx.x == 0) is_last = (atomicAdd(&st->ticket3, 1u) == gridDim.x - 1);
   __syncthreads();
-  if (!is_last || threadIdx.x != 0) return;
+  if (!is_last) return;
   __threadfence();
-  volatile unsigned int* gh = st->lhist;
-  unsigned long long cum = 0, theta = 1;  // fewer than K positive: take all
-  for (int b = 1023; b >= 0; --b) {
-    cum += gh[b];
-    if (cum >= K) {
-      theta = bucket_floor((uint32_t)b);
-      break;
-    }
-  }
   unsigned long long total = 0;
-  for (int b = 0; b < 1024; ++b) total += gh[b];
-  st->theta = theta;
-  st->positive = total;
+  const int b = block_pick_from_top<1024>(st->lhist, K, &total);
+  if (threadIdx.x == 0) {
+    st->theta = b >= 0 ? bucket_floor((uint32_t)b) : 1ull;  // fewer than K positive: take all
+    st->positive = total;
+  }
 }
 
 __global__ void __launch_bounds__(256)
@@ -236,133 +238,135 @@ k_compact_ge(const unsigned long long* __restrict__ keys, const long long* __res
              uint64_t cap, const SelState* st, Item* __restrict__ out, uint64_t out_cap,
              unsigned long long* counter) {
   const unsigned long long theta = st->theta;
+  constexpr int U = 4;   // independent loads in flight per thread
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t rounds = (cap + stride - 1) / stride;
+  const uint64_t rounds = (cap + U * stride - 1) / (U * stride);
   const uint64_t start = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (uint64_t r = 0; r < rounds; ++r) {
-    const uint64_t slot = start + r * stride;
-    bool want = false;
-    Item it;
-    if (slot < cap) {
-      const long long v = vals[slot];
-      if (v > 0 && (unsigned long long)v >= theta) {
-        it.p = (unsigned long long)v;
+    long long v[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const uint64_t slot = start + (r * U + q) * stride;
+      v[q] = slot < cap ? __ldcs(vals + slot) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const uint64_t slot = start + (r * U + q) * stride;
+      const bool want = v[q] > 0 && (unsigned long long)v[q] >= theta;
+      Item it;
+      if (want) {
+        it.p = (unsigned long long)v[q];
         it.key = keys[slot];
         it.aux = slot;
-        want = true;
       }
+      append(out, counter, want, it, out_cap);
     }
-    append(out, counter, want, it, out_cap);
   }
 }
 
-// ---- single-block MSB radix select for short lists -------------------------
-constexpr unsigned kBlockSelectMax = 1u << 15;
+// ---- tile sort + merge rank (lists up to 2^17 items) ------------------------
+// Total order: p desc, key asc, then input position asc (so repeated keys
+// still get distinct ranks).  Step 1 sorts tiles of 2048 items in shared
+// memory (bitonic network); step 2 gives every item whose rank inside its
+// tile is below K its global rank, its tile rank plus, for every other tile,
+// the number of that tile's items ordered before it (a binary search), and
+// writes the items ranked below K to their place.
+constexpr unsigned kTile = 2048;
+constexpr unsigned kTileSortMax = 1u << 17;
+
+__device__ __forceinline__ bool item_before(unsigned long long ap, unsigned long long ak, uint32_t ai,
+                                            unsigned long long bp, unsigned long long bk, uint32_t bi) {
+  return ap > bp || (ap == bp && (ak < bk || (ak == bk && ai < bi)));
+}
 
 __global__ void __launch_bounds__(1024)
-k_select_block(const Item* __restrict__ list, unsigned n, unsigned K, int dp,
-               Item* __restrict__ out) {
-  __shared__ unsigned int h[256];
-  __shared__ unsigned long long s_tp, s_tk, s_mp, s_mk;
-  __shared__ unsigned int s_krem, s_count;
-  __shared__ int s_done;
-  if (threadIdx.x == 0) {
-    s_tp = s_tk = s_mp = s_mk = 0;
-    s_krem = K;
-    s_done = 0;
-    s_count = 0;
+k_tile_sort(const Item* __restrict__ in, unsigned n, unsigned K, Item* __restrict__ out,
+            uint32_t* __restrict__ pos_out) {
+  __shared__ unsigned long long sp[kTile], sk[kTile];
+  __shared__ uint32_t si[kTile];
+  const unsigned base = blockIdx.x * kTile;
+  const unsigned len = min(kTile, n - base);
+  for (unsigned r = threadIdx.x; r < kTile; r += blockDim.x) {
+    if (r < len) {
+      sp[r] = in[base + r].p;
+      sk[r] = in[base + r].key;
+      si[r] = base + r;
+    } else {
+      sp[r] = 0;
+      sk[r] = ~0ull;
+      si[r] = 0xFFFFFFFFu;
+    }
   }
   __syncthreads();
-  const int last_q = dp + 7;
-  for (int q = 0; q <= last_q; ++q) {
-    if (s_done) break;
-    for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
-    __syncthreads();
-    const unsigned long long tp = s_tp, tk = s_tk, mp = s_mp, mk = s_mk;
-    for (unsigned x = threadIdx.x; x < n; x += blockDim.x) {
-      const Item it = list[x];
-      if ((it.p & mp) == tp && ((~it.key) & mk) == tk) atomicAdd(&h[digit_of(it, q, dp)], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned above = 0;
-      int b = 255;
-      for (; b > 0; --b) {
-        if (above + h[b] >= s_krem) break;
-        above += h[b];
+  for (unsigned k = 2; k <= kTile; k <<= 1) {
+    for (unsigned j = k >> 1; j > 0; j >>= 1) {
+      const unsigned t = threadIdx.x;   // kTile / 2 compare-exchanges
+      const unsigned a = (t / j) * 2 * j + (t % j), b = a + j;
+      const bool up = (a & k) == 0;
+      const bool b_first = item_before(sp[b], sk[b], si[b], sp[a], sk[a], si[a]);
+      if (b_first == up) {
+        const unsigned long long tp = sp[a], tk = sk[a];
+        const uint32_t ti = si[a];
+        sp[a] = sp[b]; sk[a] = sk[b]; si[a] = si[b];
+        sp[b] = tp; sk[b] = tk; si[b] = ti;
       }
-      s_krem -= above;
-      if (q < dp) {
-        const int sh = 8 * (dp - 1 - q);
-        s_tp |= (unsigned long long)b << sh;
-        s_mp |= 0xFFull << sh;
+      __syncthreads();
+    }
+  }
+  for (unsigned r = threadIdx.x; r < len; r += blockDim.x) {
+    if (pos_out) {
+      out[base + r] = in[si[r]];
+      pos_out[base + r] = si[r];
+    } else if (r < K) {
+      out[r] = in[si[r]];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_merge_rank(const Item* __restrict__ tiles, const uint32_t* __restrict__ pos, unsigned n, unsigned K,
+             Item* __restrict__ out) {
+  const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  const unsigned my_tile = x / kTile, r = x % kTile;
+  if (r >= K) return;
+  const Item me = tiles[x];
+  const uint32_t mi = pos[x];
+  const unsigned ntiles = (n + kTile - 1) / kTile;
+  unsigned rank = r;
+  for (unsigned b = 0; b < ntiles && rank < K; ++b) {
+    if (b == my_tile) continue;
+    const unsigned base = b * kTile, len = min(kTile, n - base);
+    unsigned lo = 0, cnt = len;   // first entry of tile b not ordered before me
+    while (cnt > 0) {
+      const unsigned half = cnt >> 1, q = base + lo + half;
+      if (item_before(tiles[q].p, tiles[q].key, pos[q], me.p, me.key, mi)) {
+        lo += half + 1;
+        cnt -= half + 1;
       } else {
-        const int sh = 8 * (7 - (q - dp));
-        s_tk |= (unsigned long long)b << sh;
-        s_mk |= 0xFFull << sh;
-      }
-      if (h[b] == s_krem || q == last_q) s_done = 1;
-    }
-    __syncthreads();
-  }
-  const unsigned long long tp = s_tp, tk = s_tk;
-  for (unsigned x = threadIdx.x; x < n; x += blockDim.x) {
-    const Item it = list[x];
-    if (it.p > tp || (it.p == tp && (~it.key) >= tk)) {
-      const unsigned pos = atomicAdd(&s_count, 1u);
-      if (pos < K) out[pos] = it;
-    }
-  }
-}
-
-// ---- rank sort for short lists ---------------------------------------------
-// Item x lands at its rank: the number of items that come before it by
-// (p desc, key asc, position asc).  The position makes ranks a permutation
-// even for repeated keys; only the first K ranks are written.  The n^2
-// comparisons are split over blockIdx.y slices of the list, each slice adding
-// its count with one atomic per item, so a list of a few thousand items still
-// spreads over the whole GPU.
-constexpr unsigned kRankSortMax = 1u << 14;
-constexpr int kRankTile = 1024;
-
-__global__ void __launch_bounds__(256)
-k_rank_count(const Item* __restrict__ in, unsigned n, unsigned slice, unsigned* __restrict__ rank) {
-  __shared__ ulonglong2 sv[kRankTile];
-  const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned lo = blockIdx.y * slice;
-  const unsigned hi = min(n, lo + slice);
-  unsigned long long mp = 0, mk = 0;
-  if (x < n) {
-    mp = in[x].p;
-    mk = in[x].key;
-  }
-  unsigned cnt = 0;
-  for (unsigned base = lo; base < hi; base += kRankTile) {
-    const unsigned len = min((unsigned)kRankTile, hi - base);
-    __syncthreads();
-    for (unsigned q = threadIdx.x; q < len; q += blockDim.x)
-      sv[q] = make_ulonglong2(in[base + q].p, in[base + q].key);
-    __syncthreads();
-    if (x < n) {
-#pragma unroll 8
-      for (unsigned q = 0; q < len; ++q) {
-        const ulonglong2 o = sv[q];
-        const bool before = o.x > mp || (o.x == mp && (o.y < mk || (o.y == mk && base + q < x)));
-        cnt += before ? 1u : 0u;
+        cnt = half;
       }
     }
+    rank += lo;
   }
-  if (x < n && cnt) atomicAdd(&rank[x], cnt);
+  if (rank < K) out[rank] = me;
 }
 
-__global__ void __launch_bounds__(256)
-k_rank_scatter(const Item* __restrict__ in, unsigned n, unsigned K, const unsigned* __restrict__ rank,
-               Item* __restrict__ out) {
-  const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x < n) {
-    const unsigned r = rank[x];
-    if (r < K) out[r] = in[x];
+// Sorted top K of `in[0..n)` by tiles (n <= kTileSortMax).  Uses l1 and l2
+// of the workspace as scratch; `in` may be ws.out.
+void tile_select(mad_ctx* ctx, const SelectWs& ws, const Item* in, uint64_t n, uint64_t K,
+                 cudaStream_t st) {
+  const unsigned tiles = (unsigned)((n + kTile - 1) / kTile);
+  if (tiles == 1 && in != ws.out) {
+    k_tile_sort<<<1, kTile / 2, 0, st>>>(in, (unsigned)n, (unsigned)K, ws.out, nullptr);
+    count_launch(ctx);
+    return;
   }
+  uint32_t* pos = (uint32_t*)ws.l2;
+  k_tile_sort<<<tiles, kTile / 2, 0, st>>>(in, (unsigned)n, (unsigned)K, ws.l1, pos);
+  k_merge_rank<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws.l1, pos, (unsigned)n, (unsigned)K,
+                                                            ws.out);
+  count_launch(ctx, 2);
 }
 
 // ---- bitonic sort: "before" = (p desc, key asc) --------------------------
@@ -515,19 +519,15 @@ mad_status select_list(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K,
   *n_sel = take;
   if (take == 0) return MAD_OK;
   unsigned long long n2 = 0;
-  // Short lists are ranked whole (ranks >= K are dropped).  Longer ones
-  // first pick the K largest, unordered, into `sel`; those are then ranked
-  // when K is short, else sorted in place by a bitonic network.
-  const bool rank_sort = take <= kRankSortMax;
-  Item* sel = rank_sort ? ws.l2 : ws.out;
-  uint64_t nr = take;   // items ranked
-  if (take == n || n <= kRankSortMax) {
-    sel = ws.l0;
-    nr = n;
-    if (!rank_sort) cudaMemcpyAsync(ws.out, ws.l0, n * sizeof(Item), cudaMemcpyDeviceToDevice, st);
-  } else if (n <= kBlockSelectMax) {
-    k_select_block<<<1, 1024, 0, st>>>(ws.l0, (unsigned)n, (unsigned)K, dp, sel);
-    count_launch(ctx);
+  // Lists up to 2^17 items go straight to the tile sort.  Longer ones first
+  // pick the K largest, unordered, into ws.out (an MSB radix select), which
+  // the tile sort then orders when K is short, else a bitonic network.
+  if (n <= kTileSortMax) {
+    tile_select(ctx, ws, ws.l0, n, take, st);
+    return cuda_status(cudaGetLastError());
+  }
+  if (take == n) {
+    cudaMemcpyAsync(ws.out, ws.l0, n * sizeof(Item), cudaMemcpyDeviceToDevice, st);
   } else {
     SelState* dst = (SelState*)ws.state;
     cudaMemsetAsync(dst, 0, sizeof(SelState), st);
@@ -540,24 +540,12 @@ mad_status select_list(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K,
       k_radix_filter<<<blocks, 256, 0, st>>>(ws.l0, ws.l1, ws.l2, dst, q, dp, ws.cap_n);
       count_launch(ctx, 2);
     }
-    // The filter passes ping-pong through l1/l2; collect from l0 with the
-    // final digit state, so `sel` may reuse l2 once they are done.
     cudaMemsetAsync(ws.counter, 0, sizeof(unsigned long long), st);
-    k_collect<<<grid_for(n, 152 * 8), 256, 0, st>>>(ws.l0, n, dst, sel, ws.counter,
-                                                     rank_sort ? ws.cap_n : ws.cap_out);
+    k_collect<<<grid_for(n, 152 * 8), 256, 0, st>>>(ws.l0, n, dst, ws.out, ws.counter, ws.cap_out);
     count_launch(ctx);
   }
-  if (rank_sort) {
-    unsigned* rank = (unsigned*)ws.l1;
-    const unsigned nt = (unsigned)nr;
-    const unsigned nb = (nt + 255) / 256;
-    unsigned slices = std::min((152u * 8u + nb - 1) / nb, nb);
-    const unsigned slice = (nt + slices - 1) / slices;
-    slices = (nt + slice - 1) / slice;
-    cudaMemsetAsync(rank, 0, nt * sizeof(unsigned), st);
-    k_rank_count<<<dim3(nb, slices), 256, 0, st>>>(sel, nt, slice, rank);
-    k_rank_scatter<<<nb, 256, 0, st>>>(sel, nt, (unsigned)take, rank, ws.out);
-    count_launch(ctx, 2);
+  if (take <= kTileSortMax) {
+    tile_select(ctx, ws, ws.out, take, take, st);
     return cuda_status(cudaGetLastError());
   }
   bitonic_sort(ctx, ws.out, take, st, &n2);
