@@ -34,12 +34,18 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-top-t at recall>=0.95 vs dense GEMM+top-t on 1 GB300; diamonds/sec"
 SAMPLER_SOURCES = ["paper_1506_03872_gb300/csrc/sample.cu",
                    "paper_1506_03872_gb300/csrc/mad_device.cuh"]
-# Algorithmic DRAM bytes of one dense diamond: the final entry of each of the
-# four inverse-CDF searches (T1, T2, TB, TA), b_k'j, and the read-modify-write
-# of the hash key and value sectors; one 32-byte sector per touch.
-DENSE_SECTORS_READ = 5
-DENSE_SECTORS_RMW = 2
-DENSE_BYTES_PER_DIAMOND = 32 * DENSE_SECTORS_READ + 64 * DENSE_SECTORS_RMW
+# Algorithmic bytes per diamond of the dominant kernel, one 32-byte sector
+# per random touch.  Dense draw kernel (k_sample_sorted): the final entry of
+# each of the four inverse-CDF searches (T1, T2, TA, TB) and b_k'j, plus the
+# 8-byte sorted record read and the 16-byte (key, increment) record written.
+DENSE_DRAW_BYTES = 32 * 5 + 8 + 16
+# 0/1 draw kernel (k_sample, draws and inserts): final entries of the T1 and
+# T2 searches, row i's bounds, a_ik and a_ik' column indices, row k's bounds
+# and b_kj's index, the bounds of rows j and k', and the sector where the
+# closure search ends; the hash read-modify-write of closed diamonds is
+# added per inserted diamond (2 sectors read and written).
+SPARSE_DRAW_SECTORS = 10
+HASH_RMW_BYTES = 4 * 32
 
 
 def _peaks():
@@ -59,12 +65,14 @@ def _sources_sha():
     return h.hexdigest()[:16]
 
 
-def _traffic_record():
+def _traffic_record(kernel):
+    """DRAM bytes per diamond of `kernel` from an ncu capture, valid only
+    while the sampler sources are the ones it was taken with."""
     path = os.path.join(ROOT, "profiles", "sampler_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        if rec.get("source_sha") == _sources_sha():
+        if rec.get("source_sha") == _sources_sha() and rec.get("kernel") == kernel:
             return rec
     except Exception:
         pass
@@ -383,10 +391,17 @@ def run_ours(args):
     if dist: dist.barrier()
     torch.cuda.synchronize()
     timings = []
+    phase_events = []
     for _ in range(args.steps):
         flush.fill_(1.0)   # evict the 129 MB L2 between timed steps
+        pe = [ev() for _ in range(4)]
+        mad.mad_set_phase_events(ctx.ctx, pe)
+        phase_events.append(pe)
         step(Am, Bm, timings)
     torch.cuda.synchronize()
+    mad.mad_set_phase_events(ctx.ctx, [])
+    # sampling phases: row-order sort, draw kernel, hash insert
+    phase_kernels = [[pe[q].elapsed_time(pe[q + 1]) for q in range(3)] for pe in phase_events]
     if dist: dist.barrier()
     clk = clocks.stop() if clocks else None
     launches = mad.mad_stats(ctx.ctx)["launches"] - launches0
@@ -435,20 +450,29 @@ def run_ours(args):
     h2d = int(sum(h.numel() * h.element_size() for h in host_inputs))
     d2h = int(host_res.numel() * host_res.element_size())
 
-    # Roofline of the dominant kernel (the sampler): algorithmic bytes per
-    # launch over its event-timed duration on the launching stream.
+    # Roofline of the dominant kernel (the draw kernel): algorithmic bytes per
+    # launch over its duration, from events the library records around it on
+    # its own stream during the timed steps.
     sample_ms = float(phase[:, 1].mean())
+    phase_k = np.array(phase_kernels) if phase_kernels else None
     peak, peak_kind = _peaks()
     roof = None
-    if not w.csr:
-        alg_bytes = DENSE_BYTES_PER_DIAMOND * s
-        achieved = alg_bytes / (sample_ms / 1e3) / 1e9
-        rec = _traffic_record()
-        roof = {"bound": "hbm", "kernel": "k_sample", "achieved": round(achieved, 1),
+    if phase_k is not None:
+        draw_ms = float(phase_k[:, 1].mean())
+        if w.csr:
+            kern = "k_sample"
+            alg_bytes = 32 * SPARSE_DRAW_SECTORS * s + HASH_RMW_BYTES * int(stats["inserted"])
+        else:
+            kern = "k_sample_sorted"
+            alg_bytes = DENSE_DRAW_BYTES * s
+        achieved = alg_bytes / (draw_ms / 1e3) / 1e9
+        rec = _traffic_record(kern)
+        roof = {"bound": "hbm", "kernel": kern, "achieved": round(achieved, 1),
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
                 "traffic": (round(rec["bytes_per_diamond"] * s) if rec else None),
-                "algorithmic_bytes_per_launch": alg_bytes}
+                "algorithmic_bytes_per_launch": int(alg_bytes),
+                "kernel_ms": round(draw_ms, 4)}
 
     # The dense exact comparator (BF16 tensor-core GEMM + fused top filter +
     # FP32 rescore) on the same inputs, timed the same way.
@@ -505,6 +529,9 @@ def run_ours(args):
             "phases_ms": {k: round(float(phase[:, q].mean()), 4)
                           for q, k in enumerate(["build_tables", "sample", "topk", "rescore"])},
             "diamonds_per_s_sampler": round(s / (sample_ms / 1e3), 1),
+            "sample_kernels_ms": ({k: round(float(np.mean([pk[q] for pk in phase_kernels])), 4)
+                                   for q, k in enumerate(["row_order", "draws", "insert"])}
+                                  if phase_kernels else None),
             "recall_at_s": recall, "tau_t": tau, "count_mismatches": mismatch,
             "stats": {k: stats[k] for k in ("w1", "inserted", "distinct", "positive",
                                               "hash_capacity")},

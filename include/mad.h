@@ -135,6 +135,18 @@ typedef struct mad_ctx mad_ctx;
  * mad_build_tables calls of one shape do not map memory again. */
 mad_status mad_create(mad_ctx** ctx, uint32_t flags);
 
+/* Profiling aid (the paper has no counterpart).  From the next mad_sample
+ * on, record n caller-created CUDA events (cudaEvent_t handles, n <= 4) on
+ * the sampling stream at the phase boundaries of each batch of diamonds:
+ * events[0] before the batch; events[1] after the row-order sort (dense
+ * inputs; at the start for 0/1 inputs); events[2] after the draw kernel
+ * (k_sample_sorted, or k_sample, which also inserts, for 0/1 inputs);
+ * events[3] after the hash insert (k_insert; equal to events[2] for 0/1
+ * inputs).  With several batches the events mark the last one.  The handles
+ * must stay valid while set; n = 0 stops recording.  MAD_ERR_ARG for n > 4
+ * or a null array with n > 0. */
+mad_status mad_set_phase_events(mad_ctx* ctx, void* const* events, uint32_t n);
+
 /* Free everything the context owns, its memory pool included
  * (synchronises the device). */
 void mad_destroy(mad_ctx* ctx);

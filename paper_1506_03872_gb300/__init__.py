@@ -32,7 +32,7 @@ EXPORTS = (
     "mad_create", "mad_destroy", "mad_strerror", "mad_set_hash_capacity", "mad_build_tables",
     "mad_sample", "mad_reset_hash", "mad_topk", "mad_rescore", "mad_stats", "mad_debug_draws",
     "mad_debug_draws_list", "mad_export_x", "mad_export_table", "mad_rescore_noalloc",
-    "mad_dense_topt", "mad_debug_dense_product",
+    "mad_dense_topt", "mad_debug_dense_product", "mad_set_phase_events",
 )
 MAD_NOALLOC_MAX_CANDIDATES = 16384
 
@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
         L.mad_strerror.argtypes = [i32]
         L.mad_strerror.restype = ctypes.c_char_p
         L.mad_set_hash_capacity.argtypes = [P, u64]
+        L.mad_set_phase_events.argtypes = [P, ctypes.POINTER(P), u32]
         L.mad_build_tables.argtypes = [P, ctypes.POINTER(mad_matrix), ctypes.POINTER(mad_matrix),
                                        u64, P]
         L.mad_sample.argtypes = [P, u64, u64, u64, P]
@@ -163,6 +164,18 @@ def mad_destroy(ctx) -> None:
 
 def mad_set_hash_capacity(ctx, slots: int) -> None:
     _check(lib().mad_set_hash_capacity(ctx, slots), "mad_set_hash_capacity")
+
+
+def mad_set_phase_events(ctx, events) -> None:
+    """Record the given torch.cuda.Event objects at the sampling phase
+    boundaries of later mad_sample calls (see mad.h); [] stops."""
+    handles = []
+    for ev in events:
+        if not ev.cuda_event:
+            ev.record()   # torch creates the CUDA event lazily
+        handles.append(ev.cuda_event)
+    arr = (ctypes.c_void_p * max(1, len(handles)))(*handles)
+    _check(lib().mad_set_phase_events(ctx, arr, len(handles)), "mad_set_phase_events")
 
 
 def mad_build_tables(ctx, A: mad_matrix, B: mad_matrix, s_max: int, stream=None) -> None:

@@ -149,6 +149,13 @@ mad_status mad_create(mad_ctx** out, uint32_t flags) {
   return MAD_OK;
 }
 
+mad_status mad_set_phase_events(mad_ctx* ctx, void* const* events, uint32_t n) {
+  if (!ctx || n > 4 || (n && !events)) return MAD_ERR_ARG;
+  for (uint32_t q = 0; q < 4; ++q) ctx->phase_ev[q] = q < n ? (cudaEvent_t)events[q] : nullptr;
+  ctx->n_phase_ev = n;
+  return MAD_OK;
+}
+
 void mad_destroy(mad_ctx* ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();

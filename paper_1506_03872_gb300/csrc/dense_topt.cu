@@ -279,6 +279,20 @@ __device__ unsigned epi_compact(float* cv, unsigned long long* ck, unsigned n, f
   return out;
 }
 
+// Largest |value| of 64 FP32 bit patterns, with eight independent running
+// maxima so the dependent chain is 8 deep instead of 64.
+__device__ __forceinline__ float abs_max64(const uint32_t* r) {
+  float m[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) m[k] = fabsf(__uint_as_float(r[k]));
+#pragma unroll
+  for (int q = 8; q < 64; q += 8) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m[k] = fmaxf(m[k], fabsf(__uint_as_float(r[q + k])));
+  }
+  return fmaxf(fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3])), fmaxf(fmaxf(m[4], m[5]), fmaxf(m[6], m[7])));
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
 k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const GemmArgs args) {
@@ -444,9 +458,13 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           tmem_wait_ld();
           const int64_t rem = args.n - (col_half + ch * 64);
           const int nvalid = rem >= 64 ? 64 : (rem > 0 ? (int)rem : 0);
+          if (nvalid == 64) {
+            hm = fmaxf(hm, abs_max64(r));
+          } else {
 #pragma unroll
-          for (int q = 0; q < 64; ++q)
-            hm = fmaxf(hm, q < nvalid ? fabsf(__uint_as_float(r[q])) : 0.0f);
+            for (int q = 0; q < 64; ++q)
+              hm = fmaxf(hm, q < nvalid ? fabsf(__uint_as_float(r[q])) : 0.0f);
+          }
         }
         args.max_out[v * kEpi + et] = row < args.m ? hm : 0.0f;
       } else {
@@ -466,11 +484,17 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             const int64_t rem = args.n - col0;
             const int nvalid = rem >= 64 ? 64 : (rem > 0 ? (int)rem : 0);
             // Max first: the chunk is inspected element by element only when
-            // its largest valid |c~| reaches theta.
+            // its largest valid |c~| reaches theta.  nvalid is the same for
+            // every lane of the warp, and all 64 columns are valid except in
+            // the last column block.
             float mx = 0.0f;
+            if (nvalid == 64) {
+              mx = abs_max64(r);
+            } else {
 #pragma unroll
-            for (int q = 0; q < 64; ++q)
-              mx = fmaxf(mx, q < nvalid ? fabsf(__uint_as_float(r[q])) : 0.0f);
+              for (int q = 0; q < 64; ++q)
+                mx = fmaxf(mx, q < nvalid ? fabsf(__uint_as_float(r[q])) : 0.0f);
+            }
             unsigned cnt = 0;
             if (mx >= theta && row < args.m) {
 #pragma unroll

@@ -373,8 +373,12 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 // Linear probing from `slot`, wrapping at cap, four slots per round trip:
 // the keys of the 32-byte group holding `slot` are read with two 16-byte
 // loads, and the first slot of the group (from `slot` on) that is empty or
-// holds the key is claimed with one CAS.  Returns 0 when the probe limit is
-// hit, 1 when the key existed, 2 when this call created it.
+// holds the key is picked without branching (lanes of a warp stay
+// converged).  A key already there gets the value added; an empty slot is
+// claimed with one CAS, and a CAS lost to another key re-reads the group
+// from that slot, so slots are still taken in linear-probing order.
+// Returns 0 when the probe limit is hit, 1 when the key existed, 2 when
+// this call created it.
 __device__ __forceinline__ int hash_add_from(unsigned long long* __restrict__ keys,
                                              long long* __restrict__ vals, uint64_t cap,
                                              uint64_t slot, uint32_t max_probe,
@@ -397,26 +401,34 @@ __device__ __forceinline__ int hash_add_from(unsigned long long* __restrict__ ke
       for (uint32_t q = 0; q < 4; ++q) k4[q] = (q < valid) ? __ldcg(keys + g + q) : 0ull;
     }
     const uint32_t start = (uint32_t)(slot - g);
+    uint32_t pick = 4;
 #pragma unroll
-    for (uint32_t q = 0; q < 4; ++q) {
-      if (q < start || q >= valid) continue;
-      ++probes;
-      const unsigned long long cur = k4[q];
-      if (cur == key) {
-        atomicAdd((unsigned long long*)vals + g + q, (unsigned long long)v);
-        return 1;
-      }
-      if (cur == EMPTY_KEY) {
-        const unsigned long long prev = atomicCAS(keys + g + q, EMPTY_KEY, key);
-        if (prev == EMPTY_KEY || prev == key) {
-          atomicAdd((unsigned long long*)vals + g + q, (unsigned long long)v);
-          return prev == EMPTY_KEY ? 2 : 1;
-        }
-        // another key took the slot: look at the rest of the group
-      }
+    for (int q = 3; q >= 0; --q) {
+      const bool usable = (uint32_t)q >= start && (uint32_t)q < valid &&
+                          (k4[q] == key || k4[q] == EMPTY_KEY);
+      pick = usable ? (uint32_t)q : pick;
     }
-    slot = g + 4;
-    if (slot >= cap) slot = 0;
+    if (pick == 4) {
+      probes += valid > start ? valid - start : 0u;
+      slot = g + 4;
+      if (slot >= cap) slot = 0;
+      continue;
+    }
+    probes += pick - start + 1;
+    unsigned long long cur = k4[0];
+#pragma unroll
+    for (uint32_t q = 1; q < 4; ++q) cur = (q == pick) ? k4[q] : cur;
+    int created = 0;
+    if (cur != key) {
+      const unsigned long long prev = atomicCAS(keys + g + pick, EMPTY_KEY, key);
+      if (prev != EMPTY_KEY && prev != key) {
+        slot = g + pick;  // taken by another key: look again from here
+        continue;
+      }
+      created = prev == EMPTY_KEY ? 2 : 0;
+    }
+    atomicAdd((unsigned long long*)vals + g + pick, (unsigned long long)v);
+    return created ? 2 : 1;
   }
   return 0;
 }

@@ -108,6 +108,9 @@ struct mad_ctx {
   // it keeps freed memory mapped, so rebuilding tables of the same shape
   // re-uses pages instead of mapping them again.
   cudaMemPool_t pool = nullptr;
+  // Caller events recorded at the sampling phase boundaries (profiling).
+  cudaEvent_t phase_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  uint32_t n_phase_ev = 0;
   bool built = false;
   bool integer = false;
   bool dense = false;

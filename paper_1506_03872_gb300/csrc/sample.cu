@@ -291,17 +291,24 @@ k_insert(const SampleParams p, const unsigned long long* __restrict__ keys,
          const long long* __restrict__ vals, unsigned long long s) {
   Tally t;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned long long rounds = (s + stride - 1) / stride;
+  // The next entry is loaded before the current one is inserted.
+  unsigned long long key = q < s ? __ldcs(keys + q) : EMPTY_KEY;
+  long long v = q < s ? __ldcs(vals + q) : 0;
   for (unsigned long long r = 0; r < rounds; ++r) {
-    const unsigned long long q = base + r * stride;
-    const unsigned long long key = q < s ? __ldcs(keys + q) : EMPTY_KEY;
+    const unsigned long long qn = q + stride;
+    const unsigned long long key_n = qn < s ? __ldcs(keys + qn) : EMPTY_KEY;
+    const long long v_n = qn < s ? __ldcs(vals + qn) : 0;
     if (key != EMPTY_KEY) {
       ++t.inserted;
-      const int res = hash_add(p, key, __ldcs(vals + q));
+      const int res = hash_add(p, key, v);
       if (res == 0) t.full = true;
       if (res == 2) ++t.created;
     }
+    key = key_n;
+    v = v_n;
+    q = qn;
   }
   flush_tally(p, t);
 }
@@ -344,6 +351,11 @@ unsigned grid_of(unsigned long long work, int full) {
 
 // Diamonds per sorted batch (bounds the scratch at 16 bytes per diamond).
 constexpr unsigned long long kSortBatch = 1ull << 26;
+
+// Caller's profiling event q (if set) on the sampling stream.
+void phase_event(const mad_ctx* ctx, uint32_t q, cudaStream_t st) {
+  if (q < ctx->n_phase_ev && ctx->phase_ev[q]) cudaEventRecord(ctx->phase_ev[q], st);
+}
 
 }  // namespace
 
@@ -395,8 +407,12 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
   const SampleParams p = make_params(ctx);
   const size_t smem_t1c = (size_t)p.t1c_n * sizeof(uint64_t);
   if (!ctx->dense) {
+    phase_event(ctx, 0, st);
+    phase_event(ctx, 1, st);
     k_sample<<<grid_of(s, full_grid(k_sample, smem_t1c)), 256, smem_t1c, st>>>(p, seed, first, s);
     count_launch(ctx);
+    phase_event(ctx, 2, st);
+    phase_event(ctx, 3, st);
     return cuda_status(cudaGetLastError());
   }
   const size_t smem_tbc = (size_t)(p.d * p.tbc_n) * sizeof(uint32_t);
@@ -429,15 +445,19 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
   unsigned long long* sorted = rec + batch;
   for (uint64_t done = 0; done < s; done += batch) {
     const uint64_t n = (s - done) < batch ? (s - done) : batch;
+    phase_event(ctx, 0, st);
     cudaMemsetAsync(cnt, 0, nbk * sizeof(uint32_t), st);
     k_bucket_count<<<grid_of(n, full_count), 256, 0, st>>>(ctx->t1_total, shift, seed,
                                                            first + done, n, cnt, rec);
     count_launch(ctx);
     if ((rs = scan_exclusive_u32(ctx, cnt, off, nbk, part, st)) != MAD_OK) return rs;
     k_bucket_scatter<<<grid_of(n, full_count), 256, 0, st>>>(rec, off, n, sorted);
+    phase_event(ctx, 1, st);
     k_sample_sorted<<<grid_of(n, full_sorted), 256, smem_tbc, st>>>(p, seed, first + done, n,
                                                                     sorted, rec);
+    phase_event(ctx, 2, st);
     k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, rec, (const long long*)sorted, n);
+    phase_event(ctx, 3, st);
     count_launch(ctx, 3);
   }
   return cuda_status(cudaGetLastError());

@@ -92,3 +92,25 @@ def test_unsupported_mixed_formats():
         with pytest.raises(mad.MadError) as e:
             mad.mad_build_tables(c.ctx, mad.dense(A), mad.csr(rowptr, colidx, (10, 300)), 100)
         assert e.value.status == mad.MAD_ERR_UNSUPPORTED
+
+
+def test_phase_events_bracket_the_sampling_kernels():
+    import paper_1506_03872_gb300 as mad
+    A, B = _dense_inputs(m=2000, d=20, n=3000)
+    with mad.Context() as c:
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_set_phase_events(c.ctx, [torch.cuda.Event(enable_timing=True) for _ in range(5)])
+        assert e.value.status == mad.MAD_ERR_ARG
+        mad.mad_build_tables(c.ctx, mad.dense(A), mad.dense(B), 200000)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        outer = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        mad.mad_set_phase_events(c.ctx, ev)
+        outer[0].record()
+        mad.mad_sample(c.ctx, 200000, 7)
+        outer[1].record()
+        mad.mad_set_phase_events(c.ctx, [])
+        torch.cuda.synchronize()
+        parts = [ev[q].elapsed_time(ev[q + 1]) for q in range(3)]
+        assert all(p >= 0.0 for p in parts)
+        assert sum(parts) <= outer[0].elapsed_time(outer[1]) + 1e-3
+        assert mad.mad_stats(c.ctx)["inserted"] > 0
