@@ -423,6 +423,9 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
         epi_sync();
       }
+      // The shared threshold is read before the wait so its latency overlaps it
+      // (any earlier value is a valid, lower bound).
+      const float g_theta0 = __uint_as_float(*((volatile unsigned int*)args.g_theta));
       // The epilogue warps share named barriers below, so they leave together.
       const bool ok = mbar_wait(&sh->acc_full[buf], (uint32_t)((it >> 1) & 1), abort_flag);
       if (!ok) atomicOr(&sh->epi_abort, 1);
@@ -471,7 +474,8 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         unsigned tile_start = sh->count;
         for (int round = 0; round < 8; ++round) {
           const float theta =
-              fmaxf(sh->theta, __uint_as_float(*((volatile unsigned int*)args.g_theta)));
+              fmaxf(sh->theta, round == 0 ? g_theta0
+                                          : __uint_as_float(*((volatile unsigned int*)args.g_theta)));
           // Two chunks of 64 columns, reloaded from TMEM on every pass (the
           // accumulator stays put until this tile's buffer is released).
 #pragma unroll 1

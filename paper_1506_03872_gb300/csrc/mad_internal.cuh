@@ -172,6 +172,9 @@ mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st);
 mad_status build_hash_regions(mad_ctx* ctx, cudaStream_t st);
 uint64_t hash_region_bound(uint64_t m, uint64_t s_max);
 // sample.cu
+// Diamonds among the first n of a fixed pilot seed that would add to X
+// (closed, nonzero, off-diagonal when excluded); synchronises.
+mad_status pilot_inserts(mad_ctx* ctx, uint64_t n, uint64_t* hits, cudaStream_t st);
 mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first,
                        cudaStream_t st);
 mad_status debug_draws_impl(mad_ctx* ctx, uint64_t seed, uint64_t first, const uint64_t* ells,

@@ -352,6 +352,23 @@ unsigned grid_of(unsigned long long work, int full) {
 // Diamonds per sorted batch (bounds the scratch at 16 bytes per diamond).
 constexpr unsigned long long kSortBatch = 1ull << 26;
 
+// Pilot for hash sizing: counts the diamonds that would be inserted.
+__global__ void __launch_bounds__(256)
+k_pilot(const SampleParams p, unsigned long long seed, unsigned long long n,
+        unsigned long long* __restrict__ hits) {
+  bool bad = false;
+  unsigned long long c = 0;
+  for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (unsigned long long)gridDim.x * blockDim.x) {
+    const Draw dr = draw_one(p, seed, q, &bad);
+    c += (dr.v != 0 && !((p.flags & MAD_EXCLUDE_DIAG) && dr.i == dr.j)) ? 1 : 0;
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, off);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(hits, c);
+  if (bad) atomicOr(&p.sc->err, DERR_SEARCH);
+}
+
 // Caller's profiling event q (if set) on the sampling stream.
 void phase_event(const mad_ctx* ctx, uint32_t q, cudaStream_t st) {
   if (q < ctx->n_phase_ev && ctx->phase_ev[q]) cudaEventRecord(ctx->phase_ev[q], st);
@@ -400,6 +417,22 @@ SampleParams make_params(const mad_ctx* ctx) {
   p.flags = ctx->flags;
   p.sc = ctx->sc;
   return p;
+}
+
+mad_status pilot_inserts(mad_ctx* ctx, uint64_t n, uint64_t* hits, cudaStream_t st) {
+  mad_status rs = ensure_scratch(ctx, 256, st);
+  if (rs != MAD_OK) return rs;
+  unsigned long long* dev = (unsigned long long*)ctx->scratch;
+  cudaMemsetAsync(dev, 0, sizeof(unsigned long long), st);
+  const SampleParams p = make_params(ctx);
+  k_pilot<<<grid_of(n, full_grid(k_pilot)), 256, 0, st>>>(p, 0x9E3779B97F4A7C15ull, n, dev);
+  count_launch(ctx);
+  unsigned long long h = 0;
+  cudaMemcpyAsync(&h, dev, sizeof(h), cudaMemcpyDeviceToHost, st);
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  *hits = h;
+  return MAD_OK;
 }
 
 mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, cudaStream_t st) {
