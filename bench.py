@@ -39,12 +39,13 @@ SAMPLER_SOURCES = ["paper_1506_03872_gb300/csrc/sample.cu",
 # each of the four inverse-CDF searches (T1, T2, TA, TB) and b_k'j, plus the
 # 8-byte sorted record read and the 16-byte (key, increment) record written.
 DENSE_DRAW_BYTES = 32 * 5 + 8 + 16
-# 0/1 draw kernel (k_sample, draws and inserts): final entries of the T1 and
-# T2 searches, row i's bounds, a_ik and a_ik' column indices, row k's bounds
-# and b_kj's index, the bounds of rows j and k', and the sector where the
-# closure search ends; the hash read-modify-write of closed diamonds is
-# added per inserted diamond (2 sectors read and written).
-SPARSE_DRAW_SECTORS = 10
+# 0/1 draw kernel (k_sample, draws and inserts): the final entry of the T1
+# search, row i's bounds, the T2 guide entries and the T2 window, the column
+# indices of k and k', row k's bounds, b_kj's index and the closure filter's
+# word (the exact closure search of the ~1 % of diamonds the filter passes
+# is left out); the hash read-modify-write of closed diamonds is added per
+# inserted diamond (2 sectors read and written).
+SPARSE_DRAW_SECTORS = 9
 HASH_RMW_BYTES = 4 * 32
 
 
@@ -183,6 +184,7 @@ def _ground_truth_dense(A, B, t):
     order = torch.argsort(-exact, stable=True)[:t]
     keys = (cand[order, 0].to(torch.int64) << 32) | cand[order, 1].to(torch.int64)
     tau = exact[order[-1]].item()
+    _ground_truth_dense.top1 = exact[order[0]].item()
     return set(keys.cpu().tolist()), tau
 
 
@@ -248,6 +250,7 @@ def ground_truth_gram_binary(rowptr, colidx, t, device, h0=2048):
         v[inside] = Cc[pi[inside], pj[inside]].double()
         return v.cpu().numpy()
 
+    counts.top1 = float(vals.max().item()) if vals.numel() else 0.0
     return tau, counts
 
 
@@ -419,11 +422,14 @@ def run_ours(args):
     truth = set()
     counts = None
     mismatch = None
+    top1 = None
     if rank == 0 and not args.no_recall:
         if w.csr:
             tau, counts = ground_truth_gram_binary(w.rowptr, w.colidx, t, dev)
+            top1 = counts.top1
         else:
             truth, tau = _ground_truth_dense(tensors[0], tensors[1], t)
+            top1 = _ground_truth_dense.top1
         recall, mismatch = recall_of(w, gi, gj, gc, truth, tau, counts)
     stats = mad.mad_stats(ctx.ctx)
 
@@ -533,6 +539,9 @@ def run_ours(args):
                                    for q, k in enumerate(["row_order", "draws", "insert"])}
                                   if phase_kernels else None),
             "recall_at_s": recall, "tau_t": tau, "count_mismatches": mismatch,
+            # Theorem 2's sample estimate for the top entry, ||W||_1 / max c^2
+            # (the paper's "est. samples" statistic).
+            "est_samples_top1": (round(stats["w1"] / top1 ** 2, 1) if top1 else None),
             "stats": {k: stats[k] for k in ("w1", "inserted", "distinct", "positive",
                                               "hash_capacity")},
             "e2e": {"value": round(world * s * args.steps / (e2e_total / 1e3), 1),

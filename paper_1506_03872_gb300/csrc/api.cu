@@ -67,6 +67,10 @@ void free_tables(mad_ctx* ctx, cudaStream_t st) {
   free_async(ctx->TBc, st);
   free_async(ctx->T1c2, st);
   free_async(ctx->TBc2, st);
+  free_async(ctx->T2g_ptr, st);
+  free_async(ctx->T2g, st);
+  free_async(ctx->T2g_sh, st);
+  free_async(ctx->bloom, st);
   ctx->built = false;
   ctx->regioned = false;
 }
@@ -294,6 +298,21 @@ mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   if (hs.err & DERR_OVERFLOW) return MAD_ERR_OVERFLOW;
   if (ctx->integer) {
     if (hs.t1_total == 0) return MAD_ERR_EMPTY;
+    // Guides of the long T2 rows (the 0/1 sampler's k search).
+    if ((rs = alloc(ctx, ctx->T2g_ptr, (size_t)ctx->m + 1, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->T2g_sh, (size_t)ctx->m, st)) != MAD_OK) return rs;
+    if ((rs = t2_guide_offsets(ctx, st)) != MAD_OK) return rs;
+    unsigned long long gtotal = 0;
+    cudaMemcpyAsync(&gtotal, ctx->T2g_ptr + ctx->m, sizeof(gtotal), cudaMemcpyDeviceToHost, st);
+    if ((rs = cuda_status(cudaStreamSynchronize(st))) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->T2g, (size_t)gtotal, st)) != MAD_OK) return rs;
+    if (gtotal && (rs = t2_guide_fill(ctx, st)) != MAD_OK) return rs;
+    // Closure filter: 16 bits per entry, a power of two of 64-bit words.
+    const uint64_t nnz_c = (ctx->flags & MAD_GRAM) ? ctx->nnz_a : ctx->nnz_b;
+    ctx->bloom_lg = 10;
+    while (((1ull << ctx->bloom_lg) * 4ull) < nnz_c && ctx->bloom_lg < 40) ++ctx->bloom_lg;
+    if ((rs = alloc(ctx, ctx->bloom, (size_t)1 << ctx->bloom_lg, st)) != MAD_OK) return rs;
+    if ((rs = build_bloom(ctx, st)) != MAD_OK) return rs;
     ctx->f = 0;
     ctx->e1 = 0;
   } else {

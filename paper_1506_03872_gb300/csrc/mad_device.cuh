@@ -106,6 +106,28 @@ __device__ __forceinline__ int ub_u32(const uint32_t* __restrict__ P, int len, u
   return pos;
 }
 
+// Upper bound in a long row through its guide: bucket b = target >> sh
+// holds the answer between guide entries b and b + 1, and the prefix
+// entries between those positions are counted (one window of 16 in the
+// common case, else a binary search over the bucket's range).  Same result
+// as ub_u32 over the whole row.
+__device__ __forceinline__ int ub_guided_u32(const uint32_t* __restrict__ P,
+                                             const uint32_t* __restrict__ G, int sh,
+                                             uint32_t target) {
+  const uint32_t b = target >> sh;
+  const int lo = (int)__ldg(G + b), hi = (int)__ldg(G + b + 1);
+  if (hi - lo <= 16) {
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int e = lo + q;
+      if (e < hi) cnt += (__ldg(P + e) <= target) ? 1 : 0;
+    }
+    return lo + cnt;
+  }
+  return lo + ub_u32(P + lo, hi - lo, target, 0xFFFFFFFFu);
+}
+
 // Two searches over rows of the same length at once (independent loads).
 __device__ __forceinline__ void ub2_u32(const uint32_t* __restrict__ P, const uint32_t* __restrict__ Q,
                                         int len, uint32_t tp, uint32_t tq, uint32_t mask, int* op,
@@ -431,6 +453,23 @@ __device__ __forceinline__ int hash_add_from(unsigned long long* __restrict__ ke
     return created ? 2 : 1;
   }
   return 0;
+}
+
+// Bloom filter for the 0/1 closure test: a key sets five bits (five 6-bit
+// fields of a second mix of its hash) in one 64-bit word (the top bits of
+// its hash).  A clear bit proves the entry absent; a set filter sends the
+// test to the exact search.
+__device__ __forceinline__ unsigned long long bloom_bits(unsigned long long h) {
+  const unsigned long long g = mix64(h ^ 0xA0761D6478BD642Full);
+  return (1ull << (g & 63)) | (1ull << ((g >> 6) & 63)) | (1ull << ((g >> 12) & 63)) |
+         (1ull << ((g >> 18) & 63)) | (1ull << ((g >> 24) & 63));
+}
+
+__device__ __forceinline__ bool bloom_may_contain(const unsigned long long* __restrict__ words,
+                                                  int shift, unsigned long long key) {
+  const unsigned long long h = mix64(key);
+  const unsigned long long m = bloom_bits(h);
+  return (__ldg(words + (h >> shift)) & m) == m;
 }
 
 // First slot probed for key = (a << 32) | b.

@@ -69,6 +69,16 @@ struct SampleParams {
   // blocks with all-ones entries).
   const uint64_t* T1c2;
   const uint32_t* TBc2;
+  // Guides of the long 0/1 T2 rows (null when absent): row i's guide is
+  // T2g[T2g_ptr[i] .. T2g_ptr[i+1]) with bucket width 2^T2g_sh[i]; entry b
+  // counts the row's prefix entries below b << T2g_sh[i].
+  const unsigned long long* T2g_ptr;
+  const uint32_t* T2g;
+  const uint8_t* T2g_sh;
+  // Bloom filter over the entries the 0/1 closure test looks up (null when
+  // absent): word mix64(key) >> bloom_shift holds five bits of each key.
+  const unsigned long long* bloom;
+  int bloom_shift;
   int f_exp;                       // F
   // Hash.  Regioned (dense inputs): the key (a, b) starts probing in the
   // home region of row a, [hreg[a], hreg[a+1]), sized from row a's expected
@@ -133,6 +143,11 @@ struct mad_ctx {
   uint32_t* TBc = nullptr;          // coarse index of each TB row (dense)
   uint64_t* T1c2 = nullptr;         // second-level indices
   uint32_t* TBc2 = nullptr;
+  unsigned long long* T2g_ptr = nullptr;  // guides of long 0/1 T2 rows
+  uint32_t* T2g = nullptr;
+  uint8_t* T2g_sh = nullptr;
+  unsigned long long* bloom = nullptr;    // closure-test filter (0/1 inputs)
+  int bloom_lg = 0;
   int64_t t1c_n = 0, tbc_n = 0;
   int t1c_lg = 0, tbc_lg = 0;
   void* bt = nullptr;               // dense B^T (n x d), the input dtype
@@ -167,6 +182,16 @@ mad_status scan_exclusive_u32(mad_ctx* ctx, const uint32_t* in, uint32_t* out, u
 mad_status scan_exclusive_u64(mad_ctx* ctx, const uint64_t* in, uint64_t* out, uint64_t n,
                               uint64_t* partial, cudaStream_t st);
 // tables.cu
+// Guides of the 0/1 T2 rows of at least kGuideMin entries (integer mode):
+// sizes, shifts and offsets into ctx->T2g_ptr / T2g_sh (allocated by the
+// caller, m + 1 and m entries; the total lands in T2g_ptr[m]), then the
+// entries into ctx->T2g.
+constexpr int kGuideMin = 64;
+mad_status t2_guide_offsets(mad_ctx* ctx, cudaStream_t st);
+// Bloom filter of the entries of the matrix the closure test reads (A under
+// MAD_GRAM, else B) into ctx->bloom (2^bloom_lg words, cleared here).
+mad_status build_bloom(mad_ctx* ctx, cudaStream_t st);
+mad_status t2_guide_fill(mad_ctx* ctx, cudaStream_t st);
 mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st);
 // Home regions of the dense hash: sizes from T1 and s_max, then offsets.
 mad_status build_hash_regions(mad_ctx* ctx, cudaStream_t st);

@@ -59,7 +59,12 @@ __device__ __forceinline__ Draw draw_given_row(const SampleParams& p, const Unif
   uint32_t e_k, e_kp = 0;
   if (p.integer) {
     const uint32_t t2tot = __ldg(p.T2 + a0 + alen - 1);
-    pk = ub_u32(p.T2 + a0, (int)alen, (uint32_t)draw_target(u.u1, t2tot), mask);
+    const uint32_t target = (uint32_t)draw_target(u.u1, t2tot);
+    if (p.T2g && alen >= kGuideMin) {
+      pk = ub_guided_u32(p.T2 + a0, p.T2g + __ldg(p.T2g_ptr + i), (int)__ldg(p.T2g_sh + i), target);
+    } else {
+      pk = ub_u32(p.T2 + a0, (int)alen, target, mask);
+    }
     pkp = (int64_t)draw_target(u.u3, (unsigned long long)alen);
   } else {
     const uint32_t t2tot = __ldg(p.T2 + a0 + alen - 1) & mask;
@@ -105,14 +110,22 @@ __device__ __forceinline__ Draw draw_given_row(const SampleParams& p, const Unif
   // Increment.
   long long v;
   if (p.integer) {
-    const int64_t c0 = __ldg(p.b_ptr + kp), clen = __ldg(p.b_ptr + kp + 1) - c0;
-    bool hit;
-    if (p.flags & MAD_GRAM) {
+    // b_k'j != 0: the entry (j, k') of A under MAD_GRAM, else (k', j) of B.
+    // The filter settles most tests with one load; the rest search rows.
+    const unsigned long long ekey = (p.flags & MAD_GRAM)
+                                        ? (((unsigned long long)j << 32) | (unsigned long long)kp)
+                                        : (((unsigned long long)kp << 32) | (unsigned long long)j);
+    bool hit = false;
+    if (p.bloom && !bloom_may_contain(p.bloom, p.bloom_shift, ekey)) {
+      hit = false;
+    } else if (p.flags & MAD_GRAM) {
+      const int64_t c0 = __ldg(p.b_ptr + kp), clen = __ldg(p.b_ptr + kp + 1) - c0;
       // B = A^T: b_k'j = a_jk'; search the shorter of the two sorted rows.
       const int64_t r0 = __ldg(p.a_ptr + j), rlen = __ldg(p.a_ptr + j + 1) - r0;
       hit = (rlen < clen) ? contains_sorted(p.a_col + r0, rlen, (int32_t)kp)
                           : contains_sorted(p.b_col + c0, clen, (int32_t)j);
     } else {
+      const int64_t c0 = __ldg(p.b_ptr + kp), clen = __ldg(p.b_ptr + kp + 1) - c0;
       hit = contains_sorted(p.b_col + c0, clen, (int32_t)j);
     }
     v = hit ? 1 : 0;
@@ -402,6 +415,11 @@ SampleParams make_params(const mad_ctx* ctx) {
   p.tbc_lg = ctx->tbc_lg;
   p.T1c2 = ctx->T1c2;
   p.TBc2 = ctx->TBc2;
+  p.T2g_ptr = ctx->T2g_ptr;
+  p.T2g = ctx->T2g;
+  p.T2g_sh = ctx->T2g_sh;
+  p.bloom = ctx->bloom;
+  p.bloom_shift = 64 - ctx->bloom_lg;
   p.f_exp = ctx->f;
   p.hkeys = ctx->hkeys;
   p.hvals = ctx->hvals;

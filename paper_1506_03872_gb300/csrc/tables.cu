@@ -279,6 +279,59 @@ k_a_rows_binary(const int64_t* __restrict__ a_ptr, const int32_t* __restrict__ a
 }
 
 // ---------------------------------------------------------------------------
+// Guides of long 0/1 T2 rows.  Row i (L >= kGuideMin entries, total tot)
+// gets buckets of width 2^sh, sh the smallest shift leaving at most about
+// L/4 buckets, and nb + 1 guide entries: entry b is the number of the row's
+// prefix entries below b << sh, so the first entry above a target t lies
+// between guide entries t >> sh and (t >> sh) + 1.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int bitlen_u32(uint32_t x) { return x ? 32 - __clz(x) : 0; }
+
+__global__ void __launch_bounds__(256)
+k_guide_sizes(const int64_t* __restrict__ a_ptr, const uint32_t* __restrict__ T2, int64_t m,
+              unsigned long long* __restrict__ sizes, uint8_t* __restrict__ shift) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a0 = a_ptr[i], len = a_ptr[i + 1] - a0;
+    unsigned long long size = 0;
+    int sh = 0;
+    if (len >= kGuideMin) {
+      const uint32_t tot = T2[a0 + len - 1];
+      if (tot > 0) {
+        const int want = bitlen_u32((uint32_t)(len / 8));
+        sh = bitlen_u32(tot - 1) - want;
+        if (sh < 0) sh = 0;
+        size = (unsigned long long)((tot - 1) >> sh) + 2;   // nb + 1
+      }
+    }
+    sizes[i] = size;
+    shift[i] = (uint8_t)sh;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_guide_fill(const int64_t* __restrict__ a_ptr, const uint32_t* __restrict__ T2, int64_t m,
+             const unsigned long long* __restrict__ gptr, const uint8_t* __restrict__ shift,
+             uint32_t* __restrict__ G) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += warps) {
+    const unsigned long long g0 = gptr[i], n = gptr[i + 1] - g0;
+    if (n == 0) continue;
+    const int64_t a0 = a_ptr[i], len = a_ptr[i + 1] - a0;
+    const int sh = shift[i];
+    for (unsigned long long b = lane; b < n; b += 32) {
+      const unsigned long long thr = b << sh;   // count the entries below thr
+      uint32_t cnt;
+      if (thr == 0) cnt = 0;
+      else if (thr > 0xFFFFFFFFull) cnt = (uint32_t)len;
+      else cnt = (uint32_t)ub_u32(T2 + a0, (int)len, (uint32_t)(thr - 1), 0xFFFFFFFFu);
+      G[g0 + b] = cnt;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // T1: scale exponent, per-chunk sums, chunk offsets, inclusive prefix.
 // ---------------------------------------------------------------------------
 constexpr int T1_CHUNK = 2048;  // 256 threads x 8 elements
@@ -483,6 +536,59 @@ void launch_transpose(mad_ctx* ctx, cudaStream_t st) {
 }  // namespace
 
 uint64_t hash_region_bound(uint64_t m, uint64_t s_max) { return m + 3 * s_max + 1; }
+
+mad_status t2_guide_offsets(mad_ctx* ctx, cudaStream_t st) {
+  const uint64_t m = (uint64_t)ctx->m;
+  const size_t sizes_bytes = (m * sizeof(unsigned long long) + 255) & ~(size_t)255;
+  mad_status rs = ensure_scratch(ctx, sizes_bytes + scan_partial_elems(m) * 8, st);
+  if (rs != MAD_OK) return rs;
+  unsigned long long* sizes = (unsigned long long*)ctx->scratch;
+  uint64_t* part = (uint64_t*)((char*)ctx->scratch + sizes_bytes);
+  const unsigned blocks = (unsigned)((m + 255) / 256 < 152 * 8 ? (m + 255) / 256 : 152 * 8);
+  k_guide_sizes<<<blocks, 256, 0, st>>>(ctx->A.rowptr, ctx->T2, ctx->m, sizes, ctx->T2g_sh);
+  count_launch(ctx);
+  return scan_exclusive_u64(ctx, (const uint64_t*)sizes, (uint64_t*)ctx->T2g_ptr, m, part, st);
+}
+
+// One warp per row of the closure matrix; every entry (row, col) sets its
+// five bits.
+__global__ void __launch_bounds__(256)
+k_bloom_build(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col, int64_t rows,
+              int shift, unsigned long long* __restrict__ words) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+    const int64_t e0 = ptr[r], e1 = ptr[r + 1];
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+      const unsigned long long key = ((unsigned long long)r << 32) | (uint32_t)col[e];
+      const unsigned long long h = mix64(key);
+      atomicOr(words + (h >> shift), bloom_bits(h));
+    }
+  }
+}
+
+mad_status build_bloom(mad_ctx* ctx, cudaStream_t st) {
+  const bool gram = (ctx->flags & MAD_GRAM) != 0;
+  const int64_t* ptr = gram ? ctx->A.rowptr : ctx->B.rowptr;
+  const int32_t* col = gram ? ctx->A.colidx : ctx->B.colidx;
+  const int64_t rows = gram ? ctx->m : ctx->d;
+  cudaMemsetAsync(ctx->bloom, 0, (sizeof(unsigned long long) << ctx->bloom_lg), st);
+  const int64_t blocks64 = (rows + 7) / 8;
+  const unsigned blocks = (unsigned)(blocks64 < 152 * 16 ? blocks64 : 152 * 16);
+  k_bloom_build<<<blocks, 256, 0, st>>>(ptr, col, rows, 64 - ctx->bloom_lg, ctx->bloom);
+  count_launch(ctx);
+  return cuda_status(cudaGetLastError());
+}
+
+mad_status t2_guide_fill(mad_ctx* ctx, cudaStream_t st) {
+  const int64_t warps_needed = ctx->m;
+  const int64_t blocks64 = (warps_needed + 7) / 8;
+  const unsigned blocks = (unsigned)(blocks64 < 152 * 16 ? blocks64 : 152 * 16);
+  k_guide_fill<<<blocks, 256, 0, st>>>(ctx->A.rowptr, ctx->T2, ctx->m, ctx->T2g_ptr, ctx->T2g_sh,
+                                       ctx->T2g);
+  count_launch(ctx);
+  return cuda_status(cudaGetLastError());
+}
 
 mad_status build_hash_regions(mad_ctx* ctx, cudaStream_t st) {
   const uint64_t m = (uint64_t)ctx->m;
