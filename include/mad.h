@@ -213,6 +213,40 @@ mad_status mad_dense_topt(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B
                           uint32_t rescore, mad_pair* out_dev, uint32_t* n_out_host,
                           mad_stream stream);
 
+/* ---- Batched queries (maximum |inner product| search) ----------------- *
+ * Many small instances against one item matrix: query q is the instance
+ * A = Q[q] (1 x d) with B = the items (d x n), sampled with its own budget
+ * s_q and seed + q.  Because m = 1, the stage-1 draw of Alg. 2 always gives
+ * the query's row, so diamond l of query q draws only k, j and k' (Philox
+ * key seed + q, counter l, as in mad_sample); its x accumulates in a hash
+ * region of its own, and Alg. 3 runs per query: the t' largest positive x
+ * by (x desc, j asc), their exact c = q . b_j (FP64, rescoring order of
+ * mad_rescore), the t largest |c| by (|c| desc, j asc).  Each query's result
+ * equals mad_build_tables + mad_sample + mad_topk + mad_rescore on that
+ * query alone with the same s_max.
+ *
+ * mad_mips_items: item-side tables (TB with per-row guides, row norms, the
+ * items transposed for rescoring) for dense B (d x n, F32, n < 2^31).  B
+ * must stay alive and unchanged while the context uses it.  s_max bounds
+ * every query budget (it fixes the fixed-point scale F).  Synchronises.
+ *
+ * mad_mips_plan: the batch shape: nq queries with budgets s_host[q] (host,
+ * 1 <= s_q <= s_max), t' (1..1024) and t (1..t').  Allocates the batch's
+ * device buffers and uploads the per-query layout.  Synchronises.
+ *
+ * mad_mips_run: one batch on Q (nq x d dense F32, device), asynchronous
+ * and free of host synchronisation and allocation, so it can be captured
+ * in a CUDA graph.  out_dev: nq * t pairs (query q's results at q * t, i =
+ * q); n_out_dev: nq counts (uint32, device); cand_dev (optional, nq * t'
+ * pairs): each query's top-t' candidates.  A query whose candidates above
+ * the selection threshold exceed 4096 (ties of x in the thousands) reports
+ * MAD_ERR_STATE through the device error word (read by mad_stats). */
+mad_status mad_mips_items(mad_ctx* ctx, const mad_matrix* B, uint64_t s_max, mad_stream stream);
+mad_status mad_mips_plan(mad_ctx* ctx, uint32_t nq, const uint64_t* s_host, uint32_t tprime,
+                         uint32_t t, mad_stream stream);
+mad_status mad_mips_run(mad_ctx* ctx, const mad_matrix* Q, uint64_t seed, mad_pair* out_dev,
+                        uint32_t* n_out_dev, mad_pair* cand_dev, mad_stream stream);
+
 /* Diagnostics for mad_dense_topt: the full BF16 tensor-core product C~ as
  * FP32, row-major m x n, written to c_dev (device, m*n floats). */
 mad_status mad_debug_dense_product(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B,

@@ -32,7 +32,8 @@ EXPORTS = (
     "mad_create", "mad_destroy", "mad_strerror", "mad_set_hash_capacity", "mad_build_tables",
     "mad_sample", "mad_reset_hash", "mad_topk", "mad_rescore", "mad_stats", "mad_debug_draws",
     "mad_debug_draws_list", "mad_export_x", "mad_export_table", "mad_rescore_noalloc",
-    "mad_dense_topt", "mad_debug_dense_product", "mad_set_phase_events",
+    "mad_dense_topt", "mad_debug_dense_product", "mad_set_phase_events", "mad_mips_items",
+    "mad_mips_plan", "mad_mips_run",
 )
 MAD_NOALLOC_MAX_CANDIDATES = 16384
 
@@ -82,6 +83,9 @@ def lib() -> ctypes.CDLL:
         L.mad_strerror.restype = ctypes.c_char_p
         L.mad_set_hash_capacity.argtypes = [P, u64]
         L.mad_set_phase_events.argtypes = [P, ctypes.POINTER(P), u32]
+        L.mad_mips_items.argtypes = [P, ctypes.POINTER(mad_matrix), u64, P]
+        L.mad_mips_plan.argtypes = [P, u32, ctypes.POINTER(u64), u32, u32, P]
+        L.mad_mips_run.argtypes = [P, ctypes.POINTER(mad_matrix), u64, P, P, P, P]
         L.mad_build_tables.argtypes = [P, ctypes.POINTER(mad_matrix), ctypes.POINTER(mad_matrix),
                                        u64, P]
         L.mad_sample.argtypes = [P, u64, u64, u64, P]
@@ -240,6 +244,28 @@ def mad_dense_topt(ctx, A: mad_matrix, B: mad_matrix, t: int, rescore: int = 0, 
     _check(lib().mad_dense_topt(ctx, ctypes.byref(A), ctypes.byref(B), t, rescore, _ptr(out),
                                 ctypes.byref(n), _stream(stream)), "mad_dense_topt")
     return out, n.value
+
+
+def mad_mips_items(ctx, B: mad_matrix, s_max: int, stream=None) -> None:
+    """Item-side tables for batched queries (B: d x n dense F32)."""
+    _check(lib().mad_mips_items(ctx, ctypes.byref(B), s_max, _stream(stream)), "mad_mips_items")
+
+
+def mad_mips_plan(ctx, s_per_query, tprime: int, t: int, stream=None) -> None:
+    """Batch shape: one budget per query (host integers), t' and t."""
+    import numpy as np
+    s = np.ascontiguousarray(np.asarray(s_per_query, dtype=np.uint64))
+    _check(lib().mad_mips_plan(ctx, len(s), s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                               tprime, t, _stream(stream)), "mad_mips_plan")
+
+
+def mad_mips_run(ctx, Q: mad_matrix, seed: int, out, n_out, cand=None, stream=None) -> None:
+    """One batch (asynchronous; capturable in a CUDA graph).  out: nq * t
+    pairs, n_out: nq uint32 (an int32 CUDA tensor), cand: optional nq * t'
+    pairs receiving each query's top-t' candidates."""
+    _check(lib().mad_mips_run(ctx, ctypes.byref(Q), seed, _ptr(out), _ptr(n_out),
+                              _ptr(cand) if cand is not None else None, _stream(stream)),
+           "mad_mips_run")
 
 
 def mad_debug_dense_product(ctx, A: mad_matrix, B: mad_matrix, stream=None):

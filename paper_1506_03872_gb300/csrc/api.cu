@@ -71,6 +71,14 @@ void free_tables(mad_ctx* ctx, cudaStream_t st) {
   free_async(ctx->T2g, st);
   free_async(ctx->T2g_sh, st);
   free_async(ctx->bloom, st);
+  free_async(ctx->TBg_ptr, st);
+  free_async(ctx->TBg, st);
+  free_async(ctx->TBg_sh, st);
+  free_async(ctx->mips_s, st);
+  free_async(ctx->mips_chunk_q, st);
+  free_async(ctx->mips_chunk_l0, st);
+  ctx->mips_items = false;
+  ctx->mips_nq = 0;
   ctx->built = false;
   ctx->regioned = false;
 }
@@ -85,7 +93,7 @@ mad_status alloc(mad_ctx* ctx, T*& p, size_t count, cudaStream_t st) {
 mad_status device_error_status(uint32_t err) {
   if (err & DERR_HASH_FULL) return MAD_ERR_HASH_FULL;
   if (err & DERR_OVERFLOW) return MAD_ERR_OVERFLOW;
-  if (err & DERR_SEARCH) return MAD_ERR_STATE;
+  if (err & (DERR_SEARCH | DERR_SELECT)) return MAD_ERR_STATE;
   if (err & DERR_EMPTY) return MAD_ERR_EMPTY;
   return MAD_OK;
 }

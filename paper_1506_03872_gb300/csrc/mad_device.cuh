@@ -113,7 +113,7 @@ __device__ __forceinline__ int ub_u32(const uint32_t* __restrict__ P, int len, u
 // as ub_u32 over the whole row.
 __device__ __forceinline__ int ub_guided_u32(const uint32_t* __restrict__ P,
                                              const uint32_t* __restrict__ G, int sh,
-                                             uint32_t target) {
+                                             uint32_t target, uint32_t mask = 0xFFFFFFFFu) {
   const uint32_t b = target >> sh;
   const int lo = (int)__ldg(G + b), hi = (int)__ldg(G + b + 1);
   if (hi - lo <= 16) {
@@ -121,11 +121,11 @@ __device__ __forceinline__ int ub_guided_u32(const uint32_t* __restrict__ P,
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int e = lo + q;
-      if (e < hi) cnt += (__ldg(P + e) <= target) ? 1 : 0;
+      if (e < hi) cnt += ((__ldg(P + e) & mask) <= target) ? 1 : 0;
     }
     return lo + cnt;
   }
-  return lo + ub_u32(P + lo, hi - lo, target, 0xFFFFFFFFu);
+  return lo + ub_u32(P + lo, hi - lo, target, mask);
 }
 
 // Two searches over rows of the same length at once (independent loads).
@@ -399,18 +399,19 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 // converged).  A key already there gets the value added; an empty slot is
 // claimed with one CAS, and a CAS lost to another key re-reads the group
 // from that slot, so slots are still taken in linear-probing order.
-// Returns 0 when the probe limit is hit, 1 when the key existed, 2 when
-// this call created it.
+// Probing wraps from slot hi back to slot lo ([lo, hi) is the whole table,
+// or a region whose bounds are multiples of 4).  Returns 0 when the probe
+// limit is hit, 1 when the key existed, 2 when this call created it.
 __device__ __forceinline__ int hash_add_from(unsigned long long* __restrict__ keys,
-                                             long long* __restrict__ vals, uint64_t cap,
-                                             uint64_t slot, uint32_t max_probe,
+                                             long long* __restrict__ vals, uint64_t lo,
+                                             uint64_t hi, uint64_t slot, uint32_t max_probe,
                                              unsigned long long key, long long v) {
   uint32_t probes = 0;
   while (probes < max_probe) {
     const uint64_t g = slot & ~3ull;
-    // Slots of the group at or past cap (a table size that is not a multiple
-    // of 4) are skipped; probing wraps to slot 0 after the group.
-    const uint32_t valid = (g + 4 <= cap) ? 4u : (uint32_t)(cap - g);
+    // Slots of the group at or past hi (a table size that is not a multiple
+    // of 4) are skipped; probing wraps to slot lo after the group.
+    const uint32_t valid = (g + 4 <= hi) ? 4u : (uint32_t)(hi - g);
     unsigned long long k4[4];
     if (valid == 4) {
       // L2 loads: keys only ever change from EMPTY to a key, and a stale
@@ -433,7 +434,7 @@ __device__ __forceinline__ int hash_add_from(unsigned long long* __restrict__ ke
     if (pick == 4) {
       probes += valid > start ? valid - start : 0u;
       slot = g + 4;
-      if (slot >= cap) slot = 0;
+      if (slot >= hi) slot = lo;
       continue;
     }
     probes += pick - start + 1;
@@ -453,6 +454,21 @@ __device__ __forceinline__ int hash_add_from(unsigned long long* __restrict__ ke
     return created ? 2 : 1;
   }
   return 0;
+}
+
+// Log buckets of positive 64-bit values: 16 * floor(log2 v) + the 4 bits
+// below the leading bit (1024 buckets, monotone in v), and a bucket's
+// smallest value.
+__device__ __forceinline__ uint32_t log_bucket(unsigned long long v) {
+  const int e = 63 - __clzll((long long)v);
+  const uint32_t f = e >= 4 ? (uint32_t)(v >> (e - 4)) & 15u : (uint32_t)(v << (4 - e)) & 15u;
+  return (uint32_t)e * 16u + f;
+}
+
+__host__ __device__ __forceinline__ unsigned long long bucket_floor(uint32_t b) {
+  const int e = (int)(b >> 4);
+  const unsigned long long m = 16ull + (b & 15u);
+  return e >= 4 ? (m << (e - 4)) : (m >> (4 - e));
 }
 
 // Bloom filter for the 0/1 closure test: a key sets five bits (five 6-bit
@@ -484,7 +500,7 @@ __device__ __forceinline__ uint64_t home_slot(const SampleParams& p, unsigned lo
 }
 
 __device__ __forceinline__ int hash_add(const SampleParams& p, unsigned long long key, long long v) {
-  return hash_add_from(p.hkeys, p.hvals, p.hcap, home_slot(p, key), p.max_probe, key, v);
+  return hash_add_from(p.hkeys, p.hvals, 0, p.hcap, home_slot(p, key), p.max_probe, key, v);
 }
 
 // Histogram pick by one whole block of 256 threads: the highest bucket b

@@ -16,6 +16,7 @@ enum : uint32_t {
   DERR_SEARCH = 2u,        // an inverse-CDF search left its row (corrupt table)
   DERR_OVERFLOW = 4u,      // an integer table total left its range
   DERR_EMPTY = 8u,         // ||W||_1 == 0
+  DERR_SELECT = 16u,       // a per-query selection held more candidates than it keeps
 };
 
 constexpr uint64_t EMPTY_KEY = ~0ull;
@@ -79,6 +80,10 @@ struct SampleParams {
   // absent): word mix64(key) >> bloom_shift holds five bits of each key.
   const unsigned long long* bloom;
   int bloom_shift;
+  // Guides of the dense TB rows (batched queries; null otherwise).
+  const unsigned long long* TBg_ptr;
+  const uint32_t* TBg;
+  const uint8_t* TBg_sh;
   int f_exp;                       // F
   // Hash.  Regioned (dense inputs): the key (a, b) starts probing in the
   // home region of row a, [hreg[a], hreg[a+1]), sized from row a's expected
@@ -148,6 +153,16 @@ struct mad_ctx {
   uint8_t* T2g_sh = nullptr;
   unsigned long long* bloom = nullptr;    // closure-test filter (0/1 inputs)
   int bloom_lg = 0;
+  unsigned long long* TBg_ptr = nullptr;  // guides of the TB rows (batched queries)
+  uint32_t* TBg = nullptr;
+  uint8_t* TBg_sh = nullptr;
+  // Batched queries: the plan of the current batch.
+  bool mips_items = false;
+  uint32_t mips_nq = 0, mips_tprime = 0, mips_t = 0;
+  uint64_t mips_chunks = 0;
+  unsigned long long* mips_s = nullptr;   // nq budgets
+  uint32_t* mips_chunk_q = nullptr;       // query of each 256-diamond chunk
+  uint32_t* mips_chunk_l0 = nullptr;      // its first diamond
   int64_t t1c_n = 0, tbc_n = 0;
   int t1c_lg = 0, tbc_lg = 0;
   void* bt = nullptr;               // dense B^T (n x d), the input dtype
@@ -192,6 +207,13 @@ mad_status t2_guide_offsets(mad_ctx* ctx, cudaStream_t st);
 // MAD_GRAM, else B) into ctx->bloom (2^bloom_lg words, cleared here).
 mad_status build_bloom(mad_ctx* ctx, cudaStream_t st);
 mad_status t2_guide_fill(mad_ctx* ctx, cudaStream_t st);
+// Batched queries: guides of the dense TB rows (offsets into ctx->TBg_ptr /
+// TBg_sh, d + 1 and d entries, total in TBg_ptr[d]; then the entries), the
+// item-side tables (TB, nb, maximum |b|, B^T) and the query rows (T2, TA).
+mad_status tb_guide_offsets(mad_ctx* ctx, cudaStream_t st);
+mad_status tb_guide_fill(mad_ctx* ctx, cudaStream_t st);
+mad_status build_item_tables(mad_ctx* ctx, cudaStream_t st);
+mad_status build_query_rows(mad_ctx* ctx, cudaStream_t st);
 mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st);
 // Home regions of the dense hash: sizes from T1 and s_max, then offsets.
 mad_status build_hash_regions(mad_ctx* ctx, cudaStream_t st);

@@ -169,17 +169,6 @@ k_collect(const Item* __restrict__ l0, unsigned long long n, const SelState* st,
 // (1024 buckets, monotone in v).  The collect threshold is the lower bound
 // of the bucket in which the count from the top reaches K, so at least K
 // items (all of the top K) pass and few more do.
-__device__ __forceinline__ uint32_t log_bucket(unsigned long long v) {
-  const int e = 63 - __clzll((long long)v);
-  const uint32_t f = e >= 4 ? (uint32_t)(v >> (e - 4)) & 15u : (uint32_t)(v << (4 - e)) & 15u;
-  return (uint32_t)e * 16u + f;
-}
-
-__host__ __device__ __forceinline__ unsigned long long bucket_floor(uint32_t b) {
-  const int e = (int)(b >> 4);
-  const unsigned long long m = 16ull + (b & 15u);
-  return e >= 4 ? (m << (e - 4)) : (m >> (4 - e));
-}
 
 __global__ void __launch_bounds__(256)
 k_log_hist(const long long* __restrict__ vals, uint64_t cap, unsigned long long K,

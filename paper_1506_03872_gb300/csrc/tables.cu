@@ -580,6 +580,82 @@ mad_status build_bloom(mad_ctx* ctx, cudaStream_t st) {
   return cuda_status(cudaGetLastError());
 }
 
+// Guides of the dense TB rows (batched queries): row k (n entries, masked
+// total tot) gets buckets of width 2^sh leaving at most about n/8 of them;
+// guide entry b is the first position whose prefix reaches b << sh.  Built
+// by one pass over the entries: entry e writes the guide entries of the
+// bucket starts its step (v_{e-1}, v_e] crosses.
+__global__ void __launch_bounds__(256)
+k_tbg_sizes(const uint32_t* __restrict__ TB, int64_t d, int64_t n,
+            unsigned long long* __restrict__ sizes, uint8_t* __restrict__ shift) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < d;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t tot = TB[k * n + n - 1] & PREFIX_MASK;
+    unsigned long long size = 0;
+    int sh = 0;
+    if (tot > 0) {
+      sh = bitlen_u32(tot - 1) - bitlen_u32((uint32_t)(n / 16 > 0 ? n / 16 : 1));
+      if (sh < 0) sh = 0;
+      size = (unsigned long long)((tot - 1) >> sh) + 2;   // nb + 1
+    }
+    sizes[k] = size;
+    shift[k] = (uint8_t)sh;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_tbg_fill(const uint32_t* __restrict__ TB, int64_t d, int64_t n,
+           const unsigned long long* __restrict__ gptr, const uint8_t* __restrict__ shift,
+           uint32_t* __restrict__ G) {
+  const int64_t total = d * n;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = x / n, e = x - k * n;
+    const unsigned long long g0 = gptr[k], nb1 = gptr[k + 1] - g0;   // nb + 1 entries
+    if (nb1 == 0) continue;
+    const int sh = shift[k];
+    const unsigned long long v = TB[x] & PREFIX_MASK;
+    const unsigned long long b_hi = v >> sh;
+    const unsigned long long b_lo = e ? ((unsigned long long)(TB[x - 1] & PREFIX_MASK) >> sh) + 1 : 0;
+    for (unsigned long long b = b_lo; b <= b_hi && b < nb1; ++b) G[g0 + b] = (uint32_t)e;
+    if (e == n - 1)   // bucket starts past the last prefix: no entry reaches them
+      for (unsigned long long b = b_hi + 1; b < nb1; ++b) G[g0 + b] = (uint32_t)n;
+  }
+}
+
+mad_status tb_guide_offsets(mad_ctx* ctx, cudaStream_t st) {
+  const uint64_t d = (uint64_t)ctx->d;
+  const size_t sizes_bytes = (d * sizeof(unsigned long long) + 255) & ~(size_t)255;
+  mad_status rs = ensure_scratch(ctx, sizes_bytes + scan_partial_elems(d) * 8, st);
+  if (rs != MAD_OK) return rs;
+  unsigned long long* sizes = (unsigned long long*)ctx->scratch;
+  uint64_t* part = (uint64_t*)((char*)ctx->scratch + sizes_bytes);
+  k_tbg_sizes<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(ctx->TB, ctx->d, ctx->n, sizes,
+                                                           ctx->TBg_sh);
+  count_launch(ctx);
+  return scan_exclusive_u64(ctx, (const uint64_t*)sizes, (uint64_t*)ctx->TBg_ptr, d, part, st);
+}
+
+mad_status tb_guide_fill(mad_ctx* ctx, cudaStream_t st) {
+  const int64_t total = ctx->d * ctx->n;
+  const int64_t blocks64 = (total + 255) / 256;
+  k_tbg_fill<<<(unsigned)(blocks64 < 152 * 32 ? blocks64 : 152 * 32), 256, 0, st>>>(
+      ctx->TB, ctx->d, ctx->n, ctx->TBg_ptr, ctx->TBg_sh, ctx->TBg);
+  count_launch(ctx);
+  return cuda_status(cudaGetLastError());
+}
+
+mad_status build_item_tables(mad_ctx* ctx, cudaStream_t st) {
+  launch_b_rows<float>(ctx, st);
+  launch_transpose<float>(ctx, st);
+  return cuda_status(cudaGetLastError());
+}
+
+mad_status build_query_rows(mad_ctx* ctx, cudaStream_t st) {
+  launch_a_rows<float>(ctx, st);
+  return cuda_status(cudaGetLastError());
+}
+
 mad_status t2_guide_fill(mad_ctx* ctx, cudaStream_t st) {
   const int64_t warps_needed = ctx->m;
   const int64_t blocks64 = (warps_needed + 7) / 8;

@@ -87,6 +87,26 @@ def dense_factors(m: int = 200_000, d: int = 100, n: int = 50_000, seed: int = 2
                     sampler_seed=102)
 
 
+def batched_queries(n: int = 1_000_000, d: int = 300, nq: int = 10_000, seed: int = 4,
+                    s_lo: int = 1_000, s_hi: int = 100_000, t: int = 5, tprime: int = 100,
+                    sigma: float = 0.5) -> Workload:
+    """Batched maximum-|inner-product| queries: n item vectors and nq query
+    vectors, each exp(sigma z) * a unit Gaussian direction, and a budget per
+    query drawn uniformly from [s_lo, s_hi].  A = the queries (nq x d), B =
+    the items as columns (d x n)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    B = np.empty((d, n), dtype=np.float32)
+    step = 65536
+    for j0 in range(0, n, step):
+        j1 = min(n, j0 + step)
+        B[:, j0:j1] = _unit_rows(rng, j1 - j0, d, sigma).astype(np.float32).T
+    Q = _unit_rows(rng, nq, d, sigma).astype(np.float32)
+    s_q = rng.integers(s_lo, s_hi + 1, size=nq, dtype=np.int64).astype(np.uint64)
+    return Workload("batched_queries", A=Q, B=B, m=nq, d=d, n=n, s=int(s_q.sum()), t=t,
+                    tprime=tprime, sampler_seed=104,
+                    meta={"s_per_query": s_q, "s_max": int(s_hi)})
+
+
 def _chung_lu_offset(nodes: int, exponent: float, max_share: float) -> float:
     """Offset v0 in w_v = (v + v0)^(-1/(exponent-1)) so that the heaviest
     node holds ``max_share`` of the total weight (caps the largest degree)."""
@@ -152,4 +172,4 @@ def chung_lu(nodes: int = 1_000_000, edges: int = 10_000_000, exponent: float = 
 
 def by_name(name: str, **kw) -> Workload:
     return {"plain_small": plain_small, "dense_factors": dense_factors,
-            "chung_lu": chung_lu}[name](**kw)
+            "chung_lu": chung_lu, "batched_queries": batched_queries}[name](**kw)
