@@ -350,6 +350,10 @@ def run_ours(args):
     torch.cuda.set_device(local)
     _build.build()
     w = _workload(args.workload, args.scale)
+    if getattr(args, "square_sym", False):
+        if not w.csr:
+            raise SystemExit("--square-sym needs a 0/1 Gram workload")
+        w.flags |= 8
     s, t, tprime, seed = w.s, w.t, w.tprime, w.sampler_seed
     dev = torch.device("cuda", local)
     if w.csr:
@@ -529,7 +533,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": w.name, "m": w.m, "d": w.d, "n": w.n, "s": s, "t": t,
+            "config": {"workload": w.name + ("+square_sym" if w.flags & 8 else ""), "m": w.m,
+                       "d": w.d, "n": w.n, "s": s, "t": t,
                        "tprime": tprime, "flags": w.flags, "l2": "flushed between steps",
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "phases_ms": {k: round(float(phase[:, q].mean()), 4)
@@ -740,6 +745,8 @@ def main():
     ap.add_argument("--no-ladder", action="store_true",
                     help="skip the time-to-recall ladder over s")
     ap.add_argument("--ladder-seeds", type=int, default=5)
+    ap.add_argument("--square-sym", action="store_true",
+                    help="0/1 Gram workloads: the squared-symmetric update of Sec. 3.2.3")
     ap.add_argument("--rescore", type=int, default=0,
                     help="comparator FP32 rescore budget (0: 8t)")
     args = ap.parse_args()

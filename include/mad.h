@@ -107,8 +107,15 @@ typedef struct mad_pair {
  *                     is twice the symmetrised X of Sec. 3.2.2 and ranks the
  *                     same.
  *   MAD_EXCLUDE_DIAG  diamonds with i == j are drawn but not accumulated
- *                     (the distinct-pairs application of Sec. 6.2). */
-enum { MAD_NONNEG = 1u, MAD_GRAM = 2u, MAD_EXCLUDE_DIAG = 4u };
+ *                     (the distinct-pairs application of Sec. 6.2).
+ *   MAD_SQUARE_SYM    squared symmetric input (Sec. 3.2.3): with MAD_GRAM
+ *                     and A = B = A^T (the caller guarantees symmetry),
+ *                     each diamond (k', i, k, j) also adds its value to the
+ *                     pair (k, k') (the paper adds half to each pair; the
+ *                     whole value scales every x by 2 and orders the same).
+ *                     Under MAD_EXCLUDE_DIAG a diagonal addition of either
+ *                     kind is skipped.  0/1 inputs only. */
+enum { MAD_NONNEG = 1u, MAD_GRAM = 2u, MAD_EXCLUDE_DIAG = 4u, MAD_SQUARE_SYM = 8u };
 
 typedef struct mad_stats_t {
   double w1;                /* ||W||_1 as represented by the tables */

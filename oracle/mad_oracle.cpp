@@ -44,7 +44,7 @@ namespace {
 
 enum { FMT_DENSE = 0, FMT_CSR = 1 };
 enum { DT_F32 = 0, DT_F64 = 1, DT_BINARY = 2 };
-enum { FL_NONNEG = 1u, FL_GRAM = 2u, FL_EXCLUDE_DIAG = 4u };
+enum { FL_NONNEG = 1u, FL_GRAM = 2u, FL_EXCLUDE_DIAG = 4u, FL_SQSYM = 8u };
 enum {
   ST_OK = 0, ST_ARG = 1, ST_OVERFLOW = 4, ST_EMPTY = 5, ST_UNSUPPORTED = 8
 };
@@ -441,6 +441,10 @@ void* or_create(int fmtA, int dtA, int64_t m, int64_t d, int64_t ldA, const void
                 const int64_t* ptrA, const int32_t* colA, int fmtB, int dtB, int64_t dB,
                 int64_t n, int64_t ldB, const void* valB, const int64_t* ptrB,
                 const int32_t* colB, uint32_t flags, uint64_t s_max, int* status) {
+  if ((flags & FL_SQSYM) && !(flags & FL_GRAM)) {  // Sec. 3.2.3 needs B = A^T = A
+    *status = ST_UNSUPPORTED;
+    return nullptr;
+  }
   Oracle* o = new Oracle();
   o->flags = flags;
   o->s_max = s_max;
@@ -525,18 +529,32 @@ void or_draw_list(void* h, uint64_t seed, uint64_t count, const uint64_t* ells, 
 // into X.  Gram inputs (B = A^T, Sec. 3.2.2) accumulate into the unordered
 // pair, which is twice the symmetrised X of Eq. (xsym) and orders the same;
 // the diagonal is skipped when asked (Sec. 6.2, distinct pairs only).
+//
+// Squared symmetric inputs (FL_SQSYM with FL_GRAM, A = B = A^T, Sec. 3.2.3):
+// the diamond (k', i, k, j) is also a diamond of the pair (k, k'), whose
+// roles it swaps with (i, j), so its value is added to both pairs.  The
+// paper adds half to each; adding the whole value to each scales every x by
+// the same factor 2 and orders them the same.  Each of the two additions is
+// skipped on the diagonal when asked (counted in diag_skipped).
 int or_sample(void* h, uint64_t s, uint64_t seed, uint64_t first) {
   Oracle* o = (Oracle*)h;
   if (o->sampled + s > o->s_max) return ST_OVERFLOW;
+  const bool sqsym = (o->flags & FL_SQSYM) != 0;
   for (uint64_t q = 0; q < s; ++q) {
     const Draw dr = draw_diamond(*o, seed, first + q);
     if ((o->flags & FL_EXCLUDE_DIAG) && dr.i == dr.j) {
       ++o->diag_skipped;
-      continue;
+    } else if (dr.v != 0) {
+      o->X[pair_key(*o, dr.i, dr.j)] += dr.v;
+      ++o->inserted;
     }
-    if (dr.v == 0) continue;
-    o->X[pair_key(*o, dr.i, dr.j)] += dr.v;
-    ++o->inserted;
+    if (!sqsym) continue;
+    if ((o->flags & FL_EXCLUDE_DIAG) && dr.k == dr.kp) {
+      ++o->diag_skipped;
+    } else if (dr.v != 0) {
+      o->X[pair_key(*o, dr.k, dr.kp)] += dr.v;
+      ++o->inserted;
+    }
   }
   o->sampled += s;
   return ST_OK;

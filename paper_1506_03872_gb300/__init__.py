@@ -24,7 +24,7 @@ MAD_OK, MAD_ERR_ARG, MAD_ERR_OOM, MAD_ERR_CUDA, MAD_ERR_OVERFLOW = 0, 1, 2, 3, 4
 MAD_ERR_EMPTY, MAD_ERR_HASH_FULL, MAD_ERR_STATE, MAD_ERR_UNSUPPORTED = 5, 6, 7, 8
 MAD_DENSE_ROWMAJOR, MAD_CSR = 0, 1
 MAD_F32, MAD_F64, MAD_BINARY = 0, 1, 2
-MAD_NONNEG, MAD_GRAM, MAD_EXCLUDE_DIAG = 1, 2, 4
+MAD_NONNEG, MAD_GRAM, MAD_EXCLUDE_DIAG, MAD_SQUARE_SYM = 1, 2, 4, 8
 TABLES = {"T1": 0, "T2": 1, "TA": 2, "TB": 3, "na": 4, "nb": 5, "r": 6}
 
 # Every symbol include/mad.h declares.

@@ -132,7 +132,8 @@ extern "C" {
 mad_status mad_create(mad_ctx** out, uint32_t flags) {
   if (!out) return MAD_ERR_ARG;
   *out = nullptr;
-  if (flags & ~(uint32_t)(MAD_NONNEG | MAD_GRAM | MAD_EXCLUDE_DIAG)) return MAD_ERR_ARG;
+  if (flags & ~(uint32_t)(MAD_NONNEG | MAD_GRAM | MAD_EXCLUDE_DIAG | MAD_SQUARE_SYM))
+    return MAD_ERR_ARG;
   mad_ctx* ctx = new (std::nothrow) mad_ctx();
   if (!ctx) return MAD_ERR_OOM;
   ctx->flags = flags;
@@ -218,6 +219,9 @@ mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   } else {
     return MAD_ERR_UNSUPPORTED;
   }
+  // The squared symmetric update (Sec. 3.2.3) is built for 0/1 Gram inputs.
+  if ((ctx->flags & MAD_SQUARE_SYM) && (!csr || !(ctx->flags & MAD_GRAM)))
+    return MAD_ERR_UNSUPPORTED;
   free_tables(ctx, st);
   ctx->A = *A;
   ctx->B = *B;
@@ -342,8 +346,9 @@ mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
     if ((rs = pilot_inserts(ctx, kPilot, &hits, st)) != MAD_OK) return rs;
     const double f = (double)hits / (double)kPilot;
     const double f_hi = f + 6.0 * std::sqrt(f * (1.0 - f) / (double)kPilot) + 8.0 / (double)kPilot;
-    const double want = std::min(((double)s_max * std::min(f_hi, 1.0) + 4096.0) * 16.0,
-                                 (double)s_max / 0.6);
+    const double per = (ctx->flags & MAD_SQUARE_SYM) ? 2.0 : 1.0;  // inserts per diamond
+    const double want = std::min(((double)s_max * std::min(f_hi, per) + 4096.0) * 16.0,
+                                 per * (double)s_max / 0.6);
     cap = 1024;
     while ((double)cap < want && cap < (1ull << 40)) cap <<= 1;
     ctx->hcap = ctx->hcap_alloc = cap;

@@ -35,24 +35,33 @@ struct Tally {
 
 // Filter one drawn diamond and add it to X.  Lanes holding the same key
 // insert independently (the atomics combine them).
-__device__ __forceinline__ void accumulate(const SampleParams& p, bool valid, const Draw& dr,
-                                           Tally& t) {
-  if (!valid) return;
-  if ((p.flags & MAD_EXCLUDE_DIAG) && dr.i == dr.j) {
+// One addition of v to the pair (a, b) (unordered under MAD_GRAM).
+__device__ __forceinline__ void add_pair(const SampleParams& p, uint32_t a, uint32_t b, long long v,
+                                         Tally& t) {
+  if ((p.flags & MAD_EXCLUDE_DIAG) && a == b) {
     ++t.diag;
     return;
   }
-  if (dr.v == 0) return;
-  uint32_t a = dr.i, b = dr.j;
+  if (v == 0) return;
   if ((p.flags & MAD_GRAM) && b < a) {
-    a = dr.j;
-    b = dr.i;
+    const uint32_t c = a;
+    a = b;
+    b = c;
   }
-  const unsigned long long key = ((unsigned long long)a << 32) | b;
   ++t.inserted;
-  const int r = hash_add(p, key, dr.v);
+  const int r = hash_add(p, ((unsigned long long)a << 32) | b, v);
   if (r == 0) t.full = true;
   if (r == 2) ++t.created;
+}
+
+// Filter one drawn diamond and add it to X: to the pair (i, j), and under
+// MAD_SQUARE_SYM also to the pair (k, k') (Sec. 3.2.3).  Lanes holding the
+// same key insert independently (the atomics combine them).
+__device__ __forceinline__ void accumulate(const SampleParams& p, bool valid, const Draw& dr,
+                                           Tally& t) {
+  if (!valid) return;
+  add_pair(p, dr.i, dr.j, dr.v, t);
+  if (p.flags & MAD_SQUARE_SYM) add_pair(p, dr.k, dr.kp, dr.v, t);
 }
 
 __device__ __forceinline__ void flush_tally(const SampleParams& p, Tally& t) {
@@ -250,6 +259,8 @@ k_pilot(const SampleParams p, unsigned long long seed, unsigned long long n,
        q += (unsigned long long)gridDim.x * blockDim.x) {
     const Draw dr = draw_one(p, seed, q, &bad);
     c += (dr.v != 0 && !((p.flags & MAD_EXCLUDE_DIAG) && dr.i == dr.j)) ? 1 : 0;
+    if (p.flags & MAD_SQUARE_SYM)
+      c += (dr.v != 0 && !((p.flags & MAD_EXCLUDE_DIAG) && dr.k == dr.kp)) ? 1 : 0;
   }
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, off);

@@ -46,6 +46,9 @@ def case_inputs(name: str):
     if name == "chung_lu_small":
         w = W.chung_lu(nodes=5000, edges=40000, seed=9)
         return "csr", (w.rowptr, w.colidx, w.m), w.flags
+    if name == "chung_lu_square_sym":      # Sec. 3.2.3 update on A = A^T
+        w = W.chung_lu(nodes=5000, edges=40000, seed=9)
+        return "csr", (w.rowptr, w.colidx, w.m), w.flags | 8
     if name == "bipartite_binary":         # 0/1 CSR, A != B^T, no Gram
         rng = _rng(46)
         A = (rng.random((600, 80)) < 0.05)

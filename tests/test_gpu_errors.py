@@ -114,3 +114,12 @@ def test_phase_events_bracket_the_sampling_kernels():
         assert all(p >= 0.0 for p in parts)
         assert sum(parts) <= outer[0].elapsed_time(outer[1]) + 1e-3
         assert mad.mad_stats(c.ctx)["inserted"] > 0
+
+
+def test_square_sym_needs_01_gram_inputs():
+    import paper_1506_03872_gb300 as mad
+    A, B = _dense_inputs()
+    with mad.Context(2 | 8) as c:   # dense inputs: not built for Sec. 3.2.3
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_build_tables(c.ctx, mad.dense(A), mad.dense(A.T.contiguous()), 100)
+        assert e.value.status == mad.MAD_ERR_UNSUPPORTED

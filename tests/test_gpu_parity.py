@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 from gpu_cases import Case  # noqa: E402
 
 CASES = ["plain_small", "dense_ragged_f32", "dense_factors_small", "dense_mixed_signs_zeros",
-         "dense_nonneg", "gram_dense", "chung_lu_small", "bipartite_binary"]
+         "dense_nonneg", "gram_dense", "chung_lu_small", "bipartite_binary", "chung_lu_square_sym"]
 
 
 @pytest.fixture(scope="module", autouse=True)

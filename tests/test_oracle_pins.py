@@ -362,3 +362,56 @@ def test_overflow_guard_on_s_max():
     o = _dense(A, B, s_max=100)
     assert o.sample(60, 1) == 0
     assert o.sample(60, 1, 60) == 4  # overflow: more diamonds than s_max
+
+
+def _sym_binary(n, p, seed):
+    rng = _rng(seed)
+    A = (rng.random((n, n)) < p).astype(np.int64)
+    A = np.triu(A, 1)
+    A = A + A.T
+    A[0, 1] = A[1, 0] = 1
+    rp = np.concatenate([[0], np.cumsum(A.sum(1))]).astype(np.int64)
+    return A, Matrix(rowptr=rp, colidx=np.nonzero(A)[1], shape=A.shape)
+
+
+def test_squared_symmetric_expectation_exact():
+    """Sec. 3.2.3 on a symmetric 0/1 matrix: every closed three-path credits
+    its pair {i, j} and its pair {k, k'}; the expected unordered-pair score
+    per sample is 4 c_ab^2 / ||W||_1 for every off-diagonal pair (twice the
+    Gram score 2 c_ab^2 / ||W||_1), from the enumerated law."""
+    A, M = _sym_binary(6, 0.5, 31)
+    flags = 2 | 4 | 8
+    o = Oracle(M, M, flags)
+    i, k, j, kp, prob, v = o.enumerate()
+    w1 = _w1_closed_form(A.astype(float), A.astype(float))
+    ex = np.zeros((6, 6))
+    for a, b, pr, val in ((i, j, prob, v), (k, kp, prob, v)):
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        off = lo != hi
+        np.add.at(ex, (lo[off], hi[off]), pr[off] * val[off])
+    C = A @ A
+    iu = np.triu_indices(6, 1)
+    assert np.allclose(ex[iu] * w1, 4.0 * C[iu] ** 2, rtol=1e-12, atol=1e-12)
+
+
+def test_squared_symmetric_counts_and_flag_rule():
+    """One draw of the sampler adds to at most two pairs: X from sampling
+    equals the sum over the drawn diamonds of the two additions (checked
+    against the diamonds the oracle reports), and the flag needs Gram
+    inputs."""
+    A, M = _sym_binary(40, 0.15, 32)
+    o = Oracle(M, M, 2 | 4 | 8, 5000)
+    assert o.sample(5000, 9) == 0
+    keys, vals = o.x()
+    di, dk, dj, dkp, dv = o.draw(seed=9, first=0, count=5000)
+    ref = {}
+    for a, b, c, e, val in zip(di, dk, dj, dkp, dv):
+        for p_, q_ in ((a, c), (b, e)):
+            if p_ == q_ or val == 0:
+                continue
+            key = (int(min(p_, q_)) << 32) | int(max(p_, q_))
+            ref[key] = ref.get(key, 0) + int(val)
+    got = {int(kk): int(vv) for kk, vv in zip(keys, vals)}
+    assert got == ref
+    with pytest.raises(Exception):
+        Oracle(M, M, 8)
