@@ -254,6 +254,39 @@ mad_status mad_mips_plan(mad_ctx* ctx, uint32_t nq, const uint64_t* s_host, uint
 mad_status mad_mips_run(mad_ctx* ctx, const mad_matrix* Q, uint64_t seed, mad_pair* out_dev,
                         uint32_t* n_out_dev, mad_pair* cand_dev, mad_stream stream);
 
+/* ---- Learned budget predictor (the paper has no counterpart) ----------- *
+ * Theorem 2 bounds the diamonds needed to separate the top entries by a
+ * multiple of ||W||_1 / tau^2; the predictor learns the budget from cheap
+ * statistics of an instance instead of the unknown tau.
+ *
+ * mad_budget_features: MAD_BUDGET_FEATURES statistics of the instance of the
+ * last mad_build_tables, written to features_host (host): log10 of m, n, d,
+ * nnz(A), nnz(B); 1 for 0/1 inputs else 0; log10 ||W||_1; log10 of the
+ * largest row 2-norm of A and column 2-norm of B; log10 of sum r_i^2 /
+ * (sum r_i)^2 and of max r_i / sum r_i for the row weights r_i of T1; and
+ * log10 ||W||_1 - 2 (the two largest-norm logs), a Cauchy-Schwarz stand-in
+ * for Theorem 2's ||W||_1 / tau^2.  Synchronises.
+ *
+ * mad_mlp_train / mad_mlp_predict: a perceptron f -> 64 -> 64 -> 1 (ReLU)
+ * with BF16 weights (FP32 master copies for training) and FP32 arithmetic.
+ * params_dev (device, MAD_MLP_PARAMS(f) floats, caller-initialised): W1
+ * (64 x f, row-major), b1 (64), W2 (64 x 64), b2 (64), w3 (64), b3.
+ * Training: `epochs` full-batch Adam steps (beta 0.9 / 0.999) on the pinball
+ * loss of level `quantile` (0 < quantile < 1; above 0.5 a prediction below
+ * the target costs more than one above it) over X_dev (n x f, row-major) and
+ * y_dev (n); loss_dev (optional, `epochs` floats) receives the loss before
+ * each step.  n <= 4096, f <= 32.  Uses the context's scratch.
+ * Prediction: y_dev[i] = network(X_dev row i).  Both are asynchronous. */
+#define MAD_BUDGET_FEATURES 12
+#define MAD_MLP_HIDDEN 64
+#define MAD_MLP_PARAMS(f) (MAD_MLP_HIDDEN * (f) + 3 * MAD_MLP_HIDDEN + MAD_MLP_HIDDEN * MAD_MLP_HIDDEN + 1)
+mad_status mad_budget_features(mad_ctx* ctx, float* features_host, mad_stream stream);
+mad_status mad_mlp_train(mad_ctx* ctx, float* params_dev, const float* X_dev, const float* y_dev,
+                         uint32_t n, uint32_t f, uint32_t epochs, float lr, float quantile,
+                         float* loss_dev, mad_stream stream);
+mad_status mad_mlp_predict(const float* params_dev, const float* X_dev, uint32_t n, uint32_t f,
+                           float* y_dev, mad_stream stream);
+
 /* Diagnostics for mad_dense_topt: the full BF16 tensor-core product C~ as
  * FP32, row-major m x n, written to c_dev (device, m*n floats). */
 mad_status mad_debug_dense_product(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B,

@@ -33,8 +33,15 @@ EXPORTS = (
     "mad_sample", "mad_reset_hash", "mad_topk", "mad_rescore", "mad_stats", "mad_debug_draws",
     "mad_debug_draws_list", "mad_export_x", "mad_export_table", "mad_rescore_noalloc",
     "mad_dense_topt", "mad_debug_dense_product", "mad_set_phase_events", "mad_mips_items",
-    "mad_mips_plan", "mad_mips_run",
+    "mad_mips_plan", "mad_mips_run", "mad_budget_features", "mad_mlp_train", "mad_mlp_predict",
 )
+MAD_BUDGET_FEATURES = 12
+MAD_MLP_HIDDEN = 64
+
+
+def mlp_params(f: int) -> int:
+    """Parameter count of the budget perceptron for f features."""
+    return MAD_MLP_HIDDEN * f + 3 * MAD_MLP_HIDDEN + MAD_MLP_HIDDEN * MAD_MLP_HIDDEN + 1
 MAD_NOALLOC_MAX_CANDIDATES = 16384
 
 
@@ -86,6 +93,10 @@ def lib() -> ctypes.CDLL:
         L.mad_mips_items.argtypes = [P, ctypes.POINTER(mad_matrix), u64, P]
         L.mad_mips_plan.argtypes = [P, u32, ctypes.POINTER(u64), u32, u32, P]
         L.mad_mips_run.argtypes = [P, ctypes.POINTER(mad_matrix), u64, P, P, P, P]
+        L.mad_budget_features.argtypes = [P, P, P]
+        L.mad_mlp_train.argtypes = [P, P, P, P, u32, u32, u32, ctypes.c_float, ctypes.c_float, P,
+                                    P]
+        L.mad_mlp_predict.argtypes = [P, P, u32, u32, P, P]
         L.mad_build_tables.argtypes = [P, ctypes.POINTER(mad_matrix), ctypes.POINTER(mad_matrix),
                                        u64, P]
         L.mad_sample.argtypes = [P, u64, u64, u64, P]
@@ -266,6 +277,35 @@ def mad_mips_run(ctx, Q: mad_matrix, seed: int, out, n_out, cand=None, stream=No
     _check(lib().mad_mips_run(ctx, ctypes.byref(Q), seed, _ptr(out), _ptr(n_out),
                               _ptr(cand) if cand is not None else None, _stream(stream)),
            "mad_mips_run")
+
+
+def mad_budget_features(ctx, stream=None):
+    """The MAD_BUDGET_FEATURES statistics of the built instance (numpy)."""
+    import numpy as np
+    out = np.zeros(MAD_BUDGET_FEATURES, dtype=np.float32)
+    _check(lib().mad_budget_features(ctx, out.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+           "mad_budget_features")
+    return out
+
+
+def mad_mlp_train(ctx, params, X, y, epochs: int, lr: float, quantile: float, loss=None,
+                  stream=None) -> None:
+    """Full-batch Adam on the budget perceptron (CUDA float32 tensors:
+    params (mlp_params(f),), X (n, f), y (n,), loss (epochs,) or None)."""
+    n, f = X.shape
+    _check(lib().mad_mlp_train(ctx, _ptr(params), _ptr(X), _ptr(y), n, f, epochs, lr, quantile,
+                               _ptr(loss), _stream(stream)), "mad_mlp_train")
+
+
+def mad_mlp_predict(params, X, y=None, stream=None):
+    """Network outputs for the rows of X (CUDA float32 (n, f))."""
+    import torch
+    n, f = X.shape
+    if y is None:
+        y = torch.empty(n, dtype=torch.float32, device=X.device)
+    _check(lib().mad_mlp_predict(_ptr(params), _ptr(X), n, f, _ptr(y), _stream(stream)),
+           "mad_mlp_predict")
+    return y
 
 
 def mad_debug_dense_product(ctx, A: mad_matrix, B: mad_matrix, stream=None):

@@ -415,3 +415,31 @@ def test_squared_symmetric_counts_and_flag_rule():
     assert got == ref
     with pytest.raises(Exception):
         Oracle(M, M, 8)
+
+
+def test_mlp_reference_gradient_matches_finite_differences():
+    """The NumPy statement of the budget perceptron: its backward pass is the
+    derivative of its loss (unrounded weights, float64, smooth region)."""
+    import mlp_reference as R
+    rng = _rng(33)
+    f, n = 5, 40
+    p = rng.standard_normal(R.H * f + 3 * R.H + R.H * R.H + 1) * 0.2
+    X = rng.standard_normal((n, f))
+    y = rng.standard_normal(n) * 3
+    loss, g = R.loss_and_grad(p, X, y, 0.8, np.float64, round_weights=False)
+    idx = rng.choice(len(p), 40, replace=False)
+    for q in idx:
+        e = np.zeros_like(p)
+        e[q] = 1e-6
+        lp, _ = R.loss_and_grad(p + e, X, y, 0.8, np.float64, round_weights=False)
+        lm, _ = R.loss_and_grad(p - e, X, y, 0.8, np.float64, round_weights=False)
+        assert abs((lp - lm) / 2e-6 - g[q]) < 1e-5 * max(1.0, abs(g[q]))
+
+
+def test_bf16_rounding_reference():
+    """BF16 round-to-nearest-even of the reference against the exact rule
+    on hand-picked halfway cases."""
+    import mlp_reference as R
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -7, -2.5], np.float32)
+    assert np.array_equal(R.bf16(x), np.array([1.0, 1.0, 1.0 + 2 ** -6, 1.0 + 2 ** -7, -2.5],
+                                              np.float32))
