@@ -36,6 +36,7 @@ from paper_1506_03872_gb300.truth import (ground_truth_dense, ground_truth_gram_
 
 METRIC = "time-to-top-t at recall>=0.95 vs dense GEMM+top-t on 1 GB300; diamonds/sec"
 SAMPLER_SOURCES = ["paper_1506_03872_gb300/csrc/sample.cu",
+                   "paper_1506_03872_gb300/csrc/draw.cuh",
                    "paper_1506_03872_gb300/csrc/mad_device.cuh"]
 # Algorithmic bytes per diamond of the dominant kernel, one 32-byte sector
 # per random touch.  Dense draw kernel (k_sample_sorted): the final entry of

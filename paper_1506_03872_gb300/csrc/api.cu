@@ -308,6 +308,18 @@ mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
     return rs;
   }
   if (hs.err & DERR_OVERFLOW) return MAD_ERR_OVERFLOW;
+  if (dense) {
+    // Guides of the TB rows: the j search reads two guide entries and a
+    // window instead of walking the coarse index levels.
+    if ((rs = alloc(ctx, ctx->TBg_ptr, (size_t)ctx->d + 1, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->TBg_sh, (size_t)ctx->d, st)) != MAD_OK) return rs;
+    if ((rs = tb_guide_offsets(ctx, st)) != MAD_OK) return rs;
+    unsigned long long gtotal = 0;
+    cudaMemcpyAsync(&gtotal, ctx->TBg_ptr + ctx->d, sizeof(gtotal), cudaMemcpyDeviceToHost, st);
+    if ((rs = cuda_status(cudaStreamSynchronize(st))) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->TBg, (size_t)gtotal, st)) != MAD_OK) return rs;
+    if (gtotal && (rs = tb_guide_fill(ctx, st)) != MAD_OK) return rs;
+  }
   if (ctx->integer) {
     if (hs.t1_total == 0) return MAD_ERR_EMPTY;
     // Guides of the long T2 rows (the 0/1 sampler's k search).

@@ -144,8 +144,9 @@ __global__ void __launch_bounds__(256, 4)
 k_sample_sorted(const SampleParams p, unsigned long long seed, unsigned long long first,
                 unsigned long long s, unsigned long long* __restrict__ sorted,
                 unsigned long long* __restrict__ keys) {
+  // With TB guides the j search needs no staged coarse index.
   extern __shared__ uint32_t tbc[];
-  const int64_t ntbc = p.d * p.tbc_n;
+  const int64_t ntbc = p.TBg ? 0 : p.d * p.tbc_n;
   for (int64_t g = threadIdx.x; g < ntbc; g += blockDim.x) tbc[g] = p.TBc[g];
   __syncthreads();
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -156,7 +157,7 @@ k_sample_sorted(const SampleParams p, unsigned long long seed, unsigned long lon
     const unsigned long long e = sorted[q];
     const Uniforms u = diamond_uniforms(seed, first + (uint32_t)e);
     const int64_t i = draw_row_i(p, u.u0, &bad, p.T1c);
-    const Draw dr = draw_given_row(p, u, i, &bad, tbc);
+    const Draw dr = draw_given_row(p, u, i, &bad, p.TBg ? nullptr : tbc);
     unsigned long long key = EMPTY_KEY;
     if ((p.flags & MAD_EXCLUDE_DIAG) && dr.i == dr.j) {
       ++diag;
@@ -355,7 +356,7 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
     phase_event(ctx, 3, st);
     return cuda_status(cudaGetLastError());
   }
-  const size_t smem_tbc = (size_t)(p.d * p.tbc_n) * sizeof(uint32_t);
+  const size_t smem_tbc = p.TBg ? 0 : (size_t)(p.d * p.tbc_n) * sizeof(uint32_t);
   static bool attrs = false;
   if (!attrs) {
     cudaFuncSetAttribute(k_sample_sorted, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);

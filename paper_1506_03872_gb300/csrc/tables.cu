@@ -580,8 +580,8 @@ mad_status build_bloom(mad_ctx* ctx, cudaStream_t st) {
   return cuda_status(cudaGetLastError());
 }
 
-// Guides of the dense TB rows (batched queries): row k (n entries, masked
-// total tot) gets buckets of width 2^sh leaving at most about n/8 of them;
+// Guides of the dense TB rows: row k (n entries, masked total tot) gets
+// buckets of width 2^sh leaving at most about n/4 of them;
 // guide entry b is the first position whose prefix reaches b << sh.  Built
 // by one pass over the entries: entry e writes the guide entries of the
 // bucket starts its step (v_{e-1}, v_e] crosses.
@@ -594,7 +594,7 @@ k_tbg_sizes(const uint32_t* __restrict__ TB, int64_t d, int64_t n,
     unsigned long long size = 0;
     int sh = 0;
     if (tot > 0) {
-      sh = bitlen_u32(tot - 1) - bitlen_u32((uint32_t)(n / 16 > 0 ? n / 16 : 1));
+      sh = bitlen_u32(tot - 1) - bitlen_u32((uint32_t)(n / 8 > 0 ? n / 8 : 1));
       if (sh < 0) sh = 0;
       size = (unsigned long long)((tot - 1) >> sh) + 2;   // nb + 1
     }
