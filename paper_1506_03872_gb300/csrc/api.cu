@@ -71,6 +71,7 @@ void free_tables(mad_ctx* ctx, cudaStream_t st) {
   free_async(ctx->T2g, st);
   free_async(ctx->T2g_sh, st);
   free_async(ctx->bloom, st);
+  free_async(ctx->T1g, st);
   free_async(ctx->TBg_ptr, st);
   free_async(ctx->TBg, st);
   free_async(ctx->TBg_sh, st);
@@ -347,6 +348,16 @@ mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
     ctx->e1 = hs.e1;
   }
   ctx->t1_total = hs.t1_total;
+  {
+    // Guide of T1: about m/4 power-of-two buckets over [0, total).
+    int bl_t = 0, bl_m = 0;
+    while (bl_t < 64 && ((hs.t1_total - 1) >> bl_t)) ++bl_t;
+    while (bl_m < 63 && (((uint64_t)ctx->m / 4) >> bl_m)) ++bl_m;
+    ctx->t1g_sh = bl_t > bl_m ? bl_t - bl_m : 0;
+    const uint64_t nb = ((hs.t1_total - 1) >> ctx->t1g_sh) + 1;
+    if ((rs = alloc(ctx, ctx->T1g, (size_t)nb + 1, st)) != MAD_OK) return rs;
+    if ((rs = t1_guide_fill(ctx, nb, st)) != MAD_OK) return rs;
+  }
   if (pilot) {
     // Fraction of diamonds that add to X, from kPilot diamonds of a fixed
     // seed; the table holds s_max times that fraction plus six standard

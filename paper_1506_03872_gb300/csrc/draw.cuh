@@ -18,6 +18,14 @@ struct Draw {
 __device__ __forceinline__ int64_t draw_row_i(const SampleParams& p, unsigned long long u0,
                                               bool* bad, const uint64_t* t1c = nullptr) {
   const unsigned long long target = draw_target(u0, p.t1_total);
+  if (p.T1g) {
+    const int64_t i = ub_guided_u64(p.T1, p.m, p.T1g, p.t1g_sh, target);
+    if (i >= p.m) {
+      *bad = true;
+      return p.m - 1;
+    }
+    return i;
+  }
   if (t1c) return search3_u64(t1c, p.t1c_n, p.T1c2, p.T1, p.m, p.t1c_lg, target, bad);
   return search_u64(p.T1, p.m, target, bad);
 }

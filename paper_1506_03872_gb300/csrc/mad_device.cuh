@@ -128,6 +128,34 @@ __device__ __forceinline__ int ub_guided_u32(const uint32_t* __restrict__ P,
   return lo + ub_u32(P + lo, hi - lo, target, mask);
 }
 
+// The same for a 64-bit prefix (T1): bucket b = target >> sh.
+__device__ __forceinline__ int64_t ub_guided_u64(const uint64_t* __restrict__ P, int64_t len,
+                                                 const uint32_t* __restrict__ G, int sh,
+                                                 unsigned long long target) {
+  const unsigned long long b = target >> sh;
+  const int64_t lo = (int64_t)__ldg(G + b), hi = (int64_t)__ldg(G + b + 1);
+  if (hi - lo <= 16) {
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int64_t e = lo + q;
+      if (e < hi) cnt += (__ldg(P + e) <= target) ? 1 : 0;
+    }
+    return lo + cnt;
+  }
+  int64_t pos = lo, n = hi - lo;   // first entry above target in [lo, hi)
+  while (n > 0) {
+    const int64_t half = n >> 1;
+    if (__ldg(P + pos + half) <= target) {
+      pos += half + 1;
+      n -= half + 1;
+    } else {
+      n = half;
+    }
+  }
+  return pos < len ? pos : len;
+}
+
 // Two searches over rows of the same length at once (independent loads).
 __device__ __forceinline__ void ub2_u32(const uint32_t* __restrict__ P, const uint32_t* __restrict__ Q,
                                         int len, uint32_t tp, uint32_t tq, uint32_t mask, int* op,

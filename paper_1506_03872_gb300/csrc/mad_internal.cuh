@@ -80,7 +80,11 @@ struct SampleParams {
   // absent): word mix64(key) >> bloom_shift holds five bits of each key.
   const unsigned long long* bloom;
   int bloom_shift;
-  // Guides of the dense TB rows (batched queries; null otherwise).
+  // Guide of T1 (null when absent): entry b counts the prefix entries
+  // below b << t1g_sh.
+  const uint32_t* T1g;
+  int t1g_sh;
+  // Guides of the dense TB rows (null when absent).
   const unsigned long long* TBg_ptr;
   const uint32_t* TBg;
   const uint8_t* TBg_sh;
@@ -153,7 +157,9 @@ struct mad_ctx {
   uint8_t* T2g_sh = nullptr;
   unsigned long long* bloom = nullptr;    // closure-test filter (0/1 inputs)
   int bloom_lg = 0;
-  unsigned long long* TBg_ptr = nullptr;  // guides of the TB rows (batched queries)
+  uint32_t* T1g = nullptr;                // guide of T1
+  int t1g_sh = 0;
+  unsigned long long* TBg_ptr = nullptr;  // guides of the TB rows
   uint32_t* TBg = nullptr;
   uint8_t* TBg_sh = nullptr;
   // Batched queries: the plan of the current batch.
@@ -211,6 +217,8 @@ mad_status t2_guide_fill(mad_ctx* ctx, cudaStream_t st);
 // TBg_sh, d + 1 and d entries, total in TBg_ptr[d]; then the entries), the
 // item-side tables (TB, nb, maximum |b|, B^T) and the query rows (T2, TA).
 mad_status tb_guide_offsets(mad_ctx* ctx, cudaStream_t st);
+// Guide of T1 into ctx->T1g (nb + 1 entries for the shift ctx->t1g_sh).
+mad_status t1_guide_fill(mad_ctx* ctx, uint64_t nb, cudaStream_t st);
 mad_status tb_guide_fill(mad_ctx* ctx, cudaStream_t st);
 mad_status build_item_tables(mad_ctx* ctx, cudaStream_t st);
 mad_status build_query_rows(mad_ctx* ctx, cudaStream_t st);

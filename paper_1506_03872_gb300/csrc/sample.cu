@@ -87,8 +87,10 @@ __device__ __forceinline__ void flush_tally(const SampleParams& p, Tally& t) {
 __global__ void __launch_bounds__(256)
 k_sample(const SampleParams p, unsigned long long seed, unsigned long long first,
          unsigned long long s) {
+  // With a T1 guide the row search needs no staged coarse index.
   extern __shared__ uint64_t t1c[];
-  for (int64_t g = threadIdx.x; g < p.t1c_n; g += blockDim.x) t1c[g] = p.T1c[g];
+  const int64_t nt1c = p.T1g ? 0 : p.t1c_n;
+  for (int64_t g = threadIdx.x; g < nt1c; g += blockDim.x) t1c[g] = p.T1c[g];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const unsigned long long warp_id = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -140,7 +142,7 @@ k_bucket_scatter(const unsigned long long* __restrict__ rec, const unsigned int*
 // Draws only: diamond q's hash key goes to keys[q] (EMPTY_KEY when it adds
 // nothing: v = 0 or an excluded diagonal) and its increment over sorted[q]
 // (each thread rewrites only the entry it read).  k_insert adds them to X.
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 5)
 k_sample_sorted(const SampleParams p, unsigned long long seed, unsigned long long first,
                 unsigned long long s, unsigned long long* __restrict__ sorted,
                 unsigned long long* __restrict__ keys) {
@@ -156,7 +158,7 @@ k_sample_sorted(const SampleParams p, unsigned long long seed, unsigned long lon
        q += stride) {
     const unsigned long long e = sorted[q];
     const Uniforms u = diamond_uniforms(seed, first + (uint32_t)e);
-    const int64_t i = draw_row_i(p, u.u0, &bad, p.T1c);
+    const int64_t i = draw_row_i(p, u.u0, &bad, p.T1c);   // guided when p.T1g is set
     const Draw dr = draw_given_row(p, u, i, &bad, p.TBg ? nullptr : tbc);
     unsigned long long key = EMPTY_KEY;
     if ((p.flags & MAD_EXCLUDE_DIAG) && dr.i == dr.j) {
@@ -302,6 +304,8 @@ SampleParams make_params(const mad_ctx* ctx) {
   p.tbc_lg = ctx->tbc_lg;
   p.T1c2 = ctx->T1c2;
   p.TBc2 = ctx->TBc2;
+  p.T1g = ctx->T1g;
+  p.t1g_sh = ctx->t1g_sh;
   p.T2g_ptr = ctx->T2g_ptr;
   p.T2g = ctx->T2g;
   p.T2g_sh = ctx->T2g_sh;
@@ -346,7 +350,7 @@ mad_status pilot_inserts(mad_ctx* ctx, uint64_t n, uint64_t* hits, cudaStream_t 
 mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, cudaStream_t st) {
   if (s == 0) return MAD_OK;
   const SampleParams p = make_params(ctx);
-  const size_t smem_t1c = (size_t)p.t1c_n * sizeof(uint64_t);
+  const size_t smem_t1c = p.T1g ? 0 : (size_t)p.t1c_n * sizeof(uint64_t);
   if (!ctx->dense) {
     phase_event(ctx, 0, st);
     phase_event(ctx, 1, st);

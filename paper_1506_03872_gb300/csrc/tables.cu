@@ -623,6 +623,29 @@ k_tbg_fill(const uint32_t* __restrict__ TB, int64_t d, int64_t n,
   }
 }
 
+// Guide of T1 (one 64-bit prefix row), filled like the TB guides: entry e
+// writes the guide entries of the bucket starts in (T1[e-1], T1[e]].
+__global__ void __launch_bounds__(256)
+k_t1g_fill(const uint64_t* __restrict__ T1, int64_t m, int sh, uint64_t nb1,
+           uint32_t* __restrict__ G) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long b_hi = T1[e] >> sh;
+    const unsigned long long b_lo = e ? (T1[e - 1] >> sh) + 1 : 0;
+    for (unsigned long long b = b_lo; b <= b_hi && b < nb1; ++b) G[b] = (uint32_t)e;
+    if (e == m - 1)
+      for (unsigned long long b = b_hi + 1; b < nb1; ++b) G[b] = (uint32_t)m;
+  }
+}
+
+mad_status t1_guide_fill(mad_ctx* ctx, uint64_t nb, cudaStream_t st) {
+  const int64_t blocks64 = (ctx->m + 255) / 256;
+  k_t1g_fill<<<(unsigned)(blocks64 < 152 * 16 ? blocks64 : 152 * 16), 256, 0, st>>>(
+      ctx->T1, ctx->m, ctx->t1g_sh, nb + 1, ctx->T1g);
+  count_launch(ctx);
+  return cuda_status(cudaGetLastError());
+}
+
 mad_status tb_guide_offsets(mad_ctx* ctx, cudaStream_t st) {
   const uint64_t d = (uint64_t)ctx->d;
   const size_t sizes_bytes = (d * sizeof(unsigned long long) + 255) & ~(size_t)255;
