@@ -203,6 +203,31 @@ mad_status mad_topk(mad_ctx* ctx, uint32_t tprime, mad_pair* out_dev, uint32_t* 
 mad_status mad_rescore(mad_ctx* ctx, const mad_pair* cand_dev, uint32_t ncand, uint32_t t,
                        mad_pair* out_dev, uint32_t* n_out_host, mad_stream stream);
 
+/* ---- Fused pass for dense inputs (Alg. 2 then Alg. 3) ------------------ *
+ * mad_pipeline_plan: fixes A and B (dense, their device buffers and
+ * shapes), the budget s and t <= t' <= 131072, and allocates every table,
+ * the hash (home regions for s diamonds) and the selection lists.  It
+ * replaces any earlier tables of the context.  Synchronises.  Errors as
+ * mad_build_tables; MAD_ERR_UNSUPPORTED for 0/1 inputs.
+ *
+ * mad_pipeline_run: one whole pass over the current contents of A and B:
+ * the tables, s diamonds (indices 0 .. s-1 of `seed`), Omega_t' and the
+ * exact rescore, with the same results as mad_build_tables, mad_sample,
+ * mad_topk and mad_rescore.  Asynchronous and free of host synchronisation
+ * and allocation, so it can be captured in a CUDA graph and replayed.
+ * out_dev: t pairs (device); counts_dev: two uint32 (device), the number
+ * of candidates and of results; cand_dev (optional, t' pairs, device):
+ * Omega_t'.  Errors found on the device (a compacted candidate list above
+ * 131072 entries, a hash probe limit) go to the device error word.
+ *
+ * mad_pipeline_status: synchronises, refreshes the host-side table scalars
+ * (mad_stats) and returns the status of the last run. */
+mad_status mad_pipeline_plan(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, uint64_t s,
+                             uint32_t tprime, uint32_t t, mad_stream stream);
+mad_status mad_pipeline_run(mad_ctx* ctx, uint64_t seed, mad_pair* out_dev, uint32_t* counts_dev,
+                            mad_pair* cand_dev, mad_stream stream);
+mad_status mad_pipeline_status(mad_ctx* ctx, mad_stream stream);
+
 /* Exact-computation comparator (Sec. 4.3) rebuilt for tensor cores: the t
  * pairs with the largest |a_i . b_j| by direct computation, for comparison
  * with diamond sampling.  A and B are cast to BF16 (K zero-padded to 64 or

@@ -34,6 +34,7 @@ EXPORTS = (
     "mad_debug_draws_list", "mad_export_x", "mad_export_table", "mad_rescore_noalloc",
     "mad_dense_topt", "mad_debug_dense_product", "mad_set_phase_events", "mad_mips_items",
     "mad_mips_plan", "mad_mips_run", "mad_budget_features", "mad_mlp_train", "mad_mlp_predict",
+    "mad_pipeline_plan", "mad_pipeline_run", "mad_pipeline_status",
 )
 MAD_BUDGET_FEATURES = 12
 MAD_MLP_HIDDEN = 64
@@ -100,6 +101,10 @@ def lib() -> ctypes.CDLL:
         L.mad_build_tables.argtypes = [P, ctypes.POINTER(mad_matrix), ctypes.POINTER(mad_matrix),
                                        u64, P]
         L.mad_sample.argtypes = [P, u64, u64, u64, P]
+        L.mad_pipeline_plan.argtypes = [P, ctypes.POINTER(mad_matrix), ctypes.POINTER(mad_matrix),
+                                        u64, u32, u32, P]
+        L.mad_pipeline_run.argtypes = [P, u64, P, P, P, P]
+        L.mad_pipeline_status.argtypes = [P, P]
         L.mad_reset_hash.argtypes = [P, P]
         L.mad_topk.argtypes = [P, u32, P, ctypes.POINTER(u32), P]
         L.mad_rescore.argtypes = [P, P, u32, u32, P, ctypes.POINTER(u32), P]
@@ -229,6 +234,29 @@ def mad_rescore(ctx, cand, ncand: int, t: int, out=None, stream=None):
     _check(lib().mad_rescore(ctx, _ptr(cand), ncand, t, _ptr(out), ctypes.byref(n),
                              _stream(stream)), "mad_rescore")
     return out, n.value
+
+
+def mad_pipeline_plan(ctx, A: mad_matrix, B: mad_matrix, s: int, tprime: int, t: int,
+                      stream=None) -> None:
+    """Fix the dense inputs, the budget s and t <= t' of the fused pass and
+    allocate everything it uses (synchronises)."""
+    _check(lib().mad_pipeline_plan(ctx, ctypes.byref(A), ctypes.byref(B), s, tprime, t,
+                                   _stream(stream)), "mad_pipeline_plan")
+
+
+def mad_pipeline_run(ctx, seed: int, out, counts, cand=None, stream=None) -> None:
+    """One fused pass (asynchronous; capturable in a CUDA graph).  out: t
+    pairs; counts: two uint32 on the device (an int32 CUDA tensor): the
+    candidate and result counts; cand: optional t' pairs receiving
+    Omega_t'."""
+    _check(lib().mad_pipeline_run(ctx, seed, _ptr(out), _ptr(counts),
+                                  _ptr(cand) if cand is not None else None, _stream(stream)),
+           "mad_pipeline_run")
+
+
+def mad_pipeline_status(ctx, stream=None) -> None:
+    """Wait for the last fused pass and raise MadError on a device error."""
+    _check(lib().mad_pipeline_status(ctx, _stream(stream)), "mad_pipeline_status")
 
 
 def mad_rescore_noalloc(A: mad_matrix, B: mad_matrix, cand, ncand: int, t: int, out=None,

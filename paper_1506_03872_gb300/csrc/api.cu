@@ -19,6 +19,7 @@ mad_status cuda_status(cudaError_t e) {
 
 mad_status ensure_scratch(mad_ctx* ctx, size_t bytes, cudaStream_t st) {
   if (bytes <= ctx->scratch_bytes) return MAD_OK;
+  if (ctx->scratch_fixed) return MAD_ERR_STATE;
   if (ctx->scratch) cudaFreeAsync(ctx->scratch, st);
   ctx->scratch = nullptr;
   ctx->scratch_bytes = 0;
@@ -63,18 +64,17 @@ void free_tables(mad_ctx* ctx, cudaStream_t st) {
   free_async(ctx->hkeys, st);
   free_async(ctx->hvals, st);
   free_async(ctx->hreg, st);
-  free_async(ctx->T1c, st);
-  free_async(ctx->TBc, st);
-  free_async(ctx->T1c2, st);
-  free_async(ctx->TBc2, st);
   free_async(ctx->T2g_ptr, st);
   free_async(ctx->T2g, st);
   free_async(ctx->T2g_sh, st);
   free_async(ctx->bloom, st);
   free_async(ctx->T1g, st);
-  free_async(ctx->TBg_ptr, st);
   free_async(ctx->TBg, st);
   free_async(ctx->TBg_sh, st);
+  free_async(ctx->pipe_buf, st);
+  free_async(ctx->pipe_scratch, st);
+  ctx->pipe_scratch_bytes = 0;
+  ctx->pipe = false;
   free_async(ctx->mips_s, st);
   free_async(ctx->mips_chunk_q, st);
   free_async(ctx->mips_chunk_l0, st);
@@ -91,13 +91,6 @@ mad_status alloc(mad_ctx* ctx, T*& p, size_t count, cudaStream_t st) {
   return cuda_status(cudaMallocFromPoolAsync((void**)&p, count * sizeof(T), ctx->pool, st));
 }
 
-mad_status device_error_status(uint32_t err) {
-  if (err & DERR_HASH_FULL) return MAD_ERR_HASH_FULL;
-  if (err & DERR_OVERFLOW) return MAD_ERR_OVERFLOW;
-  if (err & (DERR_SEARCH | DERR_SELECT)) return MAD_ERR_STATE;
-  if (err & DERR_EMPTY) return MAD_ERR_EMPTY;
-  return MAD_OK;
-}
 
 // Read the device scalars (synchronises the stream).
 mad_status read_scalars(mad_ctx* ctx, DevScalars* hs, cudaStream_t st) {
@@ -118,15 +111,186 @@ bool valid_csr(const mad_matrix* M) {
          M->cols > 0 && M->cols < (1ll << 31);
 }
 
+// Empty X.  When the region builder fills the dense regions, only the
+// overflow table is cleared and the regions are marked fresh (the builder
+// writes every region on its first pass); otherwise every slot is cleared.
+mad_status clear_x_slots(mad_ctx* ctx, cudaStream_t st) {
+  if (ctx->regioned && !(ctx->flags & MAD_GRAM)) {
+    ctx->x_fresh = true;
+    return clear_slots(ctx, ctx->hreg + ctx->m, hash_extent(ctx), st);
+  }
+  ctx->x_fresh = false;
+  return clear_slots(ctx, nullptr, hash_extent(ctx), st);
+}
+
 mad_status clear_hash(mad_ctx* ctx, cudaStream_t st) {
-  cudaMemsetAsync(ctx->hkeys, 0xFF, ctx->hcap * sizeof(unsigned long long), st);
-  cudaMemsetAsync(ctx->hvals, 0, ctx->hcap * sizeof(long long), st);
+  mad_status rs = clear_x_slots(ctx, st);
+  if (rs != MAD_OK) return rs;
   cudaMemsetAsync(&ctx->sc->inserted, 0, 5 * sizeof(unsigned long long), st);
   ctx->sampled = 0;
   return cuda_status(cudaGetLastError());
 }
 
 }  // namespace
+
+namespace mad {
+
+mad_status device_error_status(uint32_t err) {
+  if (err & DERR_HASH_FULL) return MAD_ERR_HASH_FULL;
+  if (err & DERR_OVERFLOW) return MAD_ERR_OVERFLOW;
+  if (err & (DERR_SEARCH | DERR_SELECT)) return MAD_ERR_STATE;
+  if (err & DERR_EMPTY) return MAD_ERR_EMPTY;
+  return MAD_OK;
+}
+
+// Shapes, formats and flags accepted by the table build.
+mad_status check_inputs(const mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B,
+                        uint64_t s_max, bool* dense_out) {
+  if (!A || !B || s_max == 0 || s_max > (1ull << 60)) return MAD_ERR_ARG;
+  if (B->rows != A->cols) return MAD_ERR_ARG;
+  if (A->rows >= (1ll << 32) - 1 || B->cols >= (1ll << 32) - 1) return MAD_ERR_ARG;
+  if ((ctx->flags & MAD_GRAM) && A->rows != B->cols) return MAD_ERR_ARG;  // B = A^T
+  const bool dense = A->fmt == MAD_DENSE_ROWMAJOR && B->fmt == MAD_DENSE_ROWMAJOR;
+  const bool csr = A->fmt == MAD_CSR && B->fmt == MAD_CSR;
+  if (dense) {
+    if (!valid_dense(A) || !valid_dense(B)) return MAD_ERR_ARG;
+    if (A->cols > 1024) return MAD_ERR_UNSUPPORTED;
+  } else if (csr) {
+    if (!valid_csr(A) || !valid_csr(B)) return MAD_ERR_ARG;
+  } else {
+    return MAD_ERR_UNSUPPORTED;
+  }
+  // The squared symmetric update (Sec. 3.2.3) is built for 0/1 Gram inputs.
+  if ((ctx->flags & MAD_SQUARE_SYM) && (!csr || !(ctx->flags & MAD_GRAM)))
+    return MAD_ERR_UNSUPPORTED;
+  *dense_out = dense;
+  return MAD_OK;
+}
+
+// Frees the previous tables and allocates the new ones: every table whose
+// size follows from the shapes (for 0/1 inputs, after reading nnz), the
+// guides of T1 and of the dense TB rows at their largest size, and the
+// hash when its capacity is known before sampling (dense home regions sized
+// for s_max, or an explicit capacity).
+mad_status alloc_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, uint64_t s_max,
+                        bool dense, cudaStream_t st) {
+  free_tables(ctx, st);
+  ctx->A = *A;
+  ctx->B = *B;
+  ctx->dense = dense;
+  ctx->integer = !dense;
+  ctx->m = A->rows;
+  ctx->d = A->cols;
+  ctx->n = B->cols;
+  ctx->s_max = s_max;
+  ctx->sampled = 0;
+  mad_status rs = MAD_OK;
+  if (!dense) {
+    int64_t na = 0, nb = 0;
+    cudaMemcpyAsync(&na, A->rowptr + A->rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&nb, B->rowptr + B->rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    rs = cuda_status(cudaStreamSynchronize(st));
+    if (rs != MAD_OK) return rs;
+    if (na <= 0 || nb <= 0) return MAD_ERR_EMPTY;
+    ctx->nnz_a = (uint64_t)na;
+    ctx->nnz_b = (uint64_t)nb;
+    if ((rs = alloc(ctx, ctx->T2, ctx->nnz_a, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->r64, (size_t)ctx->m, st)) != MAD_OK) return rs;
+  } else {
+    ctx->nnz_a = (uint64_t)(ctx->m * ctx->d);
+    ctx->nnz_b = (uint64_t)(ctx->d * ctx->n);
+    const size_t eb = B->dt == MAD_F64 ? 8 : 4;
+    if ((rs = alloc(ctx, ctx->T2, ctx->nnz_a, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->TA, ctx->nnz_a, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->TB, ctx->nnz_b, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->na, (size_t)ctx->m, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->r, (size_t)ctx->m, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->nb, (size_t)ctx->d, st)) != MAD_OK) return rs;
+    char* bt = nullptr;
+    if ((rs = alloc(ctx, bt, (size_t)(ctx->n * ctx->d) * eb, st)) != MAD_OK) return rs;
+    ctx->bt = bt;
+    // Guides of the TB rows: the j search reads two guide entries and a
+    // short window of its row.
+    ctx->tbg_stride = ((int64_t)1 << tb_guide_width(ctx->n)) + 1;
+    if ((rs = alloc(ctx, ctx->TBg_sh, (size_t)ctx->d, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->TBg, (size_t)(ctx->d * ctx->tbg_stride), st)) != MAD_OK) return rs;
+  }
+  if ((rs = alloc(ctx, ctx->T1, (size_t)ctx->m, st)) != MAD_OK) return rs;
+  // Guide of T1: about m/4 power-of-two buckets over [0, total).
+  if ((rs = alloc(ctx, ctx->T1g, ((size_t)1 << t1_guide_width(ctx->m)) + 1, st)) != MAD_OK)
+    return rs;
+  // Dense inputs get a hash with per-row home regions (sized after T1);
+  // 0/1 inputs a plain power-of-two table sized from a pilot run of the
+  // sampler (their closure rate is unknown until sampled); an explicit
+  // capacity is taken as given.
+  ctx->regioned = dense && ctx->hcap_request == 0;
+  uint64_t cap = ctx->hcap_request;
+  if (ctx->regioned) {
+    cap = hash_region_bound((uint64_t)ctx->m, s_max);
+    if ((rs = alloc(ctx, ctx->hreg, (size_t)ctx->m + 2, st)) != MAD_OK) return rs;
+  }
+  if (cap) {
+    ctx->hcap = ctx->hcap_alloc = cap;
+    if ((rs = alloc(ctx, ctx->hkeys, cap, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->hvals, cap, st)) != MAD_OK) return rs;
+  }
+  return MAD_OK;
+}
+
+// The dense table build, enqueued without any wait for the device: tables,
+// home regions, guides, and an empty hash.
+mad_status enqueue_dense_build(mad_ctx* ctx, cudaStream_t st) {
+  cudaMemsetAsync(ctx->sc, 0, sizeof(DevScalars), st);
+  mad_status rs;
+  if ((rs = build_tables_impl(ctx, st)) != MAD_OK) return rs;
+  if (ctx->regioned && (rs = build_hash_regions(ctx, st)) != MAD_OK) return rs;
+  if ((rs = tb_guide_build(ctx, st)) != MAD_OK) return rs;
+  if ((rs = t1_guide_fill(ctx, st)) != MAD_OK) return rs;
+  return clear_x_slots(ctx, st);
+}
+
+// Host mirrors of the device scalars after a dense build (synchronises).
+mad_status finish_dense_build(mad_ctx* ctx, cudaStream_t st) {
+  DevScalars hs;
+  unsigned long long used = 0;
+  if (ctx->regioned)
+    cudaMemcpyAsync(&used, ctx->hreg + ctx->m + 1, sizeof(used), cudaMemcpyDeviceToHost, st);
+  mad_status rs = read_scalars(ctx, &hs, st);
+  if (rs != MAD_OK) return rs;
+  if (hs.err & DERR_OVERFLOW) return MAD_ERR_OVERFLOW;
+  if ((hs.err & DERR_EMPTY) || hs.maxr_bits == 0u || hs.maxb_bits == 0u) return MAD_ERR_EMPTY;
+  if (ctx->regioned) {
+    if (used == 0 || used > ctx->hcap_alloc) return MAD_ERR_STATE;
+    ctx->hcap = used;
+  }
+  ctx->f = hs.f_exp;
+  ctx->e1 = hs.e1;
+  ctx->t1g_sh = hs.t1g_sh;
+  ctx->t1_total = hs.t1_total;
+  return MAD_OK;
+}
+
+
+// Scratch of the dense table build: T1 chunk totals, then the home-region
+// sizes and their scan.
+size_t dense_build_scratch_bytes(const mad_ctx* ctx) {
+  const uint64_t m = (uint64_t)ctx->m;
+  const size_t chunks = (size_t)((m + 2047) / 2048) * sizeof(unsigned long long);
+  const size_t regions = (((m + 1) * sizeof(unsigned long long) + 255) & ~(size_t)255) +
+                         scan_partial_elems(m + 1) * 8;
+  return chunks > regions ? chunks : regions;
+}
+
+mad_status plan_dense_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B,
+                             uint64_t s_max, cudaStream_t st) {
+  bool dense = false;
+  mad_status rs = check_inputs(ctx, A, B, s_max, &dense);
+  if (rs != MAD_OK) return rs;
+  if (!dense) return MAD_ERR_UNSUPPORTED;
+  return alloc_tables(ctx, A, B, s_max, true, st);
+}
+
+}  // namespace mad
 
 extern "C" {
 
@@ -205,159 +369,45 @@ mad_status mad_set_hash_capacity(mad_ctx* ctx, uint64_t slots) {
 
 mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B,
                             uint64_t s_max, mad_stream stream) {
-  if (!ctx || !A || !B || s_max == 0 || s_max > (1ull << 60)) return MAD_ERR_ARG;
+  if (!ctx) return MAD_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  if (B->rows != A->cols) return MAD_ERR_ARG;
-  if (A->rows >= (1ll << 32) - 1 || B->cols >= (1ll << 32) - 1) return MAD_ERR_ARG;
-  if ((ctx->flags & MAD_GRAM) && A->rows != B->cols) return MAD_ERR_ARG;  // B = A^T
-  const bool dense = A->fmt == MAD_DENSE_ROWMAJOR && B->fmt == MAD_DENSE_ROWMAJOR;
-  const bool csr = A->fmt == MAD_CSR && B->fmt == MAD_CSR;
+  bool dense = false;
+  mad_status rs = check_inputs(ctx, A, B, s_max, &dense);
+  if (rs != MAD_OK) return rs;
+  if ((rs = alloc_tables(ctx, A, B, s_max, dense, st)) != MAD_OK) return rs;
   if (dense) {
-    if (!valid_dense(A) || !valid_dense(B)) return MAD_ERR_ARG;
-    if (A->cols > 1024) return MAD_ERR_UNSUPPORTED;
-  } else if (csr) {
-    if (!valid_csr(A) || !valid_csr(B)) return MAD_ERR_ARG;
-  } else {
-    return MAD_ERR_UNSUPPORTED;
+    if ((rs = enqueue_dense_build(ctx, st)) != MAD_OK) return rs;
+    if ((rs = finish_dense_build(ctx, st)) != MAD_OK) return rs;
+    ctx->built = true;
+    return MAD_OK;
   }
-  // The squared symmetric update (Sec. 3.2.3) is built for 0/1 Gram inputs.
-  if ((ctx->flags & MAD_SQUARE_SYM) && (!csr || !(ctx->flags & MAD_GRAM)))
-    return MAD_ERR_UNSUPPORTED;
-  free_tables(ctx, st);
-  ctx->A = *A;
-  ctx->B = *B;
-  ctx->dense = dense;
-  ctx->integer = csr;
-  ctx->m = A->rows;
-  ctx->d = A->cols;
-  ctx->n = B->cols;
-  ctx->s_max = s_max;
-  mad_status rs = MAD_OK;
-  if (csr) {
-    int64_t na = 0, nb = 0;
-    cudaMemcpyAsync(&na, A->rowptr + A->rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(&nb, B->rowptr + B->rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-    rs = cuda_status(cudaStreamSynchronize(st));
-    if (rs != MAD_OK) return rs;
-    if (na <= 0 || nb <= 0) return MAD_ERR_EMPTY;
-    ctx->nnz_a = (uint64_t)na;
-    ctx->nnz_b = (uint64_t)nb;
-    if ((rs = alloc(ctx, ctx->T2, ctx->nnz_a, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx, ctx->r64, (size_t)ctx->m, st)) != MAD_OK) return rs;
-  } else {
-    ctx->nnz_a = (uint64_t)(ctx->m * ctx->d);
-    ctx->nnz_b = (uint64_t)(ctx->d * ctx->n);
-    const size_t eb = B->dt == MAD_F64 ? 8 : 4;
-    if ((rs = alloc(ctx, ctx->T2, ctx->nnz_a, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx, ctx->TA, ctx->nnz_a, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx, ctx->TB, ctx->nnz_b, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx, ctx->na, (size_t)ctx->m, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx, ctx->r, (size_t)ctx->m, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx, ctx->nb, (size_t)ctx->d, st)) != MAD_OK) return rs;
-    char* bt = nullptr;
-    if ((rs = alloc(ctx, bt, (size_t)(ctx->n * ctx->d) * eb, st)) != MAD_OK) return rs;
-    ctx->bt = bt;
-  }
-  if ((rs = alloc(ctx, ctx->T1, (size_t)ctx->m, st)) != MAD_OK) return rs;
-  // Coarse search indices staged in shared memory by the sampling kernels:
-  // T1 in at most 16 KB, all rows of TB (dense) in at most 40 KB.
-  // Level-1 blocks hold at least 64 entries (whole 16-byte vectors at level 2).
-  ctx->t1c_lg = 6;
-  while ((((uint64_t)ctx->m + (1ull << ctx->t1c_lg) - 1) >> ctx->t1c_lg) * 8 > 16384) ++ctx->t1c_lg;
-  ctx->t1c_n = (int64_t)(((uint64_t)ctx->m + (1ull << ctx->t1c_lg) - 1) >> ctx->t1c_lg);
-  if ((rs = alloc(ctx, ctx->T1c, (size_t)ctx->t1c_n, st)) != MAD_OK) return rs;
-  if ((rs = alloc(ctx, ctx->T1c2, (size_t)(ctx->t1c_n << (ctx->t1c_lg - 4)), st)) != MAD_OK) return rs;
-  if (dense) {
-    ctx->tbc_lg = 6;
-    while ((uint64_t)ctx->d * ((((uint64_t)ctx->n + (1ull << ctx->tbc_lg) - 1) >> ctx->tbc_lg)) * 4 >
-           40960)
-      ++ctx->tbc_lg;
-    ctx->tbc_n = (int64_t)(((uint64_t)ctx->n + (1ull << ctx->tbc_lg) - 1) >> ctx->tbc_lg);
-    if ((rs = alloc(ctx, ctx->TBc, (size_t)(ctx->d * ctx->tbc_n), st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx, ctx->TBc2, (size_t)(ctx->d * (ctx->tbc_n << (ctx->tbc_lg - 4))), st)) != MAD_OK)
-      return rs;
-  } else {
-    ctx->tbc_n = 0;
-  }
-  // Dense inputs get a hash with per-row home regions (sized after T1);
-  // 0/1 inputs a plain power-of-two table sized from a pilot run of the
-  // sampler (their closure rate is unknown until sampled); an explicit
-  // capacity is taken as given.
-  ctx->regioned = dense && ctx->hcap_request == 0;
-  const bool pilot = !ctx->regioned && ctx->hcap_request == 0;
-  uint64_t cap = ctx->hcap_request;
-  if (ctx->regioned) {
-    cap = hash_region_bound((uint64_t)ctx->m, s_max);
-    if ((rs = alloc(ctx, ctx->hreg, (size_t)ctx->m + 1, st)) != MAD_OK) return rs;
-  }
-  if (!pilot) {
-    ctx->hcap = ctx->hcap_alloc = cap;
-    if ((rs = alloc(ctx, ctx->hkeys, cap, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx, ctx->hvals, cap, st)) != MAD_OK) return rs;
-  }
+  const bool pilot = ctx->hcap_request == 0;
   cudaMemsetAsync(ctx->sc, 0, sizeof(DevScalars), st);
   if ((rs = build_tables_impl(ctx, st)) != MAD_OK) return rs;
-  if (ctx->regioned && (rs = build_hash_regions(ctx, st)) != MAD_OK) return rs;
   DevScalars hs;
-  if (ctx->regioned) {
-    unsigned long long used = 0;
-    cudaMemcpyAsync(&used, ctx->hreg + ctx->m, sizeof(used), cudaMemcpyDeviceToHost, st);
-    if ((rs = read_scalars(ctx, &hs, st)) != MAD_OK) return rs;
-    if (used == 0 || used > cap) return MAD_ERR_STATE;
-    ctx->hcap = used;
-  } else if ((rs = read_scalars(ctx, &hs, st)) != MAD_OK) {
-    return rs;
-  }
+  if ((rs = read_scalars(ctx, &hs, st)) != MAD_OK) return rs;
   if (hs.err & DERR_OVERFLOW) return MAD_ERR_OVERFLOW;
-  if (dense) {
-    // Guides of the TB rows: the j search reads two guide entries and a
-    // window instead of walking the coarse index levels.
-    if ((rs = alloc(ctx, ctx->TBg_ptr, (size_t)ctx->d + 1, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx, ctx->TBg_sh, (size_t)ctx->d, st)) != MAD_OK) return rs;
-    if ((rs = tb_guide_offsets(ctx, st)) != MAD_OK) return rs;
-    unsigned long long gtotal = 0;
-    cudaMemcpyAsync(&gtotal, ctx->TBg_ptr + ctx->d, sizeof(gtotal), cudaMemcpyDeviceToHost, st);
-    if ((rs = cuda_status(cudaStreamSynchronize(st))) != MAD_OK) return rs;
-    if ((rs = alloc(ctx, ctx->TBg, (size_t)gtotal, st)) != MAD_OK) return rs;
-    if (gtotal && (rs = tb_guide_fill(ctx, st)) != MAD_OK) return rs;
-  }
-  if (ctx->integer) {
-    if (hs.t1_total == 0) return MAD_ERR_EMPTY;
-    // Guides of the long T2 rows (the 0/1 sampler's k search).
-    if ((rs = alloc(ctx, ctx->T2g_ptr, (size_t)ctx->m + 1, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx, ctx->T2g_sh, (size_t)ctx->m, st)) != MAD_OK) return rs;
-    if ((rs = t2_guide_offsets(ctx, st)) != MAD_OK) return rs;
-    unsigned long long gtotal = 0;
-    cudaMemcpyAsync(&gtotal, ctx->T2g_ptr + ctx->m, sizeof(gtotal), cudaMemcpyDeviceToHost, st);
-    if ((rs = cuda_status(cudaStreamSynchronize(st))) != MAD_OK) return rs;
-    if ((rs = alloc(ctx, ctx->T2g, (size_t)gtotal, st)) != MAD_OK) return rs;
-    if (gtotal && (rs = t2_guide_fill(ctx, st)) != MAD_OK) return rs;
-    // Closure filter: 16 bits per entry, a power of two of 64-bit words.
-    const uint64_t nnz_c = (ctx->flags & MAD_GRAM) ? ctx->nnz_a : ctx->nnz_b;
-    ctx->bloom_lg = 10;
-    while (((1ull << ctx->bloom_lg) * 4ull) < nnz_c && ctx->bloom_lg < 40) ++ctx->bloom_lg;
-    if ((rs = alloc(ctx, ctx->bloom, (size_t)1 << ctx->bloom_lg, st)) != MAD_OK) return rs;
-    if ((rs = build_bloom(ctx, st)) != MAD_OK) return rs;
-    ctx->f = 0;
-    ctx->e1 = 0;
-  } else {
-    if (hs.maxr_bits == 0u || hs.maxb_bits == 0u) return MAD_ERR_EMPTY;
-    float maxb;
-    std::memcpy(&maxb, &hs.maxb_bits, sizeof(float));
-    ctx->f = 62 - ceil_log2(s_max) - (std::ilogb(maxb) + 1);
-    ctx->e1 = hs.e1;
-  }
+  if (hs.t1_total == 0) return MAD_ERR_EMPTY;
+  // Guides of the long T2 rows (the 0/1 sampler's k search).
+  if ((rs = alloc(ctx, ctx->T2g_ptr, (size_t)ctx->m + 1, st)) != MAD_OK) return rs;
+  if ((rs = alloc(ctx, ctx->T2g_sh, (size_t)ctx->m, st)) != MAD_OK) return rs;
+  if ((rs = t2_guide_offsets(ctx, st)) != MAD_OK) return rs;
+  unsigned long long gtotal = 0;
+  cudaMemcpyAsync(&gtotal, ctx->T2g_ptr + ctx->m, sizeof(gtotal), cudaMemcpyDeviceToHost, st);
+  if ((rs = cuda_status(cudaStreamSynchronize(st))) != MAD_OK) return rs;
+  if ((rs = alloc(ctx, ctx->T2g, (size_t)gtotal, st)) != MAD_OK) return rs;
+  if (gtotal && (rs = t2_guide_fill(ctx, st)) != MAD_OK) return rs;
+  // Closure filter: 16 bits per entry, a power of two of 64-bit words.
+  const uint64_t nnz_c = (ctx->flags & MAD_GRAM) ? ctx->nnz_a : ctx->nnz_b;
+  ctx->bloom_lg = 10;
+  while (((1ull << ctx->bloom_lg) * 4ull) < nnz_c && ctx->bloom_lg < 40) ++ctx->bloom_lg;
+  if ((rs = alloc(ctx, ctx->bloom, (size_t)1 << ctx->bloom_lg, st)) != MAD_OK) return rs;
+  if ((rs = build_bloom(ctx, st)) != MAD_OK) return rs;
+  ctx->f = 0;
+  ctx->e1 = 0;
   ctx->t1_total = hs.t1_total;
-  {
-    // Guide of T1: about m/4 power-of-two buckets over [0, total).
-    int bl_t = 0, bl_m = 0;
-    while (bl_t < 64 && ((hs.t1_total - 1) >> bl_t)) ++bl_t;
-    while (bl_m < 63 && (((uint64_t)ctx->m / 4) >> bl_m)) ++bl_m;
-    ctx->t1g_sh = bl_t > bl_m ? bl_t - bl_m : 0;
-    const uint64_t nb = ((hs.t1_total - 1) >> ctx->t1g_sh) + 1;
-    if ((rs = alloc(ctx, ctx->T1g, (size_t)nb + 1, st)) != MAD_OK) return rs;
-    if ((rs = t1_guide_fill(ctx, nb, st)) != MAD_OK) return rs;
-  }
+  ctx->t1g_sh = hs.t1g_sh;
+  if ((rs = t1_guide_fill(ctx, st)) != MAD_OK) return rs;
   if (pilot) {
     // Fraction of diamonds that add to X, from kPilot diamonds of a fixed
     // seed; the table holds s_max times that fraction plus six standard
@@ -372,14 +422,13 @@ mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
     const double per = (ctx->flags & MAD_SQUARE_SYM) ? 2.0 : 1.0;  // inserts per diamond
     const double want = std::min(((double)s_max * std::min(f_hi, per) + 4096.0) * 16.0,
                                  per * (double)s_max / 0.6);
-    cap = 1024;
+    uint64_t cap = 1024;
     while ((double)cap < want && cap < (1ull << 40)) cap <<= 1;
     ctx->hcap = ctx->hcap_alloc = cap;
     if ((rs = alloc(ctx, ctx->hkeys, cap, st)) != MAD_OK) return rs;
     if ((rs = alloc(ctx, ctx->hvals, cap, st)) != MAD_OK) return rs;
   }
   if ((rs = clear_hash(ctx, st)) != MAD_OK) return rs;
-  ctx->t1_total = hs.t1_total;
   ctx->built = true;
   return MAD_OK;
 }
@@ -410,6 +459,11 @@ mad_status mad_topk(mad_ctx* ctx, uint32_t tprime, mad_pair* out_dev, uint32_t* 
   mad_status rs = read_scalars(ctx, &hs, st);
   if (rs != MAD_OK) return rs;
   if ((rs = device_error_status(hs.err)) != MAD_OK) return rs;
+  if (ctx->x_fresh) {   // nothing sampled since the last clear
+    ctx->positive = 0;
+    ctx->distinct = 0;
+    return MAD_OK;
+  }
   uint64_t bound = hs.new_keys < ctx->hcap ? hs.new_keys : ctx->hcap;
   if (tprime == 0 || bound == 0) return MAD_OK;
   if ((rs = ensure_scratch(ctx, select_ws_bytes(bound, tprime), st)) != MAD_OK) return rs;
@@ -522,6 +576,7 @@ mad_status mad_export_x(mad_ctx* ctx, uint64_t* keys_dev, int64_t* vals_dev, uin
   if (!ctx || !n_host || (cap && (!keys_dev || !vals_dev))) return MAD_ERR_ARG;
   *n_host = 0;
   if (!ctx->built) return MAD_ERR_STATE;
+  if (ctx->x_fresh) return MAD_OK;   // nothing sampled since the last clear
   cudaStream_t st = (cudaStream_t)stream;
   mad_status rs = ensure_scratch(ctx, 256, st);
   if (rs != MAD_OK) return rs;

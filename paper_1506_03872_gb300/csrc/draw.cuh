@@ -13,10 +13,9 @@ struct Draw {
   long long v;
 };
 
-// Center edge, stage 1: row i of A from T1 (through its coarse index when
-// it is staged in shared memory).
+// Center edge, stage 1: row i of A from T1 (through its guide when built).
 __device__ __forceinline__ int64_t draw_row_i(const SampleParams& p, unsigned long long u0,
-                                              bool* bad, const uint64_t* t1c = nullptr) {
+                                              bool* bad) {
   const unsigned long long target = draw_target(u0, p.t1_total);
   if (p.T1g) {
     const int64_t i = ub_guided_u64(p.T1, p.m, p.T1g, p.t1g_sh, target);
@@ -26,14 +25,12 @@ __device__ __forceinline__ int64_t draw_row_i(const SampleParams& p, unsigned lo
     }
     return i;
   }
-  if (t1c) return search3_u64(t1c, p.t1c_n, p.T1c2, p.T1, p.m, p.t1c_lg, target, bad);
   return search_u64(p.T1, p.m, target, bad);
 }
 
 // The rest of the loop body for a diamond whose row i is known.
 __device__ __forceinline__ Draw draw_given_row(const SampleParams& p, const Uniforms& u,
-                                               int64_t i, bool* bad,
-                                               const uint32_t* tbc = nullptr) {
+                                               int64_t i, bool* bad) {
   const uint32_t mask = p.integer ? 0xFFFFFFFFu : PREFIX_MASK;
   int64_t a0, alen;
   if (p.dense) {
@@ -87,12 +84,9 @@ __device__ __forceinline__ Draw draw_given_row(const SampleParams& p, const Unif
     const uint32_t tbtot = __ldg(p.TB + b0 + blen - 1) & mask;
     const uint32_t target = (uint32_t)draw_target(u.u2, tbtot);
     if (p.TBg) {
-      pj = ub_guided_u32(p.TB + b0, p.TBg + __ldg(p.TBg_ptr + k), (int)__ldg(p.TBg_sh + k), target,
+      pj = ub_guided_u32(p.TB + b0, p.TBg + k * p.tbg_stride, (int)__ldg(p.TBg_sh + k), target,
                          mask);
       if (pj >= blen) { *bad = true; pj = blen - 1; }
-    } else if (tbc) {
-      pj = search3_u32(tbc + k * p.tbc_n, p.tbc_n, p.TBc2 + k * (p.tbc_n << (p.tbc_lg - 4)),
-                       p.TB + b0, blen, p.tbc_lg, target, mask, bad);
     } else {
       pj = ub_u32(p.TB + b0, (int)blen, target, mask);
       if (pj >= blen) { *bad = true; pj = blen - 1; }
@@ -140,10 +134,9 @@ __device__ __forceinline__ Draw draw_given_row(const SampleParams& p, const Unif
 }
 
 __device__ __forceinline__ Draw draw_one(const SampleParams& p, unsigned long long seed,
-                                         unsigned long long ell, bool* bad,
-                                         const uint64_t* t1c = nullptr) {
+                                         unsigned long long ell, bool* bad) {
   const Uniforms u = diamond_uniforms(seed, ell);
-  return draw_given_row(p, u, draw_row_i(p, u.u0, bad, t1c), bad);
+  return draw_given_row(p, u, draw_row_i(p, u.u0, bad), bad);
 }
 
 }  // namespace mad

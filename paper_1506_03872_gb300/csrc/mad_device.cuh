@@ -172,191 +172,13 @@ __device__ __forceinline__ void ub2_u32(const uint32_t* __restrict__ P, const ui
   *oq = b;
 }
 
-// The same over a shared-memory (or generic) array.
-template <typename T>
-__device__ __forceinline__ int ub_plain(const T* P, int len, T target) {
-  int pos = 0;
-  for (int step = 1 << (31 - __clz(len)); step > 0; step >>= 1) {
-    const int np = pos + step;
-    const T v = P[(np <= len ? np : len) - 1];
-    pos = (np <= len && v <= target) ? np : pos;
-  }
-  return pos;
-}
-
-// Number of entries <= target among the n (<= 16) entries at p: the
-// position of the first entry above target.  Independent loads, one round
-// trip.
-__device__ __forceinline__ int count_le_16_u32(const uint32_t* __restrict__ p, int n,
-                                               uint32_t target, uint32_t mask) {
-  int c = 0;
-#pragma unroll
-  for (int q = 0; q < 16; ++q)
-    if (q < n) c += ((__ldg(p + q) & mask) <= target) ? 1 : 0;
-  return c;
-}
-
-__device__ __forceinline__ int count_le_16_u64(const uint64_t* __restrict__ p, int n,
-                                               unsigned long long target) {
-  int c = 0;
-#pragma unroll
-  for (int q = 0; q < 16; ++q)
-    if (q < n) c += (__ldg((const unsigned long long*)p + q) <= target) ? 1 : 0;
-  return c;
-}
-
-// Entries <= target in a window of w (a multiple of 4) 16-byte-aligned
-// uint32 entries, loaded as uint4 (padding entries hold 0xFFFFFFFF).
-__device__ __forceinline__ int count_le_vec_u32(const uint32_t* __restrict__ p, int w,
-                                                uint32_t target) {
-  int c = 0;
-  const uint4* v = (const uint4*)p;
-#pragma unroll 8
-  for (int q = 0; q < (w >> 2); ++q) {
-    const uint4 x = __ldg(v + q);
-    c += (x.x <= target) + (x.y <= target) + (x.z <= target) + (x.w <= target);
-  }
-  return c;
-}
-
-__device__ __forceinline__ int count_le_vec_u64(const uint64_t* __restrict__ p, int w,
-                                                unsigned long long target) {
-  int c = 0;
-  const ulonglong2* v = (const ulonglong2*)p;
-#pragma unroll 8
-  for (int q = 0; q < (w >> 1); ++q) {
-    const ulonglong2 x = __ldg(v + q);
-    c += (x.x <= target) + (x.y <= target);
-  }
-  return c;
-}
-
-// The same searches through a coarse index (coarse[g] = prefix entry
-// min((g+1) 2^lg, len) - 1): the block whose last entry first exceeds the
-// target holds the answer, so the result equals the full search.
-__device__ __forceinline__ int64_t search_coarse_u64(const uint64_t* coarse, int64_t nc,
-                                                     const uint64_t* __restrict__ prefix,
-                                                     int64_t len, int lg,
-                                                     unsigned long long target, bool* bad) {
-  int64_t lo = 0, hi = nc;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if ((unsigned long long)coarse[mid] > target)
-      hi = mid;
-    else
-      lo = mid + 1;
-  }
-  if (lo >= nc) {
-    *bad = true;
-    lo = nc - 1;
-  }
-  const int64_t base = lo << lg;
-  const int64_t wlen = (len - base) < (1ll << lg) ? (len - base) : (1ll << lg);
-  return base + search_u64(prefix + base, wlen, target, bad);
-}
-
-__device__ __forceinline__ int64_t search_coarse_u32(const uint32_t* coarse, int64_t nc,
-                                                     const uint32_t* __restrict__ prefix,
-                                                     int64_t len, int lg, uint32_t target,
-                                                     uint32_t mask, bool* bad) {
-  int64_t lo = 0, hi = nc;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (coarse[mid] > target)
-      hi = mid;
-    else
-      lo = mid + 1;
-  }
-  if (lo >= nc) {
-    *bad = true;
-    lo = nc - 1;
-  }
-  const int64_t base = lo << lg;
-  const int64_t wlen = (len - base) < (1ll << lg) ? (len - base) : (1ll << lg);
-  return base + search_u32(prefix + base, wlen, target, mask, bad);
-}
-
-// Three-level inverse-CDF search (same result as the full search):
-//   level 1 (shared memory): c1[g] = prefix entry min((g+1) 2^lg1, len) - 1;
-//   level 2 (global): c2[h] = prefix entry min((h+1) 16, len) - 1, rows
-//     padded to a multiple of 4 with 0xFFFFFFFF; the level-1 block holds
-//     2^lg1 / 16 consecutive level-2 entries, counted with vector loads;
-//   level 3: the 16 prefix entries of the level-2 block, counted.
-// Each of levels 2 and 3 costs one round trip of independent loads.
-__device__ __forceinline__ int64_t search3_u32(const uint32_t* c1, int64_t n1,
-                                               const uint32_t* __restrict__ c2,
-                                               const uint32_t* __restrict__ prefix, int64_t len,
-                                               int lg1, uint32_t target, uint32_t mask,
-                                               bool* bad) {
-  int lo = ub_plain<uint32_t>(c1, (int)n1, target);
-  if (lo >= (int)n1) {
-    *bad = true;
-    lo = (int)n1 - 1;
-  }
-  const int w2 = 1 << (lg1 - 4);
-  const int64_t h0 = (int64_t)lo * w2;
-  const int64_t h = h0 + count_le_vec_u32(c2 + h0, w2, target);
-  const int64_t base = h << 4;
-  const int64_t n3 = (len - base) < 16 ? (len - base) : 16;
-  if (n3 <= 0) {
-    *bad = true;
-    return len - 1;
-  }
-  int c;
-  if (n3 == 16 && (((uintptr_t)(prefix + base)) & 15u) == 0) {
-    const uint4* v = (const uint4*)(prefix + base);
-    c = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint4 x = __ldg(v + q);
-      c += ((x.x & mask) <= target) + ((x.y & mask) <= target) + ((x.z & mask) <= target) +
-           ((x.w & mask) <= target);
-    }
-  } else {
-    c = count_le_16_u32(prefix + base, (int)n3, target, mask);
-  }
-  if (c >= n3) {
-    *bad = true;
-    return base + n3 - 1;
-  }
-  return base + c;
-}
-
-__device__ __forceinline__ int64_t search3_u64(const uint64_t* c1, int64_t n1,
-                                               const uint64_t* __restrict__ c2,
-                                               const uint64_t* __restrict__ prefix, int64_t len,
-                                               int lg1, unsigned long long target, bool* bad) {
-  int lo = ub_plain<unsigned long long>((const unsigned long long*)c1, (int)n1, target);
-  if (lo >= (int)n1) {
-    *bad = true;
-    lo = (int)n1 - 1;
-  }
-  const int w2 = 1 << (lg1 - 4);
-  const int64_t h0 = (int64_t)lo * w2;
-  const int64_t h = h0 + count_le_vec_u64(c2 + h0, w2, target);
-  const int64_t base = h << 4;
-  const int64_t n3 = (len - base) < 16 ? (len - base) : 16;
-  if (n3 <= 0) {
-    *bad = true;
-    return len - 1;
-  }
-  int c;
-  if (n3 == 16) {
-    const ulonglong2* v = (const ulonglong2*)(prefix + base);
-    c = 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const ulonglong2 x = __ldg(v + q);
-      c += (x.x <= target) + (x.y <= target);
-    }
-  } else {
-    c = count_le_16_u64(prefix + base, (int)n3, target);
-  }
-  if (c >= n3) {
-    *bad = true;
-    return base + n3 - 1;
-  }
-  return base + c;
+// A length known only on the device: min(cap, *n_dev), or cap itself when
+// there is no device count.
+__device__ __forceinline__ unsigned long long dev_len(unsigned long long cap,
+                                                      const unsigned long long* n_dev) {
+  if (!n_dev) return cap;
+  const unsigned long long n = *n_dev;
+  return n < cap ? n : cap;
 }
 
 // 2^e as an FP32 value, -126 <= e <= 127.

@@ -38,6 +38,12 @@ struct DevScalars {
   unsigned long long distinct;     // occupied slots (compaction)
   unsigned long long positive;     // slots with x > 0 (compaction)
   unsigned long long maxp;         // largest select key (compaction)
+  // Derived from T1's total on the device, so that nothing between the
+  // table build and the sampler waits for the host:
+  int f_exp;                       // F of the dense increments
+  int t1g_sh;                      // bucket shift of T1's guide
+  int sort_shift;                  // bucket shift of the row-order sort
+  int pad2;
 };
 
 // Everything a sampling kernel needs, passed by value.
@@ -58,18 +64,6 @@ struct SampleParams {
   const uint32_t* TA;
   const uint32_t* TB;
   unsigned long long t1_total;
-  // Coarse indices (every 2^lg-th prefix entry) staged in shared memory by
-  // the row-ordered kernels: T1c over T1, TBc over each row of TB (dense).
-  const uint64_t* T1c;
-  int64_t t1c_n;
-  int t1c_lg;
-  const uint32_t* TBc;
-  int64_t tbc_n;                   // entries per row of B
-  int tbc_lg;
-  // Second level (every 16th entry, global, rows padded to whole level-1
-  // blocks with all-ones entries).
-  const uint64_t* T1c2;
-  const uint32_t* TBc2;
   // Guides of the long 0/1 T2 rows (null when absent): row i's guide is
   // T2g[T2g_ptr[i] .. T2g_ptr[i+1]) with bucket width 2^T2g_sh[i]; entry b
   // counts the row's prefix entries below b << T2g_sh[i].
@@ -84,20 +78,24 @@ struct SampleParams {
   // below b << t1g_sh.
   const uint32_t* T1g;
   int t1g_sh;
-  // Guides of the dense TB rows (null when absent).
-  const unsigned long long* TBg_ptr;
+  // Guides of the dense TB rows (null when absent): row k's guide starts
+  // at TBg + k * tbg_stride, bucket width 2^TBg_sh[k].
   const uint32_t* TBg;
+  int64_t tbg_stride;
   const uint8_t* TBg_sh;
   int f_exp;                       // F
   // Hash.  Regioned (dense inputs): the key (a, b) starts probing in the
   // home region of row a, [hreg[a], hreg[a+1]), sized from row a's expected
   // share of the diamonds; otherwise at mix(key) & hmask.  Probing is
-  // linear and wraps at hcap.
+  // linear and wraps at hcap (for regioned hashes, the end of the overflow
+  // table, read on the device and kept within the hcap_alloc allocated
+  // slots).
   unsigned long long* hkeys;
   long long* hvals;
   const unsigned long long* hreg;
   uint64_t hmask;
   uint64_t hcap;
+  uint64_t hcap_alloc;
   uint32_t max_probe;
   int regioned;
   // Modes.
@@ -148,10 +146,6 @@ struct mad_ctx {
   float* nb = nullptr;
   float* r = nullptr;
   unsigned long long* r64 = nullptr;
-  uint64_t* T1c = nullptr;          // coarse index of T1
-  uint32_t* TBc = nullptr;          // coarse index of each TB row (dense)
-  uint64_t* T1c2 = nullptr;         // second-level indices
-  uint32_t* TBc2 = nullptr;
   unsigned long long* T2g_ptr = nullptr;  // guides of long 0/1 T2 rows
   uint32_t* T2g = nullptr;
   uint8_t* T2g_sh = nullptr;
@@ -159,9 +153,20 @@ struct mad_ctx {
   int bloom_lg = 0;
   uint32_t* T1g = nullptr;                // guide of T1
   int t1g_sh = 0;
-  unsigned long long* TBg_ptr = nullptr;  // guides of the TB rows
-  uint32_t* TBg = nullptr;
+  uint32_t* TBg = nullptr;                // guides of the TB rows (fixed row stride)
+  int64_t tbg_stride = 0;
   uint8_t* TBg_sh = nullptr;
+  // Fused pass (mad_pipeline_*): budgets fixed when planned, one buffer
+  // for its selection lists.
+  bool pipe = false;
+  uint64_t pipe_s = 0;
+  uint32_t pipe_tprime = 0, pipe_t = 0;
+  void* pipe_buf = nullptr;
+  // The pass's own scratch (a captured run keeps its addresses however the
+  // context's shared scratch changes later).
+  void* pipe_scratch = nullptr;
+  size_t pipe_scratch_bytes = 0;
+  bool scratch_fixed = false;       // no reallocation while a pass is enqueued
   // Batched queries: the plan of the current batch.
   bool mips_items = false;
   uint32_t mips_nq = 0, mips_tprime = 0, mips_t = 0;
@@ -169,12 +174,15 @@ struct mad_ctx {
   unsigned long long* mips_s = nullptr;   // nq budgets
   uint32_t* mips_chunk_q = nullptr;       // query of each 256-diamond chunk
   uint32_t* mips_chunk_l0 = nullptr;      // its first diamond
-  int64_t t1c_n = 0, tbc_n = 0;
-  int t1c_lg = 0, tbc_lg = 0;
   void* bt = nullptr;               // dense B^T (n x d), the input dtype
   unsigned long long* hkeys = nullptr;
   long long* hvals = nullptr;
-  unsigned long long* hreg = nullptr;   // home regions (m + 1 offsets), dense inputs
+  // Dense inputs: row i's home region is [hreg[i], hreg[i+1]) (m + 2
+  // offsets); the overflow table [hreg[m], hreg[m+1]) follows the regions.
+  unsigned long long* hreg = nullptr;
+  // The regions hold nothing yet since the last clear (the region builder
+  // writes them all on its first pass; nothing may read them before).
+  bool x_fresh = false;
   bool regioned = false;
   uint64_t hcap = 0, hcap_alloc = 0, hcap_request = 0;
   mad::DevScalars* sc = nullptr;
@@ -213,19 +221,38 @@ mad_status t2_guide_offsets(mad_ctx* ctx, cudaStream_t st);
 // MAD_GRAM, else B) into ctx->bloom (2^bloom_lg words, cleared here).
 mad_status build_bloom(mad_ctx* ctx, cudaStream_t st);
 mad_status t2_guide_fill(mad_ctx* ctx, cudaStream_t st);
-// Batched queries: guides of the dense TB rows (offsets into ctx->TBg_ptr /
-// TBg_sh, d + 1 and d entries, total in TBg_ptr[d]; then the entries), the
-// item-side tables (TB, nb, maximum |b|, B^T) and the query rows (T2, TA).
-mad_status tb_guide_offsets(mad_ctx* ctx, cudaStream_t st);
-// Guide of T1 into ctx->T1g (nb + 1 entries for the shift ctx->t1g_sh).
-mad_status t1_guide_fill(mad_ctx* ctx, uint64_t nb, cudaStream_t st);
-mad_status tb_guide_fill(mad_ctx* ctx, cudaStream_t st);
+// Guides of the dense TB rows into ctx->TBg (d rows of ctx->tbg_stride =
+// 2^tb_guide_width(n) + 1 entries) and ctx->TBg_sh (d shifts).
+int tb_guide_width(int64_t n);
+mad_status tb_guide_build(mad_ctx* ctx, cudaStream_t st);
+// Guide of T1 into ctx->T1g, at most 2^t1_guide_width(m) + 1 entries; its
+// shift and length come from T1's total on the device.
+int t1_guide_width(int64_t m);
+mad_status t1_guide_fill(mad_ctx* ctx, cudaStream_t st);
+// Batched queries: the item-side tables (TB, nb, maximum |b|, B^T) and the
+// query rows (T2, TA).
 mad_status build_item_tables(mad_ctx* ctx, cudaStream_t st);
 mad_status build_query_rows(mad_ctx* ctx, cudaStream_t st);
 mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st);
+// Empties the hash slots [*lo_dev, min(bound, *hi_dev)) with bound =
+// hash_slot_bound(ctx) (0 without lo_dev, bound without hi_dev).
+mad_status clear_slots(mad_ctx* ctx, const unsigned long long* lo_dev,
+                       const unsigned long long* hi_dev, cudaStream_t st);
+// Overflow table of the dense hash: a power of two >= s_max / 8 + 4096.
+uint64_t overflow_slots(uint64_t s_max);
 // Home regions of the dense hash: sizes from T1 and s_max, then offsets.
 mad_status build_hash_regions(mad_ctx* ctx, cudaStream_t st);
 uint64_t hash_region_bound(uint64_t m, uint64_t s_max);
+// End of the dense hash on the device (regions and overflow table), else
+// null (the whole ctx->hcap).
+inline const unsigned long long* hash_extent(const mad_ctx* ctx) {
+  return ctx->regioned ? ctx->hreg + ctx->m + 1 : nullptr;
+}
+// Host-side bound on the slots a scan of the hash may touch: the
+// allocation for regioned hashes (their extent is read on the device).
+inline uint64_t hash_slot_bound(const mad_ctx* ctx) {
+  return ctx->regioned ? ctx->hcap_alloc : ctx->hcap;
+}
 // sample.cu
 // Diamonds among the first n of a fixed pilot seed that would add to X
 // (closed, nonzero, off-diagonal when excluded); synchronises.
@@ -259,6 +286,28 @@ mad_status select_from_hash(mad_ctx* ctx, const SelectWs& ws, uint64_t K, uint64
                             uint64_t* n_pos, cudaStream_t st);
 mad_status items_to_pairs(mad_ctx* ctx, const Item* items, uint64_t n, const mad_pair* cand,
                           const double* cvals, mad_pair* out, cudaStream_t st);
+// Device-driven selection: every length comes from device memory, so the
+// host enqueues the whole selection without waiting (CUDA-graph capturable).
+// The K largest of the first min(cap, *n_dev) items of `in` (cap <= 2^17)
+// are sorted into out[0..min(K, n)); sorted and pos hold cap entries.  When
+// over_err is given, a device length above cap sets DERR_SELECT there.
+void tile_select_dev(mad_ctx* ctx, const Item* in, uint64_t cap, uint64_t K,
+                     const unsigned long long* n_dev, unsigned int* over_err, Item* sorted,
+                     uint32_t* pos, Item* out, cudaStream_t st);
+constexpr uint64_t kDevSelectCap = 1ull << 17;
+size_t dev_select_state_bytes();
+// Omega_t' from the hash whose extent is *hcap_dev slots (at most
+// ctx->hcap): the positive x at or above the log-bucket threshold are
+// compacted into list (kDevSelectCap entries, count at *count), then the
+// K largest sorted into out.
+void select_hash_dev(mad_ctx* ctx, uint64_t K, const unsigned long long* hcap_dev, void* state,
+                     unsigned long long* count, Item* list, Item* sorted, uint32_t* pos,
+                     Item* out, cudaStream_t st);
+// out[q] for q < min(cap, *n_dev) as in items_to_pairs; *n_out gets that
+// length.
+void items_to_pairs_dev(mad_ctx* ctx, const Item* items, uint64_t cap,
+                        const unsigned long long* n_dev, const mad_pair* cand,
+                        const double* cvals, mad_pair* out, uint32_t* n_out, cudaStream_t st);
 int significant_bytes(unsigned long long maxp);
 mad_status export_x(mad_ctx* ctx, uint64_t* keys, int64_t* vals, uint64_t cap, uint64_t* n,
                     unsigned long long* counter, cudaStream_t st);
@@ -266,9 +315,24 @@ mad_status export_x(mad_ctx* ctx, uint64_t* keys, int64_t* vals, uint64_t cap, u
 mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, uint32_t t,
                             uint32_t rescore, mad_pair* out, uint32_t* n_out, float* dense_out,
                             cudaStream_t st);
+// api.cu
+// Status of the device error word (DERR_* bits).
+mad_status device_error_status(uint32_t err);
+// Input checks and allocation of the tables of a dense build (frees the
+// previous ones).
+mad_status plan_dense_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B,
+                             uint64_t s_max, cudaStream_t st);
+size_t dense_build_scratch_bytes(const mad_ctx* ctx);
+// The dense table build enqueued without waiting for the device, and the
+// host mirrors read afterwards (synchronises).
+mad_status enqueue_dense_build(mad_ctx* ctx, cudaStream_t st);
+mad_status finish_dense_build(mad_ctx* ctx, cudaStream_t st);
+// sample.cu: scratch of sample_impl for s diamonds.
+size_t sample_scratch_bytes(const mad_ctx* ctx, uint64_t s);
 // rescore.cu
 // Exact c for every candidate: items[q] = (bits |c|, key, q), cvals[q] = c.
+// With n_dev, the candidates are the first min(ncand, *n_dev).
 mad_status rescore_items(mad_ctx* ctx, const mad_pair* cand, uint64_t ncand, Item* items,
-                         double* cvals, cudaStream_t st);
+                         double* cvals, cudaStream_t st, const unsigned long long* n_dev = nullptr);
 
 }  // namespace mad

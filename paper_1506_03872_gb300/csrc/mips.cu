@@ -310,11 +310,14 @@ mad_status mad_mips_items(mad_ctx* ctx, const mad_matrix* B, uint64_t s_max, mad
   pool_free(ctx->T1, st); pool_free(ctx->T2, st); pool_free(ctx->TA, st); pool_free(ctx->TB, st);
   pool_free(ctx->na, st); pool_free(ctx->nb, st); pool_free(ctx->r, st); pool_free(ctx->r64, st);
   pool_free(ctx->bt, st); pool_free(ctx->hkeys, st); pool_free(ctx->hvals, st);
-  pool_free(ctx->hreg, st); pool_free(ctx->T1c, st); pool_free(ctx->TBc, st);
-  pool_free(ctx->T1c2, st); pool_free(ctx->TBc2, st); pool_free(ctx->T2g_ptr, st);
+  pool_free(ctx->hreg, st); pool_free(ctx->T2g_ptr, st);
   pool_free(ctx->T2g, st); pool_free(ctx->T2g_sh, st); pool_free(ctx->bloom, st);
-  pool_free(ctx->TBg_ptr, st); pool_free(ctx->TBg, st); pool_free(ctx->TBg_sh, st);
+  pool_free(ctx->TBg, st); pool_free(ctx->TBg_sh, st);
   pool_free(ctx->mips_s, st); pool_free(ctx->mips_chunk_q, st); pool_free(ctx->mips_chunk_l0, st);
+  pool_free(ctx->pipe_buf, st);
+  pool_free(ctx->pipe_scratch, st);
+  ctx->pipe_scratch_bytes = 0;
+  ctx->pipe = false;
   ctx->built = false;
   ctx->mips_items = false;
   ctx->mips_nq = 0;
@@ -326,27 +329,22 @@ mad_status mad_mips_items(mad_ctx* ctx, const mad_matrix* B, uint64_t s_max, mad
   ctx->n = B->cols;
   ctx->m = 0;
   ctx->s_max = s_max;
-  ctx->tbc_n = 0;
-  ctx->t1c_n = 0;
   mad_status rs;
   if ((rs = pool_alloc(ctx, ctx->TB, (size_t)(ctx->d * ctx->n), st)) != MAD_OK) return rs;
   if ((rs = pool_alloc(ctx, ctx->nb, (size_t)ctx->d, st)) != MAD_OK) return rs;
   char* bt = nullptr;
   if ((rs = pool_alloc(ctx, bt, (size_t)(ctx->n * ctx->d) * 4, st)) != MAD_OK) return rs;
   ctx->bt = bt;
-  if ((rs = pool_alloc(ctx, ctx->TBg_ptr, (size_t)ctx->d + 1, st)) != MAD_OK) return rs;
+  ctx->tbg_stride = ((int64_t)1 << tb_guide_width(ctx->n)) + 1;
   if ((rs = pool_alloc(ctx, ctx->TBg_sh, (size_t)ctx->d, st)) != MAD_OK) return rs;
+  if ((rs = pool_alloc(ctx, ctx->TBg, (size_t)(ctx->d * ctx->tbg_stride), st)) != MAD_OK) return rs;
   cudaMemsetAsync(ctx->sc, 0, sizeof(DevScalars), st);
   if ((rs = build_item_tables(ctx, st)) != MAD_OK) return rs;
-  if ((rs = tb_guide_offsets(ctx, st)) != MAD_OK) return rs;
-  unsigned long long gtotal = 0;
+  if ((rs = tb_guide_build(ctx, st)) != MAD_OK) return rs;
   DevScalars hs;
-  cudaMemcpyAsync(&gtotal, ctx->TBg_ptr + ctx->d, sizeof(gtotal), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&hs, ctx->sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
   if ((rs = cuda_status(cudaStreamSynchronize(st))) != MAD_OK) return rs;
   if (hs.maxb_bits == 0u) return MAD_ERR_EMPTY;
-  if ((rs = pool_alloc(ctx, ctx->TBg, (size_t)gtotal, st)) != MAD_OK) return rs;
-  if (gtotal && (rs = tb_guide_fill(ctx, st)) != MAD_OK) return rs;
   float maxb;
   std::memcpy(&maxb, &hs.maxb_bits, sizeof(float));
   int lgs = 0;

@@ -20,10 +20,11 @@ __device__ __forceinline__ double to_f64(double v) { return v; }
 
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(256)
-k_rescore_dense(const mad_pair* __restrict__ cand, unsigned long long ncand,
+k_rescore_dense(const mad_pair* __restrict__ cand, unsigned long long ncand_max,
                 const TA* __restrict__ A, int64_t lda, const TB* __restrict__ Bt, int64_t d,
                 int64_t m, int64_t n, double* __restrict__ cvals, Item* __restrict__ items,
-                DevScalars* sc) {
+                DevScalars* sc, const unsigned long long* n_dev) {
+  const unsigned long long ncand = dev_len(ncand_max, n_dev);
   const int lane = threadIdx.x & 31;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -59,11 +60,12 @@ k_rescore_dense(const mad_pair* __restrict__ cand, unsigned long long ncand,
 }
 
 __global__ void __launch_bounds__(256)
-k_rescore_binary(const mad_pair* __restrict__ cand, unsigned long long ncand,
+k_rescore_binary(const mad_pair* __restrict__ cand, unsigned long long ncand_max,
                  const int64_t* __restrict__ a_ptr, const int32_t* __restrict__ a_col,
                  const int64_t* __restrict__ b_ptr, const int32_t* __restrict__ b_col, int64_t m,
                  int64_t n, double* __restrict__ cvals, Item* __restrict__ items,
-                 DevScalars* sc) {
+                 DevScalars* sc, const unsigned long long* n_dev) {
+  const unsigned long long ncand = dev_len(ncand_max, n_dev);
   const int lane = threadIdx.x & 31;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -116,10 +118,11 @@ __device__ __forceinline__ int ceil_log2_i(int64_t v) {
 }
 
 __global__ void __launch_bounds__(256)
-k_rescore_gram_binary(const mad_pair* __restrict__ cand, unsigned long long ncand,
+k_rescore_gram_binary(const mad_pair* __restrict__ cand, unsigned long long ncand_max,
                       const int64_t* __restrict__ a_ptr, const int32_t* __restrict__ a_col,
                       int64_t m, double* __restrict__ cvals, Item* __restrict__ items,
-                      DevScalars* sc) {
+                      DevScalars* sc, const unsigned long long* n_dev) {
+  const unsigned long long ncand = dev_len(ncand_max, n_dev);
   const int lane = threadIdx.x & 31;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -192,36 +195,36 @@ k_rescore_gram_binary(const mad_pair* __restrict__ cand, unsigned long long ncan
 
 template <typename TA, typename TB>
 void launch_dense(mad_ctx* ctx, const mad_pair* cand, uint64_t ncand, Item* items, double* cvals,
-                  cudaStream_t st) {
+                  const unsigned long long* n_dev, cudaStream_t st) {
   const unsigned long long blocks = (ncand * 32 + 255) / 256;
   k_rescore_dense<TA, TB><<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(
       cand, ncand, (const TA*)ctx->A.values, ctx->A.ld, (const TB*)ctx->bt, ctx->d, ctx->m, ctx->n,
-      cvals, items, ctx->sc);
+      cvals, items, ctx->sc, n_dev);
   count_launch(ctx);
 }
 
 }  // namespace
 
 mad_status rescore_items(mad_ctx* ctx, const mad_pair* cand, uint64_t ncand, Item* items,
-                         double* cvals, cudaStream_t st) {
+                         double* cvals, cudaStream_t st, const unsigned long long* n_dev) {
   if (ncand == 0) return MAD_OK;
   if (ctx->integer && (ctx->flags & MAD_GRAM)) {
     const unsigned long long blocks = (ncand * 32 + 255) / 256;
     k_rescore_gram_binary<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(
-        cand, ncand, ctx->A.rowptr, ctx->A.colidx, ctx->m, cvals, items, ctx->sc);
+        cand, ncand, ctx->A.rowptr, ctx->A.colidx, ctx->m, cvals, items, ctx->sc, n_dev);
     count_launch(ctx);
   } else if (ctx->integer) {
     const unsigned long long blocks = (ncand * 32 + 255) / 256;
     k_rescore_binary<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(
         cand, ncand, ctx->A.rowptr, ctx->A.colidx, ctx->B.rowptr, ctx->B.colidx, ctx->m, ctx->n,
-        cvals, items, ctx->sc);
+        cvals, items, ctx->sc, n_dev);
     count_launch(ctx);
   } else {
     const bool a64 = ctx->A.dt == MAD_F64, b64 = ctx->B.dt == MAD_F64;
-    if (a64 && b64) launch_dense<double, double>(ctx, cand, ncand, items, cvals, st);
-    else if (a64) launch_dense<double, float>(ctx, cand, ncand, items, cvals, st);
-    else if (b64) launch_dense<float, double>(ctx, cand, ncand, items, cvals, st);
-    else launch_dense<float, float>(ctx, cand, ncand, items, cvals, st);
+    if (a64 && b64) launch_dense<double, double>(ctx, cand, ncand, items, cvals, n_dev, st);
+    else if (a64) launch_dense<double, float>(ctx, cand, ncand, items, cvals, n_dev, st);
+    else if (b64) launch_dense<float, double>(ctx, cand, ncand, items, cvals, n_dev, st);
+    else launch_dense<float, float>(ctx, cand, ncand, items, cvals, n_dev, st);
   }
   return cuda_status(cudaGetLastError());
 }

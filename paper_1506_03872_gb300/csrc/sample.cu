@@ -27,6 +27,21 @@
 namespace mad {
 namespace {
 
+// The scalars derived from T1's total on the device (and, for the dense
+// hash, the end of its home regions), read once per thread, so that no
+// host round trip separates the table build from the sampler.
+__device__ __forceinline__ SampleParams resolve(const SampleParams& p) {
+  SampleParams q = p;
+  q.t1_total = p.sc->t1_total;
+  q.t1g_sh = p.sc->t1g_sh;
+  q.f_exp = p.sc->f_exp;
+  if (p.regioned) {
+    const unsigned long long used = p.hreg[p.m + 1];
+    q.hcap = used < p.hcap_alloc ? used : p.hcap_alloc;
+  }
+  return q;
+}
+
 // Per-lane bookkeeping of the sampling kernels.
 struct Tally {
   unsigned long long inserted = 0, diag = 0, created = 0;
@@ -85,13 +100,9 @@ __device__ __forceinline__ void flush_tally(const SampleParams& p, Tally& t) {
 
 // Diamonds in index order (0/1 CSR inputs).
 __global__ void __launch_bounds__(256)
-k_sample(const SampleParams p, unsigned long long seed, unsigned long long first,
+k_sample(const SampleParams p_, unsigned long long seed, unsigned long long first,
          unsigned long long s) {
-  // With a T1 guide the row search needs no staged coarse index.
-  extern __shared__ uint64_t t1c[];
-  const int64_t nt1c = p.T1g ? 0 : p.t1c_n;
-  for (int64_t g = threadIdx.x; g < nt1c; g += blockDim.x) t1c[g] = p.T1c[g];
-  __syncthreads();
+  const SampleParams p = resolve(p_);
   const int lane = threadIdx.x & 31;
   const unsigned long long warp_id = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -99,7 +110,7 @@ k_sample(const SampleParams p, unsigned long long seed, unsigned long long first
   for (unsigned long long base = warp_id * 32; base < s; base += warps * 32) {
     const unsigned long long q = base + lane;
     Draw dr{};
-    if (q < s) dr = draw_one(p, seed, first + q, &t.bad, t1c);
+    if (q < s) dr = draw_one(p, seed, first + q, &t.bad);
     accumulate(p, q < s, dr, t);
   }
   flush_tally(p, t);
@@ -111,9 +122,11 @@ k_sample(const SampleParams p, unsigned long long seed, unsigned long long first
 // bucket order is row order; the search itself is left to the draw kernel,
 // where neighbouring diamonds search the same few lines of T1.
 __global__ void __launch_bounds__(256)
-k_bucket_count(unsigned long long t1_total, int shift, unsigned long long seed,
+k_bucket_count(const DevScalars* __restrict__ sc, unsigned long long seed,
                unsigned long long first, unsigned long long s, unsigned int* __restrict__ cnt,
                unsigned long long* __restrict__ rec) {
+  const unsigned long long t1_total = sc->t1_total;
+  const int shift = sc->sort_shift;
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < s;
        q += (unsigned long long)gridDim.x * blockDim.x) {
@@ -143,14 +156,10 @@ k_bucket_scatter(const unsigned long long* __restrict__ rec, const unsigned int*
 // nothing: v = 0 or an excluded diagonal) and its increment over sorted[q]
 // (each thread rewrites only the entry it read).  k_insert adds them to X.
 __global__ void __launch_bounds__(256, 5)
-k_sample_sorted(const SampleParams p, unsigned long long seed, unsigned long long first,
+k_sample_sorted(const SampleParams p_, unsigned long long seed, unsigned long long first,
                 unsigned long long s, unsigned long long* __restrict__ sorted,
                 unsigned long long* __restrict__ keys) {
-  // With TB guides the j search needs no staged coarse index.
-  extern __shared__ uint32_t tbc[];
-  const int64_t ntbc = p.TBg ? 0 : p.d * p.tbc_n;
-  for (int64_t g = threadIdx.x; g < ntbc; g += blockDim.x) tbc[g] = p.TBc[g];
-  __syncthreads();
+  const SampleParams p = resolve(p_);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   bool bad = false;
   unsigned long long diag = 0;
@@ -158,8 +167,8 @@ k_sample_sorted(const SampleParams p, unsigned long long seed, unsigned long lon
        q += stride) {
     const unsigned long long e = sorted[q];
     const Uniforms u = diamond_uniforms(seed, first + (uint32_t)e);
-    const int64_t i = draw_row_i(p, u.u0, &bad, p.T1c);   // guided when p.T1g is set
-    const Draw dr = draw_given_row(p, u, i, &bad, p.TBg ? nullptr : tbc);
+    const int64_t i = draw_row_i(p, u.u0, &bad);
+    const Draw dr = draw_given_row(p, u, i, &bad);
     unsigned long long key = EMPTY_KEY;
     if ((p.flags & MAD_EXCLUDE_DIAG) && dr.i == dr.j) {
       ++diag;
@@ -187,8 +196,9 @@ k_sample_sorted(const SampleParams p, unsigned long long seed, unsigned long lon
 // many inserts are in flight at once; consecutive entries share row i and
 // hence its hash region.
 __global__ void __launch_bounds__(256, 6)
-k_insert(const SampleParams p, const unsigned long long* __restrict__ keys,
+k_insert(const SampleParams p_, const unsigned long long* __restrict__ keys,
          const long long* __restrict__ vals, unsigned long long s) {
+  const SampleParams p = resolve(p_);
   Tally t;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -213,12 +223,132 @@ k_insert(const SampleParams p, const unsigned long long* __restrict__ keys,
   flush_tally(p, t);
 }
 
-// Diagnostic twin of k_sample: writes each diamond's draws instead of
+// X update for the row-ordered diamonds when every key (i, j) belongs to
+// its diamond's row i (dense inputs without MAD_GRAM): one warp per row
+// builds the row's home region in shared memory and writes the whole region
+// to the hash with plain stores, so the inserts need no global atomics and
+// the regions no separate clearing.  Row i's diamonds are the records in
+// the buckets its target range [T1[i-1], T1[i]) covers (records of other
+// rows in shared boundary buckets are skipped).  A key that finds its
+// region full goes to the overflow table after the regions (global
+// atomics); regions above kSlab slots are filled in place with global
+// atomics.  `fresh`: no region holds anything yet (first batch after a
+// clear), so every region is written, also when empty; otherwise a row
+// with records merges them into its region.
+constexpr int kSlab = 512;          // slots of one warp's shared-memory region
+constexpr int kRowWarps = 8;
+constexpr size_t kRowsSmem = (size_t)kRowWarps * kSlab * 16;
+
+__device__ __forceinline__ int overflow_add(const SampleParams& p, uint64_t lo, uint64_t hi,
+                                            unsigned long long key, long long v) {
+  const uint64_t home = lo + (mix64(key) & (hi - lo - 1));
+  return hash_add_from(p.hkeys, p.hvals, lo, hi, home, (uint32_t)(hi - lo < 4096 ? hi - lo : 4096),
+                       key, v);
+}
+
+__global__ void __launch_bounds__(256)
+k_insert_rows(const SampleParams p_, const unsigned long long* __restrict__ keys,
+              const long long* __restrict__ vals, const uint32_t* __restrict__ off, int fresh) {
+  const SampleParams p = resolve(p_);
+  extern __shared__ unsigned long long slab[];   // kRowWarps x (kSlab keys, kSlab values)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long* sk = slab + (size_t)w * 2 * kSlab;
+  long long* sv = (long long*)(sk + kSlab);
+  const int shift = p.sc->sort_shift;
+  const uint64_t ovf_hi = p.hcap;   // the end of the table (kept within the allocation)
+  const uint64_t ovf_lo = p.hreg[p.m] < ovf_hi ? p.hreg[p.m] : ovf_hi;
+  Tally t;
+  // Regions past the allocation (never, by the bound on the region sizes)
+  // would be reported as a full hash, not written.
+  if (p.hreg[p.m + 1] > p.hcap_alloc || ovf_hi - ovf_lo < 4) {
+    if (threadIdx.x == 0) atomicOr(&p.sc->err, DERR_HASH_FULL);
+    return;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * kRowWarps + w; i < p.m;
+       i += (int64_t)gridDim.x * kRowWarps) {
+    const unsigned long long t0 = i ? __ldg((const unsigned long long*)p.T1 + i - 1) : 0ull;
+    const unsigned long long t1 = __ldg((const unsigned long long*)p.T1 + i);
+    const uint64_t r0 = p.hreg[i], S = p.hreg[i + 1] - r0;   // a power of two >= 4
+    uint32_t q0 = 0, q1 = 0;
+    if (t1 > t0) {
+      q0 = __ldg(off + (t0 >> shift));
+      q1 = __ldg(off + ((t1 - 1) >> shift) + 1);
+    }
+    if (q1 == q0 && !fresh) continue;
+    const unsigned long long row = (unsigned long long)i;
+    if (S <= (uint64_t)kSlab) {
+      for (uint32_t x = lane; x < S; x += 32) {
+        sk[x] = fresh ? EMPTY_KEY : p.hkeys[r0 + x];
+        sv[x] = fresh ? 0 : p.hvals[r0 + x];
+      }
+      __syncwarp();
+      for (uint32_t base = q0; base < q1; base += 32) {
+        const uint32_t q = base + lane;
+        const unsigned long long key = q < q1 ? __ldcs(keys + q) : EMPTY_KEY;
+        if (key == EMPTY_KEY || (key >> 32) != row) continue;
+        const long long v = __ldcs(vals + q);
+        ++t.inserted;
+        uint32_t slot = (uint32_t)(mix64(key) & (S - 1));
+        bool done = false;
+        for (uint32_t probe = 0; probe < S && !done; ++probe) {
+          const unsigned long long cur = ((volatile unsigned long long*)sk)[slot];
+          if (cur == EMPTY_KEY || cur == key) {
+            const unsigned long long prev =
+                cur == key ? key : atomicCAS(sk + slot, EMPTY_KEY, key);
+            if (prev == EMPTY_KEY || prev == key) {
+              atomicAdd((unsigned long long*)sv + slot, (unsigned long long)v);
+              if (prev == EMPTY_KEY) ++t.created;
+              done = true;
+              continue;
+            }
+          }
+          slot = (slot + 1) & (uint32_t)(S - 1);
+        }
+        if (!done) {
+          const int res = overflow_add(p, ovf_lo, ovf_hi, key, v);
+          if (res == 0) t.full = true;
+          if (res == 2) ++t.created;
+        }
+      }
+      __syncwarp();
+      for (uint32_t x = lane; x < S; x += 32) {
+        p.hkeys[r0 + x] = sk[x];
+        p.hvals[r0 + x] = sv[x];
+      }
+      __syncwarp();
+    } else {
+      if (fresh) {
+        for (uint64_t x = lane; x < S; x += 32) {
+          p.hkeys[r0 + x] = EMPTY_KEY;
+          p.hvals[r0 + x] = 0;
+        }
+        __threadfence();
+        __syncwarp();
+      }
+      for (uint32_t base = q0; base < q1; base += 32) {
+        const uint32_t q = base + lane;
+        const unsigned long long key = q < q1 ? __ldcs(keys + q) : EMPTY_KEY;
+        if (key == EMPTY_KEY || (key >> 32) != row) continue;
+        const long long v = __ldcs(vals + q);
+        ++t.inserted;
+        int res = hash_add_from(p.hkeys, p.hvals, r0, r0 + S, r0 + (mix64(key) & (S - 1)),
+                                (uint32_t)(S < 4096 ? S : 4096), key, v);
+        if (res == 0) res = overflow_add(p, ovf_lo, ovf_hi, key, v);
+        if (res == 0) t.full = true;
+        if (res == 2) ++t.created;
+      }
+    }
+  }
+  flush_tally(p, t);
+}
+
+// Diagnostic twin of k_sample: writes each diamond's draws instead of// Diagnostic twin of k_sample: writes each diamond's draws instead of
 // accumulating them.
 __global__ void __launch_bounds__(256)
-k_draws(const SampleParams p, unsigned long long seed, unsigned long long first,
+k_draws(const SampleParams p_, unsigned long long seed, unsigned long long first,
         const unsigned long long* __restrict__ ells, unsigned long long count, uint32_t* oi,
         uint32_t* ok, uint32_t* oj, uint32_t* okp, long long* ov) {
+  const SampleParams p = resolve(p_);
   bool bad = false;
   for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < count;
        q += (unsigned long long)gridDim.x * blockDim.x) {
@@ -233,15 +363,20 @@ k_draws(const SampleParams p, unsigned long long seed, unsigned long long first,
   if (bad) atomicOr(&p.sc->err, DERR_SEARCH);
 }
 
-template <typename K>
-int full_grid(K kernel, size_t smem = 0) {
+// Resident 256-thread blocks of `kernel` on the whole GPU (queried once
+// per kernel; one process drives one device).
+template <auto kernel>
+int full_grid() {
+  static int cached = 0;
+  if (cached) return cached;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
-  return sms * per_sm;
+  cached = sms * per_sm;
+  return cached;
 }
 
 unsigned grid_of(unsigned long long work, int full) {
@@ -254,8 +389,9 @@ constexpr unsigned long long kSortBatch = 1ull << 26;
 
 // Pilot for hash sizing: counts the diamonds that would be inserted.
 __global__ void __launch_bounds__(256)
-k_pilot(const SampleParams p, unsigned long long seed, unsigned long long n,
+k_pilot(const SampleParams p_, unsigned long long seed, unsigned long long n,
         unsigned long long* __restrict__ hits) {
+  const SampleParams p = resolve(p_);
   bool bad = false;
   unsigned long long c = 0;
   for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
@@ -296,14 +432,6 @@ SampleParams make_params(const mad_ctx* ctx) {
   p.TA = ctx->TA;
   p.TB = ctx->TB;
   p.t1_total = ctx->t1_total;
-  p.T1c = ctx->T1c;
-  p.t1c_n = ctx->t1c_n;
-  p.t1c_lg = ctx->t1c_lg;
-  p.TBc = ctx->TBc;
-  p.tbc_n = ctx->tbc_n;
-  p.tbc_lg = ctx->tbc_lg;
-  p.T1c2 = ctx->T1c2;
-  p.TBc2 = ctx->TBc2;
   p.T1g = ctx->T1g;
   p.t1g_sh = ctx->t1g_sh;
   p.T2g_ptr = ctx->T2g_ptr;
@@ -311,8 +439,8 @@ SampleParams make_params(const mad_ctx* ctx) {
   p.T2g_sh = ctx->T2g_sh;
   p.bloom = ctx->bloom;
   p.bloom_shift = 64 - ctx->bloom_lg;
-  p.TBg_ptr = ctx->TBg_ptr;
   p.TBg = ctx->TBg;
+  p.tbg_stride = ctx->tbg_stride;
   p.TBg_sh = ctx->TBg_sh;
   p.f_exp = ctx->f;
   p.hkeys = ctx->hkeys;
@@ -320,6 +448,7 @@ SampleParams make_params(const mad_ctx* ctx) {
   p.hreg = ctx->hreg;
   p.hmask = ctx->hcap - 1;
   p.hcap = ctx->hcap;
+  p.hcap_alloc = ctx->hcap_alloc;
   p.max_probe = (uint32_t)(ctx->hcap < 4096 ? ctx->hcap : 4096);
   p.regioned = ctx->regioned ? 1 : 0;
   p.dense = ctx->dense ? 1 : 0;
@@ -337,7 +466,7 @@ mad_status pilot_inserts(mad_ctx* ctx, uint64_t n, uint64_t* hits, cudaStream_t 
   unsigned long long* dev = (unsigned long long*)ctx->scratch;
   cudaMemsetAsync(dev, 0, sizeof(unsigned long long), st);
   const SampleParams p = make_params(ctx);
-  k_pilot<<<grid_of(n, full_grid(k_pilot)), 256, 0, st>>>(p, 0x9E3779B97F4A7C15ull, n, dev);
+  k_pilot<<<grid_of(n, full_grid<k_pilot>()), 256, 0, st>>>(p, 0x9E3779B97F4A7C15ull, n, dev);
   count_launch(ctx);
   unsigned long long h = 0;
   cudaMemcpyAsync(&h, dev, sizeof(h), cudaMemcpyDeviceToHost, st);
@@ -347,40 +476,56 @@ mad_status pilot_inserts(mad_ctx* ctx, uint64_t n, uint64_t* hits, cudaStream_t 
   return MAD_OK;
 }
 
+uint64_t sort_buckets(int64_t m) {
+  uint64_t nbk = 1;
+  while (nbk < (uint64_t)m) nbk <<= 1;
+  return nbk;
+}
+
+size_t sample_scratch_bytes(const mad_ctx* ctx, uint64_t s) {
+  if (!ctx->dense || s == 0) return 0;
+  const uint64_t nbk = sort_buckets(ctx->m);
+  const uint64_t batch = s < kSortBatch ? s : kSortBatch;
+  const size_t cnt_bytes = ((nbk + 1) * sizeof(uint32_t) + 255) & ~(size_t)255;
+  const size_t part_bytes = (scan_partial_elems(nbk) * sizeof(uint32_t) + 255) & ~(size_t)255;
+  return 2 * cnt_bytes + part_bytes + 2 * batch * sizeof(unsigned long long);
+}
+
 mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, cudaStream_t st) {
   if (s == 0) return MAD_OK;
   const SampleParams p = make_params(ctx);
-  const size_t smem_t1c = p.T1g ? 0 : (size_t)p.t1c_n * sizeof(uint64_t);
   if (!ctx->dense) {
     phase_event(ctx, 0, st);
     phase_event(ctx, 1, st);
-    k_sample<<<grid_of(s, full_grid(k_sample, smem_t1c)), 256, smem_t1c, st>>>(p, seed, first, s);
+    k_sample<<<grid_of(s, full_grid<k_sample>()), 256, 0, st>>>(p, seed, first, s);
     count_launch(ctx);
     phase_event(ctx, 2, st);
     phase_event(ctx, 3, st);
     return cuda_status(cudaGetLastError());
   }
-  const size_t smem_tbc = p.TBg ? 0 : (size_t)(p.d * p.tbc_n) * sizeof(uint32_t);
-  static bool attrs = false;
-  if (!attrs) {
-    cudaFuncSetAttribute(k_sample_sorted, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
-    attrs = true;
+  const int full_count = full_grid<k_bucket_count>();
+  const int full_sorted = full_grid<k_sample_sorted>();
+  const int full_insert = full_grid<k_insert>();
+  // Keys of row i only (no Gram reordering): the region builder.
+  const bool by_rows = ctx->regioned && !(ctx->flags & MAD_GRAM);
+  static int rows_grid = 0;
+  if (by_rows && !rows_grid) {
+    cudaFuncSetAttribute(k_insert_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowsSmem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_insert_rows, 256, kRowsSmem) !=
+            cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    rows_grid = sms * per_sm;
   }
-  const int full_count = full_grid(k_bucket_count);
-  const int full_sorted = full_grid(k_sample_sorted, smem_tbc);
-  const int full_insert = full_grid(k_insert);
-  // Buckets of 2^shift target values, at most 2^ceil(log2 m) of them.
-  int lgm = 0;
-  while ((1ull << lgm) < (uint64_t)ctx->m) ++lgm;
-  int lgt = 0;
-  while (lgt < 64 && (ctx->t1_total - 1) >> lgt) ++lgt;
-  const int shift = lgt > lgm ? lgt - lgm : 0;
-  const uint64_t nbk = ((ctx->t1_total - 1) >> shift) + 1;
+  // Buckets of 2^sort_shift target values (the shift comes from T1's total
+  // on the device), at most 2^ceil(log2 m) of them.
+  const uint64_t nbk = sort_buckets(ctx->m);
   const uint64_t batch = s < kSortBatch ? s : kSortBatch;
   const size_t cnt_bytes = ((nbk + 1) * sizeof(uint32_t) + 255) & ~(size_t)255;
   const size_t part_bytes = (scan_partial_elems(nbk) * sizeof(uint32_t) + 255) & ~(size_t)255;
-  const size_t rec_bytes = batch * sizeof(unsigned long long);
-  mad_status rs = ensure_scratch(ctx, 2 * cnt_bytes + part_bytes + 2 * rec_bytes, st);
+  mad_status rs = ensure_scratch(ctx, sample_scratch_bytes(ctx, s), st);
   if (rs != MAD_OK) return rs;
   char* base = (char*)ctx->scratch;
   uint32_t* cnt = (uint32_t*)base;
@@ -392,16 +537,23 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
     const uint64_t n = (s - done) < batch ? (s - done) : batch;
     phase_event(ctx, 0, st);
     cudaMemsetAsync(cnt, 0, nbk * sizeof(uint32_t), st);
-    k_bucket_count<<<grid_of(n, full_count), 256, 0, st>>>(ctx->t1_total, shift, seed,
-                                                           first + done, n, cnt, rec);
+    k_bucket_count<<<grid_of(n, full_count), 256, 0, st>>>(ctx->sc, seed, first + done, n, cnt,
+                                                           rec);
     count_launch(ctx);
     if ((rs = scan_exclusive_u32(ctx, cnt, off, nbk, part, st)) != MAD_OK) return rs;
     k_bucket_scatter<<<grid_of(n, full_count), 256, 0, st>>>(rec, off, n, sorted);
     phase_event(ctx, 1, st);
-    k_sample_sorted<<<grid_of(n, full_sorted), 256, smem_tbc, st>>>(p, seed, first + done, n,
-                                                                    sorted, rec);
+    k_sample_sorted<<<grid_of(n, full_sorted), 256, 0, st>>>(p, seed, first + done, n, sorted,
+                                                             rec);
     phase_event(ctx, 2, st);
-    k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, rec, (const long long*)sorted, n);
+    if (by_rows) {
+      const int64_t blocks = (ctx->m + kRowWarps - 1) / kRowWarps;
+      k_insert_rows<<<(unsigned)(blocks < rows_grid ? blocks : rows_grid), 256, kRowsSmem, st>>>(
+          p, rec, (const long long*)sorted, off, ctx->x_fresh ? 1 : 0);
+      ctx->x_fresh = false;
+    } else {
+      k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, rec, (const long long*)sorted, n);
+    }
     phase_event(ctx, 3, st);
     count_launch(ctx, 3);
   }

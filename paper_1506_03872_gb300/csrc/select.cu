@@ -171,8 +171,9 @@ k_collect(const Item* __restrict__ l0, unsigned long long n, const SelState* st,
 // items (all of the top K) pass and few more do.
 
 __global__ void __launch_bounds__(256)
-k_log_hist(const long long* __restrict__ vals, uint64_t cap, unsigned long long K,
-           SelState* st) {
+k_log_hist(const long long* __restrict__ vals, uint64_t cap_max, unsigned long long K,
+           SelState* st, const unsigned long long* cap_dev) {
+  const uint64_t cap = dev_len(cap_max, cap_dev);
   __shared__ unsigned int h[1024];
   for (int b = threadIdx.x; b < 1024; b += blockDim.x) h[b] = 0;
   __syncthreads();
@@ -224,8 +225,9 @@ k_log_hist(const long long* __restrict__ vals, uint64_t cap, unsigned long long 
 
 __global__ void __launch_bounds__(256)
 k_compact_ge(const unsigned long long* __restrict__ keys, const long long* __restrict__ vals,
-             uint64_t cap, const SelState* st, Item* __restrict__ out, uint64_t out_cap,
-             unsigned long long* counter) {
+             uint64_t cap_max, const SelState* st, Item* __restrict__ out, uint64_t out_cap,
+             unsigned long long* counter, const unsigned long long* cap_dev) {
+  const uint64_t cap = dev_len(cap_max, cap_dev);
   const unsigned long long theta = st->theta;
   constexpr int U = 4;   // independent loads in flight per thread
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -269,11 +271,17 @@ __device__ __forceinline__ bool item_before(unsigned long long ap, unsigned long
 }
 
 __global__ void __launch_bounds__(1024)
-k_tile_sort(const Item* __restrict__ in, unsigned n, unsigned K, Item* __restrict__ out,
-            uint32_t* __restrict__ pos_out) {
+k_tile_sort(const Item* __restrict__ in, unsigned n_max, unsigned K, Item* __restrict__ out,
+            uint32_t* __restrict__ pos_out, const unsigned long long* n_dev,
+            unsigned int* over_err) {
   __shared__ unsigned long long sp[kTile], sk[kTile];
   __shared__ uint32_t si[kTile];
+  // Under a device count: a list longer than the workspace is reported.
+  if (over_err && blockIdx.x == 0 && threadIdx.x == 0 && *n_dev > n_max)
+    atomicOr(over_err, DERR_SELECT);
+  const unsigned n = (unsigned)dev_len(n_max, n_dev);
   const unsigned base = blockIdx.x * kTile;
+  if (base >= n) return;
   const unsigned len = min(kTile, n - base);
   for (unsigned r = threadIdx.x; r < kTile; r += blockDim.x) {
     if (r < len) {
@@ -313,8 +321,9 @@ k_tile_sort(const Item* __restrict__ in, unsigned n, unsigned K, Item* __restric
 }
 
 __global__ void __launch_bounds__(256)
-k_merge_rank(const Item* __restrict__ tiles, const uint32_t* __restrict__ pos, unsigned n, unsigned K,
-             Item* __restrict__ out) {
+k_merge_rank(const Item* __restrict__ tiles, const uint32_t* __restrict__ pos, unsigned n_max,
+             unsigned K, Item* __restrict__ out, const unsigned long long* n_dev) {
+  const unsigned n = (unsigned)dev_len(n_max, n_dev);
   const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= n) return;
   const unsigned my_tile = x / kTile, r = x % kTile;
@@ -347,14 +356,16 @@ void tile_select(mad_ctx* ctx, const SelectWs& ws, const Item* in, uint64_t n, u
                  cudaStream_t st) {
   const unsigned tiles = (unsigned)((n + kTile - 1) / kTile);
   if (tiles == 1 && in != ws.out) {
-    k_tile_sort<<<1, kTile / 2, 0, st>>>(in, (unsigned)n, (unsigned)K, ws.out, nullptr);
+    k_tile_sort<<<1, kTile / 2, 0, st>>>(in, (unsigned)n, (unsigned)K, ws.out, nullptr, nullptr,
+                                         nullptr);
     count_launch(ctx);
     return;
   }
   uint32_t* pos = (uint32_t*)ws.l2;
-  k_tile_sort<<<tiles, kTile / 2, 0, st>>>(in, (unsigned)n, (unsigned)K, ws.l1, pos);
+  k_tile_sort<<<tiles, kTile / 2, 0, st>>>(in, (unsigned)n, (unsigned)K, ws.l1, pos, nullptr,
+                                            nullptr);
   k_merge_rank<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws.l1, pos, (unsigned)n, (unsigned)K,
-                                                            ws.out);
+                                                            ws.out, nullptr);
   count_launch(ctx, 2);
 }
 
@@ -423,10 +434,13 @@ __global__ void k_pad(Item* data, unsigned long long from, unsigned long long to
   }
 }
 
-__global__ void k_to_pairs(const Item* __restrict__ items, unsigned long long n,
+__global__ void k_to_pairs(const Item* __restrict__ items, unsigned long long n_max,
                            const mad_pair* __restrict__ cand, const double* __restrict__ cvals,
-                           mad_pair* __restrict__ out) {
+                           mad_pair* __restrict__ out, const unsigned long long* n_dev,
+                           uint32_t* n_out) {
+  const unsigned long long n = dev_len(n_max, n_dev);
   const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n_out && t == 0) *n_out = (uint32_t)n;
   if (t >= n) return;
   const Item it = items[t];
   mad_pair pr;
@@ -546,10 +560,12 @@ mad_status select_from_hash(mad_ctx* ctx, const SelectWs& ws, uint64_t K, uint64
   SelState* dst = (SelState*)ws.state;
   cudaMemsetAsync(dst, 0, sizeof(SelState), st);
   cudaMemsetAsync(ws.counter, 0, sizeof(unsigned long long), st);
-  const unsigned blocks = grid_for(ctx->hcap, 152 * 8);
-  k_log_hist<<<blocks, 256, 0, st>>>(ctx->hvals, ctx->hcap, K, dst);
-  k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, ctx->hcap, dst, ws.l0, ws.cap_n,
-                                       ws.counter);
+  const uint64_t bound = hash_slot_bound(ctx);
+  const unsigned blocks = grid_for(bound, 152 * 8);
+  const unsigned long long* extent = hash_extent(ctx);
+  k_log_hist<<<blocks, 256, 0, st>>>(ctx->hvals, bound, K, dst, extent);
+  k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, bound, dst, ws.l0, ws.cap_n,
+                                       ws.counter, extent);
   count_launch(ctx, 2);
   unsigned long long host[2] = {0, 0};
   cudaMemcpyAsync(&host[0], ws.counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
@@ -566,16 +582,53 @@ mad_status select_from_hash(mad_ctx* ctx, const SelectWs& ws, uint64_t K, uint64
 mad_status items_to_pairs(mad_ctx* ctx, const Item* items, uint64_t n, const mad_pair* cand,
                           const double* cvals, mad_pair* out, cudaStream_t st) {
   if (n == 0) return MAD_OK;
-  k_to_pairs<<<grid_for(n, 1u << 30), 256, 0, st>>>(items, n, cand, cvals, out);
+  k_to_pairs<<<grid_for(n, 1u << 30), 256, 0, st>>>(items, n, cand, cvals, out, nullptr, nullptr);
   count_launch(ctx);
   return cuda_status(cudaGetLastError());
+}
+
+void tile_select_dev(mad_ctx* ctx, const Item* in, uint64_t cap, uint64_t K,
+                     const unsigned long long* n_dev, unsigned int* over_err, Item* sorted,
+                     uint32_t* pos, Item* out, cudaStream_t st) {
+  const unsigned tiles = (unsigned)((cap + kTile - 1) / kTile);
+  k_tile_sort<<<tiles, kTile / 2, 0, st>>>(in, (unsigned)cap, (unsigned)K, sorted, pos, n_dev,
+                                            over_err);
+  k_merge_rank<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(sorted, pos, (unsigned)cap,
+                                                              (unsigned)K, out, n_dev);
+  count_launch(ctx, 2);
+}
+
+size_t dev_select_state_bytes() { return ((sizeof(SelState) + 255) / 256) * 256; }
+
+void select_hash_dev(mad_ctx* ctx, uint64_t K, const unsigned long long* hcap_dev, void* state,
+                     unsigned long long* count, Item* list, Item* sorted, uint32_t* pos,
+                     Item* out, cudaStream_t st) {
+  SelState* dst = (SelState*)state;
+  cudaMemsetAsync(dst, 0, sizeof(SelState), st);
+  cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+  const uint64_t bound = hash_slot_bound(ctx);
+  const unsigned blocks = grid_for(bound, 152 * 8);
+  k_log_hist<<<blocks, 256, 0, st>>>(ctx->hvals, bound, K, dst, hcap_dev);
+  k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, bound, dst, list,
+                                       kDevSelectCap, count, hcap_dev);
+  count_launch(ctx, 2);
+  tile_select_dev(ctx, list, kDevSelectCap, K, count, &ctx->sc->err, sorted, pos, out, st);
+}
+
+void items_to_pairs_dev(mad_ctx* ctx, const Item* items, uint64_t cap,
+                        const unsigned long long* n_dev, const mad_pair* cand,
+                        const double* cvals, mad_pair* out, uint32_t* n_out, cudaStream_t st) {
+  k_to_pairs<<<grid_for(cap ? cap : 1, 1u << 30), 256, 0, st>>>(items, cap, cand, cvals, out,
+                                                                 n_dev, n_out);
+  count_launch(ctx);
 }
 
 // Every occupied key with its value (diagnostics).
 __global__ void __launch_bounds__(256)
 k_export(const unsigned long long* __restrict__ keys, const long long* __restrict__ vals,
-         uint64_t cap, unsigned long long* __restrict__ ok, long long* __restrict__ ov,
-         uint64_t out_cap, unsigned long long* counter) {
+         uint64_t cap_max, unsigned long long* __restrict__ ok, long long* __restrict__ ov,
+         uint64_t out_cap, unsigned long long* counter, const unsigned long long* cap_dev) {
+  const uint64_t cap = dev_len(cap_max, cap_dev);
   for (uint64_t slot = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < cap;
        slot += (uint64_t)gridDim.x * blockDim.x) {
     const unsigned long long key = keys[slot];
@@ -591,9 +644,11 @@ k_export(const unsigned long long* __restrict__ keys, const long long* __restric
 mad_status export_x(mad_ctx* ctx, uint64_t* keys, int64_t* vals, uint64_t cap, uint64_t* n,
                     unsigned long long* counter, cudaStream_t st) {
   cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
-  k_export<<<grid_for(ctx->hcap, 152 * 8), 256, 0, st>>>(ctx->hkeys, ctx->hvals, ctx->hcap,
+  k_export<<<grid_for(hash_slot_bound(ctx), 152 * 8), 256, 0, st>>>(ctx->hkeys, ctx->hvals,
+                                                                    hash_slot_bound(ctx),
                                                          (unsigned long long*)keys,
-                                                         (long long*)vals, cap, counter);
+                                                         (long long*)vals, cap, counter,
+                                                         hash_extent(ctx));
   count_launch(ctx);
   unsigned long long cnt = 0;
   cudaMemcpyAsync(&cnt, counter, sizeof(cnt), cudaMemcpyDeviceToHost, st);

@@ -153,6 +153,110 @@ k_b_rows_dense(const T* __restrict__ B, int64_t n, int64_t ldb, float* __restric
   }
 }
 
+// Rows of dense B with 1024 threads per row, the same results as
+// k_b_rows_dense.  Sums: tiles of 4096 entries are loaded by all threads
+// (four independent loads each; the next tile's are issued before the
+// current one is used) and staged in shared memory, where the 256 canonical
+// partial sums advance in index order.  Table: four consecutive entries per
+// thread, quantised and scanned across the block, the next tile prefetched.
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_b_rows_wide(const T* __restrict__ B, int64_t n, int64_t ldb, float* __restrict__ nb,
+              uint32_t* __restrict__ TB, DevScalars* sc) {
+  constexpr int kTileB = 4096;
+  __shared__ float tile[kTileB];
+  __shared__ float part[256];
+  __shared__ uint32_t wsum[33];
+  const int64_t k = blockIdx.x;
+  const T* __restrict__ row = B + k * ldb;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  float acc = 0.0f, mx = 0.0f;
+  float cur[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int64_t idx = t + 1024 * r;
+    cur[r] = idx < n ? fabsf(to_f32(row[idx])) : 0.0f;
+  }
+  for (int64_t base = 0; base < n; base += kTileB) {
+    float nxt[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      tile[t + 1024 * r] = cur[r];
+      mx = fmaxf(mx, cur[r]);
+      const int64_t idx = base + kTileB + t + 1024 * r;
+      nxt[r] = idx < n ? fabsf(to_f32(row[idx])) : 0.0f;
+    }
+    __syncthreads();
+    if (t < 256) {
+      const int64_t len = (n - base) < kTileB ? (n - base) : kTileB;
+#pragma unroll
+      for (int j = 0; j < kTileB / 256; ++j) {
+        const int idx = t + 256 * j;
+        if (idx < len) acc = __fadd_rn(acc, tile[idx]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) cur[r] = nxt[r];
+  }
+  if (t < 256) part[t] = acc;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+  if (lane == 0 && mx > 0.0f) atomicMax(&sc->maxb_bits, __float_as_uint(mx));
+  __syncthreads();
+  for (int h = 128; h >= 1; h >>= 1) {
+    if (t < h) part[t] = __fadd_rn(part[t], part[t + h]);
+    __syncthreads();
+  }
+  const float total = part[0];
+  if (t == 0) nb[k] = total;
+
+  uint32_t* __restrict__ out = TB + k * n;
+  const int e = total > 0.0f ? 29 - ilogb_pos(total) : 0;
+  float v[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int64_t idx = 4 * t + c;
+    v[c] = idx < n ? to_f32(row[idx]) : 0.0f;
+  }
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < n; base += kTileB) {
+    float vn[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t idx = base + kTileB + 4 * t + c;
+      vn[c] = idx < n ? to_f32(row[idx]) : 0.0f;
+    }
+    uint32_t q[4], local = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t idx = base + 4 * t + c;
+      if (idx < n && total > 0.0f) local += quantize_row(fabsf(v[c]), e);
+      q[c] = local;
+    }
+    const uint32_t inc = warp_inclusive_u32(local, lane);
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t x = wsum[lane];
+      const uint32_t xi = warp_inclusive_u32(x, lane);
+      wsum[lane] = xi - x;
+      if (lane == 31) wsum[32] = xi;
+    }
+    __syncthreads();
+    const uint32_t off = carry + wsum[warp] + inc - local;
+    carry += wsum[32];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t idx = base + 4 * t + c;
+      if (idx < n) out[idx] = (off + q[c]) | (v[c] < 0.0f ? SIGN_BIT : 0u);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = vn[c];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Rows of dense A: ||a_i*||_1, s_i, r_i, T2, TA.  One warp per row; the
 // 256 canonical partials live 8 per lane (partial L + 32c in slot c).
@@ -238,6 +342,121 @@ k_a_rows_dense(const T* __restrict__ A, int64_t m, int64_t d, int64_t lda,
       c2 += __shfl_sync(0xFFFFFFFFu, i2, 31);
       ca += __shfl_sync(0xFFFFFFFFu, ia, 31);
     }
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1)
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xFFFFFFFFu, rmax, off));
+  if (lane == 0 && rmax > 0.0f) atomicMax(&sc->maxr_bits, __float_as_uint(rmax));
+}
+
+// Rows of dense A with d <= 256, the same results as k_a_rows_dense: each
+// canonical partial then holds at most one entry, so lane L keeps entries
+// L + 32c (c < 8) in registers for both the sums and the tables.  The next
+// row's entries are loaded before the current row is processed, and the
+// scans of the (at most eight) 32-entry chunks run side by side, their
+// carries added afterwards.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_a_rows_short(const T* __restrict__ A, int64_t m, int d, int64_t lda,
+               const float* __restrict__ nb_g, float* __restrict__ na_out,
+               float* __restrict__ r_out, uint32_t* __restrict__ T2, uint32_t* __restrict__ TA,
+               DevScalars* sc) {
+  __shared__ float nb[256];
+  for (int idx = threadIdx.x; idx < 256; idx += blockDim.x) nb[idx] = idx < d ? nb_g[idx] : 0.0f;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  float v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int idx = lane + 32 * c;
+    v[c] = (i < m && idx < d) ? to_f32(A[i * lda + idx]) : 0.0f;
+  }
+  float rmax = 0.0f;
+  for (; i < m; i += stride) {
+    const int64_t inext = i + stride;
+    float vn[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int idx = lane + 32 * c;
+      vn[c] = (inext < m && idx < d) ? to_f32(A[inext * lda + idx]) : 0.0f;
+    }
+    float pa[8], ps[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float a = fabsf(v[c]);
+      pa[c] = __fadd_rn(0.0f, a);
+      ps[c] = __fadd_rn(0.0f, __fmul_rn(a, nb[lane + 32 * c]));
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      pa[c] = __fadd_rn(pa[c], pa[c + 4]);
+      ps[c] = __fadd_rn(ps[c], ps[c + 4]);
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      pa[c] = __fadd_rn(pa[c], pa[c + 2]);
+      ps[c] = __fadd_rn(ps[c], ps[c + 2]);
+    }
+    float na = __fadd_rn(pa[0], pa[1]);
+    float s = __fadd_rn(ps[0], ps[1]);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      na = __fadd_rn(na, __shfl_xor_sync(0xFFFFFFFFu, na, off));
+      s = __fadd_rn(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
+    }
+    const float r = __fmul_rn(na, s);
+    if (lane == 0) {
+      na_out[i] = na;
+      r_out[i] = r;
+    }
+    rmax = fmaxf(rmax, r);
+    const bool live = s > 0.0f;
+    const int e2 = live ? 29 - ilogb_pos(s) : 0;
+    const int ea = live ? 29 - ilogb_pos(na) : 0;
+    uint32_t i2[8], ia[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int idx = lane + 32 * c;
+      uint32_t q2 = 0, qa = 0;
+      if (live && idx < d) {
+        const float a = fabsf(v[c]);
+        q2 = quantize_row(__fmul_rn(a, nb[idx]), e2);
+        qa = quantize_row(a, ea);
+      }
+      i2[c] = q2;
+      ia[c] = qa;
+    }
+    // Eight independent warp scans per table (interleaved by the unrolling).
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const uint32_t o2 = __shfl_up_sync(0xFFFFFFFFu, i2[c], off);
+        const uint32_t oa = __shfl_up_sync(0xFFFFFFFFu, ia[c], off);
+        if (lane >= off) {
+          i2[c] += o2;
+          ia[c] += oa;
+        }
+      }
+    }
+    uint32_t* __restrict__ o2 = T2 + i * d;
+    uint32_t* __restrict__ oa = TA + i * d;
+    uint32_t c2 = 0, ca = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int idx = lane + 32 * c;
+      const uint32_t sg = v[c] < 0.0f ? SIGN_BIT : 0u;
+      if (idx < d) {
+        o2[idx] = (c2 + i2[c]) | sg;
+        oa[idx] = (ca + ia[c]) | sg;
+      }
+      c2 += __shfl_sync(0xFFFFFFFFu, i2[c], 31);
+      ca += __shfl_sync(0xFFFFFFFFu, ia[c], 31);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = vn[c];
   }
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1)
@@ -381,21 +600,45 @@ k_t1_chunk_sums(const float* __restrict__ r, const unsigned long long* __restric
   if (blockIdx.x == 0 && threadIdx.x == 0 && !r64) sc->e1 = t1_exponent(sc, clog2m);
 }
 
+// One warp: exclusive offsets of the chunk totals and T1's total, then the
+// scalars the sampler derives from it: the bucket shifts of T1's guide
+// (about 2^bl_m buckets) and of the row-order sort (at most 2^lgm buckets),
+// and F = 62 - lg_s - (floor(log2 max |b|) + 1) for dense inputs.  The
+// total is exact when below 2^63: the high and low 32-bit halves of the
+// chunk totals are summed separately to detect a larger one.
 __global__ void k_t1_chunk_offsets(unsigned long long* __restrict__ partial, int64_t chunks,
-                                   DevScalars* sc) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  unsigned long long acc = 0;
-  bool over = false;
-  for (int64_t b = 0; b < chunks; ++b) {
-    const unsigned long long v = partial[b];
-    partial[b] = acc;
-    const unsigned long long nx = acc + v;
-    if (nx < acc) over = true;
-    acc = nx;
+                                   int bl_m, int lgm, int lg_s, int dense, DevScalars* sc) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32 || blockIdx.x != 0) return;
+  unsigned long long carry = 0, hi = 0, lo = 0;
+  for (int64_t base = 0; base < chunks; base += 32) {
+    const int64_t b = base + lane;
+    const unsigned long long v = b < chunks ? partial[b] : 0ull;
+    hi += v >> 32;
+    lo += v & 0xFFFFFFFFull;
+    const unsigned long long inc = warp_inclusive_u64(v, lane) + carry;
+    if (b < chunks) partial[b] = inc - v;
+    carry = __shfl_sync(0xFFFFFFFFu, inc, 31);
   }
-  if (over || acc >= (1ull << 63)) atomicOr(&sc->err, DERR_OVERFLOW);
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    hi += __shfl_xor_sync(0xFFFFFFFFu, hi, off);
+    lo += __shfl_xor_sync(0xFFFFFFFFu, lo, off);
+  }
+  if (lane != 0) return;
+  const unsigned long long acc = carry;
+  if (hi + (lo >> 32) >= (1ull << 31)) atomicOr(&sc->err, DERR_OVERFLOW);
   if (acc == 0ull) atomicOr(&sc->err, DERR_EMPTY);
   sc->t1_total = acc;
+  const int bl_t = acc > 1ull ? 64 - __clzll((long long)(acc - 1)) : 0;
+  sc->t1g_sh = bl_t > bl_m ? bl_t - bl_m : 0;
+  sc->sort_shift = bl_t > lgm ? bl_t - lgm : 0;
+  int f = 0;
+  if (dense) {
+    if (sc->maxb_bits == 0u || sc->maxr_bits == 0u) atomicOr(&sc->err, DERR_EMPTY);
+    else f = 62 - lg_s - (ilogb_pos(__uint_as_float(sc->maxb_bits)) + 1);
+  }
+  sc->f_exp = f;
 }
 
 __global__ void __launch_bounds__(256)
@@ -444,61 +687,30 @@ __global__ void k_transpose(const T* __restrict__ B, int64_t d, int64_t n, int64
   }
 }
 
-// Coarse indices for the sampling searches: every 2^lg-th prefix entry
-// (the last entry of each block).
-__global__ void k_coarse_u64(const uint64_t* __restrict__ T, int64_t len, int lg, int64_t nc,
-                             uint64_t* __restrict__ out) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nc;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t end = ((g + 1) << lg) < len ? ((g + 1) << lg) : len;
-    out[g] = T[end - 1];
-  }
-}
-
-__global__ void k_coarse_rows_u32(const uint32_t* __restrict__ T, int64_t rows, int64_t len, int lg,
-                                  int64_t nc, uint32_t* __restrict__ out) {
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < rows * nc;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = x / nc, g = x % nc;
-    const int64_t end = ((g + 1) << lg) < len ? ((g + 1) << lg) : len;
-    out[x] = T[r * len + end - 1] & PREFIX_MASK;
-  }
-}
-
-// Second-level indices: every 16th prefix entry, each row padded to whole
-// level-1 blocks (n1 * 2^(lg1-4) entries) with all-ones entries.
-__global__ void k_coarse2_u64(const uint64_t* __restrict__ T, int64_t len, int64_t padded,
-                              uint64_t* __restrict__ out) {
-  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < padded;
-       h += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t end = ((h + 1) << 4) < len ? ((h + 1) << 4) : len;
-    out[h] = (h << 4) < len ? T[end - 1] : ~0ull;
-  }
-}
-
-__global__ void k_coarse2_rows_u32(const uint32_t* __restrict__ T, int64_t rows, int64_t len,
-                                   int64_t padded, uint32_t* __restrict__ out) {
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < rows * padded;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = x / padded, h = x % padded;
-    const int64_t end = ((h + 1) << 4) < len ? ((h + 1) << 4) : len;
-    out[x] = (h << 4) < len ? (T[r * len + end - 1] & PREFIX_MASK) : 0xFFFFFFFFu;
-  }
-}
-
 // Home-region size of row i: the smallest power of two >= 1.5 x the row's
-// expected number of diamonds among s_max (at least 1).
+// expected number of diamonds among s_max, at least 4 (so every region
+// starts on a 4-slot group); entry m is the overflow table.
 __global__ void __launch_bounds__(256)
 k_region_sizes(const uint64_t* __restrict__ T1, int64_t m, unsigned long long s_max,
-               const DevScalars* sc, unsigned long long* __restrict__ sizes) {
-  const double scale = (double)s_max / (double)(sc->t1_total ? sc->t1_total : 1ull);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+               unsigned long long overflow, const DevScalars* sc,
+               unsigned long long* __restrict__ sizes) {
+  const float scale = 1.5f * ((float)s_max / (float)(sc->t1_total ? sc->t1_total : 1ull));
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= m;
        i += (int64_t)gridDim.x * blockDim.x) {
+    if (i == m) {
+      sizes[m] = overflow;
+      continue;
+    }
     const unsigned long long q = T1[i] - (i ? T1[i - 1] : 0ull);
-    const double want = 1.5 * (double)q * scale;
-    unsigned long long size = 1;
-    while ((double)size < want && size < (1ull << 40)) size <<= 1;
-    sizes[i] = size;
+    const float want = (float)q * scale;
+    // smallest power of two >= want, between 2^2 and 2^40
+    int e = 2;
+    if (want > 4.0f) {
+      const uint32_t b = __float_as_uint(want);
+      e = (int)((b >> 23) & 0xFF) - 127 + ((b & 0x7FFFFF) ? 1 : 0);
+      e = e < 40 ? e : 40;
+    }
+    sizes[i] = 1ull << e;
   }
 }
 
@@ -510,8 +722,13 @@ int ceil_log2_host(uint64_t x) {
 
 template <typename T>
 void launch_b_rows(mad_ctx* ctx, cudaStream_t st) {
-  k_b_rows_dense<T><<<(unsigned)ctx->d, 256, 0, st>>>((const T*)ctx->B.values, ctx->n, ctx->B.ld,
-                                                       ctx->nb, ctx->TB, ctx->sc);
+  if (ctx->n >= 8192) {
+    k_b_rows_wide<T><<<(unsigned)ctx->d, 1024, 0, st>>>((const T*)ctx->B.values, ctx->n, ctx->B.ld,
+                                                         ctx->nb, ctx->TB, ctx->sc);
+  } else {
+    k_b_rows_dense<T><<<(unsigned)ctx->d, 256, 0, st>>>((const T*)ctx->B.values, ctx->n,
+                                                         ctx->B.ld, ctx->nb, ctx->TB, ctx->sc);
+  }
   count_launch(ctx);
 }
 
@@ -519,6 +736,13 @@ template <typename T>
 void launch_a_rows(mad_ctx* ctx, cudaStream_t st) {
   const int64_t blocks64 = (ctx->m + 7) / 8;
   const unsigned blocks = (unsigned)(blocks64 < 152 * 16 ? blocks64 : 152 * 16);
+  if (ctx->d <= 256) {
+    k_a_rows_short<T><<<blocks, 256, 0, st>>>((const T*)ctx->A.values, ctx->m, (int)ctx->d,
+                                              ctx->A.ld, ctx->nb, ctx->na, ctx->r, ctx->T2,
+                                              ctx->TA, ctx->sc);
+    count_launch(ctx);
+    return;
+  }
   k_a_rows_dense<T><<<blocks, 256, (size_t)ctx->d * sizeof(float), st>>>(
       (const T*)ctx->A.values, ctx->m, ctx->d, ctx->A.ld, ctx->nb, ctx->na, ctx->r, ctx->T2,
       ctx->TA, ctx->sc);
@@ -535,7 +759,18 @@ void launch_transpose(mad_ctx* ctx, cudaStream_t st) {
 
 }  // namespace
 
-uint64_t hash_region_bound(uint64_t m, uint64_t s_max) { return m + 3 * s_max + 1; }
+uint64_t overflow_slots(uint64_t s_max) {
+  uint64_t c = 4096;
+  while (c < s_max / 8 + 4096) c <<= 1;
+  return c;
+}
+
+// Each region holds at most max(4, 2 x 1.5 x its expected diamonds) slots,
+// the expectation taken in FP32 (relative error below 2^-20); then the
+// overflow table.
+uint64_t hash_region_bound(uint64_t m, uint64_t s_max) {
+  return 4 * m + 3 * s_max + (s_max >> 18) + 16 + overflow_slots(s_max);
+}
 
 mad_status t2_guide_offsets(mad_ctx* ctx, cudaStream_t st) {
   const uint64_t m = (uint64_t)ctx->m;
@@ -581,53 +816,47 @@ mad_status build_bloom(mad_ctx* ctx, cudaStream_t st) {
 }
 
 // Guides of the dense TB rows: row k (n entries, masked total tot) gets
-// buckets of width 2^sh leaving at most about n/4 of them;
-// guide entry b is the first position whose prefix reaches b << sh.  Built
-// by one pass over the entries: entry e writes the guide entries of the
-// bucket starts its step (v_{e-1}, v_e] crosses.
+// buckets of width 2^sh, sh = max(0, bitlen(tot - 1) - W) with
+// W = bitlen(max(n / 8, 1)), so it has nb = ((tot - 1) >> sh) + 1 <= 2^W
+// buckets and its nb + 1 guide entries fit a fixed row stride 2^W + 1
+// (no size pass, no host read-back).  Guide entry b is the first position
+// whose prefix reaches b << sh.  Built by one pass over the entries: entry
+// e writes the guide entries of the bucket starts its step (v_{e-1}, v_e]
+// crosses; the last entry also stores the row's sh.
 __global__ void __launch_bounds__(256)
-k_tbg_sizes(const uint32_t* __restrict__ TB, int64_t d, int64_t n,
-            unsigned long long* __restrict__ sizes, uint8_t* __restrict__ shift) {
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < d;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t tot = TB[k * n + n - 1] & PREFIX_MASK;
-    unsigned long long size = 0;
-    int sh = 0;
-    if (tot > 0) {
-      sh = bitlen_u32(tot - 1) - bitlen_u32((uint32_t)(n / 8 > 0 ? n / 8 : 1));
-      if (sh < 0) sh = 0;
-      size = (unsigned long long)((tot - 1) >> sh) + 2;   // nb + 1
+k_tbg_fill(const uint32_t* __restrict__ TB, int64_t d, int64_t n, int W, int64_t stride,
+           uint8_t* __restrict__ shift, uint32_t* __restrict__ G) {
+  // Rows along grid dimension y, entries of a row along x (no division).
+  for (int64_t k = blockIdx.y; k < d; k += gridDim.y) {
+    const uint32_t* __restrict__ row = TB + k * n;
+    const uint32_t tot = __ldg(row + n - 1) & PREFIX_MASK;
+    int sh = tot ? bitlen_u32(tot - 1) - W : 0;
+    sh = sh > 0 ? sh : 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) shift[k] = (uint8_t)sh;
+    if (tot == 0) continue;
+    const unsigned long long nb1 = (unsigned long long)((tot - 1) >> sh) + 2;   // nb + 1 entries
+    uint32_t* __restrict__ g = G + k * stride;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const unsigned long long v = row[e] & PREFIX_MASK;
+      const unsigned long long b_hi = v >> sh;
+      const unsigned long long b_lo = e ? ((unsigned long long)(row[e - 1] & PREFIX_MASK) >> sh) + 1 : 0;
+      for (unsigned long long b = b_lo; b <= b_hi && b < nb1; ++b) g[b] = (uint32_t)e;
+      if (e == n - 1)   // bucket starts past the last prefix: no entry reaches them
+        for (unsigned long long b = b_hi + 1; b < nb1; ++b) g[b] = (uint32_t)n;
     }
-    sizes[k] = size;
-    shift[k] = (uint8_t)sh;
-  }
-}
-
-__global__ void __launch_bounds__(256)
-k_tbg_fill(const uint32_t* __restrict__ TB, int64_t d, int64_t n,
-           const unsigned long long* __restrict__ gptr, const uint8_t* __restrict__ shift,
-           uint32_t* __restrict__ G) {
-  const int64_t total = d * n;
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = x / n, e = x - k * n;
-    const unsigned long long g0 = gptr[k], nb1 = gptr[k + 1] - g0;   // nb + 1 entries
-    if (nb1 == 0) continue;
-    const int sh = shift[k];
-    const unsigned long long v = TB[x] & PREFIX_MASK;
-    const unsigned long long b_hi = v >> sh;
-    const unsigned long long b_lo = e ? ((unsigned long long)(TB[x - 1] & PREFIX_MASK) >> sh) + 1 : 0;
-    for (unsigned long long b = b_lo; b <= b_hi && b < nb1; ++b) G[g0 + b] = (uint32_t)e;
-    if (e == n - 1)   // bucket starts past the last prefix: no entry reaches them
-      for (unsigned long long b = b_hi + 1; b < nb1; ++b) G[g0 + b] = (uint32_t)n;
   }
 }
 
 // Guide of T1 (one 64-bit prefix row), filled like the TB guides: entry e
 // writes the guide entries of the bucket starts in (T1[e-1], T1[e]].
 __global__ void __launch_bounds__(256)
-k_t1g_fill(const uint64_t* __restrict__ T1, int64_t m, int sh, uint64_t nb1,
+k_t1g_fill(const uint64_t* __restrict__ T1, int64_t m, const DevScalars* sc,
            uint32_t* __restrict__ G) {
+  const unsigned long long total = sc->t1_total;
+  if (total == 0ull) return;
+  const int sh = sc->t1g_sh;
+  const unsigned long long nb1 = ((total - 1) >> sh) + 2;   // nb + 1 entries
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
        e += (int64_t)gridDim.x * blockDim.x) {
     const unsigned long long b_hi = T1[e] >> sh;
@@ -638,32 +867,63 @@ k_t1g_fill(const uint64_t* __restrict__ T1, int64_t m, int sh, uint64_t nb1,
   }
 }
 
-mad_status t1_guide_fill(mad_ctx* ctx, uint64_t nb, cudaStream_t st) {
-  const int64_t blocks64 = (ctx->m + 255) / 256;
-  k_t1g_fill<<<(unsigned)(blocks64 < 152 * 16 ? blocks64 : 152 * 16), 256, 0, st>>>(
-      ctx->T1, ctx->m, ctx->t1g_sh, nb + 1, ctx->T1g);
+// Empties the slots [*lo_dev, min(cap, *n_dev)) of the hash (keys to
+// EMPTY_KEY, values to 0) with 16-byte stores.
+__global__ void __launch_bounds__(256)
+k_clear_slots(unsigned long long* __restrict__ keys, long long* __restrict__ vals, uint64_t cap,
+              const unsigned long long* lo_dev, const unsigned long long* n_dev) {
+  const uint64_t n = dev_len(cap, n_dev);
+  const uint64_t lo = lo_dev ? (*lo_dev & ~1ull) : 0;   // an even start (16-byte stores)
+  const uint64_t stride = 2ull * gridDim.x * blockDim.x;
+  for (uint64_t q = lo + 2ull * (blockIdx.x * blockDim.x + threadIdx.x); q < n; q += stride) {
+    if (q + 1 < n) {
+      *(ulonglong2*)(keys + q) = make_ulonglong2(EMPTY_KEY, EMPTY_KEY);
+      *(longlong2*)(vals + q) = make_longlong2(0, 0);
+    } else {
+      keys[q] = EMPTY_KEY;
+      vals[q] = 0;
+    }
+  }
+}
+
+mad_status clear_slots(mad_ctx* ctx, const unsigned long long* lo_dev,
+                       const unsigned long long* hi_dev, cudaStream_t st) {
+  const uint64_t bound = hash_slot_bound(ctx);
+  const uint64_t blocks64 = (bound + 511) / 512;
+  k_clear_slots<<<(unsigned)(blocks64 < 152 * 8 ? (blocks64 ? blocks64 : 1) : 152 * 8), 256, 0,
+                  st>>>(ctx->hkeys, ctx->hvals, bound, lo_dev, hi_dev);
   count_launch(ctx);
   return cuda_status(cudaGetLastError());
 }
 
-mad_status tb_guide_offsets(mad_ctx* ctx, cudaStream_t st) {
-  const uint64_t d = (uint64_t)ctx->d;
-  const size_t sizes_bytes = (d * sizeof(unsigned long long) + 255) & ~(size_t)255;
-  mad_status rs = ensure_scratch(ctx, sizes_bytes + scan_partial_elems(d) * 8, st);
-  if (rs != MAD_OK) return rs;
-  unsigned long long* sizes = (unsigned long long*)ctx->scratch;
-  uint64_t* part = (uint64_t*)((char*)ctx->scratch + sizes_bytes);
-  k_tbg_sizes<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(ctx->TB, ctx->d, ctx->n, sizes,
-                                                           ctx->TBg_sh);
-  count_launch(ctx);
-  return scan_exclusive_u64(ctx, (const uint64_t*)sizes, (uint64_t*)ctx->TBg_ptr, d, part, st);
+int t1_guide_width(int64_t m) {
+  int w = 0;
+  while (w < 63 && (((uint64_t)m / 4) >> w)) ++w;
+  return w;
 }
 
-mad_status tb_guide_fill(mad_ctx* ctx, cudaStream_t st) {
-  const int64_t total = ctx->d * ctx->n;
-  const int64_t blocks64 = (total + 255) / 256;
-  k_tbg_fill<<<(unsigned)(blocks64 < 152 * 32 ? blocks64 : 152 * 32), 256, 0, st>>>(
-      ctx->TB, ctx->d, ctx->n, ctx->TBg_ptr, ctx->TBg_sh, ctx->TBg);
+mad_status t1_guide_fill(mad_ctx* ctx, cudaStream_t st) {
+  const int64_t blocks64 = (ctx->m + 255) / 256;
+  k_t1g_fill<<<(unsigned)(blocks64 < 152 * 16 ? blocks64 : 152 * 16), 256, 0, st>>>(
+      ctx->T1, ctx->m, ctx->sc, ctx->T1g);
+  count_launch(ctx);
+  return cuda_status(cudaGetLastError());
+}
+
+int tb_guide_width(int64_t n) {
+  const uint32_t x = (uint32_t)(n / 8 > 0 ? n / 8 : 1);
+  int w = 0;
+  while (w < 32 && (x >> w)) ++w;
+  return w;
+}
+
+mad_status tb_guide_build(mad_ctx* ctx, cudaStream_t st) {
+  const int W = tb_guide_width(ctx->n);
+  const int64_t xblocks = (ctx->n + 1023) / 1024;   // four entries per thread
+  const dim3 grid((unsigned)(xblocks < 64 ? xblocks : 64),
+                  (unsigned)(ctx->d < 65535 ? ctx->d : 65535));
+  k_tbg_fill<<<grid, 256, 0, st>>>(ctx->TB, ctx->d, ctx->n, W, ctx->tbg_stride, ctx->TBg_sh,
+                                   ctx->TBg);
   count_launch(ctx);
   return cuda_status(cudaGetLastError());
 }
@@ -691,15 +951,16 @@ mad_status t2_guide_fill(mad_ctx* ctx, cudaStream_t st) {
 
 mad_status build_hash_regions(mad_ctx* ctx, cudaStream_t st) {
   const uint64_t m = (uint64_t)ctx->m;
-  const size_t sizes_bytes = (m * sizeof(unsigned long long) + 255) & ~(size_t)255;
-  mad_status rs = ensure_scratch(ctx, sizes_bytes + scan_partial_elems(m) * 8, st);
+  const size_t sizes_bytes = ((m + 1) * sizeof(unsigned long long) + 255) & ~(size_t)255;
+  mad_status rs = ensure_scratch(ctx, sizes_bytes + scan_partial_elems(m + 1) * 8, st);
   if (rs != MAD_OK) return rs;
   unsigned long long* sizes = (unsigned long long*)ctx->scratch;
   uint64_t* part = (uint64_t*)((char*)ctx->scratch + sizes_bytes);
-  const unsigned blocks = (unsigned)((m + 255) / 256 < 152 * 8 ? (m + 255) / 256 : 152 * 8);
-  k_region_sizes<<<blocks, 256, 0, st>>>(ctx->T1, ctx->m, ctx->s_max, ctx->sc, sizes);
+  const unsigned blocks = (unsigned)((m + 256) / 256 < 152 * 8 ? (m + 256) / 256 : 152 * 8);
+  k_region_sizes<<<blocks, 256, 0, st>>>(ctx->T1, ctx->m, ctx->s_max, overflow_slots(ctx->s_max),
+                                         ctx->sc, sizes);
   count_launch(ctx);
-  return scan_exclusive_u64(ctx, (const uint64_t*)sizes, (uint64_t*)ctx->hreg, m, part, st);
+  return scan_exclusive_u64(ctx, (const uint64_t*)sizes, (uint64_t*)ctx->hreg, m + 1, part, st);
 }
 
 mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st) {
@@ -723,34 +984,11 @@ mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st) {
   const float* r = ctx->integer ? nullptr : ctx->r;
   const unsigned long long* r64 = ctx->integer ? ctx->r64 : nullptr;
   k_t1_chunk_sums<<<(unsigned)chunks, 256, 0, st>>>(r, r64, ctx->m, clog2m, partial, ctx->sc);
-  k_t1_chunk_offsets<<<1, 32, 0, st>>>(partial, chunks, ctx->sc);
+  const int bl_m = t1_guide_width(ctx->m);
+  k_t1_chunk_offsets<<<1, 32, 0, st>>>(partial, chunks, bl_m, clog2m,
+                                       ceil_log2_host(ctx->s_max), ctx->dense ? 1 : 0, ctx->sc);
   k_t1_write<<<(unsigned)chunks, 256, 0, st>>>(r, r64, ctx->m, clog2m, partial, ctx->T1, ctx->sc);
   count_launch(ctx, 3);
-  if (ctx->T1c) {
-    k_coarse_u64<<<(unsigned)((ctx->t1c_n + 255) / 256), 256, 0, st>>>(ctx->T1, ctx->m, ctx->t1c_lg,
-                                                                       ctx->t1c_n, ctx->T1c);
-    count_launch(ctx);
-  }
-  if (ctx->T1c2) {
-    const int64_t padded = ctx->t1c_n << (ctx->t1c_lg - 4);
-    k_coarse2_u64<<<(unsigned)((padded + 255) / 256), 256, 0, st>>>(ctx->T1, ctx->m, padded,
-                                                                    ctx->T1c2);
-    count_launch(ctx);
-  }
-  if (ctx->TBc2) {
-    const int64_t padded = ctx->tbc_n << (ctx->tbc_lg - 4);
-    const int64_t total = ctx->d * padded;
-    k_coarse2_rows_u32<<<(unsigned)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32),
-                         256, 0, st>>>(ctx->TB, ctx->d, ctx->n, padded, ctx->TBc2);
-    count_launch(ctx);
-  }
-  if (ctx->TBc) {
-    const int64_t total = ctx->d * ctx->tbc_n;
-    k_coarse_rows_u32<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(ctx->TB, ctx->d, ctx->n,
-                                                                       ctx->tbc_lg, ctx->tbc_n,
-                                                                       ctx->TBc);
-    count_launch(ctx);
-  }
   return cuda_status(cudaGetLastError());
 }
 

@@ -22,6 +22,17 @@ def case_inputs(name: str):
         A = (rng.standard_normal((2051, 100)) * np.exp(0.5 * rng.standard_normal((2051, 1))))
         B = (rng.standard_normal((100, 3001)) * np.exp(0.5 * rng.standard_normal((1, 3001))))
         return "dense", (A.astype(np.float32), B.astype(np.float32)), 0
+    if name == "dense_wide_rows":          # rows of B longer than the wide-row threshold
+        rng = _rng(47)
+        A = (rng.standard_normal((500, 60)) * np.exp(0.5 * rng.standard_normal((500, 1))))
+        B = (rng.standard_normal((60, 20011)) * np.exp(0.5 * rng.standard_normal((1, 20011))))
+        B[3, :] = 0.0
+        return "dense", (A.astype(np.float32), B.astype(np.float32)), 0
+    if name == "dense_deep":               # d above 256: the general row kernel of A
+        rng = _rng(48)
+        A = rng.standard_normal((300, 300)) * np.exp(0.5 * rng.standard_normal((300, 1)))
+        B = rng.standard_normal((300, 450))
+        return "dense", (A.astype(np.float32), B.astype(np.float32)), 0
     if name == "dense_factors_small":
         w = W.dense_factors(m=4000, d=100, n=1500, seed=8)
         return "dense", (w.A, w.B), 0

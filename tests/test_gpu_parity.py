@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 
 from gpu_cases import Case  # noqa: E402
 
-CASES = ["plain_small", "dense_ragged_f32", "dense_factors_small", "dense_mixed_signs_zeros",
+CASES = ["plain_small", "dense_ragged_f32", "dense_wide_rows", "dense_deep", "dense_factors_small",
+         "dense_mixed_signs_zeros",
          "dense_nonneg", "gram_dense", "chung_lu_small", "bipartite_binary", "chung_lu_square_sym"]
 
 

@@ -1,0 +1,164 @@
+"""The fused dense pass (mad_pipeline_*) against the CPU oracle: Omega_t'
+(keys and x) and Omega_t (keys, x and the FP64 c) bit for bit; a CUDA-graph
+replay on new contents of the same input buffers matches the oracle on the
+new inputs; device-side lengths cover short and multi-tile candidate
+lists."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _inputs(seed, m=2051, d=100, n=3001):
+    """Log-normal row and column scales times Gaussian directions (several
+    tiles and ragged tails in every table)."""
+    rng = _rng(seed)
+    A = rng.standard_normal((m, d)) * np.exp(0.5 * rng.standard_normal((m, 1)))
+    B = rng.standard_normal((d, n)) * np.exp(0.5 * rng.standard_normal((1, n)))
+    return A.astype(np.float32), B.astype(np.float32)
+
+
+def _oracle_pass(A, B, flags, s, seed, tprime, t):
+    o = oracle.Oracle(oracle.Matrix(A), oracle.Matrix(B), flags, s)
+    assert o.sample(s, seed) == 0
+    keys, x = o.topk(tprime)
+    c = o.rescore(keys)
+    tk, tc = oracle.topt(keys, c, t)
+    return keys, x, tk, tc
+
+
+def _check(mad, out, counts, cand, ref):
+    keys, x, tk, tc = ref
+    nc, nr = [int(v) for v in counts.cpu().numpy()]
+    assert nc == len(keys)
+    ci, cj, cx, _ = mad.decode_pairs(cand, nc)
+    assert np.array_equal(mad.keys_of(ci, cj), keys)
+    assert np.array_equal(cx, x)
+    assert nr == len(tk)
+    ri, rj, rx, rc = mad.decode_pairs(out, nr)
+    assert np.array_equal(mad.keys_of(ri, rj), tk)
+    assert np.array_equal(rc.view(np.int64), tc.view(np.int64))
+    xmap = dict(zip(keys.tolist(), x.tolist()))
+    assert [xmap[k] for k in tk.tolist()] == rx.tolist()
+
+
+@pytest.mark.parametrize("flags,tprime,t", [(0, 1000, 37), (0, 5000, 100), (1, 300, 10)])
+def test_pass_matches_oracle(flags, tprime, t):
+    import paper_1506_03872_gb300 as mad
+    A, B = _inputs(60 + flags)
+    if flags & 1:
+        A, B = np.abs(A), np.abs(B)
+    s, seed = 300_000, 11
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    with mad.Context(flags) as c:
+        mad.mad_pipeline_plan(c.ctx, mad.dense(tA), mad.dense(tB), s, tprime, t)
+        out = mad.new_pairs(t)
+        cand = mad.new_pairs(tprime)
+        counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+        mad.mad_pipeline_run(c.ctx, seed, out, counts, cand)
+        mad.mad_pipeline_status(c.ctx)
+        st = mad.mad_stats(c.ctx)
+        _check(mad, out, counts, cand, _oracle_pass(A, B, flags, s, seed, tprime, t))
+        o = oracle.Oracle(oracle.Matrix(A), oracle.Matrix(B), flags, s)
+        sc = o.scalars()
+        assert st["t1_total"] == sc["T1_total"] and st["f"] == sc["F"] and st["e1"] == sc["E1"]
+        assert st["sampled"] == s
+
+
+def test_gram_pass_matches_oracle():
+    import paper_1506_03872_gb300 as mad
+    rng = _rng(65)
+    A = rng.standard_normal((700, 30)).astype(np.float32)
+    B = np.ascontiguousarray(A.T)
+    flags, s, seed, tprime, t = 2 | 4, 200_000, 3, 800, 25
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    with mad.Context(flags) as c:
+        mad.mad_pipeline_plan(c.ctx, mad.dense(tA), mad.dense(tB), s, tprime, t)
+        out, cand = mad.new_pairs(t), mad.new_pairs(tprime)
+        counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+        mad.mad_pipeline_run(c.ctx, seed, out, counts, cand)
+        mad.mad_pipeline_status(c.ctx)
+        _check(mad, out, counts, cand, _oracle_pass(A, B, flags, s, seed, tprime, t))
+
+
+def test_graph_replay_on_new_inputs():
+    """Captured once, replayed after the inputs' contents change: nothing of
+    the first inputs may survive in host-side state."""
+    import paper_1506_03872_gb300 as mad
+    A0, B0 = _inputs(70)
+    A1, B1 = _inputs(71)
+    s, seed, tprime, t = 250_000, 21, 2000, 50
+    tA, tB = torch.from_numpy(A0).cuda(), torch.from_numpy(B0).cuda()
+    with mad.Context() as c:
+        mad.mad_pipeline_plan(c.ctx, mad.dense(tA), mad.dense(tB), s, tprime, t)
+        out, cand = mad.new_pairs(t), mad.new_pairs(tprime)
+        counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):   # one eager run on the capture stream first
+            mad.mad_pipeline_run(c.ctx, seed, out, counts, cand)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            mad.mad_pipeline_run(c.ctx, seed, out, counts, cand)
+        for A, B in ((A1, B1), (A0, B0)):
+            tA.copy_(torch.from_numpy(A))
+            tB.copy_(torch.from_numpy(B))
+            out.zero_()
+            cand.zero_()
+            counts.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            mad.mad_pipeline_status(c.ctx)
+            _check(mad, out, counts, cand, _oracle_pass(A, B, 0, s, seed, tprime, t))
+
+
+def test_short_lists_and_limits():
+    """Fewer positive x than t' (a tiny budget), and argument checks."""
+    import paper_1506_03872_gb300 as mad
+    A, B = _inputs(72, m=300, d=20, n=400)
+    s, seed, tprime, t = 50, 9, 1000, 30
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    with mad.Context() as c:
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_pipeline_run(c.ctx, seed, mad.new_pairs(t),
+                                 torch.zeros(2, dtype=torch.int32, device="cuda"))
+        assert e.value.status == mad.MAD_ERR_STATE
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_pipeline_plan(c.ctx, mad.dense(tA), mad.dense(tB), s, 10, 11)   # t > t'
+        assert e.value.status == mad.MAD_ERR_ARG
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_pipeline_plan(c.ctx, mad.dense(tA), mad.dense(tB), s, 1 << 18, 10)
+        assert e.value.status == mad.MAD_ERR_ARG
+        mad.mad_pipeline_plan(c.ctx, mad.dense(tA), mad.dense(tB), s, tprime, t)
+        out, cand = mad.new_pairs(t), mad.new_pairs(tprime)
+        counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+        mad.mad_pipeline_run(c.ctx, seed, out, counts, cand)
+        mad.mad_pipeline_status(c.ctx)
+        ref = _oracle_pass(A, B, 0, s, seed, tprime, t)
+        assert len(ref[0]) < tprime
+        _check(mad, out, counts, cand, ref)
+    rp = torch.tensor([0, 1, 2], dtype=torch.int64, device="cuda")
+    ci = torch.tensor([1, 0], dtype=torch.int32, device="cuda")
+    M = mad.csr(rp, ci, (2, 2))
+    with mad.Context(2) as c:
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_pipeline_plan(c.ctx, M, M, 100, 10, 5)
+        assert e.value.status == mad.MAD_ERR_UNSUPPORTED
