@@ -111,15 +111,8 @@ bool valid_csr(const mad_matrix* M) {
          M->cols > 0 && M->cols < (1ll << 31);
 }
 
-// Empty X.  When the region builder fills the dense regions, only the
-// overflow table is cleared and the regions are marked fresh (the builder
-// writes every region on its first pass); otherwise every slot is cleared.
+// Empty X: every slot up to the hash's extent.
 mad_status clear_x_slots(mad_ctx* ctx, cudaStream_t st) {
-  if (ctx->regioned && !(ctx->flags & MAD_GRAM)) {
-    ctx->x_fresh = true;
-    return clear_slots(ctx, ctx->hreg + ctx->m, hash_extent(ctx), st);
-  }
-  ctx->x_fresh = false;
   return clear_slots(ctx, nullptr, hash_extent(ctx), st);
 }
 
@@ -216,7 +209,7 @@ mad_status alloc_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, 
     if ((rs = alloc(ctx, ctx->TBg, (size_t)(ctx->d * ctx->tbg_stride), st)) != MAD_OK) return rs;
   }
   if ((rs = alloc(ctx, ctx->T1, (size_t)ctx->m, st)) != MAD_OK) return rs;
-  // Guide of T1: about m/4 power-of-two buckets over [0, total).
+  // Guide of T1: about m power-of-two buckets over [0, total).
   if ((rs = alloc(ctx, ctx->T1g, ((size_t)1 << t1_guide_width(ctx->m)) + 1, st)) != MAD_OK)
     return rs;
   // Dense inputs get a hash with per-row home regions (sized after T1);
@@ -227,7 +220,7 @@ mad_status alloc_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, 
   uint64_t cap = ctx->hcap_request;
   if (ctx->regioned) {
     cap = hash_region_bound((uint64_t)ctx->m, s_max);
-    if ((rs = alloc(ctx, ctx->hreg, (size_t)ctx->m + 2, st)) != MAD_OK) return rs;
+    if ((rs = alloc(ctx, ctx->hreg, (size_t)ctx->m + 1, st)) != MAD_OK) return rs;
   }
   if (cap) {
     ctx->hcap = ctx->hcap_alloc = cap;
@@ -254,7 +247,7 @@ mad_status finish_dense_build(mad_ctx* ctx, cudaStream_t st) {
   DevScalars hs;
   unsigned long long used = 0;
   if (ctx->regioned)
-    cudaMemcpyAsync(&used, ctx->hreg + ctx->m + 1, sizeof(used), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&used, ctx->hreg + ctx->m, sizeof(used), cudaMemcpyDeviceToHost, st);
   mad_status rs = read_scalars(ctx, &hs, st);
   if (rs != MAD_OK) return rs;
   if (hs.err & DERR_OVERFLOW) return MAD_ERR_OVERFLOW;
@@ -276,8 +269,8 @@ mad_status finish_dense_build(mad_ctx* ctx, cudaStream_t st) {
 size_t dense_build_scratch_bytes(const mad_ctx* ctx) {
   const uint64_t m = (uint64_t)ctx->m;
   const size_t chunks = (size_t)((m + 2047) / 2048) * sizeof(unsigned long long);
-  const size_t regions = (((m + 1) * sizeof(unsigned long long) + 255) & ~(size_t)255) +
-                         scan_partial_elems(m + 1) * 8;
+  const size_t regions = ((m * sizeof(unsigned long long) + 255) & ~(size_t)255) +
+                         scan_partial_elems(m) * 8;
   return chunks > regions ? chunks : regions;
 }
 
@@ -459,11 +452,6 @@ mad_status mad_topk(mad_ctx* ctx, uint32_t tprime, mad_pair* out_dev, uint32_t* 
   mad_status rs = read_scalars(ctx, &hs, st);
   if (rs != MAD_OK) return rs;
   if ((rs = device_error_status(hs.err)) != MAD_OK) return rs;
-  if (ctx->x_fresh) {   // nothing sampled since the last clear
-    ctx->positive = 0;
-    ctx->distinct = 0;
-    return MAD_OK;
-  }
   uint64_t bound = hs.new_keys < ctx->hcap ? hs.new_keys : ctx->hcap;
   if (tprime == 0 || bound == 0) return MAD_OK;
   if ((rs = ensure_scratch(ctx, select_ws_bytes(bound, tprime), st)) != MAD_OK) return rs;
@@ -576,7 +564,6 @@ mad_status mad_export_x(mad_ctx* ctx, uint64_t* keys_dev, int64_t* vals_dev, uin
   if (!ctx || !n_host || (cap && (!keys_dev || !vals_dev))) return MAD_ERR_ARG;
   *n_host = 0;
   if (!ctx->built) return MAD_ERR_STATE;
-  if (ctx->x_fresh) return MAD_OK;   // nothing sampled since the last clear
   cudaStream_t st = (cudaStream_t)stream;
   mad_status rs = ensure_scratch(ctx, 256, st);
   if (rs != MAD_OK) return rs;

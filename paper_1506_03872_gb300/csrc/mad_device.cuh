@@ -108,14 +108,23 @@ __device__ __forceinline__ int ub_u32(const uint32_t* __restrict__ P, int len, u
 
 // Upper bound in a long row through its guide: bucket b = target >> sh
 // holds the answer between guide entries b and b + 1, and the prefix
-// entries between those positions are counted (one window of 16 in the
-// common case, else a binary search over the bucket's range).  Same result
-// as ub_u32 over the whole row.
+// entries between those positions are counted (a window of 4, else of 16,
+// else a binary search over the bucket's range).  Same result as ub_u32
+// over the whole row.
 __device__ __forceinline__ int ub_guided_u32(const uint32_t* __restrict__ P,
                                              const uint32_t* __restrict__ G, int sh,
                                              uint32_t target, uint32_t mask = 0xFFFFFFFFu) {
   const uint32_t b = target >> sh;
   const int lo = (int)__ldg(G + b), hi = (int)__ldg(G + b + 1);
+  if (hi - lo <= 4) {
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = lo + q;
+      if (e < hi) cnt += ((__ldg(P + e) & mask) <= target) ? 1 : 0;
+    }
+    return lo + cnt;
+  }
   if (hi - lo <= 16) {
     int cnt = 0;
 #pragma unroll
@@ -134,6 +143,15 @@ __device__ __forceinline__ int64_t ub_guided_u64(const uint64_t* __restrict__ P,
                                                  unsigned long long target) {
   const unsigned long long b = target >> sh;
   const int64_t lo = (int64_t)__ldg(G + b), hi = (int64_t)__ldg(G + b + 1);
+  if (hi - lo <= 4) {
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = lo + q;
+      if (e < hi) cnt += (__ldg(P + e) <= target) ? 1 : 0;
+    }
+    return lo + cnt;
+  }
   if (hi - lo <= 16) {
     int cnt = 0;
 #pragma unroll

@@ -87,9 +87,8 @@ struct SampleParams {
   // Hash.  Regioned (dense inputs): the key (a, b) starts probing in the
   // home region of row a, [hreg[a], hreg[a+1]), sized from row a's expected
   // share of the diamonds; otherwise at mix(key) & hmask.  Probing is
-  // linear and wraps at hcap (for regioned hashes, the end of the overflow
-  // table, read on the device and kept within the hcap_alloc allocated
-  // slots).
+  // linear and wraps at hcap (for regioned hashes, the end of the regions,
+  // read on the device and kept within the hcap_alloc allocated slots).
   unsigned long long* hkeys;
   long long* hvals;
   const unsigned long long* hreg;
@@ -177,12 +176,9 @@ struct mad_ctx {
   void* bt = nullptr;               // dense B^T (n x d), the input dtype
   unsigned long long* hkeys = nullptr;
   long long* hvals = nullptr;
-  // Dense inputs: row i's home region is [hreg[i], hreg[i+1]) (m + 2
-  // offsets); the overflow table [hreg[m], hreg[m+1]) follows the regions.
+  // Dense inputs: row i's home region is [hreg[i], hreg[i+1]) (m + 1
+  // offsets; hreg[m] is the end of the regions).
   unsigned long long* hreg = nullptr;
-  // The regions hold nothing yet since the last clear (the region builder
-  // writes them all on its first pass; nothing may read them before).
-  bool x_fresh = false;
   bool regioned = false;
   uint64_t hcap = 0, hcap_alloc = 0, hcap_request = 0;
   mad::DevScalars* sc = nullptr;
@@ -238,15 +234,13 @@ mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st);
 // hash_slot_bound(ctx) (0 without lo_dev, bound without hi_dev).
 mad_status clear_slots(mad_ctx* ctx, const unsigned long long* lo_dev,
                        const unsigned long long* hi_dev, cudaStream_t st);
-// Overflow table of the dense hash: a power of two >= s_max / 8 + 4096.
-uint64_t overflow_slots(uint64_t s_max);
 // Home regions of the dense hash: sizes from T1 and s_max, then offsets.
 mad_status build_hash_regions(mad_ctx* ctx, cudaStream_t st);
 uint64_t hash_region_bound(uint64_t m, uint64_t s_max);
-// End of the dense hash on the device (regions and overflow table), else
+// End of the dense hash on the device (the end of the home regions), else
 // null (the whole ctx->hcap).
 inline const unsigned long long* hash_extent(const mad_ctx* ctx) {
-  return ctx->regioned ? ctx->hreg + ctx->m + 1 : nullptr;
+  return ctx->regioned ? ctx->hreg + ctx->m : nullptr;
 }
 // Host-side bound on the slots a scan of the hash may touch: the
 // allocation for regioned hashes (their extent is read on the device).

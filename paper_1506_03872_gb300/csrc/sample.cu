@@ -36,7 +36,7 @@ __device__ __forceinline__ SampleParams resolve(const SampleParams& p) {
   q.t1g_sh = p.sc->t1g_sh;
   q.f_exp = p.sc->f_exp;
   if (p.regioned) {
-    const unsigned long long used = p.hreg[p.m + 1];
+    const unsigned long long used = p.hreg[p.m];
     q.hcap = used < p.hcap_alloc ? used : p.hcap_alloc;
   }
   return q;
@@ -223,125 +223,6 @@ k_insert(const SampleParams p_, const unsigned long long* __restrict__ keys,
   flush_tally(p, t);
 }
 
-// X update for the row-ordered diamonds when every key (i, j) belongs to
-// its diamond's row i (dense inputs without MAD_GRAM): one warp per row
-// builds the row's home region in shared memory and writes the whole region
-// to the hash with plain stores, so the inserts need no global atomics and
-// the regions no separate clearing.  Row i's diamonds are the records in
-// the buckets its target range [T1[i-1], T1[i]) covers (records of other
-// rows in shared boundary buckets are skipped).  A key that finds its
-// region full goes to the overflow table after the regions (global
-// atomics); regions above kSlab slots are filled in place with global
-// atomics.  `fresh`: no region holds anything yet (first batch after a
-// clear), so every region is written, also when empty; otherwise a row
-// with records merges them into its region.
-constexpr int kSlab = 512;          // slots of one warp's shared-memory region
-constexpr int kRowWarps = 8;
-constexpr size_t kRowsSmem = (size_t)kRowWarps * kSlab * 16;
-
-__device__ __forceinline__ int overflow_add(const SampleParams& p, uint64_t lo, uint64_t hi,
-                                            unsigned long long key, long long v) {
-  const uint64_t home = lo + (mix64(key) & (hi - lo - 1));
-  return hash_add_from(p.hkeys, p.hvals, lo, hi, home, (uint32_t)(hi - lo < 4096 ? hi - lo : 4096),
-                       key, v);
-}
-
-__global__ void __launch_bounds__(256)
-k_insert_rows(const SampleParams p_, const unsigned long long* __restrict__ keys,
-              const long long* __restrict__ vals, const uint32_t* __restrict__ off, int fresh) {
-  const SampleParams p = resolve(p_);
-  extern __shared__ unsigned long long slab[];   // kRowWarps x (kSlab keys, kSlab values)
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned long long* sk = slab + (size_t)w * 2 * kSlab;
-  long long* sv = (long long*)(sk + kSlab);
-  const int shift = p.sc->sort_shift;
-  const uint64_t ovf_hi = p.hcap;   // the end of the table (kept within the allocation)
-  const uint64_t ovf_lo = p.hreg[p.m] < ovf_hi ? p.hreg[p.m] : ovf_hi;
-  Tally t;
-  // Regions past the allocation (never, by the bound on the region sizes)
-  // would be reported as a full hash, not written.
-  if (p.hreg[p.m + 1] > p.hcap_alloc || ovf_hi - ovf_lo < 4) {
-    if (threadIdx.x == 0) atomicOr(&p.sc->err, DERR_HASH_FULL);
-    return;
-  }
-  for (int64_t i = (int64_t)blockIdx.x * kRowWarps + w; i < p.m;
-       i += (int64_t)gridDim.x * kRowWarps) {
-    const unsigned long long t0 = i ? __ldg((const unsigned long long*)p.T1 + i - 1) : 0ull;
-    const unsigned long long t1 = __ldg((const unsigned long long*)p.T1 + i);
-    const uint64_t r0 = p.hreg[i], S = p.hreg[i + 1] - r0;   // a power of two >= 4
-    uint32_t q0 = 0, q1 = 0;
-    if (t1 > t0) {
-      q0 = __ldg(off + (t0 >> shift));
-      q1 = __ldg(off + ((t1 - 1) >> shift) + 1);
-    }
-    if (q1 == q0 && !fresh) continue;
-    const unsigned long long row = (unsigned long long)i;
-    if (S <= (uint64_t)kSlab) {
-      for (uint32_t x = lane; x < S; x += 32) {
-        sk[x] = fresh ? EMPTY_KEY : p.hkeys[r0 + x];
-        sv[x] = fresh ? 0 : p.hvals[r0 + x];
-      }
-      __syncwarp();
-      for (uint32_t base = q0; base < q1; base += 32) {
-        const uint32_t q = base + lane;
-        const unsigned long long key = q < q1 ? __ldcs(keys + q) : EMPTY_KEY;
-        if (key == EMPTY_KEY || (key >> 32) != row) continue;
-        const long long v = __ldcs(vals + q);
-        ++t.inserted;
-        uint32_t slot = (uint32_t)(mix64(key) & (S - 1));
-        bool done = false;
-        for (uint32_t probe = 0; probe < S && !done; ++probe) {
-          const unsigned long long cur = ((volatile unsigned long long*)sk)[slot];
-          if (cur == EMPTY_KEY || cur == key) {
-            const unsigned long long prev =
-                cur == key ? key : atomicCAS(sk + slot, EMPTY_KEY, key);
-            if (prev == EMPTY_KEY || prev == key) {
-              atomicAdd((unsigned long long*)sv + slot, (unsigned long long)v);
-              if (prev == EMPTY_KEY) ++t.created;
-              done = true;
-              continue;
-            }
-          }
-          slot = (slot + 1) & (uint32_t)(S - 1);
-        }
-        if (!done) {
-          const int res = overflow_add(p, ovf_lo, ovf_hi, key, v);
-          if (res == 0) t.full = true;
-          if (res == 2) ++t.created;
-        }
-      }
-      __syncwarp();
-      for (uint32_t x = lane; x < S; x += 32) {
-        p.hkeys[r0 + x] = sk[x];
-        p.hvals[r0 + x] = sv[x];
-      }
-      __syncwarp();
-    } else {
-      if (fresh) {
-        for (uint64_t x = lane; x < S; x += 32) {
-          p.hkeys[r0 + x] = EMPTY_KEY;
-          p.hvals[r0 + x] = 0;
-        }
-        __threadfence();
-        __syncwarp();
-      }
-      for (uint32_t base = q0; base < q1; base += 32) {
-        const uint32_t q = base + lane;
-        const unsigned long long key = q < q1 ? __ldcs(keys + q) : EMPTY_KEY;
-        if (key == EMPTY_KEY || (key >> 32) != row) continue;
-        const long long v = __ldcs(vals + q);
-        ++t.inserted;
-        int res = hash_add_from(p.hkeys, p.hvals, r0, r0 + S, r0 + (mix64(key) & (S - 1)),
-                                (uint32_t)(S < 4096 ? S : 4096), key, v);
-        if (res == 0) res = overflow_add(p, ovf_lo, ovf_hi, key, v);
-        if (res == 0) t.full = true;
-        if (res == 2) ++t.created;
-      }
-    }
-  }
-  flush_tally(p, t);
-}
-
 // Diagnostic twin of k_sample: writes each diamond's draws instead of// Diagnostic twin of k_sample: writes each diamond's draws instead of
 // accumulating them.
 __global__ void __launch_bounds__(256)
@@ -506,19 +387,6 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
   const int full_count = full_grid<k_bucket_count>();
   const int full_sorted = full_grid<k_sample_sorted>();
   const int full_insert = full_grid<k_insert>();
-  // Keys of row i only (no Gram reordering): the region builder.
-  const bool by_rows = ctx->regioned && !(ctx->flags & MAD_GRAM);
-  static int rows_grid = 0;
-  if (by_rows && !rows_grid) {
-    cudaFuncSetAttribute(k_insert_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowsSmem);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_insert_rows, 256, kRowsSmem) !=
-            cudaSuccess || per_sm < 1)
-      per_sm = 1;
-    rows_grid = sms * per_sm;
-  }
   // Buckets of 2^sort_shift target values (the shift comes from T1's total
   // on the device), at most 2^ceil(log2 m) of them.
   const uint64_t nbk = sort_buckets(ctx->m);
@@ -546,14 +414,7 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
     k_sample_sorted<<<grid_of(n, full_sorted), 256, 0, st>>>(p, seed, first + done, n, sorted,
                                                              rec);
     phase_event(ctx, 2, st);
-    if (by_rows) {
-      const int64_t blocks = (ctx->m + kRowWarps - 1) / kRowWarps;
-      k_insert_rows<<<(unsigned)(blocks < rows_grid ? blocks : rows_grid), 256, kRowsSmem, st>>>(
-          p, rec, (const long long*)sorted, off, ctx->x_fresh ? 1 : 0);
-      ctx->x_fresh = false;
-    } else {
-      k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, rec, (const long long*)sorted, n);
-    }
+    k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, rec, (const long long*)sorted, n);
     phase_event(ctx, 3, st);
     count_launch(ctx, 3);
   }
