@@ -116,38 +116,92 @@ k_sample(const SampleParams p_, unsigned long long seed, unsigned long long firs
   flush_tally(p, t);
 }
 
-// Counting sort of diamonds into row order, step 1: bucket each diamond by
-// the top bits of its stage-1 target (Philox block 0 and T1's total only).
-// The row i = upper_bound(T1, target) is non-decreasing in the target, so
-// bucket order is row order; the search itself is left to the draw kernel,
-// where neighbouring diamonds search the same few lines of T1.
-__global__ void __launch_bounds__(256)
-k_bucket_count(const DevScalars* __restrict__ sc, unsigned long long seed,
-               unsigned long long first, unsigned long long s, unsigned int* __restrict__ cnt,
-               unsigned long long* __restrict__ rec) {
+// Counting sort of diamonds into row order.  A diamond's bucket is the top
+// bits of its stage-1 target (Philox block 0 and T1's total only): the row
+// i = upper_bound(T1, target) is non-decreasing in the target, so bucket
+// order is row order; the T1 search itself is left to the draw kernel,
+// where neighbouring diamonds search the same few lines of T1.  At most
+// 2^kSortBitsMax buckets (a few rows each; the draw kernel's 256-diamond
+// windows span a few rows either way).  One block per SM takes a contiguous
+// chunk of the diamonds and counts them per bucket in shared memory (step
+// 1), the counts become per-(bucket, block) offsets (steps 2 and 3), and
+// each block places its diamonds with shared-memory cursors (step 4): no
+// global atomics and no per-diamond record between the steps.
+constexpr int kSortBitsMax = 15;
+
+__device__ __forceinline__ uint32_t sort_bucket(unsigned long long ell, uint2 key,
+                                                unsigned long long t1_total, int shift) {
+  const uint4 b0 = philox4x32_10(make_uint4((uint32_t)ell, (uint32_t)(ell >> 32), 0u, 0u), key);
+  const unsigned long long u0 = ((unsigned long long)b0.y << 32) | b0.x;
+  return (uint32_t)(draw_target(u0, t1_total) >> shift);
+}
+
+// Step 1: H[g * nbk + b] = diamonds of block g's chunk in bucket b.
+__global__ void __launch_bounds__(1024)
+k_sort_hist(const DevScalars* __restrict__ sc, unsigned long long seed, unsigned long long first,
+            unsigned long long s, unsigned long long chunk, uint32_t nbk,
+            unsigned int* __restrict__ H) {
+  extern __shared__ unsigned int sort_cnt[];
+  for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) sort_cnt[b] = 0;
+  __syncthreads();
   const unsigned long long t1_total = sc->t1_total;
   const int shift = sc->sort_shift;
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-  for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < s;
-       q += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long ell = first + q;
-    const uint4 b0 = philox4x32_10(make_uint4((uint32_t)ell, (uint32_t)(ell >> 32), 0u, 0u), key);
-    const unsigned long long u0 = ((unsigned long long)b0.y << 32) | b0.x;
-    const uint32_t b = (uint32_t)(draw_target(u0, t1_total) >> shift);
-    const unsigned int r = atomicAdd(cnt + b, 1u);
-    rec[q] = ((unsigned long long)b << 32) | r;
+  const unsigned long long q0 = (unsigned long long)blockIdx.x * chunk;
+  const unsigned long long q1 = q0 + chunk < s ? q0 + chunk : s;
+  for (unsigned long long q = q0 + threadIdx.x; q < q1; q += blockDim.x)
+    atomicAdd(&sort_cnt[sort_bucket(first + q, key, t1_total, shift)], 1u);
+  __syncthreads();
+  unsigned int* __restrict__ row = H + (size_t)blockIdx.x * nbk;
+  for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) row[b] = sort_cnt[b];
+}
+
+// Step 2: tot[b] = sum over the blocks of H[g][b].
+__global__ void __launch_bounds__(256)
+k_sort_colsum(const unsigned int* __restrict__ H, uint32_t nbk, int blocks,
+              unsigned int* __restrict__ tot) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbk) return;
+  unsigned int acc = 0;
+  for (int g = 0; g < blocks; ++g) acc += H[(size_t)g * nbk + b];
+  tot[b] = acc;
+}
+
+// Step 3 (after the exclusive scan of tot into base): H[g][b] becomes the
+// first position of block g's diamonds of bucket b.
+__global__ void __launch_bounds__(256)
+k_sort_coloff(unsigned int* __restrict__ H, uint32_t nbk, int blocks,
+              const unsigned int* __restrict__ base) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbk) return;
+  unsigned int acc = base[b];
+  for (int g = 0; g < blocks; ++g) {
+    const unsigned int c = H[(size_t)g * nbk + b];
+    H[(size_t)g * nbk + b] = acc;
+    acc += c;
   }
 }
 
-// Step 3: place diamond q at off[bucket] + rank.
-__global__ void __launch_bounds__(256)
-k_bucket_scatter(const unsigned long long* __restrict__ rec, const unsigned int* __restrict__ off,
-                 unsigned long long s, unsigned long long* __restrict__ sorted) {
-  for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < s;
-       q += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long e = rec[q];
-    const uint32_t i = (uint32_t)(e >> 32);
-    sorted[off[i] + (uint32_t)e] = ((unsigned long long)i << 32) | q;
+// Step 4: sorted[position] = (bucket << 32) | q for every diamond q of the
+// block's chunk.
+__global__ void __launch_bounds__(1024)
+k_sort_scatter(const DevScalars* __restrict__ sc, unsigned long long seed,
+               unsigned long long first, unsigned long long s, unsigned long long chunk,
+               uint32_t nbk, const unsigned int* __restrict__ H,
+               unsigned long long* __restrict__ sorted) {
+  extern __shared__ unsigned int sort_cnt[];
+  const unsigned int* __restrict__ row = H + (size_t)blockIdx.x * nbk;
+  for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) sort_cnt[b] = row[b];
+  __syncthreads();
+  const unsigned long long t1_total = sc->t1_total;
+  const int shift = sc->sort_shift;
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  const unsigned long long q0 = (unsigned long long)blockIdx.x * chunk;
+  const unsigned long long q1 = q0 + chunk < s ? q0 + chunk : s;
+  for (unsigned long long q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    const uint32_t b = sort_bucket(first + q, key, t1_total, shift);
+    const unsigned int pos = atomicAdd(&sort_cnt[b], 1u);
+    sorted[pos] = ((unsigned long long)b << 32) | q;
   }
 }
 
@@ -194,33 +248,83 @@ k_sample_sorted(const SampleParams p_, unsigned long long seed, unsigned long lo
 
 // X update for the row-ordered diamonds: a lean kernel (full occupancy) so
 // many inserts are in flight at once; consecutive entries share row i and
-// hence its hash region.
+// hence its hash region.  With row_hi > row_lo only the diamonds of rows
+// [row_lo, row_hi) are inserted: their records lie in the buckets the rows'
+// target range covers (positions from the bucket offsets `off`; records of
+// other rows in the two boundary buckets are skipped).
 __global__ void __launch_bounds__(256, 6)
 k_insert(const SampleParams p_, const unsigned long long* __restrict__ keys,
-         const long long* __restrict__ vals, unsigned long long s) {
+         const long long* __restrict__ vals, unsigned long long s,
+         const uint32_t* __restrict__ off, uint32_t row_lo, uint32_t row_hi) {
   const SampleParams p = resolve(p_);
+  // Log-bucket histogram of the positive x, kept as every addition moves
+  // its x from one bucket to another (block-local, added to p.xhist at the
+  // end), and each region row's largest bucket (warp-combined atomic max):
+  // the selection of Omega_t' reads these instead of every slot.
+  __shared__ int xh[1024];
+  const bool track = p.xhist != nullptr;
+  if (track) {
+    for (int b = threadIdx.x; b < 1024; b += blockDim.x) xh[b] = 0;
+    __syncthreads();
+  }
   Tally t;
+  unsigned long long q_lo = 0, q_hi = s;
+  if (row_hi > row_lo) {
+    const int shift = p.sc->sort_shift;
+    const unsigned long long t0 = row_lo ? __ldg((const unsigned long long*)p.T1 + row_lo - 1) : 0ull;
+    const unsigned long long t1 = __ldg((const unsigned long long*)p.T1 + row_hi - 1);
+    if (t1 > t0) {
+      q_lo = __ldg(off + (t0 >> shift));
+      q_hi = __ldg(off + ((t1 - 1) >> shift) + 1);
+    } else {
+      q_hi = 0;
+    }
+  }
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned long long rounds = (s + stride - 1) / stride;
+  unsigned long long q = q_lo + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t rows = row_hi - row_lo;   // 0: no filter
   // The next entry is loaded before the current one is inserted.
-  unsigned long long key = q < s ? __ldcs(keys + q) : EMPTY_KEY;
-  long long v = q < s ? __ldcs(vals + q) : 0;
-  for (unsigned long long r = 0; r < rounds; ++r) {
+  unsigned long long key = q < q_hi ? __ldcs(keys + q) : EMPTY_KEY;
+  long long v = q < q_hi ? __ldcs(vals + q) : 0;
+  for (; q < q_hi; q += stride) {
     const unsigned long long qn = q + stride;
-    const unsigned long long key_n = qn < s ? __ldcs(keys + qn) : EMPTY_KEY;
-    const long long v_n = qn < s ? __ldcs(vals + qn) : 0;
-    if (key != EMPTY_KEY) {
+    const unsigned long long key_n = qn < q_hi ? __ldcs(keys + qn) : EMPTY_KEY;
+    const long long v_n = qn < q_hi ? __ldcs(vals + qn) : 0;
+    uint32_t row = 0xFFFFFFFFu, rb = 0;
+    if (key != EMPTY_KEY && (rows == 0 || (uint32_t)(key >> 32) - row_lo < rows)) {
       ++t.inserted;
-      const int res = hash_add(p, key, v);
+      long long old = 0;
+      const int res = hash_add(p, key, v, track ? &old : nullptr);
       if (res == 0) t.full = true;
       if (res == 2) ++t.created;
+      if (track && res != 0) {
+        const long long now = old + v;
+        const int ob = old > 0 ? (int)log_bucket((unsigned long long)old) : -1;
+        const int nb = now > 0 ? (int)log_bucket((unsigned long long)now) : -1;
+        if (ob != nb) {
+          if (ob >= 0) atomicSub(&xh[ob], 1);
+          if (nb >= 0) atomicAdd(&xh[nb], 1);
+        }
+        row = (uint32_t)(key >> 32);
+        rb = nb >= 0 ? (uint32_t)nb + 1u : 0u;
+      }
+    }
+    if (track) {
+      const unsigned active = __activemask();
+      const unsigned peers = __match_any_sync(active, row);
+      const uint32_t best = __reduce_max_sync(peers, rb);
+      if (row != 0xFFFFFFFFu && best && (threadIdx.x & 31) == __ffs(peers) - 1)
+        atomicMax(p.rowmaxb + row, best);
     }
     key = key_n;
     v = v_n;
-    q = qn;
   }
   flush_tally(p, t);
+  if (track) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < 1024; b += blockDim.x)
+      if (xh[b]) atomicAdd(p.xhist + b, xh[b]);
+  }
 }
 
 // Diagnostic twin of k_sample: writes each diamond's draws instead of// Diagnostic twin of k_sample: writes each diamond's draws instead of
@@ -330,6 +434,8 @@ SampleParams make_params(const mad_ctx* ctx) {
   p.hmask = ctx->hcap - 1;
   p.hcap = ctx->hcap;
   p.hcap_alloc = ctx->hcap_alloc;
+  p.xhist = ctx->regioned ? ctx->xhist : nullptr;
+  p.rowmaxb = ctx->regioned ? ctx->rowmaxb : nullptr;
   p.max_probe = (uint32_t)(ctx->hcap < 4096 ? ctx->hcap : 4096);
   p.regioned = ctx->regioned ? 1 : 0;
   p.dense = ctx->dense ? 1 : 0;
@@ -357,19 +463,62 @@ mad_status pilot_inserts(mad_ctx* ctx, uint64_t n, uint64_t* hits, cudaStream_t 
   return MAD_OK;
 }
 
-uint64_t sort_buckets(int64_t m) {
-  uint64_t nbk = 1;
-  while (nbk < (uint64_t)m) nbk <<= 1;
-  return nbk;
+int sort_bits(int64_t m) {
+  int lg = 0;
+  while (lg < kSortBitsMax && (1ll << lg) < m) ++lg;
+  return lg;
+}
+
+uint64_t sort_buckets(int64_t m) { return 1ull << sort_bits(m); }
+
+// Blocks of the sort (one per SM).
+int sort_blocks() {
+  static int blocks = 0;
+  if (!blocks) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&blocks, cudaDevAttrMultiProcessorCount, dev);
+    if (blocks < 1) blocks = 1;
+  }
+  return blocks;
+}
+
+// Scratch of the sort and the draws for one batch: the per-(block, bucket)
+// counts, bucket totals and offsets, the scan's partials, the diamonds in
+// bucket order (overwritten by their increments) and their keys.
+struct SortScratch {
+  unsigned int* H;
+  unsigned int* tot;
+  unsigned int* base;
+  unsigned int* part;
+  unsigned long long* sorted;
+  unsigned long long* keys;
+  size_t bytes;
+};
+
+SortScratch carve_sort(void* p, uint64_t nbk, int blocks, uint64_t batch) {
+  SortScratch c;
+  char* b = (char*)p;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* q = b ? b + off : nullptr;
+    off += (bytes + 255) & ~(size_t)255;
+    return (void*)q;
+  };
+  c.H = (unsigned int*)take((size_t)nbk * blocks * sizeof(unsigned int));
+  c.tot = (unsigned int*)take(nbk * sizeof(unsigned int));
+  c.base = (unsigned int*)take((nbk + 1) * sizeof(unsigned int));
+  c.part = (unsigned int*)take(scan_partial_elems(nbk) * sizeof(unsigned int));
+  c.sorted = (unsigned long long*)take(batch * sizeof(unsigned long long));
+  c.keys = (unsigned long long*)take(batch * sizeof(unsigned long long));
+  c.bytes = off;
+  return c;
 }
 
 size_t sample_scratch_bytes(const mad_ctx* ctx, uint64_t s) {
   if (!ctx->dense || s == 0) return 0;
-  const uint64_t nbk = sort_buckets(ctx->m);
   const uint64_t batch = s < kSortBatch ? s : kSortBatch;
-  const size_t cnt_bytes = ((nbk + 1) * sizeof(uint32_t) + 255) & ~(size_t)255;
-  const size_t part_bytes = (scan_partial_elems(nbk) * sizeof(uint32_t) + 255) & ~(size_t)255;
-  return 2 * cnt_bytes + part_bytes + 2 * batch * sizeof(unsigned long long);
+  return carve_sort(nullptr, sort_buckets(ctx->m), sort_blocks(), batch).bytes;
 }
 
 mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, cudaStream_t st) {
@@ -384,39 +533,68 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
     phase_event(ctx, 3, st);
     return cuda_status(cudaGetLastError());
   }
-  const int full_count = full_grid<k_bucket_count>();
   const int full_sorted = full_grid<k_sample_sorted>();
   const int full_insert = full_grid<k_insert>();
-  // Buckets of 2^sort_shift target values (the shift comes from T1's total
-  // on the device), at most 2^ceil(log2 m) of them.
   const uint64_t nbk = sort_buckets(ctx->m);
+  const int blocks = sort_blocks();
+  const size_t sort_smem = nbk * sizeof(unsigned int);
+  static size_t smem_set = 0;
+  if (sort_smem > 48 * 1024 && smem_set < sort_smem) {
+    cudaFuncSetAttribute(k_sort_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
+    cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sort_smem);
+    smem_set = sort_smem;
+  }
   const uint64_t batch = s < kSortBatch ? s : kSortBatch;
-  const size_t cnt_bytes = ((nbk + 1) * sizeof(uint32_t) + 255) & ~(size_t)255;
-  const size_t part_bytes = (scan_partial_elems(nbk) * sizeof(uint32_t) + 255) & ~(size_t)255;
   mad_status rs = ensure_scratch(ctx, sample_scratch_bytes(ctx, s), st);
   if (rs != MAD_OK) return rs;
-  char* base = (char*)ctx->scratch;
-  uint32_t* cnt = (uint32_t*)base;
-  uint32_t* off = (uint32_t*)(base + cnt_bytes);
-  uint32_t* part = (uint32_t*)(base + 2 * cnt_bytes);
-  unsigned long long* rec = (unsigned long long*)(base + 2 * cnt_bytes + part_bytes);
-  unsigned long long* sorted = rec + batch;
+  const SortScratch w = carve_sort(ctx->scratch, nbk, blocks, batch);
   for (uint64_t done = 0; done < s; done += batch) {
     const uint64_t n = (s - done) < batch ? (s - done) : batch;
+    // Groups of rows whose regions hold about 32 MB each, while the
+    // regions still wait for their clearing (keys of row i only: not under
+    // MAD_GRAM, whose keys are ordered pairs of any two rows).
+    int chunks = 0;
+    if (!ctx->x_cleared && ctx->regioned && !(ctx->flags & MAD_GRAM)) {
+      const uint64_t bytes = hash_slot_bound(ctx) * 16ull;
+      chunks = (int)((bytes + (32ull << 20) - 1) >> 25);
+      chunks = chunks < 1 ? 1 : (chunks > 64 ? 64 : chunks);
+    }
     phase_event(ctx, 0, st);
-    cudaMemsetAsync(cnt, 0, nbk * sizeof(uint32_t), st);
-    k_bucket_count<<<grid_of(n, full_count), 256, 0, st>>>(ctx->sc, seed, first + done, n, cnt,
-                                                           rec);
-    count_launch(ctx);
-    if ((rs = scan_exclusive_u32(ctx, cnt, off, nbk, part, st)) != MAD_OK) return rs;
-    k_bucket_scatter<<<grid_of(n, full_count), 256, 0, st>>>(rec, off, n, sorted);
+    const unsigned long long chunk = (n + blocks - 1) / blocks;
+    const unsigned cols = (unsigned)((nbk + 255) / 256);
+    k_sort_hist<<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n, chunk,
+                                                 (uint32_t)nbk, w.H);
+    k_sort_colsum<<<cols, 256, 0, st>>>(w.H, (uint32_t)nbk, blocks, w.tot);
+    if ((rs = scan_exclusive_u32(ctx, w.tot, w.base, nbk, w.part, st)) != MAD_OK) return rs;
+    k_sort_coloff<<<cols, 256, 0, st>>>(w.H, (uint32_t)nbk, blocks, w.base);
+    k_sort_scatter<<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n, chunk,
+                                                    (uint32_t)nbk, w.H, w.sorted);
+    count_launch(ctx, 4);
     phase_event(ctx, 1, st);
-    k_sample_sorted<<<grid_of(n, full_sorted), 256, 0, st>>>(p, seed, first + done, n, sorted,
-                                                             rec);
+    k_sample_sorted<<<grid_of(n, full_sorted), 256, 0, st>>>(p, seed, first + done, n, w.sorted,
+                                                             w.keys);
+    count_launch(ctx);
     phase_event(ctx, 2, st);
-    k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, rec, (const long long*)sorted, n);
+    if (chunks > 0) {
+      // First pass after a clear: the regions of each group of rows are
+      // emptied just before that group's inserts, which then find them in
+      // L2 instead of reading the cleared lines back from DRAM.
+      for (int c = 0; c < chunks; ++c) {
+        const int64_t r0 = ctx->m * c / chunks, r1 = ctx->m * (c + 1) / chunks;
+        if (r1 <= r0) continue;
+        if ((rs = clear_slots(ctx, ctx->hreg + r0, ctx->hreg + r1, st)) != MAD_OK) return rs;
+        k_insert<<<grid_of(n / chunks + 1, full_insert), 256, 0, st>>>(
+            p, w.keys, (const long long*)w.sorted, n, w.base, (uint32_t)r0, (uint32_t)r1);
+        count_launch(ctx);
+      }
+      ctx->x_cleared = true;
+    } else {
+      k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, w.keys, (const long long*)w.sorted, n,
+                                                        nullptr, 0, 0);
+      count_launch(ctx);
+    }
     phase_event(ctx, 3, st);
-    count_launch(ctx, 3);
   }
   return cuda_status(cudaGetLastError());
 }

@@ -878,7 +878,15 @@ __global__ void __launch_bounds__(256)
 k_clear_slots(unsigned long long* __restrict__ keys, long long* __restrict__ vals, uint64_t cap,
               const unsigned long long* lo_dev, const unsigned long long* n_dev) {
   const uint64_t n = dev_len(cap, n_dev);
-  const uint64_t lo = lo_dev ? (*lo_dev & ~1ull) : 0;   // an even start (16-byte stores)
+  uint64_t lo = lo_dev ? *lo_dev : 0;
+  if (lo >= n) return;
+  if (lo & 1) {   // an odd first slot alone, then 16-byte stores
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      keys[lo] = EMPTY_KEY;
+      vals[lo] = 0;
+    }
+    ++lo;
+  }
   const uint64_t stride = 2ull * gridDim.x * blockDim.x;
   for (uint64_t q = lo + 2ull * (blockIdx.x * blockDim.x + threadIdx.x); q < n; q += stride) {
     if (q + 1 < n) {
@@ -997,7 +1005,7 @@ mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st) {
   const unsigned long long* r64 = ctx->integer ? ctx->r64 : nullptr;
   k_t1_chunk_sums<<<(unsigned)chunks, 256, 0, st>>>(r, r64, ctx->m, clog2m, partial, ctx->sc);
   const int bl_m = t1_guide_width(ctx->m);
-  k_t1_chunk_offsets<<<1, 32, 0, st>>>(partial, chunks, bl_m, clog2m,
+  k_t1_chunk_offsets<<<1, 32, 0, st>>>(partial, chunks, bl_m, sort_bits(ctx->m),
                                        ceil_log2_host(ctx->s_max), ctx->dense ? 1 : 0, ctx->sc);
   k_t1_write<<<(unsigned)chunks, 256, 0, st>>>(r, r64, ctx->m, clog2m, partial, ctx->T1, ctx->sc);
   count_launch(ctx, 3);
