@@ -213,6 +213,8 @@ k_b_rows_wide(const T* __restrict__ B, int64_t n, int64_t ldb, float* __restrict
 
   uint32_t* __restrict__ out = TB + k * n;
   const int e = total > 0.0f ? 29 - ilogb_pos(total) : 0;
+  const bool plain = e >= -126 && e <= 127;   // one exact scaling per entry
+  const float scale = plain ? pow2f(e) : 0.0f;
   float v[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
@@ -231,7 +233,17 @@ k_b_rows_wide(const T* __restrict__ B, int64_t n, int64_t ldb, float* __restrict
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int64_t idx = base + 4 * t + c;
-      if (idx < n && total > 0.0f) local += quantize_row(fabsf(v[c]), e);
+      if (idx < n && total > 0.0f) {
+        const float w = fabsf(v[c]);
+        uint32_t qv;
+        if (plain) {
+          qv = (uint32_t)__float2ll_rn(__fmul_rn(w, scale));
+          qv += (w > 0.0f && qv == 0u) ? 1u : 0u;
+        } else {
+          qv = quantize_row(w, e);
+        }
+        local += qv;
+      }
       q[c] = local;
     }
     const uint32_t inc = warp_inclusive_u32(local, lane);
@@ -423,6 +435,10 @@ k_a_rows_short(const T* __restrict__ A, int64_t m, int d, int64_t lda,
     const bool live = s > 0.0f;
     const int e2 = live ? 29 - ilogb_pos(s) : 0;
     const int ea = live ? 29 - ilogb_pos(na) : 0;
+    // Both exponents inside the normal range: one exact power-of-two
+    // scaling per entry (what quantize_row does in that range).
+    const bool plain = e2 >= -126 && e2 <= 127 && ea >= -126 && ea <= 127;
+    const float s2 = plain ? pow2f(e2) : 0.0f, sa = plain ? pow2f(ea) : 0.0f;
     uint32_t i2[NC], ia[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -430,8 +446,16 @@ k_a_rows_short(const T* __restrict__ A, int64_t m, int d, int64_t lda,
       uint32_t q2 = 0, qa = 0;
       if (live && idx < d) {
         const float a = fabsf(v[c]);
-        q2 = quantize_row(__fmul_rn(a, nb[idx]), e2);
-        qa = quantize_row(a, ea);
+        const float w2 = __fmul_rn(a, nb[idx]);
+        if (plain) {
+          q2 = (uint32_t)__float2ll_rn(__fmul_rn(w2, s2));
+          qa = (uint32_t)__float2ll_rn(__fmul_rn(a, sa));
+          q2 += (w2 > 0.0f && q2 == 0u) ? 1u : 0u;
+          qa += (a > 0.0f && qa == 0u) ? 1u : 0u;
+        } else {
+          q2 = quantize_row(w2, e2);
+          qa = quantize_row(a, ea);
+        }
       }
       i2[c] = q2;
       ia[c] = qa;
