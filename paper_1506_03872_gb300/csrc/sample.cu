@@ -558,7 +558,12 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
     if (!ctx->x_cleared && ctx->regioned && !(ctx->flags & MAD_GRAM)) {
       const uint64_t bytes = hash_slot_bound(ctx) * 16ull;
       chunks = (int)((bytes + (32ull << 20) - 1) >> 25);
-      chunks = chunks < 1 ? 1 : (chunks > 64 ? 64 : chunks);
+      chunks = chunks > 64 ? 64 : chunks;
+      // At least 1024 rows (4096 slots) per group, more than a probe run
+      // can cross.
+      const int64_t most = ctx->m / 1024;
+      chunks = (int64_t)chunks > most ? (int)most : chunks;
+      chunks = chunks < 1 ? 1 : chunks;
     }
     phase_event(ctx, 0, st);
     const unsigned long long chunk = (n + blocks - 1) / blocks;
@@ -578,12 +583,27 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
     phase_event(ctx, 2, st);
     if (chunks > 0) {
       // First pass after a clear: the regions of each group of rows are
-      // emptied just before that group's inserts, which then find them in
-      // L2 instead of reading the cleared lines back from DRAM.
+      // emptied shortly before that group's inserts, which then find them
+      // in L2 instead of reading the cleared lines back from DRAM.  Linear
+      // probing may carry a key past its group's last region (at most
+      // max_probe slots, far fewer than a group holds), so group c + 1 is
+      // cleared before group c inserts.
+      auto group = [&](int c, int64_t* r0, int64_t* r1) {
+        *r0 = ctx->m * c / chunks;
+        *r1 = ctx->m * (c + 1) / chunks;
+      };
+      int64_t r0, r1;
+      group(0, &r0, &r1);
+      if ((rs = clear_slots(ctx, ctx->hreg + r0, ctx->hreg + r1, st)) != MAD_OK) return rs;
       for (int c = 0; c < chunks; ++c) {
-        const int64_t r0 = ctx->m * c / chunks, r1 = ctx->m * (c + 1) / chunks;
+        if (c + 1 < chunks) {
+          int64_t n0, n1;
+          group(c + 1, &n0, &n1);
+          if (n1 > n0 && (rs = clear_slots(ctx, ctx->hreg + n0, ctx->hreg + n1, st)) != MAD_OK)
+            return rs;
+        }
+        group(c, &r0, &r1);
         if (r1 <= r0) continue;
-        if ((rs = clear_slots(ctx, ctx->hreg + r0, ctx->hreg + r1, st)) != MAD_OK) return rs;
         k_insert<<<grid_of(n / chunks + 1, full_insert), 256, 0, st>>>(
             p, w.keys, (const long long*)w.sorted, n, w.base, (uint32_t)r0, (uint32_t)r1);
         count_launch(ctx);

@@ -193,3 +193,35 @@ def test_empty_and_degenerate_requests():
         assert nr == 0
     finally:
         c.close()
+
+
+def test_grouped_clearing_after_reset():
+    """A hash above 32 MB is cleared group by group during the first
+    sampling pass (several row groups here); after a reset over the keys of
+    an earlier run, X still equals the oracle's for the new seed."""
+    import oracle
+    mad = _mad()
+    rng = np.random.Generator(np.random.PCG64(49))
+    A = (rng.standard_normal((4096, 16)) * np.exp(0.5 * rng.standard_normal((4096, 1))))
+    B = rng.standard_normal((16, 2000))
+    A, B = A.astype(np.float32), B.astype(np.float32)
+    s = 1_000_000
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    with mad.Context() as c:
+        mad.mad_build_tables(c.ctx, mad.dense(tA), mad.dense(tB), s)
+        assert mad.mad_stats(c.ctx)["hash_capacity"] * 16 > (24 << 20)
+        mad.mad_sample(c.ctx, s, 5)
+        mad.mad_reset_hash(c.ctx)
+        mad.mad_sample(c.ctx, s, 6)
+        keys, vals, n = mad.mad_export_x(c.ctx, cap=s + 1)
+        st = mad.mad_stats(c.ctx)
+    keys = keys.cpu().numpy().view(np.uint64)
+    vals = vals.cpu().numpy()
+    order = np.argsort(keys)
+    o = oracle.Oracle(oracle.Matrix(A), oracle.Matrix(B), 0, s)
+    assert o.sample(s, 6) == 0
+    ok, ov = o.x()
+    assert st["device_error"] == 0
+    assert n == len(ok)
+    assert np.array_equal(keys[order], ok)
+    assert np.array_equal(vals[order], ov)
