@@ -64,8 +64,6 @@ void free_tables(mad_ctx* ctx, cudaStream_t st) {
   free_async(ctx->hkeys, st);
   free_async(ctx->hvals, st);
   free_async(ctx->hreg, st);
-  free_async(ctx->xhist, st);
-  free_async(ctx->rowmaxb, st);
   free_async(ctx->T2g_ptr, st);
   free_async(ctx->T2g, st);
   free_async(ctx->T2g_sh, st);
@@ -113,19 +111,8 @@ bool valid_csr(const mad_matrix* M) {
          M->cols > 0 && M->cols < (1ll << 31);
 }
 
-// Empty X: every slot up to the hash's extent, except dense regions whose
-// keys all follow their row (no MAD_GRAM): those are cleared by the first
-// sampling pass, group by group, just before its inserts.
+// Empty X: every slot up to the hash's extent.
 mad_status clear_x_slots(mad_ctx* ctx, cudaStream_t st) {
-  if (ctx->xhist) {
-    cudaMemsetAsync(ctx->xhist, 0, 1024 * sizeof(int), st);
-    cudaMemsetAsync(ctx->rowmaxb, 0, (size_t)ctx->m * sizeof(unsigned int), st);
-  }
-  if (ctx->regioned && !(ctx->flags & MAD_GRAM)) {
-    ctx->x_cleared = false;
-    return MAD_OK;
-  }
-  ctx->x_cleared = true;
   return clear_slots(ctx, nullptr, hash_extent(ctx), st);
 }
 
@@ -234,8 +221,6 @@ mad_status alloc_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, 
   if (ctx->regioned) {
     cap = hash_region_bound((uint64_t)ctx->m, s_max);
     if ((rs = alloc(ctx, ctx->hreg, (size_t)ctx->m + 1, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx, ctx->xhist, 1024, st)) != MAD_OK) return rs;
-    if ((rs = alloc(ctx, ctx->rowmaxb, (size_t)ctx->m, st)) != MAD_OK) return rs;
   }
   if (cap) {
     ctx->hcap = ctx->hcap_alloc = cap;
@@ -467,11 +452,6 @@ mad_status mad_topk(mad_ctx* ctx, uint32_t tprime, mad_pair* out_dev, uint32_t* 
   mad_status rs = read_scalars(ctx, &hs, st);
   if (rs != MAD_OK) return rs;
   if ((rs = device_error_status(hs.err)) != MAD_OK) return rs;
-  if (!ctx->x_cleared) {   // nothing sampled since the last clear
-    ctx->positive = 0;
-    ctx->distinct = 0;
-    return MAD_OK;
-  }
   uint64_t bound = hs.new_keys < ctx->hcap ? hs.new_keys : ctx->hcap;
   if (tprime == 0 || bound == 0) return MAD_OK;
   if ((rs = ensure_scratch(ctx, select_ws_bytes(bound, tprime), st)) != MAD_OK) return rs;
@@ -584,7 +564,6 @@ mad_status mad_export_x(mad_ctx* ctx, uint64_t* keys_dev, int64_t* vals_dev, uin
   if (!ctx || !n_host || (cap && (!keys_dev || !vals_dev))) return MAD_ERR_ARG;
   *n_host = 0;
   if (!ctx->built) return MAD_ERR_STATE;
-  if (!ctx->x_cleared) return MAD_OK;   // nothing sampled since the last clear
   cudaStream_t st = (cudaStream_t)stream;
   mad_status rs = ensure_scratch(ctx, 256, st);
   if (rs != MAD_OK) return rs;

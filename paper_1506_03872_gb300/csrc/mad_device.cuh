@@ -269,13 +269,11 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 // from that slot, so slots are still taken in linear-probing order.
 // Probing wraps from slot hi back to slot lo ([lo, hi) is the whole table,
 // or a region whose bounds are multiples of 4).  Returns 0 when the probe
-// limit is hit, 1 when the key existed, 2 when this call created it; with
-// old_out, the value before this addition goes there.
+// limit is hit, 1 when the key existed, 2 when this call created it.
 __device__ __forceinline__ int hash_add_from(unsigned long long* __restrict__ keys,
                                              long long* __restrict__ vals, uint64_t lo,
                                              uint64_t hi, uint64_t slot, uint32_t max_probe,
-                                             unsigned long long key, long long v,
-                                             long long* old_out = nullptr) {
+                                             unsigned long long key, long long v) {
   uint32_t probes = 0;
   while (probes < max_probe) {
     const uint64_t g = slot & ~3ull;
@@ -320,10 +318,7 @@ __device__ __forceinline__ int hash_add_from(unsigned long long* __restrict__ ke
       }
       created = prev == EMPTY_KEY ? 2 : 0;
     }
-    if (old_out)
-      *old_out = (long long)atomicAdd((unsigned long long*)vals + g + pick, (unsigned long long)v);
-    else
-      atomicAdd((unsigned long long*)vals + g + pick, (unsigned long long)v);
+    atomicAdd((unsigned long long*)vals + g + pick, (unsigned long long)v);
     return created ? 2 : 1;
   }
   return 0;
@@ -372,10 +367,8 @@ __device__ __forceinline__ uint64_t home_slot(const SampleParams& p, unsigned lo
   return mix64(key) & p.hmask;
 }
 
-__device__ __forceinline__ int hash_add(const SampleParams& p, unsigned long long key, long long v,
-                                        long long* old_out = nullptr) {
-  return hash_add_from(p.hkeys, p.hvals, 0, p.hcap, home_slot(p, key), p.max_probe, key, v,
-                       old_out);
+__device__ __forceinline__ int hash_add(const SampleParams& p, unsigned long long key, long long v) {
+  return hash_add_from(p.hkeys, p.hvals, 0, p.hcap, home_slot(p, key), p.max_probe, key, v);
 }
 
 // Histogram pick by one whole block of 256 threads: the highest bucket b

@@ -95,11 +95,6 @@ struct SampleParams {
   uint64_t hmask;
   uint64_t hcap;
   uint64_t hcap_alloc;
-  // Dense hashes (null otherwise): the log-bucket histogram of the positive
-  // x (1024 signed counts, kept by the inserts) and, per region row, one
-  // more than the largest log bucket any of its x has reached (0: none).
-  int* xhist;
-  unsigned int* rowmaxb;
   uint32_t max_probe;
   int regioned;
   // Modes.
@@ -184,12 +179,6 @@ struct mad_ctx {
   // Dense inputs: row i's home region is [hreg[i], hreg[i+1]) (m + 1
   // offsets; hreg[m] is the end of the regions).
   unsigned long long* hreg = nullptr;
-  int* xhist = nullptr;                 // see SampleParams
-  unsigned int* rowmaxb = nullptr;
-  // False while the clearing of the dense regions is left to the first
-  // sampling pass (which clears each group of rows just before inserting
-  // into it); a read of X before that finds it empty.
-  bool x_cleared = true;
   bool regioned = false;
   uint64_t hcap = 0, hcap_alloc = 0, hcap_request = 0;
   mad::DevScalars* sc = nullptr;
@@ -298,14 +287,7 @@ mad_status items_to_pairs(mad_ctx* ctx, const Item* items, uint64_t n, const mad
 // over_err is given, a device length above cap sets DERR_SELECT there.
 void tile_select_dev(mad_ctx* ctx, const Item* in, uint64_t cap, uint64_t K,
                      const unsigned long long* n_dev, unsigned int* over_err, Item* sorted,
-                     uint32_t* pos, Item* out, cudaStream_t st,
-                     const unsigned int* gate = nullptr);
-// The same for a short K (at most 4096 items at or above the threshold):
-// one block selects and sorts; only when more items tie at the threshold do
-// the tile kernels (gated on *gate, a device word this call sets) run.
-void top_small_dev(mad_ctx* ctx, const Item* in, uint64_t cap, uint64_t K,
-                   const unsigned long long* n_dev, Item* sorted, uint32_t* pos, Item* out,
-                   unsigned int* gate, cudaStream_t st);
+                     uint32_t* pos, Item* out, cudaStream_t st);
 constexpr uint64_t kDevSelectCap = 1ull << 17;
 size_t dev_select_state_bytes();
 // Omega_t' from the hash whose extent is *hcap_dev slots (at most

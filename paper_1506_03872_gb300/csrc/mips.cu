@@ -311,7 +311,6 @@ mad_status mad_mips_items(mad_ctx* ctx, const mad_matrix* B, uint64_t s_max, mad
   pool_free(ctx->na, st); pool_free(ctx->nb, st); pool_free(ctx->r, st); pool_free(ctx->r64, st);
   pool_free(ctx->bt, st); pool_free(ctx->hkeys, st); pool_free(ctx->hvals, st);
   pool_free(ctx->hreg, st); pool_free(ctx->T2g_ptr, st);
-  pool_free(ctx->xhist, st); pool_free(ctx->rowmaxb, st);
   pool_free(ctx->T2g, st); pool_free(ctx->T2g_sh, st); pool_free(ctx->bloom, st);
   pool_free(ctx->TBg, st); pool_free(ctx->TBg_sh, st);
   pool_free(ctx->mips_s, st); pool_free(ctx->mips_chunk_q, st); pool_free(ctx->mips_chunk_l0, st);

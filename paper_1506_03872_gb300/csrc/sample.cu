@@ -163,6 +163,7 @@ k_sort_colsum(const unsigned int* __restrict__ H, uint32_t nbk, int blocks,
   const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbk) return;
   unsigned int acc = 0;
+#pragma unroll 8
   for (int g = 0; g < blocks; ++g) acc += H[(size_t)g * nbk + b];
   tot[b] = acc;
 }
@@ -175,7 +176,19 @@ k_sort_coloff(unsigned int* __restrict__ H, uint32_t nbk, int blocks,
   const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbk) return;
   unsigned int acc = base[b];
-  for (int g = 0; g < blocks; ++g) {
+  int g = 0;
+  // Eight loads in flight before their eight stores.
+  for (; g + 8 <= blocks; g += 8) {
+    unsigned int c[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) c[u] = H[(size_t)(g + u) * nbk + b];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      H[(size_t)(g + u) * nbk + b] = acc;
+      acc += c[u];
+    }
+  }
+  for (; g < blocks; ++g) {
     const unsigned int c = H[(size_t)g * nbk + b];
     H[(size_t)g * nbk + b] = acc;
     acc += c;
@@ -248,83 +261,33 @@ k_sample_sorted(const SampleParams p_, unsigned long long seed, unsigned long lo
 
 // X update for the row-ordered diamonds: a lean kernel (full occupancy) so
 // many inserts are in flight at once; consecutive entries share row i and
-// hence its hash region.  With row_hi > row_lo only the diamonds of rows
-// [row_lo, row_hi) are inserted: their records lie in the buckets the rows'
-// target range covers (positions from the bucket offsets `off`; records of
-// other rows in the two boundary buckets are skipped).
+// hence its hash region.
 __global__ void __launch_bounds__(256, 6)
 k_insert(const SampleParams p_, const unsigned long long* __restrict__ keys,
-         const long long* __restrict__ vals, unsigned long long s,
-         const uint32_t* __restrict__ off, uint32_t row_lo, uint32_t row_hi) {
+         const long long* __restrict__ vals, unsigned long long s) {
   const SampleParams p = resolve(p_);
-  // Log-bucket histogram of the positive x, kept as every addition moves
-  // its x from one bucket to another (block-local, added to p.xhist at the
-  // end), and each region row's largest bucket (warp-combined atomic max):
-  // the selection of Omega_t' reads these instead of every slot.
-  __shared__ int xh[1024];
-  const bool track = p.xhist != nullptr;
-  if (track) {
-    for (int b = threadIdx.x; b < 1024; b += blockDim.x) xh[b] = 0;
-    __syncthreads();
-  }
   Tally t;
-  unsigned long long q_lo = 0, q_hi = s;
-  if (row_hi > row_lo) {
-    const int shift = p.sc->sort_shift;
-    const unsigned long long t0 = row_lo ? __ldg((const unsigned long long*)p.T1 + row_lo - 1) : 0ull;
-    const unsigned long long t1 = __ldg((const unsigned long long*)p.T1 + row_hi - 1);
-    if (t1 > t0) {
-      q_lo = __ldg(off + (t0 >> shift));
-      q_hi = __ldg(off + ((t1 - 1) >> shift) + 1);
-    } else {
-      q_hi = 0;
-    }
-  }
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  unsigned long long q = q_lo + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t rows = row_hi - row_lo;   // 0: no filter
+  unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long rounds = (s + stride - 1) / stride;
   // The next entry is loaded before the current one is inserted.
-  unsigned long long key = q < q_hi ? __ldcs(keys + q) : EMPTY_KEY;
-  long long v = q < q_hi ? __ldcs(vals + q) : 0;
-  for (; q < q_hi; q += stride) {
+  unsigned long long key = q < s ? __ldcs(keys + q) : EMPTY_KEY;
+  long long v = q < s ? __ldcs(vals + q) : 0;
+  for (unsigned long long r = 0; r < rounds; ++r) {
     const unsigned long long qn = q + stride;
-    const unsigned long long key_n = qn < q_hi ? __ldcs(keys + qn) : EMPTY_KEY;
-    const long long v_n = qn < q_hi ? __ldcs(vals + qn) : 0;
-    uint32_t row = 0xFFFFFFFFu, rb = 0;
-    if (key != EMPTY_KEY && (rows == 0 || (uint32_t)(key >> 32) - row_lo < rows)) {
+    const unsigned long long key_n = qn < s ? __ldcs(keys + qn) : EMPTY_KEY;
+    const long long v_n = qn < s ? __ldcs(vals + qn) : 0;
+    if (key != EMPTY_KEY) {
       ++t.inserted;
-      long long old = 0;
-      const int res = hash_add(p, key, v, track ? &old : nullptr);
+      const int res = hash_add(p, key, v);
       if (res == 0) t.full = true;
       if (res == 2) ++t.created;
-      if (track && res != 0) {
-        const long long now = old + v;
-        const int ob = old > 0 ? (int)log_bucket((unsigned long long)old) : -1;
-        const int nb = now > 0 ? (int)log_bucket((unsigned long long)now) : -1;
-        if (ob != nb) {
-          if (ob >= 0) atomicSub(&xh[ob], 1);
-          if (nb >= 0) atomicAdd(&xh[nb], 1);
-        }
-        row = (uint32_t)(key >> 32);
-        rb = nb >= 0 ? (uint32_t)nb + 1u : 0u;
-      }
-    }
-    if (track) {
-      const unsigned active = __activemask();
-      const unsigned peers = __match_any_sync(active, row);
-      const uint32_t best = __reduce_max_sync(peers, rb);
-      if (row != 0xFFFFFFFFu && best && (threadIdx.x & 31) == __ffs(peers) - 1)
-        atomicMax(p.rowmaxb + row, best);
     }
     key = key_n;
     v = v_n;
+    q = qn;
   }
   flush_tally(p, t);
-  if (track) {
-    __syncthreads();
-    for (int b = threadIdx.x; b < 1024; b += blockDim.x)
-      if (xh[b]) atomicAdd(p.xhist + b, xh[b]);
-  }
 }
 
 // Diagnostic twin of k_sample: writes each diamond's draws instead of// Diagnostic twin of k_sample: writes each diamond's draws instead of
@@ -434,8 +397,6 @@ SampleParams make_params(const mad_ctx* ctx) {
   p.hmask = ctx->hcap - 1;
   p.hcap = ctx->hcap;
   p.hcap_alloc = ctx->hcap_alloc;
-  p.xhist = ctx->regioned ? ctx->xhist : nullptr;
-  p.rowmaxb = ctx->regioned ? ctx->rowmaxb : nullptr;
   p.max_probe = (uint32_t)(ctx->hcap < 4096 ? ctx->hcap : 4096);
   p.regioned = ctx->regioned ? 1 : 0;
   p.dense = ctx->dense ? 1 : 0;
@@ -551,20 +512,6 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
   const SortScratch w = carve_sort(ctx->scratch, nbk, blocks, batch);
   for (uint64_t done = 0; done < s; done += batch) {
     const uint64_t n = (s - done) < batch ? (s - done) : batch;
-    // Groups of rows whose regions hold about 32 MB each, while the
-    // regions still wait for their clearing (keys of row i only: not under
-    // MAD_GRAM, whose keys are ordered pairs of any two rows).
-    int chunks = 0;
-    if (!ctx->x_cleared && ctx->regioned && !(ctx->flags & MAD_GRAM)) {
-      const uint64_t bytes = hash_slot_bound(ctx) * 16ull;
-      chunks = (int)((bytes + (32ull << 20) - 1) >> 25);
-      chunks = chunks > 64 ? 64 : chunks;
-      // At least 1024 rows (4096 slots) per group, more than a probe run
-      // can cross.
-      const int64_t most = ctx->m / 1024;
-      chunks = (int64_t)chunks > most ? (int)most : chunks;
-      chunks = chunks < 1 ? 1 : chunks;
-    }
     phase_event(ctx, 0, st);
     const unsigned long long chunk = (n + blocks - 1) / blocks;
     const unsigned cols = (unsigned)((nbk + 255) / 256);
@@ -581,39 +528,8 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
                                                              w.keys);
     count_launch(ctx);
     phase_event(ctx, 2, st);
-    if (chunks > 0) {
-      // First pass after a clear: the regions of each group of rows are
-      // emptied shortly before that group's inserts, which then find them
-      // in L2 instead of reading the cleared lines back from DRAM.  Linear
-      // probing may carry a key past its group's last region (at most
-      // max_probe slots, far fewer than a group holds), so group c + 1 is
-      // cleared before group c inserts.
-      auto group = [&](int c, int64_t* r0, int64_t* r1) {
-        *r0 = ctx->m * c / chunks;
-        *r1 = ctx->m * (c + 1) / chunks;
-      };
-      int64_t r0, r1;
-      group(0, &r0, &r1);
-      if ((rs = clear_slots(ctx, ctx->hreg + r0, ctx->hreg + r1, st)) != MAD_OK) return rs;
-      for (int c = 0; c < chunks; ++c) {
-        if (c + 1 < chunks) {
-          int64_t n0, n1;
-          group(c + 1, &n0, &n1);
-          if (n1 > n0 && (rs = clear_slots(ctx, ctx->hreg + n0, ctx->hreg + n1, st)) != MAD_OK)
-            return rs;
-        }
-        group(c, &r0, &r1);
-        if (r1 <= r0) continue;
-        k_insert<<<grid_of(n / chunks + 1, full_insert), 256, 0, st>>>(
-            p, w.keys, (const long long*)w.sorted, n, w.base, (uint32_t)r0, (uint32_t)r1);
-        count_launch(ctx);
-      }
-      ctx->x_cleared = true;
-    } else {
-      k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, w.keys, (const long long*)w.sorted, n,
-                                                        nullptr, 0, 0);
-      count_launch(ctx);
-    }
+    k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, w.keys, (const long long*)w.sorted, n);
+    count_launch(ctx);
     phase_event(ctx, 3, st);
   }
   return cuda_status(cudaGetLastError());

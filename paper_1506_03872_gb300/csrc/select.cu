@@ -33,7 +33,7 @@ struct SelState {
   unsigned long long maxp;
   unsigned long long positive;
   unsigned int ticket3;
-  unsigned int rowb;          // rows whose largest bucket + 1 reaches this are scanned
+  unsigned int pad3;
   unsigned long long n_cur;   // survivors in the current list
   unsigned long long k_rem;   // survivors still to be taken
   unsigned long long tp, tk;  // threshold composite (tk applies to ~key)
@@ -255,66 +255,6 @@ k_compact_ge(const unsigned long long* __restrict__ keys, const long long* __res
   }
 }
 
-// Dense hashes: the threshold from the histogram the inserts keep (bucket b*
-// where the count from the top reaches K), without reading the slots.
-__global__ void __launch_bounds__(256)
-k_pick_xhist(const int* __restrict__ xhist, unsigned long long K, SelState* st) {
-  unsigned long long total = 0;
-  const int b = block_pick_from_top<1024>((const unsigned int*)xhist, K, &total);
-  if (threadIdx.x == 0) {
-    st->theta = b >= 0 ? bucket_floor((uint32_t)b) : 1ull;  // fewer than K positive: take all
-    st->rowb = b >= 0 ? (unsigned int)b + 1u : 1u;
-    st->positive = total;
-    int top = 1023;
-    while (top >= 0 && __ldcg(xhist + top) <= 0) --top;
-    st->maxp = top >= 0 ? (top < 1023 ? bucket_floor((uint32_t)top + 1) - 1 : ~0ull) : 0ull;
-  }
-}
-
-// Dense hashes: one warp per region row whose largest bucket reaches the
-// threshold.  Linear probing leaves every key of row r in the run of
-// occupied slots that starts in r's region, so the warp scans the region
-// and then the slots after it up to the first empty one (wrapping at the
-// table's end), and compacts the keys of row r at or above the threshold.
-__global__ void __launch_bounds__(256)
-k_compact_rows(const unsigned long long* __restrict__ keys, const long long* __restrict__ vals,
-               const unsigned long long* __restrict__ hreg, const unsigned int* __restrict__ rowmaxb,
-               int64_t m, uint64_t cap_max, const SelState* st, Item* __restrict__ out,
-               uint64_t out_cap, unsigned long long* counter) {
-  const uint64_t cap = dev_len(cap_max, hreg + m);
-  const unsigned long long theta = st->theta;
-  const unsigned int rowb = st->rowb;
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < m; r += warps) {
-    if (__ldg(rowmaxb + r) < rowb) continue;
-    const uint64_t r0 = hreg[r], len = hreg[r + 1] - r0;
-    for (uint64_t d = 0; d < cap; d += 32) {
-      const uint64_t off = d + lane;   // distance from the region's start
-      uint64_t slot = r0 + off;
-      while (slot >= cap) slot -= cap;
-      const unsigned long long key = off < cap ? keys[slot] : EMPTY_KEY;
-      // Past the region, the run ends at the first empty slot (a lane past
-      // the whole table counts as one).
-      const unsigned stop_mask = __ballot_sync(0xFFFFFFFFu, off >= len && key == EMPTY_KEY);
-      const int stop = stop_mask ? __ffs(stop_mask) - 1 : 32;
-      bool want = false;
-      Item it;
-      if (lane < stop && key != EMPTY_KEY && (key >> 32) == (unsigned long long)r) {
-        const long long v = vals[slot];
-        if (v > 0 && (unsigned long long)v >= theta) {
-          want = true;
-          it.p = (unsigned long long)v;
-          it.key = key;
-          it.aux = slot;
-        }
-      }
-      append(out, counter, want, it, out_cap);
-      if (stop_mask) break;
-    }
-  }
-}
-
 // ---- tile sort + merge rank (lists up to 2^17 items) ------------------------
 // Total order: p desc, key asc, then input position asc (so repeated keys
 // still get distinct ranks).  Step 1 sorts tiles of 2048 items in shared
@@ -333,10 +273,9 @@ __device__ __forceinline__ bool item_before(unsigned long long ap, unsigned long
 __global__ void __launch_bounds__(1024)
 k_tile_sort(const Item* __restrict__ in, unsigned n_max, unsigned K, Item* __restrict__ out,
             uint32_t* __restrict__ pos_out, const unsigned long long* n_dev,
-            unsigned int* over_err, const unsigned int* gate) {
+            unsigned int* over_err) {
   __shared__ unsigned long long sp[kTile], sk[kTile];
   __shared__ uint32_t si[kTile];
-  if (gate && *gate == 0u) return;   // the list was already selected
   // Under a device count: a list longer than the workspace is reported.
   if (over_err && blockIdx.x == 0 && threadIdx.x == 0 && *n_dev > n_max)
     atomicOr(over_err, DERR_SELECT);
@@ -383,9 +322,7 @@ k_tile_sort(const Item* __restrict__ in, unsigned n_max, unsigned K, Item* __res
 
 __global__ void __launch_bounds__(256)
 k_merge_rank(const Item* __restrict__ tiles, const uint32_t* __restrict__ pos, unsigned n_max,
-             unsigned K, Item* __restrict__ out, const unsigned long long* n_dev,
-             const unsigned int* gate) {
-  if (gate && *gate == 0u) return;
+             unsigned K, Item* __restrict__ out, const unsigned long long* n_dev) {
   const unsigned n = (unsigned)dev_len(n_max, n_dev);
   const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= n) return;
@@ -420,15 +357,15 @@ void tile_select(mad_ctx* ctx, const SelectWs& ws, const Item* in, uint64_t n, u
   const unsigned tiles = (unsigned)((n + kTile - 1) / kTile);
   if (tiles == 1 && in != ws.out) {
     k_tile_sort<<<1, kTile / 2, 0, st>>>(in, (unsigned)n, (unsigned)K, ws.out, nullptr, nullptr,
-                                         nullptr, nullptr);
+                                         nullptr);
     count_launch(ctx);
     return;
   }
   uint32_t* pos = (uint32_t*)ws.l2;
   k_tile_sort<<<tiles, kTile / 2, 0, st>>>(in, (unsigned)n, (unsigned)K, ws.l1, pos, nullptr,
-                                            nullptr, nullptr);
+                                            nullptr);
   k_merge_rank<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws.l1, pos, (unsigned)n, (unsigned)K,
-                                                            ws.out, nullptr, nullptr);
+                                                            ws.out, nullptr);
   count_launch(ctx, 2);
 }
 
@@ -579,28 +516,6 @@ SelectWs select_ws_carve(void* base, uint64_t n, uint64_t K) {
   return ws;
 }
 
-// The positive x at or above the log-bucket threshold of the K largest,
-// compacted into `out` (count at *counter, zeroed by the caller): for dense
-// hashes from the inserts' histogram and the rows that reach it; otherwise
-// a histogram pass and a compaction pass over every slot.
-void compact_hash(mad_ctx* ctx, uint64_t K, SelState* dst, Item* out, uint64_t out_cap,
-                  unsigned long long* counter, cudaStream_t st) {
-  const uint64_t bound = hash_slot_bound(ctx);
-  const unsigned long long* extent = hash_extent(ctx);
-  if (ctx->xhist) {
-    k_pick_xhist<<<1, 256, 0, st>>>(ctx->xhist, K, dst);
-    const int64_t blocks64 = (ctx->m + 7) / 8;
-    k_compact_rows<<<(unsigned)(blocks64 < 152 * 16 ? blocks64 : 152 * 16), 256, 0, st>>>(
-        ctx->hkeys, ctx->hvals, ctx->hreg, ctx->rowmaxb, ctx->m, bound, dst, out, out_cap, counter);
-  } else {
-    const unsigned blocks = grid_for(bound, 152 * 8);
-    k_log_hist<<<blocks, 256, 0, st>>>(ctx->hvals, bound, K, dst, extent);
-    k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, bound, dst, out, out_cap, counter,
-                                         extent);
-  }
-  count_launch(ctx, 2);
-}
-
 mad_status select_list(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K, int dp,
                        uint64_t* n_sel, cudaStream_t st) {
   const uint64_t take = K < n ? K : n;
@@ -645,7 +560,13 @@ mad_status select_from_hash(mad_ctx* ctx, const SelectWs& ws, uint64_t K, uint64
   SelState* dst = (SelState*)ws.state;
   cudaMemsetAsync(dst, 0, sizeof(SelState), st);
   cudaMemsetAsync(ws.counter, 0, sizeof(unsigned long long), st);
-  compact_hash(ctx, K, dst, ws.l0, ws.cap_n, ws.counter, st);
+  const uint64_t bound = hash_slot_bound(ctx);
+  const unsigned blocks = grid_for(bound, 152 * 8);
+  const unsigned long long* extent = hash_extent(ctx);
+  k_log_hist<<<blocks, 256, 0, st>>>(ctx->hvals, bound, K, dst, extent);
+  k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, bound, dst, ws.l0, ws.cap_n,
+                                       ws.counter, extent);
+  count_launch(ctx, 2);
   unsigned long long host[2] = {0, 0};
   cudaMemcpyAsync(&host[0], ws.counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&host[1], &dst->maxp, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
@@ -668,162 +589,13 @@ mad_status items_to_pairs(mad_ctx* ctx, const Item* items, uint64_t n, const mad
 
 void tile_select_dev(mad_ctx* ctx, const Item* in, uint64_t cap, uint64_t K,
                      const unsigned long long* n_dev, unsigned int* over_err, Item* sorted,
-                     uint32_t* pos, Item* out, cudaStream_t st, const unsigned int* gate) {
+                     uint32_t* pos, Item* out, cudaStream_t st) {
   const unsigned tiles = (unsigned)((cap + kTile - 1) / kTile);
   k_tile_sort<<<tiles, kTile / 2, 0, st>>>(in, (unsigned)cap, (unsigned)K, sorted, pos, n_dev,
-                                            over_err, gate);
+                                            over_err);
   k_merge_rank<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(sorted, pos, (unsigned)cap,
-                                                              (unsigned)K, out, n_dev, gate);
+                                                              (unsigned)K, out, n_dev);
   count_launch(ctx, 2);
-}
-
-// ---- one-block selection of a short top K ---------------------------------
-// The K (<= kSmallSel) largest of the first min(cap, *n_dev) items by
-// (p desc, key asc), sorted, in one 256-thread block: a log-bucket
-// histogram of p finds the bucket where the count from the top reaches K, a
-// 10-bit histogram inside it narrows the threshold, and the items at or
-// above it (all of the top K, and few more) are collected in shared memory
-// and sorted.  When more than kSmallSel items pass (ties of p in the
-// thousands), *gate is set to 1 and nothing is written; the tile kernels,
-// gated on that word, then select instead.
-constexpr int kSmallSel = 4096;
-
-// Offset of v inside its log bucket b, scaled to 10 bits (monotone in v).
-__device__ __forceinline__ uint32_t fine_in_bucket(unsigned long long v, uint32_t b) {
-  const int e = 63 - __clzll((long long)v);
-  const int sh = e > 14 ? e - 14 : 0;
-  const unsigned long long f = (v - bucket_floor(b)) >> sh;
-  return f < 1024 ? (uint32_t)f : 1023u;
-}
-
-__global__ void __launch_bounds__(256)
-k_select_small(const Item* __restrict__ in, unsigned long long cap,
-               const unsigned long long* n_dev, unsigned int K_max, Item* __restrict__ out,
-               unsigned int* __restrict__ gate) {
-  extern __shared__ unsigned long long small_smem[];
-  unsigned long long* cp = small_smem;                  // p
-  unsigned long long* ck = small_smem + kSmallSel;      // key
-  unsigned long long* ca = small_smem + 2 * kSmallSel;  // aux
-  __shared__ unsigned int hist[1024], fine[1024];
-  __shared__ int bstar, fstar;
-  __shared__ unsigned int ncol;
-  __shared__ unsigned long long above;
-  const unsigned long long n = dev_len(cap, n_dev);
-  const unsigned long long K = (unsigned long long)K_max < n ? (unsigned long long)K_max : n;
-  for (int b = threadIdx.x; b < 1024; b += blockDim.x) hist[b] = fine[b] = 0;
-  if (threadIdx.x == 0) ncol = 0;
-  __syncthreads();
-  for (unsigned long long x = threadIdx.x; x < n; x += blockDim.x) {
-    const unsigned long long p = in[x].p;
-    if (p) atomicAdd(&hist[log_bucket(p)], 1u);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long cum = 0;
-    int pick = -1;   // fewer than K positive p: every item is taken
-    for (int b = 1023; b >= 0; --b) {
-      if (cum + hist[b] >= K) {
-        pick = b;
-        break;
-      }
-      cum += hist[b];
-    }
-    bstar = K ? pick : 1024;
-    above = cum;
-  }
-  __syncthreads();
-  const int bs = bstar;
-  if (bs >= 0 && bs < 1024) {
-    for (unsigned long long x = threadIdx.x; x < n; x += blockDim.x) {
-      const unsigned long long p = in[x].p;
-      if (p && log_bucket(p) == (uint32_t)bs) atomicAdd(&fine[fine_in_bucket(p, (uint32_t)bs)], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long cum = above;
-      int pick = 0;
-      for (int f = 1023; f >= 0; --f) {
-        cum += fine[f];
-        if (cum >= K) {
-          pick = f;
-          break;
-        }
-      }
-      fstar = pick;
-    }
-    __syncthreads();
-  }
-  const int fs = (bs >= 0 && bs < 1024) ? fstar : 0;
-  if (bs < 1024) {
-    for (unsigned long long x = threadIdx.x; x < n; x += blockDim.x) {
-      const unsigned long long p = in[x].p;
-      bool take = true;
-      if (bs >= 0) {
-        if (!p) continue;
-        const uint32_t b = log_bucket(p);
-        take = b > (uint32_t)bs || (b == (uint32_t)bs && fine_in_bucket(p, b) >= (uint32_t)fs);
-      }
-      if (take) {
-        const unsigned pos = atomicAdd(&ncol, 1u);
-        if (pos < (unsigned)kSmallSel) {
-          cp[pos] = p;
-          ck[pos] = in[x].key;
-          ca[pos] = in[x].aux;
-        }
-      }
-    }
-  }
-  __syncthreads();
-  const unsigned nc = ncol;
-  if (nc > (unsigned)kSmallSel) {
-    if (threadIdx.x == 0) *gate = 1u;
-    return;
-  }
-  int n2 = 1;
-  while (n2 < (int)nc) n2 <<= 1;
-  for (int x = (int)nc + threadIdx.x; x < n2; x += blockDim.x) {
-    cp[x] = 0;          // after every real item (real keys are below ~0)
-    ck[x] = ~0ull;
-    ca[x] = 0;
-  }
-  __syncthreads();
-  for (int k = 2; k <= n2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = threadIdx.x; t < n2 / 2; t += blockDim.x) {
-        const int a = (t / j) * 2 * j + (t % j), b = a + j;
-        const bool up = (a & k) == 0;
-        const bool b_first = cp[b] > cp[a] || (cp[b] == cp[a] && ck[b] < ck[a]);
-        if (b_first == up) {
-          const unsigned long long tp = cp[a], tk = ck[a], ta = ca[a];
-          cp[a] = cp[b]; ck[a] = ck[b]; ca[a] = ca[b];
-          cp[b] = tp; ck[b] = tk; ca[b] = ta;
-        }
-      }
-      __syncthreads();
-    }
-  }
-  for (unsigned long long x = threadIdx.x; x < K; x += blockDim.x) {
-    Item it;
-    it.p = cp[x];
-    it.key = ck[x];
-    it.aux = ca[x];
-    out[x] = it;
-  }
-  if (threadIdx.x == 0) *gate = 0u;
-}
-
-void top_small_dev(mad_ctx* ctx, const Item* in, uint64_t cap, uint64_t K,
-                   const unsigned long long* n_dev, Item* sorted, uint32_t* pos, Item* out,
-                   unsigned int* gate, cudaStream_t st) {
-  static bool attr = false;
-  const size_t smem = (size_t)3 * kSmallSel * sizeof(unsigned long long);
-  if (!attr) {
-    cudaFuncSetAttribute(k_select_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
-  k_select_small<<<1, 256, smem, st>>>(in, cap, n_dev, (unsigned int)K, out, gate);
-  count_launch(ctx);
-  tile_select_dev(ctx, in, cap, K, n_dev, nullptr, sorted, pos, out, st, gate);
 }
 
 size_t dev_select_state_bytes() { return ((sizeof(SelState) + 255) / 256) * 256; }
@@ -834,10 +606,13 @@ void select_hash_dev(mad_ctx* ctx, uint64_t K, const unsigned long long* hcap_de
   SelState* dst = (SelState*)state;
   cudaMemsetAsync(dst, 0, sizeof(SelState), st);
   cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
-  (void)hcap_dev;
-  compact_hash(ctx, K, dst, list, kDevSelectCap, count, st);
-  tile_select_dev(ctx, list, kDevSelectCap, K, count, &ctx->sc->err, sorted, pos, out, st,
-                  nullptr);
+  const uint64_t bound = hash_slot_bound(ctx);
+  const unsigned blocks = grid_for(bound, 152 * 8);
+  k_log_hist<<<blocks, 256, 0, st>>>(ctx->hvals, bound, K, dst, hcap_dev);
+  k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, bound, dst, list,
+                                       kDevSelectCap, count, hcap_dev);
+  count_launch(ctx, 2);
+  tile_select_dev(ctx, list, kDevSelectCap, K, count, &ctx->sc->err, sorted, pos, out, st);
 }
 
 void items_to_pairs_dev(mad_ctx* ctx, const Item* items, uint64_t cap,

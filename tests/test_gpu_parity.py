@@ -195,10 +195,10 @@ def test_empty_and_degenerate_requests():
         c.close()
 
 
-def test_grouped_clearing_after_reset():
-    """A hash above 32 MB is cleared group by group during the first
-    sampling pass (several row groups here); after a reset over the keys of
-    an earlier run, X still equals the oracle's for the new seed."""
+def test_reset_over_earlier_keys():
+    """A 4096-row instance with a hash of a few million slots: after a
+    reset over the keys of an earlier run, X equals the oracle's for the new
+    seed."""
     import oracle
     mad = _mad()
     rng = np.random.Generator(np.random.PCG64(49))
