@@ -41,8 +41,9 @@ SAMPLER_SOURCES = ["paper_1506_03872_gb300/csrc/sample.cu",
 # Algorithmic bytes per diamond of the dominant kernel, one 32-byte sector
 # per random touch.  Dense draw kernel (k_sample_sorted): the final entry of
 # each of the four inverse-CDF searches (T1, T2, TA, TB) and b_k'j, plus the
-# 8-byte sorted record read and the 16-byte (key, increment) record written.
-DENSE_DRAW_BYTES = 32 * 5 + 8 + 16
+# 4-byte diamond index read in row order and the 16-byte (key, increment)
+# record written.
+DENSE_DRAW_BYTES = 32 * 5 + 4 + 16
 # 0/1 draw kernel (k_sample, draws and inserts): the final entry of the T1
 # search, row i's bounds, the T2 guide entries and the T2 window, the column
 # indices of k and k', row k's bounds, b_kj's index and the closure filter's

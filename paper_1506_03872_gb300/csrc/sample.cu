@@ -195,13 +195,11 @@ k_sort_coloff(unsigned int* __restrict__ H, uint32_t nbk, int blocks,
   }
 }
 
-// Step 4: sorted[position] = (bucket << 32) | q for every diamond q of the
-// block's chunk.
+// Step 4: order[position] = q for every diamond q of the block's chunk.
 __global__ void __launch_bounds__(1024)
 k_sort_scatter(const DevScalars* __restrict__ sc, unsigned long long seed,
                unsigned long long first, unsigned long long s, unsigned long long chunk,
-               uint32_t nbk, const unsigned int* __restrict__ H,
-               unsigned long long* __restrict__ sorted) {
+               uint32_t nbk, const unsigned int* __restrict__ H, uint32_t* __restrict__ order) {
   extern __shared__ unsigned int sort_cnt[];
   const unsigned int* __restrict__ row = H + (size_t)blockIdx.x * nbk;
   for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) sort_cnt[b] = row[b];
@@ -214,26 +212,25 @@ k_sort_scatter(const DevScalars* __restrict__ sc, unsigned long long seed,
   for (unsigned long long q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
     const uint32_t b = sort_bucket(first + q, key, t1_total, shift);
     const unsigned int pos = atomicAdd(&sort_cnt[b], 1u);
-    sorted[pos] = ((unsigned long long)b << 32) | q;
+    order[pos] = (uint32_t)q;
   }
 }
 
-// Diamonds in row order (dense inputs): sorted[q] = (bucket << 32) | (l - first).
-// Draws only: diamond q's hash key goes to keys[q] (EMPTY_KEY when it adds
-// nothing: v = 0 or an excluded diagonal) and its increment over sorted[q]
-// (each thread rewrites only the entry it read).  k_insert adds them to X.
+// Diamonds in row order (dense inputs): order[q] = l - first.  Draws only:
+// diamond q's hash key goes to keys[q] (EMPTY_KEY when it adds nothing:
+// v = 0 or an excluded diagonal) and its increment to vals[q].  k_insert
+// adds them to X.
 __global__ void __launch_bounds__(256, 5)
 k_sample_sorted(const SampleParams p_, unsigned long long seed, unsigned long long first,
-                unsigned long long s, unsigned long long* __restrict__ sorted,
-                unsigned long long* __restrict__ keys) {
+                unsigned long long s, const uint32_t* __restrict__ order,
+                unsigned long long* __restrict__ keys, long long* __restrict__ vals) {
   const SampleParams p = resolve(p_);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   bool bad = false;
   unsigned long long diag = 0;
   for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < s;
        q += stride) {
-    const unsigned long long e = sorted[q];
-    const Uniforms u = diamond_uniforms(seed, first + (uint32_t)e);
+    const Uniforms u = diamond_uniforms(seed, first + __ldcs(order + q));
     const int64_t i = draw_row_i(p, u.u0, &bad);
     const Draw dr = draw_given_row(p, u, i, &bad);
     unsigned long long key = EMPTY_KEY;
@@ -248,7 +245,7 @@ k_sample_sorted(const SampleParams p_, unsigned long long seed, unsigned long lo
       key = ((unsigned long long)a << 32) | b;
     }
     keys[q] = key;
-    sorted[q] = (unsigned long long)dr.v;
+    vals[q] = dr.v;
   }
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) diag += __shfl_xor_sync(0xFFFFFFFFu, diag, off);
@@ -332,7 +329,7 @@ unsigned grid_of(unsigned long long work, int full) {
   return (unsigned)(need < (unsigned long long)full ? (need ? need : 1) : full);
 }
 
-// Diamonds per sorted batch (bounds the scratch at 16 bytes per diamond).
+// Diamonds per sorted batch (bounds the scratch at 20 bytes per diamond).
 constexpr unsigned long long kSortBatch = 1ull << 26;
 
 // Pilot for hash sizing: counts the diamonds that would be inserted.
@@ -445,15 +442,16 @@ int sort_blocks() {
 }
 
 // Scratch of the sort and the draws for one batch: the per-(block, bucket)
-// counts, bucket totals and offsets, the scan's partials, the diamonds in
-// bucket order (overwritten by their increments) and their keys.
+// counts, bucket totals and offsets, the scan's partials, the diamond
+// indices in bucket order, and each diamond's key and increment.
 struct SortScratch {
   unsigned int* H;
   unsigned int* tot;
   unsigned int* base;
   unsigned int* part;
-  unsigned long long* sorted;
+  uint32_t* order;
   unsigned long long* keys;
+  long long* vals;
   size_t bytes;
 };
 
@@ -470,8 +468,9 @@ SortScratch carve_sort(void* p, uint64_t nbk, int blocks, uint64_t batch) {
   c.tot = (unsigned int*)take(nbk * sizeof(unsigned int));
   c.base = (unsigned int*)take((nbk + 1) * sizeof(unsigned int));
   c.part = (unsigned int*)take(scan_partial_elems(nbk) * sizeof(unsigned int));
-  c.sorted = (unsigned long long*)take(batch * sizeof(unsigned long long));
+  c.order = (uint32_t*)take(batch * sizeof(uint32_t));
   c.keys = (unsigned long long*)take(batch * sizeof(unsigned long long));
+  c.vals = (long long*)take(batch * sizeof(long long));
   c.bytes = off;
   return c;
 }
@@ -521,14 +520,14 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
     if ((rs = scan_exclusive_u32(ctx, w.tot, w.base, nbk, w.part, st)) != MAD_OK) return rs;
     k_sort_coloff<<<cols, 256, 0, st>>>(w.H, (uint32_t)nbk, blocks, w.base);
     k_sort_scatter<<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n, chunk,
-                                                    (uint32_t)nbk, w.H, w.sorted);
+                                                    (uint32_t)nbk, w.H, w.order);
     count_launch(ctx, 4);
     phase_event(ctx, 1, st);
-    k_sample_sorted<<<grid_of(n, full_sorted), 256, 0, st>>>(p, seed, first + done, n, w.sorted,
-                                                             w.keys);
+    k_sample_sorted<<<grid_of(n, full_sorted), 256, 0, st>>>(p, seed, first + done, n, w.order,
+                                                             w.keys, w.vals);
     count_launch(ctx);
     phase_event(ctx, 2, st);
-    k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, w.keys, (const long long*)w.sorted, n);
+    k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, w.keys, w.vals, n);
     count_launch(ctx);
     phase_event(ctx, 3, st);
   }
