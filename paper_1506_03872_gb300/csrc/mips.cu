@@ -84,7 +84,7 @@ __device__ void block_bitonic(unsigned long long* a, unsigned long long* b, doub
   for (int k = 2; k <= n; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int t = threadIdx.x; t < n / 2; t += blockDim.x) {
-        const int x = (t / j) * 2 * j + (t % j), y = x + j;
+        const int x = ((t & ~(j - 1)) << 1) | (t & (j - 1)), y = x + j;   // j a power of two
         const bool up = (x & k) == 0;
         const bool y_first = before(a[y], b[y], c ? c[y] : 0.0, a[x], b[x], c ? c[x] : 0.0);
         if (y_first == up) {

@@ -298,7 +298,7 @@ k_tile_sort(const Item* __restrict__ in, unsigned n_max, unsigned K, Item* __res
   for (unsigned k = 2; k <= kTile; k <<= 1) {
     for (unsigned j = k >> 1; j > 0; j >>= 1) {
       const unsigned t = threadIdx.x;   // kTile / 2 compare-exchanges
-      const unsigned a = (t / j) * 2 * j + (t % j), b = a + j;
+      const unsigned a = ((t & ~(j - 1)) << 1) | (t & (j - 1)), b = a + j;   // j a power of two
       const bool up = (a & k) == 0;
       const bool b_first = item_before(sp[b], sk[b], si[b], sp[a], sk[a], si[a]);
       if (b_first == up) {
