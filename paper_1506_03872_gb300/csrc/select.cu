@@ -21,6 +21,8 @@
 
 #include <string.h>
 
+#include <cmath>
+
 #include "mad_device.cuh"
 #include "mad_internal.cuh"
 
@@ -170,10 +172,18 @@ k_collect(const Item* __restrict__ l0, unsigned long long n, const SelState* st,
 // of the bucket in which the count from the top reaches K, so at least K
 // items (all of the top K) pass and few more do.
 
+// With lg > 0 only every 2^lg-th group of 4 slots (one 32-byte sector of
+// values) is read, and the bucket picked is where the sampled count from the
+// top reaches K (the caller scales K to the sample).  With a gate, the
+// kernel runs only when *gate is nonzero.
 __global__ void __launch_bounds__(256)
 k_log_hist(const long long* __restrict__ vals, uint64_t cap_max, unsigned long long K,
-           SelState* st, const unsigned long long* cap_dev) {
+           SelState* st, const unsigned long long* cap_dev, int lg = 0,
+           const unsigned int* gate = nullptr) {
+  if (gate && *gate == 0u) return;
   const uint64_t cap = dev_len(cap_max, cap_dev);
+  const uint64_t groups = (cap + 3) >> 2;
+  const uint64_t span = ((groups + (1ull << lg) - 1) >> lg) << 2;   // sampled slots
   __shared__ unsigned int h[1024];
   for (int b = threadIdx.x; b < 1024; b += blockDim.x) h[b] = 0;
   __syncthreads();
@@ -181,12 +191,13 @@ k_log_hist(const long long* __restrict__ vals, uint64_t cap_max, unsigned long l
   // Four independent loads per thread per round keep enough bytes in flight.
   constexpr int U = 4;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t rounds = (cap + U * stride - 1) / (U * stride);
+  const uint64_t rounds = (span + U * stride - 1) / (U * stride);
   for (uint64_t r = 0; r < rounds; ++r) {
     long long v[U];
 #pragma unroll
     for (int q = 0; q < U; ++q) {
-      const uint64_t slot = (r * U + q) * stride + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+      const uint64_t x = (r * U + q) * stride + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+      const uint64_t slot = (((x >> 2) << lg) << 2) | (x & 3);
       v[q] = slot < cap ? __ldg(vals + slot) : 0;
     }
 #pragma unroll
@@ -226,7 +237,9 @@ k_log_hist(const long long* __restrict__ vals, uint64_t cap_max, unsigned long l
 __global__ void __launch_bounds__(256)
 k_compact_ge(const unsigned long long* __restrict__ keys, const long long* __restrict__ vals,
              uint64_t cap_max, const SelState* st, Item* __restrict__ out, uint64_t out_cap,
-             unsigned long long* counter, const unsigned long long* cap_dev) {
+             unsigned long long* counter, const unsigned long long* cap_dev,
+             const unsigned int* gate = nullptr) {
+  if (gate && *gate == 0u) return;
   const uint64_t cap = dev_len(cap_max, cap_dev);
   const unsigned long long theta = st->theta;
   constexpr int U = 4;   // independent loads in flight per thread
@@ -252,6 +265,29 @@ k_compact_ge(const unsigned long long* __restrict__ keys, const long long* __res
       }
       append(out, counter, want, it, out_cap);
     }
+  }
+}
+
+// After a compaction at a threshold estimated from a sample: when it kept
+// fewer than K items although the threshold excluded some (theta > 1),
+// *gate is set and the state is reset for the exact histogram and
+// compaction, which run gated on it.
+__global__ void __launch_bounds__(256)
+k_select_check(SelState* st, unsigned long long* counter, unsigned long long K,
+               unsigned int* gate) {
+  __shared__ int redo;
+  if (threadIdx.x == 0) {
+    redo = (*counter < K && st->theta > 1ull) ? 1 : 0;
+    *gate = (unsigned int)redo;
+  }
+  __syncthreads();
+  if (!redo) return;
+  for (int b = threadIdx.x; b < 1024; b += blockDim.x) st->lhist[b] = 0;
+  if (threadIdx.x == 0) {
+    *counter = 0;
+    st->ticket3 = 0;
+    st->maxp = 0;
+    st->positive = 0;
   }
 }
 
@@ -608,10 +644,22 @@ void select_hash_dev(mad_ctx* ctx, uint64_t K, const unsigned long long* hcap_de
   cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
   const uint64_t bound = hash_slot_bound(ctx);
   const unsigned blocks = grid_for(bound, 152 * 8);
-  k_log_hist<<<blocks, 256, 0, st>>>(ctx->hvals, bound, K, dst, hcap_dev);
+  // The threshold from one 4-slot group in 8: the sampled count must reach
+  // K/8 plus four standard deviations, so the compaction keeps fewer than
+  // K items only rarely; then the exact histogram and compaction run.
+  constexpr int kLg = 3;
+  const double ks = (double)K / (1 << kLg);
+  const unsigned long long Ks = (unsigned long long)(ks + 4.0 * sqrt(ks) + 8.0);
+  unsigned int* gate = (unsigned int*)(count + 1);
+  k_log_hist<<<(blocks + (1u << kLg) - 1) >> kLg, 256, 0, st>>>(ctx->hvals, bound, Ks, dst,
+                                                                 hcap_dev, kLg);
   k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, bound, dst, list,
                                        kDevSelectCap, count, hcap_dev);
-  count_launch(ctx, 2);
+  k_select_check<<<1, 256, 0, st>>>(dst, count, K, gate);
+  k_log_hist<<<blocks, 256, 0, st>>>(ctx->hvals, bound, K, dst, hcap_dev, 0, gate);
+  k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, bound, dst, list,
+                                       kDevSelectCap, count, hcap_dev, gate);
+  count_launch(ctx, 5);
   tile_select_dev(ctx, list, kDevSelectCap, K, count, &ctx->sc->err, sorted, pos, out, st);
 }
 
