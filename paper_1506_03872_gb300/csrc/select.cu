@@ -202,11 +202,10 @@ k_log_hist(const long long* __restrict__ vals, uint64_t cap_max, unsigned long l
     }
 #pragma unroll
     for (int q = 0; q < U; ++q) {
-      const uint32_t bin = v[q] > 0 ? log_bucket((unsigned long long)v[q]) : 0xFFFFu;
-      // one shared-memory atomic per distinct bucket per warp
-      const unsigned peers = __match_any_sync(0xFFFFFFFFu, bin);
+      // (a shared-memory atomic per value measured faster than combining
+      // equal buckets of a warp first)
       if (v[q] > 0) {
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[bin], __popc(peers));
+        atomicAdd(&h[log_bucket((unsigned long long)v[q])], 1u);
         if ((unsigned long long)v[q] > mx) mx = (unsigned long long)v[q];
       }
     }
