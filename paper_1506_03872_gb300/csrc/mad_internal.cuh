@@ -322,7 +322,7 @@ size_t dense_build_scratch_bytes(const mad_ctx* ctx);
 mad_status enqueue_dense_build(mad_ctx* ctx, cudaStream_t st);
 mad_status finish_dense_build(mad_ctx* ctx, cudaStream_t st);
 // sample.cu: scratch of sample_impl for s diamonds, and the number of bits
-// of the row-order sort's buckets (at most 15, about log2 m).
+// of the row-order sort's buckets (at most 16, about log2 m).
 size_t sample_scratch_bytes(const mad_ctx* ctx, uint64_t s);
 int sort_bits(int64_t m);
 // rescore.cu

@@ -121,13 +121,19 @@ k_sample(const SampleParams p_, unsigned long long seed, unsigned long long firs
 // i = upper_bound(T1, target) is non-decreasing in the target, so bucket
 // order is row order; the T1 search itself is left to the draw kernel,
 // where neighbouring diamonds search the same few lines of T1.  At most
-// 2^kSortBitsMax buckets (a few rows each; the draw kernel's 256-diamond
-// windows span a few rows either way).  One block per SM takes a contiguous
-// chunk of the diamonds and counts them per bucket in shared memory (step
-// 1), the counts become per-(bucket, block) offsets (steps 2 and 3), and
-// each block places its diamonds with shared-memory cursors (step 4): no
-// global atomics and no per-diamond record between the steps.
-constexpr int kSortBitsMax = 15;
+// 2^kSortBitsMax buckets (a few rows each; measured on the dense factor
+// workload, 2^14 buckets made sampling 3.7 % slower than 2^15).  One block
+// per SM takes a contiguous chunk of the diamonds and counts them per
+// bucket in shared memory (step 1), the counts become per-(bucket, block)
+// offsets (steps 2 and 3), and each block places its diamonds by
+// shared-memory counts (step 4): no global atomics and no per-diamond
+// record between the steps.
+constexpr int kSortBitsMax = 16;
+// Above 2^15 buckets the shared-memory counters are 16 bits, two to a word:
+// the buckets are equal slices of the uniform target range, each at most
+// 2^-15 of it, so a block's chunk (at most 2^26 / #SMs diamonds) puts about
+// 14 diamonds into a bucket, far below 2^16.
+constexpr uint32_t kWideSort = 1u << 15;
 
 __device__ __forceinline__ uint32_t sort_bucket(unsigned long long ell, uint2 key,
                                                 unsigned long long t1_total, int shift) {
@@ -137,23 +143,29 @@ __device__ __forceinline__ uint32_t sort_bucket(unsigned long long ell, uint2 ke
 }
 
 // Step 1: H[g * nbk + b] = diamonds of block g's chunk in bucket b.
+template <bool Packed>
 __global__ void __launch_bounds__(1024)
 k_sort_hist(const DevScalars* __restrict__ sc, unsigned long long seed, unsigned long long first,
             unsigned long long s, unsigned long long chunk, uint32_t nbk,
             unsigned int* __restrict__ H) {
   extern __shared__ unsigned int sort_cnt[];
-  for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) sort_cnt[b] = 0;
+  const uint32_t words = Packed ? nbk / 2 : nbk;
+  for (uint32_t b = threadIdx.x; b < words; b += blockDim.x) sort_cnt[b] = 0;
   __syncthreads();
   const unsigned long long t1_total = sc->t1_total;
   const int shift = sc->sort_shift;
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   const unsigned long long q0 = (unsigned long long)blockIdx.x * chunk;
   const unsigned long long q1 = q0 + chunk < s ? q0 + chunk : s;
-  for (unsigned long long q = q0 + threadIdx.x; q < q1; q += blockDim.x)
-    atomicAdd(&sort_cnt[sort_bucket(first + q, key, t1_total, shift)], 1u);
+  for (unsigned long long q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    const uint32_t b = sort_bucket(first + q, key, t1_total, shift);
+    if (Packed) atomicAdd(&sort_cnt[b >> 1], 1u << ((b & 1u) << 4));
+    else atomicAdd(&sort_cnt[b], 1u);
+  }
   __syncthreads();
   unsigned int* __restrict__ row = H + (size_t)blockIdx.x * nbk;
-  for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) row[b] = sort_cnt[b];
+  for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x)
+    row[b] = Packed ? (sort_cnt[b >> 1] >> ((b & 1u) << 4)) & 0xFFFFu : sort_cnt[b];
 }
 
 // Step 2: tot[b] = sum over the blocks of H[g][b].
@@ -196,13 +208,21 @@ k_sort_coloff(unsigned int* __restrict__ H, uint32_t nbk, int blocks,
 }
 
 // Step 4: order[position] = q for every diamond q of the block's chunk.
+// Unpacked: the block's offsets are staged as shared-memory cursors.
+// Packed: a 16-bit shared-memory count gives the rank, added to the offset
+// read from H.
+template <bool Packed>
 __global__ void __launch_bounds__(1024)
 k_sort_scatter(const DevScalars* __restrict__ sc, unsigned long long seed,
                unsigned long long first, unsigned long long s, unsigned long long chunk,
                uint32_t nbk, const unsigned int* __restrict__ H, uint32_t* __restrict__ order) {
   extern __shared__ unsigned int sort_cnt[];
   const unsigned int* __restrict__ row = H + (size_t)blockIdx.x * nbk;
-  for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) sort_cnt[b] = row[b];
+  if (Packed) {
+    for (uint32_t w = threadIdx.x; w < nbk / 2; w += blockDim.x) sort_cnt[w] = 0;
+  } else {
+    for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) sort_cnt[b] = row[b];
+  }
   __syncthreads();
   const unsigned long long t1_total = sc->t1_total;
   const int shift = sc->sort_shift;
@@ -211,7 +231,13 @@ k_sort_scatter(const DevScalars* __restrict__ sc, unsigned long long seed,
   const unsigned long long q1 = q0 + chunk < s ? q0 + chunk : s;
   for (unsigned long long q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
     const uint32_t b = sort_bucket(first + q, key, t1_total, shift);
-    const unsigned int pos = atomicAdd(&sort_cnt[b], 1u);
+    unsigned int pos;
+    if (Packed) {
+      const uint32_t sh = (b & 1u) << 4;
+      pos = __ldg(row + b) + ((atomicAdd(&sort_cnt[b >> 1], 1u << sh) >> sh) & 0xFFFFu);
+    } else {
+      pos = atomicAdd(&sort_cnt[b], 1u);
+    }
     order[pos] = (uint32_t)q;
   }
 }
@@ -497,11 +523,17 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
   const int full_insert = full_grid<k_insert>();
   const uint64_t nbk = sort_buckets(ctx->m);
   const int blocks = sort_blocks();
-  const size_t sort_smem = nbk * sizeof(unsigned int);
+  const bool packed = nbk > kWideSort;
+  const size_t sort_smem = (packed ? nbk / 2 : nbk) * sizeof(unsigned int);
   static size_t smem_set = 0;
   if (sort_smem > 48 * 1024 && smem_set < sort_smem) {
-    cudaFuncSetAttribute(k_sort_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
-    cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_sort_hist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sort_smem);
+    cudaFuncSetAttribute(k_sort_hist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sort_smem);
+    cudaFuncSetAttribute(k_sort_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sort_smem);
+    cudaFuncSetAttribute(k_sort_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sort_smem);
     smem_set = sort_smem;
   }
@@ -514,13 +546,21 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
     phase_event(ctx, 0, st);
     const unsigned long long chunk = (n + blocks - 1) / blocks;
     const unsigned cols = (unsigned)((nbk + 255) / 256);
-    k_sort_hist<<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n, chunk,
-                                                 (uint32_t)nbk, w.H);
+    if (packed)
+      k_sort_hist<true><<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n, chunk,
+                                                         (uint32_t)nbk, w.H);
+    else
+      k_sort_hist<false><<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n, chunk,
+                                                          (uint32_t)nbk, w.H);
     k_sort_colsum<<<cols, 256, 0, st>>>(w.H, (uint32_t)nbk, blocks, w.tot);
     if ((rs = scan_exclusive_u32(ctx, w.tot, w.base, nbk, w.part, st)) != MAD_OK) return rs;
     k_sort_coloff<<<cols, 256, 0, st>>>(w.H, (uint32_t)nbk, blocks, w.base);
-    k_sort_scatter<<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n, chunk,
-                                                    (uint32_t)nbk, w.H, w.order);
+    if (packed)
+      k_sort_scatter<true><<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n, chunk,
+                                                            (uint32_t)nbk, w.H, w.order);
+    else
+      k_sort_scatter<false><<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n,
+                                                             chunk, (uint32_t)nbk, w.H, w.order);
     count_launch(ctx, 4);
     phase_event(ctx, 1, st);
     k_sample_sorted<<<grid_of(n, full_sorted), 256, 0, st>>>(p, seed, first + done, n, w.order,
