@@ -168,15 +168,32 @@ k_sort_hist(const DevScalars* __restrict__ sc, unsigned long long seed, unsigned
     row[b] = Packed ? (sort_cnt[b >> 1] >> ((b & 1u) << 4)) & 0xFFFFu : sort_cnt[b];
 }
 
-// Step 2: tot[b] = sum over the blocks of H[g][b].
+// Steps 2 and 3 split the blocks into kSortParts groups so that every
+// (bucket, group) pair is one thread.  Step 2: S[p][b] = the diamonds of
+// group p's blocks in bucket b, and tot[b] = their sum over the groups.
+constexpr int kSortParts = 8;
+
 __global__ void __launch_bounds__(256)
-k_sort_colsum(const unsigned int* __restrict__ H, uint32_t nbk, int blocks,
-              unsigned int* __restrict__ tot) {
+k_sort_partial(const unsigned int* __restrict__ H, uint32_t nbk, int blocks,
+               unsigned int* __restrict__ S) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  if (b >= nbk) return;
+  const int per = (blocks + kSortParts - 1) / kSortParts;
+  const int g0 = p * per, g1 = g0 + per < blocks ? g0 + per : blocks;
+  unsigned int acc = 0;
+#pragma unroll 8
+  for (int g = g0; g < g1; ++g) acc += H[(size_t)g * nbk + b];
+  S[(size_t)p * nbk + b] = acc;
+}
+
+__global__ void __launch_bounds__(256)
+k_sort_colsum(const unsigned int* __restrict__ S, uint32_t nbk, unsigned int* __restrict__ tot) {
   const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbk) return;
   unsigned int acc = 0;
-#pragma unroll 8
-  for (int g = 0; g < blocks; ++g) acc += H[(size_t)g * nbk + b];
+#pragma unroll
+  for (int p = 0; p < kSortParts; ++p) acc += S[(size_t)p * nbk + b];
   tot[b] = acc;
 }
 
@@ -184,13 +201,17 @@ k_sort_colsum(const unsigned int* __restrict__ H, uint32_t nbk, int blocks,
 // first position of block g's diamonds of bucket b.
 __global__ void __launch_bounds__(256)
 k_sort_coloff(unsigned int* __restrict__ H, uint32_t nbk, int blocks,
-              const unsigned int* __restrict__ base) {
+              const unsigned int* __restrict__ S, const unsigned int* __restrict__ base) {
   const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
   if (b >= nbk) return;
   unsigned int acc = base[b];
-  int g = 0;
+  for (int q = 0; q < p; ++q) acc += S[(size_t)q * nbk + b];
+  const int per = (blocks + kSortParts - 1) / kSortParts;
+  const int g0 = p * per, g1 = g0 + per < blocks ? g0 + per : blocks;
+  int g = g0;
   // Eight loads in flight before their eight stores.
-  for (; g + 8 <= blocks; g += 8) {
+  for (; g + 8 <= g1; g += 8) {
     unsigned int c[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) c[u] = H[(size_t)(g + u) * nbk + b];
@@ -200,7 +221,7 @@ k_sort_coloff(unsigned int* __restrict__ H, uint32_t nbk, int blocks,
       acc += c[u];
     }
   }
-  for (; g < blocks; ++g) {
+  for (; g < g1; ++g) {
     const unsigned int c = H[(size_t)g * nbk + b];
     H[(size_t)g * nbk + b] = acc;
     acc += c;
@@ -472,6 +493,7 @@ int sort_blocks() {
 // indices in bucket order, and each diamond's key and increment.
 struct SortScratch {
   unsigned int* H;
+  unsigned int* S;
   unsigned int* tot;
   unsigned int* base;
   unsigned int* part;
@@ -491,6 +513,7 @@ SortScratch carve_sort(void* p, uint64_t nbk, int blocks, uint64_t batch) {
     return (void*)q;
   };
   c.H = (unsigned int*)take((size_t)nbk * blocks * sizeof(unsigned int));
+  c.S = (unsigned int*)take((size_t)nbk * kSortParts * sizeof(unsigned int));
   c.tot = (unsigned int*)take(nbk * sizeof(unsigned int));
   c.base = (unsigned int*)take((nbk + 1) * sizeof(unsigned int));
   c.part = (unsigned int*)take(scan_partial_elems(nbk) * sizeof(unsigned int));
@@ -552,16 +575,18 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
     else
       k_sort_hist<false><<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n, chunk,
                                                           (uint32_t)nbk, w.H);
-    k_sort_colsum<<<cols, 256, 0, st>>>(w.H, (uint32_t)nbk, blocks, w.tot);
+    k_sort_partial<<<dim3(cols, kSortParts), 256, 0, st>>>(w.H, (uint32_t)nbk, blocks, w.S);
+    k_sort_colsum<<<cols, 256, 0, st>>>(w.S, (uint32_t)nbk, w.tot);
     if ((rs = scan_exclusive_u32(ctx, w.tot, w.base, nbk, w.part, st)) != MAD_OK) return rs;
-    k_sort_coloff<<<cols, 256, 0, st>>>(w.H, (uint32_t)nbk, blocks, w.base);
+    k_sort_coloff<<<dim3(cols, kSortParts), 256, 0, st>>>(w.H, (uint32_t)nbk, blocks, w.S,
+                                                         w.base);
     if (packed)
       k_sort_scatter<true><<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n, chunk,
                                                             (uint32_t)nbk, w.H, w.order);
     else
       k_sort_scatter<false><<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n,
                                                              chunk, (uint32_t)nbk, w.H, w.order);
-    count_launch(ctx, 4);
+    count_launch(ctx, 5);
     phase_event(ctx, 1, st);
     k_sample_sorted<<<grid_of(n, full_sorted), 256, 0, st>>>(p, seed, first + done, n, w.order,
                                                              w.keys, w.vals);
