@@ -134,6 +134,11 @@ constexpr int kSortBitsMax = 16;
 // 2^-15 of it, so a block's chunk (at most 2^26 / #SMs diamonds) puts about
 // 14 diamonds into a bucket, far below 2^16.
 constexpr uint32_t kWideSort = 1u << 15;
+// Row stride of the per-(block, bucket) counts: a power-of-two number of
+// buckets plus 64 words, so that the rows of successive blocks do not all
+// start on the same memory channel (the column passes read one entry of
+// every row).
+__host__ __device__ __forceinline__ size_t sort_row(uint32_t nbk) { return (size_t)nbk + 64; }
 
 __device__ __forceinline__ uint32_t sort_bucket(unsigned long long ell, uint2 key,
                                                 unsigned long long t1_total, int shift) {
@@ -142,7 +147,7 @@ __device__ __forceinline__ uint32_t sort_bucket(unsigned long long ell, uint2 ke
   return (uint32_t)(draw_target(u0, t1_total) >> shift);
 }
 
-// Step 1: H[g * nbk + b] = diamonds of block g's chunk in bucket b.
+// Step 1: H[g * sort_row(nbk) + b] = diamonds of block g's chunk in bucket b.
 template <bool Packed>
 __global__ void __launch_bounds__(1024)
 k_sort_hist(const DevScalars* __restrict__ sc, unsigned long long seed, unsigned long long first,
@@ -163,7 +168,7 @@ k_sort_hist(const DevScalars* __restrict__ sc, unsigned long long seed, unsigned
     else atomicAdd(&sort_cnt[b], 1u);
   }
   __syncthreads();
-  unsigned int* __restrict__ row = H + (size_t)blockIdx.x * nbk;
+  unsigned int* __restrict__ row = H + (size_t)blockIdx.x * sort_row(nbk);
   for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x)
     row[b] = Packed ? (sort_cnt[b >> 1] >> ((b & 1u) << 4)) & 0xFFFFu : sort_cnt[b];
 }
@@ -183,7 +188,7 @@ k_sort_partial(const unsigned int* __restrict__ H, uint32_t nbk, int blocks,
   const int g0 = p * per, g1 = g0 + per < blocks ? g0 + per : blocks;
   unsigned int acc = 0;
 #pragma unroll 8
-  for (int g = g0; g < g1; ++g) acc += H[(size_t)g * nbk + b];
+  for (int g = g0; g < g1; ++g) acc += H[(size_t)g * sort_row(nbk) + b];
   S[(size_t)p * nbk + b] = acc;
 }
 
@@ -214,16 +219,16 @@ k_sort_coloff(unsigned int* __restrict__ H, uint32_t nbk, int blocks,
   for (; g + 8 <= g1; g += 8) {
     unsigned int c[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) c[u] = H[(size_t)(g + u) * nbk + b];
+    for (int u = 0; u < 8; ++u) c[u] = H[(size_t)(g + u) * sort_row(nbk) + b];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      H[(size_t)(g + u) * nbk + b] = acc;
+      H[(size_t)(g + u) * sort_row(nbk) + b] = acc;
       acc += c[u];
     }
   }
   for (; g < g1; ++g) {
-    const unsigned int c = H[(size_t)g * nbk + b];
-    H[(size_t)g * nbk + b] = acc;
+    const unsigned int c = H[(size_t)g * sort_row(nbk) + b];
+    H[(size_t)g * sort_row(nbk) + b] = acc;
     acc += c;
   }
 }
@@ -238,7 +243,7 @@ k_sort_scatter(const DevScalars* __restrict__ sc, unsigned long long seed,
                unsigned long long first, unsigned long long s, unsigned long long chunk,
                uint32_t nbk, const unsigned int* __restrict__ H, uint32_t* __restrict__ order) {
   extern __shared__ unsigned int sort_cnt[];
-  const unsigned int* __restrict__ row = H + (size_t)blockIdx.x * nbk;
+  const unsigned int* __restrict__ row = H + (size_t)blockIdx.x * sort_row(nbk);
   if (Packed) {
     for (uint32_t w = threadIdx.x; w < nbk / 2; w += blockDim.x) sort_cnt[w] = 0;
   } else {
@@ -512,7 +517,7 @@ SortScratch carve_sort(void* p, uint64_t nbk, int blocks, uint64_t batch) {
     off += (bytes + 255) & ~(size_t)255;
     return (void*)q;
   };
-  c.H = (unsigned int*)take((size_t)nbk * blocks * sizeof(unsigned int));
+  c.H = (unsigned int*)take(sort_row((uint32_t)nbk) * blocks * sizeof(unsigned int));
   c.S = (unsigned int*)take((size_t)nbk * kSortParts * sizeof(unsigned int));
   c.tot = (unsigned int*)take(nbk * sizeof(unsigned int));
   c.base = (unsigned int*)take((nbk + 1) * sizeof(unsigned int));
