@@ -215,10 +215,11 @@ mad_status mad_rescore(mad_ctx* ctx, const mad_pair* cand_dev, uint32_t ncand, u
  * exact rescore, with the same results as mad_build_tables, mad_sample,
  * mad_topk and mad_rescore.  Asynchronous and free of host synchronisation
  * and allocation, so it can be captured in a CUDA graph and replayed.
- * out_dev: t pairs (device); counts_dev: two uint32 (device), the number
- * of candidates and of results; cand_dev (optional, t' pairs, device):
- * Omega_t'.  Errors found on the device (a compacted candidate list above
- * 131072 entries, a hash probe limit) go to the device error word.
+ * out_dev: t pairs (device), sorted as mad_rescore sorts them; counts_dev:
+ * two uint32 (device), the number of candidates and of results; cand_dev
+ * (optional, t' pairs, device): Omega_t', in no particular order.  Errors
+ * found on the device (a compacted candidate list above 131072 entries, a
+ * hash probe limit) go to the device error word.
  *
  * mad_pipeline_status: synchronises, refreshes the host-side table scalars
  * (mad_stats) and returns the status of the last run. */

@@ -287,13 +287,23 @@ mad_status items_to_pairs(mad_ctx* ctx, const Item* items, uint64_t n, const mad
 // over_err is given, a device length above cap sets DERR_SELECT there.
 void tile_select_dev(mad_ctx* ctx, const Item* in, uint64_t cap, uint64_t K,
                      const unsigned long long* n_dev, unsigned int* over_err, Item* sorted,
-                     uint32_t* pos, Item* out, cudaStream_t st);
+                     uint32_t* pos, Item* out, cudaStream_t st,
+                     const unsigned int* gate = nullptr);
+// The same set, selected in one block when min(cap, *n_dev) <= 16384 (in no
+// particular order unless `sorted` and K <= 2048); longer lists fall back to
+// the tile kernels through the device word *gate (sorted output).
+void block_select_dev(mad_ctx* ctx, const Item* in, uint64_t cap, uint64_t K,
+                      const unsigned long long* n_dev, bool sorted, Item* tile_sorted,
+                      uint32_t* pos, Item* out, unsigned int* gate, unsigned int* over_err,
+                      cudaStream_t st);
 constexpr uint64_t kDevSelectCap = 1ull << 17;
 size_t dev_select_state_bytes();
 // Omega_t' from the hash whose extent is *hcap_dev slots (at most
-// ctx->hcap): the positive x at or above the log-bucket threshold are
-// compacted into list (kDevSelectCap entries, count at *count), then the
-// K largest sorted into out.
+// ctx->hcap): the positive x at or above a log-bucket threshold (estimated
+// from one 4-slot group in 8, the exact histogram as a gated fallback) are
+// compacted into list (kDevSelectCap entries, count at *count), then the K
+// largest go to out, in no particular order when one block selects them
+// (lists up to 16384 items), else sorted.  count[1..2] are gate words.
 void select_hash_dev(mad_ctx* ctx, uint64_t K, const unsigned long long* hcap_dev, void* state,
                      unsigned long long* count, Item* list, Item* sorted, uint32_t* pos,
                      Item* out, cudaStream_t st);

@@ -82,8 +82,8 @@ mad_status enqueue_pass(mad_ctx* ctx, uint64_t seed, mad_pair* out_dev, uint32_t
   // ... the exact c of each candidate, and Omega_t.
   if ((rs = rescore_items(ctx, cand, ctx->pipe_tprime, b.rs_items, b.cvals, st, b.count)) != MAD_OK)
     return rs;
-  tile_select_dev(ctx, b.rs_items, ctx->pipe_tprime, ctx->pipe_t, b.count, nullptr, b.rs_sorted,
-                  b.rs_pos, b.rs_out, st);
+  block_select_dev(ctx, b.rs_items, ctx->pipe_tprime, ctx->pipe_t, b.count, true, b.rs_sorted,
+                   b.rs_pos, b.rs_out, (unsigned int*)(b.count + 3), nullptr, st);
   items_to_pairs_dev(ctx, b.rs_out, ctx->pipe_t, b.count, cand, b.cvals, out_dev, counts_dev + 1,
                      st);
   return cuda_status(cudaGetLastError());

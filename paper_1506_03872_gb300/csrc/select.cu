@@ -308,9 +308,10 @@ __device__ __forceinline__ bool item_before(unsigned long long ap, unsigned long
 __global__ void __launch_bounds__(1024)
 k_tile_sort(const Item* __restrict__ in, unsigned n_max, unsigned K, Item* __restrict__ out,
             uint32_t* __restrict__ pos_out, const unsigned long long* n_dev,
-            unsigned int* over_err) {
+            unsigned int* over_err, const unsigned int* gate = nullptr) {
   __shared__ unsigned long long sp[kTile], sk[kTile];
   __shared__ uint32_t si[kTile];
+  if (gate && *gate == 0u) return;   // the list was selected by k_block_select
   // Under a device count: a list longer than the workspace is reported.
   if (over_err && blockIdx.x == 0 && threadIdx.x == 0 && *n_dev > n_max)
     atomicOr(over_err, DERR_SELECT);
@@ -357,7 +358,9 @@ k_tile_sort(const Item* __restrict__ in, unsigned n_max, unsigned K, Item* __res
 
 __global__ void __launch_bounds__(256)
 k_merge_rank(const Item* __restrict__ tiles, const uint32_t* __restrict__ pos, unsigned n_max,
-             unsigned K, Item* __restrict__ out, const unsigned long long* n_dev) {
+             unsigned K, Item* __restrict__ out, const unsigned long long* n_dev,
+             const unsigned int* gate = nullptr) {
+  if (gate && *gate == 0u) return;
   const unsigned n = (unsigned)dev_len(n_max, n_dev);
   const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= n) return;
@@ -624,13 +627,233 @@ mad_status items_to_pairs(mad_ctx* ctx, const Item* items, uint64_t n, const mad
 
 void tile_select_dev(mad_ctx* ctx, const Item* in, uint64_t cap, uint64_t K,
                      const unsigned long long* n_dev, unsigned int* over_err, Item* sorted,
-                     uint32_t* pos, Item* out, cudaStream_t st) {
+                     uint32_t* pos, Item* out, cudaStream_t st, const unsigned int* gate) {
   const unsigned tiles = (unsigned)((cap + kTile - 1) / kTile);
   k_tile_sort<<<tiles, kTile / 2, 0, st>>>(in, (unsigned)cap, (unsigned)K, sorted, pos, n_dev,
-                                            over_err);
+                                            over_err, gate);
   k_merge_rank<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(sorted, pos, (unsigned)cap,
-                                                              (unsigned)K, out, n_dev);
+                                                              (unsigned)K, out, n_dev, gate);
   count_launch(ctx, 2);
+}
+
+// ---- one-block exact selection ---------------------------------------------
+// The K largest of the first n = min(cap, *n_dev) items by (p desc, key
+// asc), for n <= kBlockSel, in one 1024-thread block: the p of every item
+// sit in shared memory and an MSB radix select (eight 8-bit digits) finds
+// the K-th largest p and how many items equal to it are taken; among those
+// ties the smallest keys are found the same way.  The K items go to out in
+// no particular order, or sorted when `sorted` (K <= kBlockSort).  A longer
+// list sets *gate to 1 and writes nothing (the tile kernels, gated on that
+// word, select instead); otherwise *gate becomes 0.
+constexpr int kBlockSel = 16384;
+constexpr int kBlockSort = 2048;
+
+// The digit of the K-th largest value among those counted in hist (256
+// bins, digit order): returns it and leaves in *rank the rank of that value
+// inside its digit (from the top).  One warp.
+__device__ __forceinline__ void pick_digit(const unsigned int* hist, unsigned long long* rank,
+                                           int* digit) {
+  const int lane = threadIdx.x & 31;
+  // lane L holds bins 255 - 8L ... 248 - 8L (from the top)
+  unsigned int c[8];
+  unsigned int mine = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    c[u] = hist[255 - 8 * lane - u];
+    mine += c[u];
+  }
+  unsigned int inc = mine;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned int o = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+    if (lane >= off) inc += o;
+  }
+  const unsigned long long need = *rank;
+  const unsigned long long before = inc - mine;
+  const bool here = before < need && (unsigned long long)inc >= need;
+  const unsigned who = __ballot_sync(0xFFFFFFFFu, here);
+  if (here) {
+    unsigned long long cum = before;
+    for (int u = 0; u < 8; ++u) {
+      if (cum + c[u] >= need) {
+        *digit = 255 - 8 * lane - u;
+        *rank = need - cum;
+        break;
+      }
+      cum += c[u];
+    }
+  }
+  (void)who;
+}
+
+__global__ void __launch_bounds__(1024)
+k_block_select(const Item* __restrict__ in, unsigned long long cap, const unsigned long long* n_dev,
+               unsigned int K_max, Item* __restrict__ out, int sorted, unsigned int* gate) {
+  extern __shared__ unsigned long long bs_p[];   // kBlockSel values, then the sort buffers
+  __shared__ unsigned int hist[256];
+  __shared__ unsigned long long s_prefix, s_rank, s_kprefix, s_krank;
+  __shared__ int s_digit;
+  __shared__ unsigned int s_out, s_tie;
+  const unsigned long long n = dev_len(cap, n_dev);
+  if (n > (unsigned long long)kBlockSel) {
+    if (threadIdx.x == 0) *gate = 1u;
+    return;
+  }
+  const unsigned long long K = (unsigned long long)K_max < n ? (unsigned long long)K_max : n;
+  for (unsigned long long x = threadIdx.x; x < n; x += blockDim.x) bs_p[x] = in[x].p;
+  if (threadIdx.x == 0) {
+    s_prefix = 0;
+    s_rank = K;
+    s_out = 0;
+    s_tie = 0;
+  }
+  __syncthreads();
+  // MSB radix select of the K-th largest p.
+  unsigned long long mask = 0;
+  for (int d = 7; d >= 0 && K > 0; --d) {
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const unsigned long long prefix = s_prefix;
+    for (unsigned long long x = threadIdx.x; x < n; x += blockDim.x) {
+      const unsigned long long v = bs_p[x];
+      if ((v & mask) == prefix) atomicAdd(&hist[(v >> (8 * d)) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      unsigned long long r = s_rank;
+      int dg = -1;
+      pick_digit(hist, &r, &dg);
+      if (dg >= 0) {   // exactly one lane found the digit
+        s_digit = dg;
+        s_rank = r;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_prefix = prefix | ((unsigned long long)s_digit << (8 * d));
+    mask |= 255ull << (8 * d);
+    __syncthreads();
+  }
+  const unsigned long long pk = s_prefix;          // the K-th largest p
+  const unsigned long long take_ties = s_rank;     // items equal to pk that are taken
+  // Ties: the take_ties smallest keys among the items with p == pk.
+  unsigned long long tie_count = 0;
+  for (unsigned long long x = threadIdx.x; x < n; x += blockDim.x) tie_count += bs_p[x] == pk;
+  atomicAdd(&s_tie, (unsigned int)tie_count);
+  if (threadIdx.x == 0) {
+    s_kprefix = ~0ull;   // every tied key qualifies unless a key threshold is set
+    s_krank = take_ties;
+  }
+  __syncthreads();
+  const bool key_select = K > 0 && take_ties < s_tie;
+  if (key_select) {
+    // MSB radix select of the take_ties-th smallest key among the ties:
+    // ranks from the top of ~key.
+    if (threadIdx.x == 0) s_kprefix = 0;
+    __syncthreads();
+    unsigned long long kmask = 0;
+    for (int d = 7; d >= 0; --d) {
+      for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+      __syncthreads();
+      const unsigned long long kp = s_kprefix;
+      for (unsigned long long x = threadIdx.x; x < n; x += blockDim.x) {
+        if (bs_p[x] != pk) continue;
+        const unsigned long long nk = ~in[x].key;
+        if ((nk & kmask) == kp) atomicAdd(&hist[(nk >> (8 * d)) & 255u], 1u);
+      }
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        unsigned long long r = s_krank;
+        int dg = -1;
+        pick_digit(hist, &r, &dg);
+        if (dg >= 0) {
+          s_digit = dg;
+          s_krank = r;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_kprefix = kp | ((unsigned long long)s_digit << (8 * d));
+      kmask |= 255ull << (8 * d);
+      __syncthreads();
+    }
+  }
+  const unsigned long long nk_min = s_kprefix;   // taken ties have ~key >= this
+  // The selected items (their p values are still in shared memory).
+  const bool to_smem = sorted && K <= (unsigned long long)kBlockSort;
+  __syncthreads();
+  unsigned long long* sp = bs_p + kBlockSel;   // sort buffers after the values
+  for (unsigned long long x = threadIdx.x; x < n; x += blockDim.x) {
+    const unsigned long long v = bs_p[x];
+    bool take = K > 0 && v > pk;
+    if (!take && K > 0 && v == pk) take = !key_select || ~in[x].key >= nk_min;
+    if (take) {
+      const unsigned int pos = atomicAdd(&s_out, 1u);
+      if (pos >= K) continue;   // (never: exactly K items qualify)
+      if (to_smem) {
+        sp[pos] = v;
+        sp[kBlockSort + pos] = in[x].key;
+        sp[2 * kBlockSort + pos] = in[x].aux;
+      } else {
+        out[pos] = in[x];
+      }
+    }
+  }
+  __syncthreads();
+  if (to_smem) {
+    const int m = (int)K;
+    int m2 = 1;
+    while (m2 < m) m2 <<= 1;
+    for (int x = m + threadIdx.x; x < m2; x += blockDim.x) {
+      sp[x] = 0;
+      sp[kBlockSort + x] = ~0ull;
+      sp[2 * kBlockSort + x] = 0;
+    }
+    __syncthreads();
+    unsigned long long* kk = sp + kBlockSort;
+    unsigned long long* aa = sp + 2 * kBlockSort;
+    for (int k = 2; k <= m2; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = threadIdx.x; t < m2 / 2; t += blockDim.x) {
+          const int a = ((t & ~(j - 1)) << 1) | (t & (j - 1)), b = a + j;
+          const bool up = (a & k) == 0;
+          const bool b_first = sp[b] > sp[a] || (sp[b] == sp[a] && kk[b] < kk[a]);
+          if (b_first == up) {
+            const unsigned long long tp = sp[a], tk = kk[a], ta = aa[a];
+            sp[a] = sp[b]; kk[a] = kk[b]; aa[a] = aa[b];
+            sp[b] = tp; kk[b] = tk; aa[b] = ta;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int x = threadIdx.x; x < m; x += blockDim.x) {
+      Item it;
+      it.p = sp[x];
+      it.key = kk[x];
+      it.aux = aa[x];
+      out[x] = it;
+    }
+  }
+  if (threadIdx.x == 0) *gate = 0u;
+}
+
+void block_select_dev(mad_ctx* ctx, const Item* in, uint64_t cap, uint64_t K,
+                      const unsigned long long* n_dev, bool sorted, Item* tile_sorted,
+                      uint32_t* pos, Item* out, unsigned int* gate, unsigned int* over_err,
+                      cudaStream_t st) {
+  static bool attr = false;
+  const size_t smem = (size_t)(kBlockSel + 3 * kBlockSort) * sizeof(unsigned long long);
+  if (!attr) {
+    cudaFuncSetAttribute(k_block_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  if (sorted && K > (uint64_t)kBlockSort) {   // too many to sort in one block
+    tile_select_dev(ctx, in, cap, K, n_dev, over_err, tile_sorted, pos, out, st);
+    return;
+  }
+  k_block_select<<<1, 1024, smem, st>>>(in, cap, n_dev, (unsigned int)K, out, sorted ? 1 : 0,
+                                        gate);
+  count_launch(ctx);
+  tile_select_dev(ctx, in, cap, K, n_dev, over_err, tile_sorted, pos, out, st, gate);
 }
 
 size_t dev_select_state_bytes() { return ((sizeof(SelState) + 255) / 256) * 256; }
@@ -659,7 +882,8 @@ void select_hash_dev(mad_ctx* ctx, uint64_t K, const unsigned long long* hcap_de
   k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, bound, dst, list,
                                        kDevSelectCap, count, hcap_dev, gate);
   count_launch(ctx, 5);
-  tile_select_dev(ctx, list, kDevSelectCap, K, count, &ctx->sc->err, sorted, pos, out, st);
+  block_select_dev(ctx, list, kDevSelectCap, K, count, false, sorted, pos, out,
+                   (unsigned int*)(count + 2), &ctx->sc->err, st);
 }
 
 void items_to_pairs_dev(mad_ctx* ctx, const Item* items, uint64_t cap,

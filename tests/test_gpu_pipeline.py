@@ -1,5 +1,6 @@
 """The fused dense pass (mad_pipeline_*) against the CPU oracle: Omega_t'
-(keys and x) and Omega_t (keys, x and the FP64 c) bit for bit; a CUDA-graph
+(keys and x, as a set) and Omega_t (keys, x and the FP64 c, in order) bit
+for bit; a CUDA-graph
 replay on new contents of the same input buffers matches the oracle on the
 new inputs; device-side lengths cover short and multi-tile candidate
 lists."""
@@ -48,8 +49,11 @@ def _check(mad, out, counts, cand, ref):
     nc, nr = [int(v) for v in counts.cpu().numpy()]
     assert nc == len(keys)
     ci, cj, cx, _ = mad.decode_pairs(cand, nc)
-    assert np.array_equal(mad.keys_of(ci, cj), keys)
-    assert np.array_equal(cx, x)
+    # Omega_t' as a set (the fused pass need not order it)
+    gk = mad.keys_of(ci, cj)
+    go, oo = np.argsort(gk), np.argsort(keys)
+    assert np.array_equal(gk[go], keys[oo])
+    assert np.array_equal(cx[go], x[oo])
     assert nr == len(tk)
     ri, rj, rx, rc = mad.decode_pairs(out, nr)
     assert np.array_equal(mad.keys_of(ri, rj), tk)
@@ -79,6 +83,26 @@ def test_pass_matches_oracle(flags, tprime, t):
         sc = o.scalars()
         assert st["t1_total"] == sc["T1_total"] and st["f"] == sc["F"] and st["e1"] == sc["E1"]
         assert st["sampled"] == s
+
+
+def test_ties_and_long_lists():
+    """Inputs with few distinct values (many equal x and equal c: the key
+    breaks the ties in both selections), a candidate list longer than one
+    block selects (t' = 20000), and a final top t longer than one block
+    sorts (t = 3000)."""
+    import paper_1506_03872_gb300 as mad
+    rng = _rng(66)
+    A = rng.integers(-2, 3, (1500, 12)).astype(np.float32)
+    B = rng.integers(-2, 3, (12, 2500)).astype(np.float32)
+    for s, tprime, t in ((200_000, 3000, 200), (60_000, 20_000, 3000)):
+        tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        with mad.Context() as c:
+            mad.mad_pipeline_plan(c.ctx, mad.dense(tA), mad.dense(tB), s, tprime, t)
+            out, cand = mad.new_pairs(t), mad.new_pairs(tprime)
+            counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+            mad.mad_pipeline_run(c.ctx, 17, out, counts, cand)
+            mad.mad_pipeline_status(c.ctx)
+            _check(mad, out, counts, cand, _oracle_pass(A, B, 0, s, 17, tprime, t))
 
 
 def test_gram_pass_matches_oracle():
