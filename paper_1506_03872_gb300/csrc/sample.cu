@@ -173,62 +173,44 @@ k_sort_hist(const DevScalars* __restrict__ sc, unsigned long long seed, unsigned
     row[b] = Packed ? (sort_cnt[b >> 1] >> ((b & 1u) << 4)) & 0xFFFFu : sort_cnt[b];
 }
 
-// Steps 2 and 3 split the blocks into kSortParts groups so that every
-// (bucket, group) pair is one thread.  Step 2: S[p][b] = the diamonds of
-// group p's blocks in bucket b, and tot[b] = their sum over the groups.
-constexpr int kSortParts = 8;
-
+// Step 2: tot[b] = sum over the blocks of H[g][b].
 __global__ void __launch_bounds__(256)
-k_sort_partial(const unsigned int* __restrict__ H, uint32_t nbk, int blocks,
-               unsigned int* __restrict__ S) {
-  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-  const int p = blockIdx.y;
-  if (b >= nbk) return;
-  const int per = (blocks + kSortParts - 1) / kSortParts;
-  const int g0 = p * per, g1 = g0 + per < blocks ? g0 + per : blocks;
-  unsigned int acc = 0;
-#pragma unroll 8
-  for (int g = g0; g < g1; ++g) acc += H[(size_t)g * sort_row(nbk) + b];
-  S[(size_t)p * nbk + b] = acc;
-}
-
-__global__ void __launch_bounds__(256)
-k_sort_colsum(const unsigned int* __restrict__ S, uint32_t nbk, unsigned int* __restrict__ tot) {
+k_sort_colsum(const unsigned int* __restrict__ H, uint32_t nbk, int blocks,
+              unsigned int* __restrict__ tot) {
   const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbk) return;
   unsigned int acc = 0;
-#pragma unroll
-  for (int p = 0; p < kSortParts; ++p) acc += S[(size_t)p * nbk + b];
+#pragma unroll 16
+  for (int g = 0; g < blocks; ++g) acc += H[(size_t)g * sort_row(nbk) + b];
   tot[b] = acc;
 }
 
 // Step 3 (after the exclusive scan of tot into base): H[g][b] becomes the
-// first position of block g's diamonds of bucket b.
+// first position of block g's diamonds of bucket b.  Thirty-two loads are
+// in flight before their stores (one thread walks all the blocks of its
+// bucket; splitting the walk over more threads measured slower).
 __global__ void __launch_bounds__(256)
 k_sort_coloff(unsigned int* __restrict__ H, uint32_t nbk, int blocks,
-              const unsigned int* __restrict__ S, const unsigned int* __restrict__ base) {
+              const unsigned int* __restrict__ base) {
+  constexpr int kBatch = 32;
   const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-  const int p = blockIdx.y;
   if (b >= nbk) return;
+  const size_t row = sort_row(nbk);
   unsigned int acc = base[b];
-  for (int q = 0; q < p; ++q) acc += S[(size_t)q * nbk + b];
-  const int per = (blocks + kSortParts - 1) / kSortParts;
-  const int g0 = p * per, g1 = g0 + per < blocks ? g0 + per : blocks;
-  int g = g0;
-  // Eight loads in flight before their eight stores.
-  for (; g + 8 <= g1; g += 8) {
-    unsigned int c[8];
+  int g = 0;
+  for (; g + kBatch <= blocks; g += kBatch) {
+    unsigned int c[kBatch];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) c[u] = H[(size_t)(g + u) * sort_row(nbk) + b];
+    for (int u = 0; u < kBatch; ++u) c[u] = H[(size_t)(g + u) * row + b];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      H[(size_t)(g + u) * sort_row(nbk) + b] = acc;
+    for (int u = 0; u < kBatch; ++u) {
+      H[(size_t)(g + u) * row + b] = acc;
       acc += c[u];
     }
   }
-  for (; g < g1; ++g) {
-    const unsigned int c = H[(size_t)g * sort_row(nbk) + b];
-    H[(size_t)g * sort_row(nbk) + b] = acc;
+  for (; g < blocks; ++g) {
+    const unsigned int c = H[(size_t)g * row + b];
+    H[(size_t)g * row + b] = acc;
     acc += c;
   }
 }
@@ -498,7 +480,6 @@ int sort_blocks() {
 // indices in bucket order, and each diamond's key and increment.
 struct SortScratch {
   unsigned int* H;
-  unsigned int* S;
   unsigned int* tot;
   unsigned int* base;
   unsigned int* part;
@@ -518,7 +499,6 @@ SortScratch carve_sort(void* p, uint64_t nbk, int blocks, uint64_t batch) {
     return (void*)q;
   };
   c.H = (unsigned int*)take(sort_row((uint32_t)nbk) * blocks * sizeof(unsigned int));
-  c.S = (unsigned int*)take((size_t)nbk * kSortParts * sizeof(unsigned int));
   c.tot = (unsigned int*)take(nbk * sizeof(unsigned int));
   c.base = (unsigned int*)take((nbk + 1) * sizeof(unsigned int));
   c.part = (unsigned int*)take(scan_partial_elems(nbk) * sizeof(unsigned int));
@@ -580,18 +560,16 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
     else
       k_sort_hist<false><<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n, chunk,
                                                           (uint32_t)nbk, w.H);
-    k_sort_partial<<<dim3(cols, kSortParts), 256, 0, st>>>(w.H, (uint32_t)nbk, blocks, w.S);
-    k_sort_colsum<<<cols, 256, 0, st>>>(w.S, (uint32_t)nbk, w.tot);
+    k_sort_colsum<<<cols, 256, 0, st>>>(w.H, (uint32_t)nbk, blocks, w.tot);
     if ((rs = scan_exclusive_u32(ctx, w.tot, w.base, nbk, w.part, st)) != MAD_OK) return rs;
-    k_sort_coloff<<<dim3(cols, kSortParts), 256, 0, st>>>(w.H, (uint32_t)nbk, blocks, w.S,
-                                                         w.base);
+    k_sort_coloff<<<cols, 256, 0, st>>>(w.H, (uint32_t)nbk, blocks, w.base);
     if (packed)
       k_sort_scatter<true><<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n, chunk,
                                                             (uint32_t)nbk, w.H, w.order);
     else
       k_sort_scatter<false><<<blocks, 1024, sort_smem, st>>>(ctx->sc, seed, first + done, n,
                                                              chunk, (uint32_t)nbk, w.H, w.order);
-    count_launch(ctx, 5);
+    count_launch(ctx, 4);
     phase_event(ctx, 1, st);
     k_sample_sorted<<<grid_of(n, full_sorted), 256, 0, st>>>(p, seed, first + done, n, w.order,
                                                              w.keys, w.vals);
