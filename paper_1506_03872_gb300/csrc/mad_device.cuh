@@ -324,38 +324,6 @@ __device__ __forceinline__ int hash_add_from(unsigned long long* __restrict__ ke
   return 0;
 }
 
-// The first probe of hash_add_from for a key whose group of four slots
-// (the one holding `slot`, which lies inside the table) was loaded by the
-// caller into k4: the same pick, CAS and addition.  Returns 1 or 2 as
-// hash_add_from does, or -1 when the group holds no usable slot from
-// `slot` on or the CAS lost to another key; the caller then runs
-// hash_add_from, which probes again from `slot`.
-__device__ __forceinline__ int hash_try_group(unsigned long long* __restrict__ keys,
-                                              long long* __restrict__ vals, uint64_t slot,
-                                              const unsigned long long (&k4)[4],
-                                              unsigned long long key, long long v) {
-  const uint64_t g = slot & ~3ull;
-  const uint32_t start = (uint32_t)(slot - g);
-  uint32_t pick = 4;
-#pragma unroll
-  for (int q = 3; q >= 0; --q) {
-    const bool usable = (uint32_t)q >= start && (k4[q] == key || k4[q] == EMPTY_KEY);
-    pick = usable ? (uint32_t)q : pick;
-  }
-  if (pick == 4) return -1;
-  unsigned long long cur = k4[0];
-#pragma unroll
-  for (uint32_t q = 1; q < 4; ++q) cur = (q == pick) ? k4[q] : cur;
-  int created = 0;
-  if (cur != key) {
-    const unsigned long long prev = atomicCAS(keys + g + pick, EMPTY_KEY, key);
-    if (prev != EMPTY_KEY && prev != key) return -1;
-    created = prev == EMPTY_KEY ? 1 : 0;
-  }
-  atomicAdd((unsigned long long*)vals + g + pick, (unsigned long long)v);
-  return created ? 2 : 1;
-}
-
 // Log buckets of positive 64-bit values: 16 * floor(log2 v) + the 4 bits
 // below the leading bit (1024 buckets, monotone in v), and a bucket's
 // smallest value.

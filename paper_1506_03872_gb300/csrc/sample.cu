@@ -290,52 +290,33 @@ k_sample_sorted(const SampleParams p_, unsigned long long seed, unsigned long lo
   }
 }
 
-// X update for the row-ordered diamonds: a lean kernel so many inserts are
-// in flight at once; consecutive entries share row i and hence its hash
-// region.
-__global__ void __launch_bounds__(256, 5)
+// X update for the row-ordered diamonds: a lean kernel (full occupancy) so
+// many inserts are in flight at once; consecutive entries share row i and
+// hence its hash region.
+__global__ void __launch_bounds__(256, 6)
 k_insert(const SampleParams p_, const unsigned long long* __restrict__ keys,
          const long long* __restrict__ vals, unsigned long long s) {
   const SampleParams p = resolve(p_);
   Tally t;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  // Two entries per thread and round, q and q + stride: both records, both
-  // home groups and both first probes are in flight together.
-  for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < s;
-       q += 2 * stride) {
-    const unsigned long long qb = q + stride;
-    const unsigned long long key_a = __ldcs(keys + q);
-    const long long v_a = __ldcs(vals + q);
-    const unsigned long long key_b = qb < s ? __ldcs(keys + qb) : EMPTY_KEY;
-    const long long v_b = qb < s ? __ldcs(vals + qb) : 0;
-    const bool has_a = key_a != EMPTY_KEY, has_b = key_b != EMPTY_KEY;
-    const uint64_t sa = has_a ? home_slot(p, key_a) : 0, sb = has_b ? home_slot(p, key_b) : 0;
-    const bool ga = has_a && (sa & ~3ull) + 4 <= p.hcap, gb = has_b && (sb & ~3ull) + 4 <= p.hcap;
-    unsigned long long ka[4] = {0, 0, 0, 0}, kb[4] = {0, 0, 0, 0};
-    if (ga) {
-      const ulonglong2 x = __ldcg((const ulonglong2*)(p.hkeys + (sa & ~3ull)));
-      const ulonglong2 y = __ldcg((const ulonglong2*)(p.hkeys + (sa & ~3ull) + 2));
-      ka[0] = x.x; ka[1] = x.y; ka[2] = y.x; ka[3] = y.y;
-    }
-    if (gb) {
-      const ulonglong2 x = __ldcg((const ulonglong2*)(p.hkeys + (sb & ~3ull)));
-      const ulonglong2 y = __ldcg((const ulonglong2*)(p.hkeys + (sb & ~3ull) + 2));
-      kb[0] = x.x; kb[1] = x.y; kb[2] = y.x; kb[3] = y.y;
-    }
-    int ra = ga ? hash_try_group(p.hkeys, p.hvals, sa, ka, key_a, v_a) : -1;
-    int rb = gb ? hash_try_group(p.hkeys, p.hvals, sb, kb, key_b, v_b) : -1;
-    if (has_a && ra < 0) ra = hash_add(p, key_a, v_a);
-    if (has_b && rb < 0) rb = hash_add(p, key_b, v_b);
-    if (has_a) {
+  unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long rounds = (s + stride - 1) / stride;
+  // The next entry is loaded before the current one is inserted.
+  unsigned long long key = q < s ? __ldcs(keys + q) : EMPTY_KEY;
+  long long v = q < s ? __ldcs(vals + q) : 0;
+  for (unsigned long long r = 0; r < rounds; ++r) {
+    const unsigned long long qn = q + stride;
+    const unsigned long long key_n = qn < s ? __ldcs(keys + qn) : EMPTY_KEY;
+    const long long v_n = qn < s ? __ldcs(vals + qn) : 0;
+    if (key != EMPTY_KEY) {
       ++t.inserted;
-      if (ra == 0) t.full = true;
-      if (ra == 2) ++t.created;
+      const int res = hash_add(p, key, v);
+      if (res == 0) t.full = true;
+      if (res == 2) ++t.created;
     }
-    if (has_b) {
-      ++t.inserted;
-      if (rb == 0) t.full = true;
-      if (rb == 2) ++t.created;
-    }
+    key = key_n;
+    v = v_n;
+    q = qn;
   }
   flush_tally(p, t);
 }
