@@ -639,8 +639,9 @@ void tile_select_dev(mad_ctx* ctx, const Item* in, uint64_t cap, uint64_t K,
 // ---- one-block exact selection ---------------------------------------------
 // The K largest of the first n = min(cap, *n_dev) items by (p desc, key
 // asc), for n <= kBlockSel, in one 1024-thread block: the p of every item
-// sit in shared memory and an MSB radix select (eight 8-bit digits) finds
-// the K-th largest p and how many items equal to it are taken; among those
+// sit in shared memory and an MSB radix select (8-bit digits, from the
+// highest digit in which two items differ) finds the K-th largest p and how
+// many items equal to it are taken; among those
 // ties the smallest keys are found the same way.  The K items go to out in
 // no particular order, or sorted when `sorted` (K <= kBlockSort).  A longer
 // list sets *gate to 1 and writes nothing (the tile kernels, gated on that
@@ -691,7 +692,7 @@ k_block_select(const Item* __restrict__ in, unsigned long long cap, const unsign
                unsigned int K_max, Item* __restrict__ out, int sorted, unsigned int* gate) {
   extern __shared__ unsigned long long bs_p[];   // kBlockSel values, then the sort buffers
   __shared__ unsigned int hist[256];
-  __shared__ unsigned long long s_prefix, s_rank, s_kprefix, s_krank;
+  __shared__ unsigned long long s_prefix, s_rank, s_kprefix, s_krank, s_diff;
   __shared__ int s_digit;
   __shared__ unsigned int s_out, s_tie;
   const unsigned long long n = dev_len(cap, n_dev);
@@ -700,17 +701,35 @@ k_block_select(const Item* __restrict__ in, unsigned long long cap, const unsign
     return;
   }
   const unsigned long long K = (unsigned long long)K_max < n ? (unsigned long long)K_max : n;
-  for (unsigned long long x = threadIdx.x; x < n; x += blockDim.x) bs_p[x] = in[x].p;
+  // The bits in which the items differ from the first one: the digits
+  // above the highest of them are the same in every item and need no pass.
+  const unsigned long long v0 = n > 0 ? in[0].p : 0ull;
+  unsigned long long diff = 0;
+  for (unsigned long long x = threadIdx.x; x < n; x += blockDim.x) {
+    const unsigned long long v = in[x].p;
+    bs_p[x] = v;
+    diff |= v ^ v0;
+  }
   if (threadIdx.x == 0) {
-    s_prefix = 0;
-    s_rank = K;
+    s_diff = 0;
     s_out = 0;
     s_tie = 0;
   }
   __syncthreads();
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) diff |= __shfl_xor_sync(0xFFFFFFFFu, diff, off);
+  if ((threadIdx.x & 31) == 0 && diff) atomicOr(&s_diff, diff);
+  __syncthreads();
+  // First digit that can differ (-1: all items equal).
+  const int d_top = s_diff ? (63 - __clzll((long long)s_diff)) / 8 : -1;
+  unsigned long long mask = d_top >= 7 ? 0ull : ~0ull << (8 * (d_top + 1));
+  if (threadIdx.x == 0) {
+    s_prefix = v0 & mask;
+    s_rank = K;
+  }
+  __syncthreads();
   // MSB radix select of the K-th largest p.
-  unsigned long long mask = 0;
-  for (int d = 7; d >= 0 && K > 0; --d) {
+  for (int d = d_top; d >= 0 && K > 0; --d) {
     for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
     __syncthreads();
     const unsigned long long prefix = s_prefix;

@@ -365,8 +365,9 @@ k_a_rows_dense(const T* __restrict__ A, int64_t m, int64_t d, int64_t lda,
 // k_a_rows_dense: each canonical partial then holds at most one entry, so
 // lane L keeps entries L + 32c (c < NC) in registers for both the sums and
 // the tables.  The next row's entries are loaded before the current row is
-// processed, and the scans of the NC 32-entry chunks run side by side,
-// their carries added afterwards.
+// processed; the prefix scans take the entries in consecutive runs of NC
+// per lane (through shared memory) and the tables are written 16 bytes at a
+// time where the rows allow.
 template <typename T, int NC>
 __global__ void __launch_bounds__(256)
 k_a_rows_short(const T* __restrict__ A, int64_t m, int d, int64_t lda,
@@ -374,9 +375,12 @@ k_a_rows_short(const T* __restrict__ A, int64_t m, int d, int64_t lda,
                float* __restrict__ r_out, uint32_t* __restrict__ T2, uint32_t* __restrict__ TA,
                DevScalars* sc) {
   __shared__ float nb[32 * NC];
+  __shared__ __align__(16) uint32_t scan_buf[8][2][32 * NC];   // per warp: T2, TA entries
   for (int idx = threadIdx.x; idx < 32 * NC; idx += blockDim.x) nb[idx] = idx < d ? nb_g[idx] : 0.0f;
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  uint32_t* const w2 = scan_buf[threadIdx.x >> 5][0];
+  uint32_t* const wa = scan_buf[threadIdx.x >> 5][1];
   const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 5);
   int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   float v[NC];
@@ -460,32 +464,79 @@ k_a_rows_short(const T* __restrict__ A, int64_t m, int d, int64_t lda,
       i2[c] = q2;
       ia[c] = qa;
     }
-    // NC independent warp scans per table (interleaved by the unrolling).
+    // The scans run over consecutive entries: the warp's entries (sign in
+    // bit 31, every quantised weight is below 2^31) pass through shared
+    // memory so that lane L holds entries NC L ... NC L + NC - 1, scans them
+    // in registers and adds the exclusive prefix of the lane totals (one
+    // warp scan per table).  Integer sums: the order changes nothing.
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
+    for (int c = 0; c < NC; ++c) {
+      const uint32_t sg = v[c] < 0.0f ? SIGN_BIT : 0u;
+      w2[lane + 32 * c] = i2[c] | sg;
+      wa[lane + 32 * c] = ia[c] | sg;
+    }
+    __syncwarp();
+    uint32_t e2v[NC], eav[NC];
+    if constexpr (NC % 4 == 0) {
+#pragma unroll
+      for (int c = 0; c < NC; c += 4) {
+        const uint4 x2 = *(const uint4*)(w2 + NC * lane + c);
+        const uint4 xa = *(const uint4*)(wa + NC * lane + c);
+        e2v[c] = x2.x; e2v[c + 1] = x2.y; e2v[c + 2] = x2.z; e2v[c + 3] = x2.w;
+        eav[c] = xa.x; eav[c + 1] = xa.y; eav[c + 2] = xa.z; eav[c + 3] = xa.w;
+      }
+    } else {
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        const uint32_t o2 = __shfl_up_sync(0xFFFFFFFFu, i2[c], off);
-        const uint32_t oa = __shfl_up_sync(0xFFFFFFFFu, ia[c], off);
-        if (lane >= off) {
-          i2[c] += o2;
-          ia[c] += oa;
-        }
+        e2v[c] = w2[NC * lane + c];
+        eav[c] = wa[NC * lane + c];
       }
+    }
+    __syncwarp();
+    uint32_t run2 = 0, runa = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      run2 += e2v[c] & ~SIGN_BIT;
+      runa += eav[c] & ~SIGN_BIT;
+    }
+    uint32_t inc2 = run2, inca = runa;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t o2 = __shfl_up_sync(0xFFFFFFFFu, inc2, off);
+      const uint32_t oa = __shfl_up_sync(0xFFFFFFFFu, inca, off);
+      if (lane >= off) {
+        inc2 += o2;
+        inca += oa;
+      }
+    }
+    run2 = inc2 - run2;
+    runa = inca - runa;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      run2 += e2v[c] & ~SIGN_BIT;
+      runa += eav[c] & ~SIGN_BIT;
+      e2v[c] = run2 | (e2v[c] & SIGN_BIT);
+      eav[c] = runa | (eav[c] & SIGN_BIT);
     }
     uint32_t* __restrict__ o2 = T2 + i * d;
     uint32_t* __restrict__ oa = TA + i * d;
-    uint32_t c2 = 0, ca = 0;
+    const int first = NC * lane;
+    if (NC % 4 == 0 && (d & 3) == 0) {   // rows start on 16 bytes
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int idx = lane + 32 * c;
-      const uint32_t sg = v[c] < 0.0f ? SIGN_BIT : 0u;
-      if (idx < d) {
-        o2[idx] = (c2 + i2[c]) | sg;
-        oa[idx] = (ca + ia[c]) | sg;
+      for (int c = 0; c < NC; c += 4) {
+        if (first + c < d) {   // d a multiple of 4: all four entries exist
+          *(uint4*)(o2 + first + c) = make_uint4(e2v[c], e2v[c + 1], e2v[c + 2], e2v[c + 3]);
+          *(uint4*)(oa + first + c) = make_uint4(eav[c], eav[c + 1], eav[c + 2], eav[c + 3]);
+        }
       }
-      c2 += __shfl_sync(0xFFFFFFFFu, i2[c], 31);
-      ca += __shfl_sync(0xFFFFFFFFu, ia[c], 31);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (first + c < d) {
+          o2[first + c] = e2v[c];
+          oa[first + c] = eav[c];
+        }
+      }
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) v[c] = vn[c];

@@ -33,6 +33,13 @@ def case_inputs(name: str):
         A = rng.standard_normal((300, 300)) * np.exp(0.5 * rng.standard_normal((300, 1)))
         B = rng.standard_normal((300, 450))
         return "dense", (A.astype(np.float32), B.astype(np.float32)), 0
+    if name.startswith("dense_short_d"):   # d <= 256: the register-row kernel of A
+        d = int(name[len("dense_short_d"):])
+        rng = _rng(50 + d)
+        A = rng.standard_normal((257, d)) * np.exp(0.5 * rng.standard_normal((257, 1)))
+        A[rng.random(A.shape) < 0.1] = 0.0
+        B = rng.standard_normal((d, 301)) * np.exp(0.5 * rng.standard_normal((1, 301)))
+        return "dense", (A.astype(np.float32), B.astype(np.float32)), 0
     if name == "dense_factors_small":
         w = W.dense_factors(m=4000, d=100, n=1500, seed=8)
         return "dense", (w.A, w.B), 0

@@ -35,6 +35,17 @@ def _mad():
 
 @pytest.mark.parametrize("name", CASES)
 def test_tables_bit_exact(name):
+    _tables_match(name)
+
+
+@pytest.mark.parametrize("d", [1, 7, 33, 97, 130, 200, 229, 256])
+def test_tables_short_rows(d):
+    """Every chunk count of the register-row kernel of A (d <= 256), with
+    rows whose length is and is not a multiple of four."""
+    _tables_match(f"dense_short_d{d}")
+
+
+def _tables_match(name):
     mad = _mad()
     c = Case(name, s_max=1 << 20)
     try:
