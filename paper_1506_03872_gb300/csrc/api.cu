@@ -218,9 +218,11 @@ mad_status alloc_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, 
   // capacity is taken as given.
   ctx->regioned = dense && ctx->hcap_request == 0;
   uint64_t cap = ctx->hcap_request;
+  ctx->hov = 0;
   if (ctx->regioned) {
-    cap = hash_region_bound((uint64_t)ctx->m, s_max);
-    if ((rs = alloc(ctx, ctx->hreg, (size_t)ctx->m + 1, st)) != MAD_OK) return rs;
+    ctx->hov = hash_overflow_slots(s_max);
+    cap = hash_region_bound((uint64_t)ctx->m, s_max) + ctx->hov;
+    if ((rs = alloc(ctx, ctx->hreg, (size_t)ctx->m + 2, st)) != MAD_OK) return rs;
   }
   if (cap) {
     ctx->hcap = ctx->hcap_alloc = cap;
@@ -231,15 +233,15 @@ mad_status alloc_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, 
 }
 
 // The dense table build, enqueued without any wait for the device: tables,
-// home regions, guides, and an empty hash.
-mad_status enqueue_dense_build(mad_ctx* ctx, cudaStream_t st) {
+// home regions, guides, and (clear_x) an empty hash.
+mad_status enqueue_dense_build(mad_ctx* ctx, cudaStream_t st, bool clear_x) {
   cudaMemsetAsync(ctx->sc, 0, sizeof(DevScalars), st);
   mad_status rs;
   if ((rs = build_tables_impl(ctx, st)) != MAD_OK) return rs;
   if (ctx->regioned && (rs = build_hash_regions(ctx, st)) != MAD_OK) return rs;
   if ((rs = tb_guide_build(ctx, st)) != MAD_OK) return rs;
   if ((rs = t1_guide_fill(ctx, st)) != MAD_OK) return rs;
-  return clear_x_slots(ctx, st);
+  return clear_x ? clear_x_slots(ctx, st) : MAD_OK;
 }
 
 // Host mirrors of the device scalars after a dense build (synchronises).

@@ -176,11 +176,13 @@ struct mad_ctx {
   void* bt = nullptr;               // dense B^T (n x d), the input dtype
   unsigned long long* hkeys = nullptr;
   long long* hvals = nullptr;
-  // Dense inputs: row i's home region is [hreg[i], hreg[i+1]) (m + 1
-  // offsets; hreg[m] is the end of the regions).
+  // Dense inputs: row i's home region is [hreg[i], hreg[i+1]) (m + 2
+  // offsets; hreg[m] is the end of the regions, followed by an overflow
+  // table of hov slots that only the fused pass's region builder fills;
+  // hreg[m+1] = hreg[m] + hov is the end of X).
   unsigned long long* hreg = nullptr;
   bool regioned = false;
-  uint64_t hcap = 0, hcap_alloc = 0, hcap_request = 0;
+  uint64_t hcap = 0, hcap_alloc = 0, hcap_request = 0, hov = 0;
   mad::DevScalars* sc = nullptr;
   // Scratch (select, scans); grown on demand.
   void* scratch = nullptr;
@@ -237,11 +239,13 @@ mad_status clear_slots(mad_ctx* ctx, const unsigned long long* lo_dev,
 // Home regions of the dense hash: sizes from T1 and s_max, then offsets.
 mad_status build_hash_regions(mad_ctx* ctx, cudaStream_t st);
 uint64_t hash_region_bound(uint64_t m, uint64_t s_max);
-// End of the dense hash on the device (the end of the home regions), else
-// null (the whole ctx->hcap).
+// End of the dense hash on the device (the end of the home regions and
+// their overflow table), else null (the whole ctx->hcap).
 inline const unsigned long long* hash_extent(const mad_ctx* ctx) {
-  return ctx->regioned ? ctx->hreg + ctx->m : nullptr;
+  return ctx->regioned ? ctx->hreg + ctx->m + 1 : nullptr;
 }
+// Slots of the overflow table after the home regions.
+uint64_t hash_overflow_slots(uint64_t s_max);
 // Host-side bound on the slots a scan of the hash may touch: the
 // allocation for regioned hashes (their extent is read on the device).
 inline uint64_t hash_slot_bound(const mad_ctx* ctx) {
@@ -251,8 +255,14 @@ inline uint64_t hash_slot_bound(const mad_ctx* ctx) {
 // Diamonds among the first n of a fixed pilot seed that would add to X
 // (closed, nonzero, off-diagonal when excluded); synchronises.
 mad_status pilot_inserts(mad_ctx* ctx, uint64_t n, uint64_t* hits, cudaStream_t st);
+// Whether a sampling call of s diamonds into an empty X may build the home
+// regions whole (dense, non-Gram, one sorted batch); X then needs no
+// clearing beforehand.
+bool x_builder_applies(const mad_ctx* ctx, uint64_t s);
+// fresh_x: X is empty and this call is its only filling (the fused pass):
+// where x_builder_applies, the home regions are built whole.
 mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first,
-                       cudaStream_t st);
+                       cudaStream_t st, bool fresh_x = false);
 mad_status debug_draws_impl(mad_ctx* ctx, uint64_t seed, uint64_t first, const uint64_t* ells,
                             uint64_t count, uint32_t* oi, uint32_t* ok, uint32_t* oj,
                             uint32_t* okp, int64_t* ov, cudaStream_t st);
@@ -329,7 +339,7 @@ mad_status plan_dense_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix
 size_t dense_build_scratch_bytes(const mad_ctx* ctx);
 // The dense table build enqueued without waiting for the device, and the
 // host mirrors read afterwards (synchronises).
-mad_status enqueue_dense_build(mad_ctx* ctx, cudaStream_t st);
+mad_status enqueue_dense_build(mad_ctx* ctx, cudaStream_t st, bool clear_x = true);
 mad_status finish_dense_build(mad_ctx* ctx, cudaStream_t st);
 // sample.cu: scratch of sample_impl for s diamonds, and the number of bits
 // of the row-order sort's buckets (at most 16, about log2 m).

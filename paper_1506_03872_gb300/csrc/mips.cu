@@ -325,6 +325,7 @@ mad_status mad_mips_items(mad_ctx* ctx, const mad_matrix* B, uint64_t s_max, mad
   ctx->dense = true;
   ctx->integer = false;
   ctx->regioned = true;
+  ctx->hov = 0;
   ctx->d = B->rows;
   ctx->n = B->cols;
   ctx->m = 0;

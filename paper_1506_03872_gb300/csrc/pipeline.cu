@@ -69,10 +69,12 @@ mad_status enqueue_pass(mad_ctx* ctx, uint64_t seed, mad_pair* out_dev, uint32_t
   const PipeBufs b = carve(ctx->pipe_buf, ctx->pipe_tprime, ctx->pipe_t);
   mad_pair* cand = cand_dev ? cand_dev : b.cand;
   mad_status rs;
-  // Alg. 2: tables, an empty X, s diamonds.
-  if ((rs = enqueue_dense_build(ctx, st)) != MAD_OK) return rs;
+  // Alg. 2: tables, an empty X, s diamonds.  Where the sampler builds the
+  // home regions whole, nothing needs clearing first.
+  const bool fresh = x_builder_applies(ctx, ctx->pipe_s);
+  if ((rs = enqueue_dense_build(ctx, st, !fresh)) != MAD_OK) return rs;
   ctx->sampled = 0;
-  if ((rs = sample_impl(ctx, ctx->pipe_s, seed, 0, st)) != MAD_OK) return rs;
+  if ((rs = sample_impl(ctx, ctx->pipe_s, seed, 0, st, true)) != MAD_OK) return rs;
   ctx->sampled = ctx->pipe_s;
   ctx->built = true;
   // Alg. 3: Omega_t' (its length min(t', compacted) on the device) ...

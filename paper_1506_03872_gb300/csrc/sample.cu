@@ -321,7 +321,193 @@ k_insert(const SampleParams p_, const unsigned long long* __restrict__ keys,
   flush_tally(p, t);
 }
 
-// Diagnostic twin of k_sample: writes each diamond's draws instead of// Diagnostic twin of k_sample: writes each diamond's draws instead of
+// ---- X from empty, one group of rows per block -----------------------------
+// When a single sorted batch of diamonds fills an empty X (the fused pass),
+// the home regions are written whole instead of cleared and then updated
+// with global atomics.  The sort buckets are taken 2^lg_group at a time; group
+// g covers the targets [g << gs, (g + 1) << gs) with gs = sort shift +
+// lg_group and owns the rows whose first target lies there,
+// [R[g], R[g+1]) with R[0] = 0, R[g] = 1 + #{r : T1[r] < g << gs} and
+// R[last + 1] = m.  Their regions, [hreg[R[g]], hreg[R[g+1]]), are
+// contiguous.  A block builds them in shared memory from the diamonds of its
+// buckets (those of its last row that fall into later buckets included) and
+// stores them with plain coalesced writes, so X is written once and never read
+// back from DRAM.  Every key probes linearly from its home slot to the end
+// of its group's regions; a key that finds them full goes to the overflow
+// table after the regions, [hreg[m], hreg[m] + O), a plain linear-probing
+// hash.  Groups whose regions exceed the shared-memory image are "heavy": a
+// first kernel clears their regions and the diamonds of their rows are
+// added with global atomics by whichever block holds them in its own
+// buckets.  Each diamond is added exactly once, so X is the same set of
+// (key, sum) as the one k_insert builds (the sums are exact integers).
+constexpr int kImageSlots = 3072;   // 48 KB: keys, then values
+
+// R[h] for a group boundary h (see above): 1 + #{r : T1[r] < h << gs}, read
+// from the T1 guide (entry b counts the T1 entries below b << t1g_sh, and
+// gs >= t1g_sh: the boundary is on a guide bucket).
+__device__ __forceinline__ int64_t group_first_row(const SampleParams& p, uint32_t h,
+                                                   uint32_t ngroups, int gs) {
+  if (h == 0) return 0;
+  if (h >= ngroups) return p.m;
+  const unsigned long long t = (unsigned long long)h << gs;
+  if (t > p.t1_total) return p.m;
+  const int64_t r = (int64_t)__ldg(p.T1g + (t >> p.t1g_sh)) + 1;
+  return r < p.m ? r : p.m;
+}
+
+// Row bounds of every group, the heavy flags, the clearing of heavy groups'
+// regions and of the overflow table.  One warp per group.
+__global__ void __launch_bounds__(256)
+k_group_prep(const SampleParams p_, int lg_group, uint32_t ngroups, uint64_t ov_slots,
+             uint32_t* __restrict__ R, unsigned char* __restrict__ heavy) {
+  const SampleParams p = resolve(p_);
+  const int lane = threadIdx.x & 31;
+  const uint32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int gs = p.sc->sort_shift + lg_group;
+  const unsigned long long ov0 = p.hreg[p.m];
+  if (ov0 + ov_slots > p.hcap_alloc) {   // (the allocation bounds the regions)
+    if (g == 0 && lane == 0) atomicOr(&p.sc->err, DERR_HASH_FULL);
+    return;
+  }
+  if (g < ngroups) {
+    unsigned long long slot = 0;
+    if (lane < 2) {
+      const int64_t r = group_first_row(p, g + lane, ngroups, gs);
+      slot = p.hreg[r];
+      if (lane == 0) R[g] = (uint32_t)r;
+      if (lane == 1 && g + 1 == ngroups) R[ngroups] = (uint32_t)p.m;
+    }
+    const unsigned long long lo = __shfl_sync(0xFFFFFFFFu, slot, 0);
+    const unsigned long long hi = __shfl_sync(0xFFFFFFFFu, slot, 1);
+    const bool big = hi - lo > (unsigned long long)kImageSlots;
+    if (lane == 0) heavy[g] = big ? 1 : 0;
+    if (big)
+      for (unsigned long long x = lo + lane; x < hi; x += 32) {
+        p.hkeys[x] = EMPTY_KEY;
+        p.hvals[x] = 0;
+      }
+  }
+  for (unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+       x < ov_slots; x += (unsigned long long)gridDim.x * blockDim.x) {
+    p.hkeys[ov0 + x] = EMPTY_KEY;
+    p.hvals[ov0 + x] = 0;
+  }
+}
+
+// Global insert of key into [slot, end) without wrapping, then into the
+// overflow table.  1 existing key, 2 new key, 0 both full.
+__device__ __forceinline__ int add_span_or_overflow(const SampleParams& p, unsigned long long slot,
+                                                    unsigned long long end,
+                                                    unsigned long long ov0, uint64_t ov_slots,
+                                                    unsigned long long key, long long v) {
+  if (slot < end) {
+    const int r = hash_add_from(p.hkeys, p.hvals, slot, end, slot, (uint32_t)(end - slot), key, v);
+    if (r) return r;
+  }
+  return hash_add_from(p.hkeys, p.hvals, ov0, ov0 + ov_slots, ov0 + (mix64(key) & (ov_slots - 1)),
+                       (uint32_t)ov_slots, key, v);
+}
+
+// The regions of group blockIdx.x (see above).  base[b] is the first sorted
+// position of bucket b (base[nbk] = the batch size).
+__global__ void __launch_bounds__(256)
+k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
+          const long long* __restrict__ vals, const unsigned int* __restrict__ base,
+          uint32_t nbk, int lg_group, uint32_t ngroups, uint64_t ov_slots,
+          const uint32_t* __restrict__ R, const unsigned char* __restrict__ heavy) {
+  extern __shared__ unsigned long long img[];   // kImageSlots keys, then kImageSlots values
+  __shared__ unsigned long long s_r0, s_r1, s_lo, s_hi, s_q0, s_q1, s_qend;
+  __shared__ int s_heavy;
+  const SampleParams p = resolve(p_);
+  if (p.hreg[p.m] + ov_slots > p.hcap_alloc) return;   // reported by k_group_prep
+  const uint32_t g = blockIdx.x;
+  const int bsh = p.sc->sort_shift;
+  const int gs = bsh + lg_group;
+  const uint32_t b0 = g << lg_group;
+  const uint32_t b1 = b0 + (1u << lg_group) < nbk ? b0 + (1u << lg_group) : nbk;
+  if (threadIdx.x == 0) {
+    const uint32_t r0 = R[g], r1 = R[g + 1];
+    const unsigned long long lo = p.hreg[r0], hi = p.hreg[r1];
+    const int hv = heavy[g];
+    unsigned long long qend = base[b1];
+    if (!hv && r1 > r0) {
+      // the targets of the last owned row end at T1[r1 - 1]
+      const unsigned long long tend = p.T1[r1 - 1];
+      unsigned long long be = (tend >> bsh) + ((tend & ((1ull << bsh) - 1)) ? 1 : 0);
+      be = be < nbk ? be : nbk;
+      if (be > b1) qend = base[be];
+    }
+    s_r0 = r0;
+    s_r1 = r1;
+    s_lo = lo;
+    s_hi = hi;
+    s_heavy = hv;
+    s_q0 = base[b0];
+    s_q1 = base[b1];
+    s_qend = qend;
+  }
+  __syncthreads();
+  const unsigned long long r0 = s_r0, r1 = s_r1, lo = s_lo, q0 = s_q0, q1 = s_q1;
+  const bool hv = s_heavy != 0;
+  const unsigned long long span = hv ? 0 : s_hi - lo;
+  const unsigned long long qend = hv ? q1 : s_qend;
+  const unsigned long long ov0 = p.hreg[p.m];
+  unsigned long long* ik = img;
+  unsigned long long* iv = img + kImageSlots;
+  for (unsigned long long x = threadIdx.x; x < span; x += blockDim.x) {
+    ik[x] = EMPTY_KEY;
+    iv[x] = 0;
+  }
+  __syncthreads();
+  Tally t;
+  for (unsigned long long q = q0 + threadIdx.x; q < qend; q += blockDim.x) {
+    const unsigned long long key = keys[q];
+    if (key == EMPTY_KEY) continue;
+    const long long v = vals[q];
+    const uint32_t i = (uint32_t)(key >> 32);
+    const unsigned long long rlo = __ldg(p.hreg + i);
+    const unsigned long long home = rlo + (mix64(key) & (__ldg(p.hreg + i + 1) - rlo - 1));
+    int res;
+    if (!hv && i >= r0 && i < r1) {
+      // Linear probe of the image from the home slot to its end.
+      unsigned long long x = home - lo;
+      res = 0;
+      while (x < span) {
+        const unsigned long long cur = *(volatile unsigned long long*)(ik + x);
+        if (cur == EMPTY_KEY || cur == key) {
+          const unsigned long long prev =
+              cur == key ? key : atomicCAS(ik + x, EMPTY_KEY, key);
+          if (prev == EMPTY_KEY || prev == key) {
+            atomicAdd(iv + x, (unsigned long long)v);
+            res = prev == EMPTY_KEY ? 2 : 1;
+            break;
+          }
+        }
+        ++x;
+      }
+      if (res == 0) res = add_span_or_overflow(p, 0, 0, ov0, ov_slots, key, v);
+    } else {
+      if (q >= q1) continue;   // the owner's extension: not this block's
+      const unsigned long long ex = i ? __ldg(p.T1 + i - 1) : 0ull;
+      unsigned long long og = ex >> gs;
+      og = og < ngroups - 1 ? og : ngroups - 1;
+      if (!heavy[og]) continue;   // its owner builds it
+      res = add_span_or_overflow(p, home, p.hreg[R[og + 1]], ov0, ov_slots, key, v);
+    }
+    ++t.inserted;
+    if (res == 0) t.full = true;
+    if (res == 2) ++t.created;
+  }
+  __syncthreads();
+  // The image, 16 bytes per store (regions start on 4-slot groups).
+  for (unsigned long long x = 2ull * threadIdx.x; x < span; x += 2ull * blockDim.x) {
+    *(ulonglong2*)(p.hkeys + lo + x) = make_ulonglong2(ik[x], ik[x + 1]);
+    *(longlong2*)(p.hvals + lo + x) = make_longlong2((long long)iv[x], (long long)iv[x + 1]);
+  }
+  flush_tally(p, t);
+}
+
+// Diagnostic twin of k_sample: writes each diamond's draws instead of
 // accumulating them.
 __global__ void __launch_bounds__(256)
 k_draws(const SampleParams p_, unsigned long long seed, unsigned long long first,
@@ -486,6 +672,8 @@ struct SortScratch {
   uint32_t* order;
   unsigned long long* keys;
   long long* vals;
+  uint32_t* R;              // row bounds of the X builder's groups
+  unsigned char* heavy;     // their heavy flags
   size_t bytes;
 };
 
@@ -505,6 +693,8 @@ SortScratch carve_sort(void* p, uint64_t nbk, int blocks, uint64_t batch) {
   c.order = (uint32_t*)take(batch * sizeof(uint32_t));
   c.keys = (unsigned long long*)take(batch * sizeof(unsigned long long));
   c.vals = (long long*)take(batch * sizeof(long long));
+  c.R = (uint32_t*)take((nbk + 1) * sizeof(uint32_t));
+  c.heavy = (unsigned char*)take(nbk);
   c.bytes = off;
   return c;
 }
@@ -515,7 +705,21 @@ size_t sample_scratch_bytes(const mad_ctx* ctx, uint64_t s) {
   return carve_sort(nullptr, sort_buckets(ctx->m), sort_blocks(), batch).bytes;
 }
 
-mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, cudaStream_t st) {
+// Buckets per group of the X builder: about 640 diamonds of s_max per group
+// (regions of about 1300 slots against the 3072-slot image).
+int build_group_log2(uint64_t nbk, uint64_t s_max) {
+  int lg = 0;
+  while ((2ull << lg) <= nbk && (2ull << lg) * s_max <= 640ull * nbk) ++lg;
+  return lg;
+}
+
+bool x_builder_applies(const mad_ctx* ctx, uint64_t s) {
+  return ctx->dense && ctx->regioned && ctx->hov > 0 && s > 0 && s <= kSortBatch &&
+         !(ctx->flags & MAD_GRAM);
+}
+
+mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, cudaStream_t st,
+                       bool fresh_x) {
   if (s == 0) return MAD_OK;
   const SampleParams p = make_params(ctx);
   if (!ctx->dense) {
@@ -546,6 +750,15 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
     smem_set = sort_smem;
   }
   const uint64_t batch = s < kSortBatch ? s : kSortBatch;
+  // An empty X filled by one batch, keys owned by their drawn row: the
+  // regions are built whole (k_build_x); otherwise k_insert adds to X.
+  const bool build_x = fresh_x && x_builder_applies(ctx, s);
+  const size_t image_smem = 2 * (size_t)kImageSlots * sizeof(unsigned long long);
+  static bool image_attr = false;
+  if (build_x && !image_attr) {
+    cudaFuncSetAttribute(k_build_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)image_smem);
+    image_attr = true;
+  }
   mad_status rs = ensure_scratch(ctx, sample_scratch_bytes(ctx, s), st);
   if (rs != MAD_OK) return rs;
   const SortScratch w = carve_sort(ctx->scratch, nbk, blocks, batch);
@@ -575,8 +788,17 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
                                                              w.keys, w.vals);
     count_launch(ctx);
     phase_event(ctx, 2, st);
-    k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, w.keys, w.vals, n);
-    count_launch(ctx);
+    if (build_x) {
+      const int lg = build_group_log2(nbk, ctx->s_max);
+      const uint32_t ngroups = (uint32_t)(nbk >> lg);
+      k_group_prep<<<(ngroups + 7) / 8, 256, 0, st>>>(p, lg, ngroups, ctx->hov, w.R, w.heavy);
+      k_build_x<<<ngroups, 256, image_smem, st>>>(p, w.keys, w.vals, w.base, (uint32_t)nbk, lg,
+                                                  ngroups, ctx->hov, w.R, w.heavy);
+      count_launch(ctx, 2);
+    } else {
+      k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, w.keys, w.vals, n);
+      count_launch(ctx);
+    }
     phase_event(ctx, 3, st);
   }
   return cuda_status(cudaGetLastError());

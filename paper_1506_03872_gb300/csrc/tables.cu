@@ -792,6 +792,11 @@ k_region_sizes(const uint64_t* __restrict__ T1, int64_t m, unsigned long long s_
   }
 }
 
+// hreg[m+1] = hreg[m] + the overflow table's slots.
+__global__ void k_overflow_end(unsigned long long* hreg_m, unsigned long long hov) {
+  if (threadIdx.x == 0) hreg_m[1] = hreg_m[0] + hov;
+}
+
 int ceil_log2_host(uint64_t x) {
   int e = 0;
   while (e < 64 && (1ull << e) < x) ++e;
@@ -1055,7 +1060,17 @@ mad_status build_hash_regions(mad_ctx* ctx, cudaStream_t st) {
   const unsigned blocks = (unsigned)((m + 255) / 256 < 152 * 8 ? (m + 255) / 256 : 152 * 8);
   k_region_sizes<<<blocks, 256, 0, st>>>(ctx->T1, ctx->m, ctx->s_max, ctx->sc, sizes);
   count_launch(ctx);
-  return scan_exclusive_u64(ctx, (const uint64_t*)sizes, (uint64_t*)ctx->hreg, m, part, st);
+  rs = scan_exclusive_u64(ctx, (const uint64_t*)sizes, (uint64_t*)ctx->hreg, m, part, st);
+  if (rs != MAD_OK) return rs;
+  k_overflow_end<<<1, 32, 0, st>>>(ctx->hreg + m, ctx->hov);
+  count_launch(ctx);
+  return cuda_status(cudaGetLastError());
+}
+
+uint64_t hash_overflow_slots(uint64_t s_max) {
+  uint64_t o = 1ull << 14;
+  while (o < (s_max >> 6)) o <<= 1;
+  return o;
 }
 
 mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st) {

@@ -186,3 +186,76 @@ def test_short_lists_and_limits():
         with pytest.raises(mad.MadError) as e:
             mad.mad_pipeline_plan(c.ctx, M, M, 100, 10, 5)
         assert e.value.status == mad.MAD_ERR_UNSUPPORTED
+
+
+def _oracle_x(A, B, flags, s, seed):
+    o = oracle.Oracle(oracle.Matrix(A), oracle.Matrix(B), flags, s)
+    assert o.sample(s, seed) == 0
+    return o.x(), o.scalars()
+
+
+def _export_sorted(mad, ctx, cap):
+    keys, vals, n = mad.mad_export_x(ctx, cap=cap)
+    keys = keys.cpu().numpy().view(np.uint64)
+    vals = vals.cpu().numpy()
+    order = np.argsort(keys)
+    return keys[order], vals[order], n
+
+
+@pytest.mark.parametrize("variant", ["plain", "heavy_rows", "zero_rows", "nonneg"])
+def test_pass_x_matches_oracle(variant):
+    """X after the fused pass, every key and sum, against the oracle: the
+    pass builds the home regions whole (and an overflow table), so this
+    covers rows owned by one group of buckets, rows whose diamonds run into
+    later groups, groups too large for the shared-memory image (rows with
+    thousands of expected diamonds), rows that are never drawn, and keys
+    that spill past their group's regions."""
+    import paper_1506_03872_gb300 as mad
+    A, B = _inputs(80)
+    flags = 0
+    if variant == "heavy_rows":
+        A[[5, 900, 901, 2050]] *= 8.0
+    elif variant == "zero_rows":
+        A[[0, 1, 2, 700, 701, 2049, 2050]] = 0.0
+    elif variant == "nonneg":
+        A, B, flags = np.abs(A), np.abs(B), 1
+    s, seed, tprime, t = 300_000, 23, 2000, 40
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    (ok, ov), sc = _oracle_x(A, B, flags, s, seed)
+    with mad.Context(flags) as c:
+        mad.mad_pipeline_plan(c.ctx, mad.dense(tA), mad.dense(tB), s, tprime, t)
+        out, cand = mad.new_pairs(t), mad.new_pairs(tprime)
+        counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+        mad.mad_pipeline_run(c.ctx, seed, out, counts, cand)
+        mad.mad_pipeline_status(c.ctx)
+        keys, vals, n = _export_sorted(mad, c.ctx, s + 1)
+        assert n == len(ok)
+        assert np.array_equal(keys, ok)
+        assert np.array_equal(vals, ov)
+        st = mad.mad_stats(c.ctx)
+        assert st["inserted"] == sc["inserted"]
+        assert st["distinct"] == len(ok)
+        _check(mad, out, counts, cand, _oracle_pass(A, B, flags, s, seed, tprime, t))
+
+
+def test_stepwise_after_pass_starts_empty():
+    """mad_reset_hash after a fused pass empties the regions and the
+    overflow table; the step-wise sampler then builds the oracle's X."""
+    import paper_1506_03872_gb300 as mad
+    A, B = _inputs(81)
+    A[[3, 4]] *= 8.0
+    s, tprime, t = 200_000, 1000, 20
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    with mad.Context() as c:
+        mad.mad_pipeline_plan(c.ctx, mad.dense(tA), mad.dense(tB), s, tprime, t)
+        out, cand = mad.new_pairs(t), mad.new_pairs(tprime)
+        counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+        mad.mad_pipeline_run(c.ctx, 31, out, counts, cand)
+        mad.mad_pipeline_status(c.ctx)
+        mad.mad_reset_hash(c.ctx)
+        mad.mad_sample(c.ctx, s, 32)
+        keys, vals, n = _export_sorted(mad, c.ctx, s + 1)
+        (ok, ov), _ = _oracle_x(A, B, 0, s, 32)
+        assert n == len(ok)
+        assert np.array_equal(keys, ok)
+        assert np.array_equal(vals, ov)
