@@ -341,6 +341,7 @@ k_insert(const SampleParams p_, const unsigned long long* __restrict__ keys,
 // buckets.  Each diamond is added exactly once, so X is the same set of
 // (key, sum) as the one k_insert builds (the sums are exact integers).
 constexpr int kImageSlots = 3072;   // 48 KB: keys, then values
+constexpr int kRowCache = 256;      // owned rows whose hreg a block keeps in shared memory
 
 // R[h] for a group boundary h (see above): 1 + #{r : T1[r] < h << gs}, read
 // from the T1 guide (entry b counts the T1 entries below b << t1g_sh, and
@@ -416,20 +417,32 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
           uint32_t nbk, int lg_group, uint32_t ngroups, uint64_t ov_slots,
           const uint32_t* __restrict__ R, const unsigned char* __restrict__ heavy) {
   extern __shared__ unsigned long long img[];   // kImageSlots keys, then kImageSlots values
-  __shared__ unsigned long long s_r0, s_r1, s_lo, s_hi, s_q0, s_q1, s_qend;
-  __shared__ int s_heavy;
+  __shared__ unsigned long long s_hreg[kRowCache + 1];   // hreg of the owned rows
+  __shared__ unsigned long long s_qend;
   const SampleParams p = resolve(p_);
-  if (p.hreg[p.m] + ov_slots > p.hcap_alloc) return;   // reported by k_group_prep
+  const unsigned long long ov0 = p.hreg[p.m];
+  if (ov0 + ov_slots > p.hcap_alloc) return;   // reported by k_group_prep
   const uint32_t g = blockIdx.x;
   const int bsh = p.sc->sort_shift;
   const int gs = bsh + lg_group;
   const uint32_t b0 = g << lg_group;
   const uint32_t b1 = b0 + (1u << lg_group) < nbk ? b0 + (1u << lg_group) : nbk;
+  // Every thread reads the group's bounds (one broadcast round trip), then
+  // its regions' bounds and its first diamond, while thread 0 finds where
+  // the diamonds of the last owned row end.
+  const uint32_t r0 = R[g], r1 = R[g + 1];
+  const unsigned long long q0 = base[b0], q1 = base[b1];
+  const bool hv = heavy[g] != 0;
+  const unsigned long long lo = p.hreg[r0];
+  const unsigned long long span = hv ? 0 : p.hreg[r1] - lo;
+  const bool cached = r1 - r0 < (uint32_t)kRowCache;
+  if (!hv && cached)
+    for (uint32_t x = threadIdx.x; x <= r1 - r0; x += blockDim.x) s_hreg[x] = p.hreg[r0 + x];
+  unsigned long long q = q0 + threadIdx.x;
+  unsigned long long key = q < q1 ? keys[q] : EMPTY_KEY;
+  long long v = q < q1 ? vals[q] : 0;
   if (threadIdx.x == 0) {
-    const uint32_t r0 = R[g], r1 = R[g + 1];
-    const unsigned long long lo = p.hreg[r0], hi = p.hreg[r1];
-    const int hv = heavy[g];
-    unsigned long long qend = base[b1];
+    unsigned long long qend = q1;
     if (!hv && r1 > r0) {
       // the targets of the last owned row end at T1[r1 - 1]
       const unsigned long long tend = p.T1[r1 - 1];
@@ -437,21 +450,8 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
       be = be < nbk ? be : nbk;
       if (be > b1) qend = base[be];
     }
-    s_r0 = r0;
-    s_r1 = r1;
-    s_lo = lo;
-    s_hi = hi;
-    s_heavy = hv;
-    s_q0 = base[b0];
-    s_q1 = base[b1];
     s_qend = qend;
   }
-  __syncthreads();
-  const unsigned long long r0 = s_r0, r1 = s_r1, lo = s_lo, q0 = s_q0, q1 = s_q1;
-  const bool hv = s_heavy != 0;
-  const unsigned long long span = hv ? 0 : s_hi - lo;
-  const unsigned long long qend = hv ? q1 : s_qend;
-  const unsigned long long ov0 = p.hreg[p.m];
   unsigned long long* ik = img;
   unsigned long long* iv = img + kImageSlots;
   for (unsigned long long x = threadIdx.x; x < span; x += blockDim.x) {
@@ -459,40 +459,58 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
     iv[x] = 0;
   }
   __syncthreads();
+  const unsigned long long qend = s_qend;
+  if (q >= q1 && q < qend) {   // the first diamond lies in the extension
+    key = keys[q];
+    v = vals[q];
+  }
   Tally t;
-  for (unsigned long long q = q0 + threadIdx.x; q < qend; q += blockDim.x) {
-    const unsigned long long key = keys[q];
-    if (key == EMPTY_KEY) continue;
-    const long long v = vals[q];
-    const uint32_t i = (uint32_t)(key >> 32);
-    const unsigned long long rlo = __ldg(p.hreg + i);
-    const unsigned long long home = rlo + (mix64(key) & (__ldg(p.hreg + i + 1) - rlo - 1));
+  for (; q < qend; q += blockDim.x) {
+    // The next diamond is loaded before this one is added.
+    const unsigned long long qn = q + blockDim.x;
+    const unsigned long long key_n = qn < qend ? keys[qn] : EMPTY_KEY;
+    const long long v_n = qn < qend ? vals[qn] : 0;
+    const unsigned long long k = key;
+    const long long w = v;
+    key = key_n;
+    v = v_n;
+    if (k == EMPTY_KEY) continue;
+    const uint32_t i = (uint32_t)(k >> 32);
+    const bool own = !hv && i >= r0 && i < r1;
+    unsigned long long rlo, rhi;
+    if (own && cached) {
+      rlo = s_hreg[i - r0];
+      rhi = s_hreg[i - r0 + 1];
+    } else {
+      rlo = __ldg(p.hreg + i);
+      rhi = __ldg(p.hreg + i + 1);
+    }
+    const unsigned long long home = rlo + (mix64(k) & (rhi - rlo - 1));
     int res;
-    if (!hv && i >= r0 && i < r1) {
+    if (own) {
       // Linear probe of the image from the home slot to its end.
       unsigned long long x = home - lo;
       res = 0;
       while (x < span) {
         const unsigned long long cur = *(volatile unsigned long long*)(ik + x);
-        if (cur == EMPTY_KEY || cur == key) {
-          const unsigned long long prev =
-              cur == key ? key : atomicCAS(ik + x, EMPTY_KEY, key);
-          if (prev == EMPTY_KEY || prev == key) {
-            atomicAdd(iv + x, (unsigned long long)v);
+        if (cur == EMPTY_KEY || cur == k) {
+          const unsigned long long prev = cur == k ? k : atomicCAS(ik + x, EMPTY_KEY, k);
+          if (prev == EMPTY_KEY || prev == k) {
+            atomicAdd(iv + x, (unsigned long long)w);
             res = prev == EMPTY_KEY ? 2 : 1;
             break;
           }
         }
         ++x;
       }
-      if (res == 0) res = add_span_or_overflow(p, 0, 0, ov0, ov_slots, key, v);
+      if (res == 0) res = add_span_or_overflow(p, 0, 0, ov0, ov_slots, k, w);
     } else {
       if (q >= q1) continue;   // the owner's extension: not this block's
       const unsigned long long ex = i ? __ldg(p.T1 + i - 1) : 0ull;
       unsigned long long og = ex >> gs;
       og = og < ngroups - 1 ? og : ngroups - 1;
       if (!heavy[og]) continue;   // its owner builds it
-      res = add_span_or_overflow(p, home, p.hreg[R[og + 1]], ov0, ov_slots, key, v);
+      res = add_span_or_overflow(p, home, p.hreg[R[og + 1]], ov0, ov_slots, k, w);
     }
     ++t.inserted;
     if (res == 0) t.full = true;
