@@ -332,13 +332,14 @@ k_insert(const SampleParams p_, const unsigned long long* __restrict__ keys,
 // contiguous.  A block builds them in shared memory from the diamonds of its
 // buckets (those of its last row that fall into later buckets included) and
 // stores them with plain coalesced writes, so X is written once and never read
-// back from DRAM.  Every key probes linearly from its home slot to the end
-// of its group's regions; a key that finds them full goes to the overflow
-// table after the regions, [hreg[m], hreg[m] + O), a plain linear-probing
-// hash.  Groups whose regions exceed the shared-memory image are "heavy": a
-// first kernel clears their regions and the diamonds of their rows are
-// added with global atomics by whichever block holds them in its own
-// buckets.  Each diamond is added exactly once, so X is the same set of
+// back from DRAM.  Every key probes linearly from its home slot through its
+// group's regions, taken as one circular table; a key that finds them all
+// full goes to the overflow table after the regions, [hreg[m], hreg[m] + O),
+// a plain linear-probing hash.  Groups whose regions exceed the
+// shared-memory image are "heavy": a first kernel clears their regions and
+// the diamonds of their rows are added with global atomics (the same
+// circular probing) by whichever block holds them in its own buckets.
+// Each diamond is added exactly once, so X is the same set of
 // (key, sum) as the one k_insert builds (the sums are exact integers).
 constexpr int kImageSlots = 3072;   // 48 KB: keys, then values
 constexpr int kRowCache = 256;      // owned rows whose hreg a block keeps in shared memory
@@ -395,14 +396,15 @@ k_group_prep(const SampleParams p_, int lg_group, uint32_t ngroups, uint64_t ov_
   }
 }
 
-// Global insert of key into [slot, end) without wrapping, then into the
-// overflow table.  1 existing key, 2 new key, 0 both full.
-__device__ __forceinline__ int add_span_or_overflow(const SampleParams& p, unsigned long long slot,
-                                                    unsigned long long end,
+// Global insert of key into the circular table [lo, hi) from slot, then,
+// when it is full, into the overflow table.  1 existing key, 2 new key, 0
+// both full.
+__device__ __forceinline__ int add_span_or_overflow(const SampleParams& p, unsigned long long lo,
+                                                    unsigned long long hi, unsigned long long slot,
                                                     unsigned long long ov0, uint64_t ov_slots,
                                                     unsigned long long key, long long v) {
-  if (slot < end) {
-    const int r = hash_add_from(p.hkeys, p.hvals, slot, end, slot, (uint32_t)(end - slot), key, v);
+  if (lo < hi) {
+    const int r = hash_add_from(p.hkeys, p.hvals, lo, hi, slot, (uint32_t)(hi - lo), key, v);
     if (r) return r;
   }
   return hash_add_from(p.hkeys, p.hvals, ov0, ov0 + ov_slots, ov0 + (mix64(key) & (ov_slots - 1)),
@@ -488,10 +490,11 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
     const unsigned long long home = rlo + (mix64(k) & (rhi - rlo - 1));
     int res;
     if (own) {
-      // Linear probe of the image from the home slot to its end.
+      // Linear probe of the image from the home slot, wrapping at its end
+      // (the group's regions form one circular table).
       unsigned long long x = home - lo;
       res = 0;
-      while (x < span) {
+      for (unsigned long long probes = 0; probes < span; ++probes) {
         const unsigned long long cur = *(volatile unsigned long long*)(ik + x);
         if (cur == EMPTY_KEY || cur == k) {
           const unsigned long long prev = cur == k ? k : atomicCAS(ik + x, EMPTY_KEY, k);
@@ -501,16 +504,16 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
             break;
           }
         }
-        ++x;
+        x = x + 1 < span ? x + 1 : 0;
       }
-      if (res == 0) res = add_span_or_overflow(p, 0, 0, ov0, ov_slots, k, w);
+      if (res == 0) res = add_span_or_overflow(p, 0, 0, 0, ov0, ov_slots, k, w);
     } else {
       if (q >= q1) continue;   // the owner's extension: not this block's
       const unsigned long long ex = i ? __ldg(p.T1 + i - 1) : 0ull;
       unsigned long long og = ex >> gs;
       og = og < ngroups - 1 ? og : ngroups - 1;
       if (!heavy[og]) continue;   // its owner builds it
-      res = add_span_or_overflow(p, home, p.hreg[R[og + 1]], ov0, ov_slots, k, w);
+      res = add_span_or_overflow(p, p.hreg[R[og]], p.hreg[R[og + 1]], home, ov0, ov_slots, k, w);
     }
     ++t.inserted;
     if (res == 0) t.full = true;
