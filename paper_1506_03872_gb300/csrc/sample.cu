@@ -360,8 +360,9 @@ __device__ __forceinline__ int64_t group_first_row(const SampleParams& p, uint32
 // Row bounds of every group, the heavy flags, the clearing of heavy groups'
 // regions and of the overflow table.  One warp per group.
 __global__ void __launch_bounds__(256)
-k_group_prep(const SampleParams p_, int lg_group, uint32_t ngroups, uint64_t ov_slots,
-             uint32_t* __restrict__ R, unsigned char* __restrict__ heavy) {
+k_group_prep(const SampleParams p_, const unsigned int* __restrict__ base, uint32_t nbk,
+             int lg_group, uint32_t ngroups, uint64_t ov_slots, uint32_t* __restrict__ R,
+             unsigned char* __restrict__ heavy, uint32_t* __restrict__ qend) {
   const SampleParams p = resolve(p_);
   const int lane = threadIdx.x & 31;
   const uint32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -372,16 +373,28 @@ k_group_prep(const SampleParams p_, int lg_group, uint32_t ngroups, uint64_t ov_
     return;
   }
   if (g < ngroups) {
-    unsigned long long slot = 0;
+    unsigned long long slot = 0, tend = 0;
+    int64_t r = 0;
     if (lane < 2) {
-      const int64_t r = group_first_row(p, g + lane, ngroups, gs);
+      r = group_first_row(p, g + lane, ngroups, gs);
       slot = p.hreg[r];
+      if (lane == 1 && r > 0) tend = p.T1[r - 1];   // where the last owned row's targets end
       if (lane == 0) R[g] = (uint32_t)r;
       if (lane == 1 && g + 1 == ngroups) R[ngroups] = (uint32_t)p.m;
     }
     const unsigned long long lo = __shfl_sync(0xFFFFFFFFu, slot, 0);
     const unsigned long long hi = __shfl_sync(0xFFFFFFFFu, slot, 1);
+    const int64_t r0 = __shfl_sync(0xFFFFFFFFu, r, 0);
     const bool big = hi - lo > (unsigned long long)kImageSlots;
+    if (lane == 1) {
+      // The sorted position where the diamonds the group builds end: its
+      // own buckets, and those of its last row.
+      const int bsh = p.sc->sort_shift;
+      const uint32_t b1 = (g + 1) << lg_group;
+      unsigned long long be = (tend >> bsh) + ((tend & ((1ull << bsh) - 1)) ? 1 : 0);
+      be = be < nbk ? be : nbk;
+      qend[g] = (!big && r > r0 && be > b1) ? base[be] : base[b1];
+    }
     if (lane == 0) heavy[g] = big ? 1 : 0;
     if (big)
       for (unsigned long long x = lo + lane; x < hi; x += 32) {
@@ -417,10 +430,10 @@ __global__ void __launch_bounds__(256)
 k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
           const long long* __restrict__ vals, const unsigned int* __restrict__ base,
           uint32_t nbk, int lg_group, uint32_t ngroups, uint64_t ov_slots,
-          const uint32_t* __restrict__ R, const unsigned char* __restrict__ heavy) {
+          const uint32_t* __restrict__ R, const unsigned char* __restrict__ heavy,
+          const uint32_t* __restrict__ qend_g) {
   extern __shared__ unsigned long long img[];   // kImageSlots keys, then kImageSlots values
   __shared__ unsigned long long s_hreg[kRowCache + 1];   // hreg of the owned rows
-  __shared__ unsigned long long s_qend;
   const SampleParams p = resolve(p_);
   const unsigned long long ov0 = p.hreg[p.m];
   if (ov0 + ov_slots > p.hcap_alloc) return;   // reported by k_group_prep
@@ -430,10 +443,9 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
   const uint32_t b0 = g << lg_group;
   const uint32_t b1 = b0 + (1u << lg_group) < nbk ? b0 + (1u << lg_group) : nbk;
   // Every thread reads the group's bounds (one broadcast round trip), then
-  // its regions' bounds and its first diamond, while thread 0 finds where
-  // the diamonds of the last owned row end.
+  // its regions' bounds and its first diamond.
   const uint32_t r0 = R[g], r1 = R[g + 1];
-  const unsigned long long q0 = base[b0], q1 = base[b1];
+  const unsigned long long q0 = base[b0], q1 = base[b1], qend = qend_g[g];
   const bool hv = heavy[g] != 0;
   const unsigned long long lo = p.hreg[r0];
   const unsigned long long span = hv ? 0 : p.hreg[r1] - lo;
@@ -441,19 +453,8 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
   if (!hv && cached)
     for (uint32_t x = threadIdx.x; x <= r1 - r0; x += blockDim.x) s_hreg[x] = p.hreg[r0 + x];
   unsigned long long q = q0 + threadIdx.x;
-  unsigned long long key = q < q1 ? keys[q] : EMPTY_KEY;
-  long long v = q < q1 ? vals[q] : 0;
-  if (threadIdx.x == 0) {
-    unsigned long long qend = q1;
-    if (!hv && r1 > r0) {
-      // the targets of the last owned row end at T1[r1 - 1]
-      const unsigned long long tend = p.T1[r1 - 1];
-      unsigned long long be = (tend >> bsh) + ((tend & ((1ull << bsh) - 1)) ? 1 : 0);
-      be = be < nbk ? be : nbk;
-      if (be > b1) qend = base[be];
-    }
-    s_qend = qend;
-  }
+  unsigned long long key = q < qend ? keys[q] : EMPTY_KEY;
+  long long v = q < qend ? vals[q] : 0;
   unsigned long long* ik = img;
   unsigned long long* iv = img + kImageSlots;
   for (unsigned long long x = threadIdx.x; x < span; x += blockDim.x) {
@@ -461,11 +462,6 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
     iv[x] = 0;
   }
   __syncthreads();
-  const unsigned long long qend = s_qend;
-  if (q >= q1 && q < qend) {   // the first diamond lies in the extension
-    key = keys[q];
-    v = vals[q];
-  }
   Tally t;
   for (; q < qend; q += blockDim.x) {
     // The next diamond is loaded before this one is added.
@@ -695,6 +691,7 @@ struct SortScratch {
   long long* vals;
   uint32_t* R;              // row bounds of the X builder's groups
   unsigned char* heavy;     // their heavy flags
+  uint32_t* qend;           // where the diamonds each group builds end
   size_t bytes;
 };
 
@@ -716,6 +713,7 @@ SortScratch carve_sort(void* p, uint64_t nbk, int blocks, uint64_t batch) {
   c.vals = (long long*)take(batch * sizeof(long long));
   c.R = (uint32_t*)take((nbk + 1) * sizeof(uint32_t));
   c.heavy = (unsigned char*)take(nbk);
+  c.qend = (uint32_t*)take(nbk * sizeof(uint32_t));
   c.bytes = off;
   return c;
 }
@@ -812,9 +810,10 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
     if (build_x) {
       const int lg = build_group_log2(nbk, ctx->s_max);
       const uint32_t ngroups = (uint32_t)(nbk >> lg);
-      k_group_prep<<<(ngroups + 7) / 8, 256, 0, st>>>(p, lg, ngroups, ctx->hov, w.R, w.heavy);
+      k_group_prep<<<(ngroups + 7) / 8, 256, 0, st>>>(p, w.base, (uint32_t)nbk, lg, ngroups,
+                                                      ctx->hov, w.R, w.heavy, w.qend);
       k_build_x<<<ngroups, 256, image_smem, st>>>(p, w.keys, w.vals, w.base, (uint32_t)nbk, lg,
-                                                  ngroups, ctx->hov, w.R, w.heavy);
+                                                  ngroups, ctx->hov, w.R, w.heavy, w.qend);
       count_launch(ctx, 2);
     } else {
       k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, w.keys, w.vals, n);
