@@ -432,7 +432,7 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
           uint32_t nbk, int lg_group, uint32_t ngroups, uint64_t ov_slots,
           const uint32_t* __restrict__ R, const unsigned char* __restrict__ heavy,
           const uint32_t* __restrict__ qend_g) {
-  extern __shared__ unsigned long long img[];   // kImageSlots keys, then kImageSlots values
+  extern __shared__ __align__(16) unsigned long long img[];   // kImageSlots keys, then values
   __shared__ unsigned long long s_hreg[kRowCache + 1];   // hreg of the owned rows
   const SampleParams p = resolve(p_);
   const unsigned long long ov0 = p.hreg[p.m];
@@ -457,9 +457,9 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
   long long v = q < qend ? vals[q] : 0;
   unsigned long long* ik = img;
   unsigned long long* iv = img + kImageSlots;
-  for (unsigned long long x = threadIdx.x; x < span; x += blockDim.x) {
-    ik[x] = EMPTY_KEY;
-    iv[x] = 0;
+  for (unsigned long long x = 2ull * threadIdx.x; x < span; x += 2ull * blockDim.x) {
+    *(ulonglong2*)(ik + x) = make_ulonglong2(EMPTY_KEY, EMPTY_KEY);
+    *(ulonglong2*)(iv + x) = make_ulonglong2(0, 0);
   }
   __syncthreads();
   Tally t;
@@ -487,20 +487,38 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
     int res;
     if (own) {
       // Linear probe of the image from the home slot, wrapping at its end
-      // (the group's regions form one circular table).
+      // (the group's regions form one circular table), four slots per
+      // step (two 16-byte shared loads; regions start on 4-slot groups).
+      // A stale EMPTY is caught by the CAS; a key once set never changes.
       unsigned long long x = home - lo;
       res = 0;
-      for (unsigned long long probes = 0; probes < span; ++probes) {
-        const unsigned long long cur = *(volatile unsigned long long*)(ik + x);
-        if (cur == EMPTY_KEY || cur == k) {
-          const unsigned long long prev = cur == k ? k : atomicCAS(ik + x, EMPTY_KEY, k);
-          if (prev == EMPTY_KEY || prev == k) {
-            atomicAdd(iv + x, (unsigned long long)w);
-            res = prev == EMPTY_KEY ? 2 : 1;
-            break;
-          }
+      for (unsigned long long probes = 0; probes < span;) {
+        const unsigned long long gx = x & ~3ull;
+        const ulonglong2 ka = *(const ulonglong2*)(ik + gx);
+        const ulonglong2 kb = *(const ulonglong2*)(ik + gx + 2);
+        const unsigned long long k4[4] = {ka.x, ka.y, kb.x, kb.y};
+        const uint32_t start = (uint32_t)(x - gx);
+        uint32_t pick = 4;
+#pragma unroll
+        for (int u = 3; u >= 0; --u)
+          pick = ((uint32_t)u >= start && (k4[u] == k || k4[u] == EMPTY_KEY)) ? (uint32_t)u : pick;
+        if (pick == 4) {
+          probes += 4 - start;
+          x = gx + 4 < span ? gx + 4 : 0;
+          continue;
         }
-        x = x + 1 < span ? x + 1 : 0;
+        probes += pick - start + 1;
+        unsigned long long cur = k4[0];
+#pragma unroll
+        for (int u = 1; u < 4; ++u) cur = (uint32_t)u == pick ? k4[u] : cur;
+        const unsigned long long slot = gx + pick;
+        const unsigned long long prev = cur == k ? k : atomicCAS(ik + slot, EMPTY_KEY, k);
+        if (prev == EMPTY_KEY || prev == k) {
+          atomicAdd(iv + slot, (unsigned long long)w);
+          res = prev == EMPTY_KEY ? 2 : 1;
+          break;
+        }
+        x = slot + 1 < span ? slot + 1 : 0;   // taken by another key: go on after it
       }
       if (res == 0) res = add_span_or_overflow(p, 0, 0, 0, ov0, ov_slots, k, w);
     } else {
