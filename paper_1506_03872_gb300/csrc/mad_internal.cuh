@@ -124,6 +124,11 @@ struct mad_ctx {
   // it keeps freed memory mapped, so rebuilding tables of the same shape
   // re-uses pages instead of mapping them again.
   cudaMemPool_t pool = nullptr;
+  // Second stream of the dense table build: B^T and the TB guides need only
+  // TB, so they run beside the A-row tables and T1 (forked and joined with
+  // the two events; captured as parallel branches in a CUDA graph).
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // Caller events recorded at the sampling phase boundaries (profiling).
   cudaEvent_t phase_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   uint32_t n_phase_ev = 0;
@@ -231,7 +236,10 @@ mad_status t1_guide_fill(mad_ctx* ctx, cudaStream_t st);
 // query rows (T2, TA).
 mad_status build_item_tables(mad_ctx* ctx, cudaStream_t st);
 mad_status build_query_rows(mad_ctx* ctx, cudaStream_t st);
-mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st);
+// side_branch: dense inputs launch B^T and the TB guides on ctx->side
+// (after TB, joined by the caller through ctx->ev_join); otherwise B^T is
+// launched on st and the caller builds the TB guides.
+mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st, bool side_branch = false);
 // Empties the hash slots [*lo_dev, min(bound, *hi_dev)) with bound =
 // hash_slot_bound(ctx) (0 without lo_dev, bound without hi_dev).
 mad_status clear_slots(mad_ctx* ctx, const unsigned long long* lo_dev,

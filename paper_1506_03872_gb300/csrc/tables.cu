@@ -237,7 +237,7 @@ k_b_rows_wide(const T* __restrict__ B, int64_t n, int64_t ldb, float* __restrict
         const float w = fabsf(v[c]);
         uint32_t qv;
         if (plain) {
-          qv = (uint32_t)__float2ll_rn(__fmul_rn(w, scale));
+          qv = (uint32_t)__float2int_rn(__fmul_rn(w, scale));   // at most the sum: < 2^30
           qv += (w > 0.0f && qv == 0u) ? 1u : 0u;
         } else {
           qv = quantize_row(w, e);
@@ -452,8 +452,10 @@ k_a_rows_short(const T* __restrict__ A, int64_t m, int d, int64_t lda,
         const float a = fabsf(v[c]);
         const float w2 = __fmul_rn(a, nb[idx]);
         if (plain) {
-          q2 = (uint32_t)__float2ll_rn(__fmul_rn(w2, s2));
-          qa = (uint32_t)__float2ll_rn(__fmul_rn(a, sa));
+          // 32-bit conversions: an entry is at most its row's sum, which the
+          // scaling puts below 2^30.
+          q2 = (uint32_t)__float2int_rn(__fmul_rn(w2, s2));
+          qa = (uint32_t)__float2int_rn(__fmul_rn(a, sa));
           q2 += (w2 > 0.0f && q2 == 0u) ? 1u : 0u;
           qa += (a > 0.0f && qa == 0u) ? 1u : 0u;
         } else {
@@ -1073,7 +1075,7 @@ uint64_t hash_overflow_slots(uint64_t s_max) {
   return o;
 }
 
-mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st) {
+mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st, bool side_branch) {
   const int64_t chunks = (ctx->m + T1_CHUNK - 1) / T1_CHUNK;
   mad_status rs = ensure_scratch(ctx, (size_t)chunks * sizeof(unsigned long long), st);
   if (rs != MAD_OK) return rs;
@@ -1088,8 +1090,19 @@ mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st) {
     count_launch(ctx);
   } else {
     if (ctx->B.dt == MAD_F64) launch_b_rows<double>(ctx, st); else launch_b_rows<float>(ctx, st);
+    cudaStream_t tr = st;
+    if (side_branch) {   // B^T and the TB guides beside the A rows and T1
+      cudaEventRecord(ctx->ev_fork, st);
+      cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+      tr = ctx->side;
+    }
+    if (ctx->B.dt == MAD_F64) launch_transpose<double>(ctx, tr); else launch_transpose<float>(ctx, tr);
+    if (side_branch) {
+      const mad_status gs = tb_guide_build(ctx, ctx->side);
+      if (gs != MAD_OK) return gs;
+      cudaEventRecord(ctx->ev_join, ctx->side);
+    }
     if (ctx->A.dt == MAD_F64) launch_a_rows<double>(ctx, st); else launch_a_rows<float>(ctx, st);
-    if (ctx->B.dt == MAD_F64) launch_transpose<double>(ctx, st); else launch_transpose<float>(ctx, st);
   }
   const float* r = ctx->integer ? nullptr : ctx->r;
   const unsigned long long* r64 = ctx->integer ? ctx->r64 : nullptr;
