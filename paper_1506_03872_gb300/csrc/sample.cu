@@ -254,7 +254,7 @@ k_sort_scatter(const DevScalars* __restrict__ sc, unsigned long long seed,
 // diamond q's hash key goes to keys[q] (EMPTY_KEY when it adds nothing:
 // v = 0 or an excluded diagonal) and its increment to vals[q].  k_insert
 // adds them to X.
-__global__ void __launch_bounds__(256, 5)
+__global__ void __launch_bounds__(256, 6)
 k_sample_sorted(const SampleParams p_, unsigned long long seed, unsigned long long first,
                 unsigned long long s, const uint32_t* __restrict__ order,
                 unsigned long long* __restrict__ keys, long long* __restrict__ vals) {
