@@ -237,7 +237,7 @@ mad_status alloc_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, 
 mad_status enqueue_dense_build(mad_ctx* ctx, cudaStream_t st, bool clear_x) {
   cudaMemsetAsync(ctx->sc, 0, sizeof(DevScalars), st);
   mad_status rs;
-  const bool side = ctx->side && ctx->ev_fork && ctx->ev_join;
+  const bool side = ctx->side && ctx->ev_fork && ctx->ev_fork2 && ctx->ev_join;
   if ((rs = build_tables_impl(ctx, st, side)) != MAD_OK) return rs;
   if (ctx->regioned && (rs = build_hash_regions(ctx, st)) != MAD_OK) return rs;
   if (!side && (rs = tb_guide_build(ctx, st)) != MAD_OK) return rs;
@@ -317,9 +317,11 @@ mad_status mad_create(mad_ctx** out, uint32_t flags) {
   if (e == cudaSuccess) e = cudaMemset(ctx->sc, 0, sizeof(DevScalars));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork2, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_fork2) cudaEventDestroy(ctx->ev_fork2);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->sc) cudaFree(ctx->sc);
@@ -346,6 +348,7 @@ void mad_destroy(mad_ctx* ctx) {
   cudaStreamSynchronize(0);
   cudaFree(ctx->sc);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->ev_fork2) cudaEventDestroy(ctx->ev_fork2);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);

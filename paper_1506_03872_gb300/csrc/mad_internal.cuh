@@ -128,7 +128,7 @@ struct mad_ctx {
   // TB, so they run beside the A-row tables and T1 (forked and joined with
   // the two events; captured as parallel branches in a CUDA graph).
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_fork2 = nullptr, ev_join = nullptr;
   // Caller events recorded at the sampling phase boundaries (profiling).
   cudaEvent_t phase_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   uint32_t n_phase_ev = 0;

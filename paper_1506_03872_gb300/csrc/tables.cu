@@ -159,7 +159,9 @@ k_b_rows_dense(const T* __restrict__ B, int64_t n, int64_t ldb, float* __restric
 // current one is used) and staged in shared memory, where the 256 canonical
 // partial sums advance in index order.  Table: four consecutive entries per
 // thread, quantised and scanned across the block, the next tile prefetched.
-template <typename T>
+// Part 0: sums and table; 1: the sums (nb, max |b|) alone; 2: the table
+// alone, from the sums in nb (so that it can run beside the A rows).
+template <typename T, int Part>
 __global__ void __launch_bounds__(1024)
 k_b_rows_wide(const T* __restrict__ B, int64_t n, int64_t ldb, float* __restrict__ nb,
               uint32_t* __restrict__ TB, DevScalars* sc) {
@@ -170,46 +172,52 @@ k_b_rows_wide(const T* __restrict__ B, int64_t n, int64_t ldb, float* __restrict
   const int64_t k = blockIdx.x;
   const T* __restrict__ row = B + k * ldb;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  float acc = 0.0f, mx = 0.0f;
-  float cur[4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int64_t idx = t + 1024 * r;
-    cur[r] = idx < n ? fabsf(to_f32(row[idx])) : 0.0f;
-  }
-  for (int64_t base = 0; base < n; base += kTileB) {
-    float nxt[4];
+  float total;
+  if (Part == 2) {
+    total = nb[k];
+  } else {
+    float acc = 0.0f, mx = 0.0f;
+    float cur[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      tile[t + 1024 * r] = cur[r];
-      mx = fmaxf(mx, cur[r]);
-      const int64_t idx = base + kTileB + t + 1024 * r;
-      nxt[r] = idx < n ? fabsf(to_f32(row[idx])) : 0.0f;
+      const int64_t idx = t + 1024 * r;
+      cur[r] = idx < n ? fabsf(to_f32(row[idx])) : 0.0f;
     }
-    __syncthreads();
-    if (t < 256) {
-      const int64_t len = (n - base) < kTileB ? (n - base) : kTileB;
+    for (int64_t base = 0; base < n; base += kTileB) {
+      float nxt[4];
 #pragma unroll
-      for (int j = 0; j < kTileB / 256; ++j) {
-        const int idx = t + 256 * j;
-        if (idx < len) acc = __fadd_rn(acc, tile[idx]);
+      for (int r = 0; r < 4; ++r) {
+        tile[t + 1024 * r] = cur[r];
+        mx = fmaxf(mx, cur[r]);
+        const int64_t idx = base + kTileB + t + 1024 * r;
+        nxt[r] = idx < n ? fabsf(to_f32(row[idx])) : 0.0f;
       }
+      __syncthreads();
+      if (t < 256) {
+        const int64_t len = (n - base) < kTileB ? (n - base) : kTileB;
+#pragma unroll
+        for (int j = 0; j < kTileB / 256; ++j) {
+          const int idx = t + 256 * j;
+          if (idx < len) acc = __fadd_rn(acc, tile[idx]);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 4; ++r) cur[r] = nxt[r];
     }
-    __syncthreads();
+    if (t < 256) part[t] = acc;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) cur[r] = nxt[r];
-  }
-  if (t < 256) part[t] = acc;
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
-  if (lane == 0 && mx > 0.0f) atomicMax(&sc->maxb_bits, __float_as_uint(mx));
-  __syncthreads();
-  for (int h = 128; h >= 1; h >>= 1) {
-    if (t < h) part[t] = __fadd_rn(part[t], part[t + h]);
+    for (int off = 16; off >= 1; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+    if (lane == 0 && mx > 0.0f) atomicMax(&sc->maxb_bits, __float_as_uint(mx));
     __syncthreads();
+    for (int h = 128; h >= 1; h >>= 1) {
+      if (t < h) part[t] = __fadd_rn(part[t], part[t + h]);
+      __syncthreads();
+    }
+    total = part[0];
+    if (t == 0) nb[k] = total;
   }
-  const float total = part[0];
-  if (t == 0) nb[k] = total;
+  if (Part == 1) return;
 
   uint32_t* __restrict__ out = TB + k * n;
   const int e = total > 0.0f ? 29 - ilogb_pos(total) : 0;
@@ -806,10 +814,20 @@ int ceil_log2_host(uint64_t x) {
 }
 
 template <typename T>
-void launch_b_rows(mad_ctx* ctx, cudaStream_t st) {
+void launch_b_rows(mad_ctx* ctx, cudaStream_t st, cudaStream_t table_st = nullptr) {
+  if (ctx->n >= 8192 && table_st) {   // sums on st, then the table on table_st
+    k_b_rows_wide<T, 1><<<(unsigned)ctx->d, 1024, 0, st>>>(
+        (const T*)ctx->B.values, ctx->n, ctx->B.ld, ctx->nb, ctx->TB, ctx->sc);
+    cudaEventRecord(ctx->ev_fork2, st);
+    cudaStreamWaitEvent(table_st, ctx->ev_fork2, 0);
+    k_b_rows_wide<T, 2><<<(unsigned)ctx->d, 1024, 0, table_st>>>(
+        (const T*)ctx->B.values, ctx->n, ctx->B.ld, ctx->nb, ctx->TB, ctx->sc);
+    count_launch(ctx, 2);
+    return;
+  }
   if (ctx->n >= 8192) {
-    k_b_rows_wide<T><<<(unsigned)ctx->d, 1024, 0, st>>>((const T*)ctx->B.values, ctx->n, ctx->B.ld,
-                                                         ctx->nb, ctx->TB, ctx->sc);
+    k_b_rows_wide<T, 0><<<(unsigned)ctx->d, 1024, 0, st>>>(
+        (const T*)ctx->B.values, ctx->n, ctx->B.ld, ctx->nb, ctx->TB, ctx->sc);
   } else {
     k_b_rows_dense<T><<<(unsigned)ctx->d, 256, 0, st>>>((const T*)ctx->B.values, ctx->n,
                                                          ctx->B.ld, ctx->nb, ctx->TB, ctx->sc);
@@ -1089,18 +1107,25 @@ mad_status build_tables_impl(mad_ctx* ctx, cudaStream_t st, bool side_branch) {
                                             ctx->T2, ctx->r64, ctx->sc);
     count_launch(ctx);
   } else {
-    if (ctx->B.dt == MAD_F64) launch_b_rows<double>(ctx, st); else launch_b_rows<float>(ctx, st);
-    cudaStream_t tr = st;
-    if (side_branch) {   // B^T and the TB guides beside the A rows and T1
-      cudaEventRecord(ctx->ev_fork, st);
-      cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
-      tr = ctx->side;
-    }
-    if (ctx->B.dt == MAD_F64) launch_transpose<double>(ctx, tr); else launch_transpose<float>(ctx, tr);
     if (side_branch) {
-      const mad_status gs = tb_guide_build(ctx, ctx->side);
+      // Second stream: B^T at once (it needs only B), then, after B's row
+      // sums, the TB table (wide rows) and its guides, beside the A rows
+      // and T1 on st.  Narrow rows build TB with their sums on st.
+      cudaStream_t sd = ctx->side;
+      cudaEventRecord(ctx->ev_fork, st);
+      cudaStreamWaitEvent(sd, ctx->ev_fork, 0);
+      if (ctx->B.dt == MAD_F64) launch_transpose<double>(ctx, sd); else launch_transpose<float>(ctx, sd);
+      if (ctx->B.dt == MAD_F64) launch_b_rows<double>(ctx, st, sd); else launch_b_rows<float>(ctx, st, sd);
+      if (ctx->n < 8192) {
+        cudaEventRecord(ctx->ev_fork2, st);
+        cudaStreamWaitEvent(sd, ctx->ev_fork2, 0);
+      }
+      const mad_status gs = tb_guide_build(ctx, sd);
       if (gs != MAD_OK) return gs;
-      cudaEventRecord(ctx->ev_join, ctx->side);
+      cudaEventRecord(ctx->ev_join, sd);
+    } else {
+      if (ctx->B.dt == MAD_F64) launch_b_rows<double>(ctx, st); else launch_b_rows<float>(ctx, st);
+      if (ctx->B.dt == MAD_F64) launch_transpose<double>(ctx, st); else launch_transpose<float>(ctx, st);
     }
     if (ctx->A.dt == MAD_F64) launch_a_rows<double>(ctx, st); else launch_a_rows<float>(ctx, st);
   }
