@@ -354,6 +354,20 @@ mad_status mad_debug_draws(mad_ctx* ctx, uint64_t seed, uint64_t first, uint64_t
                            uint32_t* i_dev, uint32_t* k_dev, uint32_t* j_dev, uint32_t* kp_dev,
                            int64_t* v_dev, mad_stream stream);
 
+/* Layout of the dense hash X for the next mad_build_tables or
+ * mad_pipeline_plan, for tests of its rarely taken paths.  region_factor:
+ * row i's home region is the smallest power of two >= region_factor x its
+ * expected diamonds (at least 4 slots); 0 < region_factor <= 1.5, default
+ * 1.5.  overflow_slots: slots of the overflow table after the regions (a
+ * power of two >= 16), or 0 for the default max(2^14, s_max / 64) rounded
+ * up to a power of two.  Regions too small for their keys send them to the
+ * overflow table in the fused pass (mad_pipeline_run); a full overflow
+ * table is reported as MAD_ERR_HASH_FULL by mad_pipeline_status.  The
+ * step-wise mad_sample probes the regions as one table and reports
+ * MAD_ERR_HASH_FULL past its probe limit.  MAD_ERR_ARG outside these
+ * ranges. */
+mad_status mad_debug_set_hash_layout(mad_ctx* ctx, float region_factor, uint64_t overflow_slots);
+
 /* As mad_debug_draws for an arbitrary device list of diamond indices. */
 mad_status mad_debug_draws_list(mad_ctx* ctx, uint64_t seed, const uint64_t* ells_dev,
                                 uint64_t count, uint32_t* i_dev, uint32_t* k_dev,

@@ -31,7 +31,7 @@ TABLES = {"T1": 0, "T2": 1, "TA": 2, "TB": 3, "na": 4, "nb": 5, "r": 6}
 EXPORTS = (
     "mad_create", "mad_destroy", "mad_strerror", "mad_set_hash_capacity", "mad_build_tables",
     "mad_sample", "mad_reset_hash", "mad_topk", "mad_rescore", "mad_stats", "mad_debug_draws",
-    "mad_debug_draws_list", "mad_export_x", "mad_export_table", "mad_rescore_noalloc",
+    "mad_debug_draws_list", "mad_debug_set_hash_layout", "mad_export_x", "mad_export_table", "mad_rescore_noalloc",
     "mad_dense_topt", "mad_debug_dense_product", "mad_set_phase_events", "mad_mips_items",
     "mad_mips_plan", "mad_mips_run", "mad_budget_features", "mad_mlp_train", "mad_mlp_predict",
     "mad_pipeline_plan", "mad_pipeline_run", "mad_pipeline_status",
@@ -117,6 +117,7 @@ def lib() -> ctypes.CDLL:
                                               ctypes.POINTER(mad_matrix), P, P]
         L.mad_debug_draws.argtypes = [P, u64, u64, u64, P, P, P, P, P, P]
         L.mad_debug_draws_list.argtypes = [P, u64, P, u64, P, P, P, P, P, P]
+        L.mad_debug_set_hash_layout.argtypes = [P, ctypes.c_float, u64]
         L.mad_export_x.argtypes = [P, P, P, u64, ctypes.POINTER(u64), P]
         L.mad_export_table.argtypes = [P, i32, P, u64, ctypes.POINTER(u64), P]
         for name in EXPORTS:
@@ -358,6 +359,11 @@ def mad_debug_draws(ctx, seed: int, first: int, count: int, stream=None):
     _check(lib().mad_debug_draws(ctx, seed, first, count, *[_ptr(o) for o in outs], _ptr(v),
                                  _stream(stream)), "mad_debug_draws")
     return tuple(o[:count] for o in outs) + (v[:count],)
+
+
+def mad_debug_set_hash_layout(ctx, region_factor: float, overflow_slots: int = 0) -> None:
+    _check(lib().mad_debug_set_hash_layout(ctx, region_factor, overflow_slots),
+           "mad_debug_set_hash_layout")
 
 
 def mad_debug_draws_list(ctx, seed: int, ells, stream=None):

@@ -220,7 +220,7 @@ mad_status alloc_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, 
   uint64_t cap = ctx->hcap_request;
   ctx->hov = 0;
   if (ctx->regioned) {
-    ctx->hov = hash_overflow_slots(s_max);
+    ctx->hov = ctx->hov_request ? ctx->hov_request : hash_overflow_slots(s_max);
     cap = hash_region_bound((uint64_t)ctx->m, s_max) + ctx->hov;
     if ((rs = alloc(ctx, ctx->hreg, (size_t)ctx->m + 2, st)) != MAD_OK) return rs;
   }
@@ -374,6 +374,16 @@ mad_status mad_set_hash_capacity(mad_ctx* ctx, uint64_t slots) {
   if (!ctx) return MAD_ERR_ARG;
   if (slots != 0 && (slots < 1024 || (slots & (slots - 1)) != 0)) return MAD_ERR_ARG;
   ctx->hcap_request = slots;
+  return MAD_OK;
+}
+
+mad_status mad_debug_set_hash_layout(mad_ctx* ctx, float region_factor, uint64_t overflow_slots) {
+  if (!ctx) return MAD_ERR_ARG;
+  if (!(region_factor > 0.0f && region_factor <= 1.5f)) return MAD_ERR_ARG;
+  if (overflow_slots != 0 && (overflow_slots < 16 || (overflow_slots & (overflow_slots - 1)) != 0))
+    return MAD_ERR_ARG;
+  ctx->region_factor = region_factor;
+  ctx->hov_request = overflow_slots;
   return MAD_OK;
 }
 

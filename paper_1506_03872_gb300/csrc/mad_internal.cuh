@@ -188,6 +188,10 @@ struct mad_ctx {
   unsigned long long* hreg = nullptr;
   bool regioned = false;
   uint64_t hcap = 0, hcap_alloc = 0, hcap_request = 0, hov = 0;
+  // Region size factor and overflow table request (0: default) of the
+  // dense hash.
+  float region_factor = 1.5f;
+  uint64_t hov_request = 0;
   mad::DevScalars* sc = nullptr;
   // Scratch (select, scans); grown on demand.
   void* scratch = nullptr;

@@ -780,13 +780,13 @@ __global__ void k_transpose(const T* __restrict__ B, int64_t d, int64_t n, int64
   }
 }
 
-// Home-region size of row i: the smallest power of two >= 1.5 x the row's
-// expected number of diamonds among s_max, at least 4 (every region starts
-// on a 4-slot group).
+// Home-region size of row i: the smallest power of two >= factor x the
+// row's expected number of diamonds among s_max (factor 1.5 unless a test
+// asks for less), at least 4 (every region starts on a 4-slot group).
 __global__ void __launch_bounds__(256)
-k_region_sizes(const uint64_t* __restrict__ T1, int64_t m, unsigned long long s_max,
+k_region_sizes(const uint64_t* __restrict__ T1, int64_t m, unsigned long long s_max, float factor,
                const DevScalars* sc, unsigned long long* __restrict__ sizes) {
-  const float scale = 1.5f * ((float)s_max / (float)(sc->t1_total ? sc->t1_total : 1ull));
+  const float scale = factor * ((float)s_max / (float)(sc->t1_total ? sc->t1_total : 1ull));
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
     const unsigned long long q = T1[i] - (i ? T1[i - 1] : 0ull);
@@ -1078,7 +1078,8 @@ mad_status build_hash_regions(mad_ctx* ctx, cudaStream_t st) {
   unsigned long long* sizes = (unsigned long long*)ctx->scratch;
   uint64_t* part = (uint64_t*)((char*)ctx->scratch + sizes_bytes);
   const unsigned blocks = (unsigned)((m + 255) / 256 < 152 * 8 ? (m + 255) / 256 : 152 * 8);
-  k_region_sizes<<<blocks, 256, 0, st>>>(ctx->T1, ctx->m, ctx->s_max, ctx->sc, sizes);
+  k_region_sizes<<<blocks, 256, 0, st>>>(ctx->T1, ctx->m, ctx->s_max, ctx->region_factor, ctx->sc,
+                                         sizes);
   count_launch(ctx);
   rs = scan_exclusive_u64(ctx, (const uint64_t*)sizes, (uint64_t*)ctx->hreg, m, part, st);
   if (rs != MAD_OK) return rs;

@@ -259,3 +259,50 @@ def test_stepwise_after_pass_starts_empty():
         assert n == len(ok)
         assert np.array_equal(keys, ok)
         assert np.array_equal(vals, ov)
+
+
+def test_pass_overflow_table():
+    """Home regions sized for half the expected diamonds: most groups of
+    regions fill up and their further keys go to the overflow table, whose
+    contents must complete X exactly."""
+    import paper_1506_03872_gb300 as mad
+    A, B = _inputs(82)
+    s, seed, tprime, t = 200_000, 41, 1500, 30
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    (ok, ov), sc = _oracle_x(A, B, 0, s, seed)
+    with mad.Context() as c:
+        mad.mad_debug_set_hash_layout(c.ctx, 0.5, 1 << 19)
+        mad.mad_pipeline_plan(c.ctx, mad.dense(tA), mad.dense(tB), s, tprime, t)
+        out, cand = mad.new_pairs(t), mad.new_pairs(tprime)
+        counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+        mad.mad_pipeline_run(c.ctx, seed, out, counts, cand)
+        mad.mad_pipeline_status(c.ctx)
+        st = mad.mad_stats(c.ctx)
+        assert st["hash_capacity"] < len(ok)   # the regions alone cannot hold X
+        keys, vals, n = _export_sorted(mad, c.ctx, s + 1)
+        assert n == len(ok)
+        assert np.array_equal(keys, ok)
+        assert np.array_equal(vals, ov)
+        assert st["inserted"] == sc["inserted"]
+        _check(mad, out, counts, cand, _oracle_pass(A, B, 0, s, seed, tprime, t))
+
+
+def test_pass_overflow_full_is_reported():
+    """Regions and overflow table both too small: the pass reports
+    MAD_ERR_HASH_FULL instead of returning a partial X silently."""
+    import paper_1506_03872_gb300 as mad
+    A, B = _inputs(83)
+    s, tprime, t = 200_000, 1000, 20
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    with mad.Context() as c:
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_debug_set_hash_layout(c.ctx, 2.0, 0)
+        assert e.value.status == mad.MAD_ERR_ARG
+        mad.mad_debug_set_hash_layout(c.ctx, 0.5, 1024)
+        mad.mad_pipeline_plan(c.ctx, mad.dense(tA), mad.dense(tB), s, tprime, t)
+        out, cand = mad.new_pairs(t), mad.new_pairs(tprime)
+        counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+        mad.mad_pipeline_run(c.ctx, 43, out, counts, cand)
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_pipeline_status(c.ctx)
+        assert e.value.status == mad.MAD_ERR_HASH_FULL
