@@ -885,10 +885,10 @@ void select_hash_dev(mad_ctx* ctx, uint64_t K, const unsigned long long* hcap_de
   cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
   const uint64_t bound = hash_slot_bound(ctx);
   const unsigned blocks = grid_for(bound, 152 * 8);
-  // The threshold from one 4-slot group in 8: the sampled count must reach
-  // K/8 plus four standard deviations, so the compaction keeps fewer than
+  // The threshold from one 4-slot group in 16: the sampled count must reach
+  // K/16 plus four standard deviations, so the compaction keeps fewer than
   // K items only rarely; then the exact histogram and compaction run.
-  constexpr int kLg = 3;
+  constexpr int kLg = 4;
   const double ks = (double)K / (1 << kLg);
   const unsigned long long Ks = (unsigned long long)(ks + 4.0 * sqrt(ks) + 8.0);
   unsigned int* gate = (unsigned int*)(count + 1);
