@@ -154,8 +154,8 @@ k_b_rows_dense(const T* __restrict__ B, int64_t n, int64_t ldb, float* __restric
 }
 
 // Rows of dense B with 1024 threads per row, the same results as
-// k_b_rows_dense.  Sums: tiles of 4096 entries are loaded by all threads
-// (four independent loads each; the next tile's are issued before the
+// k_b_rows_dense.  Sums: tiles of 8192 entries are loaded by all threads
+// (eight independent loads each; the next tile's are issued before the
 // current one is used) and staged in shared memory, where the 256 canonical
 // partial sums advance in index order.  Table: four consecutive entries per
 // thread, quantised and scanned across the block, the next tile prefetched.
@@ -165,8 +165,10 @@ template <typename T, int Part>
 __global__ void __launch_bounds__(1024)
 k_b_rows_wide(const T* __restrict__ B, int64_t n, int64_t ldb, float* __restrict__ nb,
               uint32_t* __restrict__ TB, DevScalars* sc) {
-  constexpr int kTileB = 4096;
-  __shared__ float tile[kTileB];
+  constexpr int kTileB = 4096;      // table tiles: four consecutive entries per thread
+  constexpr int kSumTile = 8192;    // sum tiles: eight loads in flight per thread
+  constexpr int kSumPer = kSumTile / 1024;
+  __shared__ float tile[kSumTile];
   __shared__ float part[256];
   __shared__ uint32_t wsum[33];
   const int64_t k = blockIdx.x;
@@ -177,33 +179,33 @@ k_b_rows_wide(const T* __restrict__ B, int64_t n, int64_t ldb, float* __restrict
     total = nb[k];
   } else {
     float acc = 0.0f, mx = 0.0f;
-    float cur[4];
+    float cur[kSumPer];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < kSumPer; ++r) {
       const int64_t idx = t + 1024 * r;
       cur[r] = idx < n ? fabsf(to_f32(row[idx])) : 0.0f;
     }
-    for (int64_t base = 0; base < n; base += kTileB) {
-      float nxt[4];
+    for (int64_t base = 0; base < n; base += kSumTile) {
+      float nxt[kSumPer];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < kSumPer; ++r) {
         tile[t + 1024 * r] = cur[r];
         mx = fmaxf(mx, cur[r]);
-        const int64_t idx = base + kTileB + t + 1024 * r;
+        const int64_t idx = base + kSumTile + t + 1024 * r;
         nxt[r] = idx < n ? fabsf(to_f32(row[idx])) : 0.0f;
       }
       __syncthreads();
       if (t < 256) {
-        const int64_t len = (n - base) < kTileB ? (n - base) : kTileB;
+        const int64_t len = (n - base) < kSumTile ? (n - base) : kSumTile;
 #pragma unroll
-        for (int j = 0; j < kTileB / 256; ++j) {
+        for (int j = 0; j < kSumTile / 256; ++j) {
           const int idx = t + 256 * j;
           if (idx < len) acc = __fadd_rn(acc, tile[idx]);
         }
       }
       __syncthreads();
 #pragma unroll
-      for (int r = 0; r < 4; ++r) cur[r] = nxt[r];
+      for (int r = 0; r < kSumPer; ++r) cur[r] = nxt[r];
     }
     if (t < 256) part[t] = acc;
 #pragma unroll
