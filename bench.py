@@ -667,6 +667,7 @@ def _oracle_step(w, s):
 
 
 def cpu_baseline(w, diamonds):
+    diamonds = min(diamonds, w.s)
     sec = _oracle_step(w, diamonds)
     return {"value": round(diamonds / sec, 1), "unit": "diamonds/s", "cores": 1,
             "kind": "oracle",
@@ -679,12 +680,13 @@ def run_reference(args):
     if rank != 0:
         return
     w = _workload(args.workload, args.scale)
+    diamonds = min(args.cpu_diamonds, w.s)
     for _ in range(args.warmup):
-        _oracle_step(w, args.cpu_diamonds)
-    secs = [_oracle_step(w, args.cpu_diamonds) for _ in range(args.steps)]
+        _oracle_step(w, diamonds)
+    secs = [_oracle_step(w, diamonds) for _ in range(args.steps)]
     total = sum(secs)
-    value = args.cpu_diamonds * args.steps / total
-    sample = (f"full {w.name} tables + {args.cpu_diamonds} of the {w.s} diamonds + top-t' + "
+    value = diamonds * args.steps / total
+    sample = (f"full {w.name} tables + {diamonds} of the {w.s} diamonds + top-t' + "
               "rescore per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "diamonds/s",

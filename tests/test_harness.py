@@ -33,3 +33,24 @@ def test_tie_aware_recall():
     gc = np.array([tau, tau - 1])
     r, _ = bench.recall_of(w, gi, gj, gc, set(), tau, counts)
     assert r == 1 / w.t
+
+
+def test_reference_arm_line_on_cpu():
+    """bench.py --impl reference times the CPU oracle and prints one JSON
+    line with the contract's keys (no GPU needed)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0", "--scale", "0.02",
+                          "--cpu-diamonds", "100000"],
+                         capture_output=True, text=True, timeout=300, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "diamonds/s"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["config"]["workload"] == "dense_factors"
+    assert " 100000 of the " in line["cpu_baseline"]["sample"]
