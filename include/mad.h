@@ -219,7 +219,12 @@ mad_status mad_rescore(mad_ctx* ctx, const mad_pair* cand_dev, uint32_t ncand, u
  * two uint32 (device), the number of candidates and of results; cand_dev
  * (optional, t' pairs, device): Omega_t', in no particular order.  Errors
  * found on the device (a compacted candidate list above 131072 entries, a
- * hash probe limit) go to the device error word.
+ * full overflow table of the hash) go to the device error word.  X after a
+ * run (read by mad_export_x, mad_topk, mad_rescore) is the X of the step-wise
+ * calls, laid out differently: for dense non-Gram inputs the home regions
+ * are built whole and keys that do not fit go to an overflow table after
+ * them.  The run samples all s diamonds the plan allows, so a further
+ * mad_sample needs mad_reset_hash first (MAD_ERR_OVERFLOW otherwise).
  *
  * mad_pipeline_status: synchronises, refreshes the host-side table scalars
  * (mad_stats) and returns the status of the last run. */
