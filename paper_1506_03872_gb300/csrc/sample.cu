@@ -357,8 +357,10 @@ __device__ __forceinline__ int64_t group_first_row(const SampleParams& p, uint32
   return r < p.m ? r : p.m;
 }
 
-// Row bounds of every group, the heavy flags, the clearing of heavy groups'
-// regions and of the overflow table.  One warp per group.
+// Row bounds of every group (R), its heavy flag, the sorted position where
+// the diamonds it builds end (qend: its own buckets and those of its last
+// row's diamonds), the clearing of heavy groups' regions and of the
+// overflow table.  One warp per group.
 __global__ void __launch_bounds__(256)
 k_group_prep(const SampleParams p_, const unsigned int* __restrict__ base, uint32_t nbk,
              int lg_group, uint32_t ngroups, uint64_t ov_slots, uint32_t* __restrict__ R,
@@ -425,7 +427,8 @@ __device__ __forceinline__ int add_span_or_overflow(const SampleParams& p, unsig
 }
 
 // The regions of group blockIdx.x (see above).  base[b] is the first sorted
-// position of bucket b (base[nbk] = the batch size).
+// position of bucket b (base[nbk] = the batch size); R, heavy and qend_g
+// come from k_group_prep.
 __global__ void __launch_bounds__(256)
 k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
           const long long* __restrict__ vals, const unsigned int* __restrict__ base,
