@@ -16,6 +16,8 @@ arrays; every function mirrors one step of the paper:
 * ``rescore``                       -- exact dot products (Alg. 3).
 * ``topt``                          -- Omega_t (Alg. 3, last step).
 * ``bruteforce``                    -- exact t-MAD ground truth (Defn. 1).
+* ``sparse_exact``                  -- exact top t by the row-wise sparse
+  product (the paper's exact computation, Sec. 4.3).
 * ``enumerate``                     -- exact three-path law (Lemma 1).
 """
 from __future__ import annotations
@@ -81,6 +83,8 @@ def _L() -> ctypes.CDLL:
         lib.or_topt.argtypes = [i64, P, P, u64, P, P]
         lib.or_bruteforce.restype = i64
         lib.or_bruteforce.argtypes = [P, u64, P, P]
+        lib.or_sparse_exact.restype = i64
+        lib.or_sparse_exact.argtypes = [P, u64, P, P]
         lib.or_enumerate.restype = i64
         lib.or_enumerate.argtypes = [P, i64, P, P, P, P, P, P]
         lib.or_philox4x32_10.argtypes = [P, P, P]
@@ -215,6 +219,14 @@ class Oracle:
         keys = np.zeros(t, np.uint64)
         c = np.zeros(t, np.float64)
         cnt = _L().or_bruteforce(self.h, t, _p(keys), _p(c))
+        return keys[:cnt], c[:cnt]
+
+    def sparse_exact(self, t: int):
+        """Exact top t by the row-wise sparse product (Sec. 4.3): every
+        stored entry of C is a candidate, (|c| desc, key asc)."""
+        keys = np.zeros(t, np.uint64)
+        c = np.zeros(t, np.float64)
+        cnt = _L().or_sparse_exact(self.h, t, _p(keys), _p(c))
         return keys[:cnt], c[:cnt]
 
     def enumerate(self, cap: int = 1 << 20):

@@ -661,6 +661,58 @@ int64_t or_bruteforce(void* h, uint64_t t, uint64_t* out_keys, double* out_c) {
   return cnt;
 }
 
+// Exact top-t by the row-wise sparse product (the paper's exact computation
+// for comparison, Sec. 4.3, written for sparse inputs): row i of C is the
+// sum over the stored entries a_ik of a_ik times row k of B, accumulated in
+// a dense vector over j; every stored c_ij of the row (an entry that some k
+// reaches) is a candidate, with the same pair rules as or_bruteforce (Gram:
+// unordered pairs, j >= i; the diagonal skipped when asked).  Pairs that no
+// k reaches have c_ij = 0 and are candidates only when fewer than t stored
+// entries exist; they are not enumerated, so the result holds
+// min(t, #stored candidates) pairs.  Sums are long double in ascending k
+// (exact integers for 0/1 inputs).  Order (|c| desc, key asc).
+int64_t or_sparse_exact(void* h, uint64_t t, uint64_t* out_keys, double* out_c) {
+  Oracle* o = (Oracle*)h;
+  std::vector<long double> acc(o->n, 0.0L);
+  std::vector<char> seen(o->n, 0);
+  std::vector<int64_t> touched;
+  std::vector<Scored> best;
+  for (int64_t i = 0; i < o->m; ++i) {
+    touched.clear();
+    for (int64_t e = o->A.ptr[i]; e < o->A.ptr[i + 1]; ++e) {
+      const int64_t k = o->A.col[e];
+      const long double a = (long double)o->A.val[e];
+      for (int64_t f = o->B.ptr[k]; f < o->B.ptr[k + 1]; ++f) {
+        const int64_t j = o->B.col[f];
+        if (!seen[j]) {
+          seen[j] = 1;
+          touched.push_back(j);
+        }
+        acc[j] += a * (long double)o->B.val[f];
+      }
+    }
+    for (const int64_t j : touched) {
+      const long double c = acc[j];
+      acc[j] = 0.0L;
+      seen[j] = 0;
+      if ((o->flags & FL_GRAM) && j < i) continue;
+      if ((o->flags & FL_EXCLUDE_DIAG) && j == i) continue;
+      best.push_back({((uint64_t)i << 32) | (uint64_t)j, (double)c});
+    }
+    if (best.size() > 4 * t + 4096) {
+      std::nth_element(best.begin(), best.begin() + t, best.end(), by_abs_c);
+      best.resize(t);
+    }
+  }
+  std::sort(best.begin(), best.end(), by_abs_c);
+  const int64_t cnt = std::min<int64_t>((int64_t)best.size(), (int64_t)t);
+  for (int64_t q = 0; q < cnt; ++q) {
+    out_keys[q] = best[q].key;
+    out_c[q] = best[q].c;
+  }
+  return cnt;
+}
+
 // Lemma 1 / Lemma 2 enumerator for tiny instances: the exact probability of
 // every three-path (k', i, k, j) under the oracle's tables and its
 // increment.  Writes up to cap rows (i, k, j, k', prob, v) and returns the

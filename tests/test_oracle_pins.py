@@ -443,3 +443,120 @@ def test_bf16_rounding_reference():
     x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -7, -2.5], np.float32)
     assert np.array_equal(R.bf16(x), np.array([1.0, 1.0, 1.0 + 2 ** -6, 1.0 + 2 ** -7, -2.5],
                                               np.float32))
+
+
+# ---------------------------------------------------------------------------
+# 0/1 inputs: exact counts (Alg. 3 on binary inputs; c_ij counts the common
+# entries, Sec. 3.1) and the exact sparse product (Sec. 4.3)
+# ---------------------------------------------------------------------------
+def _csr_of(D):
+    """CSR (rowptr, colidx) of a 0/1 numpy matrix (columns ascending)."""
+    rp = np.concatenate([[0], np.cumsum((D != 0).sum(1))]).astype(np.int64)
+    return Matrix(rowptr=rp, colidx=np.nonzero(D)[1].astype(np.int32), shape=D.shape)
+
+
+def _uneven_binary(m, d, seed):
+    """0/1 matrix whose rows have very uneven degrees: row r keeps each
+    entry with probability 0.9^r-ish, plus a few full and empty rows."""
+    rng = _rng(seed)
+    p = 0.9 ** (np.arange(m) % 40)[:, None] * np.ones((1, d))
+    D = (rng.random((m, d)) < p).astype(np.int64)
+    D[3] = 1          # a full row
+    D[5] = 0          # an empty row
+    return D
+
+
+def _ref_topt(C, t, gram=False, exclude_diag=False, stored=None):
+    """numpy top-t of |C| by (|c| desc, key asc) under the pair rules."""
+    m, n = C.shape
+    ii, jj = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    keep = np.ones(C.shape, bool)
+    if gram:
+        keep &= jj >= ii
+    if exclude_diag:
+        keep &= jj != ii
+    if stored is not None:
+        keep &= stored
+    i, j, c = ii[keep], jj[keep], C[keep]
+    order = np.lexsort((j, i, -np.abs(c)))[:t]
+    keys = (i[order].astype(np.uint64) << np.uint64(32)) | j[order].astype(np.uint64)
+    return keys, c[order].astype(np.float64)
+
+
+def test_binary_rescore_counts_match_numpy_bipartite():
+    """Oracle.rescore on 0/1 CSR inputs with A != B^T equals (A B)_ij."""
+    A = _uneven_binary(70, 50, 41)
+    B = (_rng(42).random((50, 90)) < 0.2).astype(np.int64)
+    B[:, 7] = 1       # a full column
+    o = Oracle(_csr_of(A), _csr_of(B), 0)
+    ii, jj = np.meshgrid(np.arange(70), np.arange(90), indexing="ij")
+    keys = (ii.ravel().astype(np.uint64) << np.uint64(32)) | jj.ravel().astype(np.uint64)
+    c = o.rescore(keys)
+    assert np.array_equal(c, (A @ B)[ii.ravel(), jj.ravel()].astype(np.float64))
+
+
+def test_binary_rescore_counts_match_numpy_gram_with_diagonal():
+    """Gram inputs (A = B^T, here a symmetric adjacency of uneven degrees):
+    every pair including i == j equals (A A^T)_ij = |N(i) ∩ N(j)|."""
+    D = _uneven_binary(60, 60, 43)
+    S = np.triu(D, 1)
+    S = S + S.T
+    M = _csr_of(S)
+    o = Oracle(M, M, 2)
+    ii, jj = np.meshgrid(np.arange(60), np.arange(60), indexing="ij")
+    up = jj >= ii
+    keys = (ii[up].astype(np.uint64) << np.uint64(32)) | jj[up].astype(np.uint64)
+    c = o.rescore(keys)
+    assert np.array_equal(c, (S @ S.T)[ii[up], jj[up]].astype(np.float64))
+    assert np.array_equal(c[ii[up] == jj[up]], S.sum(1).astype(np.float64))  # c_ii = deg
+
+
+def test_binary_bruteforce_matches_numpy_with_ties():
+    """or_bruteforce on 0/1 CSR inputs (bipartite, Gram, Gram without the
+    diagonal) equals numpy's top t of A B, ties broken by the smaller key;
+    counts of small integers tie often."""
+    A = _uneven_binary(50, 30, 44)
+    B = (_rng(45).random((30, 40)) < 0.3).astype(np.int64)
+    keys, c = Oracle(_csr_of(A), _csr_of(B), 0).bruteforce(60)
+    rk, rc = _ref_topt(A @ B, 60)
+    assert np.array_equal(keys, rk) and np.array_equal(c, rc)
+    assert len(np.unique(rc)) < len(rc)        # the case has ties
+    S = np.triu(_uneven_binary(45, 45, 46), 1)
+    S = S + S.T
+    M = _csr_of(S)
+    for flags, ex in ((2, False), (2 | 4, True)):
+        keys, c = Oracle(M, M, flags).bruteforce(80)
+        rk, rc = _ref_topt(S @ S, 80, gram=True, exclude_diag=ex)
+        assert np.array_equal(keys, rk) and np.array_equal(c, rc)
+
+
+def test_sparse_exact_matches_numpy_and_bruteforce():
+    """The row-wise sparse product (Sec. 4.3) gives numpy's top t over the
+    stored entries of C (pairs some k reaches), ties by key, and the brute
+    force's top t whenever t stored entries exist."""
+    A = _uneven_binary(50, 30, 47)
+    B = (_rng(48).random((30, 40)) < 0.3).astype(np.int64)
+    o = Oracle(_csr_of(A), _csr_of(B), 0)
+    C = A @ B
+    for t in (1, 37, 200):
+        keys, c = o.sparse_exact(t)
+        rk, rc = _ref_topt(C, t, stored=C != 0)
+        assert np.array_equal(keys, rk) and np.array_equal(c, rc)
+        bk, bc = o.bruteforce(t)
+        assert np.array_equal(keys, bk) and np.array_equal(c, bc)
+    S = np.triu(_uneven_binary(45, 45, 49), 1)
+    S = S + S.T
+    M = _csr_of(S)
+    for flags, ex in ((2, False), (2 | 4, True)):
+        o = Oracle(M, M, flags)
+        keys, c = o.sparse_exact(90)
+        rk, rc = _ref_topt(S @ S, 90, gram=True, exclude_diag=ex, stored=(S @ S) != 0)
+        assert np.array_equal(keys, rk) and np.array_equal(c, rc)
+    # Fewer stored entries than t: only the stored ones are returned.
+    E = np.zeros((6, 5), np.int64)
+    E[1, 2] = E[4, 0] = 1
+    F = np.zeros((5, 7), np.int64)
+    F[2, 3] = F[0, 3] = F[0, 6] = 1
+    keys, c = Oracle(_csr_of(E), _csr_of(F), 0).sparse_exact(10)
+    assert keys.tolist() == [(1 << 32) | 3, (4 << 32) | 3, (4 << 32) | 6]
+    assert c.tolist() == [1.0, 1.0, 1.0]
