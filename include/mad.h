@@ -251,6 +251,30 @@ mad_status mad_dense_topt(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B
                           uint32_t rescore, mad_pair* out_dev, uint32_t* n_out_host,
                           mad_stream stream);
 
+/* Exact comparator for 0/1 inputs (Sec. 4.3, the exact computation for
+ * comparison: C formed one sparse row at a time, its top entries kept).
+ * A (m x d) and B (d x n) are 0/1 CSR (MAD_BINARY; B = A^T for MAD_GRAM
+ * contexts, where pairs are unordered, j >= i; MAD_EXCLUDE_DIAG drops
+ * i == j).  Returns the min(t, #stored) largest c_ij = |{k : a_ik = b_kj =
+ * 1}| among the stored entries of C (c_ij >= 1), sorted by (c desc, i asc,
+ * j asc), with c as an exact integer in the double and x = 0: the same
+ * pairs and counts as a full sparse product for any input.
+ * Because c_ij <= min(nnz(a_i*), nnz(b_*j)), a pilot product of the ~2048
+ * rows and columns of largest degree gives a lower bound theta on the t-th
+ * largest count, and the main pass covers only rows and columns with at
+ * least theta entries, keeping counts >= theta (MAD_SPARSE_NO_BOUND: every
+ * row and column, the threshold filtering entries only).  Counts are
+ * accumulated in shared memory, one block per row of C.  t <= 524288.
+ * Uses the context's scratch (about 40 bytes per row and column plus 4 per
+ * entry of B, and 75 MB of candidate lists); the context needs no tables.
+ * Synchronises the stream.  MAD_ERR_UNSUPPORTED for other formats, and
+ * for inputs whose t-th count ties beyond the candidate list with counts
+ * of 65535 or more. */
+#define MAD_SPARSE_NO_BOUND 1u
+mad_status mad_sparse_topt(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, uint32_t t,
+                           uint32_t options, mad_pair* out_dev, uint32_t* n_out_host,
+                           mad_stream stream);
+
 /* ---- Batched queries (maximum |inner product| search) ----------------- *
  * Many small instances against one item matrix: query q is the instance
  * A = Q[q] (1 x d) with B = the items (d x n), sampled with its own budget

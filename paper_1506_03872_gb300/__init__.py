@@ -34,7 +34,7 @@ EXPORTS = (
     "mad_debug_draws_list", "mad_debug_set_hash_layout", "mad_export_x", "mad_export_table", "mad_rescore_noalloc",
     "mad_dense_topt", "mad_debug_dense_product", "mad_set_phase_events", "mad_mips_items",
     "mad_mips_plan", "mad_mips_run", "mad_budget_features", "mad_mlp_train", "mad_mlp_predict",
-    "mad_pipeline_plan", "mad_pipeline_run", "mad_pipeline_status",
+    "mad_pipeline_plan", "mad_pipeline_run", "mad_pipeline_status", "mad_sparse_topt",
 )
 MAD_BUDGET_FEATURES = 12
 MAD_MLP_HIDDEN = 64
@@ -113,6 +113,8 @@ def lib() -> ctypes.CDLL:
                                           P, u32, u32, P, ctypes.POINTER(u32), P]
         L.mad_dense_topt.argtypes = [P, ctypes.POINTER(mad_matrix), ctypes.POINTER(mad_matrix), u32,
                                      u32, P, ctypes.POINTER(u32), P]
+        L.mad_sparse_topt.argtypes = [P, ctypes.POINTER(mad_matrix), ctypes.POINTER(mad_matrix),
+                                      u32, u32, P, ctypes.POINTER(u32), P]
         L.mad_debug_dense_product.argtypes = [P, ctypes.POINTER(mad_matrix),
                                               ctypes.POINTER(mad_matrix), P, P]
         L.mad_debug_draws.argtypes = [P, u64, u64, u64, P, P, P, P, P, P]
@@ -283,6 +285,21 @@ def mad_dense_topt(ctx, A: mad_matrix, B: mad_matrix, t: int, rescore: int = 0, 
     n = ctypes.c_uint32(0)
     _check(lib().mad_dense_topt(ctx, ctypes.byref(A), ctypes.byref(B), t, rescore, _ptr(out),
                                 ctypes.byref(n), _stream(stream)), "mad_dense_topt")
+    return out, n.value
+
+
+SPARSE_NO_BOUND = 1
+
+
+def mad_sparse_topt(ctx, A: mad_matrix, B: mad_matrix, t: int, options: int = 0, out=None,
+                    stream=None):
+    """Exact top-t counts of a 0/1 product by the sparse comparator
+    (Sec. 4.3); options SPARSE_NO_BOUND processes every row and column."""
+    if out is None:
+        out = new_pairs(t)
+    n = ctypes.c_uint32(0)
+    _check(lib().mad_sparse_topt(ctx, ctypes.byref(A), ctypes.byref(B), t, options, _ptr(out),
+                                 ctypes.byref(n), _stream(stream)), "mad_sparse_topt")
     return out, n.value
 
 
