@@ -371,6 +371,28 @@ mad_status mad_rescore_noalloc(const mad_matrix* A, const mad_matrix* B, const m
                                uint32_t ncand, uint32_t t, mad_pair* out_dev,
                                uint32_t* n_out_host, mad_stream stream);
 
+/* ---- Memory-system probes (the paper has no counterpart) --------------- *
+ * The sampler's diamonds end in random 32-byte sectors of its tables and,
+ * for 0/1 inputs, random 64-bit atomics on its hash; these kernels measure
+ * those two rates on buffers of the caller's choosing (sized like the
+ * tables and the hash), so the sampler's throughput can be stated against
+ * them.  Both are asynchronous on `stream`; time them with events.
+ *
+ * mad_probe_gather: `count` 4-byte loads, each from a uniformly random
+ * 32-byte sector of table_dev (device, `bytes` a multiple of 32, 32-byte
+ * aligned), positions from a SplitMix64 hash of `seed` and the load index.
+ * sink_dev: 8 bytes of device memory the kernel may write (keeps the loads).
+ *
+ * mad_probe_atomics: `count` 64-bit atomics on uniformly random words of
+ * table_dev (device, `bytes` a multiple of 8, 8-byte aligned): mode 0 adds
+ * 1 (a reduction, no value returned), mode 1 compare-and-swaps against 0
+ * and uses the old value (a round trip, as a hash insert's key claim).
+ * The table's contents change.  MAD_ERR_ARG for bad sizes or modes. */
+mad_status mad_probe_gather(const void* table_dev, uint64_t bytes, uint64_t count, uint64_t seed,
+                            void* sink_dev, mad_stream stream);
+mad_status mad_probe_atomics(void* table_dev, uint64_t bytes, uint64_t count, uint32_t mode,
+                             uint64_t seed, void* sink_dev, mad_stream stream);
+
 /* Counters and table scalars (synchronises the device). */
 mad_status mad_stats(mad_ctx* ctx, mad_stats_t* out);
 

@@ -35,6 +35,7 @@ EXPORTS = (
     "mad_dense_topt", "mad_debug_dense_product", "mad_set_phase_events", "mad_mips_items",
     "mad_mips_plan", "mad_mips_run", "mad_budget_features", "mad_mlp_train", "mad_mlp_predict",
     "mad_pipeline_plan", "mad_pipeline_run", "mad_pipeline_status", "mad_sparse_topt",
+    "mad_probe_gather", "mad_probe_atomics",
 )
 MAD_BUDGET_FEATURES = 12
 MAD_MLP_HIDDEN = 64
@@ -115,6 +116,8 @@ def lib() -> ctypes.CDLL:
                                      u32, P, ctypes.POINTER(u32), P]
         L.mad_sparse_topt.argtypes = [P, ctypes.POINTER(mad_matrix), ctypes.POINTER(mad_matrix),
                                       u32, u32, P, ctypes.POINTER(u32), P]
+        L.mad_probe_gather.argtypes = [P, u64, u64, u64, P, P]
+        L.mad_probe_atomics.argtypes = [P, u64, u64, u32, u64, P, P]
         L.mad_debug_dense_product.argtypes = [P, ctypes.POINTER(mad_matrix),
                                               ctypes.POINTER(mad_matrix), P, P]
         L.mad_debug_draws.argtypes = [P, u64, u64, u64, P, P, P, P, P, P]
@@ -301,6 +304,23 @@ def mad_sparse_topt(ctx, A: mad_matrix, B: mad_matrix, t: int, options: int = 0,
     _check(lib().mad_sparse_topt(ctx, ctypes.byref(A), ctypes.byref(B), t, options, _ptr(out),
                                  ctypes.byref(n), _stream(stream)), "mad_sparse_topt")
     return out, n.value
+
+
+def mad_probe_gather(table, count: int, seed: int = 1, sink=None, stream=None) -> None:
+    """`count` random 32-byte-sector loads from the device tensor `table`
+    (asynchronous; time with events)."""
+    sink = table if sink is None else sink
+    _check(lib().mad_probe_gather(_ptr(table), table.numel() * table.element_size(), count, seed,
+                                  _ptr(sink), _stream(stream)), "mad_probe_gather")
+
+
+def mad_probe_atomics(table, count: int, mode: int = 0, seed: int = 1, sink=None,
+                      stream=None) -> None:
+    """`count` random 64-bit atomics on the device tensor `table`: mode 0
+    add, mode 1 compare-and-swap (asynchronous; time with events)."""
+    sink = table if sink is None else sink
+    _check(lib().mad_probe_atomics(_ptr(table), table.numel() * table.element_size(), count, mode,
+                                   seed, _ptr(sink), _stream(stream)), "mad_probe_atomics")
 
 
 def mad_mips_items(ctx, B: mad_matrix, s_max: int, stream=None) -> None:

@@ -50,7 +50,21 @@ def test_reference_arm_line_on_cpu():
     assert out.returncode == 0, out.stderr[-2000:]
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "diamonds/s"
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["config"]["workload"] == "dense_factors"
-    assert " 100000 of the " in line["cpu_baseline"]["sample"]
+    assert line["config"]["l2"] and line["config"]["parallelism"] == "single"
+    assert "200000 of the 200000 diamonds" in line["cpu_baseline"]["sample"]
+
+
+def test_all_core_oracle_merge_equals_one_core():
+    """The CPU baseline's all-cores leg: contiguous diamond ranges sampled by
+    one oracle each merge to the X of one oracle over the whole range."""
+    import bench
+    from paper_1506_03872_gb300.workloads import dense_factors
+    w = dense_factors(m=3000, n=800, s=60_000)
+    res = bench.cpu_baseline(w, 60_000, threads=3)
+    assert res["all_cores"]["merged_x_equals_one_core"] is True
+    assert res["cores"] == 3 and res["all_cores"]["diamonds"] == 60_000
+    assert res["one_core"]["diamonds_per_s"] > 0 and res["cpu_model"]
