@@ -254,6 +254,17 @@ __device__ __forceinline__ double pow2d(int e) {
 // Open-addressing hash for X: 64-bit keys (EMPTY_KEY = free), int64 values,
 // linear probing from a splitmix64-finalised slot.
 // ---------------------------------------------------------------------------
+// 32-bit finaliser of MurmurHash3 (Appleby): spreads a column index over a
+// home region (the row is fixed within a region, so the column suffices).
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;

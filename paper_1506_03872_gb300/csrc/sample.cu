@@ -19,6 +19,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "draw.cuh"
 #include "mad_device.cuh"
@@ -77,6 +78,37 @@ __device__ __forceinline__ void accumulate(const SampleParams& p, bool valid, co
   if (!valid) return;
   add_pair(p, dr.i, dr.j, dr.v, t);
   if (p.flags & MAD_SQUARE_SYM) add_pair(p, dr.k, dr.kp, dr.v, t);
+}
+
+// The same, reduced over the whole block first (one atomic per counter and
+// block: kernels with many short blocks would otherwise queue thousands of
+// atomics on the same counters).  Every thread of the block calls it.
+__device__ __forceinline__ void flush_tally_block(const SampleParams& p, Tally& t) {
+  __shared__ unsigned long long s_ins, s_cre;
+  __shared__ unsigned int s_flags;
+  if (threadIdx.x == 0) {
+    s_ins = 0;
+    s_cre = 0;
+    s_flags = 0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    t.inserted += __shfl_xor_sync(0xFFFFFFFFu, t.inserted, off);
+    t.created += __shfl_xor_sync(0xFFFFFFFFu, t.created, off);
+  }
+  const unsigned any_full = __ballot_sync(0xFFFFFFFFu, t.full);
+  if ((threadIdx.x & 31) == 0) {
+    if (t.inserted) atomicAdd(&s_ins, t.inserted);
+    if (t.created) atomicAdd(&s_cre, t.created);
+    if (any_full) atomicOr(&s_flags, 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_ins) atomicAdd(&p.sc->inserted, s_ins);
+    if (s_cre) atomicAdd(&p.sc->new_keys, s_cre);
+    if (s_flags) atomicOr(&p.sc->err, DERR_HASH_FULL);
+  }
 }
 
 __device__ __forceinline__ void flush_tally(const SampleParams& p, Tally& t) {
@@ -363,8 +395,9 @@ __device__ __forceinline__ int64_t group_first_row(const SampleParams& p, uint32
 // overflow table.  One warp per group.
 __global__ void __launch_bounds__(256)
 k_group_prep(const SampleParams p_, const unsigned int* __restrict__ base, uint32_t nbk,
-             int lg_group, uint32_t ngroups, uint64_t ov_slots, uint32_t* __restrict__ R,
-             unsigned char* __restrict__ heavy, uint32_t* __restrict__ qend) {
+             int lg_group, uint32_t ngroups, uint64_t ov_slots, int narrow,
+             uint32_t* __restrict__ R, unsigned char* __restrict__ heavy,
+             uint32_t* __restrict__ qend) {
   const SampleParams p = resolve(p_);
   const int lane = threadIdx.x & 31;
   const uint32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -387,7 +420,10 @@ k_group_prep(const SampleParams p_, const unsigned int* __restrict__ base, uint3
     const unsigned long long lo = __shfl_sync(0xFFFFFFFFu, slot, 0);
     const unsigned long long hi = __shfl_sync(0xFFFFFFFFu, slot, 1);
     const int64_t r0 = __shfl_sync(0xFFFFFFFFu, r, 0);
-    const bool big = hi - lo > (unsigned long long)kImageSlots;
+    const int64_t r1 = __shfl_sync(0xFFFFFFFFu, r, 1);
+    // Narrow image keys name the row by its offset in the group (8 bits).
+    const bool big = hi - lo > (unsigned long long)kImageSlots ||
+                     (narrow && r1 - r0 >= (int64_t)kRowCache);
     if (lane == 1) {
       // The sorted position where the diamonds the group builds end: its
       // own buckets, and those of its last row.
@@ -429,14 +465,24 @@ __device__ __forceinline__ int add_span_or_overflow(const SampleParams& p, unsig
 // The regions of group blockIdx.x (see above).  base[b] is the first sorted
 // position of bucket b (base[nbk] = the batch size); R, heavy and qend_g
 // come from k_group_prep.
+//
+// kNarrow: the image holds 32-bit keys, (row - first owned row) << 24 | j,
+// for n <= 2^24 and groups of fewer than kRowCache rows (k_group_prep makes
+// larger groups heavy): the key claim is a 32-bit compare-and-swap and one
+// 16-byte shared load reads four probe slots.  Otherwise the image holds
+// the 64-bit keys.  The stored X holds 64-bit keys either way.
+template <bool kNarrow>
 __global__ void __launch_bounds__(256)
 k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
           const long long* __restrict__ vals, const unsigned int* __restrict__ base,
           uint32_t nbk, int lg_group, uint32_t ngroups, uint64_t ov_slots,
           const uint32_t* __restrict__ R, const unsigned char* __restrict__ heavy,
           const uint32_t* __restrict__ qend_g) {
-  extern __shared__ __align__(16) unsigned long long img[];   // kImageSlots keys, then values
-  __shared__ unsigned long long s_hreg[kRowCache + 1];   // hreg of the owned rows
+  // kImageSlots keys (4 or 8 bytes), then kImageSlots 8-byte values.
+  extern __shared__ __align__(16) unsigned long long img[];
+  using IKey = typename std::conditional<kNarrow, uint32_t, unsigned long long>::type;
+  constexpr IKey kEmptyI = (IKey)~(IKey)0;
+  __shared__ uint32_t s_off[kRowCache + 1];   // owned rows' region offsets in the image
   const SampleParams p = resolve(p_);
   const unsigned long long ov0 = p.hreg[p.m];
   if (ov0 + ov_slots > p.hcap_alloc) return;   // reported by k_group_prep
@@ -454,15 +500,23 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
   const unsigned long long span = hv ? 0 : p.hreg[r1] - lo;
   const bool cached = r1 - r0 < (uint32_t)kRowCache;
   if (!hv && cached)
-    for (uint32_t x = threadIdx.x; x <= r1 - r0; x += blockDim.x) s_hreg[x] = p.hreg[r0 + x];
+    for (uint32_t x = threadIdx.x; x <= r1 - r0; x += blockDim.x)
+      s_off[x] = (uint32_t)(p.hreg[r0 + x] - lo);
+  const uint32_t span32 = (uint32_t)span;
   unsigned long long q = q0 + threadIdx.x;
   unsigned long long key = q < qend ? keys[q] : EMPTY_KEY;
   long long v = q < qend ? vals[q] : 0;
-  unsigned long long* ik = img;
-  unsigned long long* iv = img + kImageSlots;
-  for (unsigned long long x = 2ull * threadIdx.x; x < span; x += 2ull * blockDim.x) {
-    *(ulonglong2*)(ik + x) = make_ulonglong2(EMPTY_KEY, EMPTY_KEY);
+  IKey* ik = (IKey*)img;
+  unsigned long long* iv = (unsigned long long*)((char*)img + kImageSlots * sizeof(IKey));
+  for (uint32_t x = 4 * threadIdx.x; x < span32; x += 4 * blockDim.x) {
+    if (kNarrow) {
+      *(uint4*)(ik + x) = make_uint4(~0u, ~0u, ~0u, ~0u);
+    } else {
+      *(ulonglong2*)(ik + x) = make_ulonglong2(EMPTY_KEY, EMPTY_KEY);
+      *(ulonglong2*)(ik + x + 2) = make_ulonglong2(EMPTY_KEY, EMPTY_KEY);
+    }
     *(ulonglong2*)(iv + x) = make_ulonglong2(0, 0);
+    *(ulonglong2*)(iv + x + 2) = make_ulonglong2(0, 0);
   }
   __syncthreads();
   Tally t;
@@ -478,50 +532,58 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
     if (k == EMPTY_KEY) continue;
     const uint32_t i = (uint32_t)(k >> 32);
     const bool own = !hv && i >= r0 && i < r1;
-    unsigned long long rlo, rhi;
-    if (own && cached) {
-      rlo = s_hreg[i - r0];
-      rhi = s_hreg[i - r0 + 1];
-    } else {
-      rlo = __ldg(p.hreg + i);
-      rhi = __ldg(p.hreg + i + 1);
-    }
-    const unsigned long long home = rlo + (mix64(k) & (rhi - rlo - 1));
     int res;
     if (own) {
       // Linear probe of the image from the home slot, wrapping at its end
       // (the group's regions form one circular table), four slots per
       // step (two 16-byte shared loads; regions start on 4-slot groups).
       // A stale EMPTY is caught by the CAS; a key once set never changes.
-      unsigned long long x = home - lo;
+      // Image positions are 32-bit (the image holds kImageSlots slots).
+      uint32_t roff, rsz;
+      if (cached) {
+        roff = s_off[i - r0];
+        rsz = s_off[i - r0 + 1] - roff;
+      } else {
+        const unsigned long long a = __ldg(p.hreg + i);
+        roff = (uint32_t)(a - lo);
+        rsz = (uint32_t)(__ldg(p.hreg + i + 1) - a);
+      }
+      uint32_t x = roff + (fmix32((uint32_t)k) & (rsz - 1));
+      const IKey kk = kNarrow ? (IKey)(((i - r0) << 24) | (uint32_t)k) : (IKey)k;
       res = 0;
-      for (unsigned long long probes = 0; probes < span;) {
-        const unsigned long long gx = x & ~3ull;
-        const ulonglong2 ka = *(const ulonglong2*)(ik + gx);
-        const ulonglong2 kb = *(const ulonglong2*)(ik + gx + 2);
-        const unsigned long long k4[4] = {ka.x, ka.y, kb.x, kb.y};
-        const uint32_t start = (uint32_t)(x - gx);
+      for (uint32_t probes = 0; probes < span32;) {
+        const uint32_t gx = x & ~3u;
+        IKey k4[4];
+        if (kNarrow) {
+          const uint4 ka = *(const uint4*)(ik + gx);
+          k4[0] = (IKey)ka.x; k4[1] = (IKey)ka.y; k4[2] = (IKey)ka.z; k4[3] = (IKey)ka.w;
+        } else {
+          const ulonglong2 ka = *(const ulonglong2*)(ik + gx);
+          const ulonglong2 kb = *(const ulonglong2*)(ik + gx + 2);
+          k4[0] = (IKey)ka.x; k4[1] = (IKey)ka.y; k4[2] = (IKey)kb.x; k4[3] = (IKey)kb.y;
+        }
+        const uint32_t start = x - gx;
         uint32_t pick = 4;
 #pragma unroll
         for (int u = 3; u >= 0; --u)
-          pick = ((uint32_t)u >= start && (k4[u] == k || k4[u] == EMPTY_KEY)) ? (uint32_t)u : pick;
+          pick = ((uint32_t)u >= start && (k4[u] == kk || k4[u] == kEmptyI)) ? (uint32_t)u : pick;
         if (pick == 4) {
           probes += 4 - start;
-          x = gx + 4 < span ? gx + 4 : 0;
+          x = gx + 4 < span32 ? gx + 4 : 0;
           continue;
         }
         probes += pick - start + 1;
-        unsigned long long cur = k4[0];
+        IKey cur = k4[0];
 #pragma unroll
         for (int u = 1; u < 4; ++u) cur = (uint32_t)u == pick ? k4[u] : cur;
-        const unsigned long long slot = gx + pick;
-        const unsigned long long prev = cur == k ? k : atomicCAS(ik + slot, EMPTY_KEY, k);
-        if (prev == EMPTY_KEY || prev == k) {
+        const uint32_t slot = gx + pick;
+        const IKey prev = cur == kk ? kk : atomicCAS(ik + slot, kEmptyI, kk);
+        if (prev == kEmptyI || prev == kk) {
           atomicAdd(iv + slot, (unsigned long long)w);
-          res = prev == EMPTY_KEY ? 2 : 1;
+          res = prev == kEmptyI ? 2 : 1;
           break;
         }
-        x = slot + 1 < span ? slot + 1 : 0;   // taken by another key: go on after it
+        x = slot + 1 < span32 ? slot + 1 : 0;   // taken by another key: go on after it
       }
       if (res == 0) res = add_span_or_overflow(p, 0, 0, 0, ov0, ov_slots, k, w);
     } else {
@@ -530,6 +592,8 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
       unsigned long long og = ex >> gs;
       og = og < ngroups - 1 ? og : ngroups - 1;
       if (!heavy[og]) continue;   // its owner builds it
+      const unsigned long long rlo = __ldg(p.hreg + i), rhi = __ldg(p.hreg + i + 1);
+      const unsigned long long home = rlo + (fmix32((uint32_t)k) & (rhi - rlo - 1));
       res = add_span_or_overflow(p, p.hreg[R[og]], p.hreg[R[og + 1]], home, ov0, ov_slots, k, w);
     }
     ++t.inserted;
@@ -537,12 +601,24 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
     if (res == 2) ++t.created;
   }
   __syncthreads();
-  // The image, 16 bytes per store (regions start on 4-slot groups).
-  for (unsigned long long x = 2ull * threadIdx.x; x < span; x += 2ull * blockDim.x) {
-    *(ulonglong2*)(p.hkeys + lo + x) = make_ulonglong2(ik[x], ik[x + 1]);
+  // The image, 16 bytes per store (regions start on 4-slot groups), keys
+  // widened back to (i << 32) | j.
+  for (uint32_t x = 2 * threadIdx.x; x < span32; x += 2 * blockDim.x) {
+    unsigned long long k0, k1;
+    if (kNarrow) {
+      const uint32_t a = ik[x], b = ik[x + 1];
+      k0 = a == ~0u ? EMPTY_KEY
+                    : ((unsigned long long)(r0 + (a >> 24)) << 32) | (a & 0xFFFFFFu);
+      k1 = b == ~0u ? EMPTY_KEY
+                    : ((unsigned long long)(r0 + (b >> 24)) << 32) | (b & 0xFFFFFFu);
+    } else {
+      k0 = (unsigned long long)ik[x];
+      k1 = (unsigned long long)ik[x + 1];
+    }
+    *(ulonglong2*)(p.hkeys + lo + x) = make_ulonglong2(k0, k1);
     *(longlong2*)(p.hvals + lo + x) = make_longlong2((long long)iv[x], (long long)iv[x + 1]);
   }
-  flush_tally(p, t);
+  flush_tally_block(p, t);
 }
 
 // Diagnostic twin of k_sample: writes each diamond's draws instead of
@@ -793,10 +869,16 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
   // An empty X filled by one batch, keys owned by their drawn row: the
   // regions are built whole (k_build_x); otherwise k_insert adds to X.
   const bool build_x = fresh_x && x_builder_applies(ctx, s);
-  const size_t image_smem = 2 * (size_t)kImageSlots * sizeof(unsigned long long);
+  // Narrow image keys when every column index fits in 24 bits.
+  const bool narrow = ctx->n <= (1ll << 24);
+  const size_t image_smem =
+      (size_t)kImageSlots * ((narrow ? sizeof(uint32_t) : sizeof(unsigned long long)) +
+                             sizeof(unsigned long long));
   static bool image_attr = false;
   if (build_x && !image_attr) {
-    cudaFuncSetAttribute(k_build_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)image_smem);
+    const int wide_smem = (int)(2 * (size_t)kImageSlots * sizeof(unsigned long long));
+    cudaFuncSetAttribute(k_build_x<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, wide_smem);
+    cudaFuncSetAttribute(k_build_x<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, wide_smem);
     image_attr = true;
   }
   mad_status rs = ensure_scratch(ctx, sample_scratch_bytes(ctx, s), st);
@@ -832,9 +914,16 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
       const int lg = build_group_log2(nbk, ctx->s_max);
       const uint32_t ngroups = (uint32_t)(nbk >> lg);
       k_group_prep<<<(ngroups + 7) / 8, 256, 0, st>>>(p, w.base, (uint32_t)nbk, lg, ngroups,
-                                                      ctx->hov, w.R, w.heavy, w.qend);
-      k_build_x<<<ngroups, 256, image_smem, st>>>(p, w.keys, w.vals, w.base, (uint32_t)nbk, lg,
-                                                  ngroups, ctx->hov, w.R, w.heavy, w.qend);
+                                                      ctx->hov, narrow ? 1 : 0, w.R, w.heavy,
+                                                      w.qend);
+      if (narrow)
+        k_build_x<true><<<ngroups, 256, image_smem, st>>>(p, w.keys, w.vals, w.base,
+                                                          (uint32_t)nbk, lg, ngroups, ctx->hov,
+                                                          w.R, w.heavy, w.qend);
+      else
+        k_build_x<false><<<ngroups, 256, image_smem, st>>>(p, w.keys, w.vals, w.base,
+                                                           (uint32_t)nbk, lg, ngroups, ctx->hov,
+                                                           w.R, w.heavy, w.qend);
       count_launch(ctx, 2);
     } else {
       k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, w.keys, w.vals, n);

@@ -202,7 +202,7 @@ def _export_sorted(mad, ctx, cap):
     return keys[order], vals[order], n
 
 
-@pytest.mark.parametrize("variant", ["plain", "heavy_rows", "zero_rows", "nonneg"])
+@pytest.mark.parametrize("variant", ["plain", "heavy_rows", "zero_rows", "nonneg", "wide_columns"])
 def test_pass_x_matches_oracle(variant):
     """X after the fused pass, every key and sum, against the oracle: the
     pass builds the home regions whole (and an overflow table), so this
@@ -213,6 +213,9 @@ def test_pass_x_matches_oracle(variant):
     import paper_1506_03872_gb300 as mad
     A, B = _inputs(80)
     flags = 0
+    if variant == "wide_columns":
+        # More than 2^24 columns: the builder keeps 64-bit keys in its image.
+        A, B = _inputs(81, m=600, d=3, n=(1 << 24) + 4099)
     if variant == "heavy_rows":
         A[[5, 900, 901, 2050]] *= 8.0
     elif variant == "zero_rows":
