@@ -41,6 +41,8 @@ namespace mad {
 namespace {
 
 constexpr int BM = 128;             // rows of A per tile (TMEM lanes)
+constexpr int RB = 1;               // row blocks per tile
+constexpr int TM = RB * BM;         // rows of C per tile
 constexpr int BN = 256;             // columns of C per tile (TMEM columns)
 constexpr int KATOM = 64;           // BF16 elements per 128-byte swizzle row
 constexpr int MAXKP = 128;          // padded K handled by this kernel
@@ -52,7 +54,8 @@ constexpr int kEpi = 256;           // epilogue threads
 constexpr long long kPreStride = 16; // threshold pre-pass visits every 16th tile
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s: a wait this long is a fault
 
-constexpr int A_BYTES = BM * MAXKP * 2;                 // 32 KB
+constexpr int A_RB_BYTES = BM * MAXKP * 2;              // 32 KB per row block
+constexpr int A_BYTES = RB * A_RB_BYTES;                // 32 KB
 constexpr int B_STAGE_BYTES = BN * MAXKP * 2;           // 64 KB
 constexpr int SMEM_A = 0;
 constexpr int SMEM_B = SMEM_A + A_BYTES;
@@ -64,6 +67,7 @@ constexpr int SMEM_ALLOC = SMEM_TOTAL + 1024;                      // alignment 
 struct GemmArgs {
   int64_t m, n;
   int kp;                            // padded K (64 or 128)
+  int ksteps;                        // MMA K steps of 16 that reach column d
   int64_t tiles_m, tiles_n;
   int kkeep;                         // entries kept per CTA at compaction
   unsigned int* g_theta;             // shared threshold (FP32 bits)
@@ -279,18 +283,40 @@ __device__ unsigned epi_compact(float* cv, unsigned long long* ck, unsigned n, f
   return out;
 }
 
-// Largest |value| of 64 FP32 bit patterns, with eight independent running
-// maxima so the dependent chain is 8 deep instead of 64.
+// max(|a|, |b|, |c|) in one instruction (three-input max of sm_100 and later).
+__device__ __forceinline__ float max3_abs(float a, float b, float c) {
+  float r;
+  asm("max.abs.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Largest |value| of 64 FP32 bit patterns: eight independent chains of
+// three-input maxima (four instructions each), then a three-level fold.
 __device__ __forceinline__ float abs_max64(const uint32_t* r) {
   float m[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) m[k] = fabsf(__uint_as_float(r[k]));
-#pragma unroll
-  for (int q = 8; q < 64; q += 8) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) m[k] = fmaxf(m[k], fabsf(__uint_as_float(r[q + k])));
+  for (int k = 0; k < 8; ++k) {
+    m[k] = max3_abs(__uint_as_float(r[k]), __uint_as_float(r[k + 8]), __uint_as_float(r[k + 16]));
+    m[k] = max3_abs(m[k], __uint_as_float(r[k + 24]), __uint_as_float(r[k + 32]));
+    m[k] = max3_abs(m[k], __uint_as_float(r[k + 40]), __uint_as_float(r[k + 48]));
+    m[k] = fmaxf(m[k], fabsf(__uint_as_float(r[k + 56])));
   }
-  return fmaxf(fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3])), fmaxf(fmaxf(m[4], m[5]), fmaxf(m[6], m[7])));
+  return max3_abs(max3_abs(m[0], m[1], m[2]), max3_abs(m[3], m[4], m[5]), fmaxf(m[6], m[7]));
+}
+
+// Barrier of the epilogue threads that also returns whether any of them
+// passed p = true (one barrier for the per-tile overflow and abort checks).
+__device__ __forceinline__ bool epi_any(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, 256, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)p)
+      : "memory");
+  return r != 0;
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -314,7 +340,9 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const long long t_begin = total_tiles * blockIdx.x / gridDim.x;
   const long long t_end = total_tiles * (blockIdx.x + 1) / gridDim.x;
   const int katoms = args.kp / KATOM;
-  const int ksteps = args.kp / 16;
+  // Columns d..kp-1 are zeros: the MMAs stop at the first 16-column step
+  // past d (7 steps instead of 8 for d = 100).
+  const int ksteps = args.ksteps;
 
   if (threadIdx.x == 0) {
     mbar_init(&sh->a_full, 1);
@@ -356,9 +384,11 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const long long rb = t / args.tiles_n, cb = t % args.tiles_n;
         if (rb != prev_rb) {
           if (panel > 0 && !mbar_wait(&sh->a_empty, (uint32_t)((panel - 1) & 1), abort_flag)) break;
-          mbar_expect_tx(&sh->a_full, (uint32_t)(BM * args.kp * 2));
-          for (int ka = 0; ka < katoms; ++ka)
-            tma_load_2d(sA + ka * (BM * 128), &tmA, &sh->a_full, ka * KATOM, (int)(rb * BM));
+          mbar_expect_tx(&sh->a_full, (uint32_t)(TM * args.kp * 2));
+          for (int r = 0; r < RB; ++r)
+            for (int ka = 0; ka < katoms; ++ka)
+              tma_load_2d(sA + r * A_RB_BYTES + ka * (BM * 128), &tmA, &sh->a_full, ka * KATOM,
+                          (int)(rb * TM + r * BM));
           prev_rb = rb;
           ++panel;
         }
@@ -389,13 +419,17 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         if (it >= 2 && !mbar_wait(&sh->acc_empty[buf], (uint32_t)(((it >> 1) - 1) & 1), abort_flag))
           break;
         fence_after_sync();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * (RB * BN));
         const unsigned char* tileB = sB + s * B_STAGE_BYTES;
         for (int kk = 0; kk < ksteps; ++kk) {
           const int ka = kk >> 2, ko = (kk & 3) * 32;  // atom and byte offset inside it
-          const uint64_t ad = desc_sw128(sA + ka * (BM * 128)) + (uint64_t)(ko >> 4);
           const uint64_t bd = desc_sw128(tileB + ka * (BN * 128)) + (uint64_t)(ko >> 4);
-          mma_bf16(d_tmem, ad, bd, kk > 0 ? 1u : 0u);
+#pragma unroll
+          for (int r = 0; r < RB; ++r) {
+            const uint64_t ad =
+                desc_sw128(sA + r * A_RB_BYTES + ka * (BM * 128)) + (uint64_t)(ko >> 4);
+            mma_bf16(d_tmem + (uint32_t)(r * BN), ad, bd, kk > 0 ? 1u : 0u);
+          }
         }
         mma_commit(&sh->b_empty[s]);
         mma_commit(&sh->acc_full[buf]);
@@ -409,12 +443,17 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int quarter = warp & 3;             // TMEM lane quarter of this warp
     const int half = (warp - 2) >> 2;         // column half of the tile
     const int row_in_tile = quarter * 32 + lane;
+    const bool filter = !args.dense_out && !args.max_out;
+    // The shared threshold, loaded one tile ahead so its latency never
+    // stalls a tile (any earlier value is a valid, lower bound).
+    float g_theta_next = __uint_as_float(*((volatile unsigned int*)args.g_theta));
     for (long long v = t_begin; v < t_end; ++v) {
       const long long it = v - t_begin, t = v * stride;
       const long long rb = t / args.tiles_n, cb = t % args.tiles_n;
       const int buf = (int)(it & 1);
-      // Compact first when the buffer is past its trigger.
-      if (!args.dense_out && !args.max_out && sh->count > CAND_TRIGGER) {
+      // Compact first when the buffer is past its trigger (sh->count is
+      // uniform: it was last changed before the previous tile's barrier).
+      if (filter && sh->count > CAND_TRIGGER) {
         const float th = epi_kth_largest(cv, sh->count, (unsigned)args.kkeep, sh, et);
         epi_compact(cv, ck, sh->count, th, sh, et);
         if (et == 0) {
@@ -423,19 +462,21 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
         epi_sync();
       }
-      // The shared threshold is read before the wait so its latency overlaps it
-      // (any earlier value is a valid, lower bound).
-      const float g_theta0 = __uint_as_float(*((volatile unsigned int*)args.g_theta));
-      // The epilogue warps share named barriers below, so they leave together.
+      const float g_theta0 = g_theta_next;
+      if (filter) g_theta_next = __uint_as_float(*((volatile unsigned int*)args.g_theta));
       const bool ok = mbar_wait(&sh->acc_full[buf], (uint32_t)((it >> 1) & 1), abort_flag);
-      if (!ok) atomicOr(&sh->epi_abort, 1);
-      epi_sync();
-      if (*((volatile int*)&sh->epi_abort)) break;
-      fence_after_sync();
-      const int64_t row = rb * BM + row_in_tile;
+      const int64_t row = rb * TM + row_in_tile;
       const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) +
-                             (uint32_t)(buf * BN + half * (BN / 2));
+                             (uint32_t)(buf * (RB * BN) + half * (BN / 2));
       const int64_t col_half = cb * BN + half * (BN / 2);
+      if (!filter) {
+        // The diagnostic and pre-pass epilogues share named barriers, so
+        // they leave together.
+        if (!ok) atomicOr(&sh->epi_abort, 1);
+        epi_sync();
+        if (*((volatile int*)&sh->epi_abort)) break;
+        fence_after_sync();
+      }
       if (args.dense_out) {
 #pragma unroll 1
         for (int ch = 0; ch < 2; ++ch) {
@@ -471,15 +512,19 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
         args.max_out[v * kEpi + et] = row < args.m ? hm : 0.0f;
       } else {
+        if (!ok) sh->epi_abort = 1;   // read by everyone after the barrier below
+        fence_after_sync();
         unsigned tile_start = sh->count;
+        bool stop = false;
         for (int round = 0; round < 8; ++round) {
           const float theta =
               fmaxf(sh->theta, round == 0 ? g_theta0
                                           : __uint_as_float(*((volatile unsigned int*)args.g_theta)));
+          bool over = false;
           // Two chunks of 64 columns, reloaded from TMEM on every pass (the
           // accumulator stays put until this tile's buffer is released).
 #pragma unroll 1
-          for (int ch = 0; ch < 2; ++ch) {
+          for (int ch = 0; ch < 2 && ok; ++ch) {
             uint32_t r[64];
             tmem_ld32_nowait(taddr + (uint32_t)(ch * 64), r);
             tmem_ld32_nowait(taddr + (uint32_t)(ch * 64 + 32), r + 32);
@@ -508,7 +553,10 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             if (cnt) {
               // Reserve this thread's slots with one atomic, then write them.
               unsigned pos = atomicAdd(&sh->count, cnt);
-              if (pos + cnt > CAND_CAP) sh->overflow = 1;
+              if (pos + cnt > CAND_CAP) {
+                sh->overflow = 1;
+                over = true;
+              }
 #pragma unroll
               for (int q = 0; q < 64; ++q) {
                 const float a = fabsf(__uint_as_float(r[q]));
@@ -522,8 +570,12 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
               }
             }
           }
-          epi_sync();
-          if (!sh->overflow) break;
+          // One barrier: did any thread overflow the buffer or abort?
+          if (!epi_any(over || !ok)) break;
+          if (*((volatile int*)&sh->epi_abort)) {
+            stop = true;
+            break;
+          }
           // Overflow: the buffer holds CAND_CAP real entries, so its kkeep-th
           // largest is a valid lower bound.  Drop this tile's entries, tighten
           // the earlier ones and rescan the tile above it.
@@ -538,6 +590,7 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           tile_start = sh->count;  // the earlier tiles' survivors; the rescan appends after them
           if (round == 7 && et == 0) atomicOr(args.g_err, 2u);  // pathological ties
         }
+        if (stop) break;
       }
       fence_before_sync();
       __syncwarp();
@@ -757,7 +810,7 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   const int64_t m = A->rows, d = A->cols, n = B->cols;
   if (d > MAXKP) return MAD_ERR_UNSUPPORTED;
   const int kp = d <= 64 ? 64 : 128;
-  const int64_t tiles_m = (m + BM - 1) / BM, tiles_n = (n + BN - 1) / BN;
+  const int64_t tiles_m = (m + TM - 1) / TM, tiles_n = (n + BN - 1) / BN;
   const int grid = (int)std::min<int64_t>(sm_count(), tiles_m * tiles_n);
   const uint32_t kkeep = dense_out ? 1u : std::max(t, rescore);
   if (!dense_out && kkeep > CAND_TRIGGER) return MAD_ERR_UNSUPPORTED;
@@ -809,6 +862,7 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   ga.m = m;
   ga.n = n;
   ga.kp = kp;
+  ga.ksteps = (int)((d + 15) / 16);
   ga.tiles_m = tiles_m;
   ga.tiles_n = tiles_n;
   ga.kkeep = (int)kkeep;

@@ -353,6 +353,25 @@ k_insert(const SampleParams p_, const unsigned long long* __restrict__ keys,
   flush_tally(p, t);
 }
 
+// (key, value) pairs added to X as k_insert adds drawn diamonds: partial X
+// of other diamond ranges merged into this context's X (sharded runs).
+// Counts the keys it creates, not diamonds.
+__global__ void __launch_bounds__(256)
+k_accumulate(const SampleParams p_, const unsigned long long* __restrict__ keys,
+             const long long* __restrict__ vals, unsigned long long n) {
+  const SampleParams p = resolve(p_);
+  Tally t;
+  for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long key = keys[q];
+    if (key == EMPTY_KEY) continue;
+    const int res = hash_add(p, key, vals[q]);
+    if (res == 0) t.full = true;
+    if (res == 2) ++t.created;
+  }
+  flush_tally(p, t);
+}
+
 // ---- X from empty, one group of rows per block -----------------------------
 // When a single sorted batch of diamonds fills an empty X (the fused pass),
 // the home regions are written whole instead of cleared and then updated
@@ -579,7 +598,13 @@ k_build_x(const SampleParams p_, const unsigned long long* __restrict__ keys,
         const uint32_t slot = gx + pick;
         const IKey prev = cur == kk ? kk : atomicCAS(ik + slot, kEmptyI, kk);
         if (prev == kEmptyI || prev == kk) {
-          atomicAdd(iv + slot, (unsigned long long)w);
+          // The 64-bit sum as two 32-bit shared atomics: the low word's own
+          // carry goes into the high word, so the total is the exact sum.
+          unsigned int* h2 = (unsigned int*)(iv + slot);
+          const unsigned int wlo = (unsigned int)w;
+          const unsigned int whi = (unsigned int)((unsigned long long)w >> 32);
+          const unsigned int olo = atomicAdd(h2, wlo);
+          atomicAdd(h2 + 1, whi + (olo + wlo < olo ? 1u : 0u));
           res = prev == kEmptyI ? 2 : 1;
           break;
         }
@@ -931,6 +956,16 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
     }
     phase_event(ctx, 3, st);
   }
+  return cuda_status(cudaGetLastError());
+}
+
+mad_status accumulate_pairs(mad_ctx* ctx, const uint64_t* keys, const int64_t* vals, uint64_t n,
+                            cudaStream_t st) {
+  if (n == 0) return MAD_OK;
+  const SampleParams p = make_params(ctx);
+  k_accumulate<<<grid_of(n, full_grid<k_accumulate>()), 256, 0, st>>>(
+      p, (const unsigned long long*)keys, (const long long*)vals, n);
+  count_launch(ctx);
   return cuda_status(cudaGetLastError());
 }
 
