@@ -361,11 +361,14 @@ mad_status mad_debug_dense_product(mad_ctx* ctx, const mad_matrix* A, const mad_
  * Limit: ncand <= MAD_NOALLOC_MAX_CANDIDATES; larger requests return
  * MAD_ERR_UNSUPPORTED.  The working memory is one fixed static device array
  * (about 1.8 MB) that each GPU loading the library keeps until the process
- * exits.  The first call on a device looks up that array's device address;
- * make that first call before any stream capture.  All calls share the
- * array and each clears what must start at zero, so calls that overlap on
- * the GPU (other streams or host threads) race: serialise them.  A
- * candidate outside A or B returns MAD_ERR_ARG.  Synchronises the stream. */
+ * exits.  The first call on a device looks up that array's device address
+ * and keeps it (set-up once per device; make that first call before any
+ * stream capture on the device; a device reset after it is not supported).
+ * All calls share the array and each clears what must start at zero, so
+ * calls that overlap on the GPU (other streams or host threads) race:
+ * serialise them.  A candidate outside A or B returns MAD_ERR_ARG, and the
+ * next call starts from a cleared status.  Every call copies its status
+ * word to the host and synchronises the stream. */
 #define MAD_NOALLOC_MAX_CANDIDATES 16384u
 mad_status mad_rescore_noalloc(const mad_matrix* A, const mad_matrix* B, const mad_pair* cand_dev,
                                uint32_t ncand, uint32_t t, mad_pair* out_dev,
@@ -393,7 +396,44 @@ mad_status mad_probe_gather(const void* table_dev, uint64_t bytes, uint64_t coun
 mad_status mad_probe_atomics(void* table_dev, uint64_t bytes, uint64_t count, uint32_t mode,
                              uint64_t seed, void* sink_dev, mad_stream stream);
 
-/* Counters and table scalars (synchronises the device). */
+/* ---- Sharded runs (one rank per GPU) ----------------------------------- *
+ * Diamonds are independent and counter-indexed (Alg. 2 with the Philox
+ * counter of the diamond index), so a run of s diamonds splits into
+ * contiguous diamond ranges, one per rank (mad_sample with first_diamond),
+ * over replicated tables.  X is an exact integer sum, so the partial X of
+ * the ranges summed by key equal the X of one run; each key is summed by
+ * one owner rank, owners select their top t' (mad_topk), and the union of
+ * the owners' candidates holds the global Omega_t' (Alg. 3).  These entry
+ * points are the compute steps of that exchange; the collectives belong to
+ * the caller (paper_1506_03872_gb300/shard.py uses torch.distributed).
+ *
+ * mad_export_x_by_owner: X's occupied keys and values grouped by owner
+ * rank, owner = a SplitMix64 mix of the key modulo `world` (1..65536):
+ * owner o's entries are keys_dev/vals_dev[offsets_host[o] .. offsets_host
+ * [o + 1]) (device arrays of cap entries; offsets_host: world + 1 host
+ * entries).  When the total offsets_host[world] exceeds cap nothing is
+ * written (call again with a larger buffer).  Synchronises.
+ *
+ * mad_accumulate: adds n (key, value) pairs (device arrays) to X, as
+ * sampling adds diamonds: X of the keys this rank owns, merged from every
+ * rank's partials after mad_reset_hash.  Keys must belong to the
+ * context's shape (row < m, column < n, unordered under MAD_GRAM); the
+ * hash must hold them (MAD_ERR_HASH_FULL from the next mad_topk otherwise).
+ * Asynchronous.
+ *
+ * mad_select_pairs: the min(K, #{x > 0}) pairs of pairs_dev (n, device)
+ * with the largest x, ties broken by smaller (i, j), sorted by (x desc, i
+ * asc, j asc) and copied whole to out_dev (K pairs, device): the global
+ * Omega_t' from the gathered candidates.  Synchronises. */
+mad_status mad_export_x_by_owner(mad_ctx* ctx, uint32_t world, uint64_t* keys_dev,
+                                 int64_t* vals_dev, uint64_t cap, uint64_t* offsets_host,
+                                 mad_stream stream);
+mad_status mad_accumulate(mad_ctx* ctx, const uint64_t* keys_dev, const int64_t* vals_dev,
+                          uint64_t n, mad_stream stream);
+mad_status mad_select_pairs(mad_ctx* ctx, const mad_pair* pairs_dev, uint64_t n, uint32_t K,
+                            mad_pair* out_dev, uint32_t* n_out_host, mad_stream stream);
+
+/* Counters and table scalars (synchronises the device). *//* Counters and table scalars (synchronises the device). */
 mad_status mad_stats(mad_ctx* ctx, mad_stats_t* out);
 
 /* ---- Diagnostics (used by the parity tests; not on the hot path) ------- */

@@ -37,7 +37,9 @@ std::mutex g_addr_mutex;
 void* g_addr[kMaxDevices] = {};
 
 // Device address of the static array on the current device (set up on the
-// first call per device).
+// first call per device and kept: the address stays valid for the life of
+// the CUDA context, so a device reset after the first call is not
+// supported).
 mad_status scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -88,3 +88,48 @@ def test_noalloc_rejects_more_candidates_than_its_array_holds():
         assert e.value.status == mad.MAD_ERR_UNSUPPORTED
     finally:
         c.close()
+
+
+def test_noalloc_bad_candidate_then_valid_call():
+    """A candidate outside A (i >= m) is refused with MAD_ERR_ARG; the error
+    word lives in the shared array, and the next valid call must start from
+    a cleared status and match mad_rescore."""
+    import paper_1506_03872_gb300 as mad
+    s = 200_000
+    c = Case("plain_small", s_max=s)
+    try:
+        cand, nc = _candidates(c, s, 23, 500)
+        bad = mad.encode_pairs(np.array([3, c.m + 5]), np.array([4, 1]))
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_rescore_noalloc(c.Am, c.Bm, bad, 2, 2)
+        assert e.value.status == mad.MAD_ERR_ARG
+        got, ng = mad.mad_rescore_noalloc(c.Am, c.Bm, cand, nc, 20)
+        ref, nr = mad.mad_rescore(c.ctx.ctx, cand, nc, 20)
+        assert ng == nr == 20
+        assert np.array_equal(got[:ng].cpu().numpy(), ref[:nr].cpu().numpy())
+    finally:
+        c.close()
+
+
+def test_noalloc_allocates_no_device_memory():
+    """After a warm-up call, a call leaves the device's free memory and the
+    caching allocator's reserved bytes unchanged (the output buffer is
+    allocated by the caller beforehand)."""
+    import paper_1506_03872_gb300 as mad
+    s = 200_000
+    c = Case("dense_ragged_f32", s_max=s)
+    try:
+        cand, nc = _candidates(c, s, 24, 3000)
+        out = mad.new_pairs(50)
+        mad.mad_rescore_noalloc(c.Am, c.Bm, cand, nc, 50, out=out)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        reserved0 = torch.cuda.memory_reserved()
+        _, ng = mad.mad_rescore_noalloc(c.Am, c.Bm, cand, nc, 50, out=out)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert ng == 50
+        assert free1 == free0
+        assert torch.cuda.memory_reserved() == reserved0
+    finally:
+        c.close()
