@@ -35,7 +35,8 @@ EXPORTS = (
     "mad_dense_topt", "mad_debug_dense_product", "mad_set_phase_events", "mad_mips_items",
     "mad_mips_plan", "mad_mips_run", "mad_budget_features", "mad_mlp_train", "mad_mlp_predict",
     "mad_pipeline_plan", "mad_pipeline_run", "mad_pipeline_status", "mad_sparse_topt",
-    "mad_probe_gather", "mad_probe_atomics",
+    "mad_probe_gather", "mad_probe_atomics", "mad_export_x_by_owner", "mad_accumulate",
+    "mad_select_pairs",
 )
 MAD_BUDGET_FEATURES = 12
 MAD_MLP_HIDDEN = 64
@@ -116,6 +117,9 @@ def lib() -> ctypes.CDLL:
                                      u32, P, ctypes.POINTER(u32), P]
         L.mad_sparse_topt.argtypes = [P, ctypes.POINTER(mad_matrix), ctypes.POINTER(mad_matrix),
                                       u32, u32, P, ctypes.POINTER(u32), P]
+        L.mad_export_x_by_owner.argtypes = [P, u32, P, P, u64, P, P]
+        L.mad_accumulate.argtypes = [P, P, P, u64, P]
+        L.mad_select_pairs.argtypes = [P, P, u64, u32, P, ctypes.POINTER(u32), P]
         L.mad_probe_gather.argtypes = [P, u64, u64, u64, P, P]
         L.mad_probe_atomics.argtypes = [P, u64, u64, u32, u64, P, P]
         L.mad_debug_dense_product.argtypes = [P, ctypes.POINTER(mad_matrix),
@@ -304,6 +308,40 @@ def mad_sparse_topt(ctx, A: mad_matrix, B: mad_matrix, t: int, options: int = 0,
     _check(lib().mad_sparse_topt(ctx, ctypes.byref(A), ctypes.byref(B), t, options, _ptr(out),
                                  ctypes.byref(n), _stream(stream)), "mad_sparse_topt")
     return out, n.value
+
+
+def mad_export_x_by_owner(ctx, world: int, cap: int, stream=None):
+    """X's keys and values grouped by owner rank: (keys, vals, offsets) with
+    owner o's entries at [offsets[o], offsets[o + 1]) (device int64 tensors;
+    keys are the uint64 keys bit for bit)."""
+    import numpy as np
+    import torch
+    while True:
+        keys = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
+        vals = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
+        off = np.zeros(world + 1, dtype=np.uint64)
+        _check(lib().mad_export_x_by_owner(ctx, world, _ptr(keys), _ptr(vals), cap,
+                                           off.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+               "mad_export_x_by_owner")
+        if int(off[world]) <= cap:
+            return keys[:int(off[world])], vals[:int(off[world])], off.astype(np.int64)
+        cap = int(off[world])
+
+
+def mad_accumulate(ctx, keys, vals, stream=None) -> None:
+    """Add (key, value) pairs (device int64 tensors) to X."""
+    _check(lib().mad_accumulate(ctx, _ptr(keys), _ptr(vals), keys.numel(), _stream(stream)),
+           "mad_accumulate")
+
+
+def mad_select_pairs(ctx, pairs, n: int, K: int, out=None, stream=None):
+    """The K pairs with the largest x > 0 by (x desc, key asc), copied whole."""
+    if out is None:
+        out = new_pairs(K)
+    cnt = ctypes.c_uint32(0)
+    _check(lib().mad_select_pairs(ctx, _ptr(pairs), n, K, _ptr(out), ctypes.byref(cnt),
+                                  _stream(stream)), "mad_select_pairs")
+    return out, cnt.value
 
 
 def mad_probe_gather(table, count: int, seed: int = 1, sink=None, stream=None) -> None:

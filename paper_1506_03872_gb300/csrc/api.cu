@@ -597,6 +597,36 @@ mad_status mad_export_x(mad_ctx* ctx, uint64_t* keys_dev, int64_t* vals_dev, uin
   return export_x(ctx, keys_dev, vals_dev, cap, n_host, (unsigned long long*)ctx->scratch, st);
 }
 
+mad_status mad_export_x_by_owner(mad_ctx* ctx, uint32_t world, uint64_t* keys_dev,
+                                 int64_t* vals_dev, uint64_t cap, uint64_t* offsets_host,
+                                 mad_stream stream) {
+  if (!ctx || !offsets_host || world == 0 || world > 65536 || (cap && (!keys_dev || !vals_dev)))
+    return MAD_ERR_ARG;
+  if (!ctx->built) return MAD_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  mad_status rs = ensure_scratch(ctx, sizeof(unsigned long long) * (3 * (size_t)world + 1), st);
+  if (rs != MAD_OK) return rs;
+  return export_x_by_owner(ctx, world, keys_dev, vals_dev, cap, offsets_host, st);
+}
+
+mad_status mad_accumulate(mad_ctx* ctx, const uint64_t* keys_dev, const int64_t* vals_dev,
+                          uint64_t n, mad_stream stream) {
+  if (!ctx || (n && (!keys_dev || !vals_dev))) return MAD_ERR_ARG;
+  if (!ctx->built) return MAD_ERR_STATE;
+  return accumulate_pairs(ctx, keys_dev, vals_dev, n, (cudaStream_t)stream);
+}
+
+mad_status mad_select_pairs(mad_ctx* ctx, const mad_pair* pairs_dev, uint64_t n, uint32_t K,
+                            mad_pair* out_dev, uint32_t* n_out_host, mad_stream stream) {
+  if (!ctx || !n_out_host || (n && !pairs_dev) || (K && !out_dev)) return MAD_ERR_ARG;
+  *n_out_host = 0;
+  uint64_t nsel = 0;
+  mad_status rs = select_pairs(ctx, pairs_dev, n, K, out_dev, &nsel, (cudaStream_t)stream);
+  if (rs != MAD_OK) return rs;
+  *n_out_host = (uint32_t)nsel;
+  return MAD_OK;
+}
+
 mad_status mad_export_table(mad_ctx* ctx, int which, void* out_dev, uint64_t cap,
                             uint64_t* n_host, mad_stream stream) {
   if (!ctx || !n_host) return MAD_ERR_ARG;

@@ -337,6 +337,17 @@ void items_to_pairs_dev(mad_ctx* ctx, const Item* items, uint64_t cap,
 int significant_bytes(unsigned long long maxp);
 mad_status export_x(mad_ctx* ctx, uint64_t* keys, int64_t* vals, uint64_t cap, uint64_t* n,
                     unsigned long long* counter, cudaStream_t st);
+// Sharded runs: X's occupied slots grouped by owner rank (offsets_host gets
+// world + 1 segment bounds; nothing is written when the total exceeds cap;
+// uses 8 (3 world + 1) bytes of scratch), and the K largest x > 0 of a pair
+// list by (x desc, key asc), copied from the input pairs.
+mad_status export_x_by_owner(mad_ctx* ctx, uint32_t world, uint64_t* keys, int64_t* vals,
+                             uint64_t cap, uint64_t* offsets_host, cudaStream_t st);
+mad_status select_pairs(mad_ctx* ctx, const mad_pair* pairs, uint64_t n, uint64_t K,
+                        mad_pair* out, uint64_t* n_sel, cudaStream_t st);
+// sample.cu: (key, value) pairs added to X.
+mad_status accumulate_pairs(mad_ctx* ctx, const uint64_t* keys, const int64_t* vals, uint64_t n,
+                            cudaStream_t st);
 // dense_topt.cu: the comparator; dense_out != NULL writes the full product.
 mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, uint32_t t,
                             uint32_t rescore, mad_pair* out, uint32_t* n_out, float* dense_out,

@@ -22,6 +22,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <vector>
 
 #include "mad_device.cuh"
 #include "mad_internal.cuh"
@@ -929,6 +930,129 @@ k_export(const unsigned long long* __restrict__ keys, const long long* __restric
       ov[pos] = vals[slot];
     }
   }
+}
+
+// Owner rank of a key in a sharded run (a SplitMix64 mix of the key,
+// modulo the number of ranks).
+__device__ __forceinline__ uint32_t key_owner(unsigned long long key, uint32_t world) {
+  return (uint32_t)(mix64(key ^ 0x5851F42D4C957F2Dull) % world);
+}
+
+// Occupied slots of X per owner rank (warp-combined atomics).
+__global__ void __launch_bounds__(256)
+k_owner_count(const unsigned long long* __restrict__ keys, uint64_t cap_max,
+              const unsigned long long* cap_dev, uint32_t world, unsigned long long* counts) {
+  const uint64_t cap = dev_len(cap_max, cap_dev);
+  const uint64_t cap_up = (cap + 31) & ~31ull;
+  const unsigned lane = threadIdx.x & 31;
+  for (uint64_t slot = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < cap_up;
+       slot += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned long long key = slot < cap ? keys[slot] : EMPTY_KEY;
+    const int o = key == EMPTY_KEY ? -1 : (int)key_owner(key, world);
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, o);
+    if (o >= 0 && lane == (unsigned)(__ffs(peers) - 1))
+      atomicAdd(&counts[o], (unsigned long long)__popc(peers));
+  }
+}
+
+// Every occupied slot to its owner's segment [off[o], off[o + 1]).
+__global__ void __launch_bounds__(256)
+k_owner_scatter(const unsigned long long* __restrict__ keys, const long long* __restrict__ vals,
+                uint64_t cap_max, const unsigned long long* cap_dev, uint32_t world,
+                const unsigned long long* __restrict__ off, unsigned long long* cursor,
+                unsigned long long* __restrict__ ok, long long* __restrict__ ov, uint64_t out_cap) {
+  const uint64_t cap = dev_len(cap_max, cap_dev);
+  const uint64_t cap_up = (cap + 31) & ~31ull;
+  const unsigned lane = threadIdx.x & 31;
+  for (uint64_t slot = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < cap_up;
+       slot += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned long long key = slot < cap ? keys[slot] : EMPTY_KEY;
+    const int o = key == EMPTY_KEY ? -1 : (int)key_owner(key, world);
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, o);
+    if (o < 0) continue;
+    const unsigned leader = __ffs(peers) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(&cursor[o], (unsigned long long)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const unsigned long long pos = off[o] + base + __popc(peers & ((1u << lane) - 1));
+    if (pos < out_cap) {
+      ok[pos] = key;
+      ov[pos] = vals[slot];
+    }
+  }
+}
+
+// Candidate pairs with x > 0 as select items (p = x, aux = position).
+__global__ void k_pair_items(const mad_pair* __restrict__ pairs, unsigned long long n,
+                             Item* __restrict__ items, unsigned long long* counter) {
+  const unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const mad_pair pr = pairs[q];
+  if (pr.x <= 0) return;
+  Item it;
+  it.p = (unsigned long long)pr.x;
+  it.key = ((unsigned long long)pr.i << 32) | pr.j;
+  it.aux = q;
+  items[atomicAdd(counter, 1ull)] = it;
+}
+
+__global__ void k_items_to_input_pairs(const Item* __restrict__ items, unsigned long long n,
+                                       const mad_pair* __restrict__ pairs,
+                                       mad_pair* __restrict__ out) {
+  const unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) out[q] = pairs[items[q].aux];
+}
+
+mad_status export_x_by_owner(mad_ctx* ctx, uint32_t world, uint64_t* keys, int64_t* vals,
+                             uint64_t cap, uint64_t* offsets_host, cudaStream_t st) {
+  // scratch: counts (world), offsets (world + 1), cursors (world)
+  unsigned long long* counts = (unsigned long long*)ctx->scratch;
+  unsigned long long* off = counts + world;
+  unsigned long long* cursor = off + world + 1;
+  cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * (3 * (size_t)world + 1), st);
+  const uint64_t bound = hash_slot_bound(ctx);
+  k_owner_count<<<grid_for(bound, 152 * 8), 256, 0, st>>>(ctx->hkeys, bound, hash_extent(ctx),
+                                                          world, counts);
+  count_launch(ctx);
+  std::vector<unsigned long long> hc(world);
+  cudaMemcpyAsync(hc.data(), counts, sizeof(unsigned long long) * world, cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  std::vector<unsigned long long> ho(world + 1, 0);
+  for (uint32_t o = 0; o < world; ++o) ho[o + 1] = ho[o] + hc[o];
+  for (uint32_t o = 0; o <= world; ++o) offsets_host[o] = ho[o];
+  if (ho[world] > cap) return MAD_OK;   // the caller sees the total and sizes up
+  cudaMemcpyAsync(off, ho.data(), sizeof(unsigned long long) * (world + 1), cudaMemcpyHostToDevice,
+                  st);
+  k_owner_scatter<<<grid_for(bound, 152 * 8), 256, 0, st>>>(
+      ctx->hkeys, ctx->hvals, bound, hash_extent(ctx), world, off, cursor,
+      (unsigned long long*)keys, (long long*)vals, cap);
+  count_launch(ctx);
+  return cuda_status(cudaStreamSynchronize(st));
+}
+
+mad_status select_pairs(mad_ctx* ctx, const mad_pair* pairs, uint64_t n, uint64_t K,
+                        mad_pair* out, uint64_t* n_sel, cudaStream_t st) {
+  *n_sel = 0;
+  if (n == 0 || K == 0) return MAD_OK;
+  const size_t ws_bytes = (select_ws_bytes(n, K) + 255) & ~(size_t)255;
+  mad_status rs = ensure_scratch(ctx, ws_bytes + 256, st);
+  if (rs != MAD_OK) return rs;
+  const SelectWs ws = select_ws_carve(ctx->scratch, n, K);
+  unsigned long long* counter = (unsigned long long*)((char*)ctx->scratch + ws_bytes);
+  cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+  k_pair_items<<<grid_for(n, 1u << 30), 256, 0, st>>>(pairs, n, ws.l0, counter);
+  count_launch(ctx);
+  unsigned long long npos = 0;
+  cudaMemcpyAsync(&npos, counter, sizeof(npos), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  if ((rs = select_list(ctx, ws, npos, K, 8, n_sel, st)) != MAD_OK) return rs;
+  if (*n_sel) {
+    k_items_to_input_pairs<<<grid_for(*n_sel, 1u << 30), 256, 0, st>>>(ws.out, *n_sel, pairs, out);
+    count_launch(ctx);
+  }
+  return cuda_status(cudaStreamSynchronize(st));
 }
 
 mad_status export_x(mad_ctx* ctx, uint64_t* keys, int64_t* vals, uint64_t cap, uint64_t* n,
