@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -17,6 +18,19 @@ mad_status cuda_status(cudaError_t e) {
   return MAD_ERR_CUDA;
 }
 
+// Every device allocation of a context's pool goes through here.  Host-side
+// fault injection for tests of the failure paths (no GPU fault involved):
+// with MAD_FAULT=oom[:N] in the environment at mad_create, the context's
+// N-th allocation (N = 1 without ":N") and every later one return
+// MAD_ERR_OOM instead of allocating.
+mad_status pool_malloc(mad_ctx* ctx, void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (ctx->fault_oom_at > 0 && ++ctx->allocs >= ctx->fault_oom_at) return MAD_ERR_OOM;
+  const mad_status rs = cuda_status(cudaMallocFromPoolAsync(p, bytes, ctx->pool, st));
+  if (rs != MAD_OK) *p = nullptr;
+  return rs;
+}
+
 mad_status ensure_scratch(mad_ctx* ctx, size_t bytes, cudaStream_t st) {
   if (bytes <= ctx->scratch_bytes) return MAD_OK;
   if (ctx->scratch_fixed) return MAD_ERR_STATE;
@@ -24,11 +38,8 @@ mad_status ensure_scratch(mad_ctx* ctx, size_t bytes, cudaStream_t st) {
   ctx->scratch = nullptr;
   ctx->scratch_bytes = 0;
   const size_t rounded = (bytes + (1u << 20) - 1) & ~(size_t)((1u << 20) - 1);
-  const cudaError_t e = cudaMallocFromPoolAsync(&ctx->scratch, rounded, ctx->pool, st);
-  if (e != cudaSuccess) {
-    ctx->scratch = nullptr;
-    return cuda_status(e);
-  }
+  const mad_status rs = pool_malloc(ctx, &ctx->scratch, rounded, st);
+  if (rs != MAD_OK) return rs;
   ctx->scratch_bytes = rounded;
   return MAD_OK;
 }
@@ -86,9 +97,11 @@ void free_tables(mad_ctx* ctx, cudaStream_t st) {
 
 template <typename T>
 mad_status alloc(mad_ctx* ctx, T*& p, size_t count, cudaStream_t st) {
-  p = nullptr;
   if (count == 0) count = 1;
-  return cuda_status(cudaMallocFromPoolAsync((void**)&p, count * sizeof(T), ctx->pool, st));
+  void* q = nullptr;
+  const mad_status rs = pool_malloc(ctx, &q, count * sizeof(T), st);
+  p = (T*)q;
+  return rs;
 }
 
 
@@ -300,6 +313,13 @@ mad_status mad_create(mad_ctx** out, uint32_t flags) {
   mad_ctx* ctx = new (std::nothrow) mad_ctx();
   if (!ctx) return MAD_ERR_OOM;
   ctx->flags = flags;
+  if (const char* f = std::getenv("MAD_FAULT")) {
+    if (std::strncmp(f, "oom", 3) == 0) {
+      ctx->fault_oom_at = 1;
+      if (f[3] == ':') ctx->fault_oom_at = std::strtoll(f + 4, nullptr, 10);
+      if (ctx->fault_oom_at < 1) ctx->fault_oom_at = 1;
+    }
+  }
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) {
     cudaMemPoolProps props = {};

@@ -196,6 +196,10 @@ struct mad_ctx {
   // Scratch (select, scans); grown on demand.
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  // Host-side fault injection (MAD_FAULT=oom[:N]): the allocation number
+  // from which pool allocations fail (0: off), and allocations so far.
+  int64_t fault_oom_at = 0;
+  int64_t allocs = 0;
   // Host mirrors.
   uint64_t launches = 0;
   uint64_t distinct = 0, positive = 0;
@@ -208,6 +212,9 @@ namespace mad {
 inline void count_launch(mad_ctx* ctx, int n = 1) { ctx->launches += (uint64_t)n; }
 
 mad_status cuda_status(cudaError_t e);
+// The one device allocation path of a context (its stream-ordered pool),
+// with the host-side fault injection of MAD_FAULT=oom[:N].
+mad_status pool_malloc(mad_ctx* ctx, void** p, size_t bytes, cudaStream_t st);
 mad_status ensure_scratch(mad_ctx* ctx, size_t bytes, cudaStream_t st);
 
 // scan.cu: out[0..n] = exclusive prefix of in[0..n) and the total at

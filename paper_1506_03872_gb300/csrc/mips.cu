@@ -277,9 +277,11 @@ k_mips_region_sizes(const unsigned long long* __restrict__ s_q, uint32_t nq,
 
 template <typename T>
 mad_status pool_alloc(mad_ctx* ctx, T*& p, size_t count, cudaStream_t st) {
-  p = nullptr;
   if (count == 0) count = 1;
-  return cuda_status(cudaMallocFromPoolAsync((void**)&p, count * sizeof(T), ctx->pool, st));
+  void* q = nullptr;
+  const mad_status rs = pool_malloc(ctx, &q, count * sizeof(T), st);
+  p = (T*)q;
+  return rs;
 }
 
 template <typename T>

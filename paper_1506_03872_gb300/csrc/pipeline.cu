@@ -104,19 +104,11 @@ mad_status mad_pipeline_plan(mad_ctx* ctx, const mad_matrix* A, const mad_matrix
   mad_status rs = plan_dense_tables(ctx, A, B, s, st);
   if (rs != MAD_OK) return rs;
   const PipeBufs sizes = carve(nullptr, tprime, t);
-  if ((rs = cuda_status(cudaMallocFromPoolAsync(&ctx->pipe_buf, sizes.bytes, ctx->pool, st))) !=
-      MAD_OK) {
-    ctx->pipe_buf = nullptr;
-    return rs;
-  }
+  if ((rs = pool_malloc(ctx, &ctx->pipe_buf, sizes.bytes, st)) != MAD_OK) return rs;
   // The scratch every launch of a run needs, owned by the pass.
   size_t scratch = dense_build_scratch_bytes(ctx);
   if (sample_scratch_bytes(ctx, s) > scratch) scratch = sample_scratch_bytes(ctx, s);
-  if ((rs = cuda_status(cudaMallocFromPoolAsync(&ctx->pipe_scratch, scratch, ctx->pool, st))) !=
-      MAD_OK) {
-    ctx->pipe_scratch = nullptr;
-    return rs;
-  }
+  if ((rs = pool_malloc(ctx, &ctx->pipe_scratch, scratch, st)) != MAD_OK) return rs;
   ctx->pipe_scratch_bytes = scratch;
   ctx->pipe = true;
   ctx->pipe_s = s;

@@ -123,3 +123,30 @@ def test_square_sym_needs_01_gram_inputs():
         with pytest.raises(mad.MadError) as e:
             mad.mad_build_tables(c.ctx, mad.dense(A), mad.dense(A.T.contiguous()), 100)
         assert e.value.status == mad.MAD_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("nth", [1, 2, 5])
+def test_injected_allocation_failure_returns_oom(monkeypatch, nth):
+    """Host-side fault injection (no GPU fault): with MAD_FAULT=oom:N at
+    context creation, the context's N-th device allocation and every later
+    one fail, and the call that needs them returns MAD_ERR_OOM; the context
+    is destroyed cleanly and a context created without the variable works
+    on the same device."""
+    import paper_1506_03872_gb300 as mad
+    rng = np.random.Generator(np.random.PCG64(90))
+    A = torch.from_numpy(rng.standard_normal((300, 20)).astype(np.float32)).cuda()
+    B = torch.from_numpy(rng.standard_normal((20, 400)).astype(np.float32)).cuda()
+    monkeypatch.setenv("MAD_FAULT", f"oom:{nth}")
+    with mad.Context() as c:
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_build_tables(c.ctx, mad.dense(A), mad.dense(B), 50_000)
+        assert e.value.status == mad.MAD_ERR_OOM
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_dense_topt(c.ctx, mad.dense(A), mad.dense(B), 10)
+        assert e.value.status == mad.MAD_ERR_OOM
+    monkeypatch.delenv("MAD_FAULT")
+    with mad.Context() as c:
+        mad.mad_build_tables(c.ctx, mad.dense(A), mad.dense(B), 50_000)
+        mad.mad_sample(c.ctx, 50_000, 3)
+        _, n = mad.mad_topk(c.ctx, 100)
+        assert n == 100
