@@ -634,6 +634,31 @@ def run_ours(args):
         except Exception as ex:  # the comparator must not cost the main line
             comp = {"error": str(ex)[:200]}
 
+    # 0/1 inputs: the exact sparse comparator (degree-bounded row-block
+    # product with a fused threshold) on the same inputs, timed the same way.
+    if w.csr and not args.no_comparator:
+        try:
+            out_x = mad.new_pairs(t)
+            for _ in range(2):
+                mad.mad_sparse_topt(ctx.ctx, Am, Bm, t, 0, out_x)
+            cms = []
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                c0, c1 = ev(), ev()
+                c0.record(stream)
+                res_x, nx = mad.mad_sparse_topt(ctx.ctx, Am, Bm, t, 0, out_x)
+                c1.record(stream)
+                torch.cuda.synchronize()
+                cms.append(c0.elapsed_time(c1))
+            comp = {"kernel": "k_spgemm_rowblock_topk", "ms": round(float(np.mean(cms)), 4),
+                    "results": int(nx)}
+            if counts is not None:
+                xi, xj, _, xc = mad.decode_pairs(res_x, nx)
+                comp["recall"], comp["count_mismatches"] = recall_of(w, xi, xj, xc, set(), tau,
+                                                                     counts)
+        except Exception as ex:  # the comparator must not cost the main line
+            comp = {"error": str(ex)[:200]}
+
     ladder = None
     if rank == 0 and recall is not None and not args.no_ladder:
         try:
