@@ -19,6 +19,8 @@ arrays; every function mirrors one step of the paper:
 * ``sparse_exact``                  -- exact top t by the row-wise sparse
   product (the paper's exact computation, Sec. 4.3).
 * ``enumerate``                     -- exact three-path law (Lemma 1).
+* ``enumerate_wedges``              -- exact wedge law (the appendix's wedge
+  sampling; Oracle(..., flags | WEDGE) draws wedges instead of diamonds).
 """
 from __future__ import annotations
 
@@ -35,7 +37,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 FMT_DENSE, FMT_CSR = 0, 1
 DT_F32, DT_F64, DT_BINARY = 0, 1, 2
-NONNEG, GRAM, EXCLUDE_DIAG = 1, 2, 4
+NONNEG, GRAM, EXCLUDE_DIAG, SQUARE_SYM, WEDGE = 1, 2, 4, 8, 16
 STATUS = {0: "ok", 1: "bad argument", 4: "overflow", 5: "empty", 8: "unsupported"}
 
 
@@ -85,6 +87,8 @@ def _L() -> ctypes.CDLL:
         lib.or_bruteforce.argtypes = [P, u64, P, P]
         lib.or_sparse_exact.restype = i64
         lib.or_sparse_exact.argtypes = [P, u64, P, P]
+        lib.or_enumerate_wedges.restype = i64
+        lib.or_enumerate_wedges.argtypes = [P, i64, P, P, P, P, P]
         lib.or_enumerate.restype = i64
         lib.or_enumerate.argtypes = [P, i64, P, P, P, P, P, P]
         lib.or_philox4x32_10.argtypes = [P, P, P]
@@ -162,7 +166,8 @@ class Oracle:
     # --- tables ---------------------------------------------------------
     _TABLES = {"T1": (0, np.uint64), "T2": (1, np.uint32), "TA": (2, np.uint32),
                "TB": (3, np.uint32), "na": (4, np.float32), "nb": (5, np.float32),
-               "r": (6, np.float32), "srow": (7, np.float32)}
+               "r": (6, np.float32), "srow": (7, np.float32), "TK": (8, np.uint64),
+               "TAc": (9, np.uint32), "nac": (10, np.float32)}
 
     def table(self, name: str) -> np.ndarray:
         which, dt = self._TABLES[name]
@@ -236,6 +241,19 @@ class Oracle:
         cnt = _L().or_enumerate(self.h, cap, *[_p(a) for a in arrs], _p(prob), _p(v))
         if cnt > cap:
             raise ValueError(f"{cnt} three-paths exceed cap {cap}")
+        return tuple(a[:cnt] for a in arrs) + (prob[:cnt], v[:cnt])
+
+    def enumerate_wedges(self, cap: int = 1 << 20):
+        """Every wedge (i, k, j) with its probability and increment (wedge
+        contexts only)."""
+        arrs = [np.zeros(cap, np.uint32) for _ in range(3)]
+        prob = np.zeros(cap, np.float64)
+        v = np.zeros(cap, np.int64)
+        cnt = _L().or_enumerate_wedges(self.h, cap, *[_p(a) for a in arrs], _p(prob), _p(v))
+        if cnt < 0:
+            raise ValueError("not a wedge oracle")
+        if cnt > cap:
+            raise ValueError(f"{cnt} wedges exceed cap {cap}")
         return tuple(a[:cnt] for a in arrs) + (prob[:cnt], v[:cnt])
 
     def run(self, s: int, seed: int, tprime: int, t: int):

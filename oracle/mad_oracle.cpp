@@ -44,7 +44,7 @@ namespace {
 
 enum { FMT_DENSE = 0, FMT_CSR = 1 };
 enum { DT_F32 = 0, DT_F64 = 1, DT_BINARY = 2 };
-enum { FL_NONNEG = 1u, FL_GRAM = 2u, FL_EXCLUDE_DIAG = 4u, FL_SQSYM = 8u };
+enum { FL_NONNEG = 1u, FL_GRAM = 2u, FL_EXCLUDE_DIAG = 4u, FL_SQSYM = 8u, FL_WEDGE = 16u };
 enum {
   ST_OK = 0, ST_ARG = 1, ST_OVERFLOW = 4, ST_EMPTY = 5, ST_UNSUPPORTED = 8
 };
@@ -196,6 +196,18 @@ struct Oracle {
   std::vector<uint32_t> T2, TA, TB;
   int E1 = 0, F = 0;
   uint64_t bumps = 0;
+  // Wedge sampling (FL_WEDGE): the columns of A (entry q of column k is
+  // row Acol_row[q], FP32 value Acol_val[q], rows ascending), their
+  // cumulative tables TAc, the column norms, and the center table TK over k
+  // with its scale exponent EK.
+  bool wedge = false;
+  std::vector<int64_t> Acol_ptr;
+  std::vector<int32_t> Acol_row;
+  std::vector<float> Acol_val;
+  std::vector<uint32_t> TAc;
+  std::vector<float> nac, wk;
+  std::vector<uint64_t> TK;
+  int EK = 0;
   // Sampling state.
   std::unordered_map<uint64_t, int64_t> X;
   uint64_t sampled = 0, inserted = 0, diag_skipped = 0;
@@ -315,6 +327,77 @@ int build_tables(Oracle& o) {
   return ST_OK;
 }
 
+// Tables of wedge sampling (the appendix's Alg. "MAD wedge sampling"): with
+// A m x d (rows a_i) and B d x n, the center k is drawn with probability
+// w_k / ||w||_1, w_k = ||a_*k||_1 ||b_k*||_1, then i within column k of A
+// with probability |a_ik| / ||a_*k||_1 and j within row k of B with
+// probability |b_kj| / ||b_k*||_1 (the TB table of Alg. 2 above).  Float
+// mode quantises as the diamond tables do: column tables like row tables
+// (scaled so the column's prefix stays below 2^31), TK like T1 with d in
+// place of m.  0/1 inputs: w_k = (entries of column k of A) x (entries of
+// row k of B), exact.
+int build_wedge_tables(Oracle& o) {
+  const Mat& A = o.A;
+  const Mat& B = o.B;
+  // Columns of A, rows ascending.
+  o.Acol_ptr.assign(o.d + 1, 0);
+  for (size_t e = 0; e < A.col.size(); ++e) ++o.Acol_ptr[A.col[e] + 1];
+  for (int64_t k = 0; k < o.d; ++k) o.Acol_ptr[k + 1] += o.Acol_ptr[k];
+  o.Acol_row.assign(A.col.size(), 0);
+  o.Acol_val.assign(A.col.size(), 0.0f);
+  std::vector<int64_t> fill(o.Acol_ptr.begin(), o.Acol_ptr.end() - 1);
+  for (int64_t i = 0; i < o.m; ++i)
+    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+      const int64_t q = fill[A.col[e]]++;
+      o.Acol_row[q] = (int32_t)i;
+      o.Acol_val[q] = A.valf[e];
+    }
+  o.TAc.assign(A.col.size(), 0);
+  o.TK.assign(o.d, 0);
+  if (o.integer) {
+    uint64_t total = 0;
+    for (int64_t k = 0; k < o.d; ++k) {
+      uint32_t p = 0;
+      for (int64_t q = o.Acol_ptr[k]; q < o.Acol_ptr[k + 1]; ++q) o.TAc[q] = ++p;
+      const uint64_t w = (uint64_t)(o.Acol_ptr[k + 1] - o.Acol_ptr[k]) *
+                         (uint64_t)(B.ptr[k + 1] - B.ptr[k]);
+      if (total + w < total || total + w >= (1ull << 63)) return ST_OVERFLOW;
+      total += w;
+      o.TK[k] = total;
+    }
+    o.EK = 0;
+    return total == 0 ? ST_EMPTY : ST_OK;
+  }
+  o.nac.assign(o.d, 0.0f);
+  o.wk.assign(o.d, 0.0f);
+  float maxw = 0.0f;
+  for (int64_t k = 0; k < o.d; ++k) {
+    std::vector<float> w;
+    for (int64_t q = o.Acol_ptr[k]; q < o.Acol_ptr[k + 1]; ++q) w.push_back(std::fabs(o.Acol_val[q]));
+    o.nac[k] = canonical_sum_f32(w);
+    if (o.nac[k] > 0.0f) {
+      const int e = row_exponent(o.nac[k]);
+      uint32_t p = 0;
+      for (size_t q = 0; q < w.size(); ++q) {
+        p += quantize_row(w[q], e);
+        o.TAc[o.Acol_ptr[k] + q] = p;
+      }
+    }
+    o.wk[k] = o.nac[k] * o.nb[k];
+    maxw = std::max(maxw, o.wk[k]);
+  }
+  if (maxw == 0.0f) return ST_EMPTY;
+  o.EK = 62 - ceil_log2((uint64_t)o.d) - (std::ilogb(maxw) + 1);
+  uint64_t p = 0;
+  for (int64_t k = 0; k < o.d; ++k) {
+    uint64_t v = (uint64_t)std::rint(std::ldexp((double)o.wk[k], o.EK));
+    if (o.wk[k] > 0.0f && v == 0) v = 1;
+    p += v;
+    o.TK[k] = p;
+  }
+  return ST_OK;
+}
+
 // Value b_{k'j} of B (0 when absent).
 double b_value(const Oracle& o, int64_t kp, int64_t j, float* valf) {
   const Mat& B = o.B;
@@ -338,6 +421,33 @@ struct Draw {
   uint32_t i, k, j, kp;
   int64_t v;
 };
+
+// One iteration of the wedge sampling loop for wedge index ell: the first
+// three uniforms of the index's Philox counter pick k, i and j; the
+// increment is sgn(a_ik b_kj) (1 for 0/1 and nonnegative inputs).  The
+// paper prints sgn(a_ki b_ki); its Lemma on E[x_ij] uses a_ki b_kj, which
+// is what is added.  kp is 0.
+Draw draw_wedge(const Oracle& o, uint64_t seed, uint64_t ell) {
+  uint64_t u[4];
+  diamond_uniforms(seed, ell, 0, u);
+  const Mat& B = o.B;
+  const int64_t k = inverse_cdf(o.TK.data(), o.d, draw_target(u[0], o.TK[o.d - 1]));
+  const int64_t c0 = o.Acol_ptr[k], clen = o.Acol_ptr[k + 1] - c0;
+  const int64_t pi = inverse_cdf(o.TAc.data() + c0, clen, draw_target(u[1], o.TAc[c0 + clen - 1]));
+  const int64_t b0 = B.ptr[k], blen = B.ptr[k + 1] - b0;
+  const int64_t pj = inverse_cdf(o.TB.data() + b0, blen, draw_target(u[2], o.TB[b0 + blen - 1]));
+  Draw dr;
+  dr.i = (uint32_t)o.Acol_row[c0 + pi];
+  dr.k = (uint32_t)k;
+  dr.j = (uint32_t)B.col[b0 + pj];
+  dr.kp = 0;
+  dr.v = 1;
+  if (!o.integer && !(o.flags & FL_NONNEG)) {
+    if (o.Acol_val[c0 + pi] < 0.0f) dr.v = -dr.v;
+    if (B.valf[b0 + pj] < 0.0f) dr.v = -dr.v;
+  }
+  return dr;
+}
 
 // One iteration of the sampling loop of Alg. 2 for diamond index ell.
 Draw draw_diamond(const Oracle& o, uint64_t seed, uint64_t ell) {
@@ -456,7 +566,14 @@ void* or_create(int fmtA, int dtA, int64_t m, int64_t d, int64_t ldA, const void
     return nullptr;
   }
   o->integer = (dtA == DT_BINARY);
+  o->wedge = (flags & FL_WEDGE) != 0;
+  if (o->wedge && (flags & FL_SQSYM)) {
+    *status = ST_UNSUPPORTED;
+    delete o;
+    return nullptr;
+  }
   *status = build_tables(*o);
+  if (*status == ST_OK && o->wedge) *status = build_wedge_tables(*o);
   if (*status != ST_OK) {
     delete o;
     return nullptr;
@@ -480,6 +597,9 @@ int64_t or_table(void* h, int which, void* out) {
     case 5: if (out) std::memcpy(out, o->nb.data(), o->nb.size() * 4); return (int64_t)o->nb.size();
     case 6: if (out) std::memcpy(out, o->r.data(), o->r.size() * 4); return (int64_t)o->r.size();
     case 7: if (out) std::memcpy(out, o->srow.data(), o->srow.size() * 4); return (int64_t)o->srow.size();
+    case 8: if (out) std::memcpy(out, o->TK.data(), o->TK.size() * 8); return (int64_t)o->TK.size();
+    case 9: if (out) std::memcpy(out, o->TAc.data(), o->TAc.size() * 4); return (int64_t)o->TAc.size();
+    case 10: if (out) std::memcpy(out, o->nac.data(), o->nac.size() * 4); return (int64_t)o->nac.size();
   }
   return -1;
 }
@@ -502,7 +622,7 @@ void or_draw(void* h, uint64_t seed, uint64_t first, uint64_t count, uint32_t* o
              uint32_t* oj, uint32_t* okp, int64_t* ov) {
   Oracle* o = (Oracle*)h;
   for (uint64_t q = 0; q < count; ++q) {
-    const Draw dr = draw_diamond(*o, seed, first + q);
+    const Draw dr = o->wedge ? draw_wedge(*o, seed, first + q) : draw_diamond(*o, seed, first + q);
     oi[q] = dr.i;
     ok[q] = dr.k;
     oj[q] = dr.j;
@@ -516,7 +636,7 @@ void or_draw_list(void* h, uint64_t seed, uint64_t count, const uint64_t* ells, 
                   uint32_t* ok, uint32_t* oj, uint32_t* okp, int64_t* ov) {
   Oracle* o = (Oracle*)h;
   for (uint64_t q = 0; q < count; ++q) {
-    const Draw dr = draw_diamond(*o, seed, ells[q]);
+    const Draw dr = o->wedge ? draw_wedge(*o, seed, ells[q]) : draw_diamond(*o, seed, ells[q]);
     oi[q] = dr.i;
     ok[q] = dr.k;
     oj[q] = dr.j;
@@ -541,7 +661,7 @@ int or_sample(void* h, uint64_t s, uint64_t seed, uint64_t first) {
   if (o->sampled + s > o->s_max) return ST_OVERFLOW;
   const bool sqsym = (o->flags & FL_SQSYM) != 0;
   for (uint64_t q = 0; q < s; ++q) {
-    const Draw dr = draw_diamond(*o, seed, first + q);
+    const Draw dr = o->wedge ? draw_wedge(*o, seed, first + q) : draw_diamond(*o, seed, first + q);
     if ((o->flags & FL_EXCLUDE_DIAG) && dr.i == dr.j) {
       ++o->diag_skipped;
     } else if (dr.v != 0) {
@@ -709,6 +829,49 @@ int64_t or_sparse_exact(void* h, uint64_t t, uint64_t* out_keys, double* out_c) 
   for (int64_t q = 0; q < cnt; ++q) {
     out_keys[q] = best[q].key;
     out_c[q] = best[q].c;
+  }
+  return cnt;
+}
+
+// Wedge law for tiny instances (the appendix's Lemma on the wedge event):
+// every wedge (i, k, j) with its probability under the oracle's tables and
+// its increment.  Returns the number of wedges with nonzero probability.
+int64_t or_enumerate_wedges(void* h, int64_t cap, uint32_t* oi, uint32_t* ok, uint32_t* oj,
+                            double* prob, int64_t* ov) {
+  Oracle* o = (Oracle*)h;
+  if (!o->wedge) return -1;
+  const Mat& B = o->B;
+  int64_t cnt = 0;
+  const long double tk = (long double)o->TK[o->d - 1];
+  for (int64_t k = 0; k < o->d; ++k) {
+    const uint64_t qk = o->TK[k] - (k ? o->TK[k - 1] : 0);
+    if (qk == 0) continue;
+    const int64_t c0 = o->Acol_ptr[k], clen = o->Acol_ptr[k + 1] - c0;
+    const int64_t b0 = B.ptr[k], blen = B.ptr[k + 1] - b0;
+    const long double ta = (long double)o->TAc[c0 + clen - 1];
+    const long double tb = (long double)o->TB[b0 + blen - 1];
+    for (int64_t pi = 0; pi < clen; ++pi) {
+      const uint32_t qi = o->TAc[c0 + pi] - (pi ? o->TAc[c0 + pi - 1] : 0);
+      if (qi == 0) continue;
+      for (int64_t pj = 0; pj < blen; ++pj) {
+        const uint32_t qj = o->TB[b0 + pj] - (pj ? o->TB[b0 + pj - 1] : 0);
+        if (qj == 0) continue;
+        if (cnt < cap) {
+          int64_t v = 1;
+          if (!o->integer && !(o->flags & FL_NONNEG)) {
+            if (o->Acol_val[c0 + pi] < 0.0f) v = -v;
+            if (B.valf[b0 + pj] < 0.0f) v = -v;
+          }
+          oi[cnt] = (uint32_t)o->Acol_row[c0 + pi];
+          ok[cnt] = (uint32_t)k;
+          oj[cnt] = (uint32_t)B.col[b0 + pj];
+          prob[cnt] = (double)(((long double)qk / tk) * ((long double)qi / ta) *
+                               ((long double)qj / tb));
+          ov[cnt] = v;
+        }
+        ++cnt;
+      }
+    }
   }
   return cnt;
 }

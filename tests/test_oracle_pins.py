@@ -560,3 +560,95 @@ def test_sparse_exact_matches_numpy_and_bruteforce():
     keys, c = Oracle(_csr_of(E), _csr_of(F), 0).sparse_exact(10)
     assert keys.tolist() == [(1 << 32) | 3, (4 << 32) | 3, (4 << 32) | 6]
     assert c.tolist() == [1.0, 1.0, 1.0]
+
+
+# ---------------------------------------------------------------------------
+# Wedge sampling (the appendix's Alg. "MAD wedge sampling" and its Lemmas)
+# ---------------------------------------------------------------------------
+def _wedge_w1(A, B):
+    """||w||_1 = sum_k ||a_*k||_1 ||b_k*||_1 (the wedge weights)."""
+    return float((np.abs(A).sum(axis=0) * np.abs(B).sum(axis=1)).sum())
+
+
+def test_wedge_expectation_dense():
+    """Enumerated wedge law: every wedge (i,k,j) has probability
+    |a_ik||b_kj| / ||w||_1 and E[x_ij]/s = c_ij / ||w||_1 (up to the
+    tables' fixed-point rounding)."""
+    rng = _rng(51)
+    A = rng.standard_normal((5, 4))
+    B = rng.standard_normal((4, 6))
+    A[1, 2] = 0.0
+    o = Oracle(Matrix(A), Matrix(B), oracle.WEDGE)
+    i, k, j, prob, v = o.enumerate_wedges()
+    w1 = _wedge_w1(A, B)
+    assert abs(prob.sum() - 1.0) < 1e-12
+    assert np.allclose(prob, np.abs(A[i, k] * B[k, j]) / w1, rtol=2e-5)
+    assert np.array_equal(v, np.sign(A[i, k] * B[k, j]).astype(np.int64))
+    ex = np.zeros((5, 6))
+    np.add.at(ex, (i, j), prob * v)
+    C = A @ B
+    assert np.allclose(ex * w1, C, atol=2e-5 * np.abs(C).max())
+
+
+def test_wedge_expectation_binary_exact():
+    """0/1 inputs: every wedge has probability exactly 1 / ||w||_1 and the
+    pair (i, j) is reached by exactly c_ij wedges, so E[x_ij]/s =
+    c_ij / ||w||_1 holds exactly."""
+    rng = _rng(52)
+    A = (rng.random((7, 5)) < 0.5).astype(np.int64)
+    B = (rng.random((5, 8)) < 0.5).astype(np.int64)
+    A[0, 0] = B[0, 0] = 1
+    o = Oracle(_csr_of(A), _csr_of(B), oracle.WEDGE)
+    i, k, j, prob, v = o.enumerate_wedges()
+    w1 = int((A.sum(axis=0) * B.sum(axis=1)).sum())
+    assert len(prob) == w1
+    assert np.all(prob * w1 == 1.0) and np.all(v == 1)
+    cnt = np.zeros((7, 8), np.int64)
+    np.add.at(cnt, (i, j), 1)
+    assert np.array_equal(cnt, A @ B)
+    assert int(o.table("TK")[-1]) == w1
+
+
+def test_wedge_draw_frequencies_match_the_law():
+    rng = _rng(53)
+    A = np.abs(rng.standard_normal((4, 3))) + 0.1
+    B = rng.standard_normal((3, 5))
+    o = Oracle(Matrix(A), Matrix(B), oracle.WEDGE, 1 << 20)
+    i, k, j, prob, _ = o.enumerate_wedges()
+    n = 200_000
+    di, dk, dj, dkp, dv = o.draw(seed=7, first=0, count=n)
+    assert np.all(dkp == 0)
+    idx = {(a, b, c): q for q, (a, b, c) in enumerate(zip(i.tolist(), k.tolist(), j.tolist()))}
+    counts = np.zeros(len(prob))
+    for a, b, c in zip(di.tolist(), dk.tolist(), dj.tolist()):
+        counts[idx[(a, b, c)]] += 1
+    p = stats.chisquare(counts, prob * n).pvalue
+    assert p > 1e-4
+
+
+def test_wedge_sample_accumulates_its_draws_with_pair_rules():
+    """X after s wedges is the sum of the drawn increments on the keys of
+    the pair rules (Gram: unordered, diagonal skipped and counted)."""
+    A, M = _sym_binary(30, 0.2, 54)
+    o = Oracle(M, M, 2 | 4 | oracle.WEDGE, 20_000)
+    assert o.sample(20_000, 5) == 0
+    keys, vals = o.x()
+    di, dk, dj, _, dv = o.draw(seed=5, first=0, count=20_000)
+    ref, diag = {}, 0
+    for a, c, val in zip(di.tolist(), dj.tolist(), dv.tolist()):
+        if a == c:
+            diag += 1
+            continue
+        key = (min(a, c) << 32) | max(a, c)
+        ref[key] = ref.get(key, 0) + val
+    assert {int(k_): int(v_) for k_, v_ in zip(keys, vals)} == ref
+    assert o.scalars()["diag_skipped"] == diag
+
+
+def test_wedge_sampling_finds_planted_pairs():
+    from paper_1506_03872_gb300.workloads import plain_small
+    w = plain_small(m=200, d=25, n=200, planted=10, seed=9)
+    o = Oracle(Matrix(w.A), Matrix(w.B), oracle.WEDGE, 1 << 22)
+    truth, _ = o.bruteforce(10)
+    keys, c = o.run(s=2_000_000, seed=4, tprime=100, t=10)
+    assert set(keys.tolist()) == set(truth.tolist())
