@@ -114,8 +114,22 @@ typedef struct mad_pair {
  *                     pair (k, k') (the paper adds half to each pair; the
  *                     whole value scales every x by 2 and orders the same).
  *                     Under MAD_EXCLUDE_DIAG a diagonal addition of either
- *                     kind is skipped.  0/1 inputs only. */
-enum { MAD_NONNEG = 1u, MAD_GRAM = 2u, MAD_EXCLUDE_DIAG = 4u, MAD_SQUARE_SYM = 8u };
+ *                     kind is skipped.  0/1 inputs only.
+ *   MAD_WEDGE         wedge sampling in place of diamond sampling (the
+ *                     paper's comparison method, appendix "Previous
+ *                     approach: Wedge sampling"): mad_sample draws wedges
+ *                     (i, k, j) with k ~ ||a_*k||_1 ||b_k*||_1, i ~ |a_ik|
+ *                     within column k of A and j ~ |b_kj| within row k of B
+ *                     (the first three Philox uniforms of the wedge index)
+ *                     and adds sgn(a_ik b_kj) to x_ij, so E[x_ij] = s c_ij /
+ *                     ||w||_1.  mad_topk and mad_rescore apply as for
+ *                     diamonds.  Dense inputs (d <= 1024) and 0/1 Gram
+ *                     inputs (MAD_ERR_UNSUPPORTED for other 0/1 inputs); X is
+ *                     a plain table of at least s_max / 0.6 slots; mad_stats
+ *                     reports ||w||_1 in place of ||W||_1; not with
+ *                     MAD_SQUARE_SYM or the fused pass. */
+enum { MAD_NONNEG = 1u, MAD_GRAM = 2u, MAD_EXCLUDE_DIAG = 4u, MAD_SQUARE_SYM = 8u,
+       MAD_WEDGE = 16u };
 
 typedef struct mad_stats_t {
   double w1;                /* ||W||_1 as represented by the tables */
@@ -475,6 +489,9 @@ mad_status mad_export_x(mad_ctx* ctx, uint64_t* keys_dev, int64_t* vals_dev, uin
  *   0 T1 (uint64, m)      1 T2 (uint32, nnz(A))   2 TA (uint32, nnz(A))
  *   3 TB (uint32, nnz(B)) 4 ||a_i*||_1 (f32, m)  5 ||b_k*||_1 (f32, d)
  *   6 r_i (f32, m)
+ *   wedge contexts: 7 TK (uint64, d, inclusive prefix of the centre
+ *   weights), 8 column tables of A (uint32, m x d column-major; dense
+ *   non-Gram inputs), 9 ||a_*k||_1 (f32, d; dense inputs)
  * Row-table entries carry the sign of the matching value of A or B in bit
  * 31 (float mode).  Tables the mode keeps implicit report 0 elements.
  * *n_host receives the element count.  Synchronises the stream. */

@@ -24,8 +24,9 @@ MAD_OK, MAD_ERR_ARG, MAD_ERR_OOM, MAD_ERR_CUDA, MAD_ERR_OVERFLOW = 0, 1, 2, 3, 4
 MAD_ERR_EMPTY, MAD_ERR_HASH_FULL, MAD_ERR_STATE, MAD_ERR_UNSUPPORTED = 5, 6, 7, 8
 MAD_DENSE_ROWMAJOR, MAD_CSR = 0, 1
 MAD_F32, MAD_F64, MAD_BINARY = 0, 1, 2
-MAD_NONNEG, MAD_GRAM, MAD_EXCLUDE_DIAG, MAD_SQUARE_SYM = 1, 2, 4, 8
-TABLES = {"T1": 0, "T2": 1, "TA": 2, "TB": 3, "na": 4, "nb": 5, "r": 6}
+MAD_NONNEG, MAD_GRAM, MAD_EXCLUDE_DIAG, MAD_SQUARE_SYM, MAD_WEDGE = 1, 2, 4, 8, 16
+TABLES = {"T1": 0, "T2": 1, "TA": 2, "TB": 3, "na": 4, "nb": 5, "r": 6, "TK": 7, "TAc": 8,
+          "nac": 9}
 
 # Every symbol include/mad.h declares.
 EXPORTS = (
@@ -468,8 +469,8 @@ def mad_export_table(ctx, name: str, stream=None):
     n = ctypes.c_uint64(0)
     _check(lib().mad_export_table(ctx, which, None, 0, ctypes.byref(n), _stream(stream)),
            "mad_export_table")
-    dt = torch.int64 if name == "T1" else (torch.float32 if name in ("na", "nb", "r")
-                                           else torch.int32)
+    dt = torch.int64 if name in ("T1", "TK") else (
+        torch.float32 if name in ("na", "nb", "r", "nac") else torch.int32)
     out = torch.empty(max(n.value, 1), dtype=dt, device="cuda")
     _check(lib().mad_export_table(ctx, which, _ptr(out), n.value, ctypes.byref(n),
                                   _stream(stream)), "mad_export_table")

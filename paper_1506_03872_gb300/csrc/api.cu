@@ -82,6 +82,11 @@ void free_tables(mad_ctx* ctx, cudaStream_t st) {
   free_async(ctx->T1g, st);
   free_async(ctx->TBg, st);
   free_async(ctx->TBg_sh, st);
+  free_async(ctx->TK, st);
+  free_async(ctx->TAc, st);
+  free_async(ctx->nac, st);
+  ctx->TK_shift = 0;
+  ctx->tk_total = 0;
   free_async(ctx->pipe_buf, st);
   free_async(ctx->pipe_scratch, st);
   ctx->pipe_scratch_bytes = 0;
@@ -229,8 +234,12 @@ mad_status alloc_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, 
   // 0/1 inputs a plain power-of-two table sized from a pilot run of the
   // sampler (their closure rate is unknown until sampled); an explicit
   // capacity is taken as given.
-  ctx->regioned = dense && ctx->hcap_request == 0;
+  // Wedge contexts add every wedge (no closure test): a plain table of at
+  // least s_max / 0.6 slots.
+  const bool wedge = (ctx->flags & MAD_WEDGE) != 0;
+  ctx->regioned = dense && ctx->hcap_request == 0 && !wedge;
   uint64_t cap = ctx->hcap_request;
+  if (!cap && wedge) cap = wedge_hash_slots(s_max);
   ctx->hov = 0;
   if (ctx->regioned) {
     ctx->hov = ctx->hov_request ? ctx->hov_request : hash_overflow_slots(s_max);
@@ -308,8 +317,9 @@ extern "C" {
 mad_status mad_create(mad_ctx** out, uint32_t flags) {
   if (!out) return MAD_ERR_ARG;
   *out = nullptr;
-  if (flags & ~(uint32_t)(MAD_NONNEG | MAD_GRAM | MAD_EXCLUDE_DIAG | MAD_SQUARE_SYM))
+  if (flags & ~(uint32_t)(MAD_NONNEG | MAD_GRAM | MAD_EXCLUDE_DIAG | MAD_SQUARE_SYM | MAD_WEDGE))
     return MAD_ERR_ARG;
+  if ((flags & MAD_WEDGE) && (flags & MAD_SQUARE_SYM)) return MAD_ERR_ARG;
   mad_ctx* ctx = new (std::nothrow) mad_ctx();
   if (!ctx) return MAD_ERR_OOM;
   ctx->flags = flags;
@@ -407,6 +417,17 @@ mad_status mad_debug_set_hash_layout(mad_ctx* ctx, float region_factor, uint64_t
   return MAD_OK;
 }
 
+// Wedge contexts: the wedge tables after the diamond tables, and the table
+// scalars mad_stats reports (||w||_1 = TK's total / 2^EK in place of
+// ||W||_1).
+mad_status finish_wedge_build(mad_ctx* ctx, cudaStream_t st) {
+  mad_status rs = build_wedge_tables(ctx, st);
+  if (rs != MAD_OK) return rs;
+  ctx->t1_total = ctx->tk_total;
+  ctx->e1 = ctx->ek;
+  return MAD_OK;
+}
+
 mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B,
                             uint64_t s_max, mad_stream stream) {
   if (!ctx) return MAD_ERR_ARG;
@@ -415,13 +436,15 @@ mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   mad_status rs = check_inputs(ctx, A, B, s_max, &dense);
   if (rs != MAD_OK) return rs;
   if ((rs = alloc_tables(ctx, A, B, s_max, dense, st)) != MAD_OK) return rs;
+  const bool wedge = (ctx->flags & MAD_WEDGE) != 0;
   if (dense) {
     if ((rs = enqueue_dense_build(ctx, st)) != MAD_OK) return rs;
     if ((rs = finish_dense_build(ctx, st)) != MAD_OK) return rs;
+    if (wedge && (rs = finish_wedge_build(ctx, st)) != MAD_OK) return rs;
     ctx->built = true;
     return MAD_OK;
   }
-  const bool pilot = ctx->hcap_request == 0;
+  const bool pilot = ctx->hcap_request == 0 && !wedge;
   cudaMemsetAsync(ctx->sc, 0, sizeof(DevScalars), st);
   if ((rs = build_tables_impl(ctx, st)) != MAD_OK) return rs;
   DevScalars hs;
@@ -469,6 +492,7 @@ mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
     if ((rs = alloc(ctx, ctx->hvals, cap, st)) != MAD_OK) return rs;
   }
   if ((rs = clear_hash(ctx, st)) != MAD_OK) return rs;
+  if (wedge && (rs = finish_wedge_build(ctx, st)) != MAD_OK) return rs;
   ctx->built = true;
   return MAD_OK;
 }
@@ -663,6 +687,10 @@ mad_status mad_export_table(mad_ctx* ctx, int which, void* out_dev, uint64_t cap
     case 4: src = ctx->na; count = ctx->na ? (uint64_t)ctx->m : 0; break;
     case 5: src = ctx->nb; count = ctx->nb ? (uint64_t)ctx->d : 0; break;
     case 6: src = ctx->r; count = ctx->r ? (uint64_t)ctx->m : 0; break;
+    case 7: src = ctx->TK ? ctx->TK + ctx->TK_shift : nullptr; elem = 8;
+            count = ctx->TK ? (uint64_t)ctx->d : 0; break;
+    case 8: src = ctx->TAc; count = ctx->TAc ? (uint64_t)(ctx->m * ctx->d) : 0; break;
+    case 9: src = ctx->nac; count = ctx->nac ? (uint64_t)ctx->d : 0; break;
     default: return MAD_ERR_ARG;
   }
   *n_host = count;

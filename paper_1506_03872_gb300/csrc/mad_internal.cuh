@@ -160,6 +160,15 @@ struct mad_ctx {
   uint32_t* TBg = nullptr;                // guides of the TB rows (fixed row stride)
   int64_t tbg_stride = 0;
   uint8_t* TBg_sh = nullptr;
+  // Wedge sampling (MAD_WEDGE): the centre table TK over k (its inclusive
+  // prefix starts at TK + TK_shift), its total and scale exponent, the
+  // column norms of A and, for dense non-Gram inputs, the column tables.
+  unsigned long long* TK = nullptr;
+  int TK_shift = 0;
+  unsigned long long tk_total = 0;
+  int ek = 0;
+  float* nac = nullptr;
+  uint32_t* TAc = nullptr;
   // Fused pass (mad_pipeline_*): budgets fixed when planned, one buffer
   // for its selection lists.
   bool pipe = false;
@@ -352,6 +361,16 @@ mad_status export_x_by_owner(mad_ctx* ctx, uint32_t world, uint64_t* keys, int64
                              uint64_t cap, uint64_t* offsets_host, cudaStream_t st);
 mad_status select_pairs(mad_ctx* ctx, const mad_pair* pairs, uint64_t n, uint64_t K,
                         mad_pair* out, uint64_t* n_sel, cudaStream_t st);
+// wedge.cu: wedge sampling (MAD_WEDGE contexts): the plain hash's slots for
+// s_max wedges, the centre and column tables (after the diamond tables;
+// synchronises), the sampling loop and its diagnostic draws.
+uint64_t wedge_hash_slots(uint64_t s_max);
+mad_status build_wedge_tables(mad_ctx* ctx, cudaStream_t st);
+mad_status wedge_sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first,
+                             cudaStream_t st);
+mad_status wedge_draws_impl(mad_ctx* ctx, uint64_t seed, uint64_t first, const uint64_t* ells,
+                            uint64_t count, uint32_t* oi, uint32_t* ok, uint32_t* oj,
+                            uint32_t* okp, int64_t* ov, cudaStream_t st);
 // sample.cu: (key, value) pairs added to X.
 mad_status accumulate_pairs(mad_ctx* ctx, const uint64_t* keys, const int64_t* vals, uint64_t n,
                             cudaStream_t st);

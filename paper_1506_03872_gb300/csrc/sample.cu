@@ -862,6 +862,7 @@ bool x_builder_applies(const mad_ctx* ctx, uint64_t s) {
 mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, cudaStream_t st,
                        bool fresh_x) {
   if (s == 0) return MAD_OK;
+  if (ctx->flags & MAD_WEDGE) return wedge_sample_impl(ctx, s, seed, first, st);
   const SampleParams p = make_params(ctx);
   if (!ctx->dense) {
     phase_event(ctx, 0, st);
@@ -973,6 +974,8 @@ mad_status debug_draws_impl(mad_ctx* ctx, uint64_t seed, uint64_t first, const u
                             uint64_t count, uint32_t* oi, uint32_t* ok, uint32_t* oj,
                             uint32_t* okp, int64_t* ov, cudaStream_t st) {
   if (count == 0) return MAD_OK;
+  if (ctx->flags & MAD_WEDGE)
+    return wedge_draws_impl(ctx, seed, first, ells, count, oi, ok, oj, okp, ov, st);
   const SampleParams p = make_params(ctx);
   const unsigned long long blocks = (count + 255) / 256;
   k_draws<<<(unsigned)(blocks < 152 * 8 ? blocks : 152 * 8), 256, 0, st>>>(
