@@ -790,6 +790,13 @@ def chung_lu_leg(args, dev, stream, flush, peak, peak_kind):
                                        counts, flush, cap, args.ladder_seeds, stream, 1.0)
     ctx_sq.close()
 
+    # Wedge sampling (the paper's comparison, Sec. 6.3) on the same graph:
+    # its own time to recall 0.95, up to the memory cap.
+    ctx_w = mad.Context(w.flags | 16)
+    leg["ladder_wedge"] = _ladder(lambda s_, seed_: step(s_, seed_, ctx_w), w, set(), tau,
+                                  counts, flush, cap, args.ladder_seeds, stream, 0.0)
+    ctx_w.close()
+
     # Exact sparse comparator (degree-bounded row-block product).
     comp = {}
     out_x = mad.new_pairs(w.t)
@@ -815,6 +822,8 @@ def chung_lu_leg(args, dev, stream, flush, peak, peak_kind):
     leg["time_to_top_t"] = {"recall_target": 0.95, "sampling_ms": lad.get("ms"),
                             "sampling_s": lad.get("s"), "sampling_recall": lad.get("recall"),
                             "sampling_square_sym_ms": leg["ladder_square_sym"].get("ms"),
+                            "wedge_ms": leg["ladder_wedge"].get("ms"),
+                            "wedge_s": leg["ladder_wedge"].get("s"),
                             "comparator_ms": comp["ms"], "comparator_recall": r_x}
     if not args.no_probes:
         probes = run_probes(mad, dev, stream, gather_bytes=sparse_table_bytes(w),
@@ -882,10 +891,13 @@ def run_budget(args):
 
 
 def run_batched_queries(args):
-    """Batched queries (one graph-captured batch per step)."""
+    """Batched queries: the launch shape picked by the autotuner
+    (paper_1506_03872_gb300/autotune.py), then one graph-captured batch per
+    step under the library's default shape and under the tuned one."""
     import torch
 
     import paper_1506_03872_gb300 as mad
+    from paper_1506_03872_gb300 import autotune
     from paper_1506_03872_gb300 import build as _build
     _build.build()
     from paper_1506_03872_gb300.workloads import batched_queries
@@ -900,32 +912,40 @@ def run_batched_queries(args):
     t0 = time.perf_counter()
     mad.mad_mips_items(ctx.ctx, mad.dense(tB), w.meta["s_max"])
     items_s = time.perf_counter() - t0
-    mad.mad_mips_plan(ctx.ctx, s_q, w.tprime, w.t)
+    tuned = autotune.tune_mips(ctx.ctx, tQ, w.d, w.n, s_q, w.tprime, w.t, w.sampler_seed,
+                               use_cache=not args.retune,
+                               log=lambda m: print(m, file=sys.stderr, flush=True))
     out = mad.new_pairs(w.m * w.t)
     nout = torch.zeros(w.m, dtype=torch.int32, device=dev)
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        for _ in range(args.warmup):
-            mad.mad_mips_run(ctx.ctx, mad.dense(tQ), w.sampler_seed, out, nout)
-    torch.cuda.current_stream().wait_stream(side)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        mad.mad_mips_run(ctx.ctx, mad.dense(tQ), w.sampler_seed, out, nout)
     stream = torch.cuda.current_stream()
-    launches0 = mad.mad_stats(ctx.ctx)["launches"]
+
+    def timed_graph(cfg):
+        mad.mad_mips_config(ctx.ctx, **cfg)
+        mad.mad_mips_plan(ctx.ctx, s_q, w.tprime, w.t)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(args.warmup):
+                mad.mad_mips_run(ctx.ctx, mad.dense(tQ), w.sampler_seed, out, nout)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            mad.mad_mips_run(ctx.ctx, mad.dense(tQ), w.sampler_seed, out, nout)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps, out.cpu().numpy().copy()
+
     clocks = ClockSampler(0)
     clocks.start()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        graph.replay()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms_default, res_default = timed_graph(autotune.DEFAULT)
+    ms, res_tuned = timed_graph(tuned["best"])
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
     diamonds = int(s_q.sum())
     st = mad.mad_stats(ctx.ctx)
     recall = None
@@ -948,6 +968,11 @@ def run_batched_queries(args):
                    "t": w.t, "tprime": w.tprime, "graph": "one CUDA graph replay per step",
                    "l2": "inputs and hash regions above L2"},
         "queries_per_s": round(w.m / (ms / 1e3), 1),
+        "default_shape": {"ms_per_step": round(ms_default, 3),
+                          "queries_per_s": round(w.m / (ms_default / 1e3), 1)},
+        "tuned_shape": {"shape": tuned["best"], "cached": tuned["cached"],
+                        "trials": len(tuned["trials"]),
+                        "results_equal_default": bool(np.array_equal(res_tuned, res_default))},
         "recall_top_t": recall,
         "item_tables_s": round(items_s, 3),
         # per replay: the query-row tables, the sampler, the per-query select
@@ -1132,6 +1157,8 @@ def main():
     ap.add_argument("--square-sym", action="store_true",
                     help="0/1 Gram workloads: the squared-symmetric update of Sec. 3.2.3")
     ap.add_argument("--no-probes", action="store_true", help="skip the gather/atomic probes")
+    ap.add_argument("--retune", action="store_true",
+                    help="batched queries: search the launch shape again (ignore the cache)")
     ap.add_argument("--no-sparse", action="store_true",
                     help="skip the sparse common-neighbours leg of the default run")
     ap.add_argument("--rescore", type=int, default=0,

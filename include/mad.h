@@ -318,6 +318,17 @@ mad_status mad_sparse_topt(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* 
  * the selection threshold exceed 4096 (ties of x in the thousands) reports
  * MAD_ERR_STATE through the device error word (read by mad_stats). */
 mad_status mad_mips_items(mad_ctx* ctx, const mad_matrix* B, uint64_t s_max, mad_stream stream);
+/* mad_mips_config (the paper has no counterpart; used by the package's
+ * autotuner, paper_1506_03872_gb300/autotune.py): the launch shape of the
+ * next mad_mips_plan and mad_mips_run.  region_lg: each query's region is
+ * the power of two >= 2^region_lg s_q slots (1..4; 0: 1); chunk_mult: 256
+ * x chunk_mult diamonds per chunk (1, 2, 4, 8; 0: 1); blocks_per_sm:
+ * sampler blocks per SM (0: as many as fit, at most 8); select_threads:
+ * threads of each query's selection (128, 256, 512; 0: 256).  None of
+ * these changes a result (the keys and sums of X, Omega_t' and Omega_t are
+ * the same): only the time.  MAD_ERR_ARG outside these values. */
+mad_status mad_mips_config(mad_ctx* ctx, uint32_t region_lg, uint32_t chunk_mult,
+                           uint32_t blocks_per_sm, uint32_t select_threads);
 mad_status mad_mips_plan(mad_ctx* ctx, uint32_t nq, const uint64_t* s_host, uint32_t tprime,
                          uint32_t t, mad_stream stream);
 mad_status mad_mips_run(mad_ctx* ctx, const mad_matrix* Q, uint64_t seed, mad_pair* out_dev,

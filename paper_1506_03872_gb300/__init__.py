@@ -37,7 +37,7 @@ EXPORTS = (
     "mad_mips_plan", "mad_mips_run", "mad_budget_features", "mad_mlp_train", "mad_mlp_predict",
     "mad_pipeline_plan", "mad_pipeline_run", "mad_pipeline_status", "mad_sparse_topt",
     "mad_probe_gather", "mad_probe_atomics", "mad_export_x_by_owner", "mad_accumulate",
-    "mad_select_pairs",
+    "mad_select_pairs", "mad_mips_config",
 )
 MAD_BUDGET_FEATURES = 12
 MAD_MLP_HIDDEN = 64
@@ -96,6 +96,7 @@ def lib() -> ctypes.CDLL:
         L.mad_set_phase_events.argtypes = [P, ctypes.POINTER(P), u32]
         L.mad_mips_items.argtypes = [P, ctypes.POINTER(mad_matrix), u64, P]
         L.mad_mips_plan.argtypes = [P, u32, ctypes.POINTER(u64), u32, u32, P]
+        L.mad_mips_config.argtypes = [P, u32, u32, u32, u32]
         L.mad_mips_run.argtypes = [P, ctypes.POINTER(mad_matrix), u64, P, P, P, P]
         L.mad_budget_features.argtypes = [P, P, P]
         L.mad_mlp_train.argtypes = [P, P, P, P, u32, u32, u32, ctypes.c_float, ctypes.c_float, P,
@@ -365,6 +366,13 @@ def mad_probe_atomics(table, count: int, mode: int = 0, seed: int = 1, sink=None
 def mad_mips_items(ctx, B: mad_matrix, s_max: int, stream=None) -> None:
     """Item-side tables for batched queries (B: d x n dense F32)."""
     _check(lib().mad_mips_items(ctx, ctypes.byref(B), s_max, _stream(stream)), "mad_mips_items")
+
+
+def mad_mips_config(ctx, region_lg: int = 0, chunk_mult: int = 0, blocks_per_sm: int = 0,
+                    select_threads: int = 0) -> None:
+    """Launch shape of the next batch plan and run (0: the default)."""
+    _check(lib().mad_mips_config(ctx, region_lg, chunk_mult, blocks_per_sm, select_threads),
+           "mad_mips_config")
 
 
 def mad_mips_plan(ctx, s_per_query, tprime: int, t: int, stream=None) -> None:

@@ -187,6 +187,15 @@ struct mad_ctx {
   unsigned long long* mips_s = nullptr;   // nq budgets
   uint32_t* mips_chunk_q = nullptr;       // query of each 256-diamond chunk
   uint32_t* mips_chunk_l0 = nullptr;      // its first diamond
+  // Launch shape of batched queries (mad_mips_config): region size factor
+  // 2^mips_region_lg, 256 x mips_chunk_mult diamonds per chunk (the plan's
+  // value in mips_plan_mult), sampler blocks per SM (0: as many as fit),
+  // select threads per query.
+  int mips_region_lg = 1;
+  int mips_chunk_mult = 1;
+  int mips_plan_mult = 1;
+  int mips_bps = 0;
+  int mips_select_threads = 256;
   void* bt = nullptr;               // dense B^T (n x d), the input dtype
   unsigned long long* hkeys = nullptr;
   long long* hvals = nullptr;

@@ -44,13 +44,16 @@ __device__ __forceinline__ int region_add(const SampleParams& p, uint32_t q,
 __global__ void __launch_bounds__(256, 4)
 k_mips_sample(const SampleParams p, unsigned long long seed, const uint32_t* __restrict__ chunk_q,
               const uint32_t* __restrict__ chunk_l0, const unsigned long long* __restrict__ s_q,
-              unsigned long long nchunks) {
+              unsigned long long nchunks, int mult) {
   bool bad = false, full = false;
   unsigned long long inserted = 0, created = 0;
   for (unsigned long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const uint32_t q = __ldg(chunk_q + c);
-    const unsigned long long l = (unsigned long long)__ldg(chunk_l0 + c) + threadIdx.x;
-    if (l < __ldg(s_q + q)) {
+    const unsigned long long sq = __ldg(s_q + q);
+    for (int rep = 0; rep < mult; ++rep) {
+      const unsigned long long l =
+          (unsigned long long)__ldg(chunk_l0 + c) + threadIdx.x + (unsigned long long)rep * kChunk;
+      if (l >= sq) break;
       const Uniforms u = diamond_uniforms(seed + q, l);
       const Draw dr = draw_given_row(p, u, (int64_t)q, &bad);
       if (dr.v != 0) {
@@ -117,7 +120,7 @@ __device__ __forceinline__ uint32_t fine_of(unsigned long long v, uint32_t b) {
 // top t', and few more) is collected and sorted.  Then c = q . b_j in FP64
 // (32 lane-strided fused multiply-add partial sums folded in halves) and the
 // t largest |c| by (|c| desc, key asc).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_mips_select(const unsigned long long* __restrict__ hkeys, const long long* __restrict__ hvals,
               const unsigned long long* __restrict__ hreg, const float* __restrict__ Q,
               int64_t ldq, const float* __restrict__ Bt, int64_t d, uint32_t tprime, uint32_t t,
@@ -264,13 +267,13 @@ k_mips_select(const unsigned long long* __restrict__ hkeys, const long long* __r
   if (threadIdx.x == 0) nout[q] = (uint32_t)T;
 }
 
-// Region of query q: a power of two >= max(4, 2 s_q) slots.
+// Region of query q: a power of two >= max(4, 2^lg s_q) slots.
 __global__ void __launch_bounds__(256)
-k_mips_region_sizes(const unsigned long long* __restrict__ s_q, uint32_t nq,
+k_mips_region_sizes(const unsigned long long* __restrict__ s_q, uint32_t nq, int lg,
                     unsigned long long* __restrict__ sizes) {
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
     unsigned long long size = 4;
-    while (size < 2 * s_q[q]) size <<= 1;
+    while (size < (s_q[q] << lg)) size <<= 1;
     sizes[q] = size;
   }
 }
@@ -357,6 +360,21 @@ mad_status mad_mips_items(mad_ctx* ctx, const mad_matrix* B, uint64_t s_max, mad
   return cuda_status(cudaStreamSynchronize(st));
 }
 
+mad_status mad_mips_config(mad_ctx* ctx, uint32_t region_lg, uint32_t chunk_mult,
+                           uint32_t blocks_per_sm, uint32_t select_threads) {
+  if (!ctx || region_lg > 4 || blocks_per_sm > 8) return MAD_ERR_ARG;
+  if (chunk_mult != 0 && chunk_mult != 1 && chunk_mult != 2 && chunk_mult != 4 && chunk_mult != 8)
+    return MAD_ERR_ARG;
+  if (select_threads != 0 && select_threads != 128 && select_threads != 256 &&
+      select_threads != 512)
+    return MAD_ERR_ARG;
+  ctx->mips_region_lg = region_lg == 0 ? 1 : (int)region_lg;
+  ctx->mips_chunk_mult = chunk_mult == 0 ? 1 : (int)chunk_mult;
+  ctx->mips_bps = (int)blocks_per_sm;
+  ctx->mips_select_threads = select_threads == 0 ? 256 : (int)select_threads;
+  return MAD_OK;
+}
+
 mad_status mad_mips_plan(mad_ctx* ctx, uint32_t nq, const uint64_t* s_host, uint32_t tprime,
                          uint32_t t, mad_stream stream) {
   if (!ctx || !s_host || nq == 0 || tprime == 0 || tprime > (uint32_t)kTPrimeMax || t == 0 ||
@@ -366,14 +384,15 @@ mad_status mad_mips_plan(mad_ctx* ctx, uint32_t nq, const uint64_t* s_host, uint
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<uint32_t> cq, cl;
   uint64_t chunks = 0;
+  const uint64_t csize = (uint64_t)kChunk * (uint64_t)ctx->mips_chunk_mult;
   for (uint32_t q = 0; q < nq; ++q) {
     if (s_host[q] == 0 || s_host[q] > ctx->s_max) return MAD_ERR_ARG;
-    chunks += (s_host[q] + kChunk - 1) / kChunk;
+    chunks += (s_host[q] + csize - 1) / csize;
   }
   cq.reserve(chunks);
   cl.reserve(chunks);
   for (uint32_t q = 0; q < nq; ++q)
-    for (uint64_t l = 0; l < s_host[q]; l += kChunk) {
+    for (uint64_t l = 0; l < s_host[q]; l += csize) {
       cq.push_back(q);
       cl.push_back((uint32_t)l);
     }
@@ -400,7 +419,8 @@ mad_status mad_mips_plan(mad_ctx* ctx, uint32_t nq, const uint64_t* s_host, uint
   if ((rs = ensure_scratch(ctx, sizes_bytes + scan_partial_elems(nq) * 8, st)) != MAD_OK) return rs;
   unsigned long long* sizes = (unsigned long long*)ctx->scratch;
   uint64_t* part = (uint64_t*)((char*)ctx->scratch + sizes_bytes);
-  k_mips_region_sizes<<<(nq + 255) / 256, 256, 0, st>>>(ctx->mips_s, nq, sizes);
+  k_mips_region_sizes<<<(nq + 255) / 256, 256, 0, st>>>(ctx->mips_s, nq, ctx->mips_region_lg,
+                                                       sizes);
   count_launch(ctx);
   if ((rs = scan_exclusive_u64(ctx, (const uint64_t*)sizes, (uint64_t*)ctx->hreg, nq, part, st)) !=
       MAD_OK)
@@ -416,6 +436,7 @@ mad_status mad_mips_plan(mad_ctx* ctx, uint32_t nq, const uint64_t* s_host, uint
   ctx->mips_tprime = tprime;
   ctx->mips_t = t;
   ctx->mips_chunks = chunks;
+  ctx->mips_plan_mult = ctx->mips_chunk_mult;
   if (cudaFuncSetAttribute(k_mips_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)select_smem_bytes()) != cudaSuccess)
     return MAD_ERR_CUDA;
@@ -444,11 +465,13 @@ mad_status mad_mips_run(mad_ctx* ctx, const mad_matrix* Q, uint64_t seed, mad_pa
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mips_sample, 256, 0) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
+  if (ctx->mips_bps > 0 && ctx->mips_bps < per_sm) per_sm = ctx->mips_bps;
   const unsigned long long grid =
       std::min<unsigned long long>(ctx->mips_chunks, (unsigned long long)sms * per_sm);
   k_mips_sample<<<(unsigned)grid, 256, 0, st>>>(p, seed, ctx->mips_chunk_q, ctx->mips_chunk_l0,
-                                                ctx->mips_s, ctx->mips_chunks);
-  k_mips_select<<<ctx->mips_nq, 256, select_smem_bytes(), st>>>(
+                                                ctx->mips_s, ctx->mips_chunks,
+                                                ctx->mips_plan_mult);
+  k_mips_select<<<ctx->mips_nq, ctx->mips_select_threads, select_smem_bytes(), st>>>(
       ctx->hkeys, ctx->hvals, ctx->hreg, (const float*)Q->values, Q->ld, (const float*)ctx->bt,
       ctx->d, ctx->mips_tprime, ctx->mips_t, out_dev, n_out_dev, cand_dev, ctx->sc);
   count_launch(ctx, 2);

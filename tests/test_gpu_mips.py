@@ -101,3 +101,54 @@ def test_batch_limits(batch):
         with pytest.raises(mad.MadError) as e:
             mad.mad_mips_plan(c.ctx, np.array([s_max + 1], dtype=np.uint64), 10, 5)
         assert e.value.status == mad.MAD_ERR_ARG
+
+
+@pytest.mark.parametrize("cfg", [dict(region_lg=2, chunk_mult=4, blocks_per_sm=2,
+                                      select_threads=128),
+                                 dict(region_lg=1, chunk_mult=2, blocks_per_sm=3,
+                                      select_threads=512),
+                                 dict(chunk_mult=8, select_threads=256)])
+def test_launch_shapes_give_the_same_results(batch, cfg):
+    """mad_mips_config changes the time only: every launch shape returns the
+    default shape's candidates and results bit for bit."""
+    import paper_1506_03872_gb300 as mad
+    w, s_q, s_max, ctx, (tQ, tB), out0, nout0, cand0, _ = batch
+    try:
+        mad.mad_mips_config(ctx.ctx, **cfg)
+        mad.mad_mips_plan(ctx.ctx, s_q, w.tprime, w.t)
+        out = mad.new_pairs(w.m * w.t)
+        nout = torch.zeros(w.m, dtype=torch.int32, device="cuda")
+        cand = mad.new_pairs(w.m * w.tprime)
+        mad.mad_mips_run(ctx.ctx, mad.dense(tQ), w.sampler_seed, out, nout, cand)
+        torch.cuda.synchronize()
+        assert np.array_equal(nout.cpu().numpy(), nout0)
+        assert np.array_equal(out.cpu().numpy(), out0)
+        assert np.array_equal(cand.cpu().numpy(), cand0)
+        assert mad.mad_stats(ctx.ctx)["device_error"] == 0
+    finally:
+        mad.mad_mips_config(ctx.ctx)
+        mad.mad_mips_plan(ctx.ctx, s_q, w.tprime, w.t)
+
+
+def test_autotuner_picks_a_shape_and_caches_it(batch, tmp_path, monkeypatch):
+    import paper_1506_03872_gb300 as mad
+    from paper_1506_03872_gb300 import autotune
+    w, s_q, s_max, ctx, (tQ, tB), out0, nout0, cand0, _ = batch
+    monkeypatch.setenv("MAD_TUNE_CACHE", str(tmp_path / "tuned.json"))
+    try:
+        res = autotune.tune_mips(ctx.ctx, tQ, w.d, w.n, s_q, w.tprime, w.t, w.sampler_seed,
+                                 reps=1)
+        assert res["cached"] is False and res["ms"] <= res["default_ms"]
+        assert set(res["best"]) == set(autotune.DEFAULT) and len(res["trials"]) >= 5
+        out = mad.new_pairs(w.m * w.t)
+        nout = torch.zeros(w.m, dtype=torch.int32, device="cuda")
+        mad.mad_mips_run(ctx.ctx, mad.dense(tQ), w.sampler_seed, out, nout)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), out0)
+        again = autotune.tune_mips(ctx.ctx, tQ, w.d, w.n, s_q, w.tprime, w.t, w.sampler_seed)
+        assert again["cached"] is True and again["best"] == res["best"]
+        with pytest.raises(mad.MadError):
+            mad.mad_mips_config(ctx.ctx, chunk_mult=3)
+    finally:
+        mad.mad_mips_config(ctx.ctx)
+        mad.mad_mips_plan(ctx.ctx, s_q, w.tprime, w.t)
