@@ -394,6 +394,30 @@ def test_squared_symmetric_expectation_exact():
     assert np.allclose(ex[iu] * w1, 4.0 * C[iu] ** 2, rtol=1e-12, atol=1e-12)
 
 
+def test_squared_symmetric_expectation_dense():
+    """Sec. 3.2.3 on a dense symmetric matrix with mixed signs: a diamond of
+    (i, j) through (k, k') is one of (k, k') through (i, j) with the same
+    sign product, so the unordered-pair score per sample is again
+    4 c_ab^2 / ||W||_1 (x in units of 2^-F), up to the tables' rounding."""
+    rng = _rng(34)
+    S = rng.standard_normal((5, 5))
+    S = S + S.T
+    S[1, 3] = S[3, 1] = 0.0
+    o = _dense(S, S.copy(), flags=2 | 4 | 8)
+    F = o.scalars()["F"]
+    i, k, j, kp, prob, v = o.enumerate()
+    ex = np.zeros((5, 5))
+    for a, b in ((i, j), (k, kp)):
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        off = lo != hi
+        np.add.at(ex, (lo[off], hi[off]), prob[off] * v[off].astype(np.float64) * 2.0 ** -F)
+    C = S @ S
+    iu = np.triu_indices(5, 1)
+    ref = 4.0 * C[iu] ** 2 / _w1_closed_form(S, S)
+    assert np.max(np.abs(ex[iu] - ref)) < 2e-5 * ref.max()
+    assert np.all(ex[np.tril_indices(5)] == 0.0)
+
+
 def test_squared_symmetric_counts_and_flag_rule():
     """One draw of the sampler adds to at most two pairs: X from sampling
     equals the sum over the drawn diamonds of the two additions (checked
