@@ -171,8 +171,10 @@ mad_status check_inputs(const mad_ctx* ctx, const mad_matrix* A, const mad_matri
   } else {
     return MAD_ERR_UNSUPPORTED;
   }
-  // The squared symmetric update (Sec. 3.2.3) is built for 0/1 Gram inputs.
-  if ((ctx->flags & MAD_SQUARE_SYM) && (!csr || !(ctx->flags & MAD_GRAM)))
+  // The squared symmetric update (Sec. 3.2.3) needs B = A^T = A: Gram
+  // inputs, and square ones when dense (the caller guarantees symmetry).
+  if ((ctx->flags & MAD_SQUARE_SYM) &&
+      (!(ctx->flags & MAD_GRAM) || (!csr && A->rows != A->cols)))
     return MAD_ERR_UNSUPPORTED;
   *dense_out = dense;
   return MAD_OK;

@@ -284,12 +284,14 @@ k_sort_scatter(const DevScalars* __restrict__ sc, unsigned long long seed,
 
 // Diamonds in row order (dense inputs): order[q] = l - first.  Draws only:
 // diamond q's hash key goes to keys[q] (EMPTY_KEY when it adds nothing:
-// v = 0 or an excluded diagonal) and its increment to vals[q].  k_insert
-// adds them to X.
+// v = 0 or an excluded diagonal) and its increment to vals[q].  Under
+// MAD_SQUARE_SYM the same increment for the pair (k, k') goes to keys[s +
+// q] and vals[s + q] (Sec. 3.2.3).  k_insert adds them to X.
 __global__ void __launch_bounds__(256, 6)
 k_sample_sorted(const SampleParams p_, unsigned long long seed, unsigned long long first,
                 unsigned long long s, const uint32_t* __restrict__ order,
                 unsigned long long* __restrict__ keys, long long* __restrict__ vals) {
+  const bool sqsym = (p_.flags & MAD_SQUARE_SYM) != 0;
   const SampleParams p = resolve(p_);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   bool bad = false;
@@ -312,6 +314,17 @@ k_sample_sorted(const SampleParams p_, unsigned long long seed, unsigned long lo
     }
     keys[q] = key;
     vals[q] = dr.v;
+    if (sqsym) {
+      unsigned long long key2 = EMPTY_KEY;
+      if ((p.flags & MAD_EXCLUDE_DIAG) && dr.k == dr.kp) {
+        ++diag;
+      } else if (dr.v != 0) {
+        const uint32_t a = dr.k < dr.kp ? dr.k : dr.kp, b = dr.k < dr.kp ? dr.kp : dr.k;
+        key2 = ((unsigned long long)a << 32) | b;
+      }
+      keys[s + q] = key2;
+      vals[s + q] = dr.v;
+    }
   }
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) diag += __shfl_xor_sync(0xFFFFFFFFu, diag, off);
@@ -817,7 +830,8 @@ struct SortScratch {
   size_t bytes;
 };
 
-SortScratch carve_sort(void* p, uint64_t nbk, int blocks, uint64_t batch) {
+// recs: records per diamond (2 under MAD_SQUARE_SYM).
+SortScratch carve_sort(void* p, uint64_t nbk, int blocks, uint64_t batch, int recs) {
   SortScratch c;
   char* b = (char*)p;
   size_t off = 0;
@@ -831,8 +845,8 @@ SortScratch carve_sort(void* p, uint64_t nbk, int blocks, uint64_t batch) {
   c.base = (unsigned int*)take((nbk + 1) * sizeof(unsigned int));
   c.part = (unsigned int*)take(scan_partial_elems(nbk) * sizeof(unsigned int));
   c.order = (uint32_t*)take(batch * sizeof(uint32_t));
-  c.keys = (unsigned long long*)take(batch * sizeof(unsigned long long));
-  c.vals = (long long*)take(batch * sizeof(long long));
+  c.keys = (unsigned long long*)take(batch * recs * sizeof(unsigned long long));
+  c.vals = (long long*)take(batch * recs * sizeof(long long));
   c.R = (uint32_t*)take((nbk + 1) * sizeof(uint32_t));
   c.heavy = (unsigned char*)take(nbk);
   c.qend = (uint32_t*)take(nbk * sizeof(uint32_t));
@@ -840,10 +854,12 @@ SortScratch carve_sort(void* p, uint64_t nbk, int blocks, uint64_t batch) {
   return c;
 }
 
+int sort_records(const mad_ctx* ctx) { return (ctx->flags & MAD_SQUARE_SYM) ? 2 : 1; }
+
 size_t sample_scratch_bytes(const mad_ctx* ctx, uint64_t s) {
   if (!ctx->dense || s == 0) return 0;
   const uint64_t batch = s < kSortBatch ? s : kSortBatch;
-  return carve_sort(nullptr, sort_buckets(ctx->m), sort_blocks(), batch).bytes;
+  return carve_sort(nullptr, sort_buckets(ctx->m), sort_blocks(), batch, sort_records(ctx)).bytes;
 }
 
 // Buckets per group of the X builder: about 640 diamonds of s_max per group
@@ -909,7 +925,7 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
   }
   mad_status rs = ensure_scratch(ctx, sample_scratch_bytes(ctx, s), st);
   if (rs != MAD_OK) return rs;
-  const SortScratch w = carve_sort(ctx->scratch, nbk, blocks, batch);
+  const SortScratch w = carve_sort(ctx->scratch, nbk, blocks, batch, sort_records(ctx));
   for (uint64_t done = 0; done < s; done += batch) {
     const uint64_t n = (s - done) < batch ? (s - done) : batch;
     phase_event(ctx, 0, st);
@@ -952,7 +968,8 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
                                                            w.R, w.heavy, w.qend);
       count_launch(ctx, 2);
     } else {
-      k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, w.keys, w.vals, n);
+      k_insert<<<grid_of(n, full_insert), 256, 0, st>>>(p, w.keys, w.vals,
+                                                        n * (uint64_t)sort_records(ctx));
       count_launch(ctx);
     }
     phase_event(ctx, 3, st);

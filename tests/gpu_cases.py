@@ -61,6 +61,12 @@ def case_inputs(name: str):
         rng = _rng(45)
         A = rng.standard_normal((400, 30))
         return "dense", (A, np.ascontiguousarray(A.T)), 2 | 4
+    if name == "dense_square_sym":          # Sec. 3.2.3 on dense A = A^T = B
+        rng = _rng(47)
+        S = rng.standard_normal((350, 350))
+        S = (S + S.T).astype(np.float32)
+        S[np.abs(S) < 0.3] = 0.0
+        return "dense", (S, S.copy()), 2 | 4 | 8
     if name == "chung_lu_small":
         w = W.chung_lu(nodes=5000, edges=40000, seed=9)
         return "csr", (w.rowptr, w.colidx, w.m), w.flags

@@ -17,7 +17,7 @@ from gpu_cases import Case  # noqa: E402
 
 CASES = ["plain_small", "dense_ragged_f32", "dense_wide_rows", "dense_deep", "dense_factors_small",
          "dense_mixed_signs_zeros",
-         "dense_nonneg", "gram_dense", "chung_lu_small", "bipartite_binary", "chung_lu_square_sym"]
+         "dense_nonneg", "gram_dense", "dense_square_sym", "chung_lu_small", "bipartite_binary", "chung_lu_square_sym"]
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -121,6 +121,25 @@ def test_gram_pass_matches_oracle():
         _check(mad, out, counts, cand, _oracle_pass(A, B, flags, s, seed, tprime, t))
 
 
+def test_square_sym_pass_matches_oracle():
+    """The fused pass with the squared symmetric update (Sec. 3.2.3) on a
+    dense symmetric matrix: two records per diamond reach X."""
+    import paper_1506_03872_gb300 as mad
+    rng = _rng(66)
+    S = rng.standard_normal((500, 500))
+    S = (S + S.T).astype(np.float32)
+    S[np.abs(S) < 0.4] = 0.0
+    flags, s, seed, tprime, t = 2 | 4 | 8, 150_000, 4, 900, 30
+    tA, tB = torch.from_numpy(S).cuda(), torch.from_numpy(S.copy()).cuda()
+    with mad.Context(flags) as c:
+        mad.mad_pipeline_plan(c.ctx, mad.dense(tA), mad.dense(tB), s, tprime, t)
+        out, cand = mad.new_pairs(t), mad.new_pairs(tprime)
+        counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+        mad.mad_pipeline_run(c.ctx, seed, out, counts, cand)
+        mad.mad_pipeline_status(c.ctx)
+        _check(mad, out, counts, cand, _oracle_pass(S, S.copy(), flags, s, seed, tprime, t))
+
+
 def test_graph_replay_on_new_inputs():
     """Captured once, replayed after the inputs' contents change: nothing of
     the first inputs may survive in host-side state."""
