@@ -250,16 +250,16 @@ mad_status mad_pipeline_status(mad_ctx* ctx, mad_stream stream);
 
 /* Exact-computation comparator (Sec. 4.3) rebuilt for tensor cores: the t
  * pairs with the largest |a_i . b_j| by direct computation, for comparison
- * with diamond sampling.  A and B are cast to BF16 (K zero-padded to 64 or
- * 128), C~ = A B is computed with BF16 tensor-core MMAs accumulating in FP32,
+ * with diamond sampling.  A and B are cast to BF16 (K zero-padded to a
+ * multiple of 64), C~ = A B is computed with BF16 tensor-core MMAs accumulating in FP32,
  * the `rescore` largest |c~| (0 selects 8t) are kept by a threshold filter
  * fused into the GEMM (C~ is never stored), rescored exactly in FP32 (32
  * strided fused multiply-add partial sums folded in halves), and the t
  * largest |c| are written to out_dev sorted by (|c| desc, i asc, j asc) with
  * c as the FP32 value and x = 0.  BF16 rounding can reorder near-equal
  * products, so recall against the exact top t grows with `rescore`.
- * Dense A (m x d) and B (d x n), F32 or F64, d <= 128, 1 <= t <= rescore
- * <= 2048.  The context provides scratch only (no tables needed).
+ * Dense A (m x d) and B (d x n), F32 or F64, d <= 640, 1 <= t <= rescore
+ * <= 65536.  The context provides scratch only (no tables needed).
  * Synchronises the stream.  MAD_ERR_UNSUPPORTED outside these limits. */
 mad_status mad_dense_topt(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B, uint32_t t,
                           uint32_t rescore, mad_pair* out_dev, uint32_t* n_out_host,

@@ -596,8 +596,9 @@ mad_status mad_dense_topt(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B
   *n_out_host = 0;
   if (!valid_dense(A) || !valid_dense(B)) return MAD_ERR_UNSUPPORTED;
   if (B->rows != A->cols || A->rows >= (1ll << 31) || B->cols >= (1ll << 31)) return MAD_ERR_ARG;
-  if (rescore == 0) rescore = 8 * t;
-  if (A->cols > 128 || rescore < t || rescore > 2048) return MAD_ERR_UNSUPPORTED;
+  const uint64_t keep = rescore ? (uint64_t)rescore : 8ull * t;
+  if (A->cols > 640 || keep < t || keep > 65536) return MAD_ERR_UNSUPPORTED;
+  rescore = (uint32_t)keep;
   return dense_comparator(ctx, A, B, t, rescore, out_dev, n_out_host, nullptr,
                           (cudaStream_t)stream);
 }
@@ -607,7 +608,7 @@ mad_status mad_debug_dense_product(mad_ctx* ctx, const mad_matrix* A, const mad_
   if (!ctx || !A || !B || !c_dev) return MAD_ERR_ARG;
   if (!valid_dense(A) || !valid_dense(B)) return MAD_ERR_UNSUPPORTED;
   if (B->rows != A->cols || A->rows >= (1ll << 31) || B->cols >= (1ll << 31)) return MAD_ERR_ARG;
-  if (A->cols > 128) return MAD_ERR_UNSUPPORTED;
+  if (A->cols > 640) return MAD_ERR_UNSUPPORTED;
   uint32_t dummy = 0;
   return dense_comparator(ctx, A, B, 1, 1, nullptr, &dummy, c_dev, (cudaStream_t)stream);
 }

@@ -2,7 +2,7 @@
 // the top t of |A B| for dense A (m x d) and B (d x n).
 //
 // The paper streams dgemm column blocks through a priority queue.  Here:
-//  1. A and B^T are cast to BF16, K padded with zeros to 64 or 128.
+//  1. A and B^T are cast to BF16, K padded with zeros to a multiple of 64.
 //  2. One persistent kernel per SM computes C~ = A B tile by tile with
 //     tcgen05.mma (BF16 in, FP32 accumulate in TMEM), operands brought into
 //     shared memory by TMA (128-byte swizzle), and never writes C~: its
@@ -11,19 +11,26 @@
 //     recording half-row maxima, whose K_keep-th largest bounds the global
 //     K_keep-th largest from below) and rises whenever the buffer is
 //     compacted to its K_keep largest entries (the rescore budget, 8t by
-//     default) (a tile that overflows the buffer is
+//     default; the buffer lives in global memory and holds 4 K_keep
+//     entries, at least 4096) (a tile that overflows the buffer is
 //     rescanned from TMEM above the new theta); CTAs share theta
 //     through an atomicMax, so every kept threshold is a lower bound of the
 //     global K_keep-th largest |c~| and no entry of the global top K_keep is
 //     ever dropped.
 //  3. The K_keep largest |c~| of the merged buffers are rescored exactly in FP32
 //     and the t largest |c| returned.
-// Warp roles per CTA (320 threads): warp 0 issues TMA, warp 1 allocates TMEM
-// and issues the MMAs, warps 2-9 drain the accumulators (warp w reads TMEM
-// lane quarter w mod 4 and one half of the columns, four 32-column loads in
-// flight before one wait).  Two TMEM accumulators (2 x 256 columns) and two B stages
-// overlap loads, MMAs and the epilogue.  Every wait is bounded by a clock
-// limit after which the CTA sets an error flag and winds down.
+// Warp roles per CTA (352 threads): warp 0 takes work units from a global
+// counter (runs of column tiles of one row block, so CTAs whose tiles hold
+// many candidates take fewer) and issues TMA; warps 1 and 10 issue the MMAs
+// of the even and odd tiles into their own TMEM accumulator (warp 1 also
+// allocates the 2 x 256 TMEM columns); warps 2-9 drain the accumulators
+// (warp w reads TMEM lane quarter w mod 4 and one half of the columns) and
+// release a tile's accumulator as soon as none of their values passes the
+// threshold.  The A panel (128 rows x K) of a unit stays in shared memory;
+// B arrives one 256-column tile per stage for K <= 128 (3 stages), else one
+// 64-wide K slice per stage (32 KB; 3 stages for K = 512, 2 for K = 640).
+// Every wait is bounded by a clock limit after which the CTA sets an error
+// flag and winds down.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -41,43 +48,46 @@ namespace mad {
 namespace {
 
 constexpr int BM = 128;             // rows of A per tile (TMEM lanes)
-constexpr int RB = 1;               // row blocks per tile
-constexpr int TM = RB * BM;         // rows of C per tile
+constexpr int TM = BM;              // rows of C per tile
 constexpr int BN = 256;             // columns of C per tile (TMEM columns)
 constexpr int KATOM = 64;           // BF16 elements per 128-byte swizzle row
-constexpr int MAXKP = 128;          // padded K handled by this kernel
-constexpr int NSTAGE = 2;           // B pipeline depth
-constexpr int CAND_CAP = 4096;      // per-CTA candidate buffer
-constexpr int CAND_TRIGGER = 2048;  // compact before a tile when above this
-constexpr int kThreads = 320;       // 2 producer/MMA warps + 8 epilogue warps
+constexpr int A_ATOM_BYTES = BM * KATOM * 2;  // 16 KB: one K slice of the A panel
+constexpr int B_ATOM_BYTES = BN * KATOM * 2;  // 32 KB: one K slice of a B tile (a stage)
+constexpr int MAX_KATOMS = 10;      // K up to 640 (A panel 160 KB)
+constexpr int MAX_STAGES = 8;
+constexpr int kSched = 4;           // units in flight between the scheduler and the consumers
+constexpr int kSmemOptIn = 232448;  // shared memory one block may opt into (227 KB)
+constexpr int kStaticSmem = 2048;   // allowance for the kernel's static shared memory
+constexpr int CAND_MIN = 4096;      // smallest per-CTA candidate buffer
+constexpr unsigned kKeepMax = 1u << 16;  // largest rescore budget
+constexpr int kThreads = 352;       // producer, MMA issuer 0, 8 epilogue warps, MMA issuer 1
 constexpr int kEpi = 256;           // epilogue threads
 constexpr long long kPreStride = 16; // threshold pre-pass visits every 16th tile
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s: a wait this long is a fault
 
-constexpr int A_RB_BYTES = BM * MAXKP * 2;              // 32 KB per row block
-constexpr int A_BYTES = RB * A_RB_BYTES;                // 32 KB
-constexpr int B_STAGE_BYTES = BN * MAXKP * 2;           // 64 KB
-constexpr int SMEM_A = 0;
-constexpr int SMEM_B = SMEM_A + A_BYTES;
-constexpr int SMEM_CV = SMEM_B + NSTAGE * B_STAGE_BYTES;           // float[CAND_CAP]
-constexpr int SMEM_CK = SMEM_CV + CAND_CAP * 4;                    // u64[CAND_CAP]
-constexpr int SMEM_TOTAL = SMEM_CK + CAND_CAP * 8;
-constexpr int SMEM_ALLOC = SMEM_TOTAL + 1024;                      // alignment slack
-
 struct GemmArgs {
   int64_t m, n;
-  int kp;                            // padded K (64 or 128)
+  int kp;                            // padded K (a multiple of 64)
+  int katoms;                        // kp / 64
+  int nstage;                        // B stages
+  int spt;                           // K slices per stage (a whole tile when K <= 128)
   int ksteps;                        // MMA K steps of 16 that reach column d
   int64_t tiles_m, tiles_n;
   int kkeep;                         // entries kept per CTA at compaction
   unsigned int* g_theta;             // shared threshold (FP32 bits)
   unsigned int* g_err;
+  float* cta_val;                    // per-CTA candidate buffers (cta_cap entries each)
+  unsigned long long* cta_key;
+  unsigned cta_cap, cta_trigger;     // buffer size; compact before a tile when above trigger
   float* cand_val;                   // merged candidates
   unsigned long long* cand_key;
   unsigned long long* cand_count;
   unsigned long long cand_cap;
   float* dense_out;                  // diagnostics: full C~ (m x n) when set
-  int64_t tile_stride;               // process every tile_stride-th tile
+  int64_t tile_stride;               // > 1: process every tile_stride-th tile, one per unit
+  long long total_units;             // work units, handed out through g_next
+  long long units_per_rb, unit_tiles; // stride 1: a unit is unit_tiles column tiles of a row block
+  unsigned long long* g_next;        // next unit to hand out
   float* max_out;                    // threshold pre-pass: half-row maxima
 };
 
@@ -109,6 +119,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait: false when the CTA is aborting or the limit passed.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
@@ -118,6 +129,28 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     }
   }
   return true;
+}
+
+// Work units.  The main pass hands out runs of unit_tiles column tiles of
+// one row block (tens per CTA) through a global counter, so CTAs whose
+// tiles hold many candidates take fewer units; the threshold pre-pass hands
+// out single tiles, every tile_stride-th in row-major order.
+struct Unit {
+  long long rb, c0, c1;  // row block, column tiles [c0, c1)
+};
+__device__ __forceinline__ Unit unit_of(const GemmArgs& a, long long u) {
+  Unit x;
+  if (a.tile_stride > 1) {
+    const long long t = u * a.tile_stride;
+    x.rb = t / a.tiles_n;
+    x.c0 = t % a.tiles_n;
+    x.c1 = x.c0 + 1;
+  } else {
+    x.rb = u / a.units_per_rb;
+    x.c0 = (u % a.units_per_rb) * a.unit_tiles;
+    x.c1 = min(x.c0 + a.unit_tiles, (long long)a.tiles_n);
+  }
+  return x;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
@@ -191,8 +224,11 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" :::
 
 struct Shared {
   uint64_t a_full, a_empty, done;
-  uint64_t b_full[NSTAGE], b_empty[NSTAGE];
+  uint64_t b_full[MAX_STAGES], b_empty[MAX_STAGES];
   uint64_t acc_full[2], acc_empty[2];
+  uint64_t sched_full[kSched], sched_empty[kSched];
+  long long sched_unit[kSched];  // unit index, -1 = no more work
+  long long epi_unit;
   uint32_t tmem_base;
   int abort_flag;
   int epi_abort;           // uniform exit decision of the four epilogue warps
@@ -325,36 +361,38 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = smem + SMEM_A;
-  unsigned char* sB = smem + SMEM_B;
-  float* cv = (float*)(smem + SMEM_CV);
-  unsigned long long* ck = (unsigned long long*)(smem + SMEM_CK);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + args.katoms * A_ATOM_BYTES;
+  const unsigned cap = args.cta_cap;
+  float* cv = args.cta_val + (size_t)blockIdx.x * cap;
+  unsigned long long* ck = args.cta_key + (size_t)blockIdx.x * cap;
+  const int nstage = args.nstage;
+  const int spt = args.spt;
   __shared__ Shared shared_state;
   Shared* sh = &shared_state;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort_flag = &sh->abort_flag;
 
-  // Virtual tile v is real tile v * tile_stride (row-major over row blocks).
-  const long long stride = args.tile_stride;
-  const long long total_tiles = (args.tiles_m * args.tiles_n + stride - 1) / stride;
-  const long long t_begin = total_tiles * blockIdx.x / gridDim.x;
-  const long long t_end = total_tiles * (blockIdx.x + 1) / gridDim.x;
-  const int katoms = args.kp / KATOM;
+  const int katoms = args.katoms;
   // Columns d..kp-1 are zeros: the MMAs stop at the first 16-column step
   // past d (7 steps instead of 8 for d = 100).
   const int ksteps = args.ksteps;
 
   if (threadIdx.x == 0) {
     mbar_init(&sh->a_full, 1);
-    mbar_init(&sh->a_empty, 1);
-    mbar_init(&sh->done, 1);
-    for (int s = 0; s < NSTAGE; ++s) {
+    mbar_init(&sh->a_empty, 2);   // both MMA issuers
+    mbar_init(&sh->done, 2);
+    for (int s = 0; s < nstage; ++s) {
       mbar_init(&sh->b_full[s], 1);
       mbar_init(&sh->b_empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh->acc_full[b], 1);
       mbar_init(&sh->acc_empty[b], kEpi / 32);
+    }
+    for (int k = 0; k < kSched; ++k) {
+      mbar_init(&sh->sched_full[k], 1);
+      mbar_init(&sh->sched_empty[k], 3);  // the two MMA issuers and the epilogue
     }
     sh->abort_flag = 0;
     sh->epi_abort = 0;
@@ -376,65 +414,126 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const uint32_t tmem_base = sh->tmem_base;
 
   if (warp == 0) {
-    // ---------------- TMA producer ----------------
+    // ---------------- scheduler and TMA producer ----------------
     if (lane == 0) {
-      long long prev_rb = -1, panel = 0;
-      for (long long v = t_begin; v < t_end && !*abort_flag; ++v) {
-        const long long it = v - t_begin, t = v * stride;
-        const long long rb = t / args.tiles_n, cb = t % args.tiles_n;
-        if (rb != prev_rb) {
-          if (panel > 0 && !mbar_wait(&sh->a_empty, (uint32_t)((panel - 1) & 1), abort_flag)) break;
-          mbar_expect_tx(&sh->a_full, (uint32_t)(TM * args.kp * 2));
-          for (int r = 0; r < RB; ++r)
-            for (int ka = 0; ka < katoms; ++ka)
-              tma_load_2d(sA + r * A_RB_BYTES + ka * (BM * 128), &tmA, &sh->a_full, ka * KATOM,
-                          (int)(rb * TM + r * BM));
-          prev_rb = rb;
-          ++panel;
+      int s = 0;             // B stage of the next slice
+      uint32_t phase = 0;    // parity of that stage's current use
+      bool refill = false;   // every stage has been used once
+      int ks = 0;            // scheduler slot
+      uint32_t kph = 0;
+      bool krefill = false;
+      long long panel = 0;
+      bool quit = false;
+      while (!quit) {
+        long long u = (long long)atomicAdd(args.g_next, 1ull);
+        if (u >= args.total_units || *abort_flag) u = -1;
+        if (krefill && !mbar_wait(&sh->sched_empty[ks], kph ^ 1u, abort_flag)) break;
+        *((volatile long long*)&sh->sched_unit[ks]) = u;
+        mbar_arrive(&sh->sched_full[ks]);
+        if (++ks == kSched) {
+          ks = 0;
+          kph ^= 1u;
+          krefill = true;
         }
-        const int s = (int)(it % NSTAGE);
-        const long long use = it / NSTAGE;
-        if (use > 0 && !mbar_wait(&sh->b_empty[s], (uint32_t)((use - 1) & 1), abort_flag)) break;
-        unsigned char* dstB = sB + s * B_STAGE_BYTES;
-        mbar_expect_tx(&sh->b_full[s], (uint32_t)(BN * args.kp * 2));
+        if (u < 0) break;
+        const Unit x = unit_of(args, u);
+        // The A panel of the unit's row block, once the previous unit's MMAs are done.
+        if (panel > 0 && !mbar_wait(&sh->a_empty, (uint32_t)((panel - 1) & 1), abort_flag)) break;
+        mbar_expect_tx(&sh->a_full, (uint32_t)(katoms * A_ATOM_BYTES));
         for (int ka = 0; ka < katoms; ++ka)
-          tma_load_2d(dstB + ka * (BN * 128), &tmB, &sh->b_full[s], ka * KATOM, (int)(cb * BN));
-      }
-    }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      long long prev_rb = -1, panel = 0;
-      for (long long v = t_begin; v < t_end && !*abort_flag; ++v) {
-        const long long it = v - t_begin, t = v * stride;
-        const long long rb = t / args.tiles_n;
-        if (rb != prev_rb) {
-          if (!mbar_wait(&sh->a_full, (uint32_t)(panel & 1), abort_flag)) break;
-          prev_rb = rb;
-          ++panel;
-        }
-        const int s = (int)(it % NSTAGE);
-        if (!mbar_wait(&sh->b_full[s], (uint32_t)((it / NSTAGE) & 1), abort_flag)) break;
-        const int buf = (int)(it & 1);
-        if (it >= 2 && !mbar_wait(&sh->acc_empty[buf], (uint32_t)(((it >> 1) - 1) & 1), abort_flag))
-          break;
-        fence_after_sync();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * (RB * BN));
-        const unsigned char* tileB = sB + s * B_STAGE_BYTES;
-        for (int kk = 0; kk < ksteps; ++kk) {
-          const int ka = kk >> 2, ko = (kk & 3) * 32;  // atom and byte offset inside it
-          const uint64_t bd = desc_sw128(tileB + ka * (BN * 128)) + (uint64_t)(ko >> 4);
-#pragma unroll
-          for (int r = 0; r < RB; ++r) {
-            const uint64_t ad =
-                desc_sw128(sA + r * A_RB_BYTES + ka * (BM * 128)) + (uint64_t)(ko >> 4);
-            mma_bf16(d_tmem + (uint32_t)(r * BN), ad, bd, kk > 0 ? 1u : 0u);
+          tma_load_2d(sA + ka * A_ATOM_BYTES, &tmA, &sh->a_full, ka * KATOM, (int)(x.rb * TM));
+        ++panel;
+        for (long long cb = x.c0; cb < x.c1 && !quit; ++cb) {
+          for (int k0 = 0; k0 < katoms; k0 += spt) {
+            if (refill && !mbar_wait(&sh->b_empty[s], phase ^ 1u, abort_flag)) {
+              quit = true;
+              break;
+            }
+            mbar_expect_tx(&sh->b_full[s], (uint32_t)(spt * B_ATOM_BYTES));
+            for (int j = 0; j < spt; ++j)
+              tma_load_2d(sB + (s * spt + j) * B_ATOM_BYTES, &tmB, &sh->b_full[s], (k0 + j) * KATOM,
+                          (int)(cb * BN));
+            if (++s == nstage) {
+              s = 0;
+              phase ^= 1u;
+              refill = true;
+            }
           }
         }
-        mma_commit(&sh->b_empty[s]);
-        mma_commit(&sh->acc_full[buf]);
-        const bool panel_ends = (v + 1 == t_end) || (((v + 1) * stride) / args.tiles_n != rb);
-        if (panel_ends) mma_commit(&sh->a_empty);
+      }
+    }
+  } else if (warp == 1 || warp == kThreads / 32 - 1) {
+    // ---------------- MMA issuers ----------------
+    // Issuer par takes the tiles with (tile index & 1) == par, and with
+    // them accumulator par: while one thread waits on its barriers the
+    // other's MMAs keep the tensor pipe busy (one thread alone spends as
+    // long on its waits and commits as on the 7 MMAs of a K = 100 tile).
+    if (lane == 0) {
+      const int par = warp == 1 ? 0 : 1;
+      const int groups = katoms / spt;   // stages per tile
+      int s = 0;
+      uint32_t phase = 0;
+      int ks = 0;
+      uint32_t kph = 0;
+      long long panel = 0, it = 0;
+      bool quit = false;
+      // Descriptors of the first A slice and the first B stage; a K step of
+      // 16 adds 32 bytes (2 in the descriptor's 16-byte address units).
+      const uint64_t da0 = desc_sw128(sA), db0 = desc_sw128(sB);
+      const uint32_t d_tmem = tmem_base + (uint32_t)(par * BN);
+      while (!quit) {
+        if (!mbar_wait(&sh->sched_full[ks], kph, abort_flag)) break;
+        const long long u = *((volatile long long*)&sh->sched_unit[ks]);
+        mbar_arrive(&sh->sched_empty[ks]);
+        if (++ks == kSched) {
+          ks = 0;
+          kph ^= 1u;
+        }
+        if (u < 0) break;
+        const Unit x = unit_of(args, u);
+        if (!mbar_wait(&sh->a_full, (uint32_t)(panel & 1), abort_flag)) break;
+        ++panel;
+        for (long long cb = x.c0; cb < x.c1 && !quit; ++cb, ++it) {
+          if ((int)(it & 1) != par) {   // the other issuer's tile: skip its stages
+            for (int g = 0; g < groups; ++g)
+              if (++s == nstage) {
+                s = 0;
+                phase ^= 1u;
+              }
+            continue;
+          }
+          if (it >= 2 &&
+              !mbar_wait(&sh->acc_empty[par], (uint32_t)(((it >> 1) - 1) & 1), abort_flag)) {
+            quit = true;
+            break;
+          }
+          for (int k0 = 0; k0 < katoms; k0 += spt) {
+            if (!mbar_wait(&sh->b_full[s], phase, abort_flag)) {
+              quit = true;
+              break;
+            }
+            fence_after_sync();
+            for (int j = 0; j < spt; ++j) {
+              const int ka = k0 + j;
+              const uint64_t da = da0 + (uint64_t)((ka * A_ATOM_BYTES) >> 4);
+              const uint64_t db = db0 + (uint64_t)(((s * spt + j) * B_ATOM_BYTES) >> 4);
+              // K steps of 16 inside this slice that reach column d (zeros past it).
+              const int steps = min(4, ksteps - ka * 4);
+              for (int kk = 0; kk < steps; ++kk)
+                mma_bf16(d_tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2),
+                         (ka > 0 || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(&sh->b_empty[s]);
+            if (++s == nstage) {
+              s = 0;
+              phase ^= 1u;
+            }
+          }
+          if (quit) break;
+          mma_commit(&sh->acc_full[par]);
+        }
+        if (quit) break;
+        mma_commit(&sh->a_empty);   // this issuer's MMAs of the unit done: its A panel may go
       }
     }
   } else {
@@ -447,161 +546,224 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     // The shared threshold, loaded one tile ahead so its latency never
     // stalls a tile (any earlier value is a valid, lower bound).
     float g_theta_next = __uint_as_float(*((volatile unsigned int*)args.g_theta));
-    for (long long v = t_begin; v < t_end; ++v) {
-      const long long it = v - t_begin, t = v * stride;
-      const long long rb = t / args.tiles_n, cb = t % args.tiles_n;
-      const int buf = (int)(it & 1);
-      // Compact first when the buffer is past its trigger (sh->count is
-      // uniform: it was last changed before the previous tile's barrier).
-      if (filter && sh->count > CAND_TRIGGER) {
-        const float th = epi_kth_largest(cv, sh->count, (unsigned)args.kkeep, sh, et);
-        epi_compact(cv, ck, sh->count, th, sh, et);
-        if (et == 0) {
-          sh->theta = fmaxf(sh->theta, th);
-          atomicMax(args.g_theta, __float_as_uint(sh->theta));
+    int ks = 0;
+    uint32_t kph = 0;
+    long long it = 0;
+    bool quit_all = false;
+    while (!quit_all) {
+      // Thread 0 takes the next unit from the scheduler and shares it.
+      if (et == 0) {
+        long long u = -1;
+        if (mbar_wait(&sh->sched_full[ks], kph, abort_flag)) {
+          u = *((volatile long long*)&sh->sched_unit[ks]);
+          mbar_arrive(&sh->sched_empty[ks]);
         }
-        epi_sync();
+        *((volatile long long*)&sh->epi_unit) = u;
       }
-      const float g_theta0 = g_theta_next;
-      if (filter) g_theta_next = __uint_as_float(*((volatile unsigned int*)args.g_theta));
-      const bool ok = mbar_wait(&sh->acc_full[buf], (uint32_t)((it >> 1) & 1), abort_flag);
-      const int64_t row = rb * TM + row_in_tile;
-      const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) +
-                             (uint32_t)(buf * (RB * BN) + half * (BN / 2));
-      const int64_t col_half = cb * BN + half * (BN / 2);
-      if (!filter) {
-        // The diagnostic and pre-pass epilogues share named barriers, so
-        // they leave together.
-        if (!ok) atomicOr(&sh->epi_abort, 1);
-        epi_sync();
-        if (*((volatile int*)&sh->epi_abort)) break;
-        fence_after_sync();
+      if (++ks == kSched) {
+        ks = 0;
+        kph ^= 1u;
       }
-      if (args.dense_out) {
-#pragma unroll 1
-        for (int ch = 0; ch < 2; ++ch) {
-          uint32_t r[64];
-          tmem_ld32_nowait(taddr + (uint32_t)(ch * 64), r);
-          tmem_ld32_nowait(taddr + (uint32_t)(ch * 64 + 32), r + 32);
-          tmem_wait_ld();
-          const int64_t col0 = col_half + ch * 64;
-          if (row < args.m) {
-#pragma unroll
-            for (int q = 0; q < 64; ++q)
-              if (col0 + q < args.n) args.dense_out[row * args.n + col0 + q] = __uint_as_float(r[q]);
+      epi_sync();
+      const long long u = *((volatile long long*)&sh->epi_unit);
+      epi_sync();   // read by all before thread 0 writes the next one
+      if (u < 0) break;
+      const Unit x = unit_of(args, u);
+      for (long long cb = x.c0; cb < x.c1; ++cb, ++it) {
+        const long long rb = x.rb;
+        const int buf = (int)(it & 1);
+        // Compact first when the buffer is past its trigger (sh->count is
+        // uniform: it was last changed before the previous tile's barrier).
+        if (filter && sh->count > args.cta_trigger) {
+          const float th = epi_kth_largest(cv, sh->count, (unsigned)args.kkeep, sh, et);
+          epi_compact(cv, ck, sh->count, th, sh, et);
+          if (et == 0) {
+            sh->theta = fmaxf(sh->theta, th);
+            atomicMax(args.g_theta, __float_as_uint(sh->theta));
           }
+          epi_sync();
         }
-      } else if (args.max_out) {
-        // Threshold pre-pass: the largest |c~| of this thread's half row.
-        float hm = 0.0f;
-#pragma unroll 1
-        for (int ch = 0; ch < 2; ++ch) {
-          uint32_t r[64];
-          tmem_ld32_nowait(taddr + (uint32_t)(ch * 64), r);
-          tmem_ld32_nowait(taddr + (uint32_t)(ch * 64 + 32), r + 32);
-          tmem_wait_ld();
-          const int64_t rem = args.n - (col_half + ch * 64);
-          const int nvalid = rem >= 64 ? 64 : (rem > 0 ? (int)rem : 0);
-          if (nvalid == 64) {
-            hm = fmaxf(hm, abs_max64(r));
-          } else {
-#pragma unroll
-            for (int q = 0; q < 64; ++q)
-              hm = fmaxf(hm, q < nvalid ? fabsf(__uint_as_float(r[q])) : 0.0f);
+        const float g_theta0 = g_theta_next;
+        if (filter) g_theta_next = __uint_as_float(*((volatile unsigned int*)args.g_theta));
+        const bool ok = mbar_wait(&sh->acc_full[buf], (uint32_t)((it >> 1) & 1), abort_flag);
+        const int64_t row = rb * TM + row_in_tile;
+        const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                               (uint32_t)(buf * BN + half * (BN / 2));
+        const int64_t col_half = cb * BN + half * (BN / 2);
+        bool released = false;
+        if (!filter) {
+          // The diagnostic and pre-pass epilogues share named barriers, so
+          // they leave together.
+          if (!ok) atomicOr(&sh->epi_abort, 1);
+          epi_sync();
+          if (*((volatile int*)&sh->epi_abort)) {
+            quit_all = true;
+            break;
           }
+          fence_after_sync();
         }
-        args.max_out[v * kEpi + et] = row < args.m ? hm : 0.0f;
-      } else {
-        if (!ok) sh->epi_abort = 1;   // read by everyone after the barrier below
-        fence_after_sync();
-        unsigned tile_start = sh->count;
-        bool stop = false;
-        for (int round = 0; round < 8; ++round) {
-          const float theta =
-              fmaxf(sh->theta, round == 0 ? g_theta0
-                                          : __uint_as_float(*((volatile unsigned int*)args.g_theta)));
-          bool over = false;
-          // Two chunks of 64 columns, reloaded from TMEM on every pass (the
-          // accumulator stays put until this tile's buffer is released).
-#pragma unroll 1
-          for (int ch = 0; ch < 2 && ok; ++ch) {
+        if (args.dense_out) {
+  #pragma unroll 1
+          for (int ch = 0; ch < 2; ++ch) {
             uint32_t r[64];
             tmem_ld32_nowait(taddr + (uint32_t)(ch * 64), r);
             tmem_ld32_nowait(taddr + (uint32_t)(ch * 64 + 32), r + 32);
             tmem_wait_ld();
             const int64_t col0 = col_half + ch * 64;
-            const int64_t rem = args.n - col0;
+            if (row < args.m) {
+  #pragma unroll
+              for (int q = 0; q < 64; ++q)
+                if (col0 + q < args.n) args.dense_out[row * args.n + col0 + q] = __uint_as_float(r[q]);
+            }
+          }
+        } else if (args.max_out) {
+          // Threshold pre-pass: the largest |c~| of this thread's half row.
+          float hm = 0.0f;
+  #pragma unroll 1
+          for (int ch = 0; ch < 2; ++ch) {
+            uint32_t r[64];
+            tmem_ld32_nowait(taddr + (uint32_t)(ch * 64), r);
+            tmem_ld32_nowait(taddr + (uint32_t)(ch * 64 + 32), r + 32);
+            tmem_wait_ld();
+            const int64_t rem = args.n - (col_half + ch * 64);
             const int nvalid = rem >= 64 ? 64 : (rem > 0 ? (int)rem : 0);
-            // Max first: the chunk is inspected element by element only when
-            // its largest valid |c~| reaches theta.  nvalid is the same for
-            // every lane of the warp, and all 64 columns are valid except in
-            // the last column block.
-            float mx = 0.0f;
             if (nvalid == 64) {
-              mx = abs_max64(r);
+              hm = fmaxf(hm, abs_max64(r));
             } else {
-#pragma unroll
+  #pragma unroll
               for (int q = 0; q < 64; ++q)
-                mx = fmaxf(mx, q < nvalid ? fabsf(__uint_as_float(r[q])) : 0.0f);
+                hm = fmaxf(hm, q < nvalid ? fabsf(__uint_as_float(r[q])) : 0.0f);
             }
-            unsigned cnt = 0;
-            if (mx >= theta && row < args.m) {
-#pragma unroll
-              for (int q = 0; q < 64; ++q)
-                cnt += (q < nvalid && fabsf(__uint_as_float(r[q])) >= theta) ? 1u : 0u;
+          }
+          args.max_out[u * kEpi + et] = row < args.m ? hm : 0.0f;
+        } else {
+          if (!ok) sh->epi_abort = 1;   // read by everyone after the barrier below
+          // First the largest |c~| of this thread's 128 values.  A warp none
+          // of whose values reaches theta (almost every warp once theta has
+          // risen) releases the accumulator at once, so the MMAs of the tile
+          // after next overlap the rest of this tile instead of waiting for
+          // it; the others keep it and re-read their chunks below.
+          bool hot = false;
+          if (ok) {
+            fence_after_sync();
+            uint32_t rr[128];
+            tmem_ld32_nowait(taddr, rr);
+            tmem_ld32_nowait(taddr + 32u, rr + 32);
+            tmem_ld32_nowait(taddr + 64u, rr + 64);
+            tmem_ld32_nowait(taddr + 96u, rr + 96);
+            tmem_wait_ld();
+            const int64_t rem = args.n - col_half;
+            const int nvalid = rem >= 128 ? 128 : (rem > 0 ? (int)rem : 0);
+            float mx = 0.0f;
+            if (nvalid == 128) {
+              mx = fmaxf(abs_max64(rr), abs_max64(rr + 64));
+            } else {
+  #pragma unroll
+              for (int q = 0; q < 128; ++q)
+                mx = fmaxf(mx, q < nvalid ? fabsf(__uint_as_float(rr[q])) : 0.0f);
             }
-            if (cnt) {
-              // Reserve this thread's slots with one atomic, then write them.
-              unsigned pos = atomicAdd(&sh->count, cnt);
-              if (pos + cnt > CAND_CAP) {
-                sh->overflow = 1;
-                over = true;
+            hot = mx >= fmaxf(sh->theta, g_theta0) && row < args.m;
+          }
+          if (!__any_sync(0xFFFFFFFFu, hot)) {
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->acc_empty[buf]);
+            released = true;   // and theta only rises: nothing of this warp passes below
+          }
+          unsigned tile_start = sh->count;
+          bool stop = false;
+          for (int round = 0; round < 8; ++round) {
+            const float theta =
+                fmaxf(sh->theta, round == 0 ? g_theta0
+                                            : __uint_as_float(*((volatile unsigned int*)args.g_theta)));
+            bool over = false;
+            // Two chunks of 64 columns, reloaded from TMEM on every pass (the
+            // accumulator stays put until this warp releases it).
+  #pragma unroll 1
+            for (int ch = 0; ch < 2 && ok && !released; ++ch) {
+              uint32_t r[64];
+              tmem_ld32_nowait(taddr + (uint32_t)(ch * 64), r);
+              tmem_ld32_nowait(taddr + (uint32_t)(ch * 64 + 32), r + 32);
+              tmem_wait_ld();
+              const int64_t col0 = col_half + ch * 64;
+              const int64_t rem = args.n - col0;
+              const int nvalid = rem >= 64 ? 64 : (rem > 0 ? (int)rem : 0);
+              // Max first: the chunk is inspected element by element only when
+              // its largest valid |c~| reaches theta.  nvalid is the same for
+              // every lane of the warp, and all 64 columns are valid except in
+              // the last column block.
+              float mx = 0.0f;
+              if (nvalid == 64) {
+                mx = abs_max64(r);
+              } else {
+  #pragma unroll
+                for (int q = 0; q < 64; ++q)
+                  mx = fmaxf(mx, q < nvalid ? fabsf(__uint_as_float(r[q])) : 0.0f);
               }
-#pragma unroll
-              for (int q = 0; q < 64; ++q) {
-                const float a = fabsf(__uint_as_float(r[q]));
-                if (q < nvalid && a >= theta) {
-                  if (pos < CAND_CAP) {
-                    cv[pos] = a;
-                    ck[pos] = ((unsigned long long)row << 32) | (unsigned long long)(col0 + q);
+              unsigned cnt = 0;
+              if (mx >= theta && row < args.m) {
+  #pragma unroll
+                for (int q = 0; q < 64; ++q)
+                  cnt += (q < nvalid && fabsf(__uint_as_float(r[q])) >= theta) ? 1u : 0u;
+              }
+              if (cnt) {
+                // Reserve this thread's slots with one atomic, then write them.
+                unsigned pos = atomicAdd(&sh->count, cnt);
+                if (pos + cnt > cap) {
+                  sh->overflow = 1;
+                  over = true;
+                }
+  #pragma unroll
+                for (int q = 0; q < 64; ++q) {
+                  const float a = fabsf(__uint_as_float(r[q]));
+                  if (q < nvalid && a >= theta) {
+                    if (pos < cap) {
+                      cv[pos] = a;
+                      ck[pos] = ((unsigned long long)row << 32) | (unsigned long long)(col0 + q);
+                    }
+                    ++pos;
                   }
-                  ++pos;
                 }
               }
             }
+            // One barrier: did any thread overflow the buffer or abort?
+            if (!epi_any(over || !ok)) break;
+            if (*((volatile int*)&sh->epi_abort)) {
+              stop = true;
+              break;
+            }
+            // Overflow: the buffer holds cap real entries, so its kkeep-th
+            // largest is a valid lower bound.  Drop this tile's entries, tighten
+            // the earlier ones and rescan the tile above it.
+            const float th = epi_kth_largest(cv, cap, (unsigned)args.kkeep, sh, et);
+            epi_compact(cv, ck, tile_start, th, sh, et);
+            if (et == 0) {
+              sh->theta = fmaxf(sh->theta, th);
+              sh->overflow = 0;
+              atomicMax(args.g_theta, __float_as_uint(sh->theta));
+            }
+            epi_sync();
+            tile_start = sh->count;  // the earlier tiles' survivors; the rescan appends after them
+            if (round == 7 && et == 0) atomicOr(args.g_err, 2u);  // pathological ties
           }
-          // One barrier: did any thread overflow the buffer or abort?
-          if (!epi_any(over || !ok)) break;
-          if (*((volatile int*)&sh->epi_abort)) {
-            stop = true;
+          if (stop) {
+            quit_all = true;
             break;
           }
-          // Overflow: the buffer holds CAND_CAP real entries, so its kkeep-th
-          // largest is a valid lower bound.  Drop this tile's entries, tighten
-          // the earlier ones and rescan the tile above it.
-          const float th = epi_kth_largest(cv, CAND_CAP, (unsigned)args.kkeep, sh, et);
-          epi_compact(cv, ck, tile_start, th, sh, et);
-          if (et == 0) {
-            sh->theta = fmaxf(sh->theta, th);
-            sh->overflow = 0;
-            atomicMax(args.g_theta, __float_as_uint(sh->theta));
-          }
-          epi_sync();
-          tile_start = sh->count;  // the earlier tiles' survivors; the rescan appends after them
-          if (round == 7 && et == 0) atomicOr(args.g_err, 2u);  // pathological ties
         }
-        if (stop) break;
+        if (!released) {
+          fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh->acc_empty[buf]);
+        }
       }
-      fence_before_sync();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sh->acc_empty[buf]);
     }
     // Publish this CTA's survivors.
     epi_sync();
     if (!args.dense_out && !args.max_out) {
       const float theta =
           fmaxf(sh->theta, __uint_as_float(*((volatile unsigned int*)args.g_theta)));
-      const unsigned n = min(sh->count, (unsigned)CAND_CAP);
+      const unsigned n = min(sh->count, cap);
       for (unsigned x = et; x < n; x += kEpi) {
         if (cv[x] >= theta) {
           const unsigned long long pos = atomicAdd(args.cand_count, 1ull);
@@ -617,9 +779,12 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   if (threadIdx.x == 0 && sh->abort_flag) atomicOr(args.g_err, 1u);
   // Every MMA this CTA issued has completed: the epilogue consumed each
   // accumulator (or the CTA aborted, in which case wait for the MMA queue).
+  const bool aborted = sh->abort_flag != 0;
+  if (aborted && warp == kThreads / 32 - 1 && lane == 0) mma_commit(&sh->done);
   if (warp == 1) {
-    if (sh->abort_flag && lane == 0) {
-      // Wait (bounded) for every MMA still queued before freeing TMEM.
+    if (aborted && lane == 0) {
+      // Wait (bounded) for every MMA of both issuers still queued before
+      // freeing TMEM.
       mma_commit(&sh->done);
       const long long t0 = clock64();
       while (!mbar_try_wait(&sh->done, 0) && clock64() - t0 < kWaitCycles) {
@@ -808,13 +973,25 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
                             uint32_t rescore, mad_pair* out, uint32_t* n_out, float* dense_out,
                             cudaStream_t st) {
   const int64_t m = A->rows, d = A->cols, n = B->cols;
-  if (d > MAXKP) return MAD_ERR_UNSUPPORTED;
-  const int kp = d <= 64 ? 64 : 128;
+  const int katoms = (int)((d + KATOM - 1) / KATOM);
+  if (katoms > MAX_KATOMS) return MAD_ERR_UNSUPPORTED;
+  const int kp = katoms * KATOM;
+  // B stages: a whole tile each when K <= 128 (one barrier per tile), else
+  // one K slice each; as many as the shared memory the A panel leaves holds
+  // (at least two).
+  const int spt = katoms <= 2 ? katoms : 1;
+  const int nstage = std::min<int>(
+      MAX_STAGES,
+      (kSmemOptIn - kStaticSmem - 1024 - katoms * A_ATOM_BYTES) / (spt * B_ATOM_BYTES));
+  if (nstage < 2) return MAD_ERR_UNSUPPORTED;
+  const int smem_bytes = katoms * A_ATOM_BYTES + nstage * spt * B_ATOM_BYTES + 1024;
   const int64_t tiles_m = (m + TM - 1) / TM, tiles_n = (n + BN - 1) / BN;
   const int grid = (int)std::min<int64_t>(sm_count(), tiles_m * tiles_n);
   const uint32_t kkeep = dense_out ? 1u : std::max(t, rescore);
-  if (!dense_out && kkeep > CAND_TRIGGER) return MAD_ERR_UNSUPPORTED;
-  const unsigned long long cand_cap = (unsigned long long)grid * CAND_CAP;
+  if (!dense_out && kkeep > kKeepMax) return MAD_ERR_UNSUPPORTED;
+  // Per-CTA buffer: four rescore budgets (at least 4096), compacted at half.
+  const unsigned cta_cap = std::max<unsigned>(CAND_MIN, (4u * kkeep + 255u) & ~255u);
+  const unsigned long long cand_cap = (unsigned long long)grid * cta_cap;
   auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
   const size_t a_bytes = al((size_t)m * kp * 2), b_bytes = al((size_t)n * kp * 2);
   const size_t cv_bytes = al(cand_cap * 4), ck_bytes = al(cand_cap * 8);
@@ -824,7 +1001,7 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   const long long pre_tiles = (tiles_m * tiles_n + kPreStride - 1) / kPreStride;
   const size_t pre_bytes = al((size_t)pre_tiles * kEpi * 4);
   const size_t hist_bytes = al(4097 * 4);
-  const size_t total = a_bytes + b_bytes + cv_bytes + ck_bytes + ws_bytes + ws2_bytes +
+  const size_t total = a_bytes + b_bytes + 2 * cv_bytes + 2 * ck_bytes + ws_bytes + ws2_bytes +
                        cvals_bytes + pre_bytes + hist_bytes + 1024;
   mad_status rs = ensure_scratch(ctx, total, st);
   if (rs != MAD_OK) return rs;
@@ -833,6 +1010,8 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   __nv_bfloat16* Bbf = (__nv_bfloat16*)p;             p += b_bytes;
   float* cand_val = (float*)p;                        p += cv_bytes;
   unsigned long long* cand_key = (unsigned long long*)p; p += ck_bytes;
+  float* cta_val = (float*)p;                         p += cv_bytes;
+  unsigned long long* cta_key = (unsigned long long*)p; p += ck_bytes;
   char* wsb = p;                                      p += ws_bytes;
   char* ws2b = p;                                     p += ws2_bytes;
   float* cvals = (float*)p;                           p += cvals_bytes;
@@ -841,6 +1020,8 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   unsigned int* g_theta = (unsigned int*)p;
   unsigned int* g_err = g_theta + 1;
   unsigned long long* cand_count = (unsigned long long*)(g_theta + 2);
+  unsigned long long* next_pre = cand_count + 1;   // unit counters of the two passes
+  unsigned long long* next_main = cand_count + 2;
   cudaMemsetAsync(g_theta, 0, 64, st);
   cudaMemsetAsync(pre_hist, 0, 4097 * 4, st);
 
@@ -851,42 +1032,63 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   CUtensorMap tmA, tmB;
   if (!make_map(&tmA, Abf, (uint64_t)m, kp, BM) || !make_map(&tmB, Bbf, (uint64_t)n, kp, BN))
     return MAD_ERR_CUDA;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static int attr_bytes = 0;
+  if (smem_bytes > attr_bytes) {
     cudaError_t e = cudaFuncSetAttribute(k_gemm_topk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_ALLOC);
+                                         smem_bytes);
     if (e != cudaSuccess) return cuda_status(e);
-    attr_set = true;
+    attr_bytes = smem_bytes;
   }
   GemmArgs ga;
   ga.m = m;
   ga.n = n;
   ga.kp = kp;
+  ga.katoms = katoms;
+  ga.nstage = nstage;
+  ga.spt = spt;
   ga.ksteps = (int)((d + 15) / 16);
   ga.tiles_m = tiles_m;
   ga.tiles_n = tiles_n;
   ga.kkeep = (int)kkeep;
   ga.g_theta = g_theta;
   ga.g_err = g_err;
+  ga.cta_val = cta_val;
+  ga.cta_key = cta_key;
+  ga.cta_cap = cta_cap;
+  ga.cta_trigger = cta_cap / 2;
   ga.cand_val = cand_val;
   ga.cand_key = cand_key;
   ga.cand_count = cand_count;
   ga.cand_cap = cand_cap;
   ga.dense_out = dense_out;
   ga.tile_stride = 1;
+  // Units of about a 32nd of a CTA's share of tiles, cut evenly from a row
+  // block's column tiles.
+  {
+    const long long share = tiles_m * tiles_n / ((long long)grid * 32);
+    long long ut = std::max<long long>(1, std::min<long long>(tiles_n, share));
+    const long long upr = (tiles_n + ut - 1) / ut;
+    ut = (tiles_n + upr - 1) / upr;
+    ga.unit_tiles = ut;
+    ga.units_per_rb = upr;
+    ga.total_units = tiles_m * upr;
+  }
+  ga.g_next = next_main;
   ga.max_out = nullptr;
   if (!dense_out) {
     // Threshold pre-pass over every kPreStride-th tile: half-row maxima.
     GemmArgs pre = ga;
     pre.tile_stride = kPreStride;
     pre.max_out = pre_max;
+    pre.total_units = (tiles_m * tiles_n + kPreStride - 1) / kPreStride;
+    pre.g_next = next_pre;
     const long long vt = (tiles_m * tiles_n + kPreStride - 1) / kPreStride;
-    k_gemm_topk<<<(int)std::min<long long>(grid, vt), kThreads, SMEM_ALLOC, st>>>(tmA, tmB, pre);
+    k_gemm_topk<<<(int)std::min<long long>(grid, vt), kThreads, smem_bytes, st>>>(tmA, tmB, pre);
     k_max_floor<<<152 * 2, 256, 0, st>>>(pre_max, (unsigned long long)vt * kEpi, kkeep, pre_hist,
                                          pre_hist + 4096, g_theta);
     count_launch(ctx, 2);
   }
-  k_gemm_topk<<<grid, kThreads, SMEM_ALLOC, st>>>(tmA, tmB, ga);
+  k_gemm_topk<<<grid, kThreads, smem_bytes, st>>>(tmA, tmB, ga);
   count_launch(ctx);
   if ((rs = cuda_status(cudaGetLastError())) != MAD_OK) return rs;
 

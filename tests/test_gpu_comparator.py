@@ -30,7 +30,9 @@ def _rng(seed):
 
 
 @pytest.mark.parametrize("m,d,n,dtype", [(300, 100, 700, np.float32), (129, 25, 257, np.float64),
-                                         (1000, 64, 513, np.float32), (64, 128, 300, np.float32)])
+                                         (1000, 64, 513, np.float32), (64, 128, 300, np.float32),
+                                         (200, 65, 260, np.float32), (257, 300, 600, np.float32),
+                                         (130, 640, 270, np.float64)])
 def test_product_matches_bf16_reference(m, d, n, dtype):
     import paper_1506_03872_gb300 as mad
     rng = _rng(m + d + n)
@@ -126,19 +128,47 @@ def test_factor_matrices_follow_the_precision_pattern(rescore):
         assert len(got & truth) / t >= 0.95   # a larger budget recovers the exact top t
 
 
+@pytest.mark.parametrize("d,t,rescore", [(300, 100, 0), (100, 1000, 0), (40, 50, 20000)])
+def test_wide_and_large_budgets_follow_the_precision_pattern(d, t, rescore):
+    """K split into several 64-wide slices (d = 300), and rescore budgets
+    past the old 2048 (8t = 8000, 20000) that make the per-CTA buffers
+    compact many times."""
+    import paper_1506_03872_gb300 as mad
+    from paper_1506_03872_gb300.workloads import dense_factors
+    w = dense_factors(m=6000, d=d, n=3000, seed=14 + d)
+    tA, tB = torch.from_numpy(w.A).cuda(), torch.from_numpy(w.B).cuda()
+    with mad.Context() as c:
+        out, nt = mad.mad_dense_topt(c.ctx, mad.dense(tA), mad.dense(tB), t, rescore)
+    gi, gj, gx, gc = mad.decode_pairs(out, nt)
+    assert nt == t
+    got = set(mad.keys_of(gi, gj).tolist())
+    ref = _pattern_reference(w.A, w.B, t, rescore or 8 * t)
+    assert len(got & ref) >= 0.97 * t
+    C = w.A.astype(np.float64) @ w.B.astype(np.float64)
+    exact = C[gi.astype(np.int64), gj.astype(np.int64)]
+    scale = (np.abs(w.A[gi.astype(np.int64)]).astype(np.float64) *
+             np.abs(w.B[:, gj.astype(np.int64)].T).astype(np.float64)).sum(axis=1)
+    assert np.all(np.abs(gc - exact) <= 100 * 2.0 ** -23 * scale)
+    assert np.all(np.diff(np.abs(gc)) <= 0)
+    assert len(set(zip(gi.tolist(), gj.tolist()))) == t   # no pair twice
+
+
 def test_limits():
     import paper_1506_03872_gb300 as mad
     rng = _rng(3)
-    A = torch.from_numpy(rng.standard_normal((100, 200)).astype(np.float32)).cuda()
-    B = torch.from_numpy(rng.standard_normal((200, 100)).astype(np.float32)).cuda()
+    A = torch.from_numpy(rng.standard_normal((100, 641)).astype(np.float32)).cuda()
+    B = torch.from_numpy(rng.standard_normal((641, 100)).astype(np.float32)).cuda()
     with mad.Context() as c:
         with pytest.raises(mad.MadError) as e:
-            mad.mad_dense_topt(c.ctx, mad.dense(A), mad.dense(B), 10)   # d > 128
+            mad.mad_dense_topt(c.ctx, mad.dense(A), mad.dense(B), 10)   # d > 640
         assert e.value.status == mad.MAD_ERR_UNSUPPORTED
         A2 = A[:, :100].contiguous()
         B2 = B[:100].contiguous()
         with pytest.raises(mad.MadError) as e:
-            mad.mad_dense_topt(c.ctx, mad.dense(A2), mad.dense(B2), 300)  # 8t > 2048
+            mad.mad_dense_topt(c.ctx, mad.dense(A2), mad.dense(B2), 8193)  # 8t > 65536
+        assert e.value.status == mad.MAD_ERR_UNSUPPORTED
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_dense_topt(c.ctx, mad.dense(A2), mad.dense(B2), 10, 65537)
         assert e.value.status == mad.MAD_ERR_UNSUPPORTED
         with pytest.raises(mad.MadError) as e:
             mad.mad_dense_topt(c.ctx, mad.dense(A2), mad.dense(B2), 10, 5)  # budget < t
