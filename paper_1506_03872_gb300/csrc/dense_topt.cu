@@ -8,7 +8,7 @@
 //     shared memory by TMA (128-byte swizzle), and never writes C~: its
 //     epilogue keeps only entries with |c~| >= theta in a per-CTA buffer.
 //     theta starts from a pre-pass (the same kernel over every 16th tile,
-//     recording half-row maxima, whose K_keep-th largest bounds the global
+//     recording row-segment maxima, whose K_keep-th largest bounds the global
 //     K_keep-th largest from below) and rises whenever the buffer is
 //     compacted to its K_keep largest entries (the rescore budget, 8t by
 //     default; the buffer lives in global memory and holds 4 K_keep
@@ -19,7 +19,7 @@
 //     ever dropped.
 //  3. The K_keep largest |c~| of the merged buffers are rescored exactly in FP32
 //     and the t largest |c| returned.
-// Warp roles per CTA (352 threads): warp 0 takes work units from a global
+// Warp roles per CTA (352 threads with the default 8 epilogue warps): warp 0 takes work units from a global
 // counter (runs of column tiles of one row block, so CTAs whose tiles hold
 // many candidates take fewer) and issues TMA; warps 1 and 10 issue the MMAs
 // of the even and odd tiles into their own TMEM accumulator (warp 1 also
@@ -60,10 +60,24 @@ constexpr int kSmemOptIn = 232448;  // shared memory one block may opt into (227
 constexpr int kStaticSmem = 2048;   // allowance for the kernel's static shared memory
 constexpr int CAND_MIN = 4096;      // smallest per-CTA candidate buffer
 constexpr unsigned kKeepMax = 1u << 16;  // largest rescore budget
-constexpr int kThreads = 352;       // producer, MMA issuer 0, 8 epilogue warps, MMA issuer 1
-constexpr int kEpi = 256;           // epilogue threads
-constexpr long long kPreStride = 16; // threshold pre-pass visits every 16th tile
+#ifndef MAD_EPI_WARPS
+#define MAD_EPI_WARPS 8
+#endif
+// 8 measured faster than 16: with 16 the registers drop to 96 a thread and
+// the MMA issue slows.
+constexpr int kEpiWarps = MAD_EPI_WARPS;       // epilogue warps (8 or 16)
+constexpr int kEpi = kEpiWarps * 32;           // epilogue threads
+constexpr int kThreads = kEpi + 3 * 32;        // producer, MMA issuer 0, epilogue, MMA issuer 1
+constexpr int kCols = BN * 4 / kEpiWarps;      // accumulator columns per epilogue thread
+constexpr int kChunks = kCols / 64;
+// |c~_ij| <= (1 + K 2^-24) ||a~_i|| ||b~_j|| (Cauchy-Schwarz on the BF16
+// vectors plus the FP32 accumulation error); the norms themselves carry
+// FP32 rounding.  A generous factor keeps the skip test a proven bound.
+constexpr float kBoundSlack = 1.01f;
+constexpr long long kPreFrac = 16;   // threshold pre-pass visits about one tile in 16
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s: a wait this long is a fault
+constexpr uint32_t kSleepNs = 100000;            // longest sleep inside one try_wait
+constexpr long long kDrainCycles = 200000000ll;  // ~0.1 s for copies in flight at an abort
 
 struct GemmArgs {
   int64_t m, n;
@@ -84,11 +98,12 @@ struct GemmArgs {
   unsigned long long* cand_count;
   unsigned long long cand_cap;
   float* dense_out;                  // diagnostics: full C~ (m x n) when set
-  int64_t tile_stride;               // > 1: process every tile_stride-th tile, one per unit
   long long total_units;             // work units, handed out through g_next
   long long units_per_rb, unit_tiles; // stride 1: a unit is unit_tiles column tiles of a row block
   unsigned long long* g_next;        // next unit to hand out
-  float* max_out;                    // threshold pre-pass: half-row maxima
+  const float* anorm;                // ||a~_i||_2 of the BF16 rows of A (m)
+  const float* bgmax;                // max ||b~_j||_2 over each kCols-column group of B
+  float* max_out;                    // threshold pre-pass: row-segment maxima
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -117,11 +132,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait that lets the thread sleep up to `ns` nanoseconds (it resumes
+// as soon as the phase completes): waiting warps then take no issue slots
+// from the single threads that issue the MMAs and TMA copies.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait: false when the CTA is aborting or the limit passed.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
+  while (!mbar_try_wait_sleep(bar, parity, kSleepNs)) {
     if (*abort_flag) return false;
     if (clock64() - t0 > kWaitCycles) {
       *abort_flag = 1;
@@ -133,18 +162,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
 
 // Work units.  The main pass hands out runs of unit_tiles column tiles of
 // one row block (tens per CTA) through a global counter, so CTAs whose
-// tiles hold many candidates take fewer units; the threshold pre-pass hands
-// out single tiles, every tile_stride-th in row-major order.
+// tiles hold many candidates take fewer units.  The threshold pre-pass has
+// one unit per row block: its run number u mod units_per_rb, so the runs
+// visited rotate over the column tiles.
 struct Unit {
   long long rb, c0, c1;  // row block, column tiles [c0, c1)
 };
 __device__ __forceinline__ Unit unit_of(const GemmArgs& a, long long u) {
   Unit x;
-  if (a.tile_stride > 1) {
-    const long long t = u * a.tile_stride;
-    x.rb = t / a.tiles_n;
-    x.c0 = t % a.tiles_n;
-    x.c1 = x.c0 + 1;
+  if (a.max_out) {
+    x.rb = u;
+    x.c0 = (u % a.units_per_rb) * a.unit_tiles;
+    x.c1 = min(x.c0 + a.unit_tiles, (long long)a.tiles_n);
   } else {
     x.rb = u / a.units_per_rb;
     x.c0 = (u % a.units_per_rb) * a.unit_tiles;
@@ -213,6 +242,18 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// The registers a tcgen05.ld wrote hold their values only after
+// tcgen05.wait::ld; the compiler does not know that.  An empty statement
+// that claims to rewrite them, placed after the wait, keeps every use of
+// them after it.
+template <int N>
+__device__ __forceinline__ void tmem_regs_ready(uint32_t* r) {
+#pragma unroll
+  for (int i = 0; i < N; i += 8)
+    asm volatile("" : "+r"(r[i]), "+r"(r[i + 1]), "+r"(r[i + 2]), "+r"(r[i + 3]), "+r"(r[i + 4]),
+                 "+r"(r[i + 5]), "+r"(r[i + 6]), "+r"(r[i + 7]));
+}
+
 __device__ __forceinline__ void fence_before_sync() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -220,7 +261,7 @@ __device__ __forceinline__ void fence_after_sync() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 // Barrier among the epilogue threads only.
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpi) : "memory"); }
 
 struct Shared {
   uint64_t a_full, a_empty, done;
@@ -347,10 +388,10 @@ __device__ __forceinline__ bool epi_any(bool p) {
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, 1, 256, p;\n\t"
+      "bar.red.or.pred q, 1, %2, p;\n\t"
       "selp.u32 %0, 1, 0, q;\n\t}\n"
       : "=r"(r)
-      : "r"((uint32_t)p)
+      : "r"((uint32_t)p), "n"(kEpi)
       : "memory");
   return r != 0;
 }
@@ -461,6 +502,22 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           }
         }
       }
+      if (*abort_flag) {
+        // Winding down: let this CTA's copies in flight land before it
+        // exits (stage s2's last load used parity `phase` when it is below
+        // s, else the parity before).
+        const long long t0 = clock64();
+        for (int s2 = 0; s2 < nstage; ++s2) {
+          if (s2 >= s && !refill) continue;   // never loaded
+          const uint32_t ph = s2 < s ? phase : (phase ^ 1u);
+          while (!mbar_try_wait(&sh->b_full[s2], ph) && clock64() - t0 < kDrainCycles) {
+          }
+        }
+        if (panel > 0)
+          while (!mbar_try_wait(&sh->a_full, (uint32_t)((panel - 1) & 1)) &&
+                 clock64() - t0 < kDrainCycles) {
+          }
+      }
     }
   } else if (warp == 1 || warp == kThreads / 32 - 1) {
     // ---------------- MMA issuers ----------------
@@ -502,13 +559,12 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
               }
             continue;
           }
-          if (it >= 2 &&
-              !mbar_wait(&sh->acc_empty[par], (uint32_t)(((it >> 1) - 1) & 1), abort_flag)) {
-            quit = true;
-            break;
-          }
           for (int k0 = 0; k0 < katoms; k0 += spt) {
-            if (!mbar_wait(&sh->b_full[s], phase, abort_flag)) {
+            // B first, then the accumulator: the B wait overlaps the
+            // epilogue's drain of this accumulator.
+            if (!mbar_wait(&sh->b_full[s], phase, abort_flag) ||
+                (k0 == 0 && it >= 2 &&
+                 !mbar_wait(&sh->acc_empty[par], (uint32_t)(((it >> 1) - 1) & 1), abort_flag))) {
               quit = true;
               break;
             }
@@ -540,7 +596,7 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     // ---------------- epilogue (warps 2..9) ----------------
     const int et = threadIdx.x - 64;          // 0..kEpi-1
     const int quarter = warp & 3;             // TMEM lane quarter of this warp
-    const int half = (warp - 2) >> 2;         // column half of the tile
+    const int cq = (warp - 2) >> 2;           // column group of the tile (kCols wide)
     const int row_in_tile = quarter * 32 + lane;
     const bool filter = !args.dense_out && !args.max_out;
     // The shared threshold, loaded one tile ahead so its latency never
@@ -569,14 +625,22 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       epi_sync();   // read by all before thread 0 writes the next one
       if (u < 0) break;
       const Unit x = unit_of(args, u);
+      const int64_t urow = x.rb * TM + row_in_tile;
+      const float arow = (filter && urow < args.m) ? args.anorm[urow] * kBoundSlack : 0.0f;
       for (long long cb = x.c0; cb < x.c1; ++cb, ++it) {
         const long long rb = x.rb;
         const int buf = (int)(it & 1);
-        // Compact first when the buffer is past its trigger (sh->count is
-        // uniform: it was last changed before the previous tile's barrier).
-        if (filter && sh->count > args.cta_trigger) {
-          const float th = epi_kth_largest(cv, sh->count, (unsigned)args.kkeep, sh, et);
-          epi_compact(cv, ck, sh->count, th, sh, et);
+        // The buffer's fill before this tile, the same in every thread: the
+        // previous tile's writes all came before its closing barrier, and no
+        // thread writes this tile's before the barrier below.  (Read after
+        // that barrier, a fast warp's first writes could already be in it.)
+        unsigned tile_start = filter ? sh->count : 0u;
+        if (filter) epi_sync();
+        // Compact first when the buffer is past its trigger.
+        if (filter && tile_start > args.cta_trigger) {
+          const unsigned held = min(tile_start, cap);
+          const float th = epi_kth_largest(cv, held, (unsigned)args.kkeep, sh, et);
+          tile_start = epi_compact(cv, ck, held, th, sh, et);
           if (et == 0) {
             sh->theta = fmaxf(sh->theta, th);
             atomicMax(args.g_theta, __float_as_uint(sh->theta));
@@ -585,11 +649,13 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
         const float g_theta0 = g_theta_next;
         if (filter) g_theta_next = __uint_as_float(*((volatile unsigned int*)args.g_theta));
-        const bool ok = mbar_wait(&sh->acc_full[buf], (uint32_t)((it >> 1) & 1), abort_flag);
+        // One verdict per warp: the TMEM loads below are warp-collective.
+        const bool ok =
+            __all_sync(0xFFFFFFFFu, mbar_wait(&sh->acc_full[buf], (uint32_t)((it >> 1) & 1), abort_flag));
         const int64_t row = rb * TM + row_in_tile;
         const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) +
-                               (uint32_t)(buf * BN + half * (BN / 2));
-        const int64_t col_half = cb * BN + half * (BN / 2);
+                               (uint32_t)(buf * BN + cq * kCols);
+        const int64_t col_grp = cb * BN + cq * kCols;
         bool released = false;
         if (!filter) {
           // The diagnostic and pre-pass epilogues share named barriers, so
@@ -603,66 +669,73 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
           fence_after_sync();
         }
         if (args.dense_out) {
-  #pragma unroll 1
-          for (int ch = 0; ch < 2; ++ch) {
+#pragma unroll 1
+          for (int ch = 0; ch < kChunks; ++ch) {
             uint32_t r[64];
             tmem_ld32_nowait(taddr + (uint32_t)(ch * 64), r);
             tmem_ld32_nowait(taddr + (uint32_t)(ch * 64 + 32), r + 32);
             tmem_wait_ld();
-            const int64_t col0 = col_half + ch * 64;
+            tmem_regs_ready<64>(r);
+            const int64_t col0 = col_grp + ch * 64;
             if (row < args.m) {
-  #pragma unroll
+#pragma unroll
               for (int q = 0; q < 64; ++q)
                 if (col0 + q < args.n) args.dense_out[row * args.n + col0 + q] = __uint_as_float(r[q]);
             }
           }
         } else if (args.max_out) {
-          // Threshold pre-pass: the largest |c~| of this thread's half row.
+          // Threshold pre-pass: the largest |c~| of this thread's row segment.
           float hm = 0.0f;
-  #pragma unroll 1
-          for (int ch = 0; ch < 2; ++ch) {
+#pragma unroll 1
+          for (int ch = 0; ch < kChunks; ++ch) {
             uint32_t r[64];
             tmem_ld32_nowait(taddr + (uint32_t)(ch * 64), r);
             tmem_ld32_nowait(taddr + (uint32_t)(ch * 64 + 32), r + 32);
             tmem_wait_ld();
-            const int64_t rem = args.n - (col_half + ch * 64);
+            tmem_regs_ready<64>(r);
+            const int64_t rem = args.n - (col_grp + ch * 64);
             const int nvalid = rem >= 64 ? 64 : (rem > 0 ? (int)rem : 0);
             if (nvalid == 64) {
               hm = fmaxf(hm, abs_max64(r));
             } else {
-  #pragma unroll
+#pragma unroll
               for (int q = 0; q < 64; ++q)
                 hm = fmaxf(hm, q < nvalid ? fabsf(__uint_as_float(r[q])) : 0.0f);
             }
           }
-          args.max_out[u * kEpi + et] = row < args.m ? hm : 0.0f;
+          args.max_out[(u * args.unit_tiles + (cb - x.c0)) * kEpi + et] = row < args.m ? hm : 0.0f;
         } else {
           if (!ok) sh->epi_abort = 1;   // read by everyone after the barrier below
-          // First the largest |c~| of this thread's 128 values.  A warp none
-          // of whose values reaches theta (almost every warp once theta has
-          // risen) releases the accumulator at once, so the MMAs of the tile
-          // after next overlap the rest of this tile instead of waiting for
-          // it; the others keep it and re-read their chunks below.
+          // A row segment whose norm bound ||a~_i|| max_j ||b~_j|| is below
+          // theta holds no candidate: a warp all of whose rows are below it
+          // (about nine in ten) releases the accumulator without reading it.
+          // Otherwise the largest |c~| of this thread's kCols values decides:
+          // a warp none of whose values reaches theta releases the
+          // accumulator at once; the others keep it and re-read their chunks
+          // below.
+          const float theta0 = fmaxf(sh->theta, g_theta0);
+          const bool may = arow * args.bgmax[cb * (BN / kCols) + cq] >= theta0;
           bool hot = false;
-          if (ok) {
+          if (ok && __any_sync(0xFFFFFFFFu, may)) {
             fence_after_sync();
-            uint32_t rr[128];
-            tmem_ld32_nowait(taddr, rr);
-            tmem_ld32_nowait(taddr + 32u, rr + 32);
-            tmem_ld32_nowait(taddr + 64u, rr + 64);
-            tmem_ld32_nowait(taddr + 96u, rr + 96);
+            uint32_t rr[kCols];
+#pragma unroll
+            for (int j = 0; j < kCols / 32; ++j)
+              tmem_ld32_nowait(taddr + (uint32_t)(32 * j), rr + 32 * j);
             tmem_wait_ld();
-            const int64_t rem = args.n - col_half;
-            const int nvalid = rem >= 128 ? 128 : (rem > 0 ? (int)rem : 0);
+            tmem_regs_ready<kCols>(rr);
+            const int64_t rem = args.n - col_grp;
+            const int nvalid = rem >= kCols ? kCols : (rem > 0 ? (int)rem : 0);
             float mx = 0.0f;
-            if (nvalid == 128) {
-              mx = fmaxf(abs_max64(rr), abs_max64(rr + 64));
+            if (nvalid == kCols) {
+#pragma unroll
+              for (int ch = 0; ch < kChunks; ++ch) mx = fmaxf(mx, abs_max64(rr + 64 * ch));
             } else {
-  #pragma unroll
-              for (int q = 0; q < 128; ++q)
+#pragma unroll
+              for (int q = 0; q < kCols; ++q)
                 mx = fmaxf(mx, q < nvalid ? fabsf(__uint_as_float(rr[q])) : 0.0f);
             }
-            hot = mx >= fmaxf(sh->theta, g_theta0) && row < args.m;
+            hot = mx >= theta0 && row < args.m;
           }
           if (!__any_sync(0xFFFFFFFFu, hot)) {
             fence_before_sync();
@@ -670,22 +743,22 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             if (lane == 0) mbar_arrive(&sh->acc_empty[buf]);
             released = true;   // and theta only rises: nothing of this warp passes below
           }
-          unsigned tile_start = sh->count;
           bool stop = false;
           for (int round = 0; round < 8; ++round) {
             const float theta =
                 fmaxf(sh->theta, round == 0 ? g_theta0
                                             : __uint_as_float(*((volatile unsigned int*)args.g_theta)));
             bool over = false;
-            // Two chunks of 64 columns, reloaded from TMEM on every pass (the
+            // Chunks of 64 columns, reloaded from TMEM on every pass (the
             // accumulator stays put until this warp releases it).
-  #pragma unroll 1
-            for (int ch = 0; ch < 2 && ok && !released; ++ch) {
+#pragma unroll 1
+            for (int ch = 0; ch < kChunks && ok && !released; ++ch) {
               uint32_t r[64];
               tmem_ld32_nowait(taddr + (uint32_t)(ch * 64), r);
               tmem_ld32_nowait(taddr + (uint32_t)(ch * 64 + 32), r + 32);
               tmem_wait_ld();
-              const int64_t col0 = col_half + ch * 64;
+              tmem_regs_ready<64>(r);
+              const int64_t col0 = col_grp + ch * 64;
               const int64_t rem = args.n - col0;
               const int nvalid = rem >= 64 ? 64 : (rem > 0 ? (int)rem : 0);
               // Max first: the chunk is inspected element by element only when
@@ -696,13 +769,13 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
               if (nvalid == 64) {
                 mx = abs_max64(r);
               } else {
-  #pragma unroll
+#pragma unroll
                 for (int q = 0; q < 64; ++q)
                   mx = fmaxf(mx, q < nvalid ? fabsf(__uint_as_float(r[q])) : 0.0f);
               }
               unsigned cnt = 0;
               if (mx >= theta && row < args.m) {
-  #pragma unroll
+#pragma unroll
                 for (int q = 0; q < 64; ++q)
                   cnt += (q < nvalid && fabsf(__uint_as_float(r[q])) >= theta) ? 1u : 0u;
               }
@@ -713,7 +786,7 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                   sh->overflow = 1;
                   over = true;
                 }
-  #pragma unroll
+#pragma unroll
                 for (int q = 0; q < 64; ++q) {
                   const float a = fabsf(__uint_as_float(r[q]));
                   if (q < nvalid && a >= theta) {
@@ -736,14 +809,14 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             // largest is a valid lower bound.  Drop this tile's entries, tighten
             // the earlier ones and rescan the tile above it.
             const float th = epi_kth_largest(cv, cap, (unsigned)args.kkeep, sh, et);
-            epi_compact(cv, ck, tile_start, th, sh, et);
+            // The earlier tiles' survivors; the rescan appends after them.
+            tile_start = epi_compact(cv, ck, tile_start, th, sh, et);
             if (et == 0) {
               sh->theta = fmaxf(sh->theta, th);
               sh->overflow = 0;
               atomicMax(args.g_theta, __float_as_uint(sh->theta));
             }
             epi_sync();
-            tile_start = sh->count;  // the earlier tiles' survivors; the rescan appends after them
             if (round == 7 && et == 0) atomicOr(args.g_err, 2u);  // pathological ties
           }
           if (stop) {
@@ -798,16 +871,54 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 }
 
 // ---- casts: FP32/FP64 -> BF16, K padded with zeros ------------------------
+// One warp per row; lane L writes the BF16 pairs at columns 2L + 64j, and
+// the warp the 2-norm of the rounded row.
 template <typename T>
-__global__ void k_cast_rows_bf16(const T* __restrict__ src, int64_t rows, int64_t cols, int64_t ld,
-                                 int kp, __nv_bfloat16* __restrict__ dst) {
-  const int64_t total = rows * kp;
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = x / kp, c = x % kp;
-    const float v = c < cols ? (float)src[r * ld + c] : 0.0f;
-    dst[x] = __float2bfloat16_rn(v);
+__global__ void __launch_bounds__(256)
+k_cast_rows_bf16(const T* __restrict__ src, int64_t rows, int64_t cols, int64_t ld, int kp,
+                 __nv_bfloat16* __restrict__ dst, float* __restrict__ norm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+    const T* a = src + r * ld;
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(dst + r * kp);
+    float ss = 0.0f;
+    for (int c = 2 * lane; c < kp; c += 64) {
+      const float v0 = c < cols ? (float)a[c] : 0.0f;
+      const float v1 = c + 1 < cols ? (float)a[c + 1] : 0.0f;
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+      o[c >> 1] = h;
+      const float2 f = __bfloat1622float2(h);
+      ss = fmaf(f.x, f.x, fmaf(f.y, f.y, ss));
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, off);
+    if (lane == 0) norm[r] = sqrtf(ss);
   }
+}
+
+// Largest 2-norm of the BF16 columns of B in each group of `group` columns
+// (rows of B^T, kp wide): one block per group, one thread per column.
+__global__ void __launch_bounds__(128)
+k_group_col_norms(const __nv_bfloat16* __restrict__ bt, int64_t n, int kp, int group,
+                  float* __restrict__ gmax) {
+  const int64_t j = (int64_t)blockIdx.x * group + threadIdx.x;
+  float ss = 0.0f;
+  if (threadIdx.x < group && j < n) {
+    const __nv_bfloat162* row = reinterpret_cast<const __nv_bfloat162*>(bt + j * kp);
+    for (int c = 0; c < kp / 2; ++c) {
+      const float2 f = __bfloat1622float2(row[c]);
+      ss = fmaf(f.x, f.x, fmaf(f.y, f.y, ss));
+    }
+  }
+  float v = sqrtf(ss);
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, off));
+  __shared__ float wmax[4];
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    gmax[blockIdx.x] = fmaxf(fmaxf(wmax[0], wmax[1]), fmaxf(wmax[2], wmax[3]));
 }
 
 // B (d x n) -> B^T (n x kp) in BF16.
@@ -950,13 +1061,16 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t rows, int kp, uint32_
 
 template <typename T>
 void launch_casts(const mad_matrix* A, const mad_matrix* B, int kp, __nv_bfloat16* Abf,
-                  __nv_bfloat16* Bbf, cudaStream_t st) {
-  const int64_t ta = A->rows * kp;
-  k_cast_rows_bf16<T><<<(unsigned)((ta + 255) / 256 < 152 * 32 ? (ta + 255) / 256 : 152 * 32), 256,
-                        0, st>>>((const T*)A->values, A->rows, A->cols, A->ld, kp, Abf);
+                  __nv_bfloat16* Bbf, float* anorm, float* bgmax, cudaStream_t st) {
+  const int64_t blocks = (A->rows + 7) / 8;   // a warp per row
+  k_cast_rows_bf16<T><<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(
+      (const T*)A->values, A->rows, A->cols, A->ld, kp, Abf, anorm);
   dim3 grid((unsigned)((B->cols + 31) / 32), (unsigned)((kp + 31) / 32));
   k_cast_cols_bf16<T><<<grid, dim3(32, 8), 0, st>>>((const T*)B->values, B->rows, B->cols, B->ld,
                                                     kp, Bbf);
+  // Every group of every column tile, the ones past n included (norm 0).
+  const int64_t groups = (B->cols + BN - 1) / BN * (BN / kCols);
+  k_group_col_norms<<<(unsigned)groups, 128, 0, st>>>(Bbf, B->cols, kp, kCols, bgmax);
 }
 
 int sm_count() {
@@ -998,11 +1112,15 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   const size_t ws_bytes = al(select_ws_bytes(cand_cap, kkeep));
   const size_t ws2_bytes = al(select_ws_bytes(kkeep, t ? t : 1));
   const size_t cvals_bytes = al((size_t)kkeep * 4);
-  const long long pre_tiles = (tiles_m * tiles_n + kPreStride - 1) / kPreStride;
+  // Pre-pass runs: ceil(tiles_n / 16) column tiles of every row block.
+  const long long pre_run = (tiles_n + kPreFrac - 1) / kPreFrac;
+  const long long pre_tiles = tiles_m * pre_run;   // slots of the row-segment maxima
   const size_t pre_bytes = al((size_t)pre_tiles * kEpi * 4);
   const size_t hist_bytes = al(4097 * 4);
+  const size_t anorm_bytes = al((size_t)m * 4);
+  const size_t bgmax_bytes = al((size_t)(tiles_n * (BN / kCols)) * 4);
   const size_t total = a_bytes + b_bytes + 2 * cv_bytes + 2 * ck_bytes + ws_bytes + ws2_bytes +
-                       cvals_bytes + pre_bytes + hist_bytes + 1024;
+                       cvals_bytes + pre_bytes + hist_bytes + anorm_bytes + bgmax_bytes + 1024;
   mad_status rs = ensure_scratch(ctx, total, st);
   if (rs != MAD_OK) return rs;
   char* p = (char*)ctx->scratch;
@@ -1010,6 +1128,8 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   __nv_bfloat16* Bbf = (__nv_bfloat16*)p;             p += b_bytes;
   float* cand_val = (float*)p;                        p += cv_bytes;
   unsigned long long* cand_key = (unsigned long long*)p; p += ck_bytes;
+  float* anorm = (float*)p;                           p += anorm_bytes;
+  float* bgmax = (float*)p;                           p += bgmax_bytes;
   float* cta_val = (float*)p;                         p += cv_bytes;
   unsigned long long* cta_key = (unsigned long long*)p; p += ck_bytes;
   char* wsb = p;                                      p += ws_bytes;
@@ -1025,9 +1145,9 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   cudaMemsetAsync(g_theta, 0, 64, st);
   cudaMemsetAsync(pre_hist, 0, 4097 * 4, st);
 
-  if (A->dt == MAD_F64) launch_casts<double>(A, B, kp, Abf, Bbf, st);
-  else launch_casts<float>(A, B, kp, Abf, Bbf, st);
-  count_launch(ctx, 2);
+  if (A->dt == MAD_F64) launch_casts<double>(A, B, kp, Abf, Bbf, anorm, bgmax, st);
+  else launch_casts<float>(A, B, kp, Abf, Bbf, anorm, bgmax, st);
+  count_launch(ctx, 3);
 
   CUtensorMap tmA, tmB;
   if (!make_map(&tmA, Abf, (uint64_t)m, kp, BM) || !make_map(&tmB, Bbf, (uint64_t)n, kp, BN))
@@ -1052,6 +1172,8 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   ga.kkeep = (int)kkeep;
   ga.g_theta = g_theta;
   ga.g_err = g_err;
+  ga.anorm = anorm;
+  ga.bgmax = bgmax;
   ga.cta_val = cta_val;
   ga.cta_key = cta_key;
   ga.cta_cap = cta_cap;
@@ -1061,7 +1183,6 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   ga.cand_count = cand_count;
   ga.cand_cap = cand_cap;
   ga.dense_out = dense_out;
-  ga.tile_stride = 1;
   // Units of about a 32nd of a CTA's share of tiles, cut evenly from a row
   // block's column tiles.
   {
@@ -1076,16 +1197,19 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   ga.g_next = next_main;
   ga.max_out = nullptr;
   if (!dense_out) {
-    // Threshold pre-pass over every kPreStride-th tile: half-row maxima.
+    // Threshold pre-pass over one run of pre_run column tiles per row
+    // block: row-segment maxima (slots of short last runs stay 0).
     GemmArgs pre = ga;
-    pre.tile_stride = kPreStride;
     pre.max_out = pre_max;
-    pre.total_units = (tiles_m * tiles_n + kPreStride - 1) / kPreStride;
+    pre.unit_tiles = pre_run;
+    pre.units_per_rb = (tiles_n + pre_run - 1) / pre_run;
+    pre.total_units = tiles_m;
     pre.g_next = next_pre;
-    const long long vt = (tiles_m * tiles_n + kPreStride - 1) / kPreStride;
-    k_gemm_topk<<<(int)std::min<long long>(grid, vt), kThreads, smem_bytes, st>>>(tmA, tmB, pre);
-    k_max_floor<<<152 * 2, 256, 0, st>>>(pre_max, (unsigned long long)vt * kEpi, kkeep, pre_hist,
-                                         pre_hist + 4096, g_theta);
+    cudaMemsetAsync(pre_max, 0, (size_t)pre_tiles * kEpi * 4, st);
+    k_gemm_topk<<<(int)std::min<long long>(grid, tiles_m), kThreads, smem_bytes, st>>>(tmA, tmB,
+                                                                                     pre);
+    k_max_floor<<<152 * 2, 256, 0, st>>>(pre_max, (unsigned long long)pre_tiles * kEpi, kkeep,
+                                         pre_hist, pre_hist + 4096, g_theta);
     count_launch(ctx, 2);
   }
   k_gemm_topk<<<grid, kThreads, smem_bytes, st>>>(tmA, tmB, ga);
