@@ -74,7 +74,6 @@ constexpr int kChunks = kCols / 64;
 // vectors plus the FP32 accumulation error); the norms themselves carry
 // FP32 rounding.  A generous factor keeps the skip test a proven bound.
 constexpr float kBoundSlack = 1.01f;
-constexpr long long kPreFrac = 16;   // threshold pre-pass visits about one tile in 16
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s: a wait this long is a fault
 constexpr uint32_t kSleepNs = 100000;            // longest sleep inside one try_wait
 constexpr long long kDrainCycles = 200000000ll;  // ~0.1 s for copies in flight at an abort
@@ -101,6 +100,8 @@ struct GemmArgs {
   long long total_units;             // work units, handed out through g_next
   long long units_per_rb, unit_tiles; // stride 1: a unit is unit_tiles column tiles of a row block
   unsigned long long* g_next;        // next unit to hand out
+  const uint32_t* perm_a;            // original row of A at each row position of the product
+  const uint32_t* perm_b;            // original column of B at each column position
   const float* anorm;                // ||a~_i||_2 of the BF16 rows of A (m)
   const float* bgmax;                // max ||b~_j||_2 over each kCols-column group of B
   float* max_out;                    // threshold pre-pass: row-segment maxima
@@ -163,8 +164,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
 // Work units.  The main pass hands out runs of unit_tiles column tiles of
 // one row block (tens per CTA) through a global counter, so CTAs whose
 // tiles hold many candidates take fewer units.  The threshold pre-pass has
-// one unit per row block: its run number u mod units_per_rb, so the runs
-// visited rotate over the column tiles.
+// one unit per row block of its corner: column tiles [0, unit_tiles).
 struct Unit {
   long long rb, c0, c1;  // row block, column tiles [c0, c1)
 };
@@ -680,7 +680,9 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             if (row < args.m) {
 #pragma unroll
               for (int q = 0; q < 64; ++q)
-                if (col0 + q < args.n) args.dense_out[row * args.n + col0 + q] = __uint_as_float(r[q]);
+                if (col0 + q < args.n)
+                  args.dense_out[(int64_t)args.perm_a[row] * args.n + args.perm_b[col0 + q]] =
+                      __uint_as_float(r[q]);
             }
           }
         } else if (args.max_out) {
@@ -792,7 +794,8 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                   if (q < nvalid && a >= theta) {
                     if (pos < cap) {
                       cv[pos] = a;
-                      ck[pos] = ((unsigned long long)row << 32) | (unsigned long long)(col0 + q);
+                      ck[pos] = ((unsigned long long)args.perm_a[row] << 32) |
+                                (unsigned long long)args.perm_b[col0 + q];
                     }
                     ++pos;
                   }
@@ -871,17 +874,122 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 }
 
 // ---- casts: FP32/FP64 -> BF16, K padded with zeros ------------------------
-// One warp per row; lane L writes the BF16 pairs at columns 2L + 64j, and
-// the warp the 2-norm of the rounded row.
+// ---- norm order -------------------------------------------------------------
+// Rows of A and columns of B enter the product grouped by their 2-norm,
+// largest first (256 buckets of eighths of log2), so that the row segments
+// and column groups the norm bound clears are whole warps and whole column
+// groups, and the first row blocks and column tiles hold the largest
+// products.  The order inside a bucket is the order of arrival; the
+// products, and so the result, do not depend on it.
+__device__ __forceinline__ int norm_bucket(float nrm) {
+  if (!(nrm > 0.0f)) return 255;   // zero vectors last
+  const int b = 127 - (int)floorf(log2f(nrm) * 8.0f);
+  return min(max(b, 0), 254);
+}
+
+// One warp per row of A: its bucket, and the bucket counts.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_cast_rows_bf16(const T* __restrict__ src, int64_t rows, int64_t cols, int64_t ld, int kp,
-                 __nv_bfloat16* __restrict__ dst, float* __restrict__ norm) {
+k_row_buckets(const T* __restrict__ src, int64_t rows, int64_t cols, int64_t ld,
+              uint8_t* __restrict__ bucket, unsigned int* __restrict__ hist) {
+  __shared__ unsigned int h[256];
+  for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+    float ss = 0.0f;
+    for (int64_t c = lane; c < cols; c += 32) {
+      const float v = (float)src[r * ld + c];
+      ss = fmaf(v, v, ss);
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, off);
+    if (lane == 0) {
+      const int b = norm_bucket(sqrtf(ss));
+      bucket[r] = (uint8_t)b;
+      atomicAdd(&h[b], 1u);
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < 256; b += blockDim.x)
+    if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+// One thread per column of B (d x n, row-major): its bucket and the counts.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_col_buckets(const T* __restrict__ B, int64_t d, int64_t n, int64_t ldb,
+              uint8_t* __restrict__ bucket, unsigned int* __restrict__ hist) {
+  __shared__ unsigned int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) {
+    float ss = 0.0f;
+    for (int64_t k = 0; k < d; ++k) {
+      const float v = (float)B[k * ldb + j];
+      ss = fmaf(v, v, ss);
+    }
+    const int b = norm_bucket(sqrtf(ss));
+    bucket[j] = (uint8_t)b;
+    atomicAdd(&h[b], 1u);
+  }
+  __syncthreads();
+  if (h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+// Exclusive scans of the two 256-bucket counts into cursors (one block).
+__global__ void __launch_bounds__(256)
+k_bucket_cursors(const unsigned int* __restrict__ hist_a, const unsigned int* __restrict__ hist_b,
+                 unsigned int* __restrict__ cur_a, unsigned int* __restrict__ cur_b) {
+  __shared__ unsigned int s[2][256];
+  const int t = threadIdx.x;
+  s[0][t] = hist_a[t];
+  s[1][t] = hist_b[t];
+  __syncthreads();
+  for (int off = 1; off < 256; off <<= 1) {
+    const unsigned a = t >= off ? s[0][t - off] : 0u, b = t >= off ? s[1][t - off] : 0u;
+    __syncthreads();
+    s[0][t] += a;
+    s[1][t] += b;
+    __syncthreads();
+  }
+  cur_a[t] = s[0][t] - hist_a[t];
+  cur_b[t] = s[1][t] - hist_b[t];
+}
+
+// Position of every column of B in the product, and the inverse map.
+__global__ void k_claim_cols(const uint8_t* __restrict__ bucket, int64_t n,
+                             unsigned int* __restrict__ cur, uint32_t* __restrict__ pos,
+                             uint32_t* __restrict__ perm) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const uint32_t q = atomicAdd(&cur[bucket[j]], 1u);
+  pos[j] = q;
+  perm[q] = (uint32_t)j;
+}
+
+// One warp per row; the row goes to the next place of its bucket.  Lane L
+// writes the BF16 pairs at columns 2L + 64j, and the warp the 2-norm of the
+// rounded row.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_cast_rows_bf16(const T* __restrict__ src, int64_t rows, int64_t cols, int64_t ld, int kp,
+                 const uint8_t* __restrict__ bucket, unsigned int* __restrict__ cur,
+                 __nv_bfloat16* __restrict__ dst, float* __restrict__ norm,
+                 uint32_t* __restrict__ perm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+    uint32_t q = 0;
+    if (lane == 0) {
+      q = atomicAdd(&cur[bucket[r]], 1u);
+      perm[q] = (uint32_t)r;
+    }
+    q = __shfl_sync(0xFFFFFFFFu, q, 0);
     const T* a = src + r * ld;
-    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(dst + r * kp);
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(dst + (int64_t)q * kp);
     float ss = 0.0f;
     for (int c = 2 * lane; c < kp; c += 64) {
       const float v0 = c < cols ? (float)a[c] : 0.0f;
@@ -893,7 +1001,7 @@ k_cast_rows_bf16(const T* __restrict__ src, int64_t rows, int64_t cols, int64_t 
     }
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, off);
-    if (lane == 0) norm[r] = sqrtf(ss);
+    if (lane == 0) norm[q] = sqrtf(ss);
   }
 }
 
@@ -924,7 +1032,7 @@ k_group_col_norms(const __nv_bfloat16* __restrict__ bt, int64_t n, int kp, int g
 // B (d x n) -> B^T (n x kp) in BF16.
 template <typename T>
 __global__ void k_cast_cols_bf16(const T* __restrict__ B, int64_t d, int64_t n, int64_t ldb, int kp,
-                                 __nv_bfloat16* __restrict__ dst) {
+                                 const uint32_t* __restrict__ pos, __nv_bfloat16* __restrict__ dst) {
   __shared__ float tile[32][33];
   const int64_t j0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -934,7 +1042,7 @@ __global__ void k_cast_cols_bf16(const T* __restrict__ B, int64_t d, int64_t n, 
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int64_t j = j0 + r, k = k0 + threadIdx.x;
-    if (j < n && k < kp) dst[j * kp + k] = __float2bfloat16_rn(tile[threadIdx.x][r]);
+    if (j < n && k < kp) dst[(int64_t)pos[j] * kp + k] = __float2bfloat16_rn(tile[threadIdx.x][r]);
   }
 }
 
@@ -1059,15 +1167,37 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t rows, int kp, uint32_
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+struct NormOrder {
+  uint8_t* bkt_a;      // bucket of each row of A (m)
+  uint8_t* bkt_b;      // bucket of each column of B (n)
+  unsigned int* hist;  // 256 counts for A, then 256 for B
+  unsigned int* cur;   // their exclusive scans, advanced as places are taken
+  uint32_t* perm_a;    // original row at each row position
+  uint32_t* perm_b;    // original column at each column position
+  uint32_t* pos_b;     // position of each original column
+};
+
+// BF16 copies of A (rows) and B^T (columns of B as rows) in norm order,
+// the 2-norms of the rounded rows of A and the column-group maxima of B.
 template <typename T>
-void launch_casts(const mad_matrix* A, const mad_matrix* B, int kp, __nv_bfloat16* Abf,
-                  __nv_bfloat16* Bbf, float* anorm, float* bgmax, cudaStream_t st) {
-  const int64_t blocks = (A->rows + 7) / 8;   // a warp per row
-  k_cast_rows_bf16<T><<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(
-      (const T*)A->values, A->rows, A->cols, A->ld, kp, Abf, anorm);
-  dim3 grid((unsigned)((B->cols + 31) / 32), (unsigned)((kp + 31) / 32));
-  k_cast_cols_bf16<T><<<grid, dim3(32, 8), 0, st>>>((const T*)B->values, B->rows, B->cols, B->ld,
-                                                    kp, Bbf);
+void launch_casts(const mad_matrix* A, const mad_matrix* B, int kp, const NormOrder& o,
+                  __nv_bfloat16* Abf, __nv_bfloat16* Bbf, float* anorm, float* bgmax,
+                  cudaStream_t st) {
+  const int64_t m = A->rows, n = B->cols;
+  const int64_t blocks = (m + 7) / 8;   // a warp per row
+  const unsigned rgrid = (unsigned)(blocks < 152 * 16 ? blocks : 152 * 16);
+  const unsigned cgrid = (unsigned)((n + 255) / 256);
+  cudaMemsetAsync(o.hist, 0, 512 * sizeof(unsigned int), st);
+  k_row_buckets<T><<<rgrid, 256, 0, st>>>((const T*)A->values, m, A->cols, A->ld, o.bkt_a, o.hist);
+  k_col_buckets<T><<<cgrid, 256, 0, st>>>((const T*)B->values, B->rows, n, B->ld, o.bkt_b,
+                                          o.hist + 256);
+  k_bucket_cursors<<<1, 256, 0, st>>>(o.hist, o.hist + 256, o.cur, o.cur + 256);
+  k_cast_rows_bf16<T><<<rgrid, 256, 0, st>>>((const T*)A->values, m, A->cols, A->ld, kp, o.bkt_a,
+                                             o.cur, Abf, anorm, o.perm_a);
+  k_claim_cols<<<cgrid, 256, 0, st>>>(o.bkt_b, n, o.cur + 256, o.pos_b, o.perm_b);
+  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((kp + 31) / 32));
+  k_cast_cols_bf16<T><<<grid, dim3(32, 8), 0, st>>>((const T*)B->values, B->rows, n, B->ld, kp,
+                                                    o.pos_b, Bbf);
   // Every group of every column tile, the ones past n included (norm 0).
   const int64_t groups = (B->cols + BN - 1) / BN * (BN / kCols);
   k_group_col_norms<<<(unsigned)groups, 128, 0, st>>>(Bbf, B->cols, kp, kCols, bgmax);
@@ -1112,15 +1242,19 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   const size_t ws_bytes = al(select_ws_bytes(cand_cap, kkeep));
   const size_t ws2_bytes = al(select_ws_bytes(kkeep, t ? t : 1));
   const size_t cvals_bytes = al((size_t)kkeep * 4);
-  // Pre-pass runs: ceil(tiles_n / 16) column tiles of every row block.
-  const long long pre_run = (tiles_n + kPreFrac - 1) / kPreFrac;
-  const long long pre_tiles = tiles_m * pre_run;   // slots of the row-segment maxima
+  // Pre-pass: the corner of the largest norms, the first quarter of the row
+  // blocks times the first quarter of the column tiles (a 16th of the tiles).
+  const long long pre_rows = (tiles_m + 3) / 4, pre_cols = (tiles_n + 3) / 4;
+  const long long pre_tiles = pre_rows * pre_cols;   // slots of the row-segment maxima
   const size_t pre_bytes = al((size_t)pre_tiles * kEpi * 4);
   const size_t hist_bytes = al(4097 * 4);
   const size_t anorm_bytes = al((size_t)m * 4);
+  const size_t order_bytes = al((size_t)m) + al((size_t)n) + al(1024 * 4) + al((size_t)m * 4) +
+                             2 * al((size_t)n * 4);
   const size_t bgmax_bytes = al((size_t)(tiles_n * (BN / kCols)) * 4);
   const size_t total = a_bytes + b_bytes + 2 * cv_bytes + 2 * ck_bytes + ws_bytes + ws2_bytes +
-                       cvals_bytes + pre_bytes + hist_bytes + anorm_bytes + bgmax_bytes + 1024;
+                       cvals_bytes + pre_bytes + hist_bytes + anorm_bytes + bgmax_bytes +
+                       order_bytes + 1024;
   mad_status rs = ensure_scratch(ctx, total, st);
   if (rs != MAD_OK) return rs;
   char* p = (char*)ctx->scratch;
@@ -1129,6 +1263,14 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   float* cand_val = (float*)p;                        p += cv_bytes;
   unsigned long long* cand_key = (unsigned long long*)p; p += ck_bytes;
   float* anorm = (float*)p;                           p += anorm_bytes;
+  NormOrder ord;
+  ord.bkt_a = (uint8_t*)p;                            p += al((size_t)m);
+  ord.bkt_b = (uint8_t*)p;                            p += al((size_t)n);
+  ord.hist = (unsigned int*)p;
+  ord.cur = ord.hist + 512;                           p += al(1024 * 4);
+  ord.perm_a = (uint32_t*)p;                          p += al((size_t)m * 4);
+  ord.perm_b = (uint32_t*)p;                          p += al((size_t)n * 4);
+  ord.pos_b = (uint32_t*)p;                           p += al((size_t)n * 4);
   float* bgmax = (float*)p;                           p += bgmax_bytes;
   float* cta_val = (float*)p;                         p += cv_bytes;
   unsigned long long* cta_key = (unsigned long long*)p; p += ck_bytes;
@@ -1145,9 +1287,9 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   cudaMemsetAsync(g_theta, 0, 64, st);
   cudaMemsetAsync(pre_hist, 0, 4097 * 4, st);
 
-  if (A->dt == MAD_F64) launch_casts<double>(A, B, kp, Abf, Bbf, anorm, bgmax, st);
-  else launch_casts<float>(A, B, kp, Abf, Bbf, anorm, bgmax, st);
-  count_launch(ctx, 3);
+  if (A->dt == MAD_F64) launch_casts<double>(A, B, kp, ord, Abf, Bbf, anorm, bgmax, st);
+  else launch_casts<float>(A, B, kp, ord, Abf, Bbf, anorm, bgmax, st);
+  count_launch(ctx, 7);
 
   CUtensorMap tmA, tmB;
   if (!make_map(&tmA, Abf, (uint64_t)m, kp, BM) || !make_map(&tmB, Bbf, (uint64_t)n, kp, BN))
@@ -1172,6 +1314,8 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   ga.kkeep = (int)kkeep;
   ga.g_theta = g_theta;
   ga.g_err = g_err;
+  ga.perm_a = ord.perm_a;
+  ga.perm_b = ord.perm_b;
   ga.anorm = anorm;
   ga.bgmax = bgmax;
   ga.cta_val = cta_val;
@@ -1197,17 +1341,16 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   ga.g_next = next_main;
   ga.max_out = nullptr;
   if (!dense_out) {
-    // Threshold pre-pass over one run of pre_run column tiles per row
-    // block: row-segment maxima (slots of short last runs stay 0).
+    // Threshold pre-pass over the corner of the largest norms, one unit
+    // per row block: row-segment maxima.
     GemmArgs pre = ga;
     pre.max_out = pre_max;
-    pre.unit_tiles = pre_run;
-    pre.units_per_rb = (tiles_n + pre_run - 1) / pre_run;
-    pre.total_units = tiles_m;
+    pre.unit_tiles = pre_cols;
+    pre.units_per_rb = 1;
+    pre.total_units = pre_rows;
     pre.g_next = next_pre;
-    cudaMemsetAsync(pre_max, 0, (size_t)pre_tiles * kEpi * 4, st);
-    k_gemm_topk<<<(int)std::min<long long>(grid, tiles_m), kThreads, smem_bytes, st>>>(tmA, tmB,
-                                                                                     pre);
+    k_gemm_topk<<<(int)std::min<long long>(grid, pre_rows), kThreads, smem_bytes, st>>>(tmA, tmB,
+                                                                                      pre);
     k_max_floor<<<152 * 2, 256, 0, st>>>(pre_max, (unsigned long long)pre_tiles * kEpi, kkeep,
                                          pre_hist, pre_hist + 4096, g_theta);
     count_launch(ctx, 2);
