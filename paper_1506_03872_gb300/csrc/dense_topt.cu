@@ -959,32 +959,57 @@ k_bucket_cursors(const unsigned int* __restrict__ hist_a, const unsigned int* __
   cur_b[t] = s[1][t] - hist_b[t];
 }
 
-// Position of every column of B in the product, and the inverse map.
-__global__ void k_claim_cols(const uint8_t* __restrict__ bucket, int64_t n,
-                             unsigned int* __restrict__ cur, uint32_t* __restrict__ pos,
-                             uint32_t* __restrict__ perm) {
+// Position of every column of B in the product, and the inverse map.  A
+// block counts its 256 columns per bucket, takes a range of each bucket with
+// one global atomic, and hands the places out in shared memory.
+__global__ void __launch_bounds__(256)
+k_claim_cols(const uint8_t* __restrict__ bucket, int64_t n, unsigned int* __restrict__ cur,
+             uint32_t* __restrict__ pos, uint32_t* __restrict__ perm) {
+  __shared__ unsigned int base[256];
+  base[threadIdx.x] = 0;
+  __syncthreads();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const uint32_t q = atomicAdd(&cur[bucket[j]], 1u);
+  const int b = j < n ? bucket[j] : -1;
+  if (b >= 0) atomicAdd(&base[b], 1u);
+  __syncthreads();
+  if (base[threadIdx.x]) base[threadIdx.x] = atomicAdd(&cur[threadIdx.x], base[threadIdx.x]);
+  __syncthreads();
+  if (b < 0) return;
+  const uint32_t q = atomicAdd(&base[b], 1u);
   pos[j] = q;
   perm[q] = (uint32_t)j;
 }
 
 // One warp per row; the row goes to the next place of its bucket.  Lane L
 // writes the BF16 pairs at columns 2L + 64j, and the warp the 2-norm of the
-// rounded row.
+// rounded row.  The block first counts its rows per bucket and takes a range
+// of each bucket with one global atomic; places are then handed out in
+// shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_cast_rows_bf16(const T* __restrict__ src, int64_t rows, int64_t cols, int64_t ld, int kp,
                  const uint8_t* __restrict__ bucket, unsigned int* __restrict__ cur,
                  __nv_bfloat16* __restrict__ dst, float* __restrict__ norm,
                  uint32_t* __restrict__ perm) {
+  __shared__ unsigned int base[256];
+  base[threadIdx.x] = 0;
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+  const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5);
+  // This block's rows are w0 + w + k * warps (w < 8): slot s = 8k + w.
+  for (int64_t sl = threadIdx.x;; sl += blockDim.x) {
+    const int64_t r = w0 + (sl & 7) + (sl >> 3) * warps;
+    if (r >= rows) break;
+    atomicAdd(&base[bucket[r]], 1u);
+  }
+  __syncthreads();
+  if (base[threadIdx.x]) base[threadIdx.x] = atomicAdd(&cur[threadIdx.x], base[threadIdx.x]);
+  __syncthreads();
+  for (int64_t r = w0 + (threadIdx.x >> 5); r < rows; r += warps) {
     uint32_t q = 0;
     if (lane == 0) {
-      q = atomicAdd(&cur[bucket[r]], 1u);
+      q = atomicAdd(&base[bucket[r]], 1u);
       perm[q] = (uint32_t)r;
     }
     q = __shfl_sync(0xFFFFFFFFu, q, 0);
@@ -1242,9 +1267,9 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   const size_t ws_bytes = al(select_ws_bytes(cand_cap, kkeep));
   const size_t ws2_bytes = al(select_ws_bytes(kkeep, t ? t : 1));
   const size_t cvals_bytes = al((size_t)kkeep * 4);
-  // Pre-pass: the corner of the largest norms, the first quarter of the row
-  // blocks times the first quarter of the column tiles (a 16th of the tiles).
-  const long long pre_rows = (tiles_m + 3) / 4, pre_cols = (tiles_n + 3) / 4;
+  // Pre-pass: the corner of the largest norms, the first eighth of the row
+  // blocks times the first eighth of the column tiles (a 64th of the tiles).
+  const long long pre_rows = (tiles_m + 7) / 8, pre_cols = (tiles_n + 7) / 8;
   const long long pre_tiles = pre_rows * pre_cols;   // slots of the row-segment maxima
   const size_t pre_bytes = al((size_t)pre_tiles * kEpi * 4);
   const size_t hist_bytes = al(4097 * 4);
