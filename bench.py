@@ -69,6 +69,16 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _bf16_peak():
+    """Dense BF16 tensor peak (TFLOP/s) of a kernel timed alone: the
+    measured cuBLAS burst figure, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
 def dense_table_bytes(w):
     """Bytes of the tables a dense diamond's draws read at random: T2 and TA
     (m x d uint32), TB (d x n uint32), B (d x n FP32) and T1 (m uint64)."""
@@ -622,12 +632,20 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 cms.append(c0.elapsed_time(c1))
             ci, cj, _, _ = mad.decode_pairs(res_c, nrc)
-            kp = 64 if w.d <= 64 else 128
+            k_issued = 16 * ((w.d + 15) // 16)   # the MMAs stop at the first K step past d
             cm = float(np.mean(cms))
+            useful = 2.0 * w.m * w.n * w.d / (cm / 1e3) / 1e12
+            bpeak, bkind = _bf16_peak()
             comp = {"kernel": "k_gemm_topk", "ms": round(cm, 4),
                     "rescore": args.rescore or 8 * t,
-                    "tflops_useful": round(2.0 * w.m * w.n * w.d / (cm / 1e3) / 1e12, 1),
-                    "tflops_issued": round(2.0 * w.m * w.n * kp / (cm / 1e3) / 1e12, 1)}
+                    "tflops_useful": round(useful, 1),
+                    "tflops_issued": round(2.0 * w.m * w.n * k_issued / (cm / 1e3) / 1e12, 1),
+                    # The whole call (casts, norm order, threshold pre-pass,
+                    # GEMM with its filter, selections, FP32 rescore) against
+                    # the bf16 burst peak: useful FLOPs 2 m n d.
+                    "roofline": {"bound": "tensor", "achieved": round(useful, 1), "peak": bpeak,
+                                 "peak_kind": bkind, "unit": "TFLOP/s",
+                                 "frac": round(useful / bpeak, 4)}}
             if recall is not None:
                 got_c = set(mad.keys_of(ci, cj).astype(np.int64).tolist())
                 comp["recall"] = len(got_c & truth) / t
