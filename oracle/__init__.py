@@ -21,6 +21,8 @@ arrays; every function mirrors one step of the paper:
 * ``enumerate``                     -- exact three-path law (Lemma 1).
 * ``enumerate_wedges``              -- exact wedge law (the appendix's wedge
   sampling; Oracle(..., flags | WEDGE) draws wedges instead of diamonds).
+* ``alias_table``                   -- the alias tables of Oracle(..., flags |
+  ALIAS), whose draws take the same laws from alias tables (Sec. 4.1).
 """
 from __future__ import annotations
 
@@ -37,7 +39,9 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 FMT_DENSE, FMT_CSR = 0, 1
 DT_F32, DT_F64, DT_BINARY = 0, 1, 2
-NONNEG, GRAM, EXCLUDE_DIAG, SQUARE_SYM, WEDGE = 1, 2, 4, 8, 16
+NONNEG, GRAM, EXCLUDE_DIAG, SQUARE_SYM, WEDGE, ALIAS = 1, 2, 4, 8, 16, 32
+ALIAS_SEG = 1024
+ALIAS_ENTRY = np.dtype([("t", np.uint64), ("a", np.uint32), ("pad", np.uint32)])
 STATUS = {0: "ok", 1: "bad argument", 4: "overflow", 5: "empty", 8: "unsupported"}
 
 
@@ -87,6 +91,8 @@ def _L() -> ctypes.CDLL:
         lib.or_bruteforce.argtypes = [P, u64, P, P]
         lib.or_sparse_exact.restype = i64
         lib.or_sparse_exact.argtypes = [P, u64, P, P]
+        lib.or_alias.restype = i64
+        lib.or_alias.argtypes = [P, i32, i32, P]
         lib.or_enumerate_wedges.restype = i64
         lib.or_enumerate_wedges.argtypes = [P, i64, P, P, P, P, P]
         lib.or_enumerate.restype = i64
@@ -175,6 +181,23 @@ class Oracle:
         out = np.zeros(n, dtype=dt)
         _L().or_table(self.h, which, _p(out))
         return out
+
+    _ALIAS = {"T1": 0, "T2": 1, "TA": 2, "TB": 3}
+
+    def alias_table(self, name: str):
+        """(entries, segment totals, row totals) of the alias family `name`
+        (T1, T2, TA, TB): entries has fields t, a; row r's segments' entries
+        then its top-level entries."""
+        fam = self._ALIAS[name]
+        out = []
+        for part, dt in ((0, ALIAS_ENTRY), (1, np.uint64), (2, np.uint64)):
+            n = _L().or_alias(self.h, fam, part, None)
+            if n < 0:
+                raise ValueError("no alias tables (build with flags | ALIAS)")
+            a = np.zeros(n, dtype=dt)
+            _L().or_alias(self.h, fam, part, _p(a))
+            out.append(a)
+        return tuple(out)
 
     def scalars(self) -> dict:
         out = np.zeros(8, dtype=np.int64)

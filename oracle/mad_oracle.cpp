@@ -27,7 +27,11 @@
 //     (l_lo, l_hi, instance, block) for diamond index l;
 //   * the increment sgn(a_ik b_kj a_ik') b_k'j is accumulated in int64 fixed
 //     point: b_k'j (as FP32) times 2^F rounded to nearest-even;
-//   * 0/1 CSR inputs run in exact integer mode (no scaling at all).
+//   * 0/1 CSR inputs run in exact integer mode (no scaling at all);
+//   * with FL_ALIAS (dense float inputs) the four draws take the same laws
+//     from alias tables over the same integer weights (Vose's method in
+//     exact integers, two levels above 1024 entries, the second level's
+//     uniforms from Philox blocks 2 and 3).
 //
 // Parity is pinned by the tests: Philox known-answer vectors, Lemma 1 and
 // Lemma 2 closed forms, the binary diamond count c_ij^2, brute-force top-t
@@ -44,7 +48,8 @@ namespace {
 
 enum { FMT_DENSE = 0, FMT_CSR = 1 };
 enum { DT_F32 = 0, DT_F64 = 1, DT_BINARY = 2 };
-enum { FL_NONNEG = 1u, FL_GRAM = 2u, FL_EXCLUDE_DIAG = 4u, FL_SQSYM = 8u, FL_WEDGE = 16u };
+enum { FL_NONNEG = 1u, FL_GRAM = 2u, FL_EXCLUDE_DIAG = 4u, FL_SQSYM = 8u, FL_WEDGE = 16u,
+       FL_ALIAS = 32u };
 enum {
   ST_OK = 0, ST_ARG = 1, ST_OVERFLOW = 4, ST_EMPTY = 5, ST_UNSUPPORTED = 8
 };
@@ -183,6 +188,31 @@ bool load_matrix(int fmt, int dt, int64_t rows, int64_t cols, int64_t ld, const 
   return true;
 }
 
+// Alias tables (Sec. 4.1 names the alias method for constant-time draws
+// from a discrete distribution).  A table over weights x_0..x_{n-1} with
+// total X holds, per column c, a threshold t_c in [0, X] and an alias a_c:
+// a draw takes column c uniformly and keeps c with probability t_c / X,
+// else returns a_c.  Built by Vose's method in exact integers, so that
+// P(c) = x_c / X holds exactly.  Tables longer than kAliasSeg entries have
+// two levels: segments of kAliasSeg entries, each with its own table, and
+// one table over the segment totals.
+constexpr int64_t kAliasSeg = 1024;
+
+struct AliasEnt {
+  uint64_t t;
+  uint32_t a;
+  uint32_t pad;
+};
+
+// A family of alias tables of the same length L, one per row.  Row r holds
+// its segments' entries (L of them) followed by the table over its segments
+// (nseg entries); segX and rowX hold the segment and row totals.
+struct AliasFam {
+  int64_t rows = 0, L = 0, nseg = 0;
+  std::vector<AliasEnt> ent;
+  std::vector<uint64_t> segX, rowX;
+};
+
 struct Oracle {
   uint32_t flags = 0;
   bool integer = false;
@@ -208,6 +238,10 @@ struct Oracle {
   std::vector<float> nac, wk;
   std::vector<uint64_t> TK;
   int EK = 0;
+  // Alias draws (FL_ALIAS): tables over the weights of T1, of every row of
+  // T2 and TA, and of every row of TB.
+  bool alias = false;
+  AliasFam T1al, T2al, TAal, TBal;
   // Sampling state.
   std::unordered_map<uint64_t, int64_t> X;
   uint64_t sampled = 0, inserted = 0, diag_skipped = 0;
@@ -398,6 +432,122 @@ int build_wedge_tables(Oracle& o) {
   return ST_OK;
 }
 
+// Vose's construction over x[0..n), total X: small and large columns
+// (n x_c below X, or not) are stacks filled in column order; the top small
+// column s takes its own share n x_s and the top large column l the rest,
+// after which l's remaining weight n x_l - (X - n x_s) classifies it again.
+// Columns left at the end keep themselves.
+void vose(const uint64_t* x, int64_t n, uint64_t X, AliasEnt* out) {
+  std::vector<unsigned __int128> p((size_t)n);
+  std::vector<int64_t> small, large;
+  for (int64_t c = 0; c < n; ++c) {
+    p[c] = (unsigned __int128)x[c] * (uint64_t)n;
+    if (p[c] < X) small.push_back(c);
+    else large.push_back(c);
+  }
+  while (!small.empty() && !large.empty()) {
+    const int64_t sc = small.back();
+    small.pop_back();
+    const int64_t lc = large.back();
+    large.pop_back();
+    out[sc].t = (uint64_t)p[sc];
+    out[sc].a = (uint32_t)lc;
+    out[sc].pad = 0;
+    p[lc] -= (unsigned __int128)(X - (uint64_t)p[sc]);
+    if (p[lc] < X) small.push_back(lc);
+    else large.push_back(lc);
+  }
+  for (int64_t c : large) out[c] = AliasEnt{X, (uint32_t)c, 0};
+  for (int64_t c : small) out[c] = AliasEnt{X, (uint32_t)c, 0};
+}
+
+// The family over `rows` rows of length L whose weight c of row r is
+// weight(r, c).
+template <typename Weight>
+void build_alias_family(AliasFam& f, int64_t rows, int64_t L, Weight weight) {
+  f.rows = rows;
+  f.L = L;
+  f.nseg = (L + kAliasSeg - 1) / kAliasSeg;
+  f.ent.assign((size_t)(rows * (L + f.nseg)), AliasEnt{0, 0, 0});
+  f.segX.assign((size_t)(rows * f.nseg), 0);
+  f.rowX.assign((size_t)rows, 0);
+  std::vector<uint64_t> w;
+  for (int64_t r = 0; r < rows; ++r) {
+    AliasEnt* row = f.ent.data() + r * (L + f.nseg);
+    uint64_t total = 0;
+    for (int64_t sg = 0; sg < f.nseg; ++sg) {
+      const int64_t c0 = sg * kAliasSeg, len = std::min(kAliasSeg, L - c0);
+      w.assign((size_t)len, 0);
+      uint64_t X = 0;
+      for (int64_t c = 0; c < len; ++c) {
+        w[c] = weight(r, c0 + c);
+        X += w[c];
+      }
+      vose(w.data(), len, X, row + c0);
+      f.segX[r * f.nseg + sg] = X;
+      total += X;
+    }
+    f.rowX[r] = total;
+    if (f.nseg > 1) vose(f.segX.data() + r * f.nseg, f.nseg, total, row + L);
+    else row[L] = AliasEnt{total, 0, 0};
+  }
+}
+
+// One alias draw over entries e[0..n) of total X with the 64-bit uniform u:
+// column floor(u n / 2^64); the low 64 bits f of u n decide between the
+// column and its alias, keeping the column when floor(f X / 2^64) < t.
+int64_t alias_pick(const AliasEnt* e, int64_t n, uint64_t X, uint64_t u) {
+  const unsigned __int128 pr = (unsigned __int128)u * (uint64_t)n;
+  const int64_t col = (int64_t)(pr >> 64);
+  const uint64_t f = (uint64_t)pr;
+  const uint64_t hi = (uint64_t)(((unsigned __int128)f * X) >> 64);
+  return hi < e[col].t ? col : (int64_t)e[col].a;
+}
+
+// Position in row r of family f: the segment from u_top (two levels only),
+// then the column inside it from u_in (u_top when there is one segment).
+int64_t alias_draw(const AliasFam& f, int64_t r, uint64_t u_top, uint64_t u_in) {
+  const AliasEnt* row = f.ent.data() + r * (f.L + f.nseg);
+  if (f.nseg == 1) return alias_pick(row, f.L, f.segX[r], u_top);
+  const int64_t sg = alias_pick(row + f.L, f.nseg, f.rowX[r], u_top);
+  const int64_t c0 = sg * kAliasSeg, len = std::min(kAliasSeg, f.L - c0);
+  return c0 + alias_pick(row + c0, len, f.segX[r * f.nseg + sg], u_in);
+}
+
+// Alias tables of the dense float tables: the weights are the differences
+// of consecutive prefix entries (T1 over rows, T2 and TA along each row of
+// A, TB along each row of B).
+int build_alias_tables(Oracle& o) {
+  if (o.integer || !o.A.dense || !o.B.dense) return ST_UNSUPPORTED;
+  build_alias_family(o.T1al, 1, o.m, [&](int64_t, int64_t c) {
+    return o.T1[c] - (c ? o.T1[c - 1] : 0);
+  });
+  auto row_weight = [](const std::vector<uint32_t>& T, int64_t L) {
+    return [&T, L](int64_t r, int64_t c) -> uint64_t {
+      const int64_t e = r * L + c;
+      return (uint64_t)T[e] - (c ? (uint64_t)T[e - 1] : 0);
+    };
+  };
+  build_alias_family(o.T2al, o.m, o.d, row_weight(o.T2, o.d));
+  build_alias_family(o.TAal, o.m, o.d, row_weight(o.TA, o.d));
+  build_alias_family(o.TBal, o.d, o.n, row_weight(o.TB, o.n));
+  return ST_OK;
+}
+
+// Uniforms of Philox blocks 2 and 3 of diamond ell: the segment-level
+// uniforms of the two-level alias draws (index q of (i, k, j, k') uses u[q]
+// of blocks 0-1 first and the q-th uniform here second).
+void alias_uniforms(uint64_t seed, uint64_t ell, uint64_t u[4]) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (uint32_t block = 2; block < 4; ++block) {
+    const uint32_t ctr[4] = {(uint32_t)ell, (uint32_t)(ell >> 32), 0u, block};
+    uint32_t w[4];
+    philox4x32_10(ctr, key, w);
+    u[2 * (block - 2) + 0] = ((uint64_t)w[1] << 32) | w[0];
+    u[2 * (block - 2) + 1] = ((uint64_t)w[3] << 32) | w[2];
+  }
+}
+
 // Value b_{k'j} of B (0 when absent).
 double b_value(const Oracle& o, int64_t kp, int64_t j, float* valf) {
   const Mat& B = o.B;
@@ -456,18 +606,38 @@ Draw draw_diamond(const Oracle& o, uint64_t seed, uint64_t ell) {
   const Mat& A = o.A;
   const Mat& B = o.B;
   Draw dr;
-  // Center edge (i,k) with probability w_ik / ||W||_1, in two stages.
-  const int64_t i = inverse_cdf(o.T1.data(), o.m, draw_target(u[0], o.T1[o.m - 1]));
-  const int64_t a0 = A.ptr[i], alen = A.ptr[i + 1] - A.ptr[i];
-  const int64_t pk = inverse_cdf(o.T2.data() + a0, alen, draw_target(u[1], o.T2[a0 + alen - 1]));
-  const int64_t k = A.col[a0 + pk];
-  // j with probability |b_kj| / ||b_k*||_1.
-  const int64_t b0 = B.ptr[k], blen = B.ptr[k + 1] - B.ptr[k];
-  const int64_t pj = inverse_cdf(o.TB.data() + b0, blen, draw_target(u[2], o.TB[b0 + blen - 1]));
-  const int64_t j = B.col[b0 + pj];
-  // k' with probability |a_ik'| / ||a_i*||_1.
-  const int64_t pkp = inverse_cdf(o.TA.data() + a0, alen, draw_target(u[3], o.TA[a0 + alen - 1]));
-  const int64_t kp = A.col[a0 + pkp];
+  int64_t i, a0, alen, pk, k, b0, blen, pj, j, pkp, kp;
+  if (o.alias) {
+    // The same four laws, each drawn from its alias table.
+    uint64_t v[4];
+    alias_uniforms(seed, ell, v);
+    i = alias_draw(o.T1al, 0, u[0], v[0]);
+    a0 = A.ptr[i];
+    alen = A.ptr[i + 1] - a0;
+    pk = alias_draw(o.T2al, i, u[1], v[1]);
+    k = A.col[a0 + pk];
+    b0 = B.ptr[k];
+    blen = B.ptr[k + 1] - b0;
+    pj = alias_draw(o.TBal, k, u[2], v[2]);
+    j = B.col[b0 + pj];
+    pkp = alias_draw(o.TAal, i, u[3], v[3]);
+    kp = A.col[a0 + pkp];
+  } else {
+    // Center edge (i,k) with probability w_ik / ||W||_1, in two stages.
+    i = inverse_cdf(o.T1.data(), o.m, draw_target(u[0], o.T1[o.m - 1]));
+    a0 = A.ptr[i];
+    alen = A.ptr[i + 1] - A.ptr[i];
+    pk = inverse_cdf(o.T2.data() + a0, alen, draw_target(u[1], o.T2[a0 + alen - 1]));
+    k = A.col[a0 + pk];
+    // j with probability |b_kj| / ||b_k*||_1.
+    b0 = B.ptr[k];
+    blen = B.ptr[k + 1] - B.ptr[k];
+    pj = inverse_cdf(o.TB.data() + b0, blen, draw_target(u[2], o.TB[b0 + blen - 1]));
+    j = B.col[b0 + pj];
+    // k' with probability |a_ik'| / ||a_i*||_1.
+    pkp = inverse_cdf(o.TA.data() + a0, alen, draw_target(u[3], o.TA[a0 + alen - 1]));
+    kp = A.col[a0 + pkp];
+  }
   // Increment sgn(a_ik b_kj a_ik') b_k'j.
   float bf = 0.0f;
   b_value(o, kp, j, &bf);
@@ -572,8 +742,15 @@ void* or_create(int fmtA, int dtA, int64_t m, int64_t d, int64_t ldA, const void
     delete o;
     return nullptr;
   }
+  o->alias = (flags & FL_ALIAS) != 0;
+  if (o->alias && o->wedge) {
+    *status = ST_UNSUPPORTED;
+    delete o;
+    return nullptr;
+  }
   *status = build_tables(*o);
   if (*status == ST_OK && o->wedge) *status = build_wedge_tables(*o);
+  if (*status == ST_OK && o->alias) *status = build_alias_tables(*o);
   if (*status != ST_OK) {
     delete o;
     return nullptr;
@@ -600,6 +777,22 @@ int64_t or_table(void* h, int which, void* out) {
     case 8: if (out) std::memcpy(out, o->TK.data(), o->TK.size() * 8); return (int64_t)o->TK.size();
     case 9: if (out) std::memcpy(out, o->TAc.data(), o->TAc.size() * 4); return (int64_t)o->TAc.size();
     case 10: if (out) std::memcpy(out, o->nac.data(), o->nac.size() * 4); return (int64_t)o->nac.size();
+  }
+  return -1;
+}
+
+// Alias table export: family 0 T1, 1 T2, 2 TA, 3 TB; part 0 the entries
+// (16 bytes each: u64 t, u32 a, u32 0; rows x (L + nseg)), 1 the segment
+// totals (u64, rows x nseg), 2 the row totals (u64, rows).  Returns the
+// element count, -1 without alias tables.
+int64_t or_alias(void* h, int fam, int part, void* out) {
+  Oracle* o = (Oracle*)h;
+  if (!o->alias || fam < 0 || fam > 3) return -1;
+  const AliasFam& f = fam == 0 ? o->T1al : fam == 1 ? o->T2al : fam == 2 ? o->TAal : o->TBal;
+  switch (part) {
+    case 0: if (out) std::memcpy(out, f.ent.data(), f.ent.size() * 16); return (int64_t)f.ent.size();
+    case 1: if (out) std::memcpy(out, f.segX.data(), f.segX.size() * 8); return (int64_t)f.segX.size();
+    case 2: if (out) std::memcpy(out, f.rowX.data(), f.rowX.size() * 8); return (int64_t)f.rowX.size();
   }
   return -1;
 }

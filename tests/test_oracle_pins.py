@@ -676,3 +676,129 @@ def test_wedge_sampling_finds_planted_pairs():
     truth, _ = o.bruteforce(10)
     keys, c = o.run(s=2_000_000, seed=4, tprime=100, t=10)
     assert set(keys.tolist()) == set(truth.tolist())
+
+
+# ---------------------------------------------------------------------------
+# Alias tables (Sec. 4.1: the alias method for constant-time draws)
+# ---------------------------------------------------------------------------
+def _alias_instance(seed=71, m=1500, d=7, n=2500):
+    """T1 over 1500 rows and TB rows of 2500 entries have two levels
+    (segments of 1024 entries); the rows of T2 and TA have one.  A few exact
+    zeros give zero weights."""
+    rng = _rng(seed)
+    A = rng.standard_normal((m, d)) * np.exp(0.7 * rng.standard_normal((m, 1)))
+    B = rng.standard_normal((d, n)) * np.exp(0.7 * rng.standard_normal((1, n)))
+    A[rng.random(A.shape) < 0.03] = 0.0
+    B[:, 5] = 0.0
+    return A, B
+
+
+def _weights(prefix, L):
+    """Per-row weights of a prefix table with rows of length L."""
+    P = prefix.astype(np.int64).reshape(-1, L)
+    return np.diff(np.concatenate([np.zeros((P.shape[0], 1), np.int64), P], axis=1), axis=1)
+
+
+def _check_alias_level(ent, x):
+    """One alias table over integer weights x: n x_i equals the mass that the
+    table sends to i, t_c for its own column plus X - t_c from every column
+    whose alias it is; thresholds in [0, X], aliases in range."""
+    n = len(x)
+    X = int(sum(int(v) for v in x))
+    t = [int(v) for v in ent["t"]]
+    a = [int(v) for v in ent["a"]]
+    assert all(0 <= v <= X for v in t) and all(0 <= v < n for v in a)
+    mass = [0] * n
+    for c in range(n):
+        mass[c] += t[c]
+        mass[a[c]] += X - t[c]
+    assert mass == [n * int(v) for v in x]
+
+
+def test_alias_tables_reproduce_the_weights_exactly():
+    """Every level of every alias table (T1 and TB with two levels, T2 and
+    TA with one) gives each entry exactly its weight over the total, in
+    integers: P(c) = x_c / X."""
+    A, B = _alias_instance()
+    o = _dense(A, B, flags=oracle.ALIAS)
+    m, d = A.shape
+    n = B.shape[1]
+    fams = {"T1": _weights(o.table("T1"), m), "T2": _weights(o.table("T2"), d),
+            "TA": _weights(o.table("TA"), d), "TB": _weights(o.table("TB"), n)}
+    S = oracle.ALIAS_SEG
+    for name, W in fams.items():
+        ent, segX, rowX = o.alias_table(name)
+        rows, L = W.shape
+        nseg = (L + S - 1) // S
+        assert len(ent) == rows * (L + nseg) and len(segX) == rows * nseg
+        for r in range(rows) if rows < 50 else [0, 1, rows // 2, rows - 1]:
+            e = ent[r * (L + nseg):(r + 1) * (L + nseg)]
+            seg = []
+            for s in range(nseg):
+                x = W[r, s * S:(s + 1) * S]
+                assert int(segX[r * nseg + s]) == int(x.sum())
+                _check_alias_level(e[s * S:s * S + len(x)], x)
+                seg.append(int(x.sum()))
+            assert int(rowX[r]) == int(W[r].sum())
+            if nseg > 1:
+                _check_alias_level(e[L:], seg)
+
+
+def _chi2_pvalue(obs, p):
+    from scipy.stats import chisquare
+    keep = p > 0
+    assert obs[~keep].sum() == 0   # never drawn where the law is 0
+    return chisquare(obs[keep], p[keep] * obs.sum()).pvalue
+
+
+def test_alias_draws_follow_the_laws():
+    """The alias draw mapping: 400k diamonds of the alias sampler.  Row i
+    (two-level T1) and column j (two-level TB rows, through the marginal over
+    k) against their exact laws by chi-square; zero-weight entries never
+    drawn."""
+    A, B = _alias_instance()
+    o = _dense(A, B, flags=oracle.ALIAS)
+    m, d = A.shape
+    n = B.shape[1]
+    i, k, j, kp, v = o.draw(seed=5, first=1 << 20, count=400_000)
+    w1 = _weights(o.table("T1"), m)[0].astype(np.float64)
+    p_i = w1 / w1.sum()
+    assert _chi2_pvalue(np.bincount(i, minlength=m).astype(float), p_i) > 1e-4
+    # j's marginal: sum_k P(k) P(j | k), P(k) from the T2 rows of the drawn i.
+    T2w = _weights(o.table("T2"), d).astype(np.float64)
+    TBw = _weights(o.table("TB"), n).astype(np.float64)
+    pk_given_i = T2w / T2w.sum(axis=1, keepdims=True)
+    p_k = p_i @ pk_given_i
+    p_j = p_k @ (TBw / TBw.sum(axis=1, keepdims=True))
+    assert _chi2_pvalue(np.bincount(j, minlength=n).astype(float), p_j) > 1e-4
+    assert not np.any(j == 5)   # column 5 of B is zero: weight 0 in every TB row
+
+
+def test_alias_joint_law_on_a_tiny_instance():
+    """All four draws at once on an instance small enough to enumerate: the
+    alias sampler's (i, k, j, k') frequencies against the enumerated law of
+    Lemma 1 (the same law as the prefix-table sampler's)."""
+    rng = _rng(72)
+    A = rng.standard_normal((4, 3))
+    B = rng.standard_normal((3, 5))
+    A[1, 2] = 0.0
+    o = _dense(A, B, flags=oracle.ALIAS)
+    ei, ek, ej, ekp, prob, _ = _dense(A, B).enumerate()
+    idx = {(a, b, c, e): q for q, (a, b, c, e) in enumerate(zip(ei, ek, ej, ekp))}
+    i, k, j, kp, _ = o.draw(seed=9, first=0, count=300_000)
+    obs = np.zeros(len(prob))
+    for t in zip(i, k, j, kp):
+        obs[idx[t]] += 1
+    assert _chi2_pvalue(obs, prob) > 1e-4
+
+
+def test_alias_flag_rules():
+    """Alias tables are built for dense float inputs: 0/1 inputs and wedge
+    sampling refuse the flag."""
+    A, M = _sym_binary(20, 0.2, 73)
+    with pytest.raises(Exception):
+        Oracle(M, M, oracle.ALIAS | 2)
+    rng = _rng(74)
+    with pytest.raises(Exception):
+        _dense(rng.standard_normal((5, 3)), rng.standard_normal((3, 4)),
+               flags=oracle.ALIAS | oracle.WEDGE)
