@@ -128,8 +128,24 @@ typedef struct mad_pair {
  *                     a plain table of at least s_max / 0.6 slots; mad_stats
  *                     reports ||w||_1 in place of ||W||_1; not with
  *                     MAD_SQUARE_SYM or the fused pass. */
+/* MAD_ALIAS:         draws from alias tables (Sec. 4.1 names the alias
+ *                     method for constant-time draws): mad_build_tables
+ *                     also builds, over the same integer weights as T1, the
+ *                     rows of T2 and TA and the rows of TB, tables that give
+ *                     each entry exactly its weight over the total (Vose's
+ *                     method in exact integers; tables longer than 1024
+ *                     entries have two levels, segments of 1024 and a table
+ *                     over the segment totals).  mad_sample then draws each
+ *                     of (i, k, j, k') from its alias table: a column from
+ *                     the high bits of u * n, kept against its threshold by
+ *                     the low bits, else its alias; the second level of a
+ *                     two-level draw takes its uniform from Philox blocks 2
+ *                     and 3 of the diamond.  Same law, another map from the
+ *                     uniforms.  Dense float inputs with m and n up to 2^20
+ *                     (MAD_ERR_UNSUPPORTED otherwise); not with MAD_WEDGE or
+ *                     the fused pass. */
 enum { MAD_NONNEG = 1u, MAD_GRAM = 2u, MAD_EXCLUDE_DIAG = 4u, MAD_SQUARE_SYM = 8u,
-       MAD_WEDGE = 16u };
+       MAD_WEDGE = 16u, MAD_ALIAS = 32u };
 
 typedef struct mad_stats_t {
   double w1;                /* ||W||_1 as represented by the tables */
@@ -503,6 +519,11 @@ mad_status mad_export_x(mad_ctx* ctx, uint64_t* keys_dev, int64_t* vals_dev, uin
  *   wedge contexts: 7 TK (uint64, d, inclusive prefix of the centre
  *   weights), 8 column tables of A (uint32, m x d column-major; dense
  *   non-Gram inputs), 9 ||a_*k||_1 (f32, d; dense inputs)
+ *   alias contexts (MAD_ALIAS): 10 + 3 f + part for the families f = 0 T1
+ *   (1 row of m), 1 T2 and 2 TA (m rows of d), 3 TB (d rows of n); part 0
+ *   the entries (16 bytes: uint64 threshold, uint32 alias, uint32 0; per
+ *   row its segments' entries then its nseg top-level entries), 1 the
+ *   segment totals (uint64, rows x nseg), 2 the row totals (uint64, rows)
  * Row-table entries carry the sign of the matching value of A or B in bit
  * 31 (float mode).  Tables the mode keeps implicit report 0 elements.
  * *n_host receives the element count.  Synchronises the stream. */

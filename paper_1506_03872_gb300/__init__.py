@@ -24,9 +24,13 @@ MAD_OK, MAD_ERR_ARG, MAD_ERR_OOM, MAD_ERR_CUDA, MAD_ERR_OVERFLOW = 0, 1, 2, 3, 4
 MAD_ERR_EMPTY, MAD_ERR_HASH_FULL, MAD_ERR_STATE, MAD_ERR_UNSUPPORTED = 5, 6, 7, 8
 MAD_DENSE_ROWMAJOR, MAD_CSR = 0, 1
 MAD_F32, MAD_F64, MAD_BINARY = 0, 1, 2
-MAD_NONNEG, MAD_GRAM, MAD_EXCLUDE_DIAG, MAD_SQUARE_SYM, MAD_WEDGE = 1, 2, 4, 8, 16
+MAD_NONNEG, MAD_GRAM, MAD_EXCLUDE_DIAG, MAD_SQUARE_SYM, MAD_WEDGE, MAD_ALIAS = 1, 2, 4, 8, 16, 32
 TABLES = {"T1": 0, "T2": 1, "TA": 2, "TB": 3, "na": 4, "nb": 5, "r": 6, "TK": 7, "TAc": 8,
           "nac": 9}
+# Alias families (MAD_ALIAS): <family>al entries (two int64 per entry:
+# threshold, alias), <family>as segment totals, <family>ar row totals.
+for _q, _f in enumerate(("T1", "T2", "TA", "TB")):
+    TABLES[_f + "al"], TABLES[_f + "as"], TABLES[_f + "ar"] = 10 + 3 * _q, 11 + 3 * _q, 12 + 3 * _q
 
 # Every symbol include/mad.h declares.
 EXPORTS = (
@@ -477,12 +481,14 @@ def mad_export_table(ctx, name: str, stream=None):
     n = ctypes.c_uint64(0)
     _check(lib().mad_export_table(ctx, which, None, 0, ctypes.byref(n), _stream(stream)),
            "mad_export_table")
-    dt = torch.int64 if name in ("T1", "TK") else (
+    alias = name[-2:] in ("al", "as", "ar")
+    dt = torch.int64 if name in ("T1", "TK") or alias else (
         torch.float32 if name in ("na", "nb", "r", "nac") else torch.int32)
-    out = torch.empty(max(n.value, 1), dtype=dt, device="cuda")
+    per = 2 if name.endswith("al") else 1   # alias entries: 16 bytes
+    out = torch.empty(max(per * n.value, 1), dtype=dt, device="cuda")
     _check(lib().mad_export_table(ctx, which, _ptr(out), n.value, ctypes.byref(n),
                                   _stream(stream)), "mad_export_table")
-    return out[:n.value]
+    return out[:per * n.value]
 
 
 # ---------------------------------------------------------------------------

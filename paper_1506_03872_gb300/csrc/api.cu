@@ -85,6 +85,12 @@ void free_tables(mad_ctx* ctx, cudaStream_t st) {
   free_async(ctx->TK, st);
   free_async(ctx->TAc, st);
   free_async(ctx->nac, st);
+  for (int f = 0; f < 4; ++f) {
+    free_async(ctx->al[f], st);
+    free_async(ctx->al_seg[f], st);
+    free_async(ctx->al_row[f], st);
+    ctx->al_nseg[f] = 0;
+  }
   ctx->TK_shift = 0;
   ctx->tk_total = 0;
   free_async(ctx->pipe_buf, st);
@@ -175,6 +181,10 @@ mad_status check_inputs(const mad_ctx* ctx, const mad_matrix* A, const mad_matri
   // inputs, and square ones when dense (the caller guarantees symmetry).
   if ((ctx->flags & MAD_SQUARE_SYM) &&
       (!(ctx->flags & MAD_GRAM) || (!csr && A->rows != A->cols)))
+    return MAD_ERR_UNSUPPORTED;
+  // Alias tables: dense float inputs, tables of at most 2^20 entries.
+  if ((ctx->flags & MAD_ALIAS) &&
+      (!dense || A->rows > kAliasSeg * kAliasSeg || B->cols > kAliasSeg * kAliasSeg))
     return MAD_ERR_UNSUPPORTED;
   *dense_out = dense;
   return MAD_OK;
@@ -319,9 +329,10 @@ extern "C" {
 mad_status mad_create(mad_ctx** out, uint32_t flags) {
   if (!out) return MAD_ERR_ARG;
   *out = nullptr;
-  if (flags & ~(uint32_t)(MAD_NONNEG | MAD_GRAM | MAD_EXCLUDE_DIAG | MAD_SQUARE_SYM | MAD_WEDGE))
+  if (flags & ~(uint32_t)(MAD_NONNEG | MAD_GRAM | MAD_EXCLUDE_DIAG | MAD_SQUARE_SYM | MAD_WEDGE |
+                          MAD_ALIAS))
     return MAD_ERR_ARG;
-  if ((flags & MAD_WEDGE) && (flags & MAD_SQUARE_SYM)) return MAD_ERR_ARG;
+  if ((flags & MAD_WEDGE) && (flags & (MAD_SQUARE_SYM | MAD_ALIAS))) return MAD_ERR_ARG;
   mad_ctx* ctx = new (std::nothrow) mad_ctx();
   if (!ctx) return MAD_ERR_OOM;
   ctx->flags = flags;
@@ -443,6 +454,7 @@ mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
     if ((rs = enqueue_dense_build(ctx, st)) != MAD_OK) return rs;
     if ((rs = finish_dense_build(ctx, st)) != MAD_OK) return rs;
     if (wedge && (rs = finish_wedge_build(ctx, st)) != MAD_OK) return rs;
+    if ((ctx->flags & MAD_ALIAS) && (rs = build_alias_tables(ctx, st)) != MAD_OK) return rs;
     ctx->built = true;
     return MAD_OK;
   }
@@ -694,7 +706,18 @@ mad_status mad_export_table(mad_ctx* ctx, int which, void* out_dev, uint64_t cap
             count = ctx->TK ? (uint64_t)ctx->d : 0; break;
     case 8: src = ctx->TAc; count = ctx->TAc ? (uint64_t)(ctx->m * ctx->d) : 0; break;
     case 9: src = ctx->nac; count = ctx->nac ? (uint64_t)ctx->d : 0; break;
-    default: return MAD_ERR_ARG;
+    default: {
+      // Alias families (MAD_ALIAS): 10 + 3 f + part, f = T1, T2, TA, TB.
+      if (which < 10 || which >= 22) return MAD_ERR_ARG;
+      const int f = (which - 10) / 3, part = (which - 10) % 3;
+      const int64_t rows = f == kAlT1 ? 1 : f == kAlTB ? ctx->d : ctx->m;
+      const int64_t L = f == kAlT1 ? ctx->m : f == kAlTB ? ctx->n : ctx->d;
+      const int64_t nseg = ctx->al_nseg[f];
+      if (!ctx->al[f]) break;
+      if (part == 0) { src = ctx->al[f]; elem = sizeof(AliasEnt); count = (uint64_t)(rows * (L + nseg)); }
+      else if (part == 1) { src = ctx->al_seg[f]; elem = 8; count = (uint64_t)(rows * nseg); }
+      else { src = ctx->al_row[f]; elem = 8; count = (uint64_t)rows; }
+    }
   }
   *n_host = count;
   if (count == 0 || cap == 0) return MAD_OK;

@@ -133,8 +133,63 @@ __device__ __forceinline__ Draw draw_given_row(const SampleParams& p, const Unif
   return dr;
 }
 
+// One alias draw over entries e[0..n) of total X with the uniform u: column
+// floor(u n / 2^64); the low 64 bits f of u n keep the column when
+// floor(f X / 2^64) < t, else its alias is returned.
+__device__ __forceinline__ int64_t alias_pick(const AliasEnt* e, unsigned long long n,
+                                              unsigned long long X, unsigned long long u) {
+  const unsigned long long col = __umul64hi(u, n);
+  const unsigned long long f = u * n;
+  const unsigned long long hi = __umul64hi(f, X);
+  const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(e + col));
+  return hi < v.x ? (int64_t)col : (int64_t)(uint32_t)v.y;
+}
+
+// Position in row r of alias family fam (rows of length L): the segment from
+// u_top (two levels only), then the column inside it from u_in (u_top when
+// the row has one segment).
+__device__ __forceinline__ int64_t alias_draw(const SampleParams& p, int fam, int64_t L, int64_t r,
+                                              unsigned long long u_top, unsigned long long u_in) {
+  const int nseg = p.al_nseg[fam];
+  const AliasEnt* row = p.al[fam] + r * (L + nseg);
+  if (nseg == 1) return alias_pick(row, (unsigned long long)L, __ldg(p.al_seg[fam] + r), u_top);
+  const int64_t sg = alias_pick(row + L, (unsigned long long)nseg, __ldg(p.al_row[fam] + r), u_top);
+  const int64_t c0 = sg * kAliasSeg;
+  const int64_t len = L - c0 < kAliasSeg ? L - c0 : kAliasSeg;
+  return c0 + alias_pick(row + c0, (unsigned long long)len,
+                         __ldg(p.al_seg[fam] + r * nseg + sg), u_in);
+}
+
+// The loop body with the four draws from alias tables (dense float inputs):
+// the same laws as the prefix-table draws, another map from the uniforms.
+__device__ __forceinline__ Draw draw_alias(const SampleParams& p, unsigned long long seed,
+                                           unsigned long long ell) {
+  const Uniforms u = diamond_uniforms(seed, ell);
+  const Uniforms v = alias_uniforms(seed, ell);
+  const int64_t i = alias_draw(p, kAlT1, p.m, 0, u.u0, v.u0);
+  const int64_t k = alias_draw(p, kAlT2, p.d, i, u.u1, v.u1);
+  const int64_t j = alias_draw(p, kAlTB, p.n, k, u.u2, v.u2);
+  const int64_t kp = alias_draw(p, kAlTA, p.d, i, u.u3, v.u3);
+  const uint32_t e_k = __ldg(p.T2 + i * p.d + k);
+  const uint32_t e_kp = __ldg(p.TA + i * p.d + kp);
+  const uint32_t e_j = __ldg(p.TB + k * p.n + j);
+  const int64_t off = kp * p.ldb + j;
+  const float b = p.b_f64 ? __double2float_rn(__ldg((const double*)p.b_val + off))
+                          : __ldg((const float*)p.b_val + off);
+  long long val = fixed_point(b, p.f_exp);
+  if (!(p.flags & MAD_NONNEG) && ((e_k ^ e_j ^ e_kp) & SIGN_BIT)) val = -val;
+  Draw dr;
+  dr.i = (uint32_t)i;
+  dr.k = (uint32_t)k;
+  dr.j = (uint32_t)j;
+  dr.kp = (uint32_t)kp;
+  dr.v = val;
+  return dr;
+}
+
 __device__ __forceinline__ Draw draw_one(const SampleParams& p, unsigned long long seed,
                                          unsigned long long ell, bool* bad) {
+  if (p.alias) return draw_alias(p, seed, ell);
   const Uniforms u = diamond_uniforms(seed, ell);
   return draw_given_row(p, u, draw_row_i(p, u.u0, bad), bad);
 }

@@ -47,6 +47,21 @@ __device__ __forceinline__ Uniforms diamond_uniforms(unsigned long long seed,
   return u;
 }
 
+// Uniforms of Philox blocks 2 and 3 of diamond ell: the segment-level
+// uniforms of two-level alias draws (index q of (i, k, j, k') takes u_q of
+// diamond_uniforms first and the q-th of these second).
+__device__ __forceinline__ Uniforms alias_uniforms(unsigned long long seed, unsigned long long ell) {
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint4 b2 = philox4x32_10(make_uint4((uint32_t)ell, (uint32_t)(ell >> 32), 0u, 2u), key);
+  const uint4 b3 = philox4x32_10(make_uint4((uint32_t)ell, (uint32_t)(ell >> 32), 0u, 3u), key);
+  Uniforms u;
+  u.u0 = ((unsigned long long)b2.y << 32) | b2.x;
+  u.u1 = ((unsigned long long)b2.w << 32) | b2.z;
+  u.u2 = ((unsigned long long)b3.y << 32) | b3.x;
+  u.u3 = ((unsigned long long)b3.w << 32) | b3.z;
+  return u;
+}
+
 // floor(u * total / 2^64).
 __device__ __forceinline__ unsigned long long draw_target(unsigned long long u,
                                                           unsigned long long total) {

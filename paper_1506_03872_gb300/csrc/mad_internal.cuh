@@ -47,6 +47,22 @@ struct DevScalars {
 };
 
 // Everything a sampling kernel needs, passed by value.
+// Alias tables (Sec. 4.1): per column a threshold t in [0, X] over the
+// table's total X and an alias; a draw takes a column uniformly, keeps it
+// with probability t / X, else returns the alias.  Tables longer than
+// kAliasSeg entries have two levels (segments of kAliasSeg entries, and a
+// table over the segment totals).  A family holds one table per row: row r
+// stores its segments' entries (L) and then its top-level entries (nseg).
+constexpr int64_t kAliasSeg = 1024;
+struct AliasEnt {
+  unsigned long long t;
+  uint32_t a;
+  uint32_t pad;
+};
+// Families: 0 T1 (one row over the rows of A), 1 T2 and 2 TA (one row per
+// row of A), 3 TB (one row per row of B).
+enum { kAlT1 = 0, kAlT2 = 1, kAlTA = 2, kAlTB = 3 };
+
 struct SampleParams {
   // A (m x d): dense row-major or 0/1 CSR.
   const void* a_val;
@@ -103,6 +119,13 @@ struct SampleParams {
   int integer;                     // 0/1 exact mode
   uint32_t flags;                  // MAD_NONNEG | MAD_GRAM | MAD_EXCLUDE_DIAG
   DevScalars* sc;
+  // Alias draws (MAD_ALIAS): the four families, their segment and row
+  // totals and segment counts.
+  int alias;
+  const AliasEnt* al[4];
+  const unsigned long long* al_seg[4];
+  const unsigned long long* al_row[4];
+  int al_nseg[4];
 };
 
 // Select item: primary key p (larger first), tie key (smaller first), aux.
@@ -169,6 +192,12 @@ struct mad_ctx {
   int ek = 0;
   float* nac = nullptr;
   uint32_t* TAc = nullptr;
+  // Alias draws (MAD_ALIAS): per family its entries, segment totals, row
+  // totals and segment count.
+  mad::AliasEnt* al[4] = {nullptr, nullptr, nullptr, nullptr};
+  unsigned long long* al_seg[4] = {nullptr, nullptr, nullptr, nullptr};
+  unsigned long long* al_row[4] = {nullptr, nullptr, nullptr, nullptr};
+  int al_nseg[4] = {0, 0, 0, 0};
   // Fused pass (mad_pipeline_*): budgets fixed when planned, one buffer
   // for its selection lists.
   bool pipe = false;
@@ -373,6 +402,9 @@ mad_status select_pairs(mad_ctx* ctx, const mad_pair* pairs, uint64_t n, uint64_
 // wedge.cu: wedge sampling (MAD_WEDGE contexts): the plain hash's slots for
 // s_max wedges, the centre and column tables (after the diamond tables;
 // synchronises), the sampling loop and its diagnostic draws.
+// Alias tables of a built dense float context (MAD_ALIAS); refuses 0/1
+// inputs and tables of more than kAliasSeg segments.
+mad_status build_alias_tables(mad_ctx* ctx, cudaStream_t st);
 uint64_t wedge_hash_slots(uint64_t s_max);
 mad_status build_wedge_tables(mad_ctx* ctx, cudaStream_t st);
 mad_status wedge_sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first,

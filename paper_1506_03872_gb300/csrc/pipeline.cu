@@ -100,7 +100,7 @@ mad_status mad_pipeline_plan(mad_ctx* ctx, const mad_matrix* A, const mad_matrix
   if (!ctx || !A || !B) return MAD_ERR_ARG;
   if (t == 0 || tprime < t || (uint64_t)tprime > kDevSelectCap) return MAD_ERR_ARG;
   if (A->fmt != MAD_DENSE_ROWMAJOR || B->fmt != MAD_DENSE_ROWMAJOR) return MAD_ERR_UNSUPPORTED;
-  if (ctx->flags & MAD_WEDGE) return MAD_ERR_UNSUPPORTED;
+  if (ctx->flags & (MAD_WEDGE | MAD_ALIAS)) return MAD_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   mad_status rs = plan_dense_tables(ctx, A, B, s, st);
   if (rs != MAD_OK) return rs;

@@ -774,6 +774,13 @@ SampleParams make_params(const mad_ctx* ctx) {
   p.integer = ctx->integer ? 1 : 0;
   p.flags = ctx->flags;
   p.sc = ctx->sc;
+  p.alias = (ctx->flags & MAD_ALIAS) && ctx->al[kAlT1] ? 1 : 0;
+  for (int f = 0; f < 4; ++f) {
+    p.al[f] = ctx->al[f];
+    p.al_seg[f] = ctx->al_seg[f];
+    p.al_row[f] = ctx->al_row[f];
+    p.al_nseg[f] = ctx->al_nseg[f];
+  }
   return p;
 }
 
@@ -880,7 +887,9 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
   if (s == 0) return MAD_OK;
   if (ctx->flags & MAD_WEDGE) return wedge_sample_impl(ctx, s, seed, first, st);
   const SampleParams p = make_params(ctx);
-  if (!ctx->dense) {
+  // 0/1 inputs, and alias draws (their row is not monotone in the uniform,
+  // so the row-order sort does not apply): diamonds in index order.
+  if (!ctx->dense || p.alias) {
     phase_event(ctx, 0, st);
     phase_event(ctx, 1, st);
     k_sample<<<grid_of(s, full_grid<k_sample>()), 256, 0, st>>>(p, seed, first, s);
