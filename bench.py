@@ -652,6 +652,47 @@ def run_ours(args):
         except Exception as ex:  # the comparator must not cost the main line
             comp = {"error": str(ex)[:200]}
 
+    # Alias-table draws (MAD_ALIAS, Sec. 4.1) on the same inputs and budget:
+    # the same law through another map from the uniforms, diamonds in index
+    # order.  Tables, sampling and the whole step, timed like the main line.
+    alias_leg = None
+    if rank == 0 and not w.csr and not args.no_alias:
+        try:
+            actx = mad.Context(w.flags | mad.MAD_ALIAS)
+            a_out_c, a_out_t = mad.new_pairs(tprime), mad.new_pairs(t)
+
+            def astep():
+                e = [ev() for _ in range(4)]
+                e[0].record(stream)
+                mad.mad_build_tables(actx.ctx, Am, Bm, s)
+                e[1].record(stream)
+                mad.mad_sample(actx.ctx, s, seed)
+                e[2].record(stream)
+                cand_a, nc_a = mad.mad_topk(actx.ctx, tprime, a_out_c)
+                res_a, nr_a = mad.mad_rescore(actx.ctx, cand_a, nc_a, t, a_out_t)
+                e[3].record(stream)
+                return e, res_a, nr_a
+            for _ in range(max(2, args.warmup)):
+                astep()
+            aev = []
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                e, res_a, nr_a = astep()
+                aev.append(e)
+            torch.cuda.synchronize()
+            at = np.array([[e[q].elapsed_time(e[q + 1]) for q in range(3)] for e in aev])
+            alias_leg = {"tables_ms": round(float(at[:, 0].mean()), 4),
+                         "sample_ms": round(float(at[:, 1].mean()), 4),
+                         "step_ms": round(float(at.sum(axis=1).mean()), 4),
+                         "diamonds_per_s_sampler": round(s / (float(at[:, 1].mean()) / 1e3), 1),
+                         "prefix_table_sample_ms": round(sample_ms, 4)}
+            if recall is not None:
+                ai, aj, _, ac = mad.decode_pairs(res_a, nr_a)
+                alias_leg["recall_at_s"] = recall_of(w, ai, aj, ac, truth, tau, counts)[0]
+            actx.close()
+        except Exception as ex:  # the alias leg must not cost the main line
+            alias_leg = {"error": str(ex)[:200]}
+
     # 0/1 inputs: the exact sparse comparator (degree-bounded row-block
     # product with a fused threshold) on the same inputs, timed the same way.
     if w.csr and not args.no_comparator:
@@ -729,6 +770,7 @@ def run_ours(args):
                     **({"pipelined": e2e_note} if e2e_note else {})},
             "gpu_launches": int(launches),
             "comparator": comp,
+            "alias": alias_leg,
             "time_to_top_t": {"recall_target": 0.95,
                               "sampling_ms_at_s": round(ms_per_step, 4), "sampling_recall_at_s": recall,
                               "ladder": ladder,
@@ -1177,6 +1219,7 @@ def main():
     ap.add_argument("--no-probes", action="store_true", help="skip the gather/atomic probes")
     ap.add_argument("--retune", action="store_true",
                     help="batched queries: search the launch shape again (ignore the cache)")
+    ap.add_argument("--no-alias", action="store_true", help="skip the alias-table leg")
     ap.add_argument("--no-sparse", action="store_true",
                     help="skip the sparse common-neighbours leg of the default run")
     ap.add_argument("--rescore", type=int, default=0,
