@@ -152,6 +152,12 @@ mad_status clear_hash(mad_ctx* ctx, cudaStream_t st) {
 
 namespace mad {
 
+mad_status read_device_scalars(mad_ctx* ctx, DevScalars* hs, cudaStream_t st) {
+  return read_scalars(ctx, hs, st);
+}
+
+mad_status clear_x(mad_ctx* ctx, cudaStream_t st) { return clear_x_slots(ctx, st); }
+
 mad_status device_error_status(uint32_t err) {
   if (err & DERR_HASH_FULL) return MAD_ERR_HASH_FULL;
   if (err & DERR_OVERFLOW) return MAD_ERR_OVERFLOW;
@@ -473,6 +479,7 @@ mad_status mad_build_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
   cudaMemcpyAsync(&gtotal, ctx->T2g_ptr + ctx->m, sizeof(gtotal), cudaMemcpyDeviceToHost, st);
   if ((rs = cuda_status(cudaStreamSynchronize(st))) != MAD_OK) return rs;
   if ((rs = alloc(ctx, ctx->T2g, (size_t)gtotal, st)) != MAD_OK) return rs;
+  ctx->t2g_total = gtotal;
   if (gtotal && (rs = t2_guide_fill(ctx, st)) != MAD_OK) return rs;
   // Closure filter: 16 bits per entry, a power of two of 64-bit words.
   const uint64_t nnz_c = (ctx->flags & MAD_GRAM) ? ctx->nnz_a : ctx->nnz_b;

@@ -180,6 +180,7 @@ struct mad_ctx {
   int bloom_lg = 0;
   uint32_t* T1g = nullptr;                // guide of T1
   int t1g_sh = 0;
+  unsigned long long t2g_total = 0;       // entries of the 0/1 T2 guides
   uint32_t* TBg = nullptr;                // guides of the TB rows (fixed row stride)
   int64_t tbg_stride = 0;
   uint8_t* TBg_sh = nullptr;
@@ -422,6 +423,10 @@ mad_status dense_comparator(mad_ctx* ctx, const mad_matrix* A, const mad_matrix*
 // api.cu
 // Status of the device error word (DERR_* bits).
 mad_status device_error_status(uint32_t err);
+// Host copy of the device scalars (synchronises; sets ctx->device_error).
+mad_status read_device_scalars(mad_ctx* ctx, DevScalars* hs, cudaStream_t st);
+// Every slot of X empty, up to the hash's extent (asynchronous).
+mad_status clear_x(mad_ctx* ctx, cudaStream_t st);
 // Input checks and allocation of the tables of a dense build (frees the
 // previous ones).
 mad_status plan_dense_tables(mad_ctx* ctx, const mad_matrix* A, const mad_matrix* B,

@@ -1,6 +1,11 @@
-// The fused pass of Alg. 2 and Alg. 3 over dense inputs: tables, sampling,
-// Omega_t' from X, exact rescoring and Omega_t, enqueued by the host without
-// waiting for the device.  Every size is fixed when the pass is planned (by
+// The fused pass of Alg. 2 and Alg. 3: tables, sampling, Omega_t' from X,
+// exact rescoring and Omega_t, enqueued by the host without waiting for the
+// device.  Dense inputs, and 0/1 CSR inputs: for these the plan runs the
+// step-wise table build once, which fixes the sizes that follow from the
+// graph (the T2 guides, the closure filter) and the hash capacity (from its
+// pilot); a run then rebuilds every table of the same graph on the device
+// and samples with the run's seed (the graph must not change between plan
+// and run).  Every size is fixed when the pass is planned (by
 // m, d, n, s, t' and t); every quantity that depends on the data (T1's
 // total, the increment exponent F, the extent of the hash, the list
 // lengths of the selections) is read by the kernels from device memory.  A
@@ -64,6 +69,28 @@ PipeBufs carve(void* base, uint64_t tprime, uint64_t t) {
   return b;
 }
 
+// The 0/1 tables, guides, closure filter and an empty X, on the device.
+mad_status enqueue_csr_build(mad_ctx* ctx, cudaStream_t st) {
+  cudaMemsetAsync(ctx->sc, 0, sizeof(DevScalars), st);
+  mad_status rs;
+  if ((rs = build_tables_impl(ctx, st)) != MAD_OK) return rs;
+  if ((rs = t2_guide_offsets(ctx, st)) != MAD_OK) return rs;
+  if (ctx->t2g_total && (rs = t2_guide_fill(ctx, st)) != MAD_OK) return rs;
+  if ((rs = build_bloom(ctx, st)) != MAD_OK) return rs;
+  if ((rs = t1_guide_fill(ctx, st)) != MAD_OK) return rs;
+  return clear_x(ctx, st);
+}
+
+// Scratch of a 0/1 run: T1's chunk totals, then the T2 guide sizes and
+// their scan.
+size_t csr_build_scratch_bytes(const mad_ctx* ctx) {
+  const uint64_t m = (uint64_t)ctx->m;
+  const size_t chunks = (size_t)((m + 2047) / 2048) * sizeof(unsigned long long);
+  const size_t guides = ((m * sizeof(unsigned long long) + 255) & ~(size_t)255) +
+                        scan_partial_elems(m) * 8;
+  return chunks > guides ? chunks : guides;
+}
+
 mad_status enqueue_pass(mad_ctx* ctx, uint64_t seed, mad_pair* out_dev, uint32_t* counts_dev,
                         mad_pair* cand_dev, cudaStream_t st) {
   const PipeBufs b = carve(ctx->pipe_buf, ctx->pipe_tprime, ctx->pipe_t);
@@ -71,8 +98,12 @@ mad_status enqueue_pass(mad_ctx* ctx, uint64_t seed, mad_pair* out_dev, uint32_t
   mad_status rs;
   // Alg. 2: tables, an empty X, s diamonds.  Where the sampler builds the
   // home regions whole, nothing needs clearing first.
-  const bool fresh = x_builder_applies(ctx, ctx->pipe_s);
-  if ((rs = enqueue_dense_build(ctx, st, !fresh)) != MAD_OK) return rs;
+  const bool fresh = ctx->dense && x_builder_applies(ctx, ctx->pipe_s);
+  if (!ctx->dense) {
+    if ((rs = enqueue_csr_build(ctx, st)) != MAD_OK) return rs;
+  } else if ((rs = enqueue_dense_build(ctx, st, !fresh)) != MAD_OK) {
+    return rs;
+  }
   ctx->sampled = 0;
   if ((rs = sample_impl(ctx, ctx->pipe_s, seed, 0, st, true)) != MAD_OK) return rs;
   ctx->sampled = ctx->pipe_s;
@@ -99,15 +130,19 @@ mad_status mad_pipeline_plan(mad_ctx* ctx, const mad_matrix* A, const mad_matrix
                              uint32_t tprime, uint32_t t, mad_stream stream) {
   if (!ctx || !A || !B) return MAD_ERR_ARG;
   if (t == 0 || tprime < t || (uint64_t)tprime > kDevSelectCap) return MAD_ERR_ARG;
-  if (A->fmt != MAD_DENSE_ROWMAJOR || B->fmt != MAD_DENSE_ROWMAJOR) return MAD_ERR_UNSUPPORTED;
+  const bool csr = A->fmt == MAD_CSR && B->fmt == MAD_CSR;
+  if (!csr && (A->fmt != MAD_DENSE_ROWMAJOR || B->fmt != MAD_DENSE_ROWMAJOR))
+    return MAD_ERR_UNSUPPORTED;
   if (ctx->flags & (MAD_WEDGE | MAD_ALIAS)) return MAD_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
-  mad_status rs = plan_dense_tables(ctx, A, B, s, st);
+  // 0/1 inputs: the step-wise build, once, sizes the guides, the filter
+  // and the hash (its pilot); dense inputs: the sizes from the shapes.
+  mad_status rs = csr ? mad_build_tables(ctx, A, B, s, stream) : plan_dense_tables(ctx, A, B, s, st);
   if (rs != MAD_OK) return rs;
   const PipeBufs sizes = carve(nullptr, tprime, t);
   if ((rs = pool_malloc(ctx, &ctx->pipe_buf, sizes.bytes, st)) != MAD_OK) return rs;
   // The scratch every launch of a run needs, owned by the pass.
-  size_t scratch = dense_build_scratch_bytes(ctx);
+  size_t scratch = csr ? csr_build_scratch_bytes(ctx) : dense_build_scratch_bytes(ctx);
   if (sample_scratch_bytes(ctx, s) > scratch) scratch = sample_scratch_bytes(ctx, s);
   if ((rs = pool_malloc(ctx, &ctx->pipe_scratch, scratch, st)) != MAD_OK) return rs;
   ctx->pipe_scratch_bytes = scratch;
@@ -141,6 +176,15 @@ mad_status mad_pipeline_status(mad_ctx* ctx, mad_stream stream) {
   if (!ctx) return MAD_ERR_ARG;
   if (!ctx->pipe) return MAD_ERR_STATE;
   cudaStream_t st = (cudaStream_t)stream;
+  if (!ctx->dense) {
+    DevScalars hs;
+    const mad_status rs = read_device_scalars(ctx, &hs, st);
+    if (rs != MAD_OK) return rs;
+    if (hs.err & DERR_OVERFLOW) return MAD_ERR_OVERFLOW;
+    if (hs.t1_total == 0) return MAD_ERR_EMPTY;
+    ctx->t1_total = hs.t1_total;
+    return device_error_status(ctx->device_error);
+  }
   const mad_status rs = finish_dense_build(ctx, st);
   if (rs != MAD_OK) return rs;
   return device_error_status(ctx->device_error);

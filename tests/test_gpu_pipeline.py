@@ -198,10 +198,17 @@ def test_short_lists_and_limits():
         ref = _oracle_pass(A, B, 0, s, seed, tprime, t)
         assert len(ref[0]) < tprime
         _check(mad, out, counts, cand, ref)
+    # Mixed formats and wedge contexts are refused (0/1 CSR on both sides is
+    # planned: see the CSR tests below).
     rp = torch.tensor([0, 1, 2], dtype=torch.int64, device="cuda")
     ci = torch.tensor([1, 0], dtype=torch.int32, device="cuda")
     M = mad.csr(rp, ci, (2, 2))
+    Dm = torch.ones(2, 2, device="cuda")
     with mad.Context(2) as c:
+        with pytest.raises(mad.MadError) as e:
+            mad.mad_pipeline_plan(c.ctx, M, mad.dense(Dm), 100, 10, 5)
+        assert e.value.status == mad.MAD_ERR_UNSUPPORTED
+    with mad.Context(2 | 16) as c:
         with pytest.raises(mad.MadError) as e:
             mad.mad_pipeline_plan(c.ctx, M, M, 100, 10, 5)
         assert e.value.status == mad.MAD_ERR_UNSUPPORTED
@@ -328,3 +335,73 @@ def test_pass_overflow_full_is_reported():
         with pytest.raises(mad.MadError) as e:
             mad.mad_pipeline_status(c.ctx)
         assert e.value.status == mad.MAD_ERR_HASH_FULL
+
+
+# ---------------------------------------------------------------------------
+# 0/1 CSR inputs: the fused pass planned once (the step-wise build sizes the
+# guides, the closure filter and the hash), run eagerly and from a graph.
+# ---------------------------------------------------------------------------
+def _csr_case(name):
+    """(rowptr_a, col_a, shape_a, rowptr_b, col_b, shape_b, flags, oracle matrices)."""
+    if name in ("chung_lu", "chung_lu_square_sym"):
+        from paper_1506_03872_gb300.workloads import chung_lu
+        w = chung_lu(nodes=6000, edges=60_000, seed=14)
+        M = oracle.Matrix(rowptr=w.rowptr, colidx=w.colidx, shape=(w.m, w.m))
+        flags = w.flags | (8 if name == "chung_lu_square_sym" else 0)
+        return (w.rowptr, w.colidx, (w.m, w.m), w.rowptr, w.colidx, (w.m, w.m), flags, M, M)
+    rng = _rng(15)
+    A = rng.random((900, 300)) < np.linspace(0.002, 0.08, 300)[None, :]
+    B = rng.random((300, 1100)) < 0.03
+    A[:, 0] = B[0, :] = True
+
+    def csr(D):
+        rp = np.concatenate([[0], np.cumsum(D.sum(1))]).astype(np.int64)
+        return rp, np.nonzero(D)[1].astype(np.int32)
+    ra, ca = csr(A)
+    rb, cb = csr(B)
+    MA = oracle.Matrix(rowptr=ra, colidx=ca, shape=A.shape)
+    MB = oracle.Matrix(rowptr=rb, colidx=cb, shape=B.shape)
+    return (ra, ca, A.shape, rb, cb, B.shape, 0, MA, MB)
+
+
+@pytest.mark.parametrize("name", ["chung_lu", "bipartite", "chung_lu_square_sym"])
+def test_csr_pass_matches_oracle_eager_and_from_a_graph(name):
+    import paper_1506_03872_gb300 as mad
+    ra, ca, sa, rb, cb, sb, flags, MA, MB = _csr_case(name)
+    s, seed, tprime, t = 400_000, 7, 2000, 50
+    keep = [torch.from_numpy(x).cuda() for x in (ra, ca, rb, cb)]
+    Am = mad.csr(keep[0], keep[1], sa)
+    Bm = mad.csr(keep[2], keep[3], sb)
+    o = oracle.Oracle(MA, MB, flags, s)
+    assert o.sample(s, seed) == 0
+    keys, x = o.topk(tprime)
+    tk, tc = oracle.topt(keys, o.rescore(keys), t)
+    ref = (keys, x, tk, tc)
+    with mad.Context(flags) as c:
+        mad.mad_pipeline_plan(c.ctx, Am, Bm, s, tprime, t)
+        out, cand = mad.new_pairs(t), mad.new_pairs(tprime)
+        counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):   # eager on the capture stream
+            mad.mad_pipeline_run(c.ctx, seed, out, counts, cand)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        mad.mad_pipeline_status(c.ctx)
+        _check(mad, out, counts, cand, ref)
+        # The same pass captured once and replayed (with another seed first,
+        # so nothing of the eager run survives into the replay's result).
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            mad.mad_pipeline_run(c.ctx, seed, out, counts, cand)
+        out.zero_()
+        cand.zero_()
+        counts.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        mad.mad_pipeline_status(c.ctx)
+        _check(mad, out, counts, cand, ref)
+        # Step-wise X after the pass: the pass's X is the step-wise one.
+        st = mad.mad_stats(c.ctx)
+        sc = o.scalars()
+        assert st["inserted"] == sc["inserted"] and st["diag_skipped"] == sc["diag_skipped"]
