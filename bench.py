@@ -841,6 +841,46 @@ def chung_lu_leg(args, dev, stream, flush, peak, peak_kind):
            "count_mismatches": mismatch, "tau_t": tau,
            "est_samples_top1": round(st["w1"] / counts.top1 ** 2, 1) if counts.top1 else None,
            "stats": {k: st[k] for k in ("w1", "inserted", "distinct", "hash_capacity")}}
+    # The same step as the fused pass (mad_pipeline_*), planned once and
+    # replayed from a CUDA graph: no host round trip inside a step.
+    try:
+        pctx = mad.Context(w.flags)
+        mad.mad_pipeline_plan(pctx.ctx, A, A, w.s, w.tprime, w.t)
+        p_out, p_cand = mad.new_pairs(w.t), mad.new_pairs(w.tprime)
+        p_cnt = torch.zeros(2, dtype=torch.int32, device=dev)
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            mad.mad_pipeline_run(pctx.ctx, w.sampler_seed, p_out, p_cnt, p_cand)
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        mad.mad_pipeline_status(pctx.ctx)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            mad.mad_pipeline_run(pctx.ctx, w.sampler_seed, p_out, p_cnt, p_cand)
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+        gspans = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            g0, g1 = ev(), ev()
+            g0.record(stream)
+            graph.replay()
+            g1.record(stream)
+            gspans.append((g0, g1))
+        torch.cuda.synchronize()
+        mad.mad_pipeline_status(pctx.ctx)
+        nr_p = int(p_cnt[1].item())
+        pass_ms = float(np.mean([a.elapsed_time(b) for a, b in gspans]))
+        leg["pass"] = {"graph": True, "ms_per_step": round(pass_ms, 4),
+                       "diamonds_per_s": round(w.s / (pass_ms / 1e3), 1),
+                       "matches_stepwise": bool(nr_p == nr and
+                                                torch.equal(p_out[:nr_p].cpu(), res[:nr].cpu()))}
+        del graph
+        pctx.close()
+    except Exception as ex:  # the fused pass must not cost the leg
+        leg["pass"] = {"error": str(ex)[:200]}
     cap = int(0.6 * torch.cuda.mem_get_info(dev)[0])
     leg["ladder"] = _ladder(step, w, set(), tau, counts, flush, cap, args.ladder_seeds, stream,
                             recall)

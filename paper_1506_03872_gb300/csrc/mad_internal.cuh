@@ -204,6 +204,7 @@ struct mad_ctx {
   bool pipe = false;
   uint64_t pipe_s = 0;
   uint32_t pipe_tprime = 0, pipe_t = 0;
+  uint64_t pipe_list_cap = 0;             // compacted candidates the pass holds
   void* pipe_buf = nullptr;
   // The pass's own scratch (a captured run keeps its addresses however the
   // context's shared scratch changes later).
@@ -384,6 +385,17 @@ size_t dev_select_state_bytes();
 void select_hash_dev(mad_ctx* ctx, uint64_t K, const unsigned long long* hcap_dev, void* state,
                      unsigned long long* count, Item* list, Item* sorted, uint32_t* pos,
                      Item* out, cudaStream_t st);
+// The same Omega_t' for candidate lists longer than kDevSelectCap (0/1
+// inputs, whose small integer x tie in large numbers at the K-th value):
+// the x at or above the exact log-bucket threshold are compacted into list
+// (list_cap entries; more is reported as DERR_SELECT), the K first by
+// (x desc, key asc) are found by an MSB radix select on the device length
+// (ping-pong lists l1, l2 of list_cap entries) and collected into topk,
+// then sorted into out (K <= kDevSelectCap).  count[0..3] are device words.
+void select_hash_dev_long(mad_ctx* ctx, uint64_t K, const unsigned long long* hcap_dev,
+                          void* state, unsigned long long* count, Item* list, Item* l1, Item* l2,
+                          uint64_t list_cap, Item* topk, Item* sorted, uint32_t* pos, Item* out,
+                          cudaStream_t st);
 // out[q] for q < min(cap, *n_dev) as in items_to_pairs; *n_out gets that
 // length.
 void items_to_pairs_dev(mad_ctx* ctx, const Item* items, uint64_t cap,

@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "mad_internal.cuh"
 
 using namespace mad;
@@ -29,7 +31,10 @@ namespace {
 struct PipeBufs {
   void* state;                  // selection state of Omega_t'
   unsigned long long* count;    // compacted candidates (device length)
-  Item* list;                   // compacted items, kDevSelectCap
+  Item* list;                   // compacted items, list_cap
+  Item* l1;                     // ping-pong lists of the long selection (0/1
+  Item* l2;                     //   inputs), list_cap each
+  Item* topk;                   // the K selected, unsorted (0/1 inputs), t'
   Item* sorted;                 // tile-sorted copy, kDevSelectCap
   uint32_t* pos;                // their input positions, kDevSelectCap
   Item* top;                    // Omega_t', t'
@@ -44,7 +49,8 @@ struct PipeBufs {
 
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-PipeBufs carve(void* base, uint64_t tprime, uint64_t t) {
+// long_sel: the 0/1 pass's radix selection over list_cap candidates.
+PipeBufs carve(void* base, uint64_t tprime, uint64_t t, uint64_t list_cap, bool long_sel) {
   PipeBufs b;
   char* p = (char*)base;
   size_t off = 0;
@@ -55,7 +61,10 @@ PipeBufs carve(void* base, uint64_t tprime, uint64_t t) {
   };
   b.state = take(dev_select_state_bytes());
   b.count = (unsigned long long*)take(4 * sizeof(unsigned long long));
-  b.list = (Item*)take(kDevSelectCap * sizeof(Item));
+  b.list = (Item*)take(list_cap * sizeof(Item));
+  b.l1 = (Item*)take(long_sel ? list_cap * sizeof(Item) : 0);
+  b.l2 = (Item*)take(long_sel ? list_cap * sizeof(Item) : 0);
+  b.topk = (Item*)take(long_sel ? tprime * sizeof(Item) : 0);
   b.sorted = (Item*)take(kDevSelectCap * sizeof(Item));
   b.pos = (uint32_t*)take(kDevSelectCap * sizeof(uint32_t));
   b.top = (Item*)take(tprime * sizeof(Item));
@@ -93,7 +102,9 @@ size_t csr_build_scratch_bytes(const mad_ctx* ctx) {
 
 mad_status enqueue_pass(mad_ctx* ctx, uint64_t seed, mad_pair* out_dev, uint32_t* counts_dev,
                         mad_pair* cand_dev, cudaStream_t st) {
-  const PipeBufs b = carve(ctx->pipe_buf, ctx->pipe_tprime, ctx->pipe_t);
+  const bool long_sel = !ctx->dense;
+  const PipeBufs b =
+      carve(ctx->pipe_buf, ctx->pipe_tprime, ctx->pipe_t, ctx->pipe_list_cap, long_sel);
   mad_pair* cand = cand_dev ? cand_dev : b.cand;
   mad_status rs;
   // Alg. 2: tables, an empty X, s diamonds.  Where the sampler builds the
@@ -109,7 +120,11 @@ mad_status enqueue_pass(mad_ctx* ctx, uint64_t seed, mad_pair* out_dev, uint32_t
   ctx->sampled = ctx->pipe_s;
   ctx->built = true;
   // Alg. 3: Omega_t' (its length min(t', compacted) on the device) ...
-  select_hash_dev(ctx, ctx->pipe_tprime, hash_extent(ctx), b.state, b.count, b.list, b.sorted,
+  if (long_sel)
+    select_hash_dev_long(ctx, ctx->pipe_tprime, hash_extent(ctx), b.state, b.count, b.list, b.l1,
+                         b.l2, ctx->pipe_list_cap, b.topk, b.sorted, b.pos, b.top, st);
+  else
+    select_hash_dev(ctx, ctx->pipe_tprime, hash_extent(ctx), b.state, b.count, b.list, b.sorted,
                   b.pos, b.top, st);
   items_to_pairs_dev(ctx, b.top, ctx->pipe_tprime, b.count, nullptr, nullptr, cand, counts_dev, st);
   // ... the exact c of each candidate, and Omega_t.
@@ -139,7 +154,9 @@ mad_status mad_pipeline_plan(mad_ctx* ctx, const mad_matrix* A, const mad_matrix
   // and the hash (its pilot); dense inputs: the sizes from the shapes.
   mad_status rs = csr ? mad_build_tables(ctx, A, B, s, stream) : plan_dense_tables(ctx, A, B, s, st);
   if (rs != MAD_OK) return rs;
-  const PipeBufs sizes = carve(nullptr, tprime, t);
+  // Candidate lists: 0/1 inputs tie in large numbers at the t'-th x.
+  ctx->pipe_list_cap = csr ? std::max<uint64_t>(kDevSelectCap, 8ull * tprime) : kDevSelectCap;
+  const PipeBufs sizes = carve(nullptr, tprime, t, ctx->pipe_list_cap, csr);
   if ((rs = pool_malloc(ctx, &ctx->pipe_buf, sizes.bytes, st)) != MAD_OK) return rs;
   // The scratch every launch of a run needs, owned by the pass.
   size_t scratch = csr ? csr_build_scratch_bytes(ctx) : dense_build_scratch_bytes(ctx);

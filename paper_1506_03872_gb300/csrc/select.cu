@@ -906,6 +906,70 @@ void select_hash_dev(mad_ctx* ctx, uint64_t K, const unsigned long long* hcap_de
                    (unsigned int*)(count + 2), &ctx->sc->err, st);
 }
 
+// Device-length start of the radix selection: the list holds min(*count,
+// cap) items (more than cap: the compaction overflowed, reported); with no
+// more than K of them every one is taken (the threshold stays 0).
+__global__ void k_radix_init_dev(SelState* st, const unsigned long long* count, uint64_t cap,
+                                 unsigned long long K, unsigned int* err) {
+  if (threadIdx.x != 0) return;
+  const unsigned long long n = *count;
+  if (n > cap) atomicOr(err, DERR_SELECT);
+  st->n_cur = n < cap ? n : cap;
+  st->k_rem = K;
+  st->cur = 0;
+  st->done = st->n_cur <= K ? 1 : 0;
+}
+
+// k_collect over a list of device length min(*count, cap).
+__global__ void __launch_bounds__(256)
+k_collect_dev(const Item* __restrict__ l0, const unsigned long long* count, uint64_t cap,
+              const SelState* st, Item* __restrict__ out, unsigned long long* counter,
+              uint64_t out_cap) {
+  const unsigned long long n0 = *count, n = n0 < cap ? n0 : cap;
+  const unsigned long long tp = st->tp, tk = st->tk;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long rounds = (n + stride - 1) / stride;
+  for (unsigned long long r = 0; r < rounds; ++r) {
+    const unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x + r * stride;
+    bool want = false;
+    Item it;
+    if (x < n) {
+      it = l0[x];
+      want = it.p > tp || (it.p == tp && (~it.key) >= tk);
+    }
+    append(out, counter, want, it, out_cap);
+  }
+}
+
+void select_hash_dev_long(mad_ctx* ctx, uint64_t K, const unsigned long long* hcap_dev,
+                          void* state, unsigned long long* count, Item* list, Item* l1, Item* l2,
+                          uint64_t list_cap, Item* topk, Item* sorted, uint32_t* pos, Item* out,
+                          cudaStream_t st) {
+  SelState* dst = (SelState*)state;
+  cudaMemsetAsync(dst, 0, sizeof(SelState), st);
+  cudaMemsetAsync(count, 0, 4 * sizeof(unsigned long long), st);
+  const uint64_t bound = hash_slot_bound(ctx);
+  const unsigned blocks = grid_for(bound, 152 * 8);
+  // Exact log-bucket threshold, then every x at or above it.
+  k_log_hist<<<blocks, 256, 0, st>>>(ctx->hvals, bound, K, dst, hcap_dev, 0);
+  k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, bound, dst, list, list_cap, count,
+                                       hcap_dev);
+  // The K first by (x desc, key asc): MSB radix select over the 8 bytes of
+  // x and the 8 of the key, on the device length.
+  k_radix_init_dev<<<1, 32, 0, st>>>(dst, count, list_cap, K, &ctx->sc->err);
+  const unsigned rb = grid_for(list_cap, 152 * 4);
+  constexpr int kDigits = 16;
+  for (int q = 0; q < kDigits; ++q) {
+    k_radix_hist<<<rb, 256, 0, st>>>(list, l1, l2, dst, q, 8, kDigits - 1);
+    k_radix_filter<<<rb, 256, 0, st>>>(list, l1, l2, dst, q, 8, list_cap);
+  }
+  k_collect_dev<<<grid_for(list_cap, 152 * 8), 256, 0, st>>>(list, count, list_cap, dst, topk,
+                                                             count + 1, K);
+  count_launch(ctx, 4 + 2 * kDigits);
+  // Sorted: the K items at count[1] through the tile sort.
+  tile_select_dev(ctx, topk, K, K, count + 1, &ctx->sc->err, sorted, pos, out, st);
+}
+
 void items_to_pairs_dev(mad_ctx* ctx, const Item* items, uint64_t cap,
                         const unsigned long long* n_dev, const mad_pair* cand,
                         const double* cvals, mad_pair* out, uint32_t* n_out, cudaStream_t st) {

@@ -343,9 +343,10 @@ def test_pass_overflow_full_is_reported():
 # ---------------------------------------------------------------------------
 def _csr_case(name):
     """(rowptr_a, col_a, shape_a, rowptr_b, col_b, shape_b, flags, oracle matrices)."""
-    if name in ("chung_lu", "chung_lu_square_sym"):
+    if name in ("chung_lu", "chung_lu_square_sym", "chung_lu_ties"):
         from paper_1506_03872_gb300.workloads import chung_lu
-        w = chung_lu(nodes=6000, edges=60_000, seed=14)
+        w = (chung_lu(nodes=20_000, edges=200_000, seed=16) if name == "chung_lu_ties"
+             else chung_lu(nodes=6000, edges=60_000, seed=14))
         M = oracle.Matrix(rowptr=w.rowptr, colidx=w.colidx, shape=(w.m, w.m))
         flags = w.flags | (8 if name == "chung_lu_square_sym" else 0)
         return (w.rowptr, w.colidx, (w.m, w.m), w.rowptr, w.colidx, (w.m, w.m), flags, M, M)
@@ -364,11 +365,16 @@ def _csr_case(name):
     return (ra, ca, A.shape, rb, cb, B.shape, 0, MA, MB)
 
 
-@pytest.mark.parametrize("name", ["chung_lu", "bipartite", "chung_lu_square_sym"])
+@pytest.mark.parametrize("name", ["chung_lu", "bipartite", "chung_lu_square_sym", "chung_lu_ties"])
 def test_csr_pass_matches_oracle_eager_and_from_a_graph(name):
+    """Omega_t' of a 0/1 pass comes from a radix selection over every key at
+    or above the t'-th count (counts tie in large numbers there); the last
+    case has t' = 20000 with more candidates than the dense pass's list."""
     import paper_1506_03872_gb300 as mad
     ra, ca, sa, rb, cb, sb, flags, MA, MB = _csr_case(name)
     s, seed, tprime, t = 400_000, 7, 2000, 50
+    if name == "chung_lu_ties":
+        s, tprime, t = 3_000_000, 20_000, 100
     keep = [torch.from_numpy(x).cuda() for x in (ra, ca, rb, cb)]
     Am = mad.csr(keep[0], keep[1], sa)
     Bm = mad.csr(keep[2], keep[3], sb)
