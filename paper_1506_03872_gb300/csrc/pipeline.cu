@@ -154,8 +154,10 @@ mad_status mad_pipeline_plan(mad_ctx* ctx, const mad_matrix* A, const mad_matrix
   // and the hash (its pilot); dense inputs: the sizes from the shapes.
   mad_status rs = csr ? mad_build_tables(ctx, A, B, s, stream) : plan_dense_tables(ctx, A, B, s, st);
   if (rs != MAD_OK) return rs;
-  // Candidate lists: 0/1 inputs tie in large numbers at the t'-th x.
-  ctx->pipe_list_cap = csr ? std::max<uint64_t>(kDevSelectCap, 8ull * tprime) : kDevSelectCap;
+  // Candidate lists: the 0/1 counts tie in large numbers at the t'-th x (on
+  // the Chung-Lu graph of 1e6 nodes nearly every key of X has x = 1), so the
+  // 0/1 list holds every slot of the hash: it cannot overflow.
+  ctx->pipe_list_cap = csr ? std::max<uint64_t>(kDevSelectCap, ctx->hcap_alloc) : kDevSelectCap;
   const PipeBufs sizes = carve(nullptr, tprime, t, ctx->pipe_list_cap, csr);
   if ((rs = pool_malloc(ctx, &ctx->pipe_buf, sizes.bytes, st)) != MAD_OK) return rs;
   // The scratch every launch of a run needs, owned by the pass.
