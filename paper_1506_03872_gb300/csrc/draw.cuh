@@ -187,11 +187,20 @@ __device__ __forceinline__ Draw draw_alias(const SampleParams& p, unsigned long 
   return dr;
 }
 
-__device__ __forceinline__ Draw draw_one(const SampleParams& p, unsigned long long seed,
-                                         unsigned long long ell, bool* bad) {
-  if (p.alias) return draw_alias(p, seed, ell);
+// kAlias selects the alias-table draws at compile time, so that the
+// prefix-table kernels carry none of their code; draw_one picks at run time
+// (diagnostic kernels only).
+template <bool kAlias>
+__device__ __forceinline__ Draw draw_one_as(const SampleParams& p, unsigned long long seed,
+                                            unsigned long long ell, bool* bad) {
+  if (kAlias) return draw_alias(p, seed, ell);
   const Uniforms u = diamond_uniforms(seed, ell);
   return draw_given_row(p, u, draw_row_i(p, u.u0, bad), bad);
+}
+
+__device__ __forceinline__ Draw draw_one(const SampleParams& p, unsigned long long seed,
+                                         unsigned long long ell, bool* bad) {
+  return p.alias ? draw_one_as<true>(p, seed, ell, bad) : draw_one_as<false>(p, seed, ell, bad);
 }
 
 }  // namespace mad

@@ -130,7 +130,8 @@ __device__ __forceinline__ void flush_tally(const SampleParams& p, Tally& t) {
   }
 }
 
-// Diamonds in index order (0/1 CSR inputs).
+// Diamonds in index order (0/1 CSR inputs; dense inputs with alias draws).
+template <bool kAlias>
 __global__ void __launch_bounds__(256)
 k_sample(const SampleParams p_, unsigned long long seed, unsigned long long first,
          unsigned long long s) {
@@ -142,7 +143,7 @@ k_sample(const SampleParams p_, unsigned long long seed, unsigned long long firs
   for (unsigned long long base = warp_id * 32; base < s; base += warps * 32) {
     const unsigned long long q = base + lane;
     Draw dr{};
-    if (q < s) dr = draw_one(p, seed, first + q, &t.bad);
+    if (q < s) dr = draw_one_as<kAlias>(p, seed, first + q, &t.bad);
     accumulate(p, q < s, dr, t);
   }
   flush_tally(p, t);
@@ -713,7 +714,7 @@ k_pilot(const SampleParams p_, unsigned long long seed, unsigned long long n,
   unsigned long long c = 0;
   for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (unsigned long long)gridDim.x * blockDim.x) {
-    const Draw dr = draw_one(p, seed, q, &bad);
+    const Draw dr = draw_one_as<false>(p, seed, q, &bad);
     c += (dr.v != 0 && !((p.flags & MAD_EXCLUDE_DIAG) && dr.i == dr.j)) ? 1 : 0;
     if (p.flags & MAD_SQUARE_SYM)
       c += (dr.v != 0 && !((p.flags & MAD_EXCLUDE_DIAG) && dr.k == dr.kp)) ? 1 : 0;
@@ -892,7 +893,10 @@ mad_status sample_impl(mad_ctx* ctx, uint64_t s, uint64_t seed, uint64_t first, 
   if (!ctx->dense || p.alias) {
     phase_event(ctx, 0, st);
     phase_event(ctx, 1, st);
-    k_sample<<<grid_of(s, full_grid<k_sample>()), 256, 0, st>>>(p, seed, first, s);
+    if (p.alias)
+      k_sample<true><<<grid_of(s, full_grid<k_sample<true>>()), 256, 0, st>>>(p, seed, first, s);
+    else
+      k_sample<false><<<grid_of(s, full_grid<k_sample<false>>()), 256, 0, st>>>(p, seed, first, s);
     count_launch(ctx);
     phase_event(ctx, 2, st);
     phase_event(ctx, 3, st);
