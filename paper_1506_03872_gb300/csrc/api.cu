@@ -93,6 +93,8 @@ void free_tables(mad_ctx* ctx, cudaStream_t st) {
   }
   ctx->TK_shift = 0;
   ctx->tk_total = 0;
+  free_async(ctx->rg_buf, st);
+  ctx->rg_cap = 0;
   free_async(ctx->pipe_buf, st);
   free_async(ctx->pipe_scratch, st);
   ctx->pipe_scratch_bytes = 0;
@@ -569,6 +571,7 @@ mad_status mad_rescore(mad_ctx* ctx, const mad_pair* cand_dev, uint32_t ncand, u
   const size_t cv_off = (ws_bytes + 255) & ~(size_t)255;
   mad_status rs = ensure_scratch(ctx, cv_off + (size_t)ncand * sizeof(double), st);
   if (rs != MAD_OK) return rs;
+  if ((rs = rescore_reserve(ctx, ncand, st)) != MAD_OK) return rs;
   const SelectWs ws = select_ws_carve(ctx->scratch, ncand, t);
   double* cvals = (double*)((char*)ctx->scratch + cv_off);
   if ((rs = rescore_items(ctx, cand_dev, ncand, ws.l0, cvals, st)) != MAD_OK) return rs;

@@ -245,6 +245,9 @@ struct mad_ctx {
   // Scratch (select, scans); grown on demand.
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  // Grouping buffer of the 0/1 Gram rescoring, for up to rg_cap candidates.
+  void* rg_buf = nullptr;
+  uint64_t rg_cap = 0;
   // Host-side fault injection (MAD_FAULT=oom[:N]): the allocation number
   // from which pool allocations fail (0: off), and allocations so far.
   int64_t fault_oom_at = 0;
@@ -455,6 +458,7 @@ int sort_bits(int64_t m);
 // rescore.cu
 // Exact c for every candidate: items[q] = (bits |c|, key, q), cvals[q] = c.
 // With n_dev, the candidates are the first min(ncand, *n_dev).
+mad_status rescore_reserve(mad_ctx* ctx, uint64_t ncand, cudaStream_t st);
 mad_status rescore_items(mad_ctx* ctx, const mad_pair* cand, uint64_t ncand, Item* items,
                          double* cvals, cudaStream_t st, const unsigned long long* n_dev = nullptr);
 

@@ -165,6 +165,8 @@ mad_status mad_pipeline_plan(mad_ctx* ctx, const mad_matrix* A, const mad_matrix
   if (sample_scratch_bytes(ctx, s) > scratch) scratch = sample_scratch_bytes(ctx, s);
   if ((rs = pool_malloc(ctx, &ctx->pipe_scratch, scratch, st)) != MAD_OK) return rs;
   ctx->pipe_scratch_bytes = scratch;
+  // The rescoring's grouping buffer (0/1 Gram inputs) for t' candidates.
+  if ((rs = rescore_reserve(ctx, tprime, st)) != MAD_OK) return rs;
   ctx->pipe = true;
   ctx->pipe_s = s;
   ctx->pipe_tprime = tprime;
