@@ -55,20 +55,56 @@ __device__ __forceinline__ uint32_t digit_of(const Item& it, int q, int dp) {
   return (uint32_t)((~it.key) >> (8 * (7 - (q - dp)))) & 0xFFu;
 }
 
-// Warp-aggregated append of `it` when `want`.
-__device__ __forceinline__ void append(Item* out, unsigned long long* counter, bool want,
-                                       const Item& it, uint64_t cap) {
-  const unsigned mask = __ballot_sync(0xFFFFFFFFu, want);
-  if (!mask) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(mask) - 1;
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
-  base = __shfl_sync(0xFFFFFFFFu, base, leader);
-  if (want) {
-    const unsigned long long pos = base + __popc(mask & ((1u << lane) - 1u));
-    if (pos < cap) out[pos] = it;
+// Block-wide append of up to N items per thread: every thread of the block
+// calls it the same number of times.  One atomic on the counter per block
+// and call (a single counter shared by every warp of the grid serialises
+// when most warps hold an item, as 0/1 counts near the threshold do).
+template <int N>
+__device__ __forceinline__ void append_block(Item* out, unsigned long long* counter,
+                                             const bool (&want)[N], const Item (&it)[N],
+                                             uint64_t cap) {
+  __shared__ unsigned int s_cnt[32];
+  __shared__ unsigned long long s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned mask[N];
+  unsigned total = 0;
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    mask[q] = __ballot_sync(0xFFFFFFFFu, want[q]);
+    total += __popc(mask[q]);
   }
+  if (lane == 0) s_cnt[warp] = total;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    unsigned v = lane < nw ? s_cnt[lane] : 0u;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned u = __shfl_up_sync(0xFFFFFFFFu, v, off);
+      if (lane >= off) v += u;
+    }
+    if (lane < nw) s_cnt[lane] = v;   // inclusive, per warp
+    if (lane == 31) s_base = v ? atomicAdd(counter, (unsigned long long)v) : 0ull;
+  }
+  __syncthreads();
+  unsigned long long pos = s_base + (warp ? s_cnt[warp - 1] : 0u);
+  const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    if (want[q]) {
+      const unsigned long long p = pos + __popc(mask[q] & below);
+      if (p < cap) out[p] = it[q];
+    }
+    pos += __popc(mask[q]);
+  }
+  __syncthreads();   // s_cnt and s_base are reused by the next call
+}
+
+__device__ __forceinline__ void append_block1(Item* out, unsigned long long* counter, bool want,
+                                              const Item& it, uint64_t cap) {
+  const bool w[1] = {want};
+  const Item v[1] = {it};
+  append_block<1>(out, counter, w, v, cap);
 }
 
 __global__ void __launch_bounds__(256)
@@ -135,7 +171,7 @@ k_radix_filter(const Item* __restrict__ l0, Item* __restrict__ l1, Item* __restr
       it = list[x];
       want = digit_of(it, q, dp) == picked;
     }
-    append(out, &st->n_next, want, it, cap);
+    append_block1(out, &st->n_next, want, it, cap);
   }
   __threadfence();
   __shared__ unsigned int is_last;
@@ -163,7 +199,7 @@ k_collect(const Item* __restrict__ l0, unsigned long long n, const SelState* st,
       it = l0[x];
       want = it.p > tp || (it.p == tp && (~it.key) >= tk);
     }
-    append(out, counter, want, it, cap);
+    append_block1(out, counter, want, it, cap);
   }
 }
 
@@ -253,18 +289,19 @@ k_compact_ge(const unsigned long long* __restrict__ keys, const long long* __res
       const uint64_t slot = start + (r * U + q) * stride;
       v[q] = slot < cap ? __ldcs(vals + slot) : 0;
     }
+    bool want[U];
+    Item it[U];
 #pragma unroll
     for (int q = 0; q < U; ++q) {
       const uint64_t slot = start + (r * U + q) * stride;
-      const bool want = v[q] > 0 && (unsigned long long)v[q] >= theta;
-      Item it;
-      if (want) {
-        it.p = (unsigned long long)v[q];
-        it.key = keys[slot];
-        it.aux = slot;
+      want[q] = v[q] > 0 && (unsigned long long)v[q] >= theta;
+      if (want[q]) {
+        it[q].p = (unsigned long long)v[q];
+        it[q].key = keys[slot];
+        it[q].aux = slot;
       }
-      append(out, counter, want, it, out_cap);
     }
+    append_block<U>(out, counter, want, it, out_cap);
   }
 }
 
@@ -937,7 +974,7 @@ k_collect_dev(const Item* __restrict__ l0, const unsigned long long* count, uint
       it = l0[x];
       want = it.p > tp || (it.p == tp && (~it.key) >= tk);
     }
-    append(out, counter, want, it, out_cap);
+    append_block1(out, counter, want, it, out_cap);
   }
 }
 
