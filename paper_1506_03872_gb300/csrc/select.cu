@@ -337,6 +337,10 @@ k_select_check(SelState* st, unsigned long long* counter, unsigned long long K,
 // writes the items ranked below K to their place.
 constexpr unsigned kTile = 2048;
 constexpr unsigned kTileSortMax = 1u << 17;
+// One-block selection (k_block_select, below): lists up to kBlockSel items,
+// sorted output up to kBlockSort items.
+constexpr int kBlockSel = 16384;
+constexpr int kBlockSort = 2048;
 
 __device__ __forceinline__ bool item_before(unsigned long long ap, unsigned long long ak, uint32_t ai,
                                             unsigned long long bp, unsigned long long bk, uint32_t bi) {
@@ -424,6 +428,68 @@ k_merge_rank(const Item* __restrict__ tiles, const uint32_t* __restrict__ pos, u
     rank += lo;
   }
   if (rank < K) out[rank] = me;
+}
+
+// Pairwise merge of sorted runs of length L (kTile times a power of two):
+// item x of run R goes to (R & ~1) L + its rank inside R + the number of
+// items of the partner run R ^ 1 ordered before it (a binary search; the
+// order is total, so the places are distinct).
+__global__ void __launch_bounds__(256)
+k_merge_pairs(const Item* __restrict__ in, const uint32_t* __restrict__ pin, unsigned n,
+              unsigned L, Item* __restrict__ out, uint32_t* __restrict__ pout) {
+  const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  const unsigned R = x / L, r = x - R * L;
+  const unsigned pb = (R ^ 1u) * L;
+  const Item me = in[x];
+  const uint32_t mi = pin[x];
+  unsigned lo = 0;
+  if (pb < n) {
+    unsigned cnt = min(L, n - pb);
+    while (cnt > 0) {
+      const unsigned half = cnt >> 1, q = pb + lo + half;
+      if (item_before(in[q].p, in[q].key, pin[q], me.p, me.key, mi)) {
+        lo += half + 1;
+        cnt -= half + 1;
+      } else {
+        cnt = half;
+      }
+    }
+  }
+  const unsigned dst = (R & ~1u) * L + r + lo;
+  out[dst] = me;
+  pout[dst] = mi;
+}
+
+// Every item of in[0..n) sorted into ws.out (kTile < n <= kTileSortMax):
+// tiles sorted in shared memory, then log2(tiles) rounds of pairwise
+// merges.  Items alternate between ws.l1 and ws.out, their input positions
+// between the two halves of ws.l2; `in` may be ws.out.
+void sort_merge(mad_ctx* ctx, const SelectWs& ws, const Item* in, uint64_t n, cudaStream_t st) {
+  const unsigned tiles = (unsigned)((n + kTile - 1) / kTile);
+  int rounds = 0;
+  while ((1u << rounds) < tiles) ++rounds;
+  uint32_t* pa = (uint32_t*)ws.l2;
+  uint32_t* pb = pa + n;
+  // The buffer the tile sort writes, so that the last round lands in ws.out
+  // (ws.l1 when `in` is ws.out itself, then one copy at the end).
+  Item* cur = (rounds % 2 == 0 && in != ws.out) ? ws.out : ws.l1;
+  Item* other = cur == ws.out ? ws.l1 : ws.out;
+  k_tile_sort<<<tiles, kTile / 2, 0, st>>>(in, (unsigned)n, (unsigned)n, cur, pa, nullptr,
+                                            nullptr);
+  count_launch(ctx);
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  for (int r = 0; r < rounds; ++r) {
+    k_merge_pairs<<<blocks, 256, 0, st>>>(cur, pa, (unsigned)n, kTile << r, other, pb);
+    count_launch(ctx);
+    Item* t = cur;
+    cur = other;
+    other = t;
+    uint32_t* u = pa;
+    pa = pb;
+    pb = u;
+  }
+  if (cur != ws.out) cudaMemcpyAsync(ws.out, cur, n * sizeof(Item), cudaMemcpyDeviceToDevice, st);
 }
 
 // Sorted top K of `in[0..n)` by tiles (n <= kTileSortMax).  Uses l1 and l2
@@ -592,6 +658,8 @@ SelectWs select_ws_carve(void* base, uint64_t n, uint64_t K) {
   return ws;
 }
 
+void prefilter_select(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K, cudaStream_t st);
+
 mad_status select_list(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K, int dp,
                        uint64_t* n_sel, cudaStream_t st) {
   const uint64_t take = K < n ? K : n;
@@ -602,7 +670,12 @@ mad_status select_list(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K,
   // pick the K largest, unordered, into ws.out (an MSB radix select), which
   // the tile sort then orders when K is short, else a bitonic network.
   if (n <= kTileSortMax) {
-    tile_select(ctx, ws, ws.l0, n, take, st);
+    if (take <= (uint64_t)kBlockSort && take < n && n > (uint64_t)kTile)
+      prefilter_select(ctx, ws, n, take, st);
+    else if (take == n && n > (uint64_t)kTile)
+      sort_merge(ctx, ws, ws.l0, n, st);
+    else
+      tile_select(ctx, ws, ws.l0, n, take, st);
     return cuda_status(cudaGetLastError());
   }
   if (take == n) {
@@ -624,7 +697,8 @@ mad_status select_list(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K,
     count_launch(ctx);
   }
   if (take <= kTileSortMax) {
-    tile_select(ctx, ws, ws.out, take, take, st);
+    if (take > (uint64_t)kTile) sort_merge(ctx, ws, ws.out, take, st);
+    else tile_select(ctx, ws, ws.out, take, take, st);
     return cuda_status(cudaGetLastError());
   }
   bitonic_sort(ctx, ws.out, take, st, &n2);
@@ -684,8 +758,6 @@ void tile_select_dev(mad_ctx* ctx, const Item* in, uint64_t cap, uint64_t K,
 // no particular order, or sorted when `sorted` (K <= kBlockSort).  A longer
 // list sets *gate to 1 and writes nothing (the tile kernels, gated on that
 // word, select instead); otherwise *gate becomes 0.
-constexpr int kBlockSel = 16384;
-constexpr int kBlockSort = 2048;
 
 // The digit of the K-th largest value among those counted in hist (256
 // bins, digit order): returns it and leaves in *rank the rank of that value
@@ -893,6 +965,72 @@ k_block_select(const Item* __restrict__ in, unsigned long long cap, const unsign
   if (threadIdx.x == 0) *gate = 0u;
 }
 
+// ---- prefilter for a short K of a longer list -------------------------------
+// The bits in which the p of the list differ from the first item's: the
+// bits above the highest of them are the same in every item, so the ten bits
+// from it downwards are a bin that is monotone in p.  A histogram of those
+// bins gives the lowest bin whose count from the top reaches K; the items
+// in it and above (K plus the other items of that bin) are compacted for the
+// one-block selection.
+__global__ void __launch_bounds__(256)
+k_pf_diff(const Item* __restrict__ in, unsigned long long n, SelState* st) {
+  const unsigned long long v0 = in[0].p;
+  unsigned long long diff = 0;
+  for (unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (unsigned long long)gridDim.x * blockDim.x)
+    diff |= in[x].p ^ v0;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) diff |= __shfl_xor_sync(0xFFFFFFFFu, diff, off);
+  if ((threadIdx.x & 31) == 0 && diff) atomicOr(&st->maxp, diff);
+}
+
+__device__ __forceinline__ int pf_shift(unsigned long long diff) {
+  const int hb = diff ? 63 - __clzll((long long)diff) : 0;
+  return hb > 9 ? hb - 9 : 0;
+}
+
+__global__ void __launch_bounds__(256)
+k_pf_hist(const Item* __restrict__ in, unsigned long long n, unsigned long long K, SelState* st) {
+  __shared__ unsigned int h[1024];
+  for (int b = threadIdx.x; b < 1024; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const int sh = pf_shift(st->maxp);
+  for (unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (unsigned long long)gridDim.x * blockDim.x)
+    atomicAdd(&h[(in[x].p >> sh) & 1023u], 1u);
+  __syncthreads();
+  for (int b = threadIdx.x; b < 1024; b += blockDim.x)
+    if (h[b]) atomicAdd(&st->lhist[b], h[b]);
+  __threadfence();
+  __shared__ unsigned int is_last;
+  if (threadIdx.x == 0) is_last = (atomicAdd(&st->ticket3, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  unsigned long long total = 0;
+  const int b = block_pick_from_top<1024>(st->lhist, K, &total);
+  if (threadIdx.x == 0) st->theta = b >= 0 ? (unsigned long long)b : 0ull;
+}
+
+__global__ void __launch_bounds__(256)
+k_pf_compact(const Item* __restrict__ in, unsigned long long n, const SelState* st,
+             Item* __restrict__ out, unsigned long long* counter, uint64_t cap) {
+  const int sh = pf_shift(st->maxp);
+  const unsigned long long theta = st->theta;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long rounds = (n + stride - 1) / stride;
+  for (unsigned long long r = 0; r < rounds; ++r) {
+    const unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x + r * stride;
+    bool want = false;
+    Item it;
+    if (x < n) {
+      it = in[x];
+      want = ((it.p >> sh) & 1023u) >= theta;
+    }
+    append_block1(out, counter, want, it, cap);
+  }
+}
+
 void block_select_dev(mad_ctx* ctx, const Item* in, uint64_t cap, uint64_t K,
                       const unsigned long long* n_dev, bool sorted, Item* tile_sorted,
                       uint32_t* pos, Item* out, unsigned int* gate, unsigned int* over_err,
@@ -914,6 +1052,26 @@ void block_select_dev(mad_ctx* ctx, const Item* in, uint64_t cap, uint64_t K,
 }
 
 size_t dev_select_state_bytes() { return ((sizeof(SelState) + 255) / 256) * 256; }
+
+// The sorted top K (K <= kBlockSort < n <= kTileSortMax) of ws.l0[0..n) into
+// ws.out: the prefilter, then the one-block selection of the compacted
+// items; when more than kBlockSel of them tie into the threshold bin, the
+// tile kernels (gated on the block's word) select from the whole list.
+void prefilter_select(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K, cudaStream_t st) {
+  SelState* dst = (SelState*)ws.state;
+  cudaMemsetAsync(dst, 0, sizeof(SelState), st);
+  cudaMemsetAsync(ws.counter, 0, sizeof(unsigned long long), st);
+  unsigned int* gate = (unsigned int*)(ws.counter + 2);
+  const unsigned blocks = grid_for(n, 152 * 4);
+  k_pf_diff<<<blocks, 256, 0, st>>>(ws.l0, n, dst);
+  k_pf_hist<<<blocks, 256, 0, st>>>(ws.l0, n, K, dst);
+  k_pf_compact<<<blocks, 256, 0, st>>>(ws.l0, n, dst, ws.l1, ws.counter, ws.cap_n);
+  count_launch(ctx, 3);
+  // (the fallback's input positions go to ws.l0: the compacted list holds
+  // every item it still needs)
+  block_select_dev(ctx, ws.l1, n, K, ws.counter, true, ws.l2, (uint32_t*)ws.l0, ws.out, gate,
+                   nullptr, st);
+}
 
 void select_hash_dev(mad_ctx* ctx, uint64_t K, const unsigned long long* hcap_dev, void* state,
                      unsigned long long* count, Item* list, Item* sorted, uint32_t* pos,
