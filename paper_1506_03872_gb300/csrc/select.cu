@@ -969,9 +969,12 @@ k_block_select(const Item* __restrict__ in, unsigned long long cap, const unsign
 // The bits in which the p of the list differ from the first item's: the
 // bits above the highest of them are the same in every item, so the ten bits
 // from it downwards are a bin that is monotone in p.  A histogram of those
-// bins gives the lowest bin whose count from the top reaches K; the items
-// in it and above (K plus the other items of that bin) are compacted for the
-// one-block selection.
+// bins gives the lowest bin whose count from the top reaches K; a second
+// histogram of the next ten bits, over the items of that bin only, refines
+// it (values spread over several octaves, such as the bits of doubles,
+// leave most items in one first-level bin).  The items above the refined
+// threshold (K plus the others of its bin) are compacted for the one-block
+// selection.
 __global__ void __launch_bounds__(256)
 k_pf_diff(const Item* __restrict__ in, unsigned long long n, SelState* st) {
   const unsigned long long v0 = in[0].p;
@@ -989,15 +992,26 @@ __device__ __forceinline__ int pf_shift(unsigned long long diff) {
   return hb > 9 ? hb - 9 : 0;
 }
 
+// Level 1 (bins of p >> sh1 over every item) or level 2 (bins of p >> sh2
+// over the items in the level-1 threshold bin).  The last block picks the
+// bin where the count from the top reaches K (level 1), or K less the items
+// above that bin (level 2); level 1 also leaves that count in st->positive
+// and clears the histogram for level 2.
+template <int kLevel>
 __global__ void __launch_bounds__(256)
 k_pf_hist(const Item* __restrict__ in, unsigned long long n, unsigned long long K, SelState* st) {
   __shared__ unsigned int h[1024];
   for (int b = threadIdx.x; b < 1024; b += blockDim.x) h[b] = 0;
   __syncthreads();
-  const int sh = pf_shift(st->maxp);
+  const int sh1 = pf_shift(st->maxp);
+  const int sh2 = sh1 > 10 ? sh1 - 10 : 0;
+  const unsigned long long theta1 = kLevel == 2 ? st->theta : 0ull;
   for (unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-       x += (unsigned long long)gridDim.x * blockDim.x)
-    atomicAdd(&h[(in[x].p >> sh) & 1023u], 1u);
+       x += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long v = in[x].p;
+    if (kLevel == 1) atomicAdd(&h[(v >> sh1) & 1023u], 1u);
+    else if (((v >> sh1) & 1023u) == theta1) atomicAdd(&h[(v >> sh2) & 1023u], 1u);
+  }
   __syncthreads();
   for (int b = threadIdx.x; b < 1024; b += blockDim.x)
     if (h[b]) atomicAdd(&st->lhist[b], h[b]);
@@ -1007,16 +1021,37 @@ k_pf_hist(const Item* __restrict__ in, unsigned long long n, unsigned long long 
   __syncthreads();
   if (!is_last) return;
   __threadfence();
+  const unsigned long long k = kLevel == 1 ? K : K - st->positive;
   unsigned long long total = 0;
-  const int b = block_pick_from_top<1024>(st->lhist, K, &total);
-  if (threadIdx.x == 0) st->theta = b >= 0 ? (unsigned long long)b : 0ull;
+  const int b = block_pick_from_top<1024>(st->lhist, k, &total);
+  const unsigned long long pick = b >= 0 ? (unsigned long long)b : 0ull;
+  if (kLevel == 1) {
+    // The items in bins above the pick, then a clear histogram.
+    __shared__ unsigned long long above;
+    if (threadIdx.x == 0) above = 0;
+    __syncthreads();
+    unsigned long long mine = 0;
+    for (int q = threadIdx.x; q < 1024; q += blockDim.x)
+      if ((unsigned long long)q > pick) mine += __ldcg(st->lhist + q);
+    atomicAdd(&above, mine);
+    __syncthreads();
+    for (int q = threadIdx.x; q < 1024; q += blockDim.x) st->lhist[q] = 0;
+    if (threadIdx.x == 0) {
+      st->theta = pick;
+      st->positive = above;
+      st->ticket3 = 0;
+    }
+  } else if (threadIdx.x == 0) {
+    st->tp = pick;
+  }
 }
 
 __global__ void __launch_bounds__(256)
 k_pf_compact(const Item* __restrict__ in, unsigned long long n, const SelState* st,
              Item* __restrict__ out, unsigned long long* counter, uint64_t cap) {
-  const int sh = pf_shift(st->maxp);
-  const unsigned long long theta = st->theta;
+  const int sh1 = pf_shift(st->maxp);
+  const int sh2 = sh1 > 10 ? sh1 - 10 : 0;
+  const unsigned long long theta1 = st->theta, theta2 = st->tp;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   const unsigned long long rounds = (n + stride - 1) / stride;
   for (unsigned long long r = 0; r < rounds; ++r) {
@@ -1025,7 +1060,8 @@ k_pf_compact(const Item* __restrict__ in, unsigned long long n, const SelState* 
     Item it;
     if (x < n) {
       it = in[x];
-      want = ((it.p >> sh) & 1023u) >= theta;
+      const unsigned long long b1 = (it.p >> sh1) & 1023u;
+      want = b1 > theta1 || (b1 == theta1 && ((it.p >> sh2) & 1023u) >= theta2);
     }
     append_block1(out, counter, want, it, cap);
   }
@@ -1064,9 +1100,10 @@ void prefilter_select(mad_ctx* ctx, const SelectWs& ws, uint64_t n, uint64_t K, 
   unsigned int* gate = (unsigned int*)(ws.counter + 2);
   const unsigned blocks = grid_for(n, 152 * 4);
   k_pf_diff<<<blocks, 256, 0, st>>>(ws.l0, n, dst);
-  k_pf_hist<<<blocks, 256, 0, st>>>(ws.l0, n, K, dst);
+  k_pf_hist<1><<<blocks, 256, 0, st>>>(ws.l0, n, K, dst);
+  k_pf_hist<2><<<blocks, 256, 0, st>>>(ws.l0, n, K, dst);
   k_pf_compact<<<blocks, 256, 0, st>>>(ws.l0, n, dst, ws.l1, ws.counter, ws.cap_n);
-  count_launch(ctx, 3);
+  count_launch(ctx, 4);
   // (the fallback's input positions go to ws.l0: the compacted list holds
   // every item it still needs)
   block_select_dev(ctx, ws.l1, n, K, ws.counter, true, ws.l2, (uint32_t*)ws.l0, ws.out, gate,

@@ -143,3 +143,37 @@ def test_merge_path_counts_exact():
     i, j = rng.integers(0, m, 3000), rng.integers(0, m, 3000)
     i[:10] = j[:10]
     _check(rowptr, colidx, (m, d), bt, i, j)
+
+
+def test_grouped_top_t_matches_oracle():
+    """t < ncand: the top t by c (ties by smaller key), as the oracle's
+    selection takes them, from counts that span several octaves."""
+    import oracle
+    import paper_1506_03872_gb300 as mad
+    from paper_1506_03872_gb300 import workloads as W
+    w = W.chung_lu(nodes=30000, edges=400000, seed=26)
+    rowptr, colidx, m = w.rowptr, w.colidx, w.m
+    deg = np.diff(rowptr)
+    rng = _rng(27)
+    hubs = np.argsort(-deg, kind="stable")[:120]
+    pairs = {(int(min(a, b)), int(max(a, b))) for a in hubs for b in hubs if a != b}
+    while len(pairs) < 12000:
+        a, b = rng.integers(0, m, 2)
+        if a != b:
+            pairs.add((int(min(a, b)), int(max(a, b))))
+    p = np.array(sorted(pairs), dtype=np.int64)
+    p = p[rng.permutation(len(p))]
+    i, j = p[:, 0], p[:, 1]
+    keys = mad.keys_of(i.astype(np.uint32), j.astype(np.uint32))
+    want = _expected(rowptr, colidx, i, j)
+    t = [torch.from_numpy(x).cuda() for x in (rowptr, colidx)]
+    with mad.Context(GRAM_EXCL) as c:
+        A = mad.csr(t[0], t[1], (m, m))
+        c.build(A, A, 1000, keep=tuple(t))
+        for tt in (1, 300, 2048):
+            res, nr = mad.mad_rescore(c.ctx, mad.encode_pairs(i, j), len(i), tt)
+            gi, gj, _, gc = mad.decode_pairs(res, nr)
+            tk, tc = oracle.topt(keys, want, tt)
+            assert nr == len(tk)
+            assert np.array_equal(mad.keys_of(gi, gj), tk)
+            assert np.array_equal(gc, tc)
