@@ -562,34 +562,78 @@ k_a_rows_short(const T* __restrict__ A, int64_t m, int d, int64_t lda,
 // ---------------------------------------------------------------------------
 // Rows of 0/1 CSR A (integer mode): T2 = prefix of deg_k^B, r_i.
 // ---------------------------------------------------------------------------
+// Rows of at most kShortRow entries (most rows of a sparse graph) are
+// taken one per lane, their entries' weights loaded eight at a time; the
+// warp then works through its lanes' longer rows together.  Lane l of warp
+// w (of W) takes rows w + l W + 32 W k, so that heavy rows with neighbouring
+// indices (generators often number nodes by weight) go to different warps.
+// A warp per row, as for the long rows, spent a chain of dependent loads on
+// every short row in turn.
+constexpr int64_t kShortRow = 32;
+
 __global__ void __launch_bounds__(256)
 k_a_rows_binary(const int64_t* __restrict__ a_ptr, const int32_t* __restrict__ a_col,
                 const int64_t* __restrict__ b_ptr, int64_t m, uint32_t* __restrict__ T2,
                 unsigned long long* __restrict__ r64, DevScalars* sc) {
   const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int warps = blockDim.x >> 5;
-  for (int64_t i = (int64_t)blockIdx.x * warps + warp; i < m; i += (int64_t)gridDim.x * warps) {
-    const int64_t a0 = a_ptr[i], a1 = a_ptr[i + 1];
-    unsigned long long carry = 0;
-    bool over = false;
-    for (int64_t base = a0; base < a1; base += 32) {
-      const int64_t e = base + lane;
-      unsigned long long q = 0;
-      if (e < a1) {
-        const int32_t k = a_col[e];
-        q = (unsigned long long)(b_ptr[k + 1] - b_ptr[k]);
-      }
-      const unsigned long long inc = warp_inclusive_u64(q, lane) + carry;
-      if (e < a1) {
-        if (inc > 0xFFFFFFFFull) over = true;
-        T2[e] = (uint32_t)inc;
-      }
-      carry = __shfl_sync(0xFFFFFFFFu, inc, 31);
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  bool over = false;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int64_t base = 0; base < m; base += warps * 32) {
+    const int64_t i = base + (int64_t)lane * warps + w;
+    int64_t a0 = 0, a1 = 0;
+    if (i < m) {
+      a0 = a_ptr[i];
+      a1 = a_ptr[i + 1];
     }
-    if (__any_sync(0xFFFFFFFFu, over) && lane == 0) atomicOr(&sc->err, DERR_OVERFLOW);
-    if (lane == 0) r64[i] = (unsigned long long)(a1 - a0) * carry;
+    const bool longrow = a1 - a0 > kShortRow;
+    if (i < m && !longrow) {
+      unsigned long long acc = 0;
+      for (int64_t e0 = a0; e0 < a1; e0 += 8) {
+        unsigned long long q[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          q[u] = 0;
+          if (e0 + u < a1) {
+            const int32_t k = a_col[e0 + u];
+            q[u] = (unsigned long long)(b_ptr[k + 1] - b_ptr[k]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (e0 + u < a1) {
+            acc += q[u];
+            if (acc > 0xFFFFFFFFull) over = true;
+            T2[e0 + u] = (uint32_t)acc;
+          }
+        }
+      }
+      r64[i] = (unsigned long long)(a1 - a0) * acc;
+    }
+    unsigned lm = __ballot_sync(0xFFFFFFFFu, i < m && longrow);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int64_t r0 = __shfl_sync(0xFFFFFFFFu, a0, src), r1 = __shfl_sync(0xFFFFFFFFu, a1, src);
+      unsigned long long carry = 0;
+      for (int64_t b = r0; b < r1; b += 32) {
+        const int64_t e = b + lane;
+        unsigned long long q = 0;
+        if (e < r1) {
+          const int32_t k = a_col[e];
+          q = (unsigned long long)(b_ptr[k + 1] - b_ptr[k]);
+        }
+        const unsigned long long inc = warp_inclusive_u64(q, lane) + carry;
+        if (e < r1) {
+          if (inc > 0xFFFFFFFFull) over = true;
+          T2[e] = (uint32_t)inc;
+        }
+        carry = __shfl_sync(0xFFFFFFFFu, inc, 31);
+      }
+      if (lane == 0) r64[base + (int64_t)src * warps + w] = (unsigned long long)(r1 - r0) * carry;
+    }
   }
+  if (__any_sync(0xFFFFFFFFu, over) && lane == 0) atomicOr(&sc->err, DERR_OVERFLOW);
 }
 
 // ---------------------------------------------------------------------------
@@ -627,20 +671,35 @@ __global__ void __launch_bounds__(256)
 k_guide_fill(const int64_t* __restrict__ a_ptr, const uint32_t* __restrict__ T2, int64_t m,
              const unsigned long long* __restrict__ gptr, const uint8_t* __restrict__ shift,
              uint32_t* __restrict__ G) {
+  // A warp looks at 32 rows at once (lane l of warp w of W: rows
+  // w + l W + 32 W k) and fills the guides of those that have one together.
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += warps) {
-    const unsigned long long g0 = gptr[i], n = gptr[i + 1] - g0;
-    if (n == 0) continue;
-    const int64_t a0 = a_ptr[i], len = a_ptr[i + 1] - a0;
-    const int sh = shift[i];
-    for (unsigned long long b = lane; b < n; b += 32) {
-      const unsigned long long thr = b << sh;   // count the entries below thr
-      uint32_t cnt;
-      if (thr == 0) cnt = 0;
-      else if (thr > 0xFFFFFFFFull) cnt = (uint32_t)len;
-      else cnt = (uint32_t)ub_u32(T2 + a0, (int)len, (uint32_t)(thr - 1), 0xFFFFFFFFu);
-      G[g0 + b] = cnt;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int64_t base = 0; base < m; base += warps * 32) {
+    const int64_t r = base + (int64_t)lane * warps + w;
+    unsigned long long g0r = 0, nr = 0;
+    if (r < m) {
+      g0r = gptr[r];
+      nr = gptr[r + 1] - g0r;
+    }
+    unsigned gm = __ballot_sync(0xFFFFFFFFu, nr != 0);
+    while (gm) {
+      const int src = __ffs(gm) - 1;
+      gm &= gm - 1;
+      const int64_t i = base + (int64_t)src * warps + w;
+      const unsigned long long g0 = __shfl_sync(0xFFFFFFFFu, g0r, src);
+      const unsigned long long n = __shfl_sync(0xFFFFFFFFu, nr, src);
+      const int64_t a0 = a_ptr[i], len = a_ptr[i + 1] - a0;
+      const int sh = shift[i];
+      for (unsigned long long b = lane; b < n; b += 32) {
+        const unsigned long long thr = b << sh;   // count the entries below thr
+        uint32_t cnt;
+        if (thr == 0) cnt = 0;
+        else if (thr > 0xFFFFFFFFull) cnt = (uint32_t)len;
+        else cnt = (uint32_t)ub_u32(T2 + a0, (int)len, (uint32_t)(thr - 1), 0xFFFFFFFFu);
+        G[g0 + b] = cnt;
+      }
     }
   }
 }
@@ -897,14 +956,35 @@ mad_status t2_guide_offsets(mad_ctx* ctx, cudaStream_t st) {
 __global__ void __launch_bounds__(256)
 k_bloom_build(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col, int64_t rows,
               int shift, unsigned long long* __restrict__ words) {
+  // Short rows one per lane, longer ones by the whole warp (lane l of warp
+  // w of W: rows w + l W + 32 W k).
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
-    const int64_t e0 = ptr[r], e1 = ptr[r + 1];
-    for (int64_t e = e0 + lane; e < e1; e += 32) {
-      const unsigned long long key = ((unsigned long long)r << 32) | (uint32_t)col[e];
-      const unsigned long long h = mix64(key);
-      atomicOr(words + (h >> shift), bloom_bits(h));
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int64_t base = 0; base < rows; base += warps * 32) {
+    const int64_t r = base + (int64_t)lane * warps + w;
+    int64_t e0 = 0, e1 = 0;
+    if (r < rows) {
+      e0 = ptr[r];
+      e1 = ptr[r + 1];
+    }
+    const bool longrow = e1 - e0 > 32;
+    if (r < rows && !longrow) {
+      for (int64_t e = e0; e < e1; ++e) {
+        const unsigned long long h = mix64(((unsigned long long)r << 32) | (uint32_t)col[e]);
+        atomicOr(words + (h >> shift), bloom_bits(h));
+      }
+    }
+    unsigned lm = __ballot_sync(0xFFFFFFFFu, r < rows && longrow);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const unsigned long long rr = (unsigned long long)(base + (int64_t)src * warps + w);
+      const int64_t f0 = __shfl_sync(0xFFFFFFFFu, e0, src), f1 = __shfl_sync(0xFFFFFFFFu, e1, src);
+      for (int64_t e = f0 + lane; e < f1; e += 32) {
+        const unsigned long long h = mix64((rr << 32) | (uint32_t)col[e]);
+        atomicOr(words + (h >> shift), bloom_bits(h));
+      }
     }
   }
 }
@@ -964,13 +1044,38 @@ k_t1g_fill(const uint64_t* __restrict__ T1, int64_t m, const DevScalars* sc,
   if (total == 0ull) return;
   const int sh = sc->t1g_sh;
   const unsigned long long nb1 = ((total - 1) >> sh) + 2;   // nb + 1 entries
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long b_hi = T1[e] >> sh;
-    const unsigned long long b_lo = e ? (T1[e - 1] >> sh) + 1 : 0;
-    for (unsigned long long b = b_lo; b <= b_hi && b < nb1; ++b) G[b] = (uint32_t)e;
-    if (e == m - 1)
-      for (unsigned long long b = b_hi + 1; b < nb1; ++b) G[b] = (uint32_t)m;
+  // Lane l of warp w of W takes entries w + l W + 32 W k; ranges of more
+  // than 32 guide entries (the heaviest rows) are written by the whole warp.
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int64_t base = 0; base < m; base += warps * 32) {
+    const int64_t e = base + (int64_t)lane * warps + w;
+    unsigned long long b_lo = 0, b_end = 0;   // guide entries [b_lo, b_end) get e
+    if (e < m) {
+      const unsigned long long b_hi = T1[e] >> sh;
+      b_lo = e ? (T1[e - 1] >> sh) + 1 : 0;
+      b_end = b_hi + 1 < nb1 ? b_hi + 1 : nb1;
+      if (e == m - 1) b_end = nb1;   // and every later one gets m
+      if (b_end < b_lo) b_end = b_lo;
+    }
+    const bool wide = b_end - b_lo > 32;
+    if (e < m && !wide) {
+      const unsigned long long b_last = e == m - 1 ? ((T1[e] >> sh) + 1 < nb1 ? (T1[e] >> sh) + 1 : nb1) : b_end;
+      for (unsigned long long b = b_lo; b < b_end; ++b) G[b] = b < b_last ? (uint32_t)e : (uint32_t)m;
+    }
+    unsigned wm = __ballot_sync(0xFFFFFFFFu, e < m && wide);
+    while (wm) {
+      const int src = __ffs(wm) - 1;
+      wm &= wm - 1;
+      const int64_t ee = base + (int64_t)src * warps + w;
+      const unsigned long long lo = __shfl_sync(0xFFFFFFFFu, b_lo, src);
+      const unsigned long long end = __shfl_sync(0xFFFFFFFFu, b_end, src);
+      const unsigned long long hi_t = T1[ee] >> sh;
+      const unsigned long long last = ee == m - 1 ? (hi_t + 1 < nb1 ? hi_t + 1 : nb1) : end;
+      for (unsigned long long b = lo + lane; b < end; b += 32)
+        G[b] = b < last ? (uint32_t)ee : (uint32_t)m;
+    }
   }
 }
 
