@@ -55,6 +55,23 @@ __device__ __forceinline__ uint32_t digit_of(const Item& it, int q, int dp) {
   return (uint32_t)((~it.key) >> (8 * (7 - (q - dp)))) & 0xFFu;
 }
 
+// Warp-aggregated append of `it` when `want` (one counter atomic per warp
+// that holds an item: the cheaper form when few warps do).
+__device__ __forceinline__ void append_warp(Item* out, unsigned long long* counter, bool want,
+                                            const Item& it, uint64_t cap) {
+  const unsigned mask = __ballot_sync(0xFFFFFFFFu, want);
+  if (!mask) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  if (want) {
+    const unsigned long long pos = base + __popc(mask & ((1u << lane) - 1u));
+    if (pos < cap) out[pos] = it;
+  }
+}
+
 // Block-wide append of up to N items per thread: every thread of the block
 // calls it the same number of times.  One atomic on the counter per block
 // and call (a single counter shared by every warp of the grid serialises
@@ -270,6 +287,11 @@ k_log_hist(const long long* __restrict__ vals, uint64_t cap_max, unsigned long l
   }
 }
 
+// kBlock: one counter atomic per block and round (0/1 inputs: their small
+// counts tie at the threshold, so most warps of 32 slots hold an item and
+// per-warp atomics on the one counter serialise); otherwise one atomic per
+// warp that holds an item (dense inputs: a thin band of slots passes).
+template <bool kBlock>
 __global__ void __launch_bounds__(256)
 k_compact_ge(const unsigned long long* __restrict__ keys, const long long* __restrict__ vals,
              uint64_t cap_max, const SelState* st, Item* __restrict__ out, uint64_t out_cap,
@@ -289,20 +311,27 @@ k_compact_ge(const unsigned long long* __restrict__ keys, const long long* __res
       const uint64_t slot = start + (r * U + q) * stride;
       v[q] = slot < cap ? __ldcs(vals + slot) : 0;
     }
-    bool want[U];
-    Item it[U];
 #pragma unroll
     for (int q = 0; q < U; ++q) {
       const uint64_t slot = start + (r * U + q) * stride;
-      want[q] = v[q] > 0 && (unsigned long long)v[q] >= theta;
-      if (want[q]) {
-        it[q].p = (unsigned long long)v[q];
-        it[q].key = keys[slot];
-        it[q].aux = slot;
+      const bool want = v[q] > 0 && (unsigned long long)v[q] >= theta;
+      Item it;
+      if (want) {
+        it.p = (unsigned long long)v[q];
+        it.key = keys[slot];
+        it.aux = slot;
       }
+      if (kBlock) append_block1(out, counter, want, it, out_cap);
+      else append_warp(out, counter, want, it, out_cap);
     }
-    append_block<U>(out, counter, want, it, out_cap);
   }
+}
+
+// k_compact_ge in the append mode of the context's inputs.
+template <typename... Args>
+void launch_compact_ge(const mad_ctx* ctx, unsigned blocks, cudaStream_t st, Args... args) {
+  if (ctx->integer) k_compact_ge<true><<<blocks, 256, 0, st>>>(args...);
+  else k_compact_ge<false><<<blocks, 256, 0, st>>>(args...);
 }
 
 // After a compaction at a threshold estimated from a sample: when it kept
@@ -714,8 +743,8 @@ mad_status select_from_hash(mad_ctx* ctx, const SelectWs& ws, uint64_t K, uint64
   const unsigned blocks = grid_for(bound, 152 * 8);
   const unsigned long long* extent = hash_extent(ctx);
   k_log_hist<<<blocks, 256, 0, st>>>(ctx->hvals, bound, K, dst, extent);
-  k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, bound, dst, ws.l0, ws.cap_n,
-                                       ws.counter, extent);
+  launch_compact_ge(ctx, blocks, st, ctx->hkeys, ctx->hvals, bound, dst, ws.l0, ws.cap_n,
+                    ws.counter, extent);
   count_launch(ctx, 2);
   unsigned long long host[2] = {0, 0};
   cudaMemcpyAsync(&host[0], ws.counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
@@ -1127,12 +1156,12 @@ void select_hash_dev(mad_ctx* ctx, uint64_t K, const unsigned long long* hcap_de
   unsigned int* gate = (unsigned int*)(count + 1);
   k_log_hist<<<(blocks + (1u << kLg) - 1) >> kLg, 256, 0, st>>>(ctx->hvals, bound, Ks, dst,
                                                                  hcap_dev, kLg);
-  k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, bound, dst, list,
-                                       kDevSelectCap, count, hcap_dev);
+  launch_compact_ge(ctx, blocks, st, ctx->hkeys, ctx->hvals, bound, dst, list, kDevSelectCap,
+                    count, hcap_dev);
   k_select_check<<<1, 256, 0, st>>>(dst, count, K, gate);
   k_log_hist<<<blocks, 256, 0, st>>>(ctx->hvals, bound, K, dst, hcap_dev, 0, gate);
-  k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, bound, dst, list,
-                                       kDevSelectCap, count, hcap_dev, gate);
+  launch_compact_ge(ctx, blocks, st, ctx->hkeys, ctx->hvals, bound, dst, list, kDevSelectCap,
+                    count, hcap_dev, gate);
   count_launch(ctx, 5);
   block_select_dev(ctx, list, kDevSelectCap, K, count, false, sorted, pos, out,
                    (unsigned int*)(count + 2), &ctx->sc->err, st);
@@ -1184,8 +1213,8 @@ void select_hash_dev_long(mad_ctx* ctx, uint64_t K, const unsigned long long* hc
   const unsigned blocks = grid_for(bound, 152 * 8);
   // Exact log-bucket threshold, then every x at or above it.
   k_log_hist<<<blocks, 256, 0, st>>>(ctx->hvals, bound, K, dst, hcap_dev, 0);
-  k_compact_ge<<<blocks, 256, 0, st>>>(ctx->hkeys, ctx->hvals, bound, dst, list, list_cap, count,
-                                       hcap_dev);
+  launch_compact_ge(ctx, blocks, st, ctx->hkeys, ctx->hvals, bound, dst, list, list_cap, count,
+                    hcap_dev);
   // The K first by (x desc, key asc): MSB radix select over the 8 bytes of
   // x and the 8 of the key, on the device length.
   k_radix_init_dev<<<1, 32, 0, st>>>(dst, count, list_cap, K, &ctx->sc->err);
