@@ -9,9 +9,9 @@
 // 0/1 Gram inputs (B = A^T): c_ij = |row i of A ∩ row j of A|.  When a
 // bitmap over the d columns fits in shared memory, the candidates are
 // grouped by their endpoint of larger degree (the hub) and one block per SM
-// takes 64 of them at a time: it sets the hub's row as bits, then each warp
-// counts the other endpoint's row against them with independent 16-byte
-// loads.  Otherwise one warp per candidate intersects the two sorted rows.
+// takes 64 of them at a time (from a counter): it sets the hub's row as
+// bits, then each warp counts the other endpoint's row against them with
+// independent 16-byte loads.  Otherwise one warp per candidate intersects the two sorted rows.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -212,6 +212,7 @@ struct __align__(16) GramRec {
 
 constexpr int kRgUnit = 64;        // candidates a block takes at a time
 constexpr int kRgThreads = 1024;
+constexpr int kRgKeep = 8;         // hub columns a thread keeps between set and clear
 
 __device__ __forceinline__ GramRec gram_rec(const mad_pair* __restrict__ cand, unsigned long long q,
                                             const int64_t* __restrict__ a_ptr, int64_t m) {
@@ -302,20 +303,28 @@ __global__ void __launch_bounds__(kRgThreads, 1)
 k_rescore_bitmap(const GramRec* __restrict__ rec, unsigned long long ncand_max,
                  const unsigned long long* n_dev, const int32_t* __restrict__ a_col, int64_t m,
                  int64_t d, double* __restrict__ cvals, Item* __restrict__ items,
-                 DevScalars* sc) {
+                 DevScalars* sc, unsigned long long* next_unit) {
   extern __shared__ uint32_t bits[];
   __shared__ GramRec s_rec[kRgUnit];
   __shared__ int s_start[kRgUnit + 1];
   __shared__ int s_nrun;
+  __shared__ unsigned long long s_unit;
   const unsigned long long ncand = dev_len(ncand_max, n_dev);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t words = (uint32_t)((d + 31) >> 5);
   for (uint32_t w = tid; w < words; w += kRgThreads) bits[w] = 0u;
   const unsigned long long units = (ncand + kRgUnit - 1) / kRgUnit;
-  for (unsigned long long u = blockIdx.x; u < units; u += gridDim.x) {
+  // Units from a counter: their cost varies with the number of hubs in
+  // them (one bitmap per hub), so a fixed assignment left some blocks
+  // twice the mean work.
+  for (;;) {
+    __syncthreads();   // the bitmap is clear and the previous unit's records are done
+    if (tid == 0) s_unit = atomicAdd(next_unit, 1ull);
+    __syncthreads();
+    const unsigned long long u = s_unit;
+    if (u >= units) break;
     const unsigned long long p0 = u * kRgUnit;
     const int n = (int)(ncand - p0 < (unsigned long long)kRgUnit ? ncand - p0 : kRgUnit);
-    __syncthreads();   // the bitmap is clear and the previous unit's records are done
     if (tid < n) {
       const uint4* src = reinterpret_cast<const uint4*>(rec + p0 + tid);
       uint4* dst = reinterpret_cast<uint4*>(s_rec + tid);
@@ -345,7 +354,20 @@ k_rescore_bitmap(const GramRec* __restrict__ rec, unsigned long long ncand_max,
       const bool valid = s_rec[a].hub < (uint64_t)m;
       const int32_t* H = a_col + s_rec[a].hub_start;
       const uint32_t hl = valid ? s_rec[a].hub_len : 0u;
-      for (uint32_t e = tid; e < hl; e += kRgThreads) {
+      // The hub's columns this thread sets, kept to clear them again (rows
+      // longer than kRgKeep x kRgThreads are read a second time).
+      int32_t keep[kRgKeep];
+#pragma unroll
+      for (int k = 0; k < kRgKeep; ++k) {
+        const uint32_t e = (uint32_t)tid + (uint32_t)k * kRgThreads;
+        keep[k] = e < hl ? __ldg(H + e) : -1;
+      }
+#pragma unroll
+      for (int k = 0; k < kRgKeep; ++k) {
+        const int32_t c = keep[k];
+        if ((uint32_t)c < (uint64_t)d) atomicOr(&bits[(uint32_t)c >> 5], 1u << ((uint32_t)c & 31u));
+      }
+      for (uint32_t e = tid + kRgKeep * kRgThreads; e < hl; e += kRgThreads) {
         const int32_t c = __ldg(H + e);
         if ((uint32_t)c < (uint64_t)d) atomicOr(&bits[(uint32_t)c >> 5], 1u << ((uint32_t)c & 31u));
       }
@@ -368,7 +390,12 @@ k_rescore_bitmap(const GramRec* __restrict__ rec, unsigned long long ncand_max,
         }
       }
       __syncthreads();
-      for (uint32_t e = tid; e < hl; e += kRgThreads) {
+#pragma unroll
+      for (int k = 0; k < kRgKeep; ++k) {
+        const int32_t c = keep[k];
+        if ((uint32_t)c < (uint64_t)d) bits[(uint32_t)c >> 5] = 0u;
+      }
+      for (uint32_t e = tid + kRgKeep * kRgThreads; e < hl; e += kRgThreads) {
         const int32_t c = __ldg(H + e);
         if ((uint32_t)c < (uint64_t)d) bits[(uint32_t)c >> 5] = 0u;
       }
@@ -384,7 +411,7 @@ constexpr size_t kBitmapMaxBytes = 200 * 1024;
 // Layout of the grouping buffer: hub counts and offsets (m + 1 each), the
 // scan's partials, then the records.
 struct RgLayout {
-  size_t cnt, off, part, rec, bytes;
+  size_t cnt, off, part, next, rec, bytes;
 };
 RgLayout rg_layout(int64_t m, uint64_t ncand) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -392,7 +419,8 @@ RgLayout rg_layout(int64_t m, uint64_t ncand) {
   L.cnt = 0;
   L.off = up((size_t)(m + 1) * sizeof(uint32_t));
   L.part = L.off + up((size_t)(m + 1) * sizeof(uint32_t));
-  L.rec = L.part + up(scan_partial_elems((uint64_t)m + 1) * sizeof(uint32_t));
+  L.next = L.part + up(scan_partial_elems((uint64_t)m + 1) * sizeof(uint32_t));
+  L.rec = L.next + 256;
   L.bytes = L.rec + (size_t)ncand * sizeof(GramRec);
   return L;
 }
@@ -426,8 +454,10 @@ mad_status rescore_gram_grouped(mad_ctx* ctx, const mad_pair* cand, uint64_t nca
   uint32_t* off = (uint32_t*)(base + L.off);
   uint32_t* part = (uint32_t*)(base + L.part);
   GramRec* rec = (GramRec*)(base + L.rec);
+  unsigned long long* next_unit = (unsigned long long*)(base + L.next);
   const uint64_t hubs = (uint64_t)ctx->m + 1;
   cudaMemsetAsync(cnt, 0, hubs * sizeof(uint32_t), st);
+  cudaMemsetAsync(next_unit, 0, sizeof(unsigned long long), st);
   const unsigned long long blocks = (ncand + 255) / 256;
   const unsigned grid = (unsigned)(blocks < 152 * 8 ? blocks : 152 * 8);
   k_rg_count<<<grid, 256, 0, st>>>(cand, ncand, n_dev, ctx->A.rowptr, ctx->m, cnt);
@@ -441,7 +471,7 @@ mad_status rescore_gram_grouped(mad_ctx* ctx, const mad_pair* cand, uint64_t nca
   const int full = rescore_bitmap_grid(smem);
   k_rescore_bitmap<<<(unsigned)(units < (unsigned long long)full ? units : full), kRgThreads, smem,
                      st>>>(rec, ncand, n_dev, ctx->A.colidx, ctx->m, ctx->d, cvals, items,
-                           ctx->sc);
+                           ctx->sc, next_unit);
   count_launch(ctx);
   return cuda_status(cudaGetLastError());
 }

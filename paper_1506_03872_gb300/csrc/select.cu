@@ -311,18 +311,33 @@ k_compact_ge(const unsigned long long* __restrict__ keys, const long long* __res
       const uint64_t slot = start + (r * U + q) * stride;
       v[q] = slot < cap ? __ldcs(vals + slot) : 0;
     }
+    if (kBlock) {   // the round's U items of every thread in one block-wide append
+      bool want[U];
+      Item it[U];
 #pragma unroll
-    for (int q = 0; q < U; ++q) {
-      const uint64_t slot = start + (r * U + q) * stride;
-      const bool want = v[q] > 0 && (unsigned long long)v[q] >= theta;
-      Item it;
-      if (want) {
-        it.p = (unsigned long long)v[q];
-        it.key = keys[slot];
-        it.aux = slot;
+      for (int q = 0; q < U; ++q) {
+        const uint64_t slot = start + (r * U + q) * stride;
+        want[q] = v[q] > 0 && (unsigned long long)v[q] >= theta;
+        if (want[q]) {
+          it[q].p = (unsigned long long)v[q];
+          it[q].key = keys[slot];
+          it[q].aux = slot;
+        }
       }
-      if (kBlock) append_block1(out, counter, want, it, out_cap);
-      else append_warp(out, counter, want, it, out_cap);
+      append_block<U>(out, counter, want, it, out_cap);
+    } else {
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const uint64_t slot = start + (r * U + q) * stride;
+        const bool want = v[q] > 0 && (unsigned long long)v[q] >= theta;
+        Item it;
+        if (want) {
+          it.p = (unsigned long long)v[q];
+          it.key = keys[slot];
+          it.aux = slot;
+        }
+        append_warp(out, counter, want, it, out_cap);
+      }
     }
   }
 }
