@@ -229,16 +229,23 @@ mad_status mad_topk(mad_ctx* ctx, uint32_t tprime, mad_pair* out_dev, uint32_t* 
  * (cand_dev, device), then the min(t, ncand) pairs with the largest |c|,
  * ties broken by smaller (i, j), sorted, written to out_dev with their x.
  * Uses the A and B given to mad_build_tables.  Candidates must be distinct
- * pairs with i < m, j < n.  Synchronises the stream. */
+ * pairs with i < m, j < n.  For 0/1 Gram inputs the first call after a
+ * table build (and a later call with more candidates) allocates,
+ * stream-ordered, a buffer that groups the candidates by their endpoint of
+ * larger degree (freed with the tables).  Synchronises the stream. */
 mad_status mad_rescore(mad_ctx* ctx, const mad_pair* cand_dev, uint32_t ncand, uint32_t t,
                        mad_pair* out_dev, uint32_t* n_out_host, mad_stream stream);
 
-/* ---- Fused pass for dense inputs (Alg. 2 then Alg. 3) ------------------ *
- * mad_pipeline_plan: fixes A and B (dense, their device buffers and
- * shapes), the budget s and t <= t' <= 131072, and allocates every table,
- * the hash (home regions for s diamonds) and the selection lists.  It
- * replaces any earlier tables of the context.  Synchronises.  Errors as
- * mad_build_tables; MAD_ERR_UNSUPPORTED for 0/1 inputs.
+/* ---- Fused pass (Alg. 2 then Alg. 3) ------------------------------------ *
+ * mad_pipeline_plan: fixes A and B (both dense row-major, or both 0/1 CSR:
+ * their device buffers and shapes), the budget s and t <= t' <= 131072,
+ * and allocates every table, the hash (dense: home regions for s diamonds)
+ * and the selection lists.  For 0/1 inputs it runs the step-wise build once
+ * (its pilot sizes the hash; the graph sizes the T2 guides and the closure
+ * filter), so the graph must not change between plan and run; only the
+ * contents of the same buffers may.  It replaces any earlier tables of the
+ * context.  Synchronises.  Errors as mad_build_tables; MAD_ERR_UNSUPPORTED
+ * for mixed formats and for MAD_WEDGE or MAD_ALIAS contexts.
  *
  * mad_pipeline_run: one whole pass over the current contents of A and B:
  * the tables, s diamonds (indices 0 .. s-1 of `seed`), Omega_t' and the
@@ -248,8 +255,9 @@ mad_status mad_rescore(mad_ctx* ctx, const mad_pair* cand_dev, uint32_t ncand, u
  * out_dev: t pairs (device), sorted as mad_rescore sorts them; counts_dev:
  * two uint32 (device), the number of candidates and of results; cand_dev
  * (optional, t' pairs, device): Omega_t', in no particular order.  Errors
- * found on the device (a compacted candidate list above 131072 entries, a
- * full overflow table of the hash) go to the device error word.  X after a
+ * found on the device (dense inputs: a compacted candidate list above 131072
+ * entries, a full overflow table of the hash; 0/1 inputs: a full hash) go
+ * to the device error word.  X after a
  * run (read by mad_export_x, mad_topk, mad_rescore) is the X of the step-wise
  * calls, laid out differently: for dense non-Gram inputs the home regions
  * are built whole and keys that do not fit go to an overflow table after
