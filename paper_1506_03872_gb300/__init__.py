@@ -254,8 +254,9 @@ def mad_rescore(ctx, cand, ncand: int, t: int, out=None, stream=None):
 
 def mad_pipeline_plan(ctx, A: mad_matrix, B: mad_matrix, s: int, tprime: int, t: int,
                       stream=None) -> None:
-    """Fix the dense inputs, the budget s and t <= t' of the fused pass and
-    allocate everything it uses (synchronises)."""
+    """Fix the inputs (both dense, or both 0/1 CSR), the budget s and
+    t <= t' of the fused pass and allocate everything it uses
+    (synchronises)."""
     _check(lib().mad_pipeline_plan(ctx, ctypes.byref(A), ctypes.byref(B), s, tprime, t,
                                    _stream(stream)), "mad_pipeline_plan")
 
