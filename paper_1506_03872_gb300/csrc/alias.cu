@@ -14,7 +14,8 @@
 //
 // One warp per table (a segment of up to kAliasSeg entries of a row, or a
 // row's table over its segment totals): the lanes load the weights into the
-// warp's shared memory and lane 0 runs the sequential method.
+// warp's shared memory and lane 0 runs the sequential method; rows of at
+// most 128 entries of a 32-bit prefix table take one thread per table.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -121,6 +122,81 @@ k_alias_build(const void* __restrict__ prefix, int prefix64, int64_t rows, int64
   }
 }
 
+// Short rows of a 32-bit prefix table (L <= kSmallAlias entries, one
+// segment): one thread per table runs the same construction, in the same
+// order, with 64-bit p (a weight is below 2^31 and n <= 128, so n x and X
+// stay below 2^38).  A warp per table left 31 of its lanes idle while lane 0
+// ran the sequential part.
+constexpr int kSmallAlias = 128;
+constexpr int kSmallThreads = 128;
+
+// Per-thread shared memory: p (8 bytes per entry), then the small and large
+// stacks (1 byte per entry); the stride is an odd number of 8-byte words so
+// that the threads' p arrays start in different banks.
+__host__ __device__ constexpr size_t small_alias_stride(int n) {
+  return ((((size_t)n * 10 + 7) & ~(size_t)7) | 8);
+}
+
+__global__ void __launch_bounds__(kSmallThreads)
+k_alias_build_small(const uint32_t* __restrict__ prefix, int64_t rows, int n,
+                    AliasEnt* __restrict__ ent, unsigned long long* __restrict__ seg,
+                    unsigned long long* __restrict__ rowX) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  unsigned char* mine = sm + (size_t)threadIdx.x * small_alias_stride(n);
+  unsigned long long* p = reinterpret_cast<unsigned long long*>(mine);
+  uint8_t* small = mine + (size_t)n * 8;
+  uint8_t* large = small + n;
+  const uint32_t* P = prefix + r * n;
+  unsigned long long X = 0;
+  uint32_t prev = 0;
+  for (int c = 0; c < n; ++c) {
+    const uint32_t cur = __ldg(P + c) & PREFIX_MASK;
+    const unsigned long long x = (unsigned long long)(cur - prev);
+    prev = cur;
+    p[c] = x * (unsigned long long)n;
+    X += x;
+  }
+  AliasEnt* out = ent + r * (n + 1);
+  int ns = 0, nl = 0;
+  for (int c = 0; c < n; ++c) {
+    if (p[c] < X) small[ns++] = (uint8_t)c;
+    else large[nl++] = (uint8_t)c;
+  }
+  while (ns > 0 && nl > 0) {
+    const int sc = small[--ns];
+    const int lc = large[--nl];
+    const unsigned long long ps = p[sc];
+    AliasEnt e;
+    e.t = ps;
+    e.a = (uint32_t)lc;
+    e.pad = 0;
+    out[sc] = e;
+    p[lc] -= X - ps;
+    if (p[lc] < X) small[ns++] = (uint8_t)lc;
+    else large[nl++] = (uint8_t)lc;
+  }
+  AliasEnt keep;
+  keep.t = X;
+  keep.pad = 0;
+  while (nl > 0) {
+    keep.a = large[--nl];
+    out[keep.a] = keep;
+  }
+  while (ns > 0) {
+    keep.a = small[--ns];
+    out[keep.a] = keep;
+  }
+  seg[r] = X;
+  rowX[r] = X;
+  AliasEnt top;
+  top.t = X;
+  top.a = 0;
+  top.pad = 0;
+  out[n] = top;
+}
+
 // The family over `rows` rows of length L of a prefix table.
 mad_status build_family(mad_ctx* ctx, int fam, const void* prefix, int prefix64, int64_t rows,
                         int64_t L, cudaStream_t st) {
@@ -137,6 +213,20 @@ mad_status build_family(mad_ctx* ctx, int fam, const void* prefix, int prefix64,
                         st)) != MAD_OK)
     return rs;
   ctx->al_nseg[fam] = (int)nseg;
+  if (!prefix64 && L <= kSmallAlias) {
+    const size_t smem = (size_t)kSmallThreads * small_alias_stride((int)L);
+    static size_t small_attr = 0;
+    if (small_attr < smem) {
+      cudaFuncSetAttribute(k_alias_build_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      small_attr = smem;
+    }
+    k_alias_build_small<<<(unsigned)((rows + kSmallThreads - 1) / kSmallThreads), kSmallThreads,
+                          smem, st>>>((const uint32_t*)prefix, rows, (int)L, ctx->al[fam],
+                                      ctx->al_seg[fam], ctx->al_row[fam]);
+    count_launch(ctx);
+    return cuda_status(cudaGetLastError());
+  }
   static size_t attr = 0;
   const int cap0 = (int)(L < kAliasSeg ? L : kAliasSeg);
   const size_t smem_max = kAliasWarps * alias_warp_bytes((int)kAliasSeg);
