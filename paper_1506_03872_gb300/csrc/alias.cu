@@ -26,25 +26,29 @@ namespace {
 
 constexpr int kAliasWarps = 4;   // tables per 128-thread block
 
-// Per-warp shared memory for a table of up to `cap` entries: p (128-bit),
-// then the small and large stacks (16-bit column indices), rounded up to 16
-// bytes so that every warp's p stays 16-byte aligned.
+// Per-warp shared memory for a table of up to `cap` entries: p (PT), then
+// the small and large stacks (16-bit column indices), rounded up to 16 bytes
+// so that every warp's p stays 16-byte aligned.  PT is 128-bit for the
+// 64-bit T1 weights and 64-bit for the 32-bit tables (their weights are
+// below 2^31, a segment total below 2^41 and n <= 1024, so n x < 2^51).
+template <typename PT>
 __host__ __device__ constexpr size_t alias_warp_bytes(int cap) {
-  return ((size_t)cap * 20 + 15) & ~(size_t)15;
+  return ((size_t)cap * (sizeof(PT) + 4) + 15) & ~(size_t)15;
 }
 
 // level 0: tables of the row segments, weights from a prefix table (u64
 // entries when prefix64, else u32 entries whose bit 31 is masked off);
 // level 1: tables over the segment totals of the rows with nseg > 1.
+template <typename PT>
 __global__ void __launch_bounds__(32 * kAliasWarps)
 k_alias_build(const void* __restrict__ prefix, int prefix64, int64_t rows, int64_t L, int nseg,
               int level, int cap, AliasEnt* __restrict__ ent, unsigned long long* __restrict__ seg,
               unsigned long long* __restrict__ rowX) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* mine = sm + (size_t)w * alias_warp_bytes(cap);
-  unsigned __int128* p = reinterpret_cast<unsigned __int128*>(mine);
-  uint16_t* small = reinterpret_cast<uint16_t*>(mine + (size_t)cap * 16);
+  unsigned char* mine = sm + (size_t)w * alias_warp_bytes<PT>(cap);
+  PT* p = reinterpret_cast<PT*>(mine);
+  uint16_t* small = reinterpret_cast<uint16_t*>(mine + (size_t)cap * sizeof(PT));
   uint16_t* large = small + cap;
   const int64_t tasks = level == 0 ? rows * nseg : rows;
   const int64_t task = (int64_t)blockIdx.x * kAliasWarps + w;
@@ -69,7 +73,7 @@ k_alias_build(const void* __restrict__ prefix, int prefix64, int64_t rows, int64
       const int64_t e = c0 + c;
       x = (unsigned long long)(P[e] & PREFIX_MASK) - (e ? (unsigned long long)(P[e - 1] & PREFIX_MASK) : 0ull);
     }
-    p[c] = (unsigned __int128)x * (unsigned long long)n;
+    p[c] = (PT)x * (PT)n;
     part += x;
   }
 #pragma unroll
@@ -79,7 +83,7 @@ k_alias_build(const void* __restrict__ prefix, int prefix64, int64_t rows, int64
   if (lane == 0) {
     int ns = 0, nl = 0;
     for (int c = 0; c < n; ++c) {
-      if (p[c] < (unsigned __int128)X) small[ns++] = (uint16_t)c;
+      if (p[c] < (PT)X) small[ns++] = (uint16_t)c;
       else large[nl++] = (uint16_t)c;
     }
     while (ns > 0 && nl > 0) {
@@ -91,8 +95,8 @@ k_alias_build(const void* __restrict__ prefix, int prefix64, int64_t rows, int64
       e.a = (uint32_t)lc;
       e.pad = 0;
       out[sc] = e;
-      p[lc] -= (unsigned __int128)(X - ps);
-      if (p[lc] < (unsigned __int128)X) small[ns++] = (uint16_t)lc;
+      p[lc] -= (PT)(X - ps);
+      if (p[lc] < (PT)X) small[ns++] = (uint16_t)lc;
       else large[nl++] = (uint16_t)lc;
     }
     AliasEnt keep;
@@ -197,6 +201,34 @@ k_alias_build_small(const uint32_t* __restrict__ prefix, int64_t rows, int n,
   out[n] = top;
 }
 
+// The warp kernels of a family: level 0 over its row segments, then level
+// 1 over the segment totals of rows with more than one segment.
+template <typename PT>
+void launch_warp_family(mad_ctx* ctx, int fam, const void* prefix, int prefix64, int64_t rows,
+                        int64_t L, int64_t nseg, cudaStream_t st) {
+  static size_t attr = 0;
+  const int cap0 = (int)(L < kAliasSeg ? L : kAliasSeg);
+  const size_t smem_max = kAliasWarps * alias_warp_bytes<PT>((int)kAliasSeg);
+  if (attr < smem_max) {
+    cudaFuncSetAttribute(k_alias_build<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_max);
+    attr = smem_max;
+  }
+  const int64_t t0 = rows * nseg;
+  k_alias_build<PT><<<(unsigned)((t0 + kAliasWarps - 1) / kAliasWarps), 32 * kAliasWarps,
+                      kAliasWarps * alias_warp_bytes<PT>(cap0), st>>>(
+      prefix, prefix64, rows, L, (int)nseg, 0, cap0, ctx->al[fam], ctx->al_seg[fam],
+      ctx->al_row[fam]);
+  count_launch(ctx);
+  if (nseg > 1) {
+    k_alias_build<PT><<<(unsigned)((rows + kAliasWarps - 1) / kAliasWarps), 32 * kAliasWarps,
+                        kAliasWarps * alias_warp_bytes<PT>((int)nseg), st>>>(
+        prefix, prefix64, rows, L, (int)nseg, 1, (int)nseg, ctx->al[fam], ctx->al_seg[fam],
+        ctx->al_row[fam]);
+    count_launch(ctx);
+  }
+}
+
 // The family over `rows` rows of length L of a prefix table.
 mad_status build_family(mad_ctx* ctx, int fam, const void* prefix, int prefix64, int64_t rows,
                         int64_t L, cudaStream_t st) {
@@ -227,26 +259,10 @@ mad_status build_family(mad_ctx* ctx, int fam, const void* prefix, int prefix64,
     count_launch(ctx);
     return cuda_status(cudaGetLastError());
   }
-  static size_t attr = 0;
-  const int cap0 = (int)(L < kAliasSeg ? L : kAliasSeg);
-  const size_t smem_max = kAliasWarps * alias_warp_bytes((int)kAliasSeg);
-  if (attr < smem_max) {
-    cudaFuncSetAttribute(k_alias_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
-    attr = smem_max;
-  }
-  const int64_t t0 = rows * nseg;
-  k_alias_build<<<(unsigned)((t0 + kAliasWarps - 1) / kAliasWarps), 32 * kAliasWarps,
-                  kAliasWarps * alias_warp_bytes(cap0), st>>>(
-      prefix, prefix64, rows, L, (int)nseg, 0, cap0, ctx->al[fam], ctx->al_seg[fam],
-      ctx->al_row[fam]);
-  count_launch(ctx);
-  if (nseg > 1) {
-    k_alias_build<<<(unsigned)((rows + kAliasWarps - 1) / kAliasWarps), 32 * kAliasWarps,
-                    kAliasWarps * alias_warp_bytes((int)nseg), st>>>(
-        prefix, prefix64, rows, L, (int)nseg, 1, (int)nseg, ctx->al[fam], ctx->al_seg[fam],
-        ctx->al_row[fam]);
-    count_launch(ctx);
-  }
+  if (prefix64)
+    launch_warp_family<unsigned __int128>(ctx, fam, prefix, prefix64, rows, L, nseg, st);
+  else
+    launch_warp_family<unsigned long long>(ctx, fam, prefix, prefix64, rows, L, nseg, st);
   return cuda_status(cudaGetLastError());
 }
 
