@@ -649,7 +649,7 @@ k_gemm_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
         const float g_theta0 = g_theta_next;
         if (filter) g_theta_next = __uint_as_float(*((volatile unsigned int*)args.g_theta));
-        // One verdict per warp: the TMEM loads below are warp-collective.
+        // One decision per warp: the TMEM loads below are warp-collective.
         const bool ok =
             __all_sync(0xFFFFFFFFu, mbar_wait(&sh->acc_full[buf], (uint32_t)((it >> 1) & 1), abort_flag));
         const int64_t row = rb * TM + row_in_tile;
